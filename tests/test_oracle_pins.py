@@ -1,0 +1,476 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every test here runs on the CPU.  Each one targets a part of the oracle so
+that a plausible mistake in that part (a dropped term, a wrong sign, index or
+weight) fails at least one of them:
+
+  multigrid sizes      -- the worked example of Sec. 2.2 (10 cells -> 10,5,3,1)
+  discrete fixed point -- dense direct solve (tiny grids), DST-I solve (larger)
+  Laplacian            -- exact on quadratics (both dimensions)
+  V-cycle pieces       -- residual reduction rate and cycle count (restriction,
+                          prolongation, ghost rule, smoother ordering)
+  interface            -- bi/trilinear interpolation exact on multilinear data
+  force stencil        -- Eq. 2 exact on quartics, central difference on quadratics
+  full method          -- Tables 1 and 2 (soft), second-order convergence
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.fft
+
+from paper_2001_02327_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(k=0):
+    return np.random.default_rng(I.BASE_SEED + k)
+
+
+def _block(dim, n):
+    return np.zeros((n + 4,) * dim)
+
+
+def _gamma(dim, n):
+    return tuple(slice(1, n + 3) for _ in range(dim))
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2: multigrid level sizes
+# --------------------------------------------------------------------------
+def test_mg_sizes_worked_example(oracle):
+    # "The number of cells ... of L=0 is 10" for the 8-cell patch of Fig. 1d
+    assert oracle.mg_sizes(10) == [10, 5, 3, 1]
+
+
+@pytest.mark.parametrize("M", [4, 6, 10, 34, 50, 66, 98, 130, 258, 1026])
+def test_mg_sizes_invariants(oracle, M):
+    N = oracle.mg_sizes(M)
+    assert N[0] == M and N[-1] == 1 and all(v > 1 for v in N[:-1])
+    for L in range(1, len(N)):
+        # cells of size 2^L/M must cover [0,1] to within half a cell
+        assert abs(N[L] * 2 ** L - M) <= 2 ** (L - 1)
+        assert abs(N[L - 1] - 2 * N[L]) <= 1
+
+
+# --------------------------------------------------------------------------
+# the discrete system a converged level solve must satisfy
+# --------------------------------------------------------------------------
+def _dirichlet_system(dim, n, h, phi_block, f):
+    """Dense matrix of the 5/7-point Laplacian on the M^d cells of Gamma with
+    the outer ring of phi_block moved to the right-hand side."""
+    M = n + 2
+    idx = np.arange(M ** dim).reshape((M,) * dim)
+    A = np.zeros((M ** dim, M ** dim))
+    b = f.reshape(-1).copy()
+    for c in np.ndindex(*(M,) * dim):
+        r = idx[c]
+        A[r, r] = -2.0 * dim / h ** 2
+        for a in range(dim):
+            for s in (-1, 1):
+                q = list(c)
+                q[a] += s
+                if 0 <= q[a] < M:
+                    A[r, idx[tuple(q)]] = 1.0 / h ** 2
+                else:
+                    qq = tuple(v + 1 for v in q)
+                    b[r] -= phi_block[qq] / h ** 2
+    return A, b
+
+
+def _random_level(dim, n, k):
+    rng = _rng(k)
+    phi = _block(dim, n)
+    phi[...] = rng.standard_normal(phi.shape)
+    phi[_gamma(dim, n)] = 0.0
+    rho = _block(dim, n)
+    rho[_gamma(dim, n)] = rng.standard_normal((n + 2,) * dim)
+    return phi, rho
+
+
+@pytest.mark.parametrize("dim,n", [(2, 2), (2, 6), (2, 8), (3, 2), (3, 4), (3, 6)])
+def test_fixed_point_dense(oracle, dim, n):
+    h = 0.37 / n
+    fourpiG = 4 * np.pi * 0.8
+    phi, rho = _random_level(dim, n, dim * 100 + n)
+    A, b = _dirichlet_system(dim, n, h, phi, fourpiG * rho[_gamma(dim, n)])
+    ref = np.linalg.solve(A, b).reshape((n + 2,) * dim)
+    cyc, hist = oracle.level_solve(dim, n, h, phi, rho, fourpiG, 2, 1, 200, 1e-14)
+    got = phi[_gamma(dim, n)]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def _dst_solve(dim, n, h, phi_block, f):
+    """Direct solve by sine-transform diagonalisation (type-I DST)."""
+    M = n + 2
+    A0, b = None, f.copy()
+    g = (M,) * dim
+    for a in range(dim):
+        for side, s_out, s_in in ((-1, 0, 0), (1, M + 1, M - 1)):
+            sl_out = [slice(1, M + 1)] * dim
+            sl_out[dim - 1 - a] = s_out
+            sl_in = [slice(None)] * dim
+            sl_in[dim - 1 - a] = s_in
+            b[tuple(sl_in)] -= phi_block[tuple(sl_out)] / h ** 2
+    k = np.arange(1, M + 1)
+    lam1 = (2 * np.cos(np.pi * k / (M + 1)) - 2) / h ** 2
+    lam = sum(np.meshgrid(*([lam1] * dim), indexing="ij"))
+    bh = scipy.fft.dstn(b, type=1)
+    return scipy.fft.idstn(bh / lam, type=1)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 62), (3, 30)])
+def test_fixed_point_dst(oracle, dim, n):
+    h = 1.0 / n
+    fourpiG = 4 * np.pi
+    phi, rho = _random_level(dim, n, 7 + n)
+    ref = _dst_solve(dim, n, h, phi, fourpiG * rho[_gamma(dim, n)])
+    oracle.level_solve(dim, n, h, phi, rho, fourpiG, 2, 1, 200, 1e-14)
+    got = phi[_gamma(dim, n)]
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_dst_solver_matches_dense():
+    """The DST reference itself, against the dense solve."""
+    dim, n, h = 3, 4, 0.1
+    phi, rho = _random_level(dim, n, 3)
+    f = rho[_gamma(dim, n)]
+    A, b = _dirichlet_system(dim, n, h, phi, f)
+    ref = np.linalg.solve(A, b).reshape((n + 2,) * dim)
+    assert np.allclose(_dst_solve(dim, n, h, phi, f), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dim,n", [(2, 14), (3, 10), (3, 12)])
+def test_quadratic_is_reproduced_exactly(oracle, dim, n):
+    """The 5/7-point Laplacian is exact on quadratics, so the discrete solution
+    with a quadratic's boundary values and constant RHS is that quadratic."""
+    rng = _rng(5)
+    h = 0.05
+    c = rng.uniform(-1, 1, size=12)
+    ax = (np.arange(-2, n + 2) + 0.5) * h
+    G = np.meshgrid(*([ax] * dim), indexing="ij")[::-1]  # x,y(,z) arrays in C order
+    x, y = G[0], G[1]
+    z = G[2] if dim == 3 else 0 * x
+    q = c[0] * x * x + c[1] * y * y + c[3] * x * y + c[5] * x + c[6] * y + c[8]
+    lap = 2 * (c[0] + c[1])
+    if dim == 3:
+        q = q + c[2] * z * z + c[4] * y * z + c[9] * x * z + c[7] * z
+        lap += 2 * c[2]
+    fourpiG = 4 * np.pi * 1.3
+    phi = q.copy()
+    phi[_gamma(dim, n)] = 0.0
+    rho = _block(dim, n)
+    rho[_gamma(dim, n)] = lap / fourpiG
+    oracle.level_solve(dim, n, h, phi, rho, fourpiG, 2, 1, 100, 1e-14)
+    assert np.max(np.abs(phi - q)) <= 1e-11 * np.max(np.abs(q))
+
+
+# --------------------------------------------------------------------------
+# the V-cycle: convergence rate independent of N (Sec. 3.1/3.2 remarks)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, 32), (2, 64), (2, 128), (3, 16), (3, 32)])
+def test_vcycle_rate(oracle, dim, n):
+    phi, rho = _random_level(dim, n, 11)
+    phi[...] = 0.0
+    cyc, hist = oracle.level_solve(dim, n, 1.0 / n, phi, rho, 1.0, 2, 1, 60, 1e-10)
+    rates = hist[1:] / hist[:-1]
+    assert cyc <= 20, cyc
+    assert np.max(rates[2:]) < 0.3, rates
+
+
+def test_vcycle_nu_2_2_faster(oracle):
+    dim, n = 3, 16
+    phi, rho = _random_level(dim, n, 12)
+    phi[...] = 0
+    p2 = phi.copy()
+    c21, _ = oracle.level_solve(dim, n, 1.0 / n, phi, rho, 1.0, 2, 1, 60, 1e-10)
+    c22, _ = oracle.level_solve(dim, n, 1.0 / n, p2, rho, 1.0, 2, 2, 60, 1e-10)
+    assert c22 <= c21
+
+
+# --------------------------------------------------------------------------
+# interface (Sec. 2.1 buffer zone, Appendix A weights)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interface_exact_on_multilinear(oracle, dim):
+    rng = _rng(21)
+    n_p, n_c = 16, 12
+    off = [3, 5, 4][:dim]
+    hp = 0.1
+    a = rng.uniform(-1, 1, size=8)
+
+    def field(X):
+        x, y = X[..., 0], X[..., 1]
+        z = X[..., 2] if dim == 3 else 0.0
+        return a[0] + a[1] * x + a[2] * y + a[3] * z + a[4] * x * y + a[5] * y * z + a[6] * x * z + a[7] * x * y * z
+
+    def centres(lo, h, n, pad):
+        ax = [lo[k] + (np.arange(-pad, n + pad) + 0.5) * h for k in range(dim)]
+        g = np.meshgrid(*ax[::-1], indexing="ij")
+        return np.stack(g[::-1], axis=-1)
+
+    lo_p = [0.0] * dim
+    lo_c = [o * hp for o in off]
+    Xp = centres(lo_p, hp, n_p, 2)
+    phi_p = field(Xp)
+    rho_p = 2.0 * field(Xp) + 1.0
+    phi_c = _block(dim, n_c)
+    rho_c = _block(dim, n_c)
+    oracle.interface_fill(dim, n_p, phi_p, rho_p, n_c, off, phi_c, rho_c, guess=True)
+    Xc = centres(lo_c, hp / 2, n_c, 2)
+    exact = field(Xc)
+    # outer ring and Gamma (initial guess) carry the potential ...
+    assert np.allclose(phi_c, exact, atol=1e-13)
+    # ... the inner ring the density
+    ring = np.zeros((n_c + 4,) * dim, dtype=bool)
+    ring[_gamma(dim, n_c)] = True
+    ring[tuple(slice(2, n_c + 2) for _ in range(dim))] = False
+    assert np.allclose(rho_c[ring], 2.0 * exact[ring] + 1.0, atol=1e-13)
+
+
+def test_interface_zero_guess(oracle):
+    dim, n_p, n_c = 3, 8, 8
+    phi_p = np.ones((n_p + 4,) * 3)
+    rho_p = np.ones((n_p + 4,) * 3)
+    phi_c = _block(dim, n_c) + 7.0
+    rho_c = _block(dim, n_c)
+    oracle.interface_fill(dim, n_p, phi_p, rho_p, n_c, [2, 2, 2], phi_c, rho_c, guess=False)
+    assert np.all(phi_c[_gamma(dim, n_c)] == 0.0)
+    assert phi_c[0, 5, 5] == 1.0
+
+
+# --------------------------------------------------------------------------
+# force stencils (Eq. 2; F = -grad Phi)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_force_eq2_exact_on_quartic(oracle, dim):
+    n, h = 10, 0.07
+    ax = (np.arange(-2, n + 2) + 0.5) * h - 0.3
+    G = np.meshgrid(*([ax] * dim), indexing="ij")[::-1]
+    x, y = G[0], G[1]
+    z = G[2] if dim == 3 else 0 * x
+    phi = x ** 4 - 2 * y ** 3 * x + 0.5 * y ** 4 + 3 * x * y + (z ** 4 - x * z ** 3 if dim == 3 else 0)
+    gx = 4 * x ** 3 - 2 * y ** 3 + 3 * y - (z ** 3 if dim == 3 else 0)
+    gy = -6 * y ** 2 * x + 2 * y ** 3 + 3 * x
+    gz = 4 * z ** 3 - 3 * x * z ** 2
+    F = oracle.forces(dim, n, h, np.ascontiguousarray(phi), 0)
+    inner = tuple(slice(2, n + 2) for _ in range(dim))
+    grads = [gx, gy, gz][:dim]
+    for a in range(dim):
+        assert np.allclose(F[a], -grads[a][inner], rtol=0, atol=1e-11)
+
+
+def test_force_cd2_exact_on_quadratic(oracle):
+    dim, n, h = 3, 8, 0.1
+    ax = (np.arange(-2, n + 2) + 0.5) * h
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    phi = np.ascontiguousarray(x * x - 3 * x * y + 2 * z * z + z)
+    F = oracle.forces(dim, n, h, phi, 1)
+    inner = (slice(2, n + 2),) * 3
+    assert np.allclose(F[0], -(2 * x - 3 * y)[inner], atol=1e-12)
+    assert np.allclose(F[1], (3 * x)[inner], atol=1e-12)
+    assert np.allclose(F[2], -(4 * z + 1)[inner], atol=1e-12)
+    # and Eq. 2 is not the two-point difference: on a cubic they differ
+    phi3 = np.ascontiguousarray(x ** 3)
+    assert not np.allclose(oracle.forces(dim, n, h, phi3, 1)[0], oracle.forces(dim, n, h, phi3, 0)[0])
+
+
+# --------------------------------------------------------------------------
+# analytic density/potential pairs used as inputs and as error references
+# --------------------------------------------------------------------------
+def test_paper_sphere_closed_form():
+    """The paper's printed n=2 expressions (Sec. 3.2) against the general
+    polytrope formula of the input generator."""
+    r0 = 0.25
+    Mb = 32 * np.pi * r0 ** 3 / 105
+    s = I.PolySphere((0.0, 0.0, 0.0), r0, 1.0, 2)
+    assert abs(s.mass - Mb) < 1e-15
+    r = np.linspace(0.0, 1.0, 41)
+    X = np.stack([r, 0 * r, 0 * r], axis=-1)
+    Phi = np.where(r <= r0, -2 / 3 * np.pi * r0 ** 2 + 4 * np.pi * (r ** 2 / 6 - r ** 4 / (10 * r0 ** 2) + r ** 6 / (42 * r0 ** 4)),
+                   -Mb / np.maximum(r, 1e-300))
+    fr = np.where(r <= r0, -4 * np.pi * (r / 3 - 2 * r ** 3 / (5 * r0 ** 2) + r ** 5 / (7 * r0 ** 4)), -Mb / np.maximum(r, 1e-100) ** 2)
+    assert np.allclose(s.potential(X, 1.0), Phi, rtol=1e-13, atol=1e-15)
+    assert np.allclose(s.force(X, 1.0)[:, 0], fr, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("src,dim", [(I.PolySphere((0.05, 0.03, 0.02), 0.3, 1.0, 3), 3),
+                                     (I.PolySphere((0.0, 0.01, -0.02), 0.2, 2.0, 2), 3),
+                                     (I.PolyDisk((0.03, -0.01), 0.5, 1.0, 4), 2),
+                                     (I.SoftDisk2D(0.3), 2)])
+def test_closed_forms_satisfy_poisson(src, dim):
+    """Finite-difference Laplacian of Phi -> 4 pi G rho at second order, and
+    the force is minus the gradient of the potential."""
+    G = 0.7 if not isinstance(src, I.SoftDisk2D) else 1 / (4 * np.pi)
+    rng = _rng(31)
+    X = rng.uniform(-0.45, 0.45, size=(64, dim))
+    errs = []
+    for d in (1e-2, 5e-3):
+        lap = -2 * dim * src.potential(X, G)
+        for a in range(dim):
+            e = np.zeros(dim)
+            e[a] = d
+            lap = lap + src.potential(X + e, G) + src.potential(X - e, G)
+        errs.append(np.max(np.abs(lap / d ** 2 - 4 * np.pi * G * src.density(X))))
+    assert errs[1] < errs[0] / 3.0 or errs[1] < 1e-6
+    d = 1e-5
+    for a in range(dim):
+        e = np.zeros(dim)
+        e[a] = d
+        g = (src.potential(X + e, G) - src.potential(X - e, G)) / (2 * d)
+        assert np.allclose(src.force(X, G)[:, a], -g, atol=1e-6)
+
+
+def test_sphere_mass_by_quadrature():
+    s = I.PolySphere.from_mass((0.0, 0.0, 0.0), 0.2, 1.5, 3)
+    r = np.linspace(0, 0.2, 20001)
+    rho = s.density(np.stack([r, 0 * r, 0 * r], -1))
+    m = np.trapezoid(4 * np.pi * r * r * rho, r)
+    assert abs(m - 1.5) < 1e-6
+    # n = 3: M = 64 pi rho0 R^3 / 315
+    assert abs(s.mass - 64 * np.pi * s.rho0 * 0.2 ** 3 / 315) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# the full method: Tables 1 and 2 and second-order convergence
+# --------------------------------------------------------------------------
+def _table(name):
+    rows = {}
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = line.split()
+        rows[int(v[0])] = [float(t) for t in v[1:]]
+    return rows
+
+
+def _run(oracle, H, nu=(2, 1), tol=1e-10):
+    from oracle import norms as NR
+    res = oracle.solve_hierarchy(H, I.level_inputs(H), nu[0], nu[1], 60, tol)
+    return res, NR.hierarchy_norms(H, res)
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+def test_table1_2d(oracle, N):
+    ref = _table("table1_2d.txt")[N]
+    res, nm = _run(oracle, I.paper_2d(N))
+    got = list(nm["x"]) + list(nm["R"])
+    for g, r in zip(got, ref):
+        assert 0.85 <= g / r <= 1.15, (g, r)
+    # the L-infinity columns agree more tightly
+    assert abs(got[2] / ref[2] - 1) < 0.05 and abs(got[5] / ref[5] - 1) < 0.05
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_table2_3d(oracle, N):
+    ref = _table("table2_3d.txt")[N]
+    res, nm = _run(oracle, I.paper_3d(N))
+    got = list(nm["x"]) + list(nm["r" if False else "R"])
+    for g, r in zip(got, ref):
+        assert 0.78 <= g / r <= 1.22, (g, r)
+    assert abs(got[2] / ref[2] - 1) < 0.06 and abs(got[5] / ref[5] - 1) < 0.06
+
+
+def test_table1_orders(oracle):
+    """Second order in L1, L2 and L-infinity under grid doubling (Table 1)."""
+    prev = None
+    for N in (32, 64, 128):
+        _, nm = _run(oracle, I.paper_2d(N))
+        cur = np.array(list(nm["x"]) + list(nm["R"]) + list(nm["phi"]))
+        if prev is not None:
+            order = np.log2(prev / cur)
+            assert np.all(order > 1.85) and np.all(order < 2.2), order
+        prev = cur
+
+
+def test_second_order_3d_offset_sphere(oracle):
+    """Potential and force of the offset compact sphere, 4 nested levels:
+    second order in all three norms."""
+    prev = None
+    for n in (16, 32):
+        _, nm = _run(oracle, I.config_3d_offset_sphere(n), nu=(2, 2))
+        cur = np.array(list(nm["x"]) + list(nm["R"]) + list(nm["phi"]))
+        if prev is not None:
+            order = np.log2(prev / cur)
+            assert np.all(order > 1.7), order
+        prev = cur
+
+
+def test_symmetric_problem_symmetric_solution(oracle):
+    H = I.paper_3d(16)
+    res, _ = _run(oracle, H, tol=1e-13)
+    for lev in res:
+        p = lev["phi"][(slice(1, -1),) * 3]
+        for ax in range(3):
+            assert np.allclose(p, np.flip(p, axis=ax), rtol=0, atol=1e-11 * np.abs(p).max())
+        assert np.allclose(p, np.transpose(p, (1, 0, 2)), rtol=0, atol=1e-11 * np.abs(p).max())
+
+
+def test_zero_problem(oracle):
+    dim, n = 3, 6
+    phi, rho = _block(dim, n), _block(dim, n)
+    cyc, hist = oracle.level_solve(dim, n, 0.1, phi, rho, 1.0, 2, 1, 10, 1e-10)
+    assert cyc == 0 and np.all(phi == 0)
+
+
+def test_composite_norm_weights():
+    from oracle import norms as NR
+    H = I.paper_2d(8)
+    errs = [np.full((8, 8), 1.0) for _ in range(4)]
+    n1, n2, ni = NR.norms(H, errs)
+    # composite grid tiles the base domain [-0.5,0.5]^2 exactly once
+    assert abs(n1 - 1.0) < 1e-14 and abs(n2 - 1.0) < 1e-14 and ni == 1.0
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.4: ghost values of the coarse multigrid levels
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("M,L", [(66, 1), (66, 2), (66, 3), (66, 5), (10, 2), (50, 2), (50, 4), (34, 3)])
+def test_mg_ghost_rule_exact_on_lines_through_zero(oracle, M, L):
+    """Phi = 0 on the boundary of Gamma: the left ghost reflects oddly about
+    x_MG = 0 and the right ghost extrapolates linearly through zero at x_MG = 1
+    (Eq. for the right buffer value in Sec. 2.4; at x_N = 1 it is -Phi_{N-1}).
+    Both are exact for straight lines vanishing at that end."""
+    N = oracle.mg_sizes(M)[L]
+    h = 2 ** L / M
+    x = (np.arange(0, N + 2) - 0.5) * h                   # centres incl. ghosts
+    tie = abs((N - 0.5) * h - 1.0) < 1e-15
+    for dim in (2, 3):
+        for axis in range(dim):
+            shape = [1] * dim
+            shape[dim - 1 - axis] = N + 2
+            for line, side in ((x, "left"), (1.0 - x, "right")):
+                phi = np.broadcast_to(line.reshape(shape), (N + 2,) * dim).copy()
+                sel = [slice(1, N + 1)] * dim
+                sel[dim - 1 - axis] = 0 if side == "left" else N + 1
+                want = phi[tuple(sel)].copy()
+                phi[tuple(sel)] = 12345.0
+                assert oracle.fill_ghosts(dim, M, L, phi) == N
+                assert np.allclose(phi[tuple(sel)], want, rtol=0, atol=1e-14), (side, tie)
+
+
+@pytest.mark.parametrize("M,L", [(66, 1), (66, 2), (66, 3), (66, 6), (10, 2), (50, 2), (34, 3), (34, 4)])
+def test_mg_operator_uses_ghost_rule(oracle, M, L):
+    """The coarse-level operator equals the plain 5/7-point Laplacian applied
+    after the ghost layer has been filled by the rule (Sec. 2.4: the boundary
+    value is updated with the updated potential)."""
+    rng = _rng(40 + L)
+    N = oracle.mg_sizes(M)[L]
+    h = 2.0 ** L
+    for dim in (2, 3):
+        phi = np.zeros((N + 2,) * dim)
+        act = (slice(1, N + 1),) * dim
+        phi[act] = rng.standard_normal((N,) * dim)
+        f = rng.standard_normal(phi.shape)
+        r = oracle.mg_residual(dim, M, L, phi, f)
+        ext = phi.copy()
+        oracle.fill_ghosts(dim, M, L, ext)
+        lap = -2 * dim * ext[act]
+        for a in range(dim):
+            for s in (-1, 1):
+                sl = [slice(1, N + 1)] * dim
+                sl[a] = slice(1 + s, N + 1 + s)
+                lap = lap + ext[tuple(sl)]
+        want = f[act] - lap / h ** 2
+        assert np.allclose(r[act], want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
