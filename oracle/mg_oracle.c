@@ -58,13 +58,13 @@ static long cells(int dim, int E) { return dim == 3 ? (long)E * E * E : (long)E 
  * ------------------------------------------------------------------------- */
 int or_mg_sizes(int M, int *N, int cap)
 {
-    double hL = 1.0 / (double)M;
+    /* 1/h^L = M / 2^L is evaluated exactly (a division by a power of two),
+     * so that halves are recognised and rounded up */
     int L = 0;
     N[0] = M;
     while (N[L] > 1 && L + 1 < cap) {
-        hL = 2.0 * hL;
         L++;
-        N[L] = (int)floor(1.0 / hL + 0.5);
+        N[L] = (int)floor((double)M / (double)(1 << L) + 0.5);
     }
     return L + 1;
 }
@@ -74,13 +74,17 @@ static void make_levels(int M, double h_fine, or_mglev *lv, int *nL)
     int N[OR_MAX_MG];
     int n = or_mg_sizes(M, N, OR_MAX_MG);
     for (int L = 0; L < n; L++) {
-        double hL = (double)(1 << L) / (double)M;      /* normalised size */
-        double xN = ((double)N[L] - 0.5) * hL;         /* centre of cell N */
+        /* in units of 1/(2M): x_N = (2N-1) 2^L and h^L = 2 * 2^L, so both
+         * the tie test x_N = 1 and the ratio (1 - x_N - h)/(1 - x_N) are
+         * formed from exact integers */
+        double twoM = 2.0 * (double)M;
+        double xN2 = (2.0 * (double)N[L] - 1.0) * (double)(1 << L);
+        double hL2 = 2.0 * (double)(1 << L);
         lv[L].N = N[L];
         lv[L].L = L;
         lv[L].h = h_fine * (double)(1 << L);
-        lv[L].tie = (xN == 1.0);
-        lv[L].cR = lv[L].tie ? 0.0 : (1.0 - xN - hL) / (1.0 - xN);
+        lv[L].tie = (xN2 == twoM);
+        lv[L].cR = lv[L].tie ? 0.0 : (twoM - xN2 - hL2) / (twoM - xN2);
     }
     *nL = n;
 }

@@ -42,9 +42,12 @@ def _gamma(dim, n):
 def test_mg_sizes_worked_example(oracle):
     # "The number of cells ... of L=0 is 10" for the 8-cell patch of Fig. 1d
     assert oracle.mg_sizes(10) == [10, 5, 3, 1]
+    # the same half-up rounding of exact halves at other levels and sizes
+    assert oracle.mg_sizes(93)[:3] == [93, 47, 23]
+    assert oracle.mg_sizes(66)[:4] == [66, 33, 17, 8]
 
 
-@pytest.mark.parametrize("M", [4, 6, 10, 34, 50, 66, 98, 130, 258, 1026])
+@pytest.mark.parametrize("M", [4, 6, 10, 34, 50, 66, 93, 98, 99, 130, 258, 1026])
 def test_mg_sizes_invariants(oracle, M):
     N = oracle.mg_sizes(M)
     assert N[0] == M and N[-1] == 1 and all(v > 1 for v in N[:-1])
