@@ -1,0 +1,381 @@
+"""Benchmark: finest-level zones/s to 1e-10 relative residual.
+
+Workload: 3D, base 64^3 on [-1,1]^3 plus 3 nested 64^3 levels (ratio 2,
+centred), compact polynomial sphere rho = (1 - r^2/R^2)^3, R = 0.3, centred at
+(0.05, 0.03, 0.02), G = 1, closed-form Dirichlet outer boundary, V(2,2)
+cycles to 1e-10 relative residual per level, forces by Eq. 2.  Zones are the
+cells whose potential and force are returned: 4 * 64^3 per solve.
+
+One step = set the density of every level (device to device), solve all
+levels coarse to fine, compute potential and forces of every level.  Steps
+are timed one by one with CUDA events on the solver's stream; a 256 MiB
+buffer (larger than the 129 MB L2) is written between steps, outside the
+timed events.  Forms: plain FP64, and FP32 V-cycles inside FP64 defect
+correction ("mixed").  `value` is the fastest form whose results stay within
+1e-2 of the discretisation error of the FP64 result.
+
+--impl reference times the CPU FP64 oracle on the same workload (one full
+solve per step) on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2001_02327_gb300 import inputs as I  # noqa: E402
+
+METRIC = "finest-level zones/s to 1e-10 rel. residual: plain FP64 vs mixed/learned"
+UNIT = "zones/s"
+WORKLOAD = "3D nested 4x64^3, offset compact sphere (m=3, R=0.3), V(2,2) to 1e-10 rel. residual, Eq. 2 forces"
+NU = (2, 2)
+TOL = 1e-10
+
+
+def make_workload():
+    H = I.config_3d_offset_sphere(64, 4)
+    return H, I.level_inputs(H)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu_id), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+class Runner:
+    """One hierarchy resident on the GPU plus its inputs and outputs."""
+
+    def __init__(self, mg, torch, H, inp, stream, precision):
+        self.mg, self.torch, self.H = mg, torch, H
+        self.stream = stream
+        self.opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=precision,
+                              inner_cycles=3, stream=stream)
+        self.h = mg.mg_create_hierarchy([mg.desc_from(H)], self.opt)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        self.d_in = [{k: dev(v) for k, v in d.items()} for d in inp]
+        self.d_phi = [torch.zeros((n,) * 3, dtype=torch.float64, device="cuda") for n in H.n]
+        self.d_F = [torch.zeros((3,) + (n,) * 3, dtype=torch.float64, device="cuda") for n in H.n]
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        self.h_in = [{k: pin(v) for k, v in d.items()} for d in inp]
+        self.h_phi = [torch.zeros((n,) * 3, dtype=torch.float64).pin_memory().numpy() for n in H.n]
+        self.h_F = [torch.zeros((3,) + (n,) * 3, dtype=torch.float64).pin_memory().numpy() for n in H.n]
+        self.stats = None
+
+    def step(self, host=False):
+        mg = self.mg
+        src = self.h_in if host else self.d_in
+        for l in range(self.H.num_levels):
+            if l == 0:
+                mg.mg_set_density(self.h, 0, 0, src[0]["rho"], src[0]["bc_rho"], src[0]["bc_phi"])
+            else:
+                mg.mg_set_density(self.h, 0, l, src[l]["rho"])
+        _, self.stats = mg.mg_solve(self.h, 1)
+        for l in range(self.H.num_levels):
+            if host:
+                mg.mg_forces(self.h, 0, l, self.h_phi[l], self.h_F[l])
+            else:
+                mg.mg_forces(self.h, 0, l, self.d_phi[l], self.d_F[l])
+
+    def io_bytes(self):
+        h2d = sum(a.nbytes for d in self.h_in for a in d.values())
+        d2h = sum(a.nbytes for a in self.h_phi) + sum(a.nbytes for a in self.h_F)
+        return h2d, d2h
+
+    def results(self):
+        self.torch.cuda.synchronize()
+        return [(p.cpu().numpy(), F.cpu().numpy()) for p, F in zip(self.d_phi, self.d_F)]
+
+    def close(self):
+        self.mg.mg_destroy(self.h)
+
+
+def time_device(runner, torch, steps, warmup, flush):
+    s = runner.stream
+    for _ in range(warmup):
+        runner.step()
+    torch.cuda.synchronize()
+    times = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+        ev[k][0].record(s)
+        runner.step()
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def time_e2e(runner, torch, steps):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        runner.step(host=True)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3 / steps
+
+
+def profile_pass(runner, torch, steps):
+    mg = runner.mg
+    mg.mg_profile(runner.h, 1)
+    for _ in range(steps):
+        runner.step()
+    prof = mg.mg_profile_read(runner.h)
+    mg.mg_profile(runner.h, 0)
+    return prof
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = os.path.join(ROOT, "paper_2001_02327_gb300", "csrc", "mg_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    ent = d.get(name)
+    if not ent or ent.get("csrc_sha256") != sha:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(H, inp):
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
+    dt = time.perf_counter() - t0
+    return {"value": H.zones() / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full solve of the workload (all 4 levels, forces included), {dt:.2f} s, single thread"}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+
+    H, inp = make_workload()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    forms = {}
+    results = {}
+    for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+        r = Runner(mg, torch, H, inp, stream, prec)
+        try:
+            r.step()
+            torch.cuda.synchronize()
+            results[name] = r.results()
+            cyc = [r.stats[0][l]["cycles"] for l in range(H.num_levels)]
+            if ws > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            sampler = ClockSampler(getattr(torch.cuda.get_device_properties(local), "uuid", local)) \
+                if name == "fp64" else None
+            if sampler:
+                sampler.start()
+            times = time_device(r, torch, args.steps, args.warmup, flush)
+            clocks = sampler.stop() if sampler else None
+            total = sum(times)
+            if ws > 1:
+                t = torch.tensor([total], dtype=torch.float64, device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                total = float(t.item())
+            ms = total / args.steps
+            e2e_ms = time_e2e(r, torch, max(3, args.steps // 2))
+            h2d, d2h = r.io_bytes()
+            prof = profile_pass(r, torch, max(3, min(args.steps, 10)))
+            nprof = max(3, min(args.steps, 10))
+            forms[name] = {"value": ws * H.zones() / (ms * 1e-3), "ms_per_step": ms,
+                           "ms_min": min(times), "cycles": cyc, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h,
+                           "prof": {k: (v[0] / nprof, v[1] / nprof, v[2] / nprof) for k, v in prof.items()},
+                           "clocks": clocks}
+        finally:
+            r.close()
+
+    # accuracy of the mixed form against FP64 (error budget: 1e-2 of the discretisation error)
+    ok_mixed = True
+    worst = 0.0
+    for l in range(H.num_levels):
+        X = H.centres(l, 0)
+        p64, F64 = results["fp64"][l]
+        pm, Fm = results["mixed"][l]
+        disc = np.max(np.abs(p64 - H.potential(X)))
+        discF = np.max(np.abs(np.moveaxis(F64, 0, -1) - H.force(X)))
+        e = max(np.max(np.abs(pm - p64)) / disc, np.max(np.abs(Fm - F64)) / discF)
+        worst = max(worst, e)
+        ok_mixed &= bool(e < 1e-2)
+    best = "mixed" if ok_mixed and forms["mixed"]["value"] > forms["fp64"]["value"] else "fp64"
+    fb = forms[best]
+
+    # roofline of the dominant kernel of the reported form
+    kname, (kl, kms, kbytes) = max(fb["prof"].items(), key=lambda kv: kv[1][1])
+    launch_ms = kms / kl
+    per_launch_bytes = kbytes / kl
+    peak, peak_src = measured_peaks()
+    achieved = per_launch_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = kernel_traffic(kname)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
+                "launch_us": round(launch_ms * 1e3, 2), "bytes_per_launch": per_launch_bytes,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
+
+    launches = int(round(sum(v[0] for v in fb["prof"].values()))) * args.steps
+    out = {
+        "metric": METRIC, "value": fb["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": fb["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if best == "fp64" else "f32+f64",
+        "data": "synthetic (closed-form density and boundary potential)",
+        "config": {"workload": WORKLOAD, "zones_per_solve": H.zones(), "levels": H.num_levels, "n": 64,
+                   "nu": list(NU), "rel_tol": TOL, "form": best, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "forms": {k: {"zones_per_s": v["value"], "ms_per_step": v["ms_per_step"], "cycles_per_level": v["cycles"],
+                      "kernels": {kk: {"launches": round(vv[0], 1), "ms": round(vv[1], 4)} for kk, vv in v["prof"].items()}}
+                  for k, v in forms.items()},
+        "mixed_error_vs_fp64_over_discretisation": worst,
+        "e2e": {"value": ws * H.zones() / (fb["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": fb["h2d"],
+                "d2h_bytes_per_step": fb["d2h"]},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": forms["fp64"]["clocks"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(H, inp)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    H, inp = make_workload()
+    for _ in range(args.warmup):
+        O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = H.zones() / dt
+    sample = "one full solve of the workload per step (all 4 levels, forces included), single thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form density and boundary potential)",
+        "config": {"workload": WORKLOAD, "zones_per_solve": H.zones(), "levels": H.num_levels, "n": 64,
+                   "nu": list(NU), "rel_tol": TOL, "form": "oracle"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

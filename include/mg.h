@@ -1,0 +1,187 @@
+/*
+ * mg.h -- C ABI of the GB300 nested-grid multigrid Poisson solver
+ * (Wang & Yen, "Self-gravitational Force Calculation of Second Order Accuracy
+ * Using Multigrid Method on Nested Grids").
+ *
+ * The problem (Eq. 1): lap(Phi) = 4 pi G rho, F = -grad(Phi), on a nested
+ * hierarchy of square (2D) or cubic (3D) patches Omega^0 superset Omega^1 ...
+ * with refinement ratio 2 (Sec. 2.1).  Densities are point values at cell
+ * centres.  Levels are solved one at a time from coarse to fine (the one-way
+ * scheme, Sec. 2.1): each finer level gets its Dirichlet potential (outer
+ * buffer ring) and the density of its inner buffer ring by linear
+ * interpolation from its parent, then is solved by multigrid V-cycles
+ * (Sec. 2.3) with red-black Gauss-Seidel smoothing, averaging restriction,
+ * bi/trilinear prolongation and the anti-symmetric ghost rule of Sec. 2.4 on
+ * the coarse multigrid levels.  Forces come from the fourth-order difference
+ * of Eq. 2.
+ *
+ * Conventions common to every call
+ *   - Arrays are C order with x fastest: 3D index (k*n + j)*n + i, 2D j*n + i.
+ *   - Array pointers may be host or device memory; the library inspects each
+ *     pointer (cudaPointerGetAttributes) and copies on the hierarchy's stream.
+ *     It never keeps a caller pointer after a call returns.  Host pointers make
+ *     the call synchronous with respect to that stream.
+ *   - The library owns all its device memory (allocated in
+ *     mg_create_hierarchy, freed in mg_destroy) and runs on one GPU, the
+ *     current device at creation.
+ *   - Calls on one handle are not thread-safe.  Errors are returned, never
+ *     raised; after MG_ECUDA or MG_ETIMEOUT the handle answers MG_ESTATE to
+ *     everything but mg_destroy.  mg_error_message() gives the detail.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_MAX_LEVELS 8   /* refinement levels per hierarchy */
+
+typedef struct mg_hierarchy mg_hierarchy;   /* opaque; owns all device state */
+
+typedef enum {
+    MG_OK = 0,
+    MG_EINVAL = 1,      /* bad argument (message says which) */
+    MG_ENOMEM = 2,      /* device or host allocation failed */
+    MG_ECUDA = 3,       /* a CUDA call failed; handle poisoned */
+    MG_ESTATE = 4,      /* call out of order, or handle poisoned */
+    MG_ENOCONV = 5,     /* max_cycles reached above rel_tol (results are valid, unconverged) */
+    MG_EDIVERGED = 6,   /* residual became NaN/Inf */
+    MG_ETIMEOUT = 7     /* a bounded device-side wait gave up */
+} mg_status;
+
+enum { MG_FP64 = 0,        /* every step in FP64 */
+       MG_MIXED = 1 };     /* FP32 V-cycles inside FP64 defect correction */
+
+enum { MG_GUESS_INTERP = 0,  /* initial potential interpolated from the parent (Sec. 2.4) */
+       MG_GUESS_ZERO = 1,    /* zero initial potential */
+       MG_GUESS_USER = 2 };  /* initial potential supplied by mg_set_guess */
+
+enum { MG_FORCE_EQ2 = 0,     /* fourth-order difference of Eq. 2 (default) */
+       MG_FORCE_CD2 = 1 };   /* two-point central difference */
+
+/* Geometry of one hierarchy (Sec. 2.1).  Level l has n[l] cells per edge
+ * (even, >= 4), lower corner lo[l] and cell size h0 / 2^l.  For l > 0 the
+ * patch must sit on parent cell faces, its lower corner o[a] whole parent
+ * cells above the parent's, with 1 <= o[a] <= n[l-1] - n[l]/2 - 1 so that
+ * every buffer cell interpolates from cells the parent solves for. */
+typedef struct {
+    int dim;                          /* 2 or 3 */
+    int num_levels;                   /* 1..MG_MAX_LEVELS, level 0 is the base */
+    int n[MG_MAX_LEVELS];
+    double lo[MG_MAX_LEVELS][3];
+    double h0;                        /* cell size of level 0 (> 0) */
+    double G;                         /* gravitational constant of Eq. 1 */
+} mg_hierarchy_desc;
+
+/* Solver options; mg_default_options fills the paper's choices. */
+typedef struct {
+    int nu_pre;          /* Gauss-Seidel sweeps before restriction (paper: 2, Sec. 3) */
+    int nu_post;         /* sweeps after prolongation (paper: 1) */
+    int max_cycles;      /* V-cycle limit per level (FP64: V-cycles; MIXED: FP32 V-cycles) */
+    double rel_tol;      /* stop when ||f - lap Phi||_2 / ||f - lap Phi_0||_2 < rel_tol over
+                            the solved cells, Phi_0 being zero inside with the same boundary;
+                            0 runs exactly max_cycles cycles */
+    int precision;       /* MG_FP64 | MG_MIXED */
+    int inner_cycles;    /* MIXED: FP32 V-cycles per FP64 defect-correction step (>= 1) */
+    int guess;           /* MG_GUESS_* for levels > 0 (level 0 starts from zero, or USER) */
+    int force_stencil;   /* MG_FORCE_EQ2 | MG_FORCE_CD2 */
+    void *stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
+} mg_options;
+
+/* Per (hierarchy, level) result of mg_solve. */
+typedef struct {
+    int cycles;          /* V-cycles run (FP32 V-cycles in MIXED mode) */
+    int outer_steps;     /* MIXED: FP64 defect-correction steps; FP64: equal to cycles */
+    double rel_res;      /* final ||r||_2 / ||b||_2 (FP64) */
+    double b_norm;       /* ||b||_2 */
+    int status;          /* MG_OK, MG_ENOCONV or MG_EDIVERGED */
+} mg_level_stats;
+
+/* Fill *opt with nu_pre = 2, nu_post = 1 (Sec. 3), max_cycles = 50,
+ * rel_tol = 1e-10, MG_FP64, inner_cycles = 3, MG_GUESS_INTERP, MG_FORCE_EQ2,
+ * stream NULL.  Returns MG_EINVAL if opt is NULL. */
+mg_status mg_default_options(mg_options *opt);
+
+/* Create `batch` independent hierarchies (Sec. 2.1 data structure) with
+ * descriptions descs[0..batch-1], allocate all their device memory and build
+ * the multigrid level sizes of every refinement level (Sec. 2.2: the solved
+ * region of n+2 cells per edge, halved until one active cell remains, sizes
+ * rounded half up).  opt may be NULL (defaults).  On success *out owns the
+ * memory; on failure *out is NULL.  Errors: MG_EINVAL (geometry violates the
+ * nesting rules above, batch < 1, bad options), MG_ENOMEM, MG_ECUDA. */
+mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const mg_options *opt,
+                              mg_hierarchy **out);
+
+/* Give hierarchy b its density on level `level` (Sec. 2.1: point values at
+ * the cell centres of Omega^level).
+ *   rho     n^d values on Omega^level.
+ *   bc_rho  level 0 only: (n+2)^d density at the centres of Omega^0 plus one
+ *           ring; only the ring (the inner buffer layer) is read.
+ *   bc_phi  level 0 only: (n+4)^d potential at the centres of Omega^0 plus two
+ *           rings; only the outer ring (the Dirichlet layer) is read.
+ * For level > 0 both must be NULL: the interface of Sec. 2.1 fills them from
+ * the parent during mg_solve.  Every level of a hierarchy must be set before
+ * mg_solve.  Errors: MG_EINVAL, MG_ESTATE, MG_ECUDA. */
+mg_status mg_set_density(mg_hierarchy *h, int b, int level, const double *rho, const double *bc_rho,
+                         const double *bc_phi);
+
+/* Optional initial potential of hierarchy b on `level`: (n+2)^d values on
+ * the solved region (Omega plus the inner ring), used when opt.guess is
+ * MG_GUESS_USER (for level 0 it replaces the zero start whatever the guess
+ * mode).  Must follow mg_set_density for that level.  The call only records
+ * the values; they are copied in when the level's solve starts. */
+mg_status mg_set_guess(mg_hierarchy *h, int b, int level, const double *phi0);
+
+/* Solve every hierarchy, every level, coarse to fine (Sec. 2.1 one-way
+ * scheme; Sec. 2.3 multigrid iteration).  stats, if not NULL, receives
+ * batch * MG_MAX_LEVELS entries (entry b*MG_MAX_LEVELS + level).
+ * Returns MG_OK when every level reached rel_tol, MG_ENOCONV if some level
+ * stopped at max_cycles (results still usable), MG_EDIVERGED on a non-finite
+ * residual, MG_ESTATE if a density is missing, MG_ECUDA. */
+mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats);
+
+/* Results of hierarchy b on `level` after mg_solve.
+ *   phi_out  n^d potential on Omega^level, or NULL.
+ *   F_out    dim * n^d force F = -grad(Phi) (Eq. 1) by Eq. 2 (or the two-point
+ *            difference), component a at F_out[a * n^d + cell]; or NULL.
+ * Errors: MG_EINVAL, MG_ESTATE (no solve yet), MG_ECUDA. */
+mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out);
+
+/* Release everything; NULL-safe; always MG_OK. */
+mg_status mg_destroy(mg_hierarchy *h);
+
+/* Static description of a status code. */
+const char *mg_status_str(mg_status s);
+
+/* Detail of the last error on h (empty string if none); valid until the next
+ * call on h.  h may be NULL (reports the last creation error). */
+const char *mg_error_message(const mg_hierarchy *h);
+
+/* Per-kernel timing, for measurement (not part of the method).  While
+ * enabled, every kernel launch of the handle is bracketed by CUDA events on
+ * its stream; mg_profile_read synchronises that stream and reports, per
+ * kernel kind, the launch count, the summed event time and the summed
+ * algorithmic bytes (the minimal DRAM traffic each launch must move).
+ * mg_profile(h, 0/1) also clears the totals. */
+typedef struct {
+    char name[32];
+    long launches;
+    double ms;
+    double bytes;
+} mg_kernel_stat;
+mg_status mg_profile(mg_hierarchy *h, int enable);
+/* Fills up to cap entries; returns how many kernel kinds ran, or -1. */
+int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap);
+
+/* Multigrid level sizes of Sec. 2.2 for a solved region of M cells per edge:
+ * writes up to cap sizes into N and returns how many levels there are. */
+int mg_level_sizes(int M, int *N, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

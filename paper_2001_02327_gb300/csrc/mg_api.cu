@@ -1,0 +1,739 @@
+// mg_api.cu -- C ABI (include/mg.h) and host driver of the nested-grid
+// multigrid Poisson solver.  Each refinement level is solved by V-cycles
+// (Sec. 2.3) after the one-way interface has filled its buffer rings from the
+// parent (Sec. 2.1); all arithmetic runs in the kernels of mg_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+
+namespace {
+
+struct LevelData {
+    int n = 0, M = 0, nmg = 0;
+    int off[3] = {0, 0, 0};
+    double h = 0.0;
+    MgGeom g[MG_MAX_MG];
+    double *phi[MG_MAX_MG] = {};   // phi[0]: the (n+4)^d level block
+    double *f[MG_MAX_MG] = {};     // f[0]:   4 pi G rho on the same block
+    float *phi32[MG_MAX_MG] = {};  // mixed precision correction, all multigrid levels
+    float *f32[MG_MAX_MG] = {};
+    double *rho = nullptr;         // (n+4)^d density (Omega and inner ring)
+    double *guess = nullptr;       // (n+2)^d optional initial potential
+    bool density_set = false, guess_set = false;
+};
+
+long cells(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
+
+// Sec. 2.2: N^L = round(M / 2^L), halves rounded up, until N^L = 1.
+int level_sizes(int M, int *N, int cap)
+{
+    int L = 0;
+    N[0] = M;
+    while (N[L] > 1 && L + 1 < cap) {
+        L++;
+        // floor(M / 2^L + 1/2) in integers
+        N[L] = (int)(((long)M + (1L << (L - 1))) >> L);
+    }
+    return L + 1;
+}
+
+void build_geometry(LevelData &ld, int dim)
+{
+    int N[MG_MAX_MG];
+    ld.M = ld.n + 2;
+    ld.nmg = level_sizes(ld.M, N, MG_MAX_MG);
+    (void)dim;
+    for (int L = 0; L < ld.nmg; L++) {
+        MgGeom &g = ld.g[L];
+        g.N = N[L];
+        g.E = N[L] + 2;
+        g.L = L;
+        // x_N = (N - 1/2) 2^L / M; tie <=> (2N - 1) 2^L == 2M
+        const long num = 2L * ld.M - (2L * N[L] + 1) * (1L << L);   // 2M (1 - x_N - h^L)
+        const long den = 2L * ld.M - (2L * N[L] - 1) * (1L << L);   // 2M (1 - x_N)
+        g.tie = (den == 0);
+        g.cR = g.tie ? 0.0 : (double)num / (double)den;
+        const double hL = ld.h * (double)(1L << L);
+        g.h2 = hL * hL;
+        g.inv_h2 = 1.0 / g.h2;
+    }
+}
+
+enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
+                  KK_SETDENS, KK_COUNT };
+const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
+                                         "defect",        "accumulate",     "interface",       "forces",
+                                         "set_density"};
+
+// Per-launch CUDA-event timing on the hierarchy's stream (mg_profile).
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec { int kind; size_t e0; double bytes; };
+    std::vector<Rec> recs;
+    long launches[KK_COUNT] = {};
+    double ms[KK_COUNT] = {};
+    double bytes[KK_COUNT] = {};
+};
+
+}  // namespace
+
+struct mg_hierarchy {
+    int batch = 0, dim = 0;
+    std::vector<mg_hierarchy_desc> desc;
+    std::vector<std::vector<LevelData>> lev;   // [b][l]
+    mg_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    double *stage = nullptr;        // device staging for host-pointer I/O
+    size_t stage_elems = 0;
+    double *partials = nullptr;     // MG_NORM_BLOCKS
+    double *scal = nullptr;         // device scalars: [b][l][2] = ||b||^2, ||r||^2
+    double *hscal = nullptr;        // pinned mirror
+    bool poisoned = false, solved = false;
+    std::string err;
+    Profiler prof;
+};
+
+namespace {
+
+std::string g_create_error;
+
+mg_status fail(mg_hierarchy *h, mg_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return s;
+}
+
+mg_status fail_cuda(mg_hierarchy *h, cudaError_t e, const char *what)
+{
+    if (h)
+        h->poisoned = true;
+    return fail(h, MG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess)                        \
+            return fail_cuda((h), e_, #call);         \
+    } while (0)
+
+// Launch through `fn`, bracketed by events when profiling is on.
+template <class Fn>
+cudaError_t timed(mg_hierarchy *h, int kind, double bytes, Fn &&fn)
+{
+    Profiler &P = h->prof;
+    if (!P.on)
+        return fn();
+    while (P.used + 2 > P.pool.size()) {
+        cudaEvent_t e;
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess)
+            return ce;
+        P.pool.push_back(e);
+    }
+    const size_t e0 = P.used;
+    P.used += 2;
+    cudaError_t ce = cudaEventRecord(P.pool[e0], h->stream);
+    if (ce == cudaSuccess)
+        ce = fn();
+    if (ce == cudaSuccess)
+        ce = cudaEventRecord(P.pool[e0 + 1], h->stream);
+    P.recs.push_back({kind, e0, bytes});
+    return ce;
+}
+
+cudaError_t profile_flush(mg_hierarchy *h)
+{
+    Profiler &P = h->prof;
+    if (P.recs.empty())
+        return cudaSuccess;
+    cudaError_t ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess)
+        return ce;
+    for (const auto &r : P.recs) {
+        float ms = 0.f;
+        ce = cudaEventElapsedTime(&ms, P.pool[r.e0], P.pool[r.e0 + 1]);
+        if (ce != cudaSuccess)
+            return ce;
+        P.launches[r.kind]++;
+        P.ms[r.kind] += ms;
+        P.bytes[r.kind] += r.bytes;
+    }
+    P.recs.clear();
+    P.used = 0;
+    return cudaSuccess;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mg_status check_options(const mg_options &o)
+{
+    if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 || !(o.rel_tol >= 0.0) ||
+        (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 ||
+        o.guess < MG_GUESS_INTERP || o.guess > MG_GUESS_USER ||
+        (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2))
+        return MG_EINVAL;
+    return MG_OK;
+}
+
+mg_status check_desc(const mg_hierarchy_desc &d, int b, int dim0)
+{
+    if (d.dim != 2 && d.dim != 3)
+        return fail(nullptr, MG_EINVAL, "hierarchy %d: dim must be 2 or 3", b);
+    if (d.dim != dim0)
+        return fail(nullptr, MG_EINVAL, "hierarchy %d: all hierarchies of a batch share one dim", b);
+    if (d.num_levels < 1 || d.num_levels > MG_MAX_LEVELS)
+        return fail(nullptr, MG_EINVAL, "hierarchy %d: num_levels %d out of range", b, d.num_levels);
+    if (!(d.h0 > 0.0) || !std::isfinite(d.h0) || !std::isfinite(d.G))
+        return fail(nullptr, MG_EINVAL, "hierarchy %d: h0 must be positive and G finite", b);
+    for (int l = 0; l < d.num_levels; l++) {
+        const int n = d.n[l];
+        if (n < 2 || n + 2 > (1 << (MG_MAX_MG - 1)) || (l > 0 && (n & 1)))
+            return fail(nullptr, MG_EINVAL, "hierarchy %d level %d: n=%d (need >= 2, even above level 0)", b, l, n);
+        if (l == 0)
+            continue;
+        const double hp = d.h0 / (double)(1L << (l - 1));
+        for (int a = 0; a < d.dim; a++) {
+            const double o = (d.lo[l][a] - d.lo[l - 1][a]) / hp;
+            const double r = std::floor(o + 0.5);
+            if (std::fabs(o - r) > 1e-6)
+                return fail(nullptr, MG_EINVAL, "hierarchy %d level %d axis %d: patch not on parent cell faces", b, l, a);
+            if (r < 1.0 || r > (double)(d.n[l - 1] - n / 2 - 1))
+                return fail(nullptr, MG_EINVAL,
+                            "hierarchy %d level %d axis %d: offset %g outside [1, %d] parent cells", b, l, a, r,
+                            d.n[l - 1] - n / 2 - 1);
+        }
+    }
+    return MG_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// --------------------------------------------------------------------------
+// the V-cycle of Sec. 2.3 on the arrays of one refinement level
+// --------------------------------------------------------------------------
+double cells_d(int N, int dim) { return dim == 3 ? (double)N * N * N : (double)N * N; }
+
+cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int sweeps)
+{
+    const int dim = h->dim;
+    const MgGeom &g = ld.g[L];
+    void *phi = fp32 ? (void *)ld.phi32[L] : (void *)ld.phi[L];
+    const void *f = fp32 ? (const void *)ld.f32[L] : (const void *)ld.f[L];
+    const double bytes = 2.0 * (fp32 ? 4 : 8) * cells_d(g.N, dim);   // read Phi, read/write one colour
+    for (int sw = 0; sw < sweeps; sw++)
+        for (int c = 0; c < 2; c++) {
+            cudaError_t e = timed(h, KK_SMOOTH, bytes, [&] { return mg_launch_smooth(dim, fp32, phi, f, g, c, h->stream); });
+            if (e)
+                return e;
+        }
+    return cudaSuccess;
+}
+
+// the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level
+cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32)
+{
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    cudaStream_t s = h->stream;
+    const int w = fp32 ? 4 : 8;
+    auto P = [&](int L) -> void * { return fp32 ? (void *)ld.phi32[L] : (void *)ld.phi[L]; };
+    auto F = [&](int L) -> void * { return fp32 ? (void *)ld.f32[L] : (void *)ld.f[L]; };
+    cudaError_t e;
+    if (ld.nmg == 1)
+        return smooth(h, ld, 0, fp32, o.nu_pre + o.nu_post);
+    if ((e = smooth(h, ld, 0, fp32, o.nu_pre)))                                           // step 2
+        return e;
+    int L = 0;
+    do {
+        const double by = 2.0 * w * (cells_d(ld.g[L].N, dim) + cells_d(ld.g[L + 1].N, dim));
+        e = timed(h, KK_RESTRICT, by, [&] {
+            return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s);
+        });                                                                               // steps 4-5
+        if (e)
+            return e;
+        const int sweeps = ld.g[L + 1].N == 1 ? (o.nu_pre > 0 ? 1 : 0) : o.nu_pre;       // one cell: exact
+        if ((e = smooth(h, ld, L + 1, fp32, sweeps)))                                     // step 6
+            return e;
+        L++;
+    } while (ld.g[L].N > 1 && L + 1 < ld.nmg);                                            // step 8
+    do {
+        const double by = w * (cells_d(ld.g[L].N, dim) + 2.0 * cells_d(ld.g[L - 1].N, dim));
+        e = timed(h, KK_PROLONG, by, [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
+        if (e)                                                                            // step 10
+            return e;
+        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post)))                                  // step 11
+            return e;
+        L--;
+    } while (L > 0);                                                                      // step 13
+    return cudaSuccess;
+}
+
+cudaError_t resid_norm(mg_hierarchy *h, const LevelData &ld, bool zero_inside, double *out)
+{
+    return timed(h, KK_NORM, 16.0 * cells_d(ld.g[0].N, h->dim), [&] {
+        return mg_launch_resid_norm2(h->dim, ld.phi[0], ld.f[0], ld.g[0], zero_inside, h->partials, out, h->stream);
+    });
+}
+
+mg_status read_scalars(mg_hierarchy *h, int b, int l, double &b2, double &r2)
+{
+    double *ds = h->scal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
+    double *hs = h->hscal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
+    CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    b2 = hs[0];
+    r2 = hs[1];
+    return MG_OK;
+}
+
+mg_status solve_level(mg_hierarchy *h, int b, int l, mg_level_stats *st)
+{
+    const mg_hierarchy_desc &d = h->desc[b];
+    LevelData &ld = h->lev[b][l];
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    cudaStream_t s = h->stream;
+    const double fourpiG = 4.0 * M_PI * d.G;
+    double *ds = h->scal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
+
+    if (l > 0) {
+        const LevelData &pd = h->lev[b][l - 1];
+        int gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
+        const double by = 8.0 * cells_d(ld.n + 4, dim) + 16.0 * (cells_d(ld.n + 2, dim) - cells_d(ld.n, dim));
+        CK(h, timed(h, KK_IFACE, by, [&] {
+               return mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2],
+                                          ld.phi[0], ld.rho, ld.f[0], fourpiG, gmode, ld.guess, s);
+           }));
+    } else if (ld.guess_set) {
+        CK(h, mg_launch_copy_guess(dim, ld.n, ld.guess, ld.phi[0], s));
+    }
+    CK(h, resid_norm(h, ld, true, ds));
+    CK(h, resid_norm(h, ld, false, ds + 1));
+    double b2, r2;
+    mg_status rs = read_scalars(h, b, l, b2, r2);
+    if (rs)
+        return rs;
+    const double bn = std::sqrt(b2);
+    double rel = bn > 0.0 ? std::sqrt(r2) / bn : 0.0;
+    int cycles = 0, outer = 0;
+    int status = MG_OK;
+    const bool mixed = o.precision == MG_MIXED;
+    while (bn > 0.0 && cycles < o.max_cycles && !(rel < o.rel_tol)) {
+        if (!mixed) {
+            CK(h, vcycle(h, ld, false));
+            cycles++;
+        } else {
+            const double nd = cells_d(ld.g[0].N, dim);
+            CK(h, timed(h, KK_DEFECT, 24.0 * nd, [&] {
+                   return mg_launch_defect(dim, ld.phi[0], ld.f[0], ld.g[0], ld.f32[0], ld.phi32[0], s);
+               }));
+            for (int c = 0; c < o.inner_cycles && cycles < o.max_cycles; c++) {
+                CK(h, vcycle(h, ld, true));
+                cycles++;
+            }
+            CK(h, timed(h, KK_ACCUM, 20.0 * nd,
+                        [&] { return mg_launch_accumulate(dim, ld.phi[0], ld.phi32[0], ld.g[0], s); }));
+        }
+        outer++;
+        CK(h, resid_norm(h, ld, false, ds + 1));
+        rs = read_scalars(h, b, l, b2, r2);
+        if (rs)
+            return rs;
+        rel = std::sqrt(r2) / bn;
+        if (!std::isfinite(rel)) {
+            status = MG_EDIVERGED;
+            break;
+        }
+    }
+    if (status == MG_OK && bn > 0.0 && !(rel < o.rel_tol) && o.rel_tol > 0.0)
+        status = MG_ENOCONV;
+    if (st) {
+        st->cycles = cycles;
+        st->outer_steps = mixed ? outer : cycles;
+        st->rel_res = rel;
+        st->b_norm = bn;
+        st->status = status;
+    }
+    return (mg_status)status;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+mg_status mg_default_options(mg_options *opt)
+{
+    if (!opt)
+        return MG_EINVAL;
+    opt->nu_pre = 2;
+    opt->nu_post = 1;
+    opt->max_cycles = 50;
+    opt->rel_tol = 1e-10;
+    opt->precision = MG_FP64;
+    opt->inner_cycles = 3;
+    opt->guess = MG_GUESS_INTERP;
+    opt->force_stencil = MG_FORCE_EQ2;
+    opt->stream = nullptr;
+    return MG_OK;
+}
+
+int mg_level_sizes(int M, int *N, int cap)
+{
+    if (M < 1 || !N || cap < 1)
+        return 0;
+    return level_sizes(M, N, cap);
+}
+
+const char *mg_status_str(mg_status s)
+{
+    switch (s) {
+    case MG_OK: return "MG_OK";
+    case MG_EINVAL: return "MG_EINVAL: invalid argument";
+    case MG_ENOMEM: return "MG_ENOMEM: out of memory";
+    case MG_ECUDA: return "MG_ECUDA: CUDA error";
+    case MG_ESTATE: return "MG_ESTATE: call out of order or handle poisoned";
+    case MG_ENOCONV: return "MG_ENOCONV: not converged within max_cycles";
+    case MG_EDIVERGED: return "MG_EDIVERGED: residual not finite";
+    case MG_ETIMEOUT: return "MG_ETIMEOUT: device wait timed out";
+    }
+    return "unknown mg_status";
+}
+
+const char *mg_error_message(const mg_hierarchy *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const mg_options *opt, mg_hierarchy **out)
+{
+    g_create_error.clear();
+    if (!out)
+        return fail(nullptr, MG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!descs || batch < 1)
+        return fail(nullptr, MG_EINVAL, "descs is NULL or batch < 1");
+    mg_options o;
+    mg_default_options(&o);
+    if (opt)
+        o = *opt;
+    if (check_options(o))
+        return fail(nullptr, MG_EINVAL, "invalid options");
+    for (int b = 0; b < batch; b++) {
+        mg_status s = check_desc(descs[b], b, descs[0].dim);
+        if (s)
+            return s;
+    }
+    mg_hierarchy *h = new (std::nothrow) mg_hierarchy();
+    if (!h)
+        return fail(nullptr, MG_ENOMEM, "host allocation failed");
+    h->batch = batch;
+    h->dim = descs[0].dim;
+    h->desc.assign(descs, descs + batch);
+    h->opt = o;
+    h->stream = (cudaStream_t)o.stream;
+    const int dim = h->dim;
+    if (h->stream) {
+        // run on the device the caller's stream belongs to
+        int sd = -1;
+        if (cudaStreamGetDevice(h->stream, &sd) == cudaSuccess && sd >= 0)
+            cudaSetDevice(sd);
+        cudaGetLastError();
+    }
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, MG_ECUDA, "no CUDA device");
+    }
+
+    // geometry and arena layout
+    h->lev.resize(batch);
+    size_t bytes = 0, stage = 0;
+    struct Slot { void **dst; size_t bytes; };
+    std::vector<Slot> slots;
+    for (int b = 0; b < batch; b++) {
+        const mg_hierarchy_desc &d = descs[b];
+        h->lev[b].resize(d.num_levels);
+        for (int l = 0; l < d.num_levels; l++) {
+            LevelData &ld = h->lev[b][l];
+            ld.n = d.n[l];
+            ld.h = d.h0 / (double)(1L << l);
+            if (l > 0) {
+                const double hp = d.h0 / (double)(1L << (l - 1));
+                for (int a = 0; a < dim; a++)
+                    ld.off[a] = (int)std::floor((d.lo[l][a] - d.lo[l - 1][a]) / hp + 0.5);
+            }
+            build_geometry(ld, dim);
+            for (int L = 0; L < ld.nmg; L++) {
+                const size_t c = (size_t)cells(ld.g[L].E, dim);
+                slots.push_back({(void **)&ld.phi[L], align256(c * sizeof(double))});
+                slots.push_back({(void **)&ld.f[L], align256(c * sizeof(double))});
+                if (o.precision == MG_MIXED) {
+                    slots.push_back({(void **)&ld.phi32[L], align256(c * sizeof(float))});
+                    slots.push_back({(void **)&ld.f32[L], align256(c * sizeof(float))});
+                }
+            }
+            slots.push_back({(void **)&ld.rho, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
+            slots.push_back({(void **)&ld.guess, align256((size_t)cells(ld.n + 2, dim) * sizeof(double))});
+            const size_t st = std::max((size_t)cells(ld.n + 4, dim) * 3, (size_t)cells(ld.n, dim) * (dim + 1));
+            stage = std::max(stage, st);
+        }
+    }
+    h->stage_elems = stage;
+    slots.push_back({(void **)&h->stage, align256(stage * sizeof(double))});
+    slots.push_back({(void **)&h->partials, align256(MG_NORM_BLOCKS * sizeof(double))});
+    slots.push_back({(void **)&h->scal, align256((size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double))});
+    for (auto &sl : slots)
+        bytes += sl.bytes;
+    cudaError_t e = cudaMalloc((void **)&h->arena, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, MG_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    h->arena_bytes = bytes;
+    size_t pos = 0;
+    for (auto &sl : slots) {
+        *sl.dst = h->arena + pos;
+        pos += sl.bytes;
+    }
+    e = cudaMallocHost((void **)&h->hscal, (size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->arena);
+        delete h;
+        return fail(nullptr, MG_ENOMEM, "pinned host allocation failed");
+    }
+    // ghost layers and rings start at zero
+    e = mg_launch_zero(h->arena, bytes, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h->hscal);
+        cudaFree(h->arena);
+        delete h;
+        return fail(nullptr, MG_ECUDA, "arena initialisation failed: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return MG_OK;
+}
+
+mg_status mg_set_density(mg_hierarchy *h, int b, int level, const double *rho, const double *bc_rho,
+                         const double *bc_phi)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (b < 0 || b >= h->batch || level < 0 || level >= h->desc[b].num_levels)
+        return fail(h, MG_EINVAL, "hierarchy %d level %d out of range", b, level);
+    if (!rho)
+        return fail(h, MG_EINVAL, "rho is NULL");
+    if (level == 0 && (!bc_rho || !bc_phi))
+        return fail(h, MG_EINVAL, "level 0 needs bc_rho and bc_phi");
+    if (level > 0 && (bc_rho || bc_phi))
+        return fail(h, MG_EINVAL, "bc_rho/bc_phi must be NULL above level 0 (the interface fills them)");
+    LevelData &ld = h->lev[b][level];
+    const int dim = h->dim;
+    const size_t nr = (size_t)cells(ld.n, dim), nb = (size_t)cells(ld.n + 2, dim), np = (size_t)cells(ld.n + 4, dim);
+    const double *d_rho = rho, *d_bcr = bc_rho, *d_bcp = bc_phi;
+    double *stage = h->stage;
+    if (!is_device_ptr(rho)) {
+        CK(h, cudaMemcpyAsync(stage, rho, nr * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        d_rho = stage;
+    }
+    if (level == 0) {
+        if (!is_device_ptr(bc_rho)) {
+            CK(h, cudaMemcpyAsync(stage + np, bc_rho, nb * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d_bcr = stage + np;
+        }
+        if (!is_device_ptr(bc_phi)) {
+            CK(h, cudaMemcpyAsync(stage + 2 * np, bc_phi, np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d_bcp = stage + 2 * np;
+        }
+    }
+    const double fourpiG = 4.0 * M_PI * h->desc[b].G;
+    CK(h, timed(h, KK_SETDENS, 24.0 * (double)nr, [&] {
+           return mg_launch_set_density(dim, ld.n, d_rho, d_bcr, d_bcp, ld.rho, ld.f[0], ld.phi[0], fourpiG,
+                                        h->stream);
+       }));
+    if (d_rho == stage || d_bcr == stage + np || d_bcp == stage + 2 * np)
+        CK(h, cudaStreamSynchronize(h->stream));   // the staging area is reused by the next call
+    ld.density_set = true;
+    ld.guess_set = false;
+    h->solved = false;
+    return MG_OK;
+}
+
+mg_status mg_set_guess(mg_hierarchy *h, int b, int level, const double *phi0)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (b < 0 || b >= h->batch || level < 0 || level >= h->desc[b].num_levels || !phi0)
+        return fail(h, MG_EINVAL, "bad hierarchy/level or NULL phi0");
+    LevelData &ld = h->lev[b][level];
+    if (!ld.density_set)
+        return fail(h, MG_ESTATE, "mg_set_guess before mg_set_density");
+    const size_t nb = (size_t)cells(ld.n + 2, h->dim);
+    CK(h, cudaMemcpyAsync(ld.guess, phi0, nb * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (!is_device_ptr(phi0))
+        CK(h, cudaStreamSynchronize(h->stream));
+    ld.guess_set = true;
+    return MG_OK;
+}
+
+mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    for (int b = 0; b < h->batch; b++)
+        for (int l = 0; l < h->desc[b].num_levels; l++)
+            if (!h->lev[b][l].density_set)
+                return fail(h, MG_ESTATE, "density of hierarchy %d level %d not set", b, l);
+    mg_status worst = MG_OK;
+    for (int b = 0; b < h->batch; b++) {
+        for (int l = 0; l < h->desc[b].num_levels; l++) {
+            mg_level_stats st{};
+            mg_status s = solve_level(h, b, l, &st);
+            if (s == MG_ECUDA || s == MG_ETIMEOUT)
+                return s;
+            if (stats)
+                stats[(size_t)b * MG_MAX_LEVELS + l] = st;
+            if (s == MG_EDIVERGED || (s == MG_ENOCONV && worst == MG_OK))
+                worst = s;
+        }
+    }
+    h->solved = true;
+    return worst;
+}
+
+mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (b < 0 || b >= h->batch || level < 0 || level >= h->desc[b].num_levels)
+        return fail(h, MG_EINVAL, "hierarchy %d level %d out of range", b, level);
+    if (!h->solved)
+        return fail(h, MG_ESTATE, "mg_forces before mg_solve");
+    const LevelData &ld = h->lev[b][level];
+    const int dim = h->dim;
+    const size_t nr = (size_t)cells(ld.n, dim);
+    const bool phi_dev = phi_out && is_device_ptr(phi_out);
+    const bool F_dev = F_out && is_device_ptr(F_out);
+    double *dF = F_out ? (F_dev ? F_out : h->stage) : nullptr;
+    double *dP = phi_out ? (phi_dev ? phi_out : h->stage + (size_t)dim * nr) : nullptr;
+    if (!dF) {
+        // potential only: the kernel still needs somewhere to write forces
+        dF = h->stage;
+        if (phi_out && !phi_dev)
+            dP = h->stage + (size_t)dim * nr;
+    }
+    CK(h, timed(h, KK_FORCES, 8.0 * (cells_d(ld.n + 4, dim) + (dim + 1) * (double)nr), [&] {
+           return mg_launch_forces(dim, ld.n, ld.h, ld.phi[0], dF, dP, h->opt.force_stencil, h->stream);
+       }));
+    bool sync = false;
+    if (F_out && !F_dev) {
+        CK(h, cudaMemcpyAsync(F_out, dF, (size_t)dim * nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        sync = true;
+    }
+    if (phi_out && !phi_dev) {
+        CK(h, cudaMemcpyAsync(phi_out, dP, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        sync = true;
+    }
+    if (sync)
+        CK(h, cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+mg_status mg_profile(mg_hierarchy *h, int enable)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    CK(h, profile_flush(h));
+    Profiler &P = h->prof;
+    P.on = enable != 0;
+    for (int k = 0; k < KK_COUNT; k++) {
+        P.launches[k] = 0;
+        P.ms[k] = 0.0;
+        P.bytes[k] = 0.0;
+    }
+    return MG_OK;
+}
+
+int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap)
+{
+    if (!h || h->poisoned || profile_flush(h) != cudaSuccess)
+        return -1;
+    int k = 0;
+    for (int i = 0; i < KK_COUNT && k < cap; i++) {
+        if (!h->prof.launches[i])
+            continue;
+        if (out) {
+            std::snprintf(out[k].name, sizeof out[k].name, "%s", kKindName[i]);
+            out[k].launches = h->prof.launches[i];
+            out[k].ms = h->prof.ms[i];
+            out[k].bytes = h->prof.bytes[i];
+        }
+        k++;
+    }
+    return k;
+}
+
+mg_status mg_destroy(mg_hierarchy *h)
+{
+    if (!h)
+        return MG_OK;
+    if (h->arena) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->arena);
+    }
+    for (cudaEvent_t e : h->prof.pool)
+        cudaEventDestroy(e);
+    if (h->hscal)
+        cudaFreeHost(h->hscal);
+    cudaGetLastError();
+    delete h;
+    return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// mg_internal.h -- declarations shared by the host driver and the kernels of
+// the nested-grid multigrid solver.  Not part of the public ABI (include/mg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MG_MAX_MG 16          // multigrid levels per refinement level (n+2 <= 2^15)
+
+// One multigrid level L of one refinement level (Sec. 2.2).  Active cells use
+// 1-based indices 1..N per axis inside an (N+2)^d array with one ghost layer.
+// At L = 0 the ghost layer is the outer buffer ring of the refinement level
+// and holds Dirichlet data; at L > 0 it is never read: the ghost rule of
+// Sec. 2.4 is folded into the boundary cells' stencil coefficients.
+struct MgGeom {
+    int N;          // active cells per edge
+    int E;          // N + 2, storage edge
+    int L;          // multigrid level, 0 = finest
+    int tie;        // centre of cell N sits exactly at x_MG = 1
+    double cR;      // right ghost = cR * Phi_N when !tie
+    double h2;      // squared physical cell size of this multigrid level
+    double inv_h2;  // 1 / h2
+};
+
+// Per-axis stencil coefficients of an active index i on level g, with the
+// ghost rule folded in (left ghost -Phi_1; right ghost cR Phi_N, or -Phi_{N-1}
+// when x_N = 1).
+template <typename T>
+__device__ __forceinline__ void mg_axis_coef(int i, const MgGeom &g, T &wm, T &wp, T &dg)
+{
+    wm = T(1);
+    wp = T(1);
+    dg = T(-2);
+    if (g.L == 0)
+        return;
+    if (i == 1) {
+        wm = T(0);
+        dg -= T(1);
+    }
+    if (i == g.N) {
+        wp = T(0);
+        if (g.tie) {
+            if (g.N >= 2)
+                wm = T(0);      // +Phi_{N-1} from the left, -Phi_{N-1} from the ghost
+            else
+                dg += T(1);     // -Phi_0 = +Phi_1
+        } else {
+            dg += T(g.cR);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (mg_kernels.cu).  `fp32` selects float arrays; the
+// geometry is the same.  All launches go to stream s and return the launch
+// error (cudaGetLastError).
+// ---------------------------------------------------------------------------
+// One colour (0 = red, (i+j[+k]) even; 1 = black) of a Gauss-Seidel sweep.
+cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int colour,
+                             cudaStream_t s);
+cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
+                                     void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s);
+cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeom &gc, void *phi_f, const MgGeom &gf,
+                              cudaStream_t s);
+
+// ||f - lap(Phi)||^2 over the active cells of a finest multigrid level
+// (zero_inside: Phi taken as zero on the active cells, ring kept), written to
+// *out after a fixed-order two-pass reduction through `partials`
+// (MG_NORM_BLOCKS doubles).
+#define MG_NORM_BLOCKS 304
+cudaError_t mg_launch_resid_norm2(int dim, const double *phi, const double *f, const MgGeom &g, bool zero_inside,
+                                  double *partials, double *out, cudaStream_t s);
+
+// Mixed precision: r32 = float(f - lap(Phi)) on the active cells of the
+// finest level (ring of r32 and e32 untouched), and Phi += double(e32).
+cudaError_t mg_launch_defect(int dim, const double *phi, const double *f, const MgGeom &g, float *r32, float *e32,
+                             cudaStream_t s);
+cudaError_t mg_launch_accumulate(int dim, double *phi, const float *e32, const MgGeom &g, cudaStream_t s);
+
+// Level data copy-in: rho (n^d) into the Omega part of rho_blk/f_blk
+// ((n+4)^d); for level 0 also bc_rho's ring ((n+2)^d) and bc_phi's outer
+// ring ((n+4)^d), and a zero start on Gamma.  fourpiG = 4 pi G.
+cudaError_t mg_launch_set_density(int dim, int n, const double *rho, const double *bc_rho, const double *bc_phi,
+                                  double *rho_blk, double *f_blk, double *phi_blk, double fourpiG, cudaStream_t s);
+
+// Interface of Sec. 2.1 / 2.4: from the parent's (np+4)^d potential and
+// density fill the child's outer-ring potential, inner-ring density (and
+// f = 4 pi G rho there) and the initial potential on Gamma (guess 0: parent
+// interpolation, 1: zero, 2: copy of guess_src ((nc+2)^d)).
+cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const double *rho_p, int nc, int ox, int oy,
+                                int oz, double *phi_c, double *rho_c, double *f_c, double fourpiG, int guess,
+                                const double *guess_src, cudaStream_t s);
+cudaError_t mg_launch_copy_guess(int dim, int n, const double *guess_src, double *phi_blk, cudaStream_t s);
+
+// Forces F = -grad(Phi) on Omega ((n+4)^d block in, dim * n^d out) and the
+// potential on Omega (n^d, optional).
+cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, double *F, double *phi_out,
+                             int stencil, cudaStream_t s);
+
+cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s);

@@ -1,0 +1,594 @@
+// mg_kernels.cu -- CUDA kernels of the nested-grid multigrid Poisson solver
+// for sm_103a: red-black Gauss-Seidel smoothing, fused residual+restriction,
+// prolongation+correction, residual norms, the coarse-to-fine interface and
+// the force stencil.  Arrays are C order, x fastest.
+#include "mg_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(long work, int cap = 152 * 16)
+{
+    long b = (work + kThreads - 1) / kThreads;
+    if (b < 1)
+        b = 1;
+    if (b > cap)
+        b = cap;
+    return (int)b;
+}
+
+template <int DIM>
+__device__ __forceinline__ long lin(int i, int j, int k, int E)
+{
+    return DIM == 3 ? ((long)k * E + j) * E + i : (long)j * E + i;
+}
+
+// Sum of the (ghost-folded) neighbours and the diagonal coefficient of the
+// 5/7-point Laplacian (Sec. 2.3, item 1) at active cell (i,j,k), p = its index.
+template <typename T, int DIM>
+__device__ __forceinline__ void stencil_terms(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, long p,
+                                              T &other, T &diag)
+{
+    const long E = g.E;
+    if (g.L == 0) {
+        other = (phi[p - 1] + phi[p + 1]) + (phi[p - E] + phi[p + E]);
+        if (DIM == 3)
+            other += phi[p - E * E] + phi[p + E * E];
+        diag = T(-2 * DIM);
+        return;
+    }
+    T wm, wp, dg;
+    mg_axis_coef<T>(i, g, wm, wp, dg);
+    other = wm * phi[p - 1] + wp * phi[p + 1];
+    diag = dg;
+    mg_axis_coef<T>(j, g, wm, wp, dg);
+    other += wm * phi[p - E] + wp * phi[p + E];
+    diag += dg;
+    if (DIM == 3) {
+        mg_axis_coef<T>(k, g, wm, wp, dg);
+        other += wm * phi[p - E * E] + wp * phi[p + E * E];
+        diag += dg;
+    }
+}
+
+// One colour of a red-black Gauss-Seidel sweep (Sec. 2.3 steps 2, 6, 11).
+// Red cells have (i+j[+k]) even and are updated first.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
+                                                            int colour)
+{
+    const int N = g.N;
+    const int half = (N + 1) >> 1;
+    const long total = (long)half * N * (DIM == 3 ? N : 1);
+    const T h2 = T(g.h2);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i2 = (int)(t % half);
+        const long r = t / half;
+        const int j = (int)(r % N) + 1;
+        const int k = DIM == 3 ? (int)(r / N) + 1 : 0;
+        const int i = ((((1 + j + k) & 1) == colour) ? 1 : 2) + 2 * i2;
+        if (i > N)
+            continue;
+        const long p = lin<DIM>(i, j, k, g.E);
+        T other, diag;
+        stencil_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
+        // interior cells share the diagonal 2d: multiply by its reciprocal
+        const T inv = diag == T(-2 * DIM) ? T(1.0 / (2 * DIM)) : T(1) / (-diag);
+        phi[p] = (other - h2 * f[p]) * inv;
+    }
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g, int i,
+                                         int j, int k)
+{
+    const long p = lin<DIM>(i, j, k, g.E);
+    T other, diag;
+    stencil_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
+    return f[p] - (other + diag * phi[p]) * T(g.inv_h2);
+}
+
+// Residual (Sec. 2.3 step 4) restricted to the next coarser level by the
+// 2^d-child average (step 5; fine cells beyond N contribute zero); the
+// coarse correction starts from zero.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                             MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
+                                                             MgGeom gc)
+{
+    const int Nc = gc.N, Nf = gf.N;
+    const long total = (long)Nc * Nc * (DIM == 3 ? Nc : 1);
+    const T w = DIM == 3 ? T(0.125) : T(0.25);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int I = (int)(t % Nc) + 1;
+        const int J = (int)((t / Nc) % Nc) + 1;
+        const int K = DIM == 3 ? (int)(t / ((long)Nc * Nc)) + 1 : 0;
+        T s = T(0);
+        for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++) {
+            const int k = DIM == 3 ? 2 * K - 1 + dk : 0;
+            if (DIM == 3 && k > Nf)
+                continue;
+            for (int dj = 0; dj < 2; dj++) {
+                const int j = 2 * J - 1 + dj;
+                if (j > Nf)
+                    continue;
+                for (int di = 0; di < 2; di++) {
+                    const int i = 2 * I - 1 + di;
+                    if (i > Nf)
+                        continue;
+                    s += residual_at<T, DIM>(phi_f, f_f, gf, i, j, k);
+                }
+            }
+        }
+        const long pc = lin<DIM>(I, J, K, gc.E);
+        f_c[pc] = w * s;
+        phi_c[pc] = T(0);
+    }
+}
+
+// Coarse index q along one axis of level gc (ghosts included) written as
+// coefficient * active value (Sec. 2.4 ghost rule).
+__device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, double &c)
+{
+    if (q >= 1 && q <= gc.N) {
+        idx = q;
+        c = 1.0;
+    } else if (q == 0) {
+        idx = 1;
+        c = -1.0;
+    } else if (gc.tie) {
+        if (gc.N >= 2) {
+            idx = gc.N - 1;
+            c = -1.0;
+        } else {
+            idx = 1;
+            c = 1.0;
+        }
+    } else {
+        idx = gc.N;
+        c = gc.cR;
+    }
+}
+
+// Prolongation and correction (Sec. 2.3 step 10; weights 3/4, 1/4 per axis,
+// i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse ghosts by the rule.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_c, MgGeom gc, T *__restrict__ phi_f,
+                                                      MgGeom gf)
+{
+    const int Nf = gf.N;
+    const long total = (long)Nf * Nf * (DIM == 3 ? Nf : 1);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        int f[3];
+        f[0] = (int)(t % Nf) + 1;
+        f[1] = (int)((t / Nf) % Nf) + 1;
+        f[2] = DIM == 3 ? (int)(t / ((long)Nf * Nf)) + 1 : 0;
+        int idx[3][2];
+        T w[3][2];
+        for (int a = 0; a < DIM; a++) {
+            const int near = (f[a] + 1) >> 1;
+            const int far = (f[a] & 1) ? near - 1 : near + 1;
+            double c0, c1;
+            ghost_map(near, gc, idx[a][0], c0);
+            ghost_map(far, gc, idx[a][1], c1);
+            w[a][0] = T(0.75 * c0);
+            w[a][1] = T(0.25 * c1);
+        }
+        T v = T(0);
+        if (DIM == 3) {
+            for (int c = 0; c < 2; c++)
+                for (int b = 0; b < 2; b++)
+                    for (int a = 0; a < 2; a++)
+                        v += w[0][a] * w[1][b] * w[2][c] * phi_c[lin<3>(idx[0][a], idx[1][b], idx[2][c], gc.E)];
+        } else {
+            for (int b = 0; b < 2; b++)
+                for (int a = 0; a < 2; a++)
+                    v += w[0][a] * w[1][b] * phi_c[lin<2>(idx[0][a], idx[1][b], 0, gc.E)];
+        }
+        phi_f[lin<DIM>(f[0], f[1], f[2], gf.E)] += v;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sm[kThreads / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        sm[w] = v;
+    __syncthreads();
+    v = threadIdx.x < kThreads / 32 ? sm[threadIdx.x] : 0.0;
+    if (w == 0)
+        v = warp_sum(v);
+    return v;
+}
+
+// Partial sums of r^2 (r = f - lap(Phi)) over the active cells of a finest
+// multigrid level; one partial per block, fixed assignment of cells.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_resid_norm2(const double *__restrict__ phi, const double *__restrict__ f,
+                                                          MgGeom g, int zero_inside, double *__restrict__ partials)
+{
+    const int N = g.N;
+    const long E = g.E;
+    const long total = (long)N * N * (DIM == 3 ? N : 1);
+    double acc = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % N) + 1;
+        const int j = (int)((t / N) % N) + 1;
+        const int k = DIM == 3 ? (int)(t / ((long)N * N)) + 1 : 0;
+        const long p = lin<DIM>(i, j, k, g.E);
+        double r;
+        if (zero_inside) {
+            // neighbours inside the solved region count as zero
+            double o = 0.0;
+            if (i == 1) o += phi[p - 1];
+            if (i == N) o += phi[p + 1];
+            if (j == 1) o += phi[p - E];
+            if (j == N) o += phi[p + E];
+            if (DIM == 3) {
+                if (k == 1) o += phi[p - E * E];
+                if (k == N) o += phi[p + E * E];
+            }
+            r = f[p] - o * g.inv_h2;
+        } else {
+            r = residual_at<double, DIM>(phi, f, g, i, j, k);
+        }
+        acc += r * r;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const double *__restrict__ partials, int n,
+                                                           double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+        acc += partials[t];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0)
+        *out = acc;
+}
+
+// Mixed precision defect: r32 = (float)(f - lap Phi) in FP64 on the finest
+// level; the FP32 correction restarts from zero.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_defect(const double *__restrict__ phi, const double *__restrict__ f,
+                                                     MgGeom g, float *__restrict__ r32, float *__restrict__ e32)
+{
+    const int N = g.N;
+    const long total = (long)N * N * (DIM == 3 ? N : 1);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % N) + 1;
+        const int j = (int)((t / N) % N) + 1;
+        const int k = DIM == 3 ? (int)(t / ((long)N * N)) + 1 : 0;
+        const long p = lin<DIM>(i, j, k, g.E);
+        r32[p] = (float)residual_at<double, DIM>(phi, f, g, i, j, k);
+        e32[p] = 0.0f;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_accumulate(double *__restrict__ phi, const float *__restrict__ e32,
+                                                         MgGeom g)
+{
+    const int N = g.N;
+    const long total = (long)N * N * (DIM == 3 ? N : 1);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % N) + 1;
+        const int j = (int)((t / N) % N) + 1;
+        const int k = DIM == 3 ? (int)(t / ((long)N * N)) + 1 : 0;
+        const long p = lin<DIM>(i, j, k, g.E);
+        phi[p] += (double)e32[p];
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_set_density(int n, const double *__restrict__ rho,
+                                                          const double *__restrict__ bc_rho,
+                                                          const double *__restrict__ bc_phi, double *__restrict__ rho_blk,
+                                                          double *__restrict__ f_blk, double *__restrict__ phi_blk,
+                                                          double fourpiG)
+{
+    const int E = n + 4;
+    const long total = (long)E * E * (DIM == 3 ? E : 1);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % E), j = (int)((t / E) % E), k = DIM == 3 ? (int)(t / ((long)E * E)) : 2;
+        const bool outer = i == 0 || i == n + 3 || j == 0 || j == n + 3 || (DIM == 3 && (k == 0 || k == n + 3));
+        const bool omega = i >= 2 && i <= n + 1 && j >= 2 && j <= n + 1 && (DIM == 2 || (k >= 2 && k <= n + 1));
+        if (omega) {
+            const double v = rho[lin<DIM>(i - 2, j - 2, k - 2, n)];
+            rho_blk[t] = v;
+            f_blk[t] = fourpiG * v;
+            if (bc_phi)
+                phi_blk[t] = 0.0;
+        } else if (bc_phi) {          // level 0: caller-owned buffer data
+            if (outer) {
+                phi_blk[t] = bc_phi[t];
+            } else {
+                const double v = bc_rho[lin<DIM>(i - 1, j - 1, DIM == 3 ? k - 1 : 0, n + 2)];
+                rho_blk[t] = v;
+                f_blk[t] = fourpiG * v;
+                phi_blk[t] = 0.0;
+            }
+        }
+    }
+}
+
+// Child storage index s -> parent storage index p0 and weight t of p0+1
+// (child centre at parent coordinate off + 3/4 + s/2).
+__device__ __forceinline__ void iface_axis(int s, int off, int &p0, double &t)
+{
+    if ((s & 1) == 0) {
+        p0 = off + (s >> 1);
+        t = 0.75;
+    } else {
+        p0 = off + ((s + 1) >> 1);
+        t = 0.25;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ double interp(const double *__restrict__ src, int Ep, const int *p0, const double *t)
+{
+    double v = 0.0;
+    for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++)
+        for (int dj = 0; dj < 2; dj++)
+            for (int di = 0; di < 2; di++) {
+                double w = (di ? t[0] : 1.0 - t[0]) * (dj ? t[1] : 1.0 - t[1]);
+                if (DIM == 3)
+                    w *= dk ? t[2] : 1.0 - t[2];
+                v += w * src[lin<DIM>(p0[0] + di, p0[1] + dj, DIM == 3 ? p0[2] + dk : 0, Ep)];
+            }
+    return v;
+}
+
+// One-way interface (Sec. 2.1; Sec. 2.4): bilinear/trilinear interpolation
+// from the 2^d enclosing parent centres (Appendix A weights).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__restrict__ phi_p,
+                                                        const double *__restrict__ rho_p, int nc, int ox, int oy, int oz,
+                                                        double *__restrict__ phi_c, double *__restrict__ rho_c,
+                                                        double *__restrict__ f_c, double fourpiG, int guess,
+                                                        const double *__restrict__ guess_src)
+{
+    const int E = nc + 4, Ep = np + 4;
+    const long total = (long)E * E * (DIM == 3 ? E : 1);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        int s[3];
+        s[0] = (int)(t % E);
+        s[1] = (int)((t / E) % E);
+        s[2] = DIM == 3 ? (int)(t / ((long)E * E)) : 2;
+        bool outer = false, inner = false;
+        for (int a = 0; a < DIM; a++) {
+            if (s[a] == 0 || s[a] == nc + 3)
+                outer = true;
+            else if (s[a] == 1 || s[a] == nc + 2)
+                inner = true;
+        }
+        int p0[3] = {0, 0, 0};
+        double w[3] = {0, 0, 0};
+        const int off[3] = {ox, oy, oz};
+        for (int a = 0; a < DIM; a++)
+            iface_axis(s[a], off[a], p0[a], w[a]);
+        if (outer) {
+            phi_c[t] = interp<DIM>(phi_p, Ep, p0, w);
+            continue;
+        }
+        if (inner) {
+            const double r = interp<DIM>(rho_p, Ep, p0, w);
+            rho_c[t] = r;
+            f_c[t] = fourpiG * r;
+        }
+        if (guess == 0)
+            phi_c[t] = interp<DIM>(phi_p, Ep, p0, w);
+        else if (guess == 1)
+            phi_c[t] = 0.0;
+        else
+            phi_c[t] = guess_src[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_copy_guess(int n, const double *__restrict__ src,
+                                                         double *__restrict__ phi_blk)
+{
+    const int M = n + 2;
+    const long total = (long)M * M * (DIM == 3 ? M : 1);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % M), j = (int)((t / M) % M), k = DIM == 3 ? (int)(t / ((long)M * M)) : 0;
+        phi_blk[lin<DIM>(i + 1, j + 1, DIM == 3 ? k + 1 : 0, n + 4)] = src[t];
+    }
+}
+
+// F = -grad(Phi) on Omega: Eq. 2 (stencil 0) or the two-point difference.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_forces(int n, double h, const double *__restrict__ phi,
+                                                     double *__restrict__ F, double *__restrict__ phi_out, int stencil)
+{
+    const int E = n + 4;
+    const long total = (long)n * n * (DIM == 3 ? n : 1);
+    const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * h) : 1.0 / (2.0 * h);
+    const double c2 = stencil == 0 ? (1.0 / 3.0) / (4.0 * h) : 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % n) + 2, j = (int)((t / n) % n) + 2;
+        const int k = DIM == 3 ? (int)(t / ((long)n * n)) + 2 : 0;
+        const long p = lin<DIM>(i, j, k, E);
+        const long st[3] = {1, E, (long)E * E};
+        for (int a = 0; a < DIM; a++) {
+            const double d1 = phi[p + st[a]] - phi[p - st[a]];
+            const double d2 = phi[p + 2 * st[a]] - phi[p - 2 * st[a]];
+            F[(long)a * total + t] = -(c1 * d1 - c2 * d2);
+        }
+        if (phi_out)
+            phi_out[t] = phi[p];
+    }
+}
+
+__global__ void k_zero(uint4 *p, size_t n16)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n16; t += (size_t)gridDim.x * blockDim.x)
+        p[t] = make_uint4(0, 0, 0, 0);
+}
+
+inline long cube(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int c, cudaStream_t s)
+{
+    const long work = (long)((g.N + 1) / 2) * g.N * (dim == 3 ? g.N : 1);
+    const int grid = grid_for(work);
+    if (dim == 3) {
+        if (fp32)
+            k_smooth_colour<float, 3><<<grid, kThreads, 0, s>>>((float *)phi, (const float *)f, g, c);
+        else
+            k_smooth_colour<double, 3><<<grid, kThreads, 0, s>>>((double *)phi, (const double *)f, g, c);
+    } else {
+        if (fp32)
+            k_smooth_colour<float, 2><<<grid, kThreads, 0, s>>>((float *)phi, (const float *)f, g, c);
+        else
+            k_smooth_colour<double, 2><<<grid, kThreads, 0, s>>>((double *)phi, (const double *)f, g, c);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
+                                     void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s)
+{
+    const int grid = grid_for(cube(gc.N, dim));
+    if (dim == 3) {
+        if (fp32)
+            k_resid_restrict<float, 3><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
+                                                                 (float *)phi_c, (float *)f_c, gc);
+        else
+            k_resid_restrict<double, 3><<<grid, kThreads, 0, s>>>((const double *)phi_f, (const double *)f_f, gf,
+                                                                  (double *)phi_c, (double *)f_c, gc);
+    } else {
+        if (fp32)
+            k_resid_restrict<float, 2><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
+                                                                 (float *)phi_c, (float *)f_c, gc);
+        else
+            k_resid_restrict<double, 2><<<grid, kThreads, 0, s>>>((const double *)phi_f, (const double *)f_f, gf,
+                                                                  (double *)phi_c, (double *)f_c, gc);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeom &gc, void *phi_f, const MgGeom &gf,
+                              cudaStream_t s)
+{
+    const int grid = grid_for(cube(gf.N, dim));
+    if (dim == 3) {
+        if (fp32)
+            k_prolong<float, 3><<<grid, kThreads, 0, s>>>((const float *)phi_c, gc, (float *)phi_f, gf);
+        else
+            k_prolong<double, 3><<<grid, kThreads, 0, s>>>((const double *)phi_c, gc, (double *)phi_f, gf);
+    } else {
+        if (fp32)
+            k_prolong<float, 2><<<grid, kThreads, 0, s>>>((const float *)phi_c, gc, (float *)phi_f, gf);
+        else
+            k_prolong<double, 2><<<grid, kThreads, 0, s>>>((const double *)phi_c, gc, (double *)phi_f, gf);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_resid_norm2(int dim, const double *phi, const double *f, const MgGeom &g, bool zero_inside,
+                                  double *partials, double *out, cudaStream_t s)
+{
+    if (dim == 3)
+        k_resid_norm2<3><<<MG_NORM_BLOCKS, kThreads, 0, s>>>(phi, f, g, zero_inside ? 1 : 0, partials);
+    else
+        k_resid_norm2<2><<<MG_NORM_BLOCKS, kThreads, 0, s>>>(phi, f, g, zero_inside ? 1 : 0, partials);
+    k_sum_partials<<<1, kThreads, 0, s>>>(partials, MG_NORM_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_defect(int dim, const double *phi, const double *f, const MgGeom &g, float *r32, float *e32,
+                             cudaStream_t s)
+{
+    const int grid = grid_for(cube(g.N, dim));
+    if (dim == 3)
+        k_defect<3><<<grid, kThreads, 0, s>>>(phi, f, g, r32, e32);
+    else
+        k_defect<2><<<grid, kThreads, 0, s>>>(phi, f, g, r32, e32);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_accumulate(int dim, double *phi, const float *e32, const MgGeom &g, cudaStream_t s)
+{
+    const int grid = grid_for(cube(g.N, dim));
+    if (dim == 3)
+        k_accumulate<3><<<grid, kThreads, 0, s>>>(phi, e32, g);
+    else
+        k_accumulate<2><<<grid, kThreads, 0, s>>>(phi, e32, g);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_set_density(int dim, int n, const double *rho, const double *bc_rho, const double *bc_phi,
+                                  double *rho_blk, double *f_blk, double *phi_blk, double fourpiG, cudaStream_t s)
+{
+    const int grid = grid_for(cube(n + 4, dim));
+    if (dim == 3)
+        k_set_density<3><<<grid, kThreads, 0, s>>>(n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
+    else
+        k_set_density<2><<<grid, kThreads, 0, s>>>(n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const double *rho_p, int nc, int ox, int oy,
+                                int oz, double *phi_c, double *rho_c, double *f_c, double fourpiG, int guess,
+                                const double *guess_src, cudaStream_t s)
+{
+    const int grid = grid_for(cube(nc + 4, dim));
+    if (dim == 3)
+        k_interface<3><<<grid, kThreads, 0, s>>>(np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
+                                                 guess_src);
+    else
+        k_interface<2><<<grid, kThreads, 0, s>>>(np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
+                                                 guess_src);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_copy_guess(int dim, int n, const double *guess_src, double *phi_blk, cudaStream_t s)
+{
+    const int grid = grid_for(cube(n + 2, dim));
+    if (dim == 3)
+        k_copy_guess<3><<<grid, kThreads, 0, s>>>(n, guess_src, phi_blk);
+    else
+        k_copy_guess<2><<<grid, kThreads, 0, s>>>(n, guess_src, phi_blk);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, double *F, double *phi_out, int stencil,
+                             cudaStream_t s)
+{
+    const int grid = grid_for(cube(n, dim));
+    if (dim == 3)
+        k_forces<3><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
+    else
+        k_forces<2><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s)
+{
+    // callers pass 256-byte aligned sub-allocations whose sizes are multiples of 16
+    const size_t n16 = bytes / 16;
+    if (n16)
+        k_zero<<<grid_for((long)n16), kThreads, 0, s>>>((uint4 *)p, n16);
+    return cudaGetLastError();
+}

@@ -1,0 +1,105 @@
+"""The C ABI library builds, loads and answers its host-only calls (no GPU).
+
+Checks that libmg.so exports every function include/mg.h declares, that the
+multigrid level sizes it computes agree with the oracle's for many sizes,
+and that argument validation happens on the host before any CUDA call.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mg():
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg as M
+    return M
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(mg):
+    names = _declared()
+    assert "mg_create_hierarchy" in names and "mg_solve" in names and len(names) >= 10
+    lib = C.CDLL(mg.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_abi(mg):
+    for n in _declared():
+        assert hasattr(mg, n), n
+
+
+def test_default_options(mg):
+    o = mg.mg_default_options()
+    assert (o.nu_pre, o.nu_post, o.max_cycles, o.rel_tol) == (2, 1, 50, 1e-10)
+    assert o.precision == mg.MG_FP64 and o.guess == mg.MG_GUESS_INTERP and o.force_stencil == mg.MG_FORCE_EQ2
+
+
+def test_level_sizes_match_oracle(mg, oracle):
+    for M in list(range(2, 600)) + [1026, 2050, 4098]:
+        assert mg.mg_level_sizes(M) == oracle.mg_sizes(M), M
+
+
+def test_status_strings(mg):
+    for s in range(8):
+        assert mg.mg_status_str(s).startswith("MG_")
+
+
+def _desc(mg, **kw):
+    from paper_2001_02327_gb300 import inputs as I
+    H = I.config_3d_offset_sphere(n=16, levels=2)
+    d = mg.desc_from(H)
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("bad", ["dim", "levels", "n_odd", "offset", "h0", "opt"])
+def test_invalid_arguments_rejected_on_host(mg, bad):
+    d = _desc(mg)
+    opt = None
+    if bad == "dim":
+        d.dim = 4
+    elif bad == "levels":
+        d.num_levels = 9
+    elif bad == "n_odd":
+        d.n[1] = 15
+    elif bad == "offset":
+        d.lo[1][0] = d.lo[0][0]           # offset 0 parent cells: buffer would leave the parent
+    elif bad == "h0":
+        d.h0 = -1.0
+    elif bad == "opt":
+        opt = mg.options(nu_pre=0, nu_post=0)
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_create_hierarchy([d], opt)
+    assert e.value.status == mg.MG_EINVAL
+    assert mg.mg_error_message(None)
+
+
+def test_null_handles(mg):
+    assert mg.LIB.mg_destroy(None) == mg.MG_OK
+    assert mg.LIB.mg_solve(None, None) == mg.MG_EINVAL
+    assert mg.LIB.mg_forces(None, 0, 0, None, None) == mg.MG_EINVAL
+    assert mg.LIB.mg_set_density(None, 0, 0, None, None, None) == mg.MG_EINVAL
+    assert mg.LIB.mg_default_options(None) == mg.MG_EINVAL
+
+
+def test_product_path_does_not_touch_the_oracle():
+    """No file of the package or the C sources refers to the oracle."""
+    pkg = os.path.join(ROOT, "paper_2001_02327_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "liboracle" not in txt, f
