@@ -71,7 +71,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu_id), "-lms", "100"], stdout=subprocess.PIPE,
+                                          "-i", str(self.gpu_id), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -157,6 +157,15 @@ class Runner:
 
     def close(self):
         self.mg.mg_destroy(self.h)
+
+
+def gpu_ident(torch, local):
+    """nvidia-smi -i argument for the torch device: its UUID when known."""
+    u = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+    if u is None:
+        return local
+    u = str(u)
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 def time_device(runner, torch, steps, warmup, flush):
@@ -256,8 +265,7 @@ def run_ours(args):
             if ws > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
-            sampler = ClockSampler(getattr(torch.cuda.get_device_properties(local), "uuid", local)) \
-                if name == "fp64" else None
+            sampler = ClockSampler(gpu_ident(torch, local)) if name == "fp64" else None
             if sampler:
                 sampler.start()
             times = time_device(r, torch, args.steps, args.warmup, flush)

@@ -98,3 +98,22 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
                              int stencil, cudaStream_t s);
 
 cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s);
+
+// Device-side state of one level solve, updated by the control kernels that
+// close every iteration of the solve graph.
+struct MgSolveCtl {
+    int cycles;      // V-cycles run (FP32 V-cycles in mixed mode)
+    int outer;       // iterations of the loop body
+    int status;      // 0 ok, 6 (MG_EDIVERGED) on a non-finite residual
+    int go;          // last value given to the loop condition
+    double rel;      // ||r|| / ||b||
+    double bnorm;    // ||b||
+};
+
+// ctl_init: from scal = {||b||^2, ||r||^2} start the counters and set the
+// loop condition (handle) to 1 iff another iteration is needed.
+// ctl_step: after one iteration of `inc` V-cycles, with scal[1] = ||r||^2.
+cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
+                               cudaGraphConditionalHandle hc, cudaStream_t s);
+cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
+                               cudaGraphConditionalHandle hc, cudaStream_t s);

@@ -441,6 +441,39 @@ __global__ void k_zero(uint4 *p, size_t n16)
         p[t] = make_uint4(0, 0, 0, 0);
 }
 
+__device__ __forceinline__ int keep_going(const MgSolveCtl &c, double tol, int max_cycles)
+{
+    return c.bnorm > 0.0 && c.status == 0 && c.cycles < max_cycles && !(c.rel < tol);
+}
+
+__global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
+                           cudaGraphConditionalHandle hc)
+{
+    MgSolveCtl c;
+    c.bnorm = sqrt(scal[0]);
+    c.rel = c.bnorm > 0.0 ? sqrt(scal[1]) / c.bnorm : 0.0;
+    c.cycles = 0;
+    c.outer = 0;
+    c.status = 0;
+    c.go = keep_going(c, tol, max_cycles);
+    *ctl = c;
+    cudaGraphSetConditional(hc, c.go);
+}
+
+__global__ void k_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
+                           cudaGraphConditionalHandle hc)
+{
+    MgSolveCtl c = *ctl;
+    c.cycles += inc;
+    c.outer += 1;
+    c.rel = sqrt(scal[1]) / c.bnorm;
+    if (!isfinite(c.rel))
+        c.status = 6;
+    c.go = keep_going(c, tol, max_cycles);
+    *ctl = c;
+    cudaGraphSetConditional(hc, c.go);
+}
+
 inline long cube(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
 
 }  // namespace
@@ -581,6 +614,20 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
         k_forces<3><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
     else
         k_forces<2><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
+                               cudaGraphConditionalHandle hc, cudaStream_t s)
+{
+    k_ctl_init<<<1, 1, 0, s>>>(ctl, scal, tol, max_cycles, hc);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
+                               cudaGraphConditionalHandle hc, cudaStream_t s)
+{
+    k_ctl_step<<<1, 1, 0, s>>>(ctl, scal, inc, tol, max_cycles, hc);
     return cudaGetLastError();
 }
 

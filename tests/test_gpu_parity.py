@@ -161,7 +161,9 @@ def test_full_size_config_converged(mg, oracle):
     for l in range(H.num_levels):
         assert g[l]["cycles"] == ref[l]["cycles"], (l, g[l]["cycles"], ref[l]["cycles"])
         assert g[l]["rel_res"] < 1e-10
-        assert abs(g[l]["rel_res"] / ref[l]["hist"][-1] - 1) < 1e-6
+        # ||r|| ~ 1e-10 ||b|| is a difference of O(||b||) terms: round-off of
+        # 1e-16 in the operands is ~1e-6 of it
+        assert abs(g[l]["rel_res"] / ref[l]["hist"][-1] - 1) < 1e-4
     check_parity(H, g, ref)
 
 
