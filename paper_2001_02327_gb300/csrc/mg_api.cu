@@ -4,6 +4,7 @@
 // parent (Sec. 2.1); all arithmetic runs in the kernels of mg_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -68,6 +69,8 @@ void build_geometry(LevelData &ld, int dim)
     }
 }
 
+#define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
+
 enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
                   KK_SETDENS, KK_COUNT };
 const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
@@ -99,12 +102,21 @@ struct mg_hierarchy {
     size_t arena_bytes = 0;
     double *stage = nullptr;        // device staging for host-pointer I/O
     size_t stage_elems = 0;
-    double *partials = nullptr;     // MG_NORM_BLOCKS
+    double *partials = nullptr;     // MG_BRANCHES * MG_NORM_BLOCKS reduction scratch
     double *scal = nullptr;         // device scalars: [b][l][2] = ||b||^2, ||r||^2
     double *hscal = nullptr;        // pinned mirror
+    MgSolveCtl *ctl = nullptr;      // device loop state per (b, l)
+    MgSolveCtl *hctl = nullptr;     // pinned mirror
     bool poisoned = false, solved = false;
     std::string err;
     Profiler prof;
+    // solve graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<char> graph_sig;
+    cudaStream_t cap[MG_BRANCHES] = {};
+    cudaStream_t body_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join[MG_BRANCHES] = {};
 };
 
 namespace {
@@ -245,7 +257,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // --------------------------------------------------------------------------
 double cells_d(int N, int dim) { return dim == 3 ? (double)N * N * N : (double)N * N; }
 
-cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int sweeps)
+cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int sweeps, cudaStream_t s)
 {
     const int dim = h->dim;
     const MgGeom &g = ld.g[L];
@@ -254,7 +266,7 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     const double bytes = 2.0 * (fp32 ? 4 : 8) * cells_d(g.N, dim);   // read Phi, read/write one colour
     for (int sw = 0; sw < sweeps; sw++)
         for (int c = 0; c < 2; c++) {
-            cudaError_t e = timed(h, KK_SMOOTH, bytes, [&] { return mg_launch_smooth(dim, fp32, phi, f, g, c, h->stream); });
+            cudaError_t e = timed(h, KK_SMOOTH, bytes, [&] { return mg_launch_smooth(dim, fp32, phi, f, g, c, s); });
             if (e)
                 return e;
         }
@@ -262,18 +274,17 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
 }
 
 // the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level
-cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32)
+cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t s)
 {
     const int dim = h->dim;
     const mg_options &o = h->opt;
-    cudaStream_t s = h->stream;
     const int w = fp32 ? 4 : 8;
     auto P = [&](int L) -> void * { return fp32 ? (void *)ld.phi32[L] : (void *)ld.phi[L]; };
     auto F = [&](int L) -> void * { return fp32 ? (void *)ld.f32[L] : (void *)ld.f[L]; };
     cudaError_t e;
     if (ld.nmg == 1)
-        return smooth(h, ld, 0, fp32, o.nu_pre + o.nu_post);
-    if ((e = smooth(h, ld, 0, fp32, o.nu_pre)))                                           // step 2
+        return smooth(h, ld, 0, fp32, o.nu_pre + o.nu_post, s);
+    if ((e = smooth(h, ld, 0, fp32, o.nu_pre, s)))                                        // step 2
         return e;
     int L = 0;
     do {
@@ -284,7 +295,7 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32)
         if (e)
             return e;
         const int sweeps = ld.g[L + 1].N == 1 ? (o.nu_pre > 0 ? 1 : 0) : o.nu_pre;       // one cell: exact
-        if ((e = smooth(h, ld, L + 1, fp32, sweeps)))                                     // step 6
+        if ((e = smooth(h, ld, L + 1, fp32, sweeps, s)))                                  // step 6
             return e;
         L++;
     } while (ld.g[L].N > 1 && L + 1 < ld.nmg);                                            // step 8
@@ -293,100 +304,252 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32)
         e = timed(h, KK_PROLONG, by, [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
         if (e)                                                                            // step 10
             return e;
-        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post)))                                  // step 11
+        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s)))                               // step 11
             return e;
         L--;
     } while (L > 0);                                                                      // step 13
     return cudaSuccess;
 }
 
-cudaError_t resid_norm(mg_hierarchy *h, const LevelData &ld, bool zero_inside, double *out)
+cudaError_t resid_norm(mg_hierarchy *h, const LevelData &ld, bool zero_inside, double *out, cudaStream_t s,
+                       double *partials)
 {
     return timed(h, KK_NORM, 16.0 * cells_d(ld.g[0].N, h->dim), [&] {
-        return mg_launch_resid_norm2(h->dim, ld.phi[0], ld.f[0], ld.g[0], zero_inside, h->partials, out, h->stream);
+        return mg_launch_resid_norm2(h->dim, ld.phi[0], ld.f[0], ld.g[0], zero_inside, partials, out, s);
     });
 }
 
-mg_status read_scalars(mg_hierarchy *h, int b, int l, double &b2, double &r2)
-{
-    double *ds = h->scal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
-    double *hs = h->hscal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
-    CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    b2 = hs[0];
-    r2 = hs[1];
-    return MG_OK;
-}
+double *level_scal(mg_hierarchy *h, int b, int l) { return h->scal + 2 * ((size_t)b * MG_MAX_LEVELS + l); }
+MgSolveCtl *level_ctl(mg_hierarchy *h, int b, int l) { return h->ctl + (size_t)b * MG_MAX_LEVELS + l; }
 
-mg_status solve_level(mg_hierarchy *h, int b, int l, mg_level_stats *st)
+// Before the iterations of one level: the one-way interface from the parent
+// (Sec. 2.1) with the initial potential (Sec. 2.4), then ||b||^2 and ||r||^2.
+cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, double *partials)
 {
-    const mg_hierarchy_desc &d = h->desc[b];
     LevelData &ld = h->lev[b][l];
     const int dim = h->dim;
     const mg_options &o = h->opt;
-    cudaStream_t s = h->stream;
-    const double fourpiG = 4.0 * M_PI * d.G;
-    double *ds = h->scal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
-
+    const double fourpiG = 4.0 * M_PI * h->desc[b].G;
+    double *ds = level_scal(h, b, l);
+    cudaError_t e;
     if (l > 0) {
         const LevelData &pd = h->lev[b][l - 1];
-        int gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
+        const int gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
         const double by = 8.0 * cells_d(ld.n + 4, dim) + 16.0 * (cells_d(ld.n + 2, dim) - cells_d(ld.n, dim));
-        CK(h, timed(h, KK_IFACE, by, [&] {
-               return mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2],
-                                          ld.phi[0], ld.rho, ld.f[0], fourpiG, gmode, ld.guess, s);
-           }));
+        e = timed(h, KK_IFACE, by, [&] {
+            return mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2],
+                                       ld.phi[0], ld.rho, ld.f[0], fourpiG, gmode, ld.guess, s);
+        });
+        if (e)
+            return e;
     } else if (ld.guess_set) {
-        CK(h, mg_launch_copy_guess(dim, ld.n, ld.guess, ld.phi[0], s));
+        if ((e = mg_launch_copy_guess(dim, ld.n, ld.guess, ld.phi[0], s)))
+            return e;
     }
-    CK(h, resid_norm(h, ld, true, ds));
-    CK(h, resid_norm(h, ld, false, ds + 1));
-    double b2, r2;
-    mg_status rs = read_scalars(h, b, l, b2, r2);
-    if (rs)
-        return rs;
-    const double bn = std::sqrt(b2);
-    double rel = bn > 0.0 ? std::sqrt(r2) / bn : 0.0;
-    int cycles = 0, outer = 0;
-    int status = MG_OK;
-    const bool mixed = o.precision == MG_MIXED;
-    while (bn > 0.0 && cycles < o.max_cycles && !(rel < o.rel_tol)) {
-        if (!mixed) {
-            CK(h, vcycle(h, ld, false));
-            cycles++;
-        } else {
-            const double nd = cells_d(ld.g[0].N, dim);
-            CK(h, timed(h, KK_DEFECT, 24.0 * nd, [&] {
-                   return mg_launch_defect(dim, ld.phi[0], ld.f[0], ld.g[0], ld.f32[0], ld.phi32[0], s);
-               }));
-            for (int c = 0; c < o.inner_cycles && cycles < o.max_cycles; c++) {
-                CK(h, vcycle(h, ld, true));
-                cycles++;
-            }
-            CK(h, timed(h, KK_ACCUM, 20.0 * nd,
-                        [&] { return mg_launch_accumulate(dim, ld.phi[0], ld.phi32[0], ld.g[0], s); }));
-        }
-        outer++;
-        CK(h, resid_norm(h, ld, false, ds + 1));
-        rs = read_scalars(h, b, l, b2, r2);
-        if (rs)
-            return rs;
-        rel = std::sqrt(r2) / bn;
-        if (!std::isfinite(rel)) {
-            status = MG_EDIVERGED;
-            break;
-        }
+    if ((e = resid_norm(h, ld, true, ds, s, partials)))
+        return e;
+    return resid_norm(h, ld, false, ds + 1, s, partials);
+}
+
+// One iteration of a level's loop (Sec. 2.3 step 14): an FP64 V-cycle, or in
+// mixed precision an FP64 defect, inner_cycles FP32 V-cycles on the
+// correction and its FP64 accumulation; then ||r||^2.
+cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, double *partials)
+{
+    const LevelData &ld = h->lev[b][l];
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    cudaError_t e;
+    if (o.precision != MG_MIXED) {
+        if ((e = vcycle(h, ld, false, s)))
+            return e;
+    } else {
+        const double nd = cells_d(ld.g[0].N, dim);
+        e = timed(h, KK_DEFECT, 24.0 * nd, [&] {
+            return mg_launch_defect(dim, ld.phi[0], ld.f[0], ld.g[0], ld.f32[0], ld.phi32[0], s);
+        });
+        if (e)
+            return e;
+        for (int c = 0; c < o.inner_cycles; c++)
+            if ((e = vcycle(h, ld, true, s)))
+                return e;
+        e = timed(h, KK_ACCUM, 20.0 * nd, [&] { return mg_launch_accumulate(dim, ld.phi[0], ld.phi32[0], ld.g[0], s); });
+        if (e)
+            return e;
     }
-    if (status == MG_OK && bn > 0.0 && !(rel < o.rel_tol) && o.rel_tol > 0.0)
+    return resid_norm(h, ld, false, level_scal(h, b, l) + 1, s, partials);
+}
+
+int cycles_per_iteration(const mg_hierarchy *h) { return h->opt.precision == MG_MIXED ? h->opt.inner_cycles : 1; }
+
+void fill_stats(const mg_hierarchy *h, const MgSolveCtl &c, mg_level_stats *st)
+{
+    int status = c.status ? MG_EDIVERGED : MG_OK;
+    if (status == MG_OK && c.bnorm > 0.0 && h->opt.rel_tol > 0.0 && !(c.rel < h->opt.rel_tol))
         status = MG_ENOCONV;
-    if (st) {
-        st->cycles = cycles;
-        st->outer_steps = mixed ? outer : cycles;
-        st->rel_res = rel;
-        st->b_norm = bn;
-        st->status = status;
+    st->cycles = c.cycles;
+    st->outer_steps = c.outer;
+    st->rel_res = c.rel;
+    st->b_norm = c.bnorm;
+    st->status = status;
+}
+
+// Host-driven loop (used while per-kernel profiling is on): the same
+// launches as the graph, with the loop decision taken on the host.
+mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
+{
+    const mg_options &o = h->opt;
+    cudaStream_t s = h->stream;
+    double *hs = h->hscal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
+    double *ds = level_scal(h, b, l);
+    CK(h, level_prelude(h, b, l, s, h->partials));
+    CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    MgSolveCtl c{};
+    c.bnorm = std::sqrt(hs[0]);
+    c.rel = c.bnorm > 0.0 ? std::sqrt(hs[1]) / c.bnorm : 0.0;
+    while (c.bnorm > 0.0 && c.status == 0 && c.cycles < o.max_cycles && !(c.rel < o.rel_tol)) {
+        CK(h, level_iteration(h, b, l, s, h->partials));
+        CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(h, cudaStreamSynchronize(s));
+        c.cycles += cycles_per_iteration(h);
+        c.outer++;
+        c.rel = std::sqrt(hs[1]) / c.bnorm;
+        if (!std::isfinite(c.rel))
+            c.status = 1;
     }
-    return (mg_status)status;
+    fill_stats(h, c, st);
+    return (mg_status)st->status;
+}
+
+// --------------------------------------------------------------------------
+// The whole solve as one CUDA graph: per (hierarchy, level) the prelude and a
+// conditional WHILE node whose body is one iteration plus a control kernel
+// that counts cycles and decides, on the device, whether to go on.
+// Hierarchies of a batch are independent and run as parallel branches.
+// --------------------------------------------------------------------------
+void destroy_graph(mg_hierarchy *h)
+{
+    if (h->gexec)
+        cudaGraphExecDestroy(h->gexec);
+    if (h->graph)
+        cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+}
+
+std::vector<char> graph_signature(const mg_hierarchy *h)
+{
+    std::vector<char> sig;
+    for (const auto &hl : h->lev)
+        for (const auto &ld : hl)
+            sig.push_back(ld.guess_set ? 1 : 0);
+    return sig;
+}
+
+cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, double *partials)
+{
+    const mg_options &o = h->opt;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e)
+        return e;
+    cudaGraphConditionalHandle hc;
+    if ((e = cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault)))
+        return e;
+    if ((e = level_prelude(h, b, l, s, partials)))
+        return e;
+    if ((e = mg_launch_ctl_init(level_ctl(h, b, l), level_scal(h, b, l), o.rel_tol, o.max_cycles, hc, s)))
+        return e;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd)))
+        return e;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &p)))
+        return e;
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)))
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+        return e;
+    cudaError_t eb = level_iteration(h, b, l, h->body_stream, partials);
+    if (!eb)
+        eb = mg_launch_ctl_step(level_ctl(h, b, l), level_scal(h, b, l), cycles_per_iteration(h), o.rel_tol,
+                                o.max_cycles, hc, h->body_stream);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(h->body_stream, &out);
+    return eb ? eb : e;
+}
+
+mg_status build_graph(mg_hierarchy *h)
+{
+    destroy_graph(h);
+    const int nbr = std::min(h->batch, MG_BRANCHES);
+    for (int i = 0; i < nbr; i++)
+        if (!h->cap[i])
+            CK(h, cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
+    if (!h->body_stream)
+        CK(h, cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+    if (!h->ev_fork) {
+        CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        for (int i = 0; i < MG_BRANCHES; i++)
+            CK(h, cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
+    }
+    CK(h, cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->cap[0]);
+    for (int i = 1; i < nbr && !e; i++)
+        e = cudaStreamWaitEvent(h->cap[i], h->ev_fork, 0);
+    for (int b = 0; b < h->batch && !e; b++)
+        for (int l = 0; l < h->desc[b].num_levels && !e; l++)
+            e = capture_level(h, b, l, h->cap[b % nbr], h->partials + (size_t)(b % nbr) * MG_NORM_BLOCKS);
+    for (int i = 1; i < nbr && !e; i++) {
+        e = cudaEventRecord(h->ev_join[i], h->cap[i]);
+        if (!e)
+            e = cudaStreamWaitEvent(h->cap[0], h->ev_join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h->cap[0], &g);
+    if (e || ee) {
+        if (g)
+            cudaGraphDestroy(g);
+        return fail_cuda(h, e ? e : ee, "capture of the solve graph");
+    }
+    h->graph = g;
+    CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
+    h->graph_sig = graph_signature(h);
+    return MG_OK;
+}
+
+mg_status solve_graph(mg_hierarchy *h, mg_level_stats *stats)
+{
+    if (!h->gexec || h->graph_sig != graph_signature(h)) {
+        mg_status s = build_graph(h);
+        if (s)
+            return s;
+    }
+    const size_t nctl = (size_t)h->batch * MG_MAX_LEVELS;
+    CK(h, cudaGraphLaunch(h->gexec, h->stream));
+    CK(h, cudaMemcpyAsync(h->hctl, h->ctl, nctl * sizeof(MgSolveCtl), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    mg_status worst = MG_OK;
+    for (int b = 0; b < h->batch; b++)
+        for (int l = 0; l < h->desc[b].num_levels; l++) {
+            mg_level_stats st{};
+            fill_stats(h, h->hctl[(size_t)b * MG_MAX_LEVELS + l], &st);
+            if (stats)
+                stats[(size_t)b * MG_MAX_LEVELS + l] = st;
+            if (st.status == MG_EDIVERGED || (st.status == MG_ENOCONV && worst == MG_OK))
+                worst = (mg_status)st.status;
+        }
+    return worst;
 }
 
 }  // namespace
@@ -512,7 +675,8 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     }
     h->stage_elems = stage;
     slots.push_back({(void **)&h->stage, align256(stage * sizeof(double))});
-    slots.push_back({(void **)&h->partials, align256(MG_NORM_BLOCKS * sizeof(double))});
+    slots.push_back({(void **)&h->partials, align256((size_t)MG_BRANCHES * MG_NORM_BLOCKS * sizeof(double))});
+    slots.push_back({(void **)&h->ctl, align256((size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl))});
     slots.push_back({(void **)&h->scal, align256((size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double))});
     for (auto &sl : slots)
         bytes += sl.bytes;
@@ -529,8 +693,12 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
         pos += sl.bytes;
     }
     e = cudaMallocHost((void **)&h->hscal, (size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h->hctl, (size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl));
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (h->hscal)
+            cudaFreeHost(h->hscal);
         cudaFree(h->arena);
         delete h;
         return fail(nullptr, MG_ENOMEM, "pinned host allocation failed");
@@ -542,6 +710,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFreeHost(h->hscal);
+        cudaFreeHost(h->hctl);
         cudaFree(h->arena);
         delete h;
         return fail(nullptr, MG_ECUDA, "arena initialisation failed: %s", cudaGetErrorString(e));
@@ -627,17 +796,22 @@ mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats)
             if (!h->lev[b][l].density_set)
                 return fail(h, MG_ESTATE, "density of hierarchy %d level %d not set", b, l);
     mg_status worst = MG_OK;
-    for (int b = 0; b < h->batch; b++) {
-        for (int l = 0; l < h->desc[b].num_levels; l++) {
-            mg_level_stats st{};
-            mg_status s = solve_level(h, b, l, &st);
-            if (s == MG_ECUDA || s == MG_ETIMEOUT)
-                return s;
-            if (stats)
-                stats[(size_t)b * MG_MAX_LEVELS + l] = st;
-            if (s == MG_EDIVERGED || (s == MG_ENOCONV && worst == MG_OK))
-                worst = s;
-        }
+    if (!h->prof.on) {
+        worst = solve_graph(h, stats);
+        if (worst == MG_ECUDA || worst == MG_ETIMEOUT)
+            return worst;
+    } else {
+        for (int b = 0; b < h->batch; b++)
+            for (int l = 0; l < h->desc[b].num_levels; l++) {
+                mg_level_stats st{};
+                mg_status s = solve_level_host(h, b, l, &st);
+                if (s == MG_ECUDA || s == MG_ETIMEOUT)
+                    return s;
+                if (stats)
+                    stats[(size_t)b * MG_MAX_LEVELS + l] = st;
+                if (s == MG_EDIVERGED || (s == MG_ENOCONV && worst == MG_OK))
+                    worst = s;
+            }
     }
     h->solved = true;
     return worst;
@@ -729,8 +903,21 @@ mg_status mg_destroy(mg_hierarchy *h)
     }
     for (cudaEvent_t e : h->prof.pool)
         cudaEventDestroy(e);
+    destroy_graph(h);
+    for (int i = 0; i < MG_BRANCHES; i++) {
+        if (h->cap[i])
+            cudaStreamDestroy(h->cap[i]);
+        if (h->ev_join[i])
+            cudaEventDestroy(h->ev_join[i]);
+    }
+    if (h->body_stream)
+        cudaStreamDestroy(h->body_stream);
+    if (h->ev_fork)
+        cudaEventDestroy(h->ev_fork);
     if (h->hscal)
         cudaFreeHost(h->hscal);
+    if (h->hctl)
+        cudaFreeHost(h->hctl);
     cudaGetLastError();
     delete h;
     return MG_OK;

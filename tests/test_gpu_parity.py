@@ -261,3 +261,63 @@ def test_second_order_on_gpu(mg):
             order = np.log2(prev / cur)
             assert np.all(order > 1.7), order
         prev = cur
+
+
+def test_graph_path_equals_host_loop(mg):
+    """The solve graph (device-side loop control) and the host-driven loop
+    (taken while per-kernel profiling is on) launch the same kernels in the
+    same order: identical results and cycle counts."""
+    import torch
+    H = I.config_3d_offset_sphere(32, 3)
+    inp = I.level_inputs(H)
+    res = {}
+    for prof in (False, True):
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=2, nu_post=2))
+        try:
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            for l in range(1, H.num_levels):
+                mg.mg_set_density(h, 0, l, dev(inp[l]["rho"]))
+            mg.mg_profile(h, prof)
+            _, st = mg.mg_solve(h, 1)
+            if prof:
+                k = mg.mg_profile_read(h)
+                assert k["smooth_colour"][0] > 0 and k["resid_norm"][0] > 0
+            out = []
+            for l in range(H.num_levels):
+                phi = torch.zeros((H.n[l],) * 3, dtype=torch.float64, device="cuda")
+                mg.mg_forces(h, 0, l, phi, None)
+                torch.cuda.synchronize()
+                out.append((phi.cpu().numpy(), st[0][l]["cycles"]))
+            res[prof] = out
+        finally:
+            mg.mg_destroy(h)
+    for (a, ca), (b, cb) in zip(res[False], res[True]):
+        assert ca == cb and np.array_equal(a, b)
+
+
+def test_heterogeneous_batch(mg):
+    """Uneven hierarchies solved together (parallel branches of the solve
+    graph) give the same results as each solved alone."""
+    Hs = [I.random_hierarchy(s) for s in range(5)]
+    Hs = [H for H in Hs if max(H.n) <= 96][:3]
+    import torch
+    h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], mg.options())
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        for b, H in enumerate(Hs):
+            inp = I.level_inputs(H)
+            mg.mg_set_density(h, b, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            for l in range(1, H.num_levels):
+                mg.mg_set_density(h, b, l, dev(inp[l]["rho"]))
+        _, st = mg.mg_solve(h, len(Hs))
+        for b, H in enumerate(Hs):
+            _, alone = gpu_solve(mg, H, I.level_inputs(H), allow_noconv=False)
+            for l in range(H.num_levels):
+                phi = torch.zeros((H.n[l],) * 3, dtype=torch.float64, device="cuda")
+                mg.mg_forces(h, b, l, phi, None)
+                torch.cuda.synchronize()
+                assert st[b][l]["cycles"] == alone[l]["cycles"]
+                assert np.array_equal(phi.cpu().numpy(), alone[l]["phi"])
+    finally:
+        mg.mg_destroy(h)
