@@ -176,6 +176,34 @@ mg_status mg_profile(mg_hierarchy *h, int enable);
 /* Fills up to cap entries; returns how many kernel kinds ran, or -1. */
 int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap);
 
+/* Allocation-free solve of one refinement level, for callers that cannot
+ * allocate device memory: codes that give all of the GPU's memory to their
+ * own pool, or call the Poisson solve inside a time step where cudaMalloc and
+ * cudaFree (and the device-wide synchronisation they imply) are not allowed.
+ * The paper has no counterpart; the arithmetic is that of mg_solve for a
+ * single level (FP64 V-cycles, zero ghost rule on coarse levels), with the
+ * same kernels in the same order.
+ *   rho   device, (n+4)^d block: density on the solved region (Omega and the
+ *         inner buffer ring, storage indices 1..n+2); other cells unread.
+ *   phi   device, (n+4)^d block: on entry the outer ring holds the Dirichlet
+ *         potential and the solved region the initial guess; on return the
+ *         solved region holds the solution.
+ *   h, G  cell size and gravitational constant; opt as for mg_solve (NULL =
+ *         defaults); precision must be MG_FP64; opt->stream is used.
+ *   stats host, may be NULL.
+ * Working memory is one library-owned device array of 4 MiB (every GPU that
+ * loads the library holds it until the process exits): n <= 64 in 3D and
+ * n <= 540 in 2D; larger n is rejected with MG_EINVAL before any GPU work.
+ * The array is shared by every call and keeps the previous call's contents
+ * (the call clears the part it uses): calls whose GPU work overlaps race and
+ * must not be issued concurrently.  The first call on each device looks the
+ * array's device address up once (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture.  Errors:
+ * MG_EINVAL (message on stderr), MG_ECUDA, and MG_ENOCONV / MG_EDIVERGED as
+ * for mg_solve.  The call returns after the solve has finished. */
+mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, const double *rho, double *phi,
+                                 const mg_options *opt, mg_level_stats *stats);
+
 /* Multigrid level sizes of Sec. 2.2 for a solved region of M cells per edge:
  * writes up to cap sizes into N and returns how many levels there are. */
 int mg_level_sizes(int M, int *N, int cap);

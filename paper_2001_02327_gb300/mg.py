@@ -55,6 +55,8 @@ _SIGS = {
     "mg_error_message": (C.c_char_p, [_vp]),
     "mg_level_sizes": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int]),
     "mg_profile": (C.c_int, [_vp, C.c_int]),
+    "mg_solve_level_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
+                                         C.POINTER(mg_options), C.POINTER(mg_level_stats)]),
     "mg_profile_read": (C.c_int, [_vp, C.POINTER(mg_kernel_stat), C.c_int]),
 }
 
@@ -170,6 +172,14 @@ def mg_profile_read(h):
     if k < 0:
         raise MGError(MG_ESTATE, mg_error_message(h))
     return {buf[i].name.decode(): (buf[i].launches, buf[i].ms, buf[i].bytes) for i in range(k)}
+
+
+def mg_solve_level_noalloc(dim, n, h, G, rho, phi, opt=None):
+    """Allocation-free single-level solve (device (n+4)^d blocks); returns (status, stats dict)."""
+    st = mg_level_stats()
+    s = LIB.mg_solve_level_noalloc(dim, n, h, G, _addr(rho), _addr(phi),
+                                   C.byref(opt) if opt is not None else None, C.byref(st))
+    return s, {"cycles": st.cycles, "rel_res": st.rel_res, "b_norm": st.b_norm, "status": st.status}
 
 
 def mg_destroy(h):
