@@ -370,6 +370,37 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_level_case(args):
+    """One 3D level of n=254 (arrays of 258^3 doubles, 137 MB each: larger
+    than L2) with seeded random density and boundary, a fixed number of
+    V-cycles.  Used for profiler captures of the kernels on DRAM-resident
+    data; prints one line of timing, not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    n = args.level_n
+    rng = np.random.default_rng(I.BASE_SEED + 254)
+    H = I.Hierarchy(3, [n], [(0.0, 0.0, 0.0)], 1.0 / n, 1.0, [], f"level{n}")
+    dev = lambda a: torch.from_numpy(a).cuda()
+    rho, bcr, bcp = (dev(rng.standard_normal((k,) * 3)) for k in (n, n + 2, n + 4))
+    prec = mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(max_cycles=args.cycles, rel_tol=0.0, precision=prec,
+                                                             inner_cycles=1))
+    try:
+        for rep in range(2):
+            mg.mg_set_density(h, 0, 0, rho, bcr, bcp)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = mg.mg_solve(h, 1, allow_noconv=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        print(json.dumps({"case": f"level n={n}", "precision": args.precision, "cycles": st[0][0]["cycles"],
+                          "ms": dt * 1e3, "rel_res": st[0][0]["rel_res"]}))
+    finally:
+        mg.mg_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,9 +408,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="bench", choices=["bench", "level"],
+                    help="level: one DRAM-resident 3D level for profiler captures")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--level-n", type=int, default=254)
+    ap.add_argument("--cycles", type=int, default=2)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.impl == "reference":
+    if args.case == "level":
+        run_level_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
