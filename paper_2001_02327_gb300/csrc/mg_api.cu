@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -30,7 +31,46 @@ struct LevelData {
     double *rho = nullptr;         // (n+4)^d density (Omega and inner ring)
     double *guess = nullptr;       // (n+2)^d optional initial potential
     bool density_set = false, guess_set = false;
+    int Ls[2] = {0, 0};            // first level handled by the one-block kernel [fp64, fp32]
+    MgBottom bt[2];
 };
+
+// Largest multigrid level (cells per edge) given to the one-block bottom
+// kernel: one SM does FP32 work fast enough for 17^3, FP64 (two FMA per
+// clock per SM on this part) only for 8^3.  MG_BOTTOM_N64 / MG_BOTTOM_N32
+// override (0 disables the kernel for all but the one-cell level).
+int bottom_limit(bool fp32)
+{
+    const char *v = std::getenv(fp32 ? "MG_BOTTOM_N32" : "MG_BOTTOM_N64");
+    if (v && *v)
+        return std::atoi(v);
+    return fp32 ? 17 : 8;
+}
+
+void plan_bottom(LevelData &ld, int dim)
+{
+    for (int w = 0; w < 2; w++) {
+        const bool fp32 = w == 1;
+        const int lim = bottom_limit(fp32);
+        int Ls = ld.nmg - 1;
+        for (int L = 0; L < ld.nmg; L++) {
+            if (ld.g[L].N > lim || ld.nmg - L > MG_BOTTOM_MAX)
+                continue;
+            MgBottom bt;
+            bt.nlev = ld.nmg - L;
+            for (int q = 0; q < bt.nlev; q++)
+                bt.g[q] = ld.g[L + q];
+            if (mg_bottom_smem(dim, fp32, bt) <= MG_BOTTOM_SMEM_MAX) {
+                Ls = L;
+                break;
+            }
+        }
+        ld.Ls[w] = Ls;
+        ld.bt[w].nlev = ld.nmg - Ls;
+        for (int q = 0; q < ld.bt[w].nlev; q++)
+            ld.bt[w].g[q] = ld.g[Ls + q];
+    }
+}
 
 long cells(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
 
@@ -72,10 +112,10 @@ void build_geometry(LevelData &ld, int dim)
 #define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
 
 enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
-                  KK_SETDENS, KK_COUNT };
+                  KK_SETDENS, KK_BOTTOM, KK_COUNT };
 const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
                                          "defect",        "accumulate",     "interface",       "forces",
-                                         "set_density"};
+                                         "set_density",   "bottom"};
 
 // Per-launch CUDA-event timing on the hierarchy's stream (mg_profile).
 struct Profiler {
@@ -111,6 +151,7 @@ struct mg_hierarchy {
     std::string err;
     Profiler prof;
     // solve graph
+    bool use_graph = true;          // MG_SOLVE_GRAPH=0: host-driven loop (for kernel profilers)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<char> graph_sig;
@@ -273,7 +314,8 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     return cudaSuccess;
 }
 
-// the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level
+// the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level;
+// the levels from Ls down run in the one-block kernel
 cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t s)
 {
     const int dim = h->dim;
@@ -281,33 +323,37 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     const int w = fp32 ? 4 : 8;
     auto P = [&](int L) -> void * { return fp32 ? (void *)ld.phi32[L] : (void *)ld.phi[L]; };
     auto F = [&](int L) -> void * { return fp32 ? (void *)ld.f32[L] : (void *)ld.f[L]; };
+    const int Ls = ld.Ls[fp32 ? 1 : 0];
+    const MgBottom &bt = ld.bt[fp32 ? 1 : 0];
+    auto bottom = [&]() {
+        return timed(h, KK_BOTTOM, 3.0 * w * cells_d(ld.g[Ls].E, dim),
+                     [&] { return mg_launch_bottom(dim, fp32, P(Ls), F(Ls), bt, o.nu_pre, o.nu_post, s); });
+    };
     cudaError_t e;
-    if (ld.nmg == 1)
-        return smooth(h, ld, 0, fp32, o.nu_pre + o.nu_post, s);
+    if (Ls == 0)
+        return bottom();                                                                  // whole cycle
     if ((e = smooth(h, ld, 0, fp32, o.nu_pre, s)))                                        // step 2
         return e;
-    int L = 0;
-    do {
+    for (int L = 0; L < Ls; L++) {
         const double by = 2.0 * w * (cells_d(ld.g[L].N, dim) + cells_d(ld.g[L + 1].N, dim));
         e = timed(h, KK_RESTRICT, by, [&] {
             return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s);
         });                                                                               // steps 4-5
         if (e)
             return e;
-        const int sweeps = ld.g[L + 1].N == 1 ? (o.nu_pre > 0 ? 1 : 0) : o.nu_pre;       // one cell: exact
-        if ((e = smooth(h, ld, L + 1, fp32, sweeps, s)))                                  // step 6
+        if (L + 1 < Ls && (e = smooth(h, ld, L + 1, fp32, o.nu_pre, s)))                  // step 6
             return e;
-        L++;
-    } while (ld.g[L].N > 1 && L + 1 < ld.nmg);                                            // step 8
-    do {
+    }
+    if ((e = bottom()))                                                                   // steps 6-11, L >= Ls
+        return e;
+    for (int L = Ls; L > 0; L--) {
         const double by = w * (cells_d(ld.g[L].N, dim) + 2.0 * cells_d(ld.g[L - 1].N, dim));
         e = timed(h, KK_PROLONG, by, [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
         if (e)                                                                            // step 10
             return e;
         if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s)))                               // step 11
             return e;
-        L--;
-    } while (L > 0);                                                                      // step 13
+    }
     return cudaSuccess;
 }
 
@@ -658,6 +704,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                     ld.off[a] = (int)std::floor((d.lo[l][a] - d.lo[l - 1][a]) / hp + 0.5);
             }
             build_geometry(ld, dim);
+            plan_bottom(ld, dim);
             for (int L = 0; L < ld.nmg; L++) {
                 const size_t c = (size_t)cells(ld.g[L].E, dim);
                 slots.push_back({(void **)&ld.phi[L], align256(c * sizeof(double))});
@@ -703,8 +750,14 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
         delete h;
         return fail(nullptr, MG_ENOMEM, "pinned host allocation failed");
     }
+    {
+        const char *v = std::getenv("MG_SOLVE_GRAPH");
+        h->use_graph = !(v && v[0] == '0');
+    }
     // ghost layers and rings start at zero
-    e = mg_launch_zero(h->arena, bytes, h->stream);
+    e = mg_bottom_prepare();
+    if (e == cudaSuccess)
+        e = mg_launch_zero(h->arena, bytes, h->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -796,7 +849,7 @@ mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats)
             if (!h->lev[b][l].density_set)
                 return fail(h, MG_ESTATE, "density of hierarchy %d level %d not set", b, l);
     mg_status worst = MG_OK;
-    if (!h->prof.on) {
+    if (!h->prof.on && h->use_graph) {
         worst = solve_graph(h, stats);
         if (worst == MG_ECUDA || worst == MG_ETIMEOUT)
             return worst;

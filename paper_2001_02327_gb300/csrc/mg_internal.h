@@ -58,6 +58,19 @@ __device__ __forceinline__ void mg_axis_coef(int i, const MgGeom &g, T &wm, T &w
 // One colour (0 = red, (i+j[+k]) even; 1 = black) of a Gauss-Seidel sweep.
 cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int colour,
                              cudaStream_t s);
+// The levels at and below a multigrid level Ls, run by one thread block with
+// all their arrays in shared memory (k_bottom).
+#define MG_BOTTOM_MAX 12
+#define MG_BOTTOM_SMEM_MAX (200 * 1024)
+struct MgBottom {
+    int nlev;                   // levels Ls .. Ls+nlev-1 (the last one has one cell)
+    MgGeom g[MG_BOTTOM_MAX];
+};
+size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt);
+cudaError_t mg_bottom_prepare();   // once per device before the first launch
+cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const MgBottom &bt, int nu_pre,
+                             int nu_post, cudaStream_t s);
+
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
                                      void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s);
 cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeom &gc, void *phi_f, const MgGeom &gf,

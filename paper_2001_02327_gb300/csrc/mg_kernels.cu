@@ -7,6 +7,7 @@
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kBottomThreads = 512;
 
 inline int grid_for(long work, int cap = 152 * 16)
 {
@@ -52,17 +53,18 @@ __device__ __forceinline__ void stencil_terms(const T *__restrict__ phi, const M
     }
 }
 
-// One colour of a red-black Gauss-Seidel sweep (Sec. 2.3 steps 2, 6, 11).
-// Red cells have (i+j[+k]) even and are updated first.
+// One colour of a red-black Gauss-Seidel sweep (Sec. 2.3 steps 2, 6, 11)
+// over work items t0, t0+stride, ...  Red cells have (i+j[+k]) even and are
+// updated first.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
-                                                            int colour)
+__device__ __forceinline__ void op_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g,
+                                                 int colour, long t0, long stride)
 {
     const int N = g.N;
     const int half = (N + 1) >> 1;
     const long total = (long)half * N * (DIM == 3 ? N : 1);
     const T h2 = T(g.h2);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    for (long t = t0; t < total; t += stride) {
         const int i2 = (int)(t % half);
         const long r = t / half;
         const int j = (int)(r % N) + 1;
@@ -93,14 +95,14 @@ __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__r
 // 2^d-child average (step 5; fine cells beyond N contribute zero); the
 // coarse correction starts from zero.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
-                                                             MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
-                                                             MgGeom gc)
+__device__ __forceinline__ void op_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                  const MgGeom &gf, T *__restrict__ phi_c, T *__restrict__ f_c,
+                                                  const MgGeom &gc, long t0, long stride)
 {
     const int Nc = gc.N, Nf = gf.N;
     const long total = (long)Nc * Nc * (DIM == 3 ? Nc : 1);
     const T w = DIM == 3 ? T(0.125) : T(0.25);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    for (long t = t0; t < total; t += stride) {
         const int I = (int)(t % Nc) + 1;
         const int J = (int)((t / Nc) % Nc) + 1;
         const int K = DIM == 3 ? (int)(t / ((long)Nc * Nc)) + 1 : 0;
@@ -154,12 +156,12 @@ __device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, dou
 // Prolongation and correction (Sec. 2.3 step 10; weights 3/4, 1/4 per axis,
 // i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse ghosts by the rule.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_c, MgGeom gc, T *__restrict__ phi_f,
-                                                      MgGeom gf)
+__device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const MgGeom &gc, T *__restrict__ phi_f,
+                                           const MgGeom &gf, long t0, long stride)
 {
     const int Nf = gf.N;
     const long total = (long)Nf * Nf * (DIM == 3 ? Nf : 1);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    for (long t = t0; t < total; t += stride) {
         int f[3];
         f[0] = (int)(t % Nf) + 1;
         f[1] = (int)((t / Nf) % Nf) + 1;
@@ -188,6 +190,89 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_
         }
         phi_f[lin<DIM>(f[0], f[1], f[2], gf.E)] += v;
     }
+}
+
+__device__ __forceinline__ long gtid() { return blockIdx.x * (long)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long gstride() { return (long)gridDim.x * blockDim.x; }
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
+                                                            int colour)
+{
+    op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                             MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
+                                                             MgGeom gc)
+{
+    op_resid_restrict<T, DIM>(phi_f, f_f, gf, phi_c, f_c, gc, gtid(), gstride());
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_c, MgGeom gc, T *__restrict__ phi_f,
+                                                      MgGeom gf)
+{
+    op_prolong<T, DIM>(phi_c, gc, phi_f, gf, gtid(), gstride());
+}
+
+// The part of the V-cycle at and below multigrid level Ls (Sec. 2.3 steps
+// 6-11 restricted to those levels) in one thread block, every array of those
+// levels in shared memory: pre-smoothing at Ls, restriction and smoothing
+// down to the one-cell level, prolongation and post-smoothing back up to Ls.
+// Phi and f of level Ls come from global memory (f written by the
+// restriction from Ls-1, Phi zero; or the finest level itself when Ls = 0);
+// the smoothed Phi of level Ls goes back.  Same per-cell arithmetic and the
+// same order of phases as the one-kernel-per-phase path.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g, const T *__restrict__ f_g,
+                                                           MgBottom bt, int nu_pre, int nu_post)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *phi[MG_BOTTOM_MAX];
+    T *f[MG_BOTTOM_MAX];
+    long off = 0;
+    for (int q = 0; q < bt.nlev; q++) {
+        const long c = DIM == 3 ? (long)bt.g[q].E * bt.g[q].E * bt.g[q].E : (long)bt.g[q].E * bt.g[q].E;
+        phi[q] = sm + off;
+        f[q] = sm + off + c;
+        off += 2 * c;
+    }
+    const long tid = threadIdx.x, nth = blockDim.x;
+    const long c0 = DIM == 3 ? (long)bt.g[0].E * bt.g[0].E * bt.g[0].E : (long)bt.g[0].E * bt.g[0].E;
+    for (long t = tid; t < off; t += nth)
+        sm[t] = T(0);
+    __syncthreads();
+    for (long t = tid; t < c0; t += nth) {
+        phi[0][t] = phi_g[t];
+        f[0][t] = f_g[t];
+    }
+    __syncthreads();
+    auto smooth = [&](int q, int sweeps) {
+        for (int sw = 0; sw < sweeps; sw++)
+            for (int c = 0; c < 2; c++) {
+                op_smooth_colour<T, DIM>(phi[q], f[q], bt.g[q], c, tid, nth);
+                __syncthreads();
+            }
+    };
+    smooth(0, bt.g[0].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
+    int q = 0;
+    while (bt.g[q].N > 1 && q + 1 < bt.nlev) {
+        op_resid_restrict<T, DIM>(phi[q], f[q], bt.g[q], phi[q + 1], f[q + 1], bt.g[q + 1], tid, nth);
+        __syncthreads();
+        smooth(q + 1, bt.g[q + 1].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
+        q++;
+    }
+    while (q > 0) {
+        op_prolong<T, DIM>(phi[q], bt.g[q], phi[q - 1], bt.g[q - 1], tid, nth);
+        __syncthreads();
+        smooth(q - 1, nu_post);
+        q--;
+    }
+    for (long t = tid; t < c0; t += nth)
+        phi_g[t] = phi[0][t];
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -495,6 +580,46 @@ cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const
             k_smooth_colour<float, 2><<<grid, kThreads, 0, s>>>((float *)phi, (const float *)f, g, c);
         else
             k_smooth_colour<double, 2><<<grid, kThreads, 0, s>>>((double *)phi, (const double *)f, g, c);
+    }
+    return cudaGetLastError();
+}
+
+size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt)
+{
+    size_t c = 0;
+    for (int q = 0; q < bt.nlev; q++)
+        c += 2 * (size_t)cube(bt.g[q].E, dim);
+    return c * (fp32 ? 4 : 8);
+}
+
+cudaError_t mg_bottom_prepare()
+{
+    // allow the bottom kernel the dynamic shared memory it may ask for (current device)
+    const int lim = MG_BOTTOM_SMEM_MAX;
+    cudaError_t e = cudaFuncSetAttribute(k_bottom<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(k_bottom<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(k_bottom<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(k_bottom<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return e;
+}
+
+cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const MgBottom &bt, int nu_pre,
+                             int nu_post, cudaStream_t s)
+{
+    const size_t smem = mg_bottom_smem(dim, fp32, bt);
+    if (dim == 3) {
+        if (fp32)
+            k_bottom<float, 3><<<1, kBottomThreads, smem, s>>>((float *)phi, (const float *)f, bt, nu_pre, nu_post);
+        else
+            k_bottom<double, 3><<<1, kBottomThreads, smem, s>>>((double *)phi, (const double *)f, bt, nu_pre, nu_post);
+    } else {
+        if (fp32)
+            k_bottom<float, 2><<<1, kBottomThreads, smem, s>>>((float *)phi, (const float *)f, bt, nu_pre, nu_post);
+        else
+            k_bottom<double, 2><<<1, kBottomThreads, smem, s>>>((double *)phi, (const double *)f, bt, nu_pre, nu_post);
     }
     return cudaGetLastError();
 }
