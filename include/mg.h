@@ -63,7 +63,8 @@ enum { MG_FORCE_EQ2 = 0,     /* fourth-order difference of Eq. 2 (default) */
        MG_FORCE_CD2 = 1 };   /* two-point central difference */
 
 /* Geometry of one hierarchy (Sec. 2.1).  Level l has n[l] cells per edge
- * (even, >= 4), lower corner lo[l] and cell size h0 / 2^l.  For l > 0 the
+ * (>= 2; even above level 0; at most 1286 in 3D), lower corner lo[l] and
+ * cell size h0 / 2^l.  For l > 0 the
  * patch must sit on parent cell faces, its lower corner o[a] whole parent
  * cells above the parent's, with 1 <= o[a] <= n[l-1] - n[l]/2 - 1 so that
  * every buffer cell interpolates from cells the parent solves for. */

@@ -31,20 +31,23 @@ struct LevelData {
     double *rho = nullptr;         // (n+4)^d density (Omega and inner ring)
     double *guess = nullptr;       // (n+2)^d optional initial potential
     bool density_set = false, guess_set = false;
+    double *tab64[MG_MAX_MG] = {}; // boundary diagonal tables of the coarse levels (device)
+    float *tab32[MG_MAX_MG] = {};
     int Ls[2] = {0, 0};            // first level handled by the one-block kernel [fp64, fp32]
     MgBottom bt[2];
 };
 
 // Largest multigrid level (cells per edge) given to the one-block bottom
-// kernel: one SM does FP32 work fast enough for 17^3, FP64 (two FMA per
-// clock per SM on this part) only for 8^3.  MG_BOTTOM_N64 / MG_BOTTOM_N32
-// override (0 disables the kernel for all but the one-cell level).
+// kernel.  Measured on the 4x64^3 workload: 8 beats 17 in both precisions
+// (one SM runs FP64 at two FMA per clock; even in FP32 a 17^3 level is
+// faster spread over the GPU).  MG_BOTTOM_N64 / MG_BOTTOM_N32 override
+// (0 leaves only the one-cell level to the kernel).
 int bottom_limit(bool fp32)
 {
     const char *v = std::getenv(fp32 ? "MG_BOTTOM_N32" : "MG_BOTTOM_N64");
     if (v && *v)
         return std::atoi(v);
-    return fp32 ? 17 : 8;
+    return 8;
 }
 
 void plan_bottom(LevelData &ld, int dim)
@@ -95,6 +98,8 @@ void build_geometry(LevelData &ld, int dim)
     (void)dim;
     for (int L = 0; L < ld.nmg; L++) {
         MgGeom &g = ld.g[L];
+        g.tab64 = nullptr;
+        g.tab32 = nullptr;
         g.N = N[L];
         g.E = N[L] + 2;
         g.L = L;
@@ -142,7 +147,8 @@ struct mg_hierarchy {
     size_t arena_bytes = 0;
     double *stage = nullptr;        // device staging for host-pointer I/O
     size_t stage_elems = 0;
-    double *partials = nullptr;     // MG_BRANCHES * MG_NORM_BLOCKS reduction scratch
+    double *partials = nullptr;     // MG_BRANCHES * 2 * MG_NORM_BLOCKS_MAX reduction scratch
+    unsigned *counters = nullptr;   // MG_BRANCHES block counters of the norm kernel
     double *scal = nullptr;         // device scalars: [b][l][2] = ||b||^2, ||r||^2
     double *hscal = nullptr;        // pinned mirror
     MgSolveCtl *ctl = nullptr;      // device loop state per (b, l)
@@ -274,6 +280,8 @@ mg_status check_desc(const mg_hierarchy_desc &d, int b, int dim0)
         const int n = d.n[l];
         if (n < 2 || n + 2 > (1 << (MG_MAX_MG - 1)) || (l > 0 && (n & 1)))
             return fail(nullptr, MG_EINVAL, "hierarchy %d level %d: n=%d (need >= 2, even above level 0)", b, l, n);
+        if (d.dim == 3 && n > 1286)   // (n+4)^3 cells indexed in 32 bits
+            return fail(nullptr, MG_EINVAL, "hierarchy %d level %d: n=%d exceeds 1286 in 3D", b, l, n);
         if (l == 0)
             continue;
         const double hp = d.h0 / (double)(1L << (l - 1));
@@ -357,11 +365,13 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     return cudaSuccess;
 }
 
-cudaError_t resid_norm(mg_hierarchy *h, const LevelData &ld, bool zero_inside, double *out, cudaStream_t s,
-                       double *partials)
+// ||b||^2 (which & 1) and ||r||^2 (which & 2) of a level into scal[0..1];
+// `branch` selects the reduction scratch of a parallel graph branch.
+cudaError_t norms(mg_hierarchy *h, const LevelData &ld, int which, double *scal, cudaStream_t s, int branch)
 {
     return timed(h, KK_NORM, 16.0 * cells_d(ld.g[0].N, h->dim), [&] {
-        return mg_launch_resid_norm2(h->dim, ld.phi[0], ld.f[0], ld.g[0], zero_inside, partials, out, s);
+        return mg_launch_norms2(h->dim, ld.phi[0], ld.f[0], ld.g[0], which,
+                                h->partials + (size_t)branch * 2 * MG_NORM_BLOCKS_MAX, h->counters + branch, scal, s);
     });
 }
 
@@ -370,7 +380,7 @@ MgSolveCtl *level_ctl(mg_hierarchy *h, int b, int l) { return h->ctl + (size_t)b
 
 // Before the iterations of one level: the one-way interface from the parent
 // (Sec. 2.1) with the initial potential (Sec. 2.4), then ||b||^2 and ||r||^2.
-cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, double *partials)
+cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, int branch)
 {
     LevelData &ld = h->lev[b][l];
     const int dim = h->dim;
@@ -392,15 +402,13 @@ cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, double 
         if ((e = mg_launch_copy_guess(dim, ld.n, ld.guess, ld.phi[0], s)))
             return e;
     }
-    if ((e = resid_norm(h, ld, true, ds, s, partials)))
-        return e;
-    return resid_norm(h, ld, false, ds + 1, s, partials);
+    return norms(h, ld, 3, ds, s, branch);
 }
 
 // One iteration of a level's loop (Sec. 2.3 step 14): an FP64 V-cycle, or in
 // mixed precision an FP64 defect, inner_cycles FP32 V-cycles on the
 // correction and its FP64 accumulation; then ||r||^2.
-cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, double *partials)
+cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int branch)
 {
     const LevelData &ld = h->lev[b][l];
     const int dim = h->dim;
@@ -423,7 +431,7 @@ cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, doubl
         if (e)
             return e;
     }
-    return resid_norm(h, ld, false, level_scal(h, b, l) + 1, s, partials);
+    return norms(h, ld, 2, level_scal(h, b, l), s, branch);
 }
 
 int cycles_per_iteration(const mg_hierarchy *h) { return h->opt.precision == MG_MIXED ? h->opt.inner_cycles : 1; }
@@ -448,14 +456,14 @@ mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
     cudaStream_t s = h->stream;
     double *hs = h->hscal + 2 * ((size_t)b * MG_MAX_LEVELS + l);
     double *ds = level_scal(h, b, l);
-    CK(h, level_prelude(h, b, l, s, h->partials));
+    CK(h, level_prelude(h, b, l, s, 0));
     CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
     MgSolveCtl c{};
     c.bnorm = std::sqrt(hs[0]);
     c.rel = c.bnorm > 0.0 ? std::sqrt(hs[1]) / c.bnorm : 0.0;
     while (c.bnorm > 0.0 && c.status == 0 && c.cycles < o.max_cycles && !(c.rel < o.rel_tol)) {
-        CK(h, level_iteration(h, b, l, s, h->partials));
+        CK(h, level_iteration(h, b, l, s, 0));
         CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(h, cudaStreamSynchronize(s));
         c.cycles += cycles_per_iteration(h);
@@ -493,7 +501,7 @@ std::vector<char> graph_signature(const mg_hierarchy *h)
     return sig;
 }
 
-cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, double *partials)
+cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, int branch)
 {
     const mg_options &o = h->opt;
     cudaStreamCaptureStatus cs;
@@ -504,7 +512,7 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, double 
     cudaGraphConditionalHandle hc;
     if ((e = cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault)))
         return e;
-    if ((e = level_prelude(h, b, l, s, partials)))
+    if ((e = level_prelude(h, b, l, s, branch)))
         return e;
     if ((e = mg_launch_ctl_init(level_ctl(h, b, l), level_scal(h, b, l), o.rel_tol, o.max_cycles, hc, s)))
         return e;
@@ -526,7 +534,7 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, double 
         return e;
     if ((e = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
         return e;
-    cudaError_t eb = level_iteration(h, b, l, h->body_stream, partials);
+    cudaError_t eb = level_iteration(h, b, l, h->body_stream, branch);
     if (!eb)
         eb = mg_launch_ctl_step(level_ctl(h, b, l), level_scal(h, b, l), cycles_per_iteration(h), o.rel_tol,
                                 o.max_cycles, hc, h->body_stream);
@@ -555,7 +563,7 @@ mg_status build_graph(mg_hierarchy *h)
         e = cudaStreamWaitEvent(h->cap[i], h->ev_fork, 0);
     for (int b = 0; b < h->batch && !e; b++)
         for (int l = 0; l < h->desc[b].num_levels && !e; l++)
-            e = capture_level(h, b, l, h->cap[b % nbr], h->partials + (size_t)(b % nbr) * MG_NORM_BLOCKS);
+            e = capture_level(h, b, l, h->cap[b % nbr], b % nbr);
     for (int i = 1; i < nbr && !e; i++) {
         e = cudaEventRecord(h->ev_join[i], h->cap[i]);
         if (!e)
@@ -704,7 +712,6 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                     ld.off[a] = (int)std::floor((d.lo[l][a] - d.lo[l - 1][a]) / hp + 0.5);
             }
             build_geometry(ld, dim);
-            plan_bottom(ld, dim);
             for (int L = 0; L < ld.nmg; L++) {
                 const size_t c = (size_t)cells(ld.g[L].E, dim);
                 slots.push_back({(void **)&ld.phi[L], align256(c * sizeof(double))});
@@ -714,6 +721,10 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                     slots.push_back({(void **)&ld.f32[L], align256(c * sizeof(float))});
                 }
             }
+            for (int L = 1; L < ld.nmg; L++) {
+                slots.push_back({(void **)&ld.tab64[L], align256(128 * sizeof(double))});
+                slots.push_back({(void **)&ld.tab32[L], align256(128 * sizeof(float))});
+            }
             slots.push_back({(void **)&ld.rho, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
             slots.push_back({(void **)&ld.guess, align256((size_t)cells(ld.n + 2, dim) * sizeof(double))});
             const size_t st = std::max((size_t)cells(ld.n + 4, dim) * 3, (size_t)cells(ld.n, dim) * (dim + 1));
@@ -722,7 +733,8 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     }
     h->stage_elems = stage;
     slots.push_back({(void **)&h->stage, align256(stage * sizeof(double))});
-    slots.push_back({(void **)&h->partials, align256((size_t)MG_BRANCHES * MG_NORM_BLOCKS * sizeof(double))});
+    slots.push_back({(void **)&h->partials, align256((size_t)MG_BRANCHES * 2 * MG_NORM_BLOCKS_MAX * sizeof(double))});
+    slots.push_back({(void **)&h->counters, align256((size_t)MG_BRANCHES * sizeof(unsigned))});
     slots.push_back({(void **)&h->ctl, align256((size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl))});
     slots.push_back({(void **)&h->scal, align256((size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double))});
     for (auto &sl : slots)
@@ -758,6 +770,24 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     e = mg_bottom_prepare();
     if (e == cudaSuccess)
         e = mg_launch_zero(h->arena, bytes, h->stream);
+    // boundary-diagonal tables of the coarse multigrid levels, then the plan
+    // of the one-block kernel (which copies the level descriptions)
+    for (int b = 0; b < batch && e == cudaSuccess; b++)
+        for (auto &ld : h->lev[b]) {
+            for (int L = 1; L < ld.nmg && e == cudaSuccess; L++) {
+                double t64[128];
+                float t32[128];
+                mg_fill_diag_table(ld.g[L], dim, t64);
+                for (int c = 0; c < 128; c++)
+                    t32[c] = (float)t64[c];
+                e = cudaMemcpy(ld.tab64[L], t64, sizeof t64, cudaMemcpyHostToDevice);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(ld.tab32[L], t32, sizeof t32, cudaMemcpyHostToDevice);
+                ld.g[L].tab64 = ld.tab64[L];
+                ld.g[L].tab32 = ld.tab32[L];
+            }
+            plan_bottom(ld, dim);
+        }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {

@@ -20,33 +20,44 @@ struct MgGeom {
     double cR;      // right ghost = cR * Phi_N when !tie
     double h2;      // squared physical cell size of this multigrid level
     double inv_h2;  // 1 / h2
+    // Optional device tables of the ghost-folded diagonal of boundary cells
+    // (L > 0), indexed by the per-axis boundary class c_x + 4 c_y + 16 c_z
+    // (class: bit 0 = first active cell, bit 1 = last): entries 0..63 hold
+    // the diagonal, 64..127 its negated reciprocal.  NULL: computed in place.
+    const double *tab64;
+    const float *tab32;
 };
 
-// Per-axis stencil coefficients of an active index i on level g, with the
-// ghost rule folded in (left ghost -Phi_1; right ghost cR Phi_N, or -Phi_{N-1}
-// when x_N = 1).
-template <typename T>
-__device__ __forceinline__ void mg_axis_coef(int i, const MgGeom &g, T &wm, T &wp, T &dg)
+// Diagonal contribution of one axis for boundary class c (Sec. 2.4 ghost
+// rule folded in): left ghost -Phi_1 adds -1; right ghost cR Phi_N adds cR,
+// or, when x_N = 1, -Phi_{N-1} cancels the left neighbour instead.
+__host__ __device__ inline double mg_axis_diag(int c, const MgGeom &g)
 {
-    wm = T(1);
-    wp = T(1);
-    dg = T(-2);
-    if (g.L == 0)
-        return;
-    if (i == 1) {
-        wm = T(0);
-        dg -= T(1);
-    }
-    if (i == g.N) {
-        wp = T(0);
+    double d = -2.0;
+    if (c & 1)
+        d -= 1.0;
+    if (c & 2) {
         if (g.tie) {
-            if (g.N >= 2)
-                wm = T(0);      // +Phi_{N-1} from the left, -Phi_{N-1} from the ghost
-            else
-                dg += T(1);     // -Phi_0 = +Phi_1
+            if (g.N < 2)
+                d += 1.0;   // -Phi_0 = +Phi_1
         } else {
-            dg += T(g.cR);
+            d += g.cR;
         }
+    }
+    return d;
+}
+
+// Fill tab[0..127] (diagonal, then -1/diagonal) for a level of dimension dim.
+inline void mg_fill_diag_table(const MgGeom &g, int dim, double *tab)
+{
+    for (int c = 0; c < 64; c++) {
+        const int cx = c & 3, cy = (c >> 2) & 3, cz = (c >> 4) & 3;
+        double d = mg_axis_diag(cx, g);
+        d += mg_axis_diag(cy, g);
+        if (dim == 3)
+            d += mg_axis_diag(cz, g);
+        tab[c] = d;
+        tab[64 + c] = 1.0 / (-d);
     }
 }
 
@@ -81,6 +92,13 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
 // *out after a fixed-order two-pass reduction through `partials`
 // (MG_NORM_BLOCKS doubles).
 #define MG_NORM_BLOCKS 304
+// Single-launch form: out2[0] = ||b||^2 if (which & 1), out2[1] = ||r||^2 if
+// (which & 2); the last block to finish reduces the per-block partials
+// (MG_NORM_BLOCKS_MAX doubles) in a fixed order; counter (one unsigned, zero
+// between launches) tracks finished blocks.
+#define MG_NORM_BLOCKS_MAX 1216
+cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const MgGeom &g, int which,
+                             double *partials, unsigned *counter, double *out2, cudaStream_t s);
 cudaError_t mg_launch_resid_norm2(int dim, const double *phi, const double *f, const MgGeom &g, bool zero_inside,
                                   double *partials, double *out, cudaStream_t s);
 

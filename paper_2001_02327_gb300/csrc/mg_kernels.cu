@@ -1,7 +1,14 @@
 // mg_kernels.cu -- CUDA kernels of the nested-grid multigrid Poisson solver
 // for sm_103a: red-black Gauss-Seidel smoothing, fused residual+restriction,
-// prolongation+correction, residual norms, the coarse-to-fine interface and
+// prolongation+correction, the one-block bottom of the V-cycle, residual
+// norms, mixed-precision defect correction, the coarse-to-fine interface and
 // the force stencil.  Arrays are C order, x fastest.
+//
+// The part runs FP64 at two FMA per clock per SM, so the FP64 kernels are
+// written to minimise double-precision operations per cell: no device
+// divisions (host tables of the boundary diagonals), neighbour folding by
+// selects rather than multiplies, separable interpolation.  Index arithmetic
+// is 32-bit.
 #include "mg_internal.h"
 
 namespace {
@@ -19,65 +26,112 @@ inline int grid_for(long work, int cap = 152 * 16)
     return (int)b;
 }
 
+inline long cube(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
+
 template <int DIM>
-__device__ __forceinline__ long lin(int i, int j, int k, int E)
+__device__ __forceinline__ int lin(int i, int j, int k, int E)
 {
-    return DIM == 3 ? ((long)k * E + j) * E + i : (long)j * E + i;
+    return DIM == 3 ? (k * E + j) * E + i : j * E + i;
 }
 
-// Sum of the (ghost-folded) neighbours and the diagonal coefficient of the
-// 5/7-point Laplacian (Sec. 2.3, item 1) at active cell (i,j,k), p = its index.
+template <typename T>
+__device__ __forceinline__ const T *tab_of(const MgGeom &g);
+template <>
+__device__ __forceinline__ const double *tab_of<double>(const MgGeom &g) { return g.tab64; }
+template <>
+__device__ __forceinline__ const float *tab_of<float>(const MgGeom &g) { return g.tab32; }
+
+// Ghost-folded neighbour sum of the 5/7-point Laplacian (Sec. 2.3 item 1) at
+// active cell (i,j,k) of index p, and the cell's boundary class (0 if it
+// touches no multigrid boundary, always 0 on the finest level where the outer
+// ring holds Dirichlet data).
 template <typename T, int DIM>
-__device__ __forceinline__ void stencil_terms(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, long p,
-                                              T &other, T &diag)
+__device__ __forceinline__ T neighbour_sum(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, int p,
+                                          int &cls)
 {
-    const long E = g.E;
-    if (g.L == 0) {
-        other = (phi[p - 1] + phi[p + 1]) + (phi[p - E] + phi[p + E]);
+    const int E = g.E, N = g.N;
+    const bool coarse = g.L > 0;
+    const bool inner = !coarse || (i > 1 && i < N && j > 1 && j < N && (DIM == 2 || (k > 1 && k < N)));
+    if (inner) {
+        cls = 0;
+        T s = (phi[p - 1] + phi[p + 1]) + (phi[p - E] + phi[p + E]);
         if (DIM == 3)
-            other += phi[p - E * E] + phi[p + E * E];
-        diag = T(-2 * DIM);
-        return;
+            s += phi[p - E * E] + phi[p + E * E];
+        return s;
     }
-    T wm, wp, dg;
-    mg_axis_coef<T>(i, g, wm, wp, dg);
-    other = wm * phi[p - 1] + wp * phi[p + 1];
-    diag = dg;
-    mg_axis_coef<T>(j, g, wm, wp, dg);
-    other += wm * phi[p - E] + wp * phi[p + E];
-    diag += dg;
-    if (DIM == 3) {
-        mg_axis_coef<T>(k, g, wm, wp, dg);
-        other += wm * phi[p - E * E] + wp * phi[p + E * E];
-        diag += dg;
-    }
+    // left neighbour dropped at index 1 (ghost = -self: goes to the diagonal)
+    // and at index N when x_N = 1 (ghost = -Phi_{N-1} cancels it); right
+    // neighbour dropped at index N (ghost cR Phi_N: diagonal)
+    const bool tieN = g.tie && N >= 2;
+    cls = 0;
+    auto axis = [&](int c, int st, int shift) -> T {
+        const bool lo = c == 1, hi = c == N;
+        cls |= ((lo ? 1 : 0) | (hi ? 2 : 0)) << shift;
+        const T l = (!lo && !(hi && tieN)) ? phi[p - st] : T(0);
+        const T r = !hi ? phi[p + st] : T(0);
+        return l + r;
+    };
+    T s = axis(i, 1, 0) + axis(j, E, 2);
+    if (DIM == 3)
+        s += axis(k, E * E, 4);
+    return s;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T diag_of(const MgGeom &g, int cls)
+{
+    if (cls == 0)
+        return T(-2 * DIM);
+    const T *tab = tab_of<T>(g);
+    if (tab)
+        return tab[cls];
+    double d = mg_axis_diag(cls & 3, g) + mg_axis_diag((cls >> 2) & 3, g);
+    if (DIM == 3)
+        d += mg_axis_diag((cls >> 4) & 3, g);
+    return T(d);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T neg_inv_diag(const MgGeom &g, int cls)
+{
+    if (cls == 0)
+        return T(1.0 / (2 * DIM));
+    const T *tab = tab_of<T>(g);
+    if (tab)
+        return tab[64 + cls];
+    return T(1) / (-diag_of<T, DIM>(g, cls));
 }
 
 // One colour of a red-black Gauss-Seidel sweep (Sec. 2.3 steps 2, 6, 11)
 // over work items t0, t0+stride, ...  Red cells have (i+j[+k]) even and are
-// updated first.
+// updated first.  Each update solves the cell's own equation.
 template <typename T, int DIM>
 __device__ __forceinline__ void op_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g,
-                                                 int colour, long t0, long stride)
+                                                 int colour, int t0, int stride)
 {
     const int N = g.N;
     const int half = (N + 1) >> 1;
-    const long total = (long)half * N * (DIM == 3 ? N : 1);
+    const int total = half * N * (DIM == 3 ? N : 1);
     const T h2 = T(g.h2);
-    for (long t = t0; t < total; t += stride) {
-        const int i2 = (int)(t % half);
-        const long r = t / half;
-        const int j = (int)(r % N) + 1;
-        const int k = DIM == 3 ? (int)(r / N) + 1 : 0;
+    for (int t = t0; t < total; t += stride) {
+        const int r = t / half;
+        const int i2 = t - r * half;
+        int j, k;
+        if (DIM == 3) {
+            k = r / N;
+            j = r - k * N + 1;
+            k += 1;
+        } else {
+            j = r + 1;
+            k = 0;
+        }
         const int i = ((((1 + j + k) & 1) == colour) ? 1 : 2) + 2 * i2;
         if (i > N)
             continue;
-        const long p = lin<DIM>(i, j, k, g.E);
-        T other, diag;
-        stencil_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
-        // interior cells share the diagonal 2d: multiply by its reciprocal
-        const T inv = diag == T(-2 * DIM) ? T(1.0 / (2 * DIM)) : T(1) / (-diag);
-        phi[p] = (other - h2 * f[p]) * inv;
+        const int p = lin<DIM>(i, j, k, g.E);
+        int cls;
+        const T other = neighbour_sum<T, DIM>(phi, g, i, j, k, p, cls);
+        phi[p] = (other - h2 * f[p]) * neg_inv_diag<T, DIM>(g, cls);
     }
 }
 
@@ -85,27 +139,36 @@ template <typename T, int DIM>
 __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g, int i,
                                          int j, int k)
 {
-    const long p = lin<DIM>(i, j, k, g.E);
-    T other, diag;
-    stencil_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
-    return f[p] - (other + diag * phi[p]) * T(g.inv_h2);
+    const int p = lin<DIM>(i, j, k, g.E);
+    int cls;
+    const T other = neighbour_sum<T, DIM>(phi, g, i, j, k, p, cls);
+    return f[p] - (other + diag_of<T, DIM>(g, cls) * phi[p]) * T(g.inv_h2);
 }
 
 // Residual (Sec. 2.3 step 4) restricted to the next coarser level by the
 // 2^d-child average (step 5; fine cells beyond N contribute zero); the
-// coarse correction starts from zero.
+// coarse correction starts from zero.  Generic form (one coarse cell per work
+// item) for the one-block kernel.
 template <typename T, int DIM>
 __device__ __forceinline__ void op_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
                                                   const MgGeom &gf, T *__restrict__ phi_c, T *__restrict__ f_c,
-                                                  const MgGeom &gc, long t0, long stride)
+                                                  const MgGeom &gc, int t0, int stride)
 {
     const int Nc = gc.N, Nf = gf.N;
-    const long total = (long)Nc * Nc * (DIM == 3 ? Nc : 1);
+    const int total = Nc * Nc * (DIM == 3 ? Nc : 1);
     const T w = DIM == 3 ? T(0.125) : T(0.25);
-    for (long t = t0; t < total; t += stride) {
-        const int I = (int)(t % Nc) + 1;
-        const int J = (int)((t / Nc) % Nc) + 1;
-        const int K = DIM == 3 ? (int)(t / ((long)Nc * Nc)) + 1 : 0;
+    for (int t = t0; t < total; t += stride) {
+        const int r = t / Nc;
+        const int I = t - r * Nc + 1;
+        int J, K;
+        if (DIM == 3) {
+            K = r / Nc;
+            J = r - K * Nc + 1;
+            K += 1;
+        } else {
+            J = r + 1;
+            K = 0;
+        }
         T s = T(0);
         for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++) {
             const int k = DIM == 3 ? 2 * K - 1 + dk : 0;
@@ -123,7 +186,7 @@ __device__ __forceinline__ void op_resid_restrict(const T *__restrict__ phi_f, c
                 }
             }
         }
-        const long pc = lin<DIM>(I, J, K, gc.E);
+        const int pc = lin<DIM>(I, J, K, gc.E);
         f_c[pc] = w * s;
         phi_c[pc] = T(0);
     }
@@ -153,19 +216,27 @@ __device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, dou
     }
 }
 
-// Prolongation and correction (Sec. 2.3 step 10; weights 3/4, 1/4 per axis,
-// i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse ghosts by the rule.
+// Prolongation and correction (Sec. 2.3 step 10; bi/trilinear 3/4-1/4
+// weights per axis, i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse
+// ghosts by the rule, evaluated one axis at a time.
 template <typename T, int DIM>
 __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const MgGeom &gc, T *__restrict__ phi_f,
-                                           const MgGeom &gf, long t0, long stride)
+                                           const MgGeom &gf, int t0, int stride)
 {
-    const int Nf = gf.N;
-    const long total = (long)Nf * Nf * (DIM == 3 ? Nf : 1);
-    for (long t = t0; t < total; t += stride) {
+    const int Nf = gf.N, Ec = gc.E;
+    const int total = Nf * Nf * (DIM == 3 ? Nf : 1);
+    for (int t = t0; t < total; t += stride) {
         int f[3];
-        f[0] = (int)(t % Nf) + 1;
-        f[1] = (int)((t / Nf) % Nf) + 1;
-        f[2] = DIM == 3 ? (int)(t / ((long)Nf * Nf)) + 1 : 0;
+        const int r = t / Nf;
+        f[0] = t - r * Nf + 1;
+        if (DIM == 3) {
+            const int k = r / Nf;
+            f[1] = r - k * Nf + 1;
+            f[2] = k + 1;
+        } else {
+            f[1] = r + 1;
+            f[2] = 0;
+        }
         int idx[3][2];
         T w[3][2];
         for (int a = 0; a < DIM; a++) {
@@ -177,23 +248,34 @@ __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const Mg
             w[a][0] = T(0.75 * c0);
             w[a][1] = T(0.25 * c1);
         }
-        T v = T(0);
+        T v;
         if (DIM == 3) {
-            for (int c = 0; c < 2; c++)
-                for (int b = 0; b < 2; b++)
-                    for (int a = 0; a < 2; a++)
-                        v += w[0][a] * w[1][b] * w[2][c] * phi_c[lin<3>(idx[0][a], idx[1][b], idx[2][c], gc.E)];
+            T zsum = T(0);
+            for (int c = 0; c < 2; c++) {
+                T ysum = T(0);
+                for (int b = 0; b < 2; b++) {
+                    const int row = (idx[2][c] * Ec + idx[1][b]) * Ec;
+                    const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
+                    ysum += w[1][b] * xv;
+                }
+                zsum += w[2][c] * ysum;
+            }
+            v = zsum;
         } else {
-            for (int b = 0; b < 2; b++)
-                for (int a = 0; a < 2; a++)
-                    v += w[0][a] * w[1][b] * phi_c[lin<2>(idx[0][a], idx[1][b], 0, gc.E)];
+            T ysum = T(0);
+            for (int b = 0; b < 2; b++) {
+                const int row = idx[1][b] * Ec;
+                const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
+                ysum += w[1][b] * xv;
+            }
+            v = ysum;
         }
         phi_f[lin<DIM>(f[0], f[1], f[2], gf.E)] += v;
     }
 }
 
-__device__ __forceinline__ long gtid() { return blockIdx.x * (long)blockDim.x + threadIdx.x; }
-__device__ __forceinline__ long gstride() { return (long)gridDim.x * blockDim.x; }
+__device__ __forceinline__ int gtid() { return blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int gstride() { return gridDim.x * blockDim.x; }
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
@@ -202,12 +284,42 @@ __global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi,
     op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
 }
 
+// Residual and restriction with one fine cell per thread: a block computes the
+// residuals of a fine tile (16x8x2 in 3D, 32x8 in 2D) into shared memory and
+// its first threads average the children of the coarse cells of the tile
+// (8x4x1 in 3D, 16x4 in 2D).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
                                                              MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
                                                              MgGeom gc)
 {
-    op_resid_restrict<T, DIM>(phi_f, f_f, gf, phi_c, f_c, gc, gtid(), gstride());
+    __shared__ T r[kThreads];
+    const int Nf = gf.N, Nc = gc.N;
+    constexpr int FX = DIM == 3 ? 16 : 32, FY = 8;
+    const int tx = threadIdx.x % FX, ty = (threadIdx.x / FX) % FY, tz = DIM == 3 ? threadIdx.x / (FX * FY) : 0;
+    const int i = 1 + FX * blockIdx.x + tx, j = 1 + FY * blockIdx.y + ty;
+    const int k = DIM == 3 ? 1 + 2 * blockIdx.z + tz : 0;
+    T v = T(0);
+    if (i <= Nf && j <= Nf && (DIM == 2 || k <= Nf))
+        v = residual_at<T, DIM>(phi_f, f_f, gf, i, j, k);
+    r[threadIdx.x] = v;
+    __syncthreads();
+    constexpr int CX = FX / 2, CY = FY / 2;
+    if (threadIdx.x < CX * CY) {
+        const int cx = threadIdx.x % CX, cy = threadIdx.x / CX;
+        const int I = 1 + CX * blockIdx.x + cx, J = 1 + CY * blockIdx.y + cy;
+        const int K = DIM == 3 ? 1 + blockIdx.z : 0;
+        if (I <= Nc && J <= Nc && (DIM == 2 || K <= Nc)) {
+            T s = T(0);
+            for (int dz = 0; dz < (DIM == 3 ? 2 : 1); dz++)
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++)
+                        s += r[(dz * FY + 2 * cy + dy) * FX + 2 * cx + dx];
+            const int pc = lin<DIM>(I, J, K, gc.E);
+            f_c[pc] = (DIM == 3 ? T(0.125) : T(0.25)) * s;
+            phi_c[pc] = T(0);
+        }
+    }
 }
 
 template <typename T, int DIM>
@@ -231,48 +343,48 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *phi[MG_BOTTOM_MAX];
-    T *f[MG_BOTTOM_MAX];
-    long off = 0;
+    int offs[MG_BOTTOM_MAX + 1];
+    offs[0] = 0;
     for (int q = 0; q < bt.nlev; q++) {
-        const long c = DIM == 3 ? (long)bt.g[q].E * bt.g[q].E * bt.g[q].E : (long)bt.g[q].E * bt.g[q].E;
-        phi[q] = sm + off;
-        f[q] = sm + off + c;
-        off += 2 * c;
+        const int c = DIM == 3 ? bt.g[q].E * bt.g[q].E * bt.g[q].E : bt.g[q].E * bt.g[q].E;
+        offs[q + 1] = offs[q] + 2 * c;
     }
-    const long tid = threadIdx.x, nth = blockDim.x;
-    const long c0 = DIM == 3 ? (long)bt.g[0].E * bt.g[0].E * bt.g[0].E : (long)bt.g[0].E * bt.g[0].E;
-    for (long t = tid; t < off; t += nth)
+    auto PHI = [&](int q) { return sm + offs[q]; };
+    auto F = [&](int q) { return sm + offs[q] + (offs[q + 1] - offs[q]) / 2; };
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int total = offs[bt.nlev];
+    const int c0 = (offs[1] - offs[0]) / 2;
+    for (int t = tid; t < total; t += nth)
         sm[t] = T(0);
     __syncthreads();
-    for (long t = tid; t < c0; t += nth) {
-        phi[0][t] = phi_g[t];
-        f[0][t] = f_g[t];
+    for (int t = tid; t < c0; t += nth) {
+        PHI(0)[t] = phi_g[t];
+        F(0)[t] = f_g[t];
     }
     __syncthreads();
     auto smooth = [&](int q, int sweeps) {
         for (int sw = 0; sw < sweeps; sw++)
             for (int c = 0; c < 2; c++) {
-                op_smooth_colour<T, DIM>(phi[q], f[q], bt.g[q], c, tid, nth);
+                op_smooth_colour<T, DIM>(PHI(q), F(q), bt.g[q], c, tid, nth);
                 __syncthreads();
             }
     };
     smooth(0, bt.g[0].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
     int q = 0;
     while (bt.g[q].N > 1 && q + 1 < bt.nlev) {
-        op_resid_restrict<T, DIM>(phi[q], f[q], bt.g[q], phi[q + 1], f[q + 1], bt.g[q + 1], tid, nth);
+        op_resid_restrict<T, DIM>(PHI(q), F(q), bt.g[q], PHI(q + 1), F(q + 1), bt.g[q + 1], tid, nth);
         __syncthreads();
         smooth(q + 1, bt.g[q + 1].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
         q++;
     }
     while (q > 0) {
-        op_prolong<T, DIM>(phi[q], bt.g[q], phi[q - 1], bt.g[q - 1], tid, nth);
+        op_prolong<T, DIM>(PHI(q), bt.g[q], PHI(q - 1), bt.g[q - 1], tid, nth);
         __syncthreads();
         smooth(q - 1, nu_post);
         q--;
     }
-    for (long t = tid; t < c0; t += nth)
-        phi_g[t] = phi[0][t];
+    for (int t = tid; t < c0; t += nth)
+        phi_g[t] = PHI(0)[t];
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -282,11 +394,12 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-__device__ __forceinline__ double block_sum(double v)
+// Fixed-order block sum; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sm)
 {
-    __shared__ double sm[kThreads / 32];
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
     if (lane == 0)
         sm[w] = v;
     __syncthreads();
@@ -296,40 +409,96 @@ __device__ __forceinline__ double block_sum(double v)
     return v;
 }
 
-// Partial sums of r^2 (r = f - lap(Phi)) over the active cells of a finest
-// multigrid level; one partial per block, fixed assignment of cells.
+// r^2 and b^2 at active cell t of a finest level: b is the residual of the
+// zero potential inside (only the outer-ring neighbours count).
+template <int DIM>
+__device__ __forceinline__ void norm_terms(const double *__restrict__ phi, const double *__restrict__ f,
+                                           const MgGeom &g, int t, int which, double &b2, double &r2)
+{
+    const int N = g.N, E = g.E;
+    const int r = t / N;
+    const int i = t - r * N + 1;
+    int j, k;
+    if (DIM == 3) {
+        k = r / N;
+        j = r - k * N + 1;
+        k += 1;
+    } else {
+        j = r + 1;
+        k = 0;
+    }
+    const int p = lin<DIM>(i, j, k, E);
+    if (which & 1) {
+        double o = 0.0;
+        if (i == 1) o += phi[p - 1];
+        if (i == N) o += phi[p + 1];
+        if (j == 1) o += phi[p - E];
+        if (j == N) o += phi[p + E];
+        if (DIM == 3) {
+            if (k == 1) o += phi[p - E * E];
+            if (k == N) o += phi[p + E * E];
+        }
+        const double v = f[p] - o * g.inv_h2;
+        b2 += v * v;
+    }
+    if (which & 2) {
+        const double v = residual_at<double, DIM>(phi, f, g, i, j, k);
+        r2 += v * v;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_norms2(const double *__restrict__ phi, const double *__restrict__ f,
+                                                     MgGeom g, int which, double *__restrict__ partials,
+                                                     unsigned *__restrict__ counter, double *__restrict__ out2)
+{
+    __shared__ double sm[kThreads / 32];
+    __shared__ bool last;
+    const int N = g.N;
+    const int total = N * N * (DIM == 3 ? N : 1);
+    double b2 = 0.0, r2 = 0.0;
+    for (int t = gtid(); t < total; t += gstride())
+        norm_terms<DIM>(phi, f, g, t, which, b2, r2);
+    b2 = block_sum(b2, sm);
+    r2 = block_sum(r2, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = b2;
+        partials[2 * blockIdx.x + 1] = r2;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    double sb = 0.0, sr = 0.0;
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
+        sb += partials[2 * t];
+        sr += partials[2 * t + 1];
+    }
+    sb = block_sum(sb, sm);
+    sr = block_sum(sr, sm);
+    if (threadIdx.x == 0) {
+        if (which & 1)
+            out2[0] = sb;
+        if (which & 2)
+            out2[1] = sr;
+        *counter = 0u;
+    }
+}
+
+// Two-launch form kept for the allocation-free entry point.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_resid_norm2(const double *__restrict__ phi, const double *__restrict__ f,
                                                           MgGeom g, int zero_inside, double *__restrict__ partials)
 {
+    __shared__ double sm[kThreads / 32];
     const int N = g.N;
-    const long E = g.E;
-    const long total = (long)N * N * (DIM == 3 ? N : 1);
-    double acc = 0.0;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % N) + 1;
-        const int j = (int)((t / N) % N) + 1;
-        const int k = DIM == 3 ? (int)(t / ((long)N * N)) + 1 : 0;
-        const long p = lin<DIM>(i, j, k, g.E);
-        double r;
-        if (zero_inside) {
-            // neighbours inside the solved region count as zero
-            double o = 0.0;
-            if (i == 1) o += phi[p - 1];
-            if (i == N) o += phi[p + 1];
-            if (j == 1) o += phi[p - E];
-            if (j == N) o += phi[p + E];
-            if (DIM == 3) {
-                if (k == 1) o += phi[p - E * E];
-                if (k == N) o += phi[p + E * E];
-            }
-            r = f[p] - o * g.inv_h2;
-        } else {
-            r = residual_at<double, DIM>(phi, f, g, i, j, k);
-        }
-        acc += r * r;
-    }
-    acc = block_sum(acc);
+    const int total = N * N * (DIM == 3 ? N : 1);
+    double b2 = 0.0, r2 = 0.0;
+    for (int t = gtid(); t < total; t += gstride())
+        norm_terms<DIM>(phi, f, g, t, zero_inside ? 1 : 2, b2, r2);
+    const double acc = block_sum(zero_inside ? b2 : r2, sm);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = acc;
 }
@@ -337,10 +506,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_norm2(const double *__restri
 __global__ void __launch_bounds__(kThreads) k_sum_partials(const double *__restrict__ partials, int n,
                                                            double *__restrict__ out)
 {
+    __shared__ double sm[kThreads / 32];
     double acc = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x)
         acc += partials[t];
-    acc = block_sum(acc);
+    acc = block_sum(acc, sm);
     if (threadIdx.x == 0)
         *out = acc;
 }
@@ -352,12 +522,20 @@ __global__ void __launch_bounds__(kThreads) k_defect(const double *__restrict__ 
                                                      MgGeom g, float *__restrict__ r32, float *__restrict__ e32)
 {
     const int N = g.N;
-    const long total = (long)N * N * (DIM == 3 ? N : 1);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % N) + 1;
-        const int j = (int)((t / N) % N) + 1;
-        const int k = DIM == 3 ? (int)(t / ((long)N * N)) + 1 : 0;
-        const long p = lin<DIM>(i, j, k, g.E);
+    const int total = N * N * (DIM == 3 ? N : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / N;
+        const int i = t - r * N + 1;
+        int j, k;
+        if (DIM == 3) {
+            k = r / N;
+            j = r - k * N + 1;
+            k += 1;
+        } else {
+            j = r + 1;
+            k = 0;
+        }
+        const int p = lin<DIM>(i, j, k, g.E);
         r32[p] = (float)residual_at<double, DIM>(phi, f, g, i, j, k);
         e32[p] = 0.0f;
     }
@@ -368,12 +546,20 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(double *__restrict__ ph
                                                          MgGeom g)
 {
     const int N = g.N;
-    const long total = (long)N * N * (DIM == 3 ? N : 1);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % N) + 1;
-        const int j = (int)((t / N) % N) + 1;
-        const int k = DIM == 3 ? (int)(t / ((long)N * N)) + 1 : 0;
-        const long p = lin<DIM>(i, j, k, g.E);
+    const int total = N * N * (DIM == 3 ? N : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / N;
+        const int i = t - r * N + 1;
+        int j, k;
+        if (DIM == 3) {
+            k = r / N;
+            j = r - k * N + 1;
+            k += 1;
+        } else {
+            j = r + 1;
+            k = 0;
+        }
+        const int p = lin<DIM>(i, j, k, g.E);
         phi[p] += (double)e32[p];
     }
 }
@@ -386,9 +572,12 @@ __global__ void __launch_bounds__(kThreads) k_set_density(int n, const double *_
                                                           double fourpiG)
 {
     const int E = n + 4;
-    const long total = (long)E * E * (DIM == 3 ? E : 1);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % E), j = (int)((t / E) % E), k = DIM == 3 ? (int)(t / ((long)E * E)) : 2;
+    const int total = E * E * (DIM == 3 ? E : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / E;
+        const int i = t - r * E;
+        const int j = DIM == 3 ? r % E : r;
+        const int k = DIM == 3 ? r / E : 2;
         const bool outer = i == 0 || i == n + 3 || j == 0 || j == n + 3 || (DIM == 3 && (k == 0 || k == n + 3));
         const bool omega = i >= 2 && i <= n + 1 && j >= 2 && j <= n + 1 && (DIM == 2 || (k >= 2 && k <= n + 1));
         if (omega) {
@@ -423,23 +612,25 @@ __device__ __forceinline__ void iface_axis(int s, int off, int &p0, double &t)
     }
 }
 
+// Bilinear / trilinear interpolation (Appendix A) from the 2^d enclosing
+// parent centres, one axis at a time.
 template <int DIM>
 __device__ __forceinline__ double interp(const double *__restrict__ src, int Ep, const int *p0, const double *t)
 {
-    double v = 0.0;
-    for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++)
-        for (int dj = 0; dj < 2; dj++)
-            for (int di = 0; di < 2; di++) {
-                double w = (di ? t[0] : 1.0 - t[0]) * (dj ? t[1] : 1.0 - t[1]);
-                if (DIM == 3)
-                    w *= dk ? t[2] : 1.0 - t[2];
-                v += w * src[lin<DIM>(p0[0] + di, p0[1] + dj, DIM == 3 ? p0[2] + dk : 0, Ep)];
-            }
-    return v;
+    double zs = 0.0;
+    for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++) {
+        double ys = 0.0;
+        for (int dj = 0; dj < 2; dj++) {
+            const int row = DIM == 3 ? ((p0[2] + dk) * Ep + p0[1] + dj) * Ep : (p0[1] + dj) * Ep;
+            const double xv = (1.0 - t[0]) * src[row + p0[0]] + t[0] * src[row + p0[0] + 1];
+            ys += (dj ? t[1] : 1.0 - t[1]) * xv;
+        }
+        zs += DIM == 3 ? (dk ? t[2] : 1.0 - t[2]) * ys : ys;
+    }
+    return zs;
 }
 
-// One-way interface (Sec. 2.1; Sec. 2.4): bilinear/trilinear interpolation
-// from the 2^d enclosing parent centres (Appendix A weights).
+// One-way interface (Sec. 2.1; Sec. 2.4).
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__restrict__ phi_p,
                                                         const double *__restrict__ rho_p, int nc, int ox, int oy, int oz,
@@ -448,12 +639,13 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
                                                         const double *__restrict__ guess_src)
 {
     const int E = nc + 4, Ep = np + 4;
-    const long total = (long)E * E * (DIM == 3 ? E : 1);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int total = E * E * (DIM == 3 ? E : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
         int s[3];
-        s[0] = (int)(t % E);
-        s[1] = (int)((t / E) % E);
-        s[2] = DIM == 3 ? (int)(t / ((long)E * E)) : 2;
+        const int r = t / E;
+        s[0] = t - r * E;
+        s[1] = DIM == 3 ? r % E : r;
+        s[2] = DIM == 3 ? r / E : 2;
         bool outer = false, inner = false;
         for (int a = 0; a < DIM; a++) {
             if (s[a] == 0 || s[a] == nc + 3)
@@ -471,9 +663,9 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
             continue;
         }
         if (inner) {
-            const double r = interp<DIM>(rho_p, Ep, p0, w);
-            rho_c[t] = r;
-            f_c[t] = fourpiG * r;
+            const double rv = interp<DIM>(rho_p, Ep, p0, w);
+            rho_c[t] = rv;
+            f_c[t] = fourpiG * rv;
         }
         if (guess == 0)
             phi_c[t] = interp<DIM>(phi_p, Ep, p0, w);
@@ -489,9 +681,12 @@ __global__ void __launch_bounds__(kThreads) k_copy_guess(int n, const double *__
                                                          double *__restrict__ phi_blk)
 {
     const int M = n + 2;
-    const long total = (long)M * M * (DIM == 3 ? M : 1);
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % M), j = (int)((t / M) % M), k = DIM == 3 ? (int)(t / ((long)M * M)) : 0;
+    const int total = M * M * (DIM == 3 ? M : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / M;
+        const int i = t - r * M;
+        const int j = DIM == 3 ? r % M : r;
+        const int k = DIM == 3 ? r / M : 0;
         phi_blk[lin<DIM>(i + 1, j + 1, DIM == 3 ? k + 1 : 0, n + 4)] = src[t];
     }
 }
@@ -502,14 +697,16 @@ __global__ void __launch_bounds__(kThreads) k_forces(int n, double h, const doub
                                                      double *__restrict__ F, double *__restrict__ phi_out, int stencil)
 {
     const int E = n + 4;
-    const long total = (long)n * n * (DIM == 3 ? n : 1);
+    const int total = n * n * (DIM == 3 ? n : 1);
     const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * h) : 1.0 / (2.0 * h);
     const double c2 = stencil == 0 ? (1.0 / 3.0) / (4.0 * h) : 0.0;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % n) + 2, j = (int)((t / n) % n) + 2;
-        const int k = DIM == 3 ? (int)(t / ((long)n * n)) + 2 : 0;
-        const long p = lin<DIM>(i, j, k, E);
-        const long st[3] = {1, E, (long)E * E};
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / n;
+        const int i = t - r * n + 2;
+        const int j = DIM == 3 ? r % n + 2 : r + 2;
+        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int p = lin<DIM>(i, j, k, E);
+        const int st[3] = {1, E, E * E};
         for (int a = 0; a < DIM; a++) {
             const double d1 = phi[p + st[a]] - phi[p - st[a]];
             const double d2 = phi[p + 2 * st[a]] - phi[p - 2 * st[a]];
@@ -558,8 +755,6 @@ __global__ void k_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double 
     *ctl = c;
     cudaGraphSetConditional(hc, c.go);
 }
-
-inline long cube(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
 
 }  // namespace
 
@@ -627,8 +822,9 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
                                      void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s)
 {
-    const int grid = grid_for(cube(gc.N, dim));
+    const int Nc = gc.N;
     if (dim == 3) {
+        const dim3 grid((Nc + 7) / 8, (Nc + 3) / 4, Nc);
         if (fp32)
             k_resid_restrict<float, 3><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
@@ -636,6 +832,7 @@ cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, cons
             k_resid_restrict<double, 3><<<grid, kThreads, 0, s>>>((const double *)phi_f, (const double *)f_f, gf,
                                                                   (double *)phi_c, (double *)f_c, gc);
     } else {
+        const dim3 grid((Nc + 15) / 16, (Nc + 3) / 4, 1);
         if (fp32)
             k_resid_restrict<float, 2><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
@@ -661,6 +858,17 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
         else
             k_prolong<double, 2><<<grid, kThreads, 0, s>>>((const double *)phi_c, gc, (double *)phi_f, gf);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const MgGeom &g, int which,
+                             double *partials, unsigned *counter, double *out2, cudaStream_t s)
+{
+    const int grid = grid_for(cube(g.N, dim), MG_NORM_BLOCKS_MAX);
+    if (dim == 3)
+        k_norms2<3><<<grid, kThreads, 0, s>>>(phi, f, g, which, partials, counter, out2);
+    else
+        k_norms2<2><<<grid, kThreads, 0, s>>>(phi, f, g, which, partials, counter, out2);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,8 @@ int geometry(int M, double h, MgGeom *g)
     }
     const int nmg = L + 1;
     for (int q = 0; q < nmg; q++) {
+        g[q].tab64 = nullptr;   // boundary diagonals computed in place
+        g[q].tab32 = nullptr;
         g[q].N = N[q];
         g[q].E = N[q] + 2;
         g[q].L = q;
