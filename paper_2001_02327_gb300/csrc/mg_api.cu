@@ -111,6 +111,9 @@ void build_geometry(LevelData &ld, int dim)
         const double hL = ld.h * (double)(1L << L);
         g.h2 = hL * hL;
         g.inv_h2 = 1.0 / g.h2;
+        g.cRf = (float)g.cR;
+        g.h2f = (float)g.h2;
+        g.inv_h2f = (float)g.inv_h2;
     }
 }
 

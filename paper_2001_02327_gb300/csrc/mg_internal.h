@@ -20,6 +20,9 @@ struct MgGeom {
     double cR;      // right ghost = cR * Phi_N when !tie
     double h2;      // squared physical cell size of this multigrid level
     double inv_h2;  // 1 / h2
+    // the same constants rounded to FP32 for the FP32 kernels (a conversion
+    // from double runs on the FP64 pipe, which this part has little of)
+    float cRf, h2f, inv_h2f;
     // Optional device tables of the ghost-folded diagonal of boundary cells
     // (L > 0), indexed by the per-axis boundary class c_x + 4 c_y + 16 c_z
     // (class: bit 0 = first active cell, bit 1 = last): entries 0..63 hold

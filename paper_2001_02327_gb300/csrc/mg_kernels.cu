@@ -34,6 +34,26 @@ __device__ __forceinline__ int lin(int i, int j, int k, int E)
     return DIM == 3 ? (k * E + j) * E + i : j * E + i;
 }
 
+// level constants in the working precision
+template <typename T>
+__device__ __forceinline__ T geo_h2(const MgGeom &g);
+template <>
+__device__ __forceinline__ double geo_h2<double>(const MgGeom &g) { return g.h2; }
+template <>
+__device__ __forceinline__ float geo_h2<float>(const MgGeom &g) { return g.h2f; }
+template <typename T>
+__device__ __forceinline__ T geo_inv_h2(const MgGeom &g);
+template <>
+__device__ __forceinline__ double geo_inv_h2<double>(const MgGeom &g) { return g.inv_h2; }
+template <>
+__device__ __forceinline__ float geo_inv_h2<float>(const MgGeom &g) { return g.inv_h2f; }
+template <typename T>
+__device__ __forceinline__ T geo_cR(const MgGeom &g);
+template <>
+__device__ __forceinline__ double geo_cR<double>(const MgGeom &g) { return g.cR; }
+template <>
+__device__ __forceinline__ float geo_cR<float>(const MgGeom &g) { return g.cRf; }
+
 template <typename T>
 __device__ __forceinline__ const T *tab_of(const MgGeom &g);
 template <>
@@ -112,7 +132,7 @@ __device__ __forceinline__ void op_smooth_colour(T *__restrict__ phi, const T *_
     const int N = g.N;
     const int half = (N + 1) >> 1;
     const int total = half * N * (DIM == 3 ? N : 1);
-    const T h2 = T(g.h2);
+    const T h2 = geo_h2<T>(g);
     for (int t = t0; t < total; t += stride) {
         const int r = t / half;
         const int i2 = t - r * half;
@@ -142,7 +162,7 @@ __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__r
     const int p = lin<DIM>(i, j, k, g.E);
     int cls;
     const T other = neighbour_sum<T, DIM>(phi, g, i, j, k, p, cls);
-    return f[p] - (other + diag_of<T, DIM>(g, cls) * phi[p]) * T(g.inv_h2);
+    return f[p] - (other + diag_of<T, DIM>(g, cls) * phi[p]) * geo_inv_h2<T>(g);
 }
 
 // Residual (Sec. 2.3 step 4) restricted to the next coarser level by the
@@ -194,25 +214,26 @@ __device__ __forceinline__ void op_resid_restrict(const T *__restrict__ phi_f, c
 
 // Coarse index q along one axis of level gc (ghosts included) written as
 // coefficient * active value (Sec. 2.4 ghost rule).
-__device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, double &c)
+template <typename T>
+__device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, T &c)
 {
     if (q >= 1 && q <= gc.N) {
         idx = q;
-        c = 1.0;
+        c = T(1);
     } else if (q == 0) {
         idx = 1;
-        c = -1.0;
+        c = T(-1);
     } else if (gc.tie) {
         if (gc.N >= 2) {
             idx = gc.N - 1;
-            c = -1.0;
+            c = T(-1);
         } else {
             idx = 1;
-            c = 1.0;
+            c = T(1);
         }
     } else {
         idx = gc.N;
-        c = gc.cR;
+        c = geo_cR<T>(gc);
     }
 }
 
@@ -242,11 +263,11 @@ __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const Mg
         for (int a = 0; a < DIM; a++) {
             const int near = (f[a] + 1) >> 1;
             const int far = (f[a] & 1) ? near - 1 : near + 1;
-            double c0, c1;
-            ghost_map(near, gc, idx[a][0], c0);
-            ghost_map(far, gc, idx[a][1], c1);
-            w[a][0] = T(0.75 * c0);
-            w[a][1] = T(0.25 * c1);
+            T c0, c1;
+            ghost_map<T>(near, gc, idx[a][0], c0);
+            ghost_map<T>(far, gc, idx[a][1], c1);
+            w[a][0] = T(0.75) * c0;
+            w[a][1] = T(0.25) * c1;
         }
         T v;
         if (DIM == 3) {

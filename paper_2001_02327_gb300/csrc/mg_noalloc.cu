@@ -97,6 +97,9 @@ int geometry(int M, double h, MgGeom *g)
         const double hq = h * (double)(1L << q);
         g[q].h2 = hq * hq;
         g[q].inv_h2 = 1.0 / g[q].h2;
+        g[q].cRf = (float)g[q].cR;
+        g[q].h2f = (float)g[q].h2;
+        g[q].inv_h2f = (float)g[q].inv_h2;
     }
     return nmg;
 }
