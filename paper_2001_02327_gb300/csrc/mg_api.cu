@@ -27,6 +27,8 @@ struct LevelData {
     double *phi[MG_MAX_MG] = {};   // phi[0]: the (n+4)^d level block
     double *f[MG_MAX_MG] = {};     // f[0]:   4 pi G rho on the same block
     float *phi32[MG_MAX_MG] = {};  // mixed precision correction, all multigrid levels
+    float *phi32b[MG_MAX_MG] = {}; // second FP32 buffer of the temporally blocked levels
+    int tile[MG_MAX_MG] = {};      // FP32 temporal-blocking tile per level (0: one kernel per phase)
     float *f32[MG_MAX_MG] = {};
     double *rho = nullptr;         // (n+4)^d density (Omega and inner ring)
     double *guess = nullptr;       // (n+2)^d optional initial potential
@@ -48,6 +50,23 @@ int bottom_limit(bool fp32)
     if (v && *v)
         return std::atoi(v);
     return 8;
+}
+
+// FP32 temporal-blocking tile of each level above the bottom kernel: 16 for
+// levels of 48 cells or more, 8 below (MG_TB_TILE overrides; 0 = one kernel
+// per phase).  Tiles must be even and fit the shared-memory limit.
+void plan_tiles(LevelData &ld, int dim, int nu_pre, int nu_post)
+{
+    const char *v = std::getenv("MG_TB_TILE");
+    const int forced = (v && *v) ? std::atoi(v) : -1;
+    for (int L = 0; L < ld.nmg; L++) {
+        int t = forced >= 0 ? forced : (ld.g[L].N >= 48 ? 16 : 8);
+        t &= ~1;
+        while (t > 0 && (mg_tb_smem(dim, true, t, 2 * nu_pre + 1) > MG_TB_SMEM_MAX ||
+                         mg_tb_smem(dim, true, t, 2 * nu_post) > MG_TB_SMEM_MAX))
+            t -= 2;
+        ld.tile[L] = t;
+    }
 }
 
 void plan_bottom(LevelData &ld, int dim)
@@ -120,10 +139,10 @@ void build_geometry(LevelData &ld, int dim)
 #define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
 
 enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
-                  KK_SETDENS, KK_BOTTOM, KK_COUNT };
+                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_COUNT };
 const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
                                          "defect",        "accumulate",     "interface",       "forces",
-                                         "set_density",   "bottom"};
+                                         "set_density",   "bottom",         "tb_pre",          "tb_post"};
 
 // Per-launch CUDA-event timing on the hierarchy's stream (mg_profile).
 struct Profiler {
@@ -165,6 +184,21 @@ struct mg_hierarchy {
     cudaGraphExec_t gexec = nullptr;
     std::vector<char> graph_sig;
     cudaStream_t cap[MG_BRANCHES] = {};
+    // batched mixed-precision plan (one launch per phase over all hierarchies)
+    struct BatchLevel {
+        int nparts = 0, maxLs = 0;
+        MgBPart *parts = nullptr;
+        int *active = nullptr;
+        std::vector<int> ntasks;              // per depth
+        std::vector<MgBTask *> tasks;         // per depth
+        MgBCell *cells_act = nullptr, *cells_blk = nullptr;
+        int ncells_act = 0, ncells_blk = 0;
+        std::vector<size_t> smem_pre, smem_post;
+        size_t smem_bottom = 0;
+    };
+    std::vector<BatchLevel> bl;
+    char *batch_mem = nullptr;
+    bool batched = false;
     cudaStream_t body_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join[MG_BRANCHES] = {};
 };
@@ -343,26 +377,46 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     cudaError_t e;
     if (Ls == 0)
         return bottom();                                                                  // whole cycle
-    if ((e = smooth(h, ld, 0, fp32, o.nu_pre, s)))                                        // step 2
-        return e;
+    // descent: at each level above Ls, nu_pre sweeps then residual and
+    // restriction (steps 2/6, 4, 5) -- one temporally blocked kernel per
+    // level in FP32 when the level has a tile, else one kernel per phase
     for (int L = 0; L < Ls; L++) {
-        const double by = 2.0 * w * (cells_d(ld.g[L].N, dim) + cells_d(ld.g[L + 1].N, dim));
-        e = timed(h, KK_RESTRICT, by, [&] {
-            return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s);
-        });                                                                               // steps 4-5
-        if (e)
+        const double nf = cells_d(ld.g[L].N, dim), nc = cells_d(ld.g[L + 1].N, dim);
+        if (fp32 && ld.tile[L]) {
+            e = timed(h, KK_TB_PRE, w * (3.0 * nf + 2.0 * nc), [&] {
+                return mg_launch_tb_pre(dim, ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
+                                        ld.f32[L + 1], ld.g[L + 1], ld.tile[L], o.nu_pre, s);
+            });
+            if (e)
+                return e;
+            continue;
+        }
+        if ((e = smooth(h, ld, L, fp32, o.nu_pre, s)))
             return e;
-        if (L + 1 < Ls && (e = smooth(h, ld, L + 1, fp32, o.nu_pre, s)))                  // step 6
+        e = timed(h, KK_RESTRICT, 2.0 * w * (nf + nc), [&] {
+            return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s);
+        });
+        if (e)
             return e;
     }
     if ((e = bottom()))                                                                   // steps 6-11, L >= Ls
         return e;
+    // ascent: prolongation + correction, then nu_post sweeps (steps 10-11)
     for (int L = Ls; L > 0; L--) {
-        const double by = w * (cells_d(ld.g[L].N, dim) + 2.0 * cells_d(ld.g[L - 1].N, dim));
-        e = timed(h, KK_PROLONG, by, [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
-        if (e)                                                                            // step 10
+        const double nf = cells_d(ld.g[L - 1].N, dim), nc = cells_d(ld.g[L].N, dim);
+        if (fp32 && ld.tile[L - 1]) {
+            e = timed(h, KK_TB_POST, w * (3.0 * nf + nc), [&] {
+                return mg_launch_tb_post(dim, ld.phi32b[L - 1], ld.phi32[L - 1], ld.f32[L - 1], ld.g[L - 1],
+                                         ld.phi32[L], ld.g[L], ld.tile[L - 1], o.nu_post, s);
+            });
+            if (e)
+                return e;
+            continue;
+        }
+        e = timed(h, KK_PROLONG, w * (nc + 2.0 * nf), [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
+        if (e)
             return e;
-        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s)))                               // step 11
+        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s)))
             return e;
     }
     return cudaSuccess;
@@ -546,6 +600,228 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
     return eb ? eb : e;
 }
 
+// Plan of the batched mixed-precision solve: per refinement level the parts
+// (hierarchies that have the level), their tile tasks per multigrid depth and
+// their cell-chunk tasks.  Returns false (no batched plan) when some part has
+// a level above its one-block kernel without an FP32 tile.
+bool plan_batched(mg_hierarchy *h, mg_status &err)
+{
+    err = MG_OK;
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    int maxL = 0;
+    for (int b = 0; b < h->batch; b++)
+        maxL = std::max(maxL, h->desc[b].num_levels);
+    struct HostLevel {
+        std::vector<MgBPart> parts;
+        std::vector<std::vector<MgBTask>> tasks;
+        std::vector<MgBCell> act, blk;
+    };
+    std::vector<HostLevel> HL(maxL);
+    size_t npart_total = 0;
+    for (int l = 0; l < maxL; l++) {
+        HostLevel &H = HL[l];
+        for (int b = 0; b < h->batch; b++) {
+            if (l >= h->desc[b].num_levels)
+                continue;
+            LevelData &ld = h->lev[b][l];
+            MgBPart P;
+            std::memset(&P, 0, sizeof P);
+            P.b = b;
+            P.l = l;
+            P.nmg = ld.nmg;
+            P.Ls = ld.Ls[1];
+            for (int L = 0; L < ld.nmg; L++) {
+                P.g[L] = ld.g[L];
+                P.tile[L] = ld.tile[L];
+                P.phi32[L] = ld.phi32[L];
+                P.phi32b[L] = ld.phi32b[L];
+                P.f32[L] = ld.f32[L];
+            }
+            for (int L = 0; L < P.Ls; L++)
+                if (!ld.tile[L])
+                    return false;
+            P.phi = ld.phi[0];
+            P.f = ld.f[0];
+            P.rho = ld.rho;
+            P.scal = level_scal(h, b, l);
+            P.ctl = level_ctl(h, b, l);
+            const long act = (long)std::pow((double)ld.g[0].N, dim), blk = cells(ld.n + 4, dim);
+            P.nblk_act = (int)std::min<long>((act + 255) / 256, MG_NORM_BLOCKS_MAX);
+            P.nblk_blk = (int)std::min<long>((blk + 255) / 256, 4096);
+            P.bt = ld.bt[1];
+            P.n = ld.n;
+            P.fourpiG = 4.0 * M_PI * h->desc[b].G;
+            P.guess = ld.guess;
+            if (l == 0) {
+                P.gmode = ld.guess_set ? 2 : -1;
+            } else {
+                const LevelData &pd = h->lev[b][l - 1];
+                P.np = pd.n;
+                P.phi_p = pd.phi[0];
+                P.rho_p = pd.rho;
+                for (int a = 0; a < 3; a++)
+                    P.off[a] = ld.off[a];
+                P.gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
+            }
+            const int p = (int)H.parts.size();
+            if ((int)H.tasks.size() < P.Ls)
+                H.tasks.resize(P.Ls);
+            for (int L = 0; L < P.Ls; L++) {
+                const int nb = (ld.g[L].N + ld.tile[L] - 1) / ld.tile[L];
+                for (int z = 0; z < (dim == 3 ? nb : 1); z++)
+                    for (int y = 0; y < nb; y++)
+                        for (int x = 0; x < nb; x++)
+                            H.tasks[L].push_back({p, x, y, z});
+            }
+            for (int c = 0; c < P.nblk_act; c++)
+                H.act.push_back({p, c});
+            for (int c = 0; c < P.nblk_blk; c++)
+                H.blk.push_back({p, c});
+            H.parts.push_back(P);
+        }
+        npart_total += H.parts.size();
+    }
+    // one allocation for the metadata and the per-part reduction scratch
+    size_t bytes = 0;
+    auto add = [&](size_t b) { const size_t at = bytes; bytes += align256(b); return at; };
+    std::vector<size_t> off_parts(maxL), off_active(maxL), off_act(maxL), off_blk(maxL);
+    std::vector<std::vector<size_t>> off_tasks(maxL);
+    for (int l = 0; l < maxL; l++) {
+        off_parts[l] = add(HL[l].parts.size() * sizeof(MgBPart));
+        off_active[l] = add(HL[l].parts.size() * sizeof(int));
+        off_act[l] = add(HL[l].act.size() * sizeof(MgBCell));
+        off_blk[l] = add(HL[l].blk.size() * sizeof(MgBCell));
+        for (auto &t : HL[l].tasks)
+            off_tasks[l].push_back(add(t.size() * sizeof(MgBTask)));
+    }
+    const size_t off_partials = add(npart_total * 2 * MG_NORM_BLOCKS_MAX * sizeof(double));
+    const size_t off_counters = add(npart_total * sizeof(unsigned));
+    if (h->batch_mem)
+        cudaFree(h->batch_mem);
+    h->batch_mem = nullptr;
+    cudaError_t e = cudaMalloc((void **)&h->batch_mem, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        err = fail(h, MG_ENOMEM, "cudaMalloc of %zu bytes for the batched plan failed", bytes);
+        return false;
+    }
+    char *base = h->batch_mem;
+    e = cudaMemsetAsync(base, 0, bytes, h->stream);
+    size_t pidx = 0;
+    h->bl.assign(maxL, mg_hierarchy::BatchLevel());
+    for (int l = 0; l < maxL && !e; l++) {
+        HostLevel &H = HL[l];
+        auto &B = h->bl[l];
+        for (auto &P : H.parts) {
+            P.partials = (double *)(base + off_partials) + pidx * 2 * MG_NORM_BLOCKS_MAX;
+            P.counter = (unsigned *)(base + off_counters) + pidx;
+            pidx++;
+            B.maxLs = std::max(B.maxLs, P.Ls);
+            B.smem_bottom = std::max(B.smem_bottom, mg_bottom_smem(dim, true, P.bt));
+        }
+        B.nparts = (int)H.parts.size();
+        B.parts = (MgBPart *)(base + off_parts[l]);
+        B.active = (int *)(base + off_active[l]);
+        B.cells_act = (MgBCell *)(base + off_act[l]);
+        B.cells_blk = (MgBCell *)(base + off_blk[l]);
+        B.ncells_act = (int)H.act.size();
+        B.ncells_blk = (int)H.blk.size();
+        B.smem_pre.assign(B.maxLs, 0);
+        B.smem_post.assign(B.maxLs, 0);
+        for (auto &P : H.parts)
+            for (int L = 0; L < P.Ls; L++) {
+                B.smem_pre[L] = std::max(B.smem_pre[L], mg_tb_smem(dim, true, P.tile[L], 2 * o.nu_pre + 1));
+                B.smem_post[L] = std::max(B.smem_post[L], mg_tb_smem(dim, true, P.tile[L], 2 * o.nu_post));
+            }
+        B.tasks.resize(H.tasks.size());
+        B.ntasks.resize(H.tasks.size());
+        e = cudaMemcpyAsync(B.parts, H.parts.data(), H.parts.size() * sizeof(MgBPart), cudaMemcpyHostToDevice, h->stream);
+        if (!e)
+            e = cudaMemcpyAsync(B.cells_act, H.act.data(), H.act.size() * sizeof(MgBCell), cudaMemcpyHostToDevice, h->stream);
+        if (!e)
+            e = cudaMemcpyAsync(B.cells_blk, H.blk.data(), H.blk.size() * sizeof(MgBCell), cudaMemcpyHostToDevice, h->stream);
+        for (size_t d = 0; d < H.tasks.size() && !e; d++) {
+            B.tasks[d] = (MgBTask *)(base + off_tasks[l][d]);
+            B.ntasks[d] = (int)H.tasks[d].size();
+            e = cudaMemcpyAsync(B.tasks[d], H.tasks[d].data(), H.tasks[d].size() * sizeof(MgBTask),
+                                cudaMemcpyHostToDevice, h->stream);
+        }
+    }
+    if (!e)
+        e = cudaStreamSynchronize(h->stream);
+    if (e) {
+        err = fail_cuda(h, e, "batched plan upload");
+        return false;
+    }
+    return true;
+}
+
+// One iteration of the batched loop of level l: FP64 defect, inner_cycles
+// FP32 V-cycles over all parts (pre legs by depth, the one-block kernels,
+// post legs), FP64 accumulation, norms and the loop control.
+cudaError_t capture_batched_level(mg_hierarchy *h, int l, cudaStream_t s, cudaStream_t body)
+{
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    auto &B = h->bl[l];
+    if (B.nparts == 0)
+        return cudaSuccess;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e)
+        return e;
+    cudaGraphConditionalHandle hc;
+    if ((e = cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault)))
+        return e;
+    if ((e = mg_launch_b_interface(dim, B.parts, B.cells_blk, B.ncells_blk, s)))
+        return e;
+    if ((e = cudaMemsetAsync(B.active, 0x01, B.nparts * sizeof(int), s)))
+        return e;
+    if ((e = mg_launch_b_norms2(dim, B.parts, B.cells_act, B.ncells_act, B.active, 3, s)))
+        return e;
+    if ((e = mg_launch_b_ctl(B.parts, B.nparts, B.active, 1, 0, o.rel_tol, o.max_cycles, hc, s)))
+        return e;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd)))
+        return e;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &p)))
+        return e;
+    cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)))
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(body, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+        return e;
+    cudaError_t eb = mg_launch_b_defect(dim, B.parts, B.cells_act, B.ncells_act, B.active, body);
+    for (int c = 0; c < o.inner_cycles && !eb; c++) {
+        for (int d = 0; d < B.maxLs && !eb; d++)
+            eb = mg_launch_b_tb_pre(dim, B.parts, B.tasks[d], B.ntasks[d], B.active, d, o.nu_pre, B.smem_pre[d], body);
+        if (!eb)
+            eb = mg_launch_b_bottom(dim, B.parts, B.nparts, B.active, o.nu_pre, o.nu_post, B.smem_bottom, body);
+        for (int d = B.maxLs - 1; d >= 0 && !eb; d--)
+            eb = mg_launch_b_tb_post(dim, B.parts, B.tasks[d], B.ntasks[d], B.active, d, o.nu_post, B.smem_post[d],
+                                     body);
+    }
+    if (!eb)
+        eb = mg_launch_b_accumulate(dim, B.parts, B.cells_act, B.ncells_act, B.active, body);
+    if (!eb)
+        eb = mg_launch_b_norms2(dim, B.parts, B.cells_act, B.ncells_act, B.active, 2, body);
+    if (!eb)
+        eb = mg_launch_b_ctl(B.parts, B.nparts, B.active, 0, o.inner_cycles, o.rel_tol, o.max_cycles, hc, body);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(body, &out);
+    return eb ? eb : e;
+}
+
 mg_status build_graph(mg_hierarchy *h)
 {
     destroy_graph(h);
@@ -559,6 +835,33 @@ mg_status build_graph(mg_hierarchy *h)
         CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         for (int i = 0; i < MG_BRANCHES; i++)
             CK(h, cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
+    }
+    h->batched = false;
+    if (h->opt.precision == MG_MIXED && h->batch > 1) {
+        const char *v = std::getenv("MG_BATCHED");
+        if (!(v && v[0] == '0')) {
+            mg_status perr;
+            h->batched = plan_batched(h, perr);
+            if (perr)
+                return perr;
+        }
+    }
+    if (h->batched) {
+        CK(h, cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < (int)h->bl.size() && !e; l++)
+            e = capture_batched_level(h, l, h->cap[0], h->body_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(h->cap[0], &g);
+        if (e || ee) {
+            if (g)
+                cudaGraphDestroy(g);
+            return fail_cuda(h, e ? e : ee, "capture of the batched solve graph");
+        }
+        h->graph = g;
+        CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
+        h->graph_sig = graph_signature(h);
+        return MG_OK;
     }
     CK(h, cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaEventRecord(h->ev_fork, h->cap[0]);
@@ -721,6 +1024,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 slots.push_back({(void **)&ld.f[L], align256(c * sizeof(double))});
                 if (o.precision == MG_MIXED) {
                     slots.push_back({(void **)&ld.phi32[L], align256(c * sizeof(float))});
+                    slots.push_back({(void **)&ld.phi32b[L], align256(c * sizeof(float))});
                     slots.push_back({(void **)&ld.f32[L], align256(c * sizeof(float))});
                 }
             }
@@ -772,6 +1076,10 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     // ghost layers and rings start at zero
     e = mg_bottom_prepare();
     if (e == cudaSuccess)
+        e = mg_tb_prepare();
+    if (e == cudaSuccess)
+        e = mg_batch_prepare();
+    if (e == cudaSuccess)
         e = mg_launch_zero(h->arena, bytes, h->stream);
     // boundary-diagonal tables of the coarse multigrid levels, then the plan
     // of the one-block kernel (which copies the level descriptions)
@@ -790,6 +1098,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 ld.g[L].tab32 = ld.tab32[L];
             }
             plan_bottom(ld, dim);
+            plan_tiles(ld, dim, o.nu_pre, o.nu_post);
         }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(h->stream);
@@ -990,6 +1299,8 @@ mg_status mg_destroy(mg_hierarchy *h)
     for (cudaEvent_t e : h->prof.pool)
         cudaEventDestroy(e);
     destroy_graph(h);
+    if (h->batch_mem)
+        cudaFree(h->batch_mem);
     for (int i = 0; i < MG_BRANCHES; i++) {
         if (h->cap[i])
             cudaStreamDestroy(h->cap[i]);

@@ -85,6 +85,18 @@ cudaError_t mg_bottom_prepare();   // once per device before the first launch
 cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const MgBottom &bt, int nu_pre,
                              int nu_post, cudaStream_t s);
 
+// Temporally blocked FP32 legs of the V-cycle (tile^d fine cells per block,
+// tile even): pre = nu red-black sweeps, residual and restriction to the
+// next level (phi_in -> phi_out, f_c, phi_c = 0); post = prolongation of
+// phi_c, correction and nu sweeps (phi_in -> phi_out).
+#define MG_TB_SMEM_MAX (200 * 1024)
+size_t mg_tb_smem(int dim, bool fp32, int tile, int halo);
+cudaError_t mg_tb_prepare();
+cudaError_t mg_launch_tb_pre(int dim, const float *phi_in, float *phi_out, const float *f, const MgGeom &g,
+                             float *phi_c, float *f_c, const MgGeom &gc, int tile, int nu, cudaStream_t s);
+cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, const float *f, const MgGeom &g,
+                              const float *phi_c, const MgGeom &gc, int tile, int nu, cudaStream_t s);
+
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
                                      void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s);
 cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeom &gc, void *phi_f, const MgGeom &gf,
@@ -151,3 +163,54 @@ cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, 
                                cudaGraphConditionalHandle hc, cudaStream_t s);
 cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
                                cudaGraphConditionalHandle hc, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Batched mixed-precision solve: one launch per phase over every hierarchy
+// of a batch that has refinement level l.  A part is one hierarchy's level;
+// tile tasks and cell-chunk tasks say which part and which piece a block
+// works on; active[p] masks the parts that have converged.
+// ---------------------------------------------------------------------------
+struct MgBPart {
+    int b, l;                      // hierarchy and refinement level
+    int nmg, Ls;                   // multigrid levels; first level of the one-block kernel
+    MgGeom g[MG_MAX_MG];
+    int tile[MG_MAX_MG];
+    float *phi32[MG_MAX_MG], *phi32b[MG_MAX_MG], *f32[MG_MAX_MG];
+    double *phi, *f, *rho;         // (n+4)^d finest blocks
+    double *scal;                  // ||b||^2, ||r||^2
+    MgSolveCtl *ctl;
+    double *partials;              // 2 * MG_NORM_BLOCKS_MAX
+    unsigned *counter;
+    int nblk_act;                  // cell chunks over the active finest cells
+    int nblk_blk;                  // cell chunks over the (n+4)^d block
+    MgBottom bt;
+    // interface from the parent (l > 0), initial guess
+    int n, np, off[3], gmode;      // gmode: 0 interpolate, 1 zero, 2 copy guess, -1 none (level 0)
+    const double *phi_p, *rho_p, *guess;
+    double fourpiG;
+};
+struct MgBTask {                   // tile task
+    int part, bx, by, bz;
+};
+struct MgBCell {                   // cell-chunk task
+    int part, chunk;
+};
+
+cudaError_t mg_batch_prepare();
+cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,
+                               int depth, int nu, size_t smem, cudaStream_t s);
+cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,
+                                int depth, int nu, size_t smem, cudaStream_t s);
+cudaError_t mg_launch_b_bottom(int dim, const MgBPart *parts, int nparts, const int *active, int nu_pre, int nu_post,
+                               size_t smem, cudaStream_t s);
+cudaError_t mg_launch_b_defect(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                               cudaStream_t s);
+cudaError_t mg_launch_b_accumulate(int dim, const MgBPart *parts, const MgBCell *cells, int ncells,
+                                   const int *active, cudaStream_t s);
+cudaError_t mg_launch_b_norms2(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                               int which, cudaStream_t s);
+cudaError_t mg_launch_b_interface(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, cudaStream_t s);
+// init = 1: start every part's loop from its norms; else account `inc`
+// cycles to the active parts.  Sets active[] and the loop condition.
+cudaError_t mg_launch_b_ctl(const MgBPart *parts, int nparts, int *active, int init, int inc, double tol,
+                            int max_cycles, cudaGraphConditionalHandle hc, cudaStream_t s);

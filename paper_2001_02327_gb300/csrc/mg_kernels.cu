@@ -66,17 +66,17 @@ __device__ __forceinline__ const float *tab_of<float>(const MgGeom &g) { return 
 // touches no multigrid boundary, always 0 on the finest level where the outer
 // ring holds Dirichlet data).
 template <typename T, int DIM>
-__device__ __forceinline__ T neighbour_sum(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, int p,
-                                          int &cls)
+__device__ __forceinline__ T neighbour_sum_s(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, int p,
+                                            int sy, int sz, int &cls)
 {
-    const int E = g.E, N = g.N;
+    const int N = g.N;
     const bool coarse = g.L > 0;
     const bool inner = !coarse || (i > 1 && i < N && j > 1 && j < N && (DIM == 2 || (k > 1 && k < N)));
     if (inner) {
         cls = 0;
-        T s = (phi[p - 1] + phi[p + 1]) + (phi[p - E] + phi[p + E]);
+        T s = (phi[p - 1] + phi[p + 1]) + (phi[p - sy] + phi[p + sy]);
         if (DIM == 3)
-            s += phi[p - E * E] + phi[p + E * E];
+            s += phi[p - sz] + phi[p + sz];
         return s;
     }
     // left neighbour dropped at index 1 (ghost = -self: goes to the diagonal)
@@ -91,10 +91,18 @@ __device__ __forceinline__ T neighbour_sum(const T *__restrict__ phi, const MgGe
         const T r = !hi ? phi[p + st] : T(0);
         return l + r;
     };
-    T s = axis(i, 1, 0) + axis(j, E, 2);
+    T s = axis(i, 1, 0) + axis(j, sy, 2);
     if (DIM == 3)
-        s += axis(k, E * E, 4);
+        s += axis(k, sz, 4);
     return s;
+}
+
+// the same on a level array of edge g.E
+template <typename T, int DIM>
+__device__ __forceinline__ T neighbour_sum(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, int p,
+                                          int &cls)
+{
+    return neighbour_sum_s<T, DIM>(phi, g, i, j, k, p, g.E, g.E * g.E, cls);
 }
 
 template <typename T, int DIM>
@@ -240,11 +248,52 @@ __device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, T &
 // Prolongation and correction (Sec. 2.3 step 10; bi/trilinear 3/4-1/4
 // weights per axis, i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse
 // ghosts by the rule, evaluated one axis at a time.
+// P(Phi_c) at fine active cell f (Sec. 2.3 step 10)
+template <typename T, int DIM>
+__device__ __forceinline__ T prolong_value(const T *__restrict__ phi_c, const MgGeom &gc, const int *f)
+{
+    const int Ec = gc.E;
+    int idx[3][2];
+    T w[3][2];
+    for (int a = 0; a < DIM; a++) {
+        const int near = (f[a] + 1) >> 1;
+        const int far = (f[a] & 1) ? near - 1 : near + 1;
+        T c0, c1;
+        ghost_map<T>(near, gc, idx[a][0], c0);
+        ghost_map<T>(far, gc, idx[a][1], c1);
+        w[a][0] = T(0.75) * c0;
+        w[a][1] = T(0.25) * c1;
+    }
+    if (DIM == 3) {
+        T zsum = T(0);
+        for (int c = 0; c < 2; c++) {
+            T ysum = T(0);
+            for (int b = 0; b < 2; b++) {
+                const int row = (idx[2][c] * Ec + idx[1][b]) * Ec;
+                const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
+                ysum += w[1][b] * xv;
+            }
+            zsum += w[2][c] * ysum;
+        }
+        return zsum;
+    }
+    T ysum = T(0);
+    for (int b = 0; b < 2; b++) {
+        const int row = idx[1][b] * Ec;
+        const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
+        ysum += w[1][b] * xv;
+    }
+    return ysum;
+}
+
+// Prolongation and correction (Sec. 2.3 step 10; bi/trilinear 3/4-1/4
+// weights per axis, i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse
+// ghosts by the rule, evaluated one axis at a time.
 template <typename T, int DIM>
 __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const MgGeom &gc, T *__restrict__ phi_f,
                                            const MgGeom &gf, int t0, int stride)
 {
-    const int Nf = gf.N, Ec = gc.E;
+    const int Nf = gf.N;
     const int total = Nf * Nf * (DIM == 3 ? Nf : 1);
     for (int t = t0; t < total; t += stride) {
         int f[3];
@@ -258,40 +307,7 @@ __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const Mg
             f[1] = r + 1;
             f[2] = 0;
         }
-        int idx[3][2];
-        T w[3][2];
-        for (int a = 0; a < DIM; a++) {
-            const int near = (f[a] + 1) >> 1;
-            const int far = (f[a] & 1) ? near - 1 : near + 1;
-            T c0, c1;
-            ghost_map<T>(near, gc, idx[a][0], c0);
-            ghost_map<T>(far, gc, idx[a][1], c1);
-            w[a][0] = T(0.75) * c0;
-            w[a][1] = T(0.25) * c1;
-        }
-        T v;
-        if (DIM == 3) {
-            T zsum = T(0);
-            for (int c = 0; c < 2; c++) {
-                T ysum = T(0);
-                for (int b = 0; b < 2; b++) {
-                    const int row = (idx[2][c] * Ec + idx[1][b]) * Ec;
-                    const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
-                    ysum += w[1][b] * xv;
-                }
-                zsum += w[2][c] * ysum;
-            }
-            v = zsum;
-        } else {
-            T ysum = T(0);
-            for (int b = 0; b < 2; b++) {
-                const int row = idx[1][b] * Ec;
-                const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
-                ysum += w[1][b] * xv;
-            }
-            v = ysum;
-        }
-        phi_f[lin<DIM>(f[0], f[1], f[2], gf.E)] += v;
+        phi_f[lin<DIM>(f[0], f[1], f[2], gf.E)] += prolong_value<T, DIM>(phi_c, gc, f);
     }
 }
 
@@ -359,10 +375,9 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_
 // the smoothed Phi of level Ls goes back.  Same per-cell arithmetic and the
 // same order of phases as the one-kernel-per-phase path.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g, const T *__restrict__ f_g,
-                                                           MgBottom bt, int nu_pre, int nu_post)
+__device__ __forceinline__ void bottom_body(T *__restrict__ phi_g, const T *__restrict__ f_g, const MgBottom &bt,
+                                            int nu_pre, int nu_post, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     int offs[MG_BOTTOM_MAX + 1];
     offs[0] = 0;
@@ -406,6 +421,254 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g
     }
     for (int t = tid; t < c0; t += nth)
         phi_g[t] = PHI(0)[t];
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g, const T *__restrict__ f_g,
+                                                           MgBottom bt, int nu_pre, int nu_post)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bottom_body<T, DIM>(phi_g, f_g, bt, nu_pre, nu_post, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Temporally blocked FP32 V-cycle legs.  A block owns a tile of `tile`^d
+// fine active cells (origin at an odd 1-based index, tile even, so the tile
+// holds whole restriction families) and keeps the tile plus a halo in shared
+// memory.  Each half-sweep updates a region one cell narrower than the one
+// before, so the halo's values -- recomputed identically by the neighbouring
+// blocks -- stay exact for the next half-sweep; only the tile is written
+// back, into the other Phi buffer (the neighbours still read the input).
+// The arithmetic per cell and the order of the phases are those of the
+// one-kernel-per-phase path.
+// ---------------------------------------------------------------------------
+struct TbBox {
+    int b0[3];   // storage coordinates of the Phi box origin
+    int P;       // Phi box edge (tile + 2 halo)
+};
+
+// Visit the cells of colour `colour` in the storage box [lo, hi] (inclusive).
+template <int DIM, class Fn>
+__device__ __forceinline__ void for_colour_cells(const int *lo, const int *hi, int colour, Fn &&fn)
+{
+    if (hi[0] < lo[0] || hi[1] < lo[1] || (DIM == 3 && hi[2] < lo[2]))
+        return;
+    const int W = hi[0] - lo[0] + 1, hw = (W + 1) >> 1;
+    const int ny = hi[1] - lo[1] + 1, nz = DIM == 3 ? hi[2] - lo[2] + 1 : 1;
+    const int total = hw * ny * nz;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int r = t / hw;
+        const int i2 = t - r * hw;
+        const int j = lo[1] + (DIM == 3 ? r % ny : r);
+        const int k = DIM == 3 ? lo[2] + r / ny : 0;
+        const int i0 = lo[0] + (((lo[0] + j + k + colour) & 1) ? 1 : 0);
+        const int i = i0 + 2 * i2;
+        if (i <= hi[0])
+            fn(i, j, k);
+    }
+}
+
+// Visit every cell of the storage box [lo, hi].
+template <int DIM, class Fn>
+__device__ __forceinline__ void for_box_cells(const int *lo, const int *hi, Fn &&fn)
+{
+    if (hi[0] < lo[0] || hi[1] < lo[1] || (DIM == 3 && hi[2] < lo[2]))
+        return;
+    const int W = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = DIM == 3 ? hi[2] - lo[2] + 1 : 1;
+    const int total = W * ny * nz;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int r = t / W;
+        const int i = lo[0] + t - r * W;
+        const int j = lo[1] + (DIM == 3 ? r % ny : r);
+        const int k = DIM == 3 ? lo[2] + r / ny : 0;
+        fn(i, j, k);
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ int box_index(const TbBox &b, int i, int j, int k)
+{
+    return DIM == 3 ? ((k - b.b0[2]) * b.P + (j - b.b0[1])) * b.P + (i - b.b0[0]) : (j - b.b0[1]) * b.P + (i - b.b0[0]);
+}
+
+// Load the Phi box (cells outside the level's storage read as zero) and f
+// (active cells only) of a tile whose origin is o and halo H.
+template <typename T, int DIM>
+__device__ __forceinline__ void tb_load(const T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g,
+                                        const TbBox &b, T *sPhi, T *sF)
+{
+    const int N = g.N;
+    const int P = b.P;
+    const int nP = P * P * (DIM == 3 ? P : 1);
+    for (int t = threadIdx.x; t < nP; t += blockDim.x) {
+        const int r = t / P;
+        const int a0 = t - r * P;
+        const int a1 = DIM == 3 ? r % P : r;
+        const int a2 = DIM == 3 ? r / P : 0;
+        const int i = b.b0[0] + a0, j = b.b0[1] + a1, k = DIM == 3 ? b.b0[2] + a2 : 0;
+        const bool in = i >= 0 && i <= N + 1 && j >= 0 && j <= N + 1 && (DIM == 2 || (k >= 0 && k <= N + 1));
+        const bool act = i >= 1 && i <= N && j >= 1 && j <= N && (DIM == 2 || (k >= 1 && k <= N));
+        const int gq = in ? lin<DIM>(i, j, k, g.E) : 0;
+        sPhi[t] = in ? phi[gq] : T(0);
+        sF[t] = act ? f[gq] : T(0);
+    }
+}
+
+// Half-sweeps s = 0 .. nhalf-1 over regions [o - (H-1-s), o + tile - 1 + (H-1-s)]
+template <typename T, int DIM>
+__device__ __forceinline__ void tb_sweeps(T *sPhi, const T *sF, const MgGeom &g, const TbBox &b, const int *o,
+                                          int tile, int H, int nhalf)
+{
+    const int N = g.N;
+    const T h2 = geo_h2<T>(g);
+    const int sy = b.P, sz = b.P * b.P;
+    for (int s = 0; s < nhalf; s++) {
+        const int w = H - 1 - s;
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = max(o[a] - w, 1);
+            hi[a] = min(o[a] + tile - 1 + w, N);
+        }
+        for_colour_cells<DIM>(lo, hi, s & 1, [&](int i, int j, int k) {
+            const int q = box_index<DIM>(b, i, j, k);
+            int cls;
+            const T other = neighbour_sum_s<T, DIM>(sPhi, g, i, j, k, q, sy, sz, cls);
+            sPhi[q] = (other - h2 * sF[q]) * neg_inv_diag<T, DIM>(g, cls);
+        });
+        __syncthreads();
+    }
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void tb_store(T *__restrict__ phi, const MgGeom &g, const T *sPhi, const TbBox &b,
+                                         const int *o, int tile)
+{
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = o[a];
+        hi[a] = min(o[a] + tile - 1, g.N);
+    }
+    for_box_cells<DIM>(lo, hi, [&](int i, int j, int k) { phi[lin<DIM>(i, j, k, g.E)] = sPhi[box_index<DIM>(b, i, j, k)]; });
+}
+
+// Pre-smoothing (nu sweeps), residual and restriction of the tile at block
+// coordinates blk.
+template <typename T, int DIM>
+__device__ __forceinline__ void tb_pre_body(const T *__restrict__ phi_in, T *__restrict__ phi_out,
+                                            const T *__restrict__ f, const MgGeom &g, T *__restrict__ phi_c,
+                                            T *__restrict__ f_c, const MgGeom &gc, int tile, int nu, const int *blk,
+                                            unsigned char *smem_raw)
+{
+    const int H = 2 * nu + 1;
+    TbBox b;
+    b.P = tile + 2 * H;
+    const int o[3] = {1 + tile * blk[0], 1 + tile * blk[1], DIM == 3 ? 1 + tile * blk[2] : 0};
+    for (int a = 0; a < 3; a++)
+        b.b0[a] = (DIM == 2 && a == 2) ? 0 : o[a] - H;
+    const int nP = b.P * b.P * (DIM == 3 ? b.P : 1);
+    T *sPhi = reinterpret_cast<T *>(smem_raw);
+    T *sF = sPhi + nP;
+    tb_load<T, DIM>(phi_in, f, g, b, sPhi, sF);
+    __syncthreads();
+    tb_sweeps<T, DIM>(sPhi, sF, g, b, o, tile, H, 2 * nu);
+    // residual on the tile and the 2^d-child averages (fine cells beyond N count zero)
+    const int Nf = g.N, Nc = gc.N;
+    const int ch = tile / 2;
+    int clo[3], chi[3];
+    for (int a = 0; a < 3; a++) {
+        clo[a] = (o[a] + 1) / 2;
+        chi[a] = min(clo[a] + ch - 1, Nc);
+    }
+    if (DIM == 2) {
+        clo[2] = chi[2] = 0;
+    }
+    const T w = DIM == 3 ? T(0.125) : T(0.25);
+    const T ih2 = geo_inv_h2<T>(g);
+    const int sy = b.P, sz = b.P * b.P;
+    for_box_cells<DIM>(clo, chi, [&](int I, int J, int K) {
+        T s = T(0);
+        for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++) {
+            const int k = DIM == 3 ? 2 * K - 1 + dk : 0;
+            if (DIM == 3 && k > Nf)
+                continue;
+            for (int dj = 0; dj < 2; dj++) {
+                const int j = 2 * J - 1 + dj;
+                if (j > Nf)
+                    continue;
+                for (int di = 0; di < 2; di++) {
+                    const int i = 2 * I - 1 + di;
+                    if (i > Nf)
+                        continue;
+                    const int q = box_index<DIM>(b, i, j, k);
+                    int cls;
+                    const T other = neighbour_sum_s<T, DIM>(sPhi, g, i, j, k, q, sy, sz, cls);
+                    s += sF[q] - (other + diag_of<T, DIM>(g, cls) * sPhi[q]) * ih2;
+                }
+            }
+        }
+        const int pc = lin<DIM>(I, J, K, gc.E);
+        f_c[pc] = w * s;
+        phi_c[pc] = T(0);
+    });
+    tb_store<T, DIM>(phi_out, g, sPhi, b, o, tile);
+}
+
+// Prolongation + correction and post-smoothing (nu sweeps) of the tile at
+// block coordinates blk.
+template <typename T, int DIM>
+__device__ __forceinline__ void tb_post_body(const T *__restrict__ phi_in, T *__restrict__ phi_out,
+                                             const T *__restrict__ f, const MgGeom &g, const T *__restrict__ phi_c,
+                                             const MgGeom &gc, int tile, int nu, const int *blk,
+                                             unsigned char *smem_raw)
+{
+    const int H = 2 * nu;
+    TbBox b;
+    b.P = tile + 2 * H;
+    const int o[3] = {1 + tile * blk[0], 1 + tile * blk[1], DIM == 3 ? 1 + tile * blk[2] : 0};
+    for (int a = 0; a < 3; a++)
+        b.b0[a] = (DIM == 2 && a == 2) ? 0 : o[a] - H;
+    const int nP = b.P * b.P * (DIM == 3 ? b.P : 1);
+    T *sPhi = reinterpret_cast<T *>(smem_raw);
+    T *sF = sPhi + nP;
+    tb_load<T, DIM>(phi_in, f, g, b, sPhi, sF);
+    __syncthreads();
+    // correct every active cell of the box
+    {
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = max(b.b0[a], 1);
+            hi[a] = min(b.b0[a] + b.P - 1, g.N);
+        }
+        if (DIM == 2)
+            lo[2] = hi[2] = 0;
+        for_box_cells<DIM>(lo, hi, [&](int i, int j, int k) {
+            const int fc[3] = {i, j, k};
+            sPhi[box_index<DIM>(b, i, j, k)] += prolong_value<T, DIM>(phi_c, gc, fc);
+        });
+    }
+    __syncthreads();
+    tb_sweeps<T, DIM>(sPhi, sF, g, b, o, tile, H, 2 * nu);
+    tb_store<T, DIM>(phi_out, g, sPhi, b, o, tile);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(512) k_tb_pre(const T *__restrict__ phi_in, T *__restrict__ phi_out,
+                                                const T *__restrict__ f, MgGeom g, T *__restrict__ phi_c,
+                                                T *__restrict__ f_c, MgGeom gc, int tile, int nu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int blk[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
+    tb_pre_body<T, DIM>(phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu, blk, smem_raw);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(512) k_tb_post(const T *__restrict__ phi_in, T *__restrict__ phi_out,
+                                                 const T *__restrict__ f, MgGeom g, const T *__restrict__ phi_c,
+                                                 MgGeom gc, int tile, int nu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int blk[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
+    tb_post_body<T, DIM>(phi_in, phi_out, f, g, phi_c, gc, tile, nu, blk, smem_raw);
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -777,6 +1040,231 @@ __global__ void k_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double 
     cudaGraphSetConditional(hc, c.go);
 }
 
+
+// ---------------------------------------------------------------------------
+// batched kernels (one launch per phase over all parts)
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(512) kb_tb_pre(const MgBPart *__restrict__ parts, const MgBTask *__restrict__ tasks,
+                                                 const int *__restrict__ active, int L, int nu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const MgBTask tk = tasks[blockIdx.x];
+    if (!active[tk.part])
+        return;
+    const MgBPart &P = parts[tk.part];
+    const int blk[3] = {tk.bx, tk.by, tk.bz};
+    tb_pre_body<float, DIM>(P.phi32[L], P.phi32b[L], P.f32[L], P.g[L], P.phi32[L + 1], P.f32[L + 1], P.g[L + 1],
+                            P.tile[L], nu, blk, smem_raw);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(512) kb_tb_post(const MgBPart *__restrict__ parts, const MgBTask *__restrict__ tasks,
+                                                  const int *__restrict__ active, int L, int nu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const MgBTask tk = tasks[blockIdx.x];
+    if (!active[tk.part])
+        return;
+    const MgBPart &P = parts[tk.part];
+    const int blk[3] = {tk.bx, tk.by, tk.bz};
+    tb_post_body<float, DIM>(P.phi32b[L], P.phi32[L], P.f32[L], P.g[L], P.phi32[L + 1], P.g[L + 1], P.tile[L], nu,
+                             blk, smem_raw);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBottomThreads) kb_bottom(const MgBPart *__restrict__ parts,
+                                                            const int *__restrict__ active, int nu_pre, int nu_post)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (!active[blockIdx.x])
+        return;
+    const MgBPart &P = parts[blockIdx.x];
+    bottom_body<float, DIM>(P.phi32[P.Ls], P.f32[P.Ls], P.bt, nu_pre, nu_post, smem_raw);
+}
+
+template <int DIM>
+__device__ __forceinline__ void active_cell(const MgGeom &g, int t, int &i, int &j, int &k)
+{
+    const int N = g.N;
+    const int r = t / N;
+    i = t - r * N + 1;
+    if (DIM == 3) {
+        k = r / N;
+        j = r - k * N + 1;
+        k += 1;
+    } else {
+        j = r + 1;
+        k = 0;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_defect(const MgBPart *__restrict__ parts,
+                                                      const MgBCell *__restrict__ cells, const int *__restrict__ active)
+{
+    const MgBCell c = cells[blockIdx.x];
+    if (!active[c.part])
+        return;
+    const MgBPart &P = parts[c.part];
+    const MgGeom &g = P.g[0];
+    const int total = g.N * g.N * (DIM == 3 ? g.N : 1);
+    for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_act * kThreads) {
+        int i, j, k;
+        active_cell<DIM>(g, t, i, j, k);
+        const int p = lin<DIM>(i, j, k, g.E);
+        P.f32[0][p] = (float)residual_at<double, DIM>(P.phi, P.f, g, i, j, k);
+        P.phi32[0][p] = 0.0f;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_accumulate(const MgBPart *__restrict__ parts,
+                                                          const MgBCell *__restrict__ cells,
+                                                          const int *__restrict__ active)
+{
+    const MgBCell c = cells[blockIdx.x];
+    if (!active[c.part])
+        return;
+    const MgBPart &P = parts[c.part];
+    const MgGeom &g = P.g[0];
+    const int total = g.N * g.N * (DIM == 3 ? g.N : 1);
+    for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_act * kThreads) {
+        int i, j, k;
+        active_cell<DIM>(g, t, i, j, k);
+        const int p = lin<DIM>(i, j, k, g.E);
+        P.phi[p] += (double)P.phi32[0][p];
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_norms2(const MgBPart *__restrict__ parts,
+                                                      const MgBCell *__restrict__ cells, const int *__restrict__ active,
+                                                      int which)
+{
+    __shared__ double sm[kThreads / 32];
+    __shared__ bool last;
+    const MgBCell c = cells[blockIdx.x];
+    if (!active[c.part])
+        return;
+    const MgBPart &P = parts[c.part];
+    const MgGeom &g = P.g[0];
+    const int total = g.N * g.N * (DIM == 3 ? g.N : 1);
+    double b2 = 0.0, r2 = 0.0;
+    for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_act * kThreads)
+        norm_terms<DIM>(P.phi, P.f, g, t, which, b2, r2);
+    b2 = block_sum(b2, sm);
+    r2 = block_sum(r2, sm);
+    if (threadIdx.x == 0) {
+        P.partials[2 * c.chunk] = b2;
+        P.partials[2 * c.chunk + 1] = r2;
+        __threadfence();
+        last = atomicAdd(P.counter, 1u) == (unsigned)P.nblk_act - 1;
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    double sb = 0.0, sr = 0.0;
+    for (int t = threadIdx.x; t < P.nblk_act; t += blockDim.x) {
+        sb += P.partials[2 * t];
+        sr += P.partials[2 * t + 1];
+    }
+    sb = block_sum(sb, sm);
+    sr = block_sum(sr, sm);
+    if (threadIdx.x == 0) {
+        if (which & 1)
+            P.scal[0] = sb;
+        if (which & 2)
+            P.scal[1] = sr;
+        *P.counter = 0u;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_interface(const MgBPart *__restrict__ parts,
+                                                         const MgBCell *__restrict__ cells)
+{
+    const MgBCell c = cells[blockIdx.x];
+    const MgBPart &P = parts[c.part];
+    if (P.gmode < 0)
+        return;
+    const int nc = P.n, E = nc + 4, Ep = P.np + 4;
+    const int total = E * E * (DIM == 3 ? E : 1);
+    for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_blk * kThreads) {
+        int s[3];
+        const int r = t / E;
+        s[0] = t - r * E;
+        s[1] = DIM == 3 ? r % E : r;
+        s[2] = DIM == 3 ? r / E : 2;
+        bool outer = false, inner = false;
+        for (int a = 0; a < DIM; a++) {
+            if (s[a] == 0 || s[a] == nc + 3)
+                outer = true;
+            else if (s[a] == 1 || s[a] == nc + 2)
+                inner = true;
+        }
+        if (P.l == 0) {            // level 0: only a caller-supplied start inside
+            if (!outer && P.gmode == 2)
+                P.phi[t] = P.guess[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+            continue;
+        }
+        int p0[3] = {0, 0, 0};
+        double w[3] = {0, 0, 0};
+        for (int a = 0; a < DIM; a++)
+            iface_axis(s[a], P.off[a], p0[a], w[a]);
+        if (outer) {
+            P.phi[t] = interp<DIM>(P.phi_p, Ep, p0, w);
+            continue;
+        }
+        if (inner) {
+            const double rv = interp<DIM>(P.rho_p, Ep, p0, w);
+            P.rho[t] = rv;
+            P.f[t] = P.fourpiG * rv;
+        }
+        if (P.gmode == 0)
+            P.phi[t] = interp<DIM>(P.phi_p, Ep, p0, w);
+        else if (P.gmode == 1)
+            P.phi[t] = 0.0;
+        else
+            P.phi[t] = P.guess[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+    }
+}
+
+__global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts, int nparts, int *__restrict__ active,
+                                               int init, int inc, double tol, int max_cycles,
+                                               cudaGraphConditionalHandle hc)
+{
+    int any = 0;
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+        const MgBPart &P = parts[p];
+        MgSolveCtl c;
+        if (init) {
+            c.bnorm = sqrt(P.scal[0]);
+            c.rel = c.bnorm > 0.0 ? sqrt(P.scal[1]) / c.bnorm : 0.0;
+            c.cycles = 0;
+            c.outer = 0;
+            c.status = 0;
+        } else {
+            c = *P.ctl;
+            if (!active[p])
+                continue;
+            c.cycles += inc;
+            c.outer += 1;
+            c.rel = sqrt(P.scal[1]) / c.bnorm;
+            if (!isfinite(c.rel))
+                c.status = 6;
+        }
+        c.go = keep_going(c, tol, max_cycles);
+        *P.ctl = c;
+        active[p] = c.go;
+        any |= c.go;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0)
+        cudaGraphSetConditional(hc, any ? 1u : 0u);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -837,6 +1325,49 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
         else
             k_bottom<double, 2><<<1, kBottomThreads, smem, s>>>((double *)phi, (const double *)f, bt, nu_pre, nu_post);
     }
+    return cudaGetLastError();
+}
+
+size_t mg_tb_smem(int dim, bool fp32, int tile, int halo)
+{
+    const size_t P = tile + 2 * halo;
+    return 2 * (dim == 3 ? P * P * P : P * P) * (fp32 ? 4 : 8);
+}
+
+cudaError_t mg_tb_prepare()
+{
+    const int lim = MG_TB_SMEM_MAX;
+    cudaError_t e = cudaFuncSetAttribute(k_tb_pre<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(k_tb_post<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(k_tb_pre<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(k_tb_post<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return e;
+}
+
+cudaError_t mg_launch_tb_pre(int dim, const float *phi_in, float *phi_out, const float *f, const MgGeom &g,
+                             float *phi_c, float *f_c, const MgGeom &gc, int tile, int nu, cudaStream_t s)
+{
+    const int nb = (g.N + tile - 1) / tile;
+    const size_t smem = mg_tb_smem(dim, true, tile, 2 * nu + 1);
+    if (dim == 3)
+        k_tb_pre<float, 3><<<dim3(nb, nb, nb), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
+    else
+        k_tb_pre<float, 2><<<dim3(nb, nb, 1), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, const float *f, const MgGeom &g,
+                              const float *phi_c, const MgGeom &gc, int tile, int nu, cudaStream_t s)
+{
+    const int nb = (g.N + tile - 1) / tile;
+    const size_t smem = mg_tb_smem(dim, true, tile, 2 * nu);
+    if (dim == 3)
+        k_tb_post<float, 3><<<dim3(nb, nb, nb), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, gc, tile, nu);
+    else
+        k_tb_post<float, 2><<<dim3(nb, nb, 1), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, gc, tile, nu);
     return cudaGetLastError();
 }
 
@@ -991,5 +1522,105 @@ cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s)
     const size_t n16 = bytes / 16;
     if (n16)
         k_zero<<<grid_for((long)n16), kThreads, 0, s>>>((uint4 *)p, n16);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched launchers
+// ---------------------------------------------------------------------------
+cudaError_t mg_batch_prepare()
+{
+    const int lim = MG_TB_SMEM_MAX;
+    cudaError_t e = cudaFuncSetAttribute(kb_tb_pre<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(kb_tb_post<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(kb_tb_pre<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(kb_tb_post<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (!e)
+        e = cudaFuncSetAttribute(kb_bottom<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MG_BOTTOM_SMEM_MAX);
+    if (!e)
+        e = cudaFuncSetAttribute(kb_bottom<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MG_BOTTOM_SMEM_MAX);
+    return e;
+}
+
+cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,
+                               int depth, int nu, size_t smem, cudaStream_t s)
+{
+    if (ntasks <= 0)
+        return cudaSuccess;
+    if (dim == 3)
+        kb_tb_pre<3><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+    else
+        kb_tb_pre<2><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,
+                                int depth, int nu, size_t smem, cudaStream_t s)
+{
+    if (ntasks <= 0)
+        return cudaSuccess;
+    if (dim == 3)
+        kb_tb_post<3><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+    else
+        kb_tb_post<2><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_bottom(int dim, const MgBPart *parts, int nparts, const int *active, int nu_pre, int nu_post,
+                               size_t smem, cudaStream_t s)
+{
+    if (dim == 3)
+        kb_bottom<3><<<nparts, kBottomThreads, smem, s>>>(parts, active, nu_pre, nu_post);
+    else
+        kb_bottom<2><<<nparts, kBottomThreads, smem, s>>>(parts, active, nu_pre, nu_post);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_defect(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                               cudaStream_t s)
+{
+    if (dim == 3)
+        kb_defect<3><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+    else
+        kb_defect<2><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_accumulate(int dim, const MgBPart *parts, const MgBCell *cells, int ncells,
+                                   const int *active, cudaStream_t s)
+{
+    if (dim == 3)
+        kb_accumulate<3><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+    else
+        kb_accumulate<2><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_norms2(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                               int which, cudaStream_t s)
+{
+    if (dim == 3)
+        kb_norms2<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, which);
+    else
+        kb_norms2<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, which);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_interface(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, cudaStream_t s)
+{
+    if (dim == 3)
+        kb_interface<3><<<ncells, kThreads, 0, s>>>(parts, cells);
+    else
+        kb_interface<2><<<ncells, kThreads, 0, s>>>(parts, cells);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_ctl(const MgBPart *parts, int nparts, int *active, int init, int inc, double tol,
+                            int max_cycles, cudaGraphConditionalHandle hc, cudaStream_t s)
+{
+    kb_ctl<<<1, 1024, 0, s>>>(parts, nparts, active, init, inc, tol, max_cycles, hc);
     return cudaGetLastError();
 }

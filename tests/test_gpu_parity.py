@@ -321,3 +321,60 @@ def test_heterogeneous_batch(mg):
                 assert np.array_equal(phi.cpu().numpy(), alone[l]["phi"])
     finally:
         mg.mg_destroy(h)
+
+
+@pytest.mark.parametrize("n,levels,dim", [(64, 4, 3), (30, 3, 3), (64, 3, 2)])
+def test_mixed_temporal_blocking_matches_one_kernel_per_phase(mg, n, levels, dim, monkeypatch):
+    """The temporally blocked FP32 legs (tile + halo in shared memory) repeat
+    the one-kernel-per-phase arithmetic; only FMA contraction may differ."""
+    H = I.config_3d_offset_sphere(n, levels) if dim == 3 else I.config_2d_disk(n, levels)
+    inp = I.level_inputs(H)
+    res = {}
+    for tile in ("0", None):
+        if tile is None:
+            monkeypatch.delenv("MG_TB_TILE", raising=False)
+        else:
+            monkeypatch.setenv("MG_TB_TILE", tile)
+        _, res[tile] = gpu_solve(mg, H, inp, nu_pre=2, nu_post=2, precision=mg.MG_MIXED, allow_noconv=False)
+    for l in range(H.num_levels):
+        a, b = res["0"][l], res[None][l]
+        assert abs(a["cycles"] - b["cycles"]) <= 3
+        assert relmax(b["phi"], a["phi"]) < 1e-8 and relmax(b["F"], a["F"]) < 1e-7
+
+
+def test_batched_mixed_equals_per_hierarchy_branches(mg, monkeypatch):
+    """The batched mixed-precision solve (one launch per phase over every
+    hierarchy of the batch, converged ones masked) gives the results of the
+    per-hierarchy solve graph."""
+    import torch
+    Hs = [I.random_hierarchy(s) for s in range(12)]
+    Hs = [H for H in Hs if max(H.n) <= 96][:5]
+    res = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("MG_BATCHED", mode)
+        h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], mg.options(precision=mg.MG_MIXED, nu_pre=2,
+                                                                             nu_post=2))
+        try:
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            for b, H in enumerate(Hs):
+                inp = I.level_inputs(H)
+                mg.mg_set_density(h, b, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+                for l in range(1, H.num_levels):
+                    mg.mg_set_density(h, b, l, dev(inp[l]["rho"]))
+            _, st = mg.mg_solve(h, len(Hs))
+            out = []
+            for b, H in enumerate(Hs):
+                lev = []
+                for l in range(H.num_levels):
+                    phi = torch.zeros((H.n[l],) * 3, dtype=torch.float64, device="cuda")
+                    mg.mg_forces(h, b, l, phi, None)
+                    torch.cuda.synchronize()
+                    lev.append((phi.cpu().numpy(), st[b][l]["cycles"], st[b][l]["rel_res"]))
+                out.append(lev)
+            res[mode] = out
+        finally:
+            mg.mg_destroy(h)
+    for a_h, b_h in zip(res["0"], res["1"]):
+        for (pa, ca, ra), (pb, cb, rb) in zip(a_h, b_h):
+            assert ca == cb and rb < 1e-10
+            assert relmax(pb, pa) < 1e-10
