@@ -401,6 +401,53 @@ def run_level_case(args):
         mg.mg_destroy(h)
 
 
+def run_batch_case(args):
+    """Uneven batch: `--batch` seeded hierarchies (2-4 levels, edges from
+    {32,48,64,96,128}, 1-4 compact spheres each), mixed precision, V(2,2) to
+    1e-10, solved together in one graph launch.  Prints one line of timing
+    (zones/s over all hierarchies), not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    Hs = [I.random_hierarchy(I.BASE_SEED + b) for b in range(args.batch)]
+    zones = sum(H.zones() for H in Hs)
+    opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED, inner_cycles=3)
+    h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], opt)
+    try:
+        if args.autotune:
+            mg.mg_autotune(h, None)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        ins = []
+        for H in Hs:
+            inp = I.level_inputs(H)
+            ins.append([{k: dev(v) for k, v in d.items()} for d in inp])
+
+        def step():
+            for b, H in enumerate(Hs):
+                d = ins[b]
+                mg.mg_set_density(h, b, 0, d[0]["rho"], d[0]["bc_rho"], d[0]["bc_phi"])
+                for l in range(1, H.num_levels):
+                    mg.mg_set_density(h, b, l, d[l]["rho"])
+            return mg.mg_solve(h, len(Hs))[1]
+
+        for _ in range(args.warmup):
+            st = step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        worst = max(st[b][l]["rel_res"] for b, H in enumerate(Hs) for l in range(H.num_levels))
+        cyc = sum(st[b][l]["cycles"] for b, H in enumerate(Hs) for l in range(H.num_levels))
+        print(json.dumps({"case": f"batch of {len(Hs)} uneven hierarchies", "zones": zones, "ms_per_solve": dt * 1e3,
+                          "zones_per_s": zones / dt, "worst_rel_res": worst, "fp32_cycles_total": cyc,
+                          "autotune": bool(args.autotune)}))
+    finally:
+        mg.mg_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,8 +455,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "level"],
-                    help="level: one DRAM-resident 3D level for profiler captures")
+    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch"],
+                    help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--level-n", type=int, default=254)
     ap.add_argument("--cycles", type=int, default=2)
@@ -417,6 +466,8 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.case == "level":
         run_level_case(args)
+    elif args.case == "batch":
+        run_batch_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

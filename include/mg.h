@@ -177,6 +177,24 @@ mg_status mg_profile(mg_hierarchy *h, int enable);
 /* Fills up to cap entries; returns how many kernel kinds ran, or -1. */
 int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap);
 
+/* Autotuner of the mixed-precision V-cycle (not part of the method; it picks
+ * among equivalent launch plans).  For each distinct level size it times, on
+ * the level's own FP32 correction arrays, (1) the size limit of the one-block
+ * kernel for the coarse multigrid levels (4, 8 or 17 cells per edge) and
+ * (2) for every multigrid level above it, the temporal-blocking tile of its
+ * pre-/post-smoothing kernels (8, 12, 16, or 0 = one kernel per phase).
+ * Every choice computes the same result.  cache_path (may be NULL) is a text
+ * file of earlier choices keyed by (dim, n, nu_pre, nu_post); new choices are
+ * appended.  No-op for MG_FP64.  Call after mg_create_hierarchy, before
+ * mg_solve.  Errors: MG_EINVAL, MG_ESTATE, MG_ECUDA. */
+mg_status mg_autotune(mg_hierarchy *h, const char *cache_path);
+
+/* The current FP32 plan of hierarchy b's level: writes the tile of each
+ * multigrid level (0 = one kernel per phase) into tiles[0..cap) and returns
+ * the edge of the first level run by the one-block kernel (-1 on bad
+ * arguments). */
+int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap);
+
 /* Allocation-free solve of one refinement level, for callers that cannot
  * allocate device memory: codes that give all of the GPU's memory to their
  * own pool, or call the Poisson solve inside a time step where cudaMalloc and

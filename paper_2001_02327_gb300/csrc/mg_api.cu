@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -69,11 +70,11 @@ void plan_tiles(LevelData &ld, int dim, int nu_pre, int nu_post)
     }
 }
 
-void plan_bottom(LevelData &ld, int dim)
+void plan_bottom(LevelData &ld, int dim, int lim32 = -1)
 {
     for (int w = 0; w < 2; w++) {
         const bool fp32 = w == 1;
-        const int lim = bottom_limit(fp32);
+        const int lim = (fp32 && lim32 >= 0) ? lim32 : bottom_limit(fp32);
         int Ls = ld.nmg - 1;
         for (int L = 0; L < ld.nmg; L++) {
             if (ld.g[L].N > lim || ld.nmg - L > MG_BOTTOM_MAX)
@@ -912,6 +913,156 @@ mg_status solve_graph(mg_hierarchy *h, mg_level_stats *stats)
     return worst;
 }
 
+// --------------------------------------------------------------------------
+// Autotuner of the FP32 V-cycle: per distinct level size, the temporal-
+// blocking tile of every multigrid level above the one-block kernel and the
+// one-block kernel's size limit.  Timing runs on the level's own FP32
+// correction arrays (scratch: rewritten by the next defect), so tuning does
+// not disturb a solve.
+// --------------------------------------------------------------------------
+struct TuneEntry {
+    int dim, n, nu_pre, nu_post, bottom_n;
+    int tile[MG_MAX_MG];
+};
+
+float time_ms(mg_hierarchy *h, int reps, const std::function<cudaError_t()> &fn, cudaError_t &err)
+{
+    cudaEvent_t a, b;
+    err = cudaEventCreate(&a);
+    if (!err)
+        err = cudaEventCreate(&b);
+    if (err)
+        return 0.f;
+    err = fn();                                   // warm-up
+    if (!err)
+        err = cudaEventRecord(a, h->stream);
+    for (int r = 0; r < reps && !err; r++)
+        err = fn();
+    if (!err)
+        err = cudaEventRecord(b, h->stream);
+    if (!err)
+        err = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (!err)
+        err = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms / reps;
+}
+
+bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
+{
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    cudaStream_t s = h->stream;
+    te.dim = dim;
+    te.n = ld.n;
+    te.nu_pre = o.nu_pre;
+    te.nu_post = o.nu_post;
+    // 1. the bottom limit, with the default tiles
+    const int nbs[3] = {4, 8, 17};
+    float best = 1e30f;
+    int bestnb = 8;
+    for (int nb : nbs) {
+        plan_bottom(ld, dim, nb);
+        plan_tiles(ld, dim, o.nu_pre, o.nu_post);
+        const float ms = time_ms(h, 5, [&] { return vcycle(h, ld, true, s); }, err);
+        if (err)
+            return false;
+        if (ms < best) {
+            best = ms;
+            bestnb = nb;
+        }
+    }
+    plan_bottom(ld, dim, bestnb);
+    te.bottom_n = bestnb;
+    // 2. per level above the bottom: the tile of its pre/post pair
+    const int Ls = ld.Ls[1];
+    for (int L = 0; L < MG_MAX_MG; L++)
+        te.tile[L] = 0;
+    const int cands[4] = {0, 8, 12, 16};
+    for (int L = 0; L < Ls; L++) {
+        float bl = 1e30f;
+        int bt = 0;
+        for (int t : cands) {
+            if (t && (mg_tb_smem(dim, true, t, 2 * o.nu_pre + 1) > MG_TB_SMEM_MAX ||
+                      mg_tb_smem(dim, true, t, 2 * o.nu_post) > MG_TB_SMEM_MAX))
+                continue;
+            ld.tile[L] = t;
+            const float ms = time_ms(h, 5, [&] {
+                cudaError_t e;
+                if (t) {
+                    e = mg_launch_tb_pre(dim, ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
+                                         ld.f32[L + 1], ld.g[L + 1], t, o.nu_pre, s);
+                    if (!e)
+                        e = mg_launch_tb_post(dim, ld.phi32b[L], ld.phi32[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
+                                              ld.g[L + 1], t, o.nu_post, s);
+                    return e;
+                }
+                for (int sw = 0; sw < o.nu_pre; sw++)
+                    for (int c = 0; c < 2; c++)
+                        if ((e = mg_launch_smooth(dim, true, ld.phi32[L], ld.f32[L], ld.g[L], c, s)))
+                            return e;
+                if ((e = mg_launch_resid_restrict(dim, true, ld.phi32[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
+                                                  ld.f32[L + 1], ld.g[L + 1], s)))
+                    return e;
+                if ((e = mg_launch_prolong(dim, true, ld.phi32[L + 1], ld.g[L + 1], ld.phi32[L], ld.g[L], s)))
+                    return e;
+                for (int sw = 0; sw < o.nu_post; sw++)
+                    for (int c = 0; c < 2; c++)
+                        if ((e = mg_launch_smooth(dim, true, ld.phi32[L], ld.f32[L], ld.g[L], c, s)))
+                            return e;
+                return cudaSuccess;
+            }, err);
+            if (err)
+                return false;
+            if (ms < bl) {
+                bl = ms;
+                bt = t;
+            }
+        }
+        ld.tile[L] = bt;
+        te.tile[L] = bt;
+    }
+    for (int L = Ls; L < ld.nmg; L++)
+        ld.tile[L] = 0;
+    return true;
+}
+
+void apply_entry(mg_hierarchy *h, LevelData &ld, const TuneEntry &te)
+{
+    plan_bottom(ld, h->dim, te.bottom_n);
+    for (int L = 0; L < ld.nmg; L++)
+        ld.tile[L] = L < ld.Ls[1] ? te.tile[L] : 0;
+}
+
+std::vector<TuneEntry> read_cache(const char *path)
+{
+    std::vector<TuneEntry> v;
+    if (!path)
+        return v;
+    FILE *fp = std::fopen(path, "r");
+    if (!fp)
+        return v;
+    char line[512];
+    while (std::fgets(line, sizeof line, fp)) {
+        TuneEntry te{};
+        int pos = 0;
+        if (line[0] == '#' || std::sscanf(line, "%d %d %d %d %d%n", &te.dim, &te.n, &te.nu_pre, &te.nu_post,
+                                          &te.bottom_n, &pos) != 5)
+            continue;
+        for (int L = 0; L < MG_MAX_MG; L++) {
+            int used = 0;
+            if (std::sscanf(line + pos, "%d%n", &te.tile[L], &used) != 1)
+                break;
+            pos += used;
+        }
+        v.push_back(te);
+    }
+    std::fclose(fp);
+    return v;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1286,6 +1437,60 @@ int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap)
         k++;
     }
     return k;
+}
+
+mg_status mg_autotune(mg_hierarchy *h, const char *cache_path)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (h->opt.precision != MG_MIXED)
+        return MG_OK;                 // the FP64 path has nothing to tune
+    std::vector<TuneEntry> cache = read_cache(cache_path);
+    std::vector<TuneEntry> fresh;
+    for (int b = 0; b < h->batch; b++)
+        for (auto &ld : h->lev[b]) {
+            const TuneEntry *hit = nullptr;
+            for (auto *v : {&cache, &fresh})
+                for (auto &te : *v)
+                    if (te.dim == h->dim && te.n == ld.n && te.nu_pre == h->opt.nu_pre &&
+                        te.nu_post == h->opt.nu_post)
+                        hit = &te;
+            if (hit) {
+                apply_entry(h, ld, *hit);
+                continue;
+            }
+            TuneEntry te{};
+            cudaError_t e = cudaSuccess;
+            if (!tune_level(h, ld, te, e))
+                return fail_cuda(h, e, "autotune timing");
+            fresh.push_back(te);
+        }
+    if (cache_path && !fresh.empty()) {
+        FILE *fp = std::fopen(cache_path, "a");
+        if (fp) {
+            for (auto &te : fresh) {
+                std::fprintf(fp, "%d %d %d %d %d", te.dim, te.n, te.nu_pre, te.nu_post, te.bottom_n);
+                for (int L = 0; L < MG_MAX_MG; L++)
+                    std::fprintf(fp, " %d", te.tile[L]);
+                std::fprintf(fp, "\n");
+            }
+            std::fclose(fp);
+        }
+    }
+    destroy_graph(h);                 // the solve graph is rebuilt with the new plan
+    return MG_OK;
+}
+
+int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap)
+{
+    if (!h || b < 0 || b >= h->batch || level < 0 || level >= h->desc[b].num_levels || !tiles)
+        return -1;
+    const LevelData &ld = h->lev[b][level];
+    for (int L = 0; L < cap && L < ld.nmg; L++)
+        tiles[L] = ld.tile[L];
+    return ld.g[ld.Ls[1]].N;
 }
 
 mg_status mg_destroy(mg_hierarchy *h)

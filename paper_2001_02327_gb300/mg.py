@@ -55,6 +55,8 @@ _SIGS = {
     "mg_error_message": (C.c_char_p, [_vp]),
     "mg_level_sizes": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int]),
     "mg_profile": (C.c_int, [_vp, C.c_int]),
+    "mg_autotune": (C.c_int, [_vp, C.c_char_p]),
+    "mg_tuning": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "mg_solve_level_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
                                          C.POINTER(mg_options), C.POINTER(mg_level_stats)]),
     "mg_profile_read": (C.c_int, [_vp, C.POINTER(mg_kernel_stat), C.c_int]),
@@ -180,6 +182,17 @@ def mg_solve_level_noalloc(dim, n, h, G, rho, phi, opt=None):
     s = LIB.mg_solve_level_noalloc(dim, n, h, G, _addr(rho), _addr(phi),
                                    C.byref(opt) if opt is not None else None, C.byref(st))
     return s, {"cycles": st.cycles, "rel_res": st.rel_res, "b_norm": st.b_norm, "status": st.status}
+
+
+def mg_autotune(h, cache_path=None):
+    return _check(h, LIB.mg_autotune(h, cache_path.encode() if cache_path else None))
+
+
+def mg_tuning(h, b, level):
+    """(tiles per multigrid level, edge of the first one-block level)."""
+    buf = (C.c_int * 16)()
+    nb = LIB.mg_tuning(h, b, level, buf, 16)
+    return [buf[i] for i in range(16)], nb
 
 
 def mg_destroy(h):

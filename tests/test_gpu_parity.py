@@ -378,3 +378,33 @@ def test_batched_mixed_equals_per_hierarchy_branches(mg, monkeypatch):
         for (pa, ca, ra), (pb, cb, rb) in zip(a_h, b_h):
             assert ca == cb and rb < 1e-10
             assert relmax(pb, pa) < 1e-10
+
+
+def test_autotune_keeps_results_and_caches(mg, tmp_path):
+    """Autotuning only changes the launch plan: the mixed solve gives the
+    same results; a second hierarchy takes the plan from the cache."""
+    import torch
+    H = I.config_3d_offset_sphere(64, 2)
+    inp = I.level_inputs(H)
+    _, plain = gpu_solve(mg, H, inp, nu_pre=2, nu_post=2, precision=mg.MG_MIXED, allow_noconv=False)
+    cache = str(tmp_path / "tune.txt")
+    plans = []
+    for rep in range(2):
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=2, nu_post=2, precision=mg.MG_MIXED))
+        try:
+            mg.mg_autotune(h, cache)
+            plans.append(mg.mg_tuning(h, 0, 0))
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            mg.mg_set_density(h, 0, 1, dev(inp[1]["rho"]))
+            _, st = mg.mg_solve(h, 1)
+            for l in range(H.num_levels):
+                phi = torch.zeros((64,) * 3, dtype=torch.float64, device="cuda")
+                mg.mg_forces(h, 0, l, phi, None)
+                torch.cuda.synchronize()
+                assert st[0][l]["rel_res"] < 1e-10
+                assert relmax(phi.cpu().numpy(), plain[l]["phi"]) < 1e-8
+        finally:
+            mg.mg_destroy(h)
+    assert plans[0] == plans[1]
+    assert len(open(cache).read().strip().splitlines()) == 1
