@@ -648,7 +648,7 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
             P.scal = level_scal(h, b, l);
             P.ctl = level_ctl(h, b, l);
             const long act = (long)std::pow((double)ld.g[0].N, dim), blk = cells(ld.n + 4, dim);
-            P.nblk_act = (int)std::min<long>((act + 255) / 256, MG_NORM_BLOCKS_MAX);
+            P.nblk_act = (int)std::max<long>(1, std::min<long>((act + 1023) / 1024, MG_NORM_BLOCKS_MAX));
             P.nblk_blk = (int)std::min<long>((blk + 255) / 256, 4096);
             P.bt = ld.bt[1];
             P.n = ld.n;

@@ -9,6 +9,8 @@
 // divisions (host tables of the boundary diagonals), neighbour folding by
 // selects rather than multiplies, separable interpolation.  Index arithmetic
 // is 32-bit.
+#include <algorithm>
+
 #include "mg_internal.h"
 
 namespace {
@@ -492,7 +494,11 @@ __device__ __forceinline__ int box_index(const TbBox &b, int i, int j, int k)
 }
 
 // Load the Phi box (cells outside the level's storage read as zero) and f
-// (active cells only) of a tile whose origin is o and halo H.
+// (active cells only) of a tile.  Each thread keeps kLoadBatch loads in
+// flight: the box comes from L2/HBM and one load at a time would leave the
+// kernel bound by memory latency.
+constexpr int kLoadBatch = 8;
+
 template <typename T, int DIM>
 __device__ __forceinline__ void tb_load(const T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g,
                                         const TbBox &b, T *sPhi, T *sF)
@@ -500,17 +506,37 @@ __device__ __forceinline__ void tb_load(const T *__restrict__ phi, const T *__re
     const int N = g.N;
     const int P = b.P;
     const int nP = P * P * (DIM == 3 ? P : 1);
-    for (int t = threadIdx.x; t < nP; t += blockDim.x) {
-        const int r = t / P;
-        const int a0 = t - r * P;
-        const int a1 = DIM == 3 ? r % P : r;
-        const int a2 = DIM == 3 ? r / P : 0;
-        const int i = b.b0[0] + a0, j = b.b0[1] + a1, k = DIM == 3 ? b.b0[2] + a2 : 0;
-        const bool in = i >= 0 && i <= N + 1 && j >= 0 && j <= N + 1 && (DIM == 2 || (k >= 0 && k <= N + 1));
-        const bool act = i >= 1 && i <= N && j >= 1 && j <= N && (DIM == 2 || (k >= 1 && k <= N));
-        const int gq = in ? lin<DIM>(i, j, k, g.E) : 0;
-        sPhi[t] = in ? phi[gq] : T(0);
-        sF[t] = act ? f[gq] : T(0);
+    const int step = blockDim.x * kLoadBatch;
+    for (int t0 = threadIdx.x; t0 < nP; t0 += step) {
+        T vp[kLoadBatch], vf[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; u++) {
+            const int t = t0 + u * blockDim.x;
+            vp[u] = T(0);
+            vf[u] = T(0);
+            if (t < nP) {
+                const int r = t / P;
+                const int a0 = t - r * P;
+                const int a1 = DIM == 3 ? r % P : r;
+                const int a2 = DIM == 3 ? r / P : 0;
+                const int i = b.b0[0] + a0, j = b.b0[1] + a1, k = DIM == 3 ? b.b0[2] + a2 : 0;
+                const bool in = i >= 0 && i <= N + 1 && j >= 0 && j <= N + 1 && (DIM == 2 || (k >= 0 && k <= N + 1));
+                const bool act = i >= 1 && i <= N && j >= 1 && j <= N && (DIM == 2 || (k >= 1 && k <= N));
+                const int gq = in ? lin<DIM>(i, j, k, g.E) : 0;
+                if (in)
+                    vp[u] = phi[gq];
+                if (act)
+                    vf[u] = f[gq];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; u++) {
+            const int t = t0 + u * blockDim.x;
+            if (t < nP) {
+                sPhi[t] = vp[u];
+                sF[t] = vf[u];
+            }
+        }
     }
 }
 
@@ -537,6 +563,43 @@ __device__ __forceinline__ void tb_sweeps(T *sPhi, const T *sF, const MgGeom &g,
         });
         __syncthreads();
     }
+}
+
+// P(Phi_c) at fine cell f with the coarse values read from a shared-memory box
+template <typename T, int DIM>
+__device__ __forceinline__ T prolong_value_box(const T *sC, const TbBox &cb, const MgGeom &gc, const int *f)
+{
+    int idx[3][2];
+    T w[3][2];
+    for (int a = 0; a < DIM; a++) {
+        const int near = (f[a] + 1) >> 1;
+        const int far = (f[a] & 1) ? near - 1 : near + 1;
+        T c0, c1;
+        ghost_map<T>(near, gc, idx[a][0], c0);
+        ghost_map<T>(far, gc, idx[a][1], c1);
+        w[a][0] = T(0.75) * c0;
+        w[a][1] = T(0.25) * c1;
+    }
+    if (DIM == 3) {
+        T zsum = T(0);
+        for (int c = 0; c < 2; c++) {
+            T ysum = T(0);
+            for (int b = 0; b < 2; b++) {
+                const int row = ((idx[2][c] - cb.b0[2]) * cb.P + (idx[1][b] - cb.b0[1])) * cb.P - cb.b0[0];
+                const T xv = w[0][0] * sC[row + idx[0][0]] + w[0][1] * sC[row + idx[0][1]];
+                ysum += w[1][b] * xv;
+            }
+            zsum += w[2][c] * ysum;
+        }
+        return zsum;
+    }
+    T ysum = T(0);
+    for (int b = 0; b < 2; b++) {
+        const int row = (idx[1][b] - cb.b0[1]) * cb.P - cb.b0[0];
+        const T xv = w[0][0] * sC[row + idx[0][0]] + w[0][1] * sC[row + idx[0][1]];
+        ysum += w[1][b] * xv;
+    }
+    return ysum;
 }
 
 template <typename T, int DIM>
@@ -632,7 +695,8 @@ __device__ __forceinline__ void tb_post_body(const T *__restrict__ phi_in, T *__
     T *sF = sPhi + nP;
     tb_load<T, DIM>(phi_in, f, g, b, sPhi, sF);
     __syncthreads();
-    // correct every active cell of the box
+    // correct every active cell of the box from the coarse cells around it,
+    // staged in shared memory behind the fine box
     {
         int lo[3], hi[3];
         for (int a = 0; a < 3; a++) {
@@ -641,9 +705,46 @@ __device__ __forceinline__ void tb_post_body(const T *__restrict__ phi_in, T *__
         }
         if (DIM == 2)
             lo[2] = hi[2] = 0;
+        TbBox cb;
+        cb.P = 0;
+        int cl[3] = {0, 0, 0}, chh[3] = {0, 0, 0};
+        for (int a = 0; a < DIM; a++) {
+            cl[a] = max(((lo[a] + 1) >> 1) - 1, 0);
+            chh[a] = min(((hi[a] + 1) >> 1) + 1, gc.N + 1);
+            cb.b0[a] = cl[a];
+            cb.P = max(cb.P, chh[a] - cl[a] + 1);
+        }
+        if (DIM == 2)
+            cb.b0[2] = 0;
+        T *sC = sF + nP;
+        const int nC = cb.P * cb.P * (DIM == 3 ? cb.P : 1);
+        const int step = blockDim.x * kLoadBatch;
+        for (int t0 = threadIdx.x; t0 < nC; t0 += step) {
+            T v[kLoadBatch];
+#pragma unroll
+            for (int u = 0; u < kLoadBatch; u++) {
+                const int t = t0 + u * blockDim.x;
+                v[u] = T(0);
+                if (t < nC) {
+                    const int r = t / cb.P;
+                    const int i = cb.b0[0] + t - r * cb.P;
+                    const int j = cb.b0[1] + (DIM == 3 ? r % cb.P : r);
+                    const int k = DIM == 3 ? cb.b0[2] + r / cb.P : 0;
+                    if (i <= gc.N + 1 && j <= gc.N + 1 && (DIM == 2 || k <= gc.N + 1))
+                        v[u] = phi_c[lin<DIM>(i, j, k, gc.E)];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kLoadBatch; u++) {
+                const int t = t0 + u * blockDim.x;
+                if (t < nC)
+                    sC[t] = v[u];
+            }
+        }
+        __syncthreads();
         for_box_cells<DIM>(lo, hi, [&](int i, int j, int k) {
             const int fc[3] = {i, j, k};
-            sPhi[box_index<DIM>(b, i, j, k)] += prolong_value<T, DIM>(phi_c, gc, fc);
+            sPhi[box_index<DIM>(b, i, j, k)] += prolong_value_box<T, DIM>(sC, cb, gc, fc);
         });
     }
     __syncthreads();
@@ -743,8 +844,11 @@ __global__ void __launch_bounds__(kThreads) k_norms2(const double *__restrict__ 
     double b2 = 0.0, r2 = 0.0;
     for (int t = gtid(); t < total; t += gstride())
         norm_terms<DIM>(phi, f, g, t, which, b2, r2);
-    b2 = block_sum(b2, sm);
-    r2 = block_sum(r2, sm);
+    // FP64 reductions cost FP64-pipe time: reduce only what was asked for
+    if (which & 1)
+        b2 = block_sum(b2, sm);
+    if (which & 2)
+        r2 = block_sum(r2, sm);
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = b2;
         partials[2 * blockIdx.x + 1] = r2;
@@ -760,8 +864,10 @@ __global__ void __launch_bounds__(kThreads) k_norms2(const double *__restrict__ 
         sb += partials[2 * t];
         sr += partials[2 * t + 1];
     }
-    sb = block_sum(sb, sm);
-    sr = block_sum(sr, sm);
+    if (which & 1)
+        sb = block_sum(sb, sm);
+    if (which & 2)
+        sr = block_sum(sr, sm);
     if (threadIdx.x == 0) {
         if (which & 1)
             out2[0] = sb;
@@ -1153,8 +1259,10 @@ __global__ void __launch_bounds__(kThreads) kb_norms2(const MgBPart *__restrict_
     double b2 = 0.0, r2 = 0.0;
     for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_act * kThreads)
         norm_terms<DIM>(P.phi, P.f, g, t, which, b2, r2);
-    b2 = block_sum(b2, sm);
-    r2 = block_sum(r2, sm);
+    if (which & 1)
+        b2 = block_sum(b2, sm);
+    if (which & 2)
+        r2 = block_sum(r2, sm);
     if (threadIdx.x == 0) {
         P.partials[2 * c.chunk] = b2;
         P.partials[2 * c.chunk + 1] = r2;
@@ -1170,8 +1278,10 @@ __global__ void __launch_bounds__(kThreads) kb_norms2(const MgBPart *__restrict_
         sb += P.partials[2 * t];
         sr += P.partials[2 * t + 1];
     }
-    sb = block_sum(sb, sm);
-    sr = block_sum(sr, sm);
+    if (which & 1)
+        sb = block_sum(sb, sm);
+    if (which & 2)
+        sr = block_sum(sr, sm);
     if (threadIdx.x == 0) {
         if (which & 1)
             P.scal[0] = sb;
@@ -1331,7 +1441,8 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
 size_t mg_tb_smem(int dim, bool fp32, int tile, int halo)
 {
     const size_t P = tile + 2 * halo;
-    return 2 * (dim == 3 ? P * P * P : P * P) * (fp32 ? 4 : 8);
+    const size_t C = P / 2 + 3;   // coarse box of the post leg
+    return (2 * (dim == 3 ? P * P * P : P * P) + (dim == 3 ? C * C * C : C * C)) * (fp32 ? 4 : 8);
 }
 
 cudaError_t mg_tb_prepare()
@@ -1416,7 +1527,8 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
 cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const MgGeom &g, int which,
                              double *partials, unsigned *counter, double *out2, cudaStream_t s)
 {
-    const int grid = grid_for(cube(g.N, dim), MG_NORM_BLOCKS_MAX);
+    // about four cells per thread: fewer block reductions on the FP64 pipe
+    const int grid = std::max(1, std::min<int>((int)((cube(g.N, dim) + 4 * kThreads - 1) / (4 * kThreads)), MG_NORM_BLOCKS_MAX));
     if (dim == 3)
         k_norms2<3><<<grid, kThreads, 0, s>>>(phi, f, g, which, partials, counter, out2);
     else
