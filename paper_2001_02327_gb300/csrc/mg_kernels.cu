@@ -36,6 +36,40 @@ __device__ __forceinline__ int lin(int i, int j, int k, int E)
     return DIM == 3 ? (k * E + j) * E + i : j * E + i;
 }
 
+// Walk t = t0, t0 + S, t0 + 2S, ... over an nx * ny * nz box (x fastest) with
+// the coordinates advanced incrementally: the divisions happen once, not per
+// cell (integer division is tens of instructions).
+struct Walk3 {
+    int x, y, z, dx, dy, dz, nx, ny;
+    __device__ __forceinline__ Walk3(int t0, int S, int nx_, int ny_) : nx(nx_), ny(ny_)
+    {
+        const int r = t0 / nx;
+        x = t0 - r * nx;
+        y = r % ny;
+        z = r / ny;
+        const int q = S / nx;
+        dx = S - q * nx;
+        dy = q % ny;
+        dz = q / ny;
+    }
+    __device__ __forceinline__ void next()
+    {
+        x += dx;
+        int c = 0;
+        if (x >= nx) {
+            x -= nx;
+            c = 1;
+        }
+        y += dy + c;
+        c = 0;
+        if (y >= ny) {
+            y -= ny;
+            c = 1;
+        }
+        z += dz + c;
+    }
+};
+
 // level constants in the working precision
 template <typename T>
 __device__ __forceinline__ T geo_h2(const MgGeom &g);
@@ -143,19 +177,11 @@ __device__ __forceinline__ void op_smooth_colour(T *__restrict__ phi, const T *_
     const int half = (N + 1) >> 1;
     const int total = half * N * (DIM == 3 ? N : 1);
     const T h2 = geo_h2<T>(g);
-    for (int t = t0; t < total; t += stride) {
-        const int r = t / half;
-        const int i2 = t - r * half;
-        int j, k;
-        if (DIM == 3) {
-            k = r / N;
-            j = r - k * N + 1;
-            k += 1;
-        } else {
-            j = r + 1;
-            k = 0;
-        }
-        const int i = ((((1 + j + k) & 1) == colour) ? 1 : 2) + 2 * i2;
+    Walk3 w(t0, stride, half, DIM == 3 ? N : total);
+    for (int t = t0; t < total; t += stride, w.next()) {
+        const int j = w.y + 1;
+        const int k = DIM == 3 ? w.z + 1 : 0;
+        const int i = ((((1 + j + k) & 1) == colour) ? 1 : 2) + 2 * w.x;
         if (i > N)
             continue;
         const int p = lin<DIM>(i, j, k, g.E);
@@ -187,18 +213,9 @@ __device__ __forceinline__ void op_resid_restrict(const T *__restrict__ phi_f, c
     const int Nc = gc.N, Nf = gf.N;
     const int total = Nc * Nc * (DIM == 3 ? Nc : 1);
     const T w = DIM == 3 ? T(0.125) : T(0.25);
-    for (int t = t0; t < total; t += stride) {
-        const int r = t / Nc;
-        const int I = t - r * Nc + 1;
-        int J, K;
-        if (DIM == 3) {
-            K = r / Nc;
-            J = r - K * Nc + 1;
-            K += 1;
-        } else {
-            J = r + 1;
-            K = 0;
-        }
+    Walk3 wk(t0, stride, Nc, DIM == 3 ? Nc : total);
+    for (int t = t0; t < total; t += stride, wk.next()) {
+        const int I = wk.x + 1, J = wk.y + 1, K = DIM == 3 ? wk.z + 1 : 0;
         T s = T(0);
         for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++) {
             const int k = DIM == 3 ? 2 * K - 1 + dk : 0;
@@ -297,18 +314,9 @@ __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const Mg
 {
     const int Nf = gf.N;
     const int total = Nf * Nf * (DIM == 3 ? Nf : 1);
-    for (int t = t0; t < total; t += stride) {
-        int f[3];
-        const int r = t / Nf;
-        f[0] = t - r * Nf + 1;
-        if (DIM == 3) {
-            const int k = r / Nf;
-            f[1] = r - k * Nf + 1;
-            f[2] = k + 1;
-        } else {
-            f[1] = r + 1;
-            f[2] = 0;
-        }
+    Walk3 wk(t0, stride, Nf, DIM == 3 ? Nf : total);
+    for (int t = t0; t < total; t += stride, wk.next()) {
+        const int f[3] = {wk.x + 1, wk.y + 1, DIM == 3 ? wk.z + 1 : 0};
         phi_f[lin<DIM>(f[0], f[1], f[2], gf.E)] += prolong_value<T, DIM>(phi_c, gc, f);
     }
 }
@@ -458,13 +466,12 @@ __device__ __forceinline__ void for_colour_cells(const int *lo, const int *hi, i
     const int W = hi[0] - lo[0] + 1, hw = (W + 1) >> 1;
     const int ny = hi[1] - lo[1] + 1, nz = DIM == 3 ? hi[2] - lo[2] + 1 : 1;
     const int total = hw * ny * nz;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int r = t / hw;
-        const int i2 = t - r * hw;
-        const int j = lo[1] + (DIM == 3 ? r % ny : r);
-        const int k = DIM == 3 ? lo[2] + r / ny : 0;
+    Walk3 w(threadIdx.x, blockDim.x, hw, ny);
+    for (int t = threadIdx.x; t < total; t += blockDim.x, w.next()) {
+        const int j = lo[1] + w.y;
+        const int k = DIM == 3 ? lo[2] + w.z : 0;
         const int i0 = lo[0] + (((lo[0] + j + k + colour) & 1) ? 1 : 0);
-        const int i = i0 + 2 * i2;
+        const int i = i0 + 2 * w.x;
         if (i <= hi[0])
             fn(i, j, k);
     }
@@ -478,13 +485,9 @@ __device__ __forceinline__ void for_box_cells(const int *lo, const int *hi, Fn &
         return;
     const int W = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = DIM == 3 ? hi[2] - lo[2] + 1 : 1;
     const int total = W * ny * nz;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int r = t / W;
-        const int i = lo[0] + t - r * W;
-        const int j = lo[1] + (DIM == 3 ? r % ny : r);
-        const int k = DIM == 3 ? lo[2] + r / ny : 0;
-        fn(i, j, k);
-    }
+    Walk3 w(threadIdx.x, blockDim.x, W, ny);
+    for (int t = threadIdx.x; t < total; t += blockDim.x, w.next())
+        fn(lo[0] + w.x, lo[1] + w.y, DIM == 3 ? lo[2] + w.z : 0);
 }
 
 template <int DIM>
@@ -507,6 +510,7 @@ __device__ __forceinline__ void tb_load(const T *__restrict__ phi, const T *__re
     const int P = b.P;
     const int nP = P * P * (DIM == 3 ? P : 1);
     const int step = blockDim.x * kLoadBatch;
+    Walk3 w(threadIdx.x, blockDim.x, P, DIM == 3 ? P : nP);
     for (int t0 = threadIdx.x; t0 < nP; t0 += step) {
         T vp[kLoadBatch], vf[kLoadBatch];
 #pragma unroll
@@ -515,11 +519,7 @@ __device__ __forceinline__ void tb_load(const T *__restrict__ phi, const T *__re
             vp[u] = T(0);
             vf[u] = T(0);
             if (t < nP) {
-                const int r = t / P;
-                const int a0 = t - r * P;
-                const int a1 = DIM == 3 ? r % P : r;
-                const int a2 = DIM == 3 ? r / P : 0;
-                const int i = b.b0[0] + a0, j = b.b0[1] + a1, k = DIM == 3 ? b.b0[2] + a2 : 0;
+                const int i = b.b0[0] + w.x, j = b.b0[1] + w.y, k = DIM == 3 ? b.b0[2] + w.z : 0;
                 const bool in = i >= 0 && i <= N + 1 && j >= 0 && j <= N + 1 && (DIM == 2 || (k >= 0 && k <= N + 1));
                 const bool act = i >= 1 && i <= N && j >= 1 && j <= N && (DIM == 2 || (k >= 1 && k <= N));
                 const int gq = in ? lin<DIM>(i, j, k, g.E) : 0;
@@ -528,6 +528,7 @@ __device__ __forceinline__ void tb_load(const T *__restrict__ phi, const T *__re
                 if (act)
                     vf[u] = f[gq];
             }
+            w.next();
         }
 #pragma unroll
         for (int u = 0; u < kLoadBatch; u++) {
@@ -719,6 +720,7 @@ __device__ __forceinline__ void tb_post_body(const T *__restrict__ phi_in, T *__
         T *sC = sF + nP;
         const int nC = cb.P * cb.P * (DIM == 3 ? cb.P : 1);
         const int step = blockDim.x * kLoadBatch;
+        Walk3 wc(threadIdx.x, blockDim.x, cb.P, DIM == 3 ? cb.P : nC);
         for (int t0 = threadIdx.x; t0 < nC; t0 += step) {
             T v[kLoadBatch];
 #pragma unroll
@@ -726,13 +728,11 @@ __device__ __forceinline__ void tb_post_body(const T *__restrict__ phi_in, T *__
                 const int t = t0 + u * blockDim.x;
                 v[u] = T(0);
                 if (t < nC) {
-                    const int r = t / cb.P;
-                    const int i = cb.b0[0] + t - r * cb.P;
-                    const int j = cb.b0[1] + (DIM == 3 ? r % cb.P : r);
-                    const int k = DIM == 3 ? cb.b0[2] + r / cb.P : 0;
+                    const int i = cb.b0[0] + wc.x, j = cb.b0[1] + wc.y, k = DIM == 3 ? cb.b0[2] + wc.z : 0;
                     if (i <= gc.N + 1 && j <= gc.N + 1 && (DIM == 2 || k <= gc.N + 1))
                         v[u] = phi_c[lin<DIM>(i, j, k, gc.E)];
                 }
+                wc.next();
             }
 #pragma unroll
             for (int u = 0; u < kLoadBatch; u++) {
