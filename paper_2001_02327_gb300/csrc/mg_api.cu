@@ -53,15 +53,18 @@ int bottom_limit(bool fp32)
     return 8;
 }
 
-// FP32 temporal-blocking tile of each level above the bottom kernel: 16 for
-// levels of 48 cells or more, 8 below (MG_TB_TILE overrides; 0 = one kernel
-// per phase).  Tiles must be even and fit the shared-memory limit.
+// FP32 temporal-blocking tile of each level above the bottom kernel.  The
+// default is 0 (one kernel per phase): on L2-resident levels the halo
+// recomputation of a blocked leg (about 4x the updates at tile 16 and halo 5)
+// costs more than the launches it saves; mg_autotune picks tiles where they
+// pay.  MG_TB_TILE forces one tile for every level.  Tiles are even and fit
+// the shared-memory limit.
 void plan_tiles(LevelData &ld, int dim, int nu_pre, int nu_post)
 {
     const char *v = std::getenv("MG_TB_TILE");
     const int forced = (v && *v) ? std::atoi(v) : -1;
     for (int L = 0; L < ld.nmg; L++) {
-        int t = forced >= 0 ? forced : (ld.g[L].N >= 48 ? 16 : 8);
+        int t = forced >= 0 ? forced : 0;
         t &= ~1;
         while (t > 0 && (mg_tb_smem(dim, true, t, 2 * nu_pre + 1) > MG_TB_SMEM_MAX ||
                          mg_tb_smem(dim, true, t, 2 * nu_post) > MG_TB_SMEM_MAX))
@@ -190,8 +193,11 @@ struct mg_hierarchy {
         int nparts = 0, maxLs = 0;
         MgBPart *parts = nullptr;
         int *active = nullptr;
-        std::vector<int> ntasks;              // per depth
-        std::vector<MgBTask *> tasks;         // per depth
+        std::vector<int> ntasks;              // per depth: blocked-leg tile tasks
+        std::vector<MgBTask *> tasks;
+        // per depth, one-kernel-per-phase chunk tasks of the parts without a tile
+        std::vector<int> n_sm, n_rr, n_pr;
+        std::vector<MgBCell *> t_sm, t_rr, t_pr;
         MgBCell *cells_act = nullptr, *cells_blk = nullptr;
         int ncells_act = 0, ncells_blk = 0;
         std::vector<size_t> smem_pre, smem_post;
@@ -616,6 +622,7 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
     struct HostLevel {
         std::vector<MgBPart> parts;
         std::vector<std::vector<MgBTask>> tasks;
+        std::vector<std::vector<MgBCell>> sm, rr, pr;
         std::vector<MgBCell> act, blk;
     };
     std::vector<HostLevel> HL(maxL);
@@ -639,9 +646,6 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
                 P.phi32b[L] = ld.phi32b[L];
                 P.f32[L] = ld.f32[L];
             }
-            for (int L = 0; L < P.Ls; L++)
-                if (!ld.tile[L])
-                    return false;
             P.phi = ld.phi[0];
             P.f = ld.f[0];
             P.rho = ld.rho;
@@ -666,14 +670,30 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
                 P.gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
             }
             const int p = (int)H.parts.size();
-            if ((int)H.tasks.size() < P.Ls)
+            if ((int)H.tasks.size() < P.Ls) {
                 H.tasks.resize(P.Ls);
+                H.sm.resize(P.Ls);
+                H.rr.resize(P.Ls);
+                H.pr.resize(P.Ls);
+            }
             for (int L = 0; L < P.Ls; L++) {
-                const int nb = (ld.g[L].N + ld.tile[L] - 1) / ld.tile[L];
-                for (int z = 0; z < (dim == 3 ? nb : 1); z++)
-                    for (int y = 0; y < nb; y++)
-                        for (int x = 0; x < nb; x++)
-                            H.tasks[L].push_back({p, x, y, z});
+                if (ld.tile[L]) {
+                    const int nb = (ld.g[L].N + ld.tile[L] - 1) / ld.tile[L];
+                    for (int z = 0; z < (dim == 3 ? nb : 1); z++)
+                        for (int y = 0; y < nb; y++)
+                            for (int x = 0; x < nb; x++)
+                                H.tasks[L].push_back({p, x, y, z});
+                    continue;
+                }
+                // one chunk of 256 threads per 256 cells of the level (same
+                // count for the colour, coarse and fine passes: grid-stride)
+                const long cl = (long)std::pow((double)ld.g[L].N, dim);
+                P.nblk_lvl[L] = (int)std::max<long>(1, std::min<long>((cl + 255) / 256, 152 * 16));
+                for (int c = 0; c < P.nblk_lvl[L]; c++) {
+                    H.sm[L].push_back({p, c});
+                    H.rr[L].push_back({p, c});
+                    H.pr[L].push_back({p, c});
+                }
             }
             for (int c = 0; c < P.nblk_act; c++)
                 H.act.push_back({p, c});
@@ -695,6 +715,9 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
         off_blk[l] = add(HL[l].blk.size() * sizeof(MgBCell));
         for (auto &t : HL[l].tasks)
             off_tasks[l].push_back(add(t.size() * sizeof(MgBTask)));
+        for (auto *v : {&HL[l].sm, &HL[l].rr, &HL[l].pr})
+            for (auto &t : *v)
+                off_tasks[l].push_back(add(t.size() * sizeof(MgBCell)));
     }
     const size_t off_partials = add(npart_total * 2 * MG_NORM_BLOCKS_MAX * sizeof(double));
     const size_t off_counters = add(npart_total * sizeof(unsigned));
@@ -737,17 +760,37 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
             }
         B.tasks.resize(H.tasks.size());
         B.ntasks.resize(H.tasks.size());
+        const size_t nd = H.tasks.size();
+        B.n_sm.assign(nd, 0);
+        B.n_rr.assign(nd, 0);
+        B.n_pr.assign(nd, 0);
+        B.t_sm.assign(nd, nullptr);
+        B.t_rr.assign(nd, nullptr);
+        B.t_pr.assign(nd, nullptr);
         e = cudaMemcpyAsync(B.parts, H.parts.data(), H.parts.size() * sizeof(MgBPart), cudaMemcpyHostToDevice, h->stream);
         if (!e)
             e = cudaMemcpyAsync(B.cells_act, H.act.data(), H.act.size() * sizeof(MgBCell), cudaMemcpyHostToDevice, h->stream);
         if (!e)
             e = cudaMemcpyAsync(B.cells_blk, H.blk.data(), H.blk.size() * sizeof(MgBCell), cudaMemcpyHostToDevice, h->stream);
-        for (size_t d = 0; d < H.tasks.size() && !e; d++) {
-            B.tasks[d] = (MgBTask *)(base + off_tasks[l][d]);
+        size_t oi = 0;
+        for (size_t d = 0; d < nd && !e; d++, oi++) {
+            B.tasks[d] = (MgBTask *)(base + off_tasks[l][oi]);
             B.ntasks[d] = (int)H.tasks[d].size();
-            e = cudaMemcpyAsync(B.tasks[d], H.tasks[d].data(), H.tasks[d].size() * sizeof(MgBTask),
-                                cudaMemcpyHostToDevice, h->stream);
+            if (!H.tasks[d].empty())
+                e = cudaMemcpyAsync(B.tasks[d], H.tasks[d].data(), H.tasks[d].size() * sizeof(MgBTask),
+                                    cudaMemcpyHostToDevice, h->stream);
         }
+        std::vector<MgBCell *> *dst[3] = {&B.t_sm, &B.t_rr, &B.t_pr};
+        std::vector<int> *cnt[3] = {&B.n_sm, &B.n_rr, &B.n_pr};
+        std::vector<std::vector<MgBCell>> *src[3] = {&H.sm, &H.rr, &H.pr};
+        for (int w = 0; w < 3 && !e; w++)
+            for (size_t d = 0; d < nd && !e; d++, oi++) {
+                (*dst[w])[d] = (MgBCell *)(base + off_tasks[l][oi]);
+                (*cnt[w])[d] = (int)(*src[w])[d].size();
+                if (!(*src[w])[d].empty())
+                    e = cudaMemcpyAsync((*dst[w])[d], (*src[w])[d].data(), (*src[w])[d].size() * sizeof(MgBCell),
+                                        cudaMemcpyHostToDevice, h->stream);
+            }
     }
     if (!e)
         e = cudaStreamSynchronize(h->stream);
@@ -804,13 +847,30 @@ cudaError_t capture_batched_level(mg_hierarchy *h, int l, cudaStream_t s, cudaSt
         return e;
     cudaError_t eb = mg_launch_b_defect(dim, B.parts, B.cells_act, B.ncells_act, B.active, body);
     for (int c = 0; c < o.inner_cycles && !eb; c++) {
-        for (int d = 0; d < B.maxLs && !eb; d++)
-            eb = mg_launch_b_tb_pre(dim, B.parts, B.tasks[d], B.ntasks[d], B.active, d, o.nu_pre, B.smem_pre[d], body);
+        for (int d = 0; d < B.maxLs && !eb; d++) {
+            // parts without a tile at this depth: sweeps, then residual + restriction
+            for (int sw = 0; sw < o.nu_pre && !eb; sw++)
+                for (int col = 0; col < 2 && !eb; col++)
+                    eb = mg_launch_b_smooth(dim, B.parts, B.t_sm[d], B.n_sm[d], B.active, d, col, body);
+            if (!eb)
+                eb = mg_launch_b_restrict(dim, B.parts, B.t_rr[d], B.n_rr[d], B.active, d, body);
+            // parts with a tile: the blocked leg
+            if (!eb)
+                eb = mg_launch_b_tb_pre(dim, B.parts, B.tasks[d], B.ntasks[d], B.active, d, o.nu_pre, B.smem_pre[d],
+                                        body);
+        }
         if (!eb)
             eb = mg_launch_b_bottom(dim, B.parts, B.nparts, B.active, o.nu_pre, o.nu_post, B.smem_bottom, body);
-        for (int d = B.maxLs - 1; d >= 0 && !eb; d--)
-            eb = mg_launch_b_tb_post(dim, B.parts, B.tasks[d], B.ntasks[d], B.active, d, o.nu_post, B.smem_post[d],
-                                     body);
+        for (int d = B.maxLs - 1; d >= 0 && !eb; d--) {
+            if (!eb)
+                eb = mg_launch_b_prolong(dim, B.parts, B.t_pr[d], B.n_pr[d], B.active, d, body);
+            for (int sw = 0; sw < o.nu_post && !eb; sw++)
+                for (int col = 0; col < 2 && !eb; col++)
+                    eb = mg_launch_b_smooth(dim, B.parts, B.t_sm[d], B.n_sm[d], B.active, d, col, body);
+            if (!eb)
+                eb = mg_launch_b_tb_post(dim, B.parts, B.tasks[d], B.ntasks[d], B.active, d, o.nu_post,
+                                         B.smem_post[d], body);
+        }
     }
     if (!eb)
         eb = mg_launch_b_accumulate(dim, B.parts, B.cells_act, B.ncells_act, B.active, body);

@@ -181,6 +181,7 @@ struct MgBPart {
     MgSolveCtl *ctl;
     double *partials;              // 2 * MG_NORM_BLOCKS_MAX
     unsigned *counter;
+    int nblk_lvl[MG_MAX_MG];       // cell chunks of the one-kernel-per-phase launches per level
     int nblk_act;                  // cell chunks over the active finest cells
     int nblk_blk;                  // cell chunks over the (n+4)^d block
     MgBottom bt;
@@ -201,6 +202,14 @@ cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tas
                                int depth, int nu, size_t smem, cudaStream_t s);
 cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,
                                 int depth, int nu, size_t smem, cudaStream_t s);
+// one-kernel-per-phase legs over parts: cells = (part, chunk) tasks of level L
+// (chunks over that level's colour cells / coarse cells / fine cells)
+cudaError_t mg_launch_b_smooth(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                               int L, int colour, cudaStream_t s);
+cudaError_t mg_launch_b_restrict(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                                 int L, cudaStream_t s);
+cudaError_t mg_launch_b_prolong(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                                int L, cudaStream_t s);
 cudaError_t mg_launch_b_bottom(int dim, const MgBPart *parts, int nparts, const int *active, int nu_pre, int nu_post,
                                size_t smem, cudaStream_t s);
 cudaError_t mg_launch_b_defect(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,

@@ -1189,6 +1189,46 @@ __global__ void __launch_bounds__(kBottomThreads) kb_bottom(const MgBPart *__res
     bottom_body<float, DIM>(P.phi32[P.Ls], P.f32[P.Ls], P.bt, nu_pre, nu_post, smem_raw);
 }
 
+// level L of a part in one-kernel-per-phase form: chunk c of nblk_lvl[L]
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_smooth(const MgBPart *__restrict__ parts,
+                                                      const MgBCell *__restrict__ cells, const int *__restrict__ active,
+                                                      int L, int colour)
+{
+    const MgBCell c = cells[blockIdx.x];
+    if (!active[c.part])
+        return;
+    const MgBPart &P = parts[c.part];
+    op_smooth_colour<float, DIM>(P.phi32[L], P.f32[L], P.g[L], colour, c.chunk * kThreads + threadIdx.x,
+                                 P.nblk_lvl[L] * kThreads);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_restrict(const MgBPart *__restrict__ parts,
+                                                        const MgBCell *__restrict__ cells,
+                                                        const int *__restrict__ active, int L)
+{
+    const MgBCell c = cells[blockIdx.x];
+    if (!active[c.part])
+        return;
+    const MgBPart &P = parts[c.part];
+    op_resid_restrict<float, DIM>(P.phi32[L], P.f32[L], P.g[L], P.phi32[L + 1], P.f32[L + 1], P.g[L + 1],
+                                  c.chunk * kThreads + threadIdx.x, P.nblk_lvl[L] * kThreads);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) kb_prolong(const MgBPart *__restrict__ parts,
+                                                       const MgBCell *__restrict__ cells,
+                                                       const int *__restrict__ active, int L)
+{
+    const MgBCell c = cells[blockIdx.x];
+    if (!active[c.part])
+        return;
+    const MgBPart &P = parts[c.part];
+    op_prolong<float, DIM>(P.phi32[L + 1], P.g[L + 1], P.phi32[L], P.g[L], c.chunk * kThreads + threadIdx.x,
+                           P.nblk_lvl[L] * kThreads);
+}
+
 template <int DIM>
 __device__ __forceinline__ void active_cell(const MgGeom &g, int t, int &i, int &j, int &k)
 {
@@ -1678,6 +1718,42 @@ cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *ta
         kb_tb_post<3><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
     else
         kb_tb_post<2><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_smooth(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                               int L, int colour, cudaStream_t s)
+{
+    if (ncells <= 0)
+        return cudaSuccess;
+    if (dim == 3)
+        kb_smooth<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, L, colour);
+    else
+        kb_smooth<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, L, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_restrict(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                                 int L, cudaStream_t s)
+{
+    if (ncells <= 0)
+        return cudaSuccess;
+    if (dim == 3)
+        kb_restrict<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+    else
+        kb_restrict<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_b_prolong(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, const int *active,
+                                int L, cudaStream_t s)
+{
+    if (ncells <= 0)
+        return cudaSuccess;
+    if (dim == 3)
+        kb_prolong<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+    else
+        kb_prolong<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
     return cudaGetLastError();
 }
 
