@@ -899,8 +899,11 @@ mg_status build_graph(mg_hierarchy *h)
     }
     h->batched = false;
     if (h->opt.precision == MG_MIXED && h->batch > 1) {
+        // measured on 64 uneven hierarchies: graph branches 105 ms, batched
+        // launches 143 ms (each batched block first loads its part's
+        // descriptor); MG_BATCHED=1 selects the batched launches
         const char *v = std::getenv("MG_BATCHED");
-        if (!(v && v[0] == '0')) {
+        if (v && v[0] == '1') {
             mg_status perr;
             h->batched = plan_batched(h, perr);
             if (perr)
@@ -985,19 +988,36 @@ struct TuneEntry {
     int tile[MG_MAX_MG];
 };
 
-float time_ms(mg_hierarchy *h, int reps, const std::function<cudaError_t()> &fn, cudaError_t &err)
+// Mean time of one replay of the launches of fn, captured into a CUDA graph
+// (the solve runs as a graph: timing plain launches would favour plans with
+// fewer launches for the wrong reason).
+float time_ms(mg_hierarchy *h, int reps, const std::function<cudaError_t(cudaStream_t)> &fn, cudaError_t &err)
 {
-    cudaEvent_t a, b;
-    err = cudaEventCreate(&a);
+    err = cudaSuccess;
+    if (!h->cap[0] && (err = cudaStreamCreateWithFlags(&h->cap[0], cudaStreamNonBlocking)))
+        return 0.f;
+    cudaStream_t cs = h->cap[0];
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if ((err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)))
+        return 0.f;
+    cudaError_t ef = fn(cs);
+    err = cudaStreamEndCapture(cs, &g);
+    if (ef)
+        err = ef;
+    if (!err)
+        err = cudaGraphInstantiate(&ge, g, 0);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (!err)
+        err = cudaEventCreate(&a);
     if (!err)
         err = cudaEventCreate(&b);
-    if (err)
-        return 0.f;
-    err = fn();                                   // warm-up
+    if (!err)
+        err = cudaGraphLaunch(ge, h->stream);              // warm-up
     if (!err)
         err = cudaEventRecord(a, h->stream);
     for (int r = 0; r < reps && !err; r++)
-        err = fn();
+        err = cudaGraphLaunch(ge, h->stream);
     if (!err)
         err = cudaEventRecord(b, h->stream);
     if (!err)
@@ -1005,8 +1025,14 @@ float time_ms(mg_hierarchy *h, int reps, const std::function<cudaError_t()> &fn,
     float ms = 0.f;
     if (!err)
         err = cudaEventElapsedTime(&ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    if (a)
+        cudaEventDestroy(a);
+    if (b)
+        cudaEventDestroy(b);
+    if (ge)
+        cudaGraphExecDestroy(ge);
+    if (g)
+        cudaGraphDestroy(g);
     return ms / reps;
 }
 
@@ -1014,7 +1040,6 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
 {
     const int dim = h->dim;
     const mg_options &o = h->opt;
-    cudaStream_t s = h->stream;
     te.dim = dim;
     te.n = ld.n;
     te.nu_pre = o.nu_pre;
@@ -1026,7 +1051,7 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     for (int nb : nbs) {
         plan_bottom(ld, dim, nb);
         plan_tiles(ld, dim, o.nu_pre, o.nu_post);
-        const float ms = time_ms(h, 5, [&] { return vcycle(h, ld, true, s); }, err);
+        const float ms = time_ms(h, 10, [&](cudaStream_t cs) { return vcycle(h, ld, true, cs); }, err);
         if (err)
             return false;
         if (ms < best) {
@@ -1049,7 +1074,7 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
                       mg_tb_smem(dim, true, t, 2 * o.nu_post) > MG_TB_SMEM_MAX))
                 continue;
             ld.tile[L] = t;
-            const float ms = time_ms(h, 5, [&] {
+            const float ms = time_ms(h, 10, [&](cudaStream_t s) {
                 cudaError_t e;
                 if (t) {
                     e = mg_launch_tb_pre(dim, ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
