@@ -57,7 +57,10 @@ enum { MG_FP64 = 0,        /* every step in FP64 */
 
 enum { MG_GUESS_INTERP = 0,  /* initial potential interpolated from the parent (Sec. 2.4) */
        MG_GUESS_ZERO = 1,    /* zero initial potential */
-       MG_GUESS_USER = 2 };  /* initial potential supplied by mg_set_guess */
+       MG_GUESS_USER = 2,    /* initial potential supplied by mg_set_guess */
+       MG_GUESS_LEARNED = 3 };  /* interpolated potential corrected by the network of mg_set_unet
+                                   (levels whose n is a power of two <= the network's nmax;
+                                   others use the interpolated potential) */
 
 enum { MG_FORCE_EQ2 = 0,     /* fourth-order difference of Eq. 2 (default) */
        MG_FORCE_CD2 = 1 };   /* two-point central difference */
@@ -176,6 +179,18 @@ typedef struct {
 mg_status mg_profile(mg_hierarchy *h, int enable);
 /* Fills up to cap entries; returns how many kernel kinds ran, or -1. */
 int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap);
+
+/* Attach the learned initial guess (include/unet.h) used by MG_GUESS_LEARNED;
+ * the solver runs it on its stream inside mg_solve.  net may be NULL
+ * (detach).  The network must outlive its use by h. */
+struct mg_unet;
+mg_status mg_set_unet(mg_hierarchy *h, struct mg_unet *net);
+
+/* After mg_solve: the initial potential level `level` (> 0) of hierarchy b
+ * started from under MG_GUESS_INTERP -- the parent's solution interpolated
+ * onto the level (Sec. 2.4) -- on Omega, n^d values into out (device or
+ * host).  Used to build training data for the learned guess. */
+mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out);
 
 /* Autotuner of the mixed-precision V-cycle (not part of the method; it picks
  * among equivalent launch plans).  For each distinct level size it times, on

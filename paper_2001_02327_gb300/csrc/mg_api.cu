@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/mg.h"
+#include "../../include/unet.h"
 #include "mg_internal.h"
 
 namespace {
@@ -178,6 +179,8 @@ struct mg_hierarchy {
     double *scal = nullptr;         // device scalars: [b][l][2] = ||b||^2, ||r||^2
     double *hscal = nullptr;        // pinned mirror
     MgSolveCtl *ctl = nullptr;      // device loop state per (b, l)
+    double *frho = nullptr;         // device 4 pi G h_l^2 per (b, l) (input scaling of the learned guess)
+    mg_unet *unet = nullptr;        // learned initial guess (MG_GUESS_LEARNED)
     MgSolveCtl *hctl = nullptr;     // pinned mirror
     bool poisoned = false, solved = false;
     std::string err;
@@ -304,7 +307,7 @@ mg_status check_options(const mg_options &o)
 {
     if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 || !(o.rel_tol >= 0.0) ||
         (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 ||
-        o.guess < MG_GUESS_INTERP || o.guess > MG_GUESS_USER ||
+        o.guess < MG_GUESS_INTERP || o.guess > MG_GUESS_LEARNED ||
         (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2))
         return MG_EINVAL;
     return MG_OK;
@@ -462,6 +465,13 @@ cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
         });
         if (e)
             return e;
+        if (o.guess == MG_GUESS_LEARNED && h->unet && dim == 3 && (ld.n & (ld.n - 1)) == 0) {
+            // network correction of the interpolated potential on Omega
+            const int r = mg_unet_predict_dev(h->unet, 1, ld.n, 1, ld.rho, ld.phi[0],
+                                              h->frho + (size_t)b * MG_MAX_LEVELS + l, 1, s);
+            if (r == 3)
+                return cudaErrorLaunchFailure;
+        }
     } else if (ld.guess_set) {
         if ((e = mg_launch_copy_guess(dim, ld.n, ld.guess, ld.phi[0], s)))
             return e;
@@ -559,6 +569,7 @@ void destroy_graph(mg_hierarchy *h)
 std::vector<char> graph_signature(const mg_hierarchy *h)
 {
     std::vector<char> sig;
+    sig.push_back(h->unet ? 1 : 0);
     for (const auto &hl : h->lev)
         for (const auto &ld : hl)
             sig.push_back(ld.guess_set ? 1 : 0);
@@ -1279,6 +1290,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     slots.push_back({(void **)&h->partials, align256((size_t)MG_BRANCHES * 2 * MG_NORM_BLOCKS_MAX * sizeof(double))});
     slots.push_back({(void **)&h->counters, align256((size_t)MG_BRANCHES * sizeof(unsigned))});
     slots.push_back({(void **)&h->ctl, align256((size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl))});
+    slots.push_back({(void **)&h->frho, align256((size_t)batch * MG_MAX_LEVELS * sizeof(double))});
     slots.push_back({(void **)&h->scal, align256((size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double))});
     for (auto &sl : slots)
         bytes += sl.bytes;
@@ -1336,6 +1348,15 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
             plan_bottom(ld, dim);
             plan_tiles(ld, dim, o.nu_pre, o.nu_post);
         }
+    if (e == cudaSuccess) {
+        std::vector<double> fr((size_t)batch * MG_MAX_LEVELS, 0.0);
+        for (int b = 0; b < batch; b++)
+            for (int l = 0; l < descs[b].num_levels; l++) {
+                const double hl = descs[b].h0 / (double)(1L << l);
+                fr[(size_t)b * MG_MAX_LEVELS + l] = 4.0 * M_PI * descs[b].G * hl * hl;
+            }
+        e = cudaMemcpy(h->frho, fr.data(), fr.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -1522,6 +1543,46 @@ int mg_profile_read(mg_hierarchy *h, mg_kernel_stat *out, int cap)
         k++;
     }
     return k;
+}
+
+mg_status mg_set_unet(mg_hierarchy *h, struct mg_unet *net)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (net && mg_unet_pack(net) != 0)
+        return fail(h, MG_ECUDA, "packing the network weights failed");
+    h->unet = net;
+    destroy_graph(h);
+    return MG_OK;
+}
+
+mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out)
+{
+    if (!h || !out)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (b < 0 || b >= h->batch || level < 1 || level >= h->desc[b].num_levels)
+        return fail(h, MG_EINVAL, "hierarchy %d level %d: need 1 <= level < num_levels", b, level);
+    if (!h->solved)
+        return fail(h, MG_ESTATE, "mg_interp_guess before mg_solve");
+    LevelData &ld = h->lev[b][level];
+    const LevelData &pd = h->lev[b][level - 1];
+    const int dim = h->dim;
+    const size_t nr = (size_t)cells(ld.n, dim), nb = (size_t)cells(ld.n + 4, dim);
+    double *blk = h->stage, *dense = h->stage + nb;
+    // the interface rewrites the inner-ring density and f with the values it
+    // already holds; the potential goes to the staging block
+    CK(h, mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2], blk, ld.rho,
+                              ld.f[0], 4.0 * M_PI * h->desc[b].G, 0, nullptr, h->stream));
+    const bool dev = is_device_ptr(out);
+    CK(h, mg_launch_extract(dim, ld.n, blk, dev ? out : dense, h->stream));
+    if (!dev)
+        CK(h, cudaMemcpyAsync(out, dense, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return MG_OK;
 }
 
 mg_status mg_autotune(mg_hierarchy *h, const char *cache_path)

@@ -144,6 +144,7 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
                              int stencil, cudaStream_t s);
 
 cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s);
+cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cudaStream_t s);
 
 // Device-side state of one level solve, updated by the control kernels that
 // close every iteration of the solve graph.

@@ -1107,6 +1107,21 @@ __global__ void __launch_bounds__(kThreads) k_forces(int n, double h, const doub
     }
 }
 
+// copy Omega of an (n+4)^d block into a dense n^d array
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_extract(int n, const double *__restrict__ blk, double *__restrict__ out)
+{
+    const int E = n + 4;
+    const int total = n * n * (DIM == 3 ? n : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / n;
+        const int i = t - r * n + 2;
+        const int j = DIM == 3 ? r % n + 2 : r + 2;
+        const int k = DIM == 3 ? r / n + 2 : 0;
+        out[t] = blk[lin<DIM>(i, j, k, E)];
+    }
+}
+
 __global__ void k_zero(uint4 *p, size_t n16)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n16; t += (size_t)gridDim.x * blockDim.x)
@@ -1665,6 +1680,16 @@ cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, dou
                                cudaGraphConditionalHandle hc, cudaStream_t s)
 {
     k_ctl_step<<<1, 1, 0, s>>>(ctl, scal, inc, tol, max_cycles, hc);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cudaStream_t s)
+{
+    const int grid = grid_for(cube(n, dim));
+    if (dim == 3)
+        k_extract<3><<<grid, kThreads, 0, s>>>(n, blk, out);
+    else
+        k_extract<2><<<grid, kThreads, 0, s>>>(n, blk, out);
     return cudaGetLastError();
 }
 

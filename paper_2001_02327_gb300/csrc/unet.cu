@@ -1,0 +1,886 @@
+// unet.cu -- the learned initial guess: a small 3D U-Net that predicts the
+// correction of a refinement level's interpolated initial potential, with
+// hand-written BF16 tensor-core convolutions (FP32 accumulate), its backward
+// pass, AdamW training and the hook into the solver.
+//
+// Network (channels-last BF16 activations, n = 2^k spatial edge, 4 scales):
+//   x0 = [4 pi G rho h^2 / s, Phi_interp / s]           (s = max |Phi_interp| on Omega)
+//   a0 = relu(c3(x0; 2->16))      s0 = relu(c3(a0; 16->16))          n
+//   a1 = relu(c3(pool s0; 16->32)) s1 = relu(c3(a1; 32->32))         n/2
+//   s2 = relu(c3(pool s1; 32->64))                                   n/4
+//   a3 = relu(c3(pool s2; 64->64))                                   n/8
+//   d2 = relu(c3([up a3, s2]; 128->32))                              n/4
+//   d1 = relu(c3([up d2, s1]; 64->16))                               n/2
+//   d0 = relu(c3([up d1, s0]; 32->16))                               n
+//   y  = c1(d0; 16->1);   Phi_guess = Phi_interp + s * y  on Omega
+// c3: 3x3x3 convolution, zero padding, bias; pool: 2x2x2 mean; up: nearest.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/unet.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kT = 256;
+
+inline int blocks_for(long n, int cap = 152 * 32)
+{
+    long b = (n + kT - 1) / kT;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t ld2(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+__device__ __forceinline__ uint32_t ld2(const float *p)
+{
+    const float2 f = *reinterpret_cast<const float2 *>(p);
+    return pack2(f.x, f.y);
+}
+
+// D += A (16x16, row) * B (16x8, col), BF16 in, FP32 accumulate
+__device__ __forceinline__ void mma16816(float *d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// 3x3x3 convolution as an implicit GEMM on the tensor cores.
+//   out[v][nn] = sum_{tap, c} in[v +/- off(tap)][c] * W[tap][nn][c]  (+ bias, relu)
+// in: [V][CK] (CK a multiple of 16), W: [27][NT*8][CK] BF16, V = batch * n^3
+// with n = 2^lg.  FLIP = true gathers at v - off (the transpose convolution of
+// the backward data pass).  A block of 4 warps covers 64 voxels; a warp owns
+// 16 voxels and all NT*8 output channels.
+template <int NT, bool FLIP, typename TIn>
+__global__ void __launch_bounds__(128) k_conv3(const TIn *__restrict__ in, int CK, const bf16 *__restrict__ W,
+                                               const float *__restrict__ bias, void *__restrict__ out, int out_bf16,
+                                               int relu, int lg, int V)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int n = 1 << lg, msk = n - 1;
+    const int r0 = blockIdx.x * 64 + warp * 16 + g, r1 = r0 + 8;
+    const bool ok0 = r0 < V, ok1 = r1 < V;
+    const int x0 = r0 & msk, y0 = (r0 >> lg) & msk, z0 = (r0 >> (2 * lg)) & msk, b0 = r0 >> (3 * lg);
+    const int x1 = r1 & msk, y1 = (r1 >> lg) & msk, z1 = (r1 >> (2 * lg)) & msk, b1 = r1 >> (3 * lg);
+    float acc[NT][4];
+#pragma unroll
+    for (int q = 0; q < NT; q++)
+        acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    constexpr int N = NT * 8;
+    for (int tap = 0; tap < 27; tap++) {
+        int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        if (FLIP) {
+            dz = -dz;
+            dy = -dy;
+            dx = -dx;
+        }
+        int q0 = -1, q1 = -1;
+        {
+            const int zz = z0 + dz, yy = y0 + dy, xx = x0 + dx;
+            if (ok0 && (unsigned)zz < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)xx < (unsigned)n)
+                q0 = (((b0 << lg | zz) << lg | yy) << lg) | xx;
+        }
+        {
+            const int zz = z1 + dz, yy = y1 + dy, xx = x1 + dx;
+            if (ok1 && (unsigned)zz < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)xx < (unsigned)n)
+                q1 = (((b1 << lg | zz) << lg | yy) << lg) | xx;
+        }
+        const bf16 *Wt = W + (size_t)tap * N * CK;
+        for (int c0 = 0; c0 < CK; c0 += 16) {
+            const uint32_t a0 = q0 >= 0 ? ld2(in + (size_t)q0 * CK + c0 + 2 * t) : 0u;
+            const uint32_t a1 = q1 >= 0 ? ld2(in + (size_t)q1 * CK + c0 + 2 * t) : 0u;
+            const uint32_t a2 = q0 >= 0 ? ld2(in + (size_t)q0 * CK + c0 + 2 * t + 8) : 0u;
+            const uint32_t a3 = q1 >= 0 ? ld2(in + (size_t)q1 * CK + c0 + 2 * t + 8) : 0u;
+#pragma unroll
+            for (int q = 0; q < NT; q++) {
+                const bf16 *wp = Wt + (size_t)(q * 8 + g) * CK + c0 + 2 * t;
+                mma16816(acc[q], a0, a1, a2, a3, ld2(wp), ld2(wp + 8));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NT; q++) {
+        const int c = q * 8 + 2 * t;
+        float v[4] = {acc[q][0], acc[q][1], acc[q][2], acc[q][3]};
+        if (bias) {
+            v[0] += bias[c];
+            v[1] += bias[c + 1];
+            v[2] += bias[c];
+            v[3] += bias[c + 1];
+        }
+        if (relu)
+            for (int e = 0; e < 4; e++)
+                v[e] = fmaxf(v[e], 0.f);
+        if (out_bf16) {
+            bf16 *o = reinterpret_cast<bf16 *>(out);
+            if (ok0)
+                *reinterpret_cast<uint32_t *>(o + (size_t)r0 * N + c) = pack2(v[0], v[1]);
+            if (ok1)
+                *reinterpret_cast<uint32_t *>(o + (size_t)r1 * N + c) = pack2(v[2], v[3]);
+        } else {
+            float *o = reinterpret_cast<float *>(out);
+            if (ok0)
+                *reinterpret_cast<float2 *>(o + (size_t)r0 * N + c) = make_float2(v[0], v[1]);
+            if (ok1)
+                *reinterpret_cast<float2 *>(o + (size_t)r1 * N + c) = make_float2(v[2], v[3]);
+        }
+    }
+}
+
+// Weight and bias gradients of a 3x3x3 convolution (FP32 on the CUDA cores):
+//   dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * d[v][co],  db[co] += sum_v d[v][co]
+// Each block takes one tap and a run of voxels, stages 32 voxels at a time
+// in shared memory and accumulates 4x4 (ci, co) tiles per thread.
+__global__ void __launch_bounds__(kT) k_wgrad(const bf16 *__restrict__ in, int CKin, int Cin, const float *__restrict__ d,
+                                              int N, float *__restrict__ dW, float *__restrict__ db, int lg, int V,
+                                              int vox_per_block)
+{
+    constexpr int VS = 32;
+    __shared__ float sIn[VS][128 + 1];
+    __shared__ float sD[VS][64 + 1];
+    const int tap = blockIdx.y;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int n = 1 << lg, msk = n - 1;
+    const int ntc = Cin / 4 > 0 ? (Cin + 3) / 4 : 1, nto = N / 4;
+    const int ntiles = ntc * nto;
+    float acc[2][16];
+    for (int u = 0; u < 2; u++)
+        for (int e = 0; e < 16; e++)
+            acc[u][e] = 0.f;
+    float bacc = 0.f;
+    const int vbeg = blockIdx.x * vox_per_block, vend = min(vbeg + vox_per_block, V);
+    for (int v0 = vbeg; v0 < vend; v0 += VS) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < VS * Cin; e += kT) {
+            const int vv = e / Cin, ci = e - vv * Cin;
+            const int v = v0 + vv;
+            float val = 0.f;
+            if (v < vend) {
+                const int x = v & msk, y = (v >> lg) & msk, z = (v >> (2 * lg)) & msk, b = v >> (3 * lg);
+                const int zz = z + dz, yy = y + dy, xx = x + dx;
+                if ((unsigned)zz < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)xx < (unsigned)n)
+                    val = __bfloat162float(in[(size_t)((((b << lg | zz) << lg | yy) << lg) | xx) * CKin + ci]);
+            }
+            sIn[vv][ci] = val;
+        }
+        for (int e = threadIdx.x; e < VS * N; e += kT) {
+            const int vv = e / N, co = e - vv * N;
+            const int v = v0 + vv;
+            sD[vv][co] = v < vend ? d[(size_t)v * N + co] : 0.f;
+        }
+        __syncthreads();
+        for (int u = 0; u < 2; u++) {
+            const int tile = threadIdx.x + u * kT;
+            if (tile >= ntiles)
+                break;
+            const int tc = tile / nto, to = tile - tc * nto;
+            for (int vv = 0; vv < VS; vv++) {
+                float a[4], bb[4];
+                for (int e = 0; e < 4; e++) {
+                    const int ci = tc * 4 + e;
+                    a[e] = ci < Cin ? sIn[vv][ci] : 0.f;
+                    bb[e] = sD[vv][to * 4 + e];
+                }
+                for (int i = 0; i < 4; i++)
+                    for (int j = 0; j < 4; j++)
+                        acc[u][i * 4 + j] = fmaf(a[i], bb[j], acc[u][i * 4 + j]);
+            }
+        }
+        if (tap == 13 && threadIdx.x < N)
+            for (int vv = 0; vv < VS; vv++)
+                bacc += sD[vv][threadIdx.x];
+    }
+    for (int u = 0; u < 2; u++) {
+        const int tile = threadIdx.x + u * kT;
+        if (tile >= ntiles)
+            break;
+        const int tc = tile / nto, to = tile - tc * nto;
+        for (int i = 0; i < 4; i++) {
+            const int ci = tc * 4 + i;
+            if (ci >= Cin)
+                continue;
+            for (int j = 0; j < 4; j++)
+                atomicAdd(&dW[((size_t)tap * Cin + ci) * N + to * 4 + j], acc[u][i * 4 + j]);
+        }
+    }
+    if (tap == 13 && threadIdx.x < N && db)
+        atomicAdd(&db[threadIdx.x], bacc);
+}
+
+// master FP32 weights [27][Cin][Cout] -> forward layout [27][Cout][CKin] and
+// backward-data layout [27][Cin_p16][Cout] (BF16, zero padded)
+__global__ void k_pack_weights(const float *__restrict__ w, int Cin, int CKin, int Cout, bf16 *__restrict__ wf,
+                               bf16 *__restrict__ wd)
+{
+    const int total = 27 * CKin * Cout;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int co = e % Cout, ci = (e / Cout) % CKin, tap = e / (Cout * CKin);
+        const float v = ci < Cin ? w[((size_t)tap * Cin + ci) * Cout + co] : 0.f;
+        wf[((size_t)tap * Cout + co) * CKin + ci] = __float2bfloat16_rn(v);
+        if (wd)
+            wd[((size_t)tap * CKin + ci) * Cout + co] = __float2bfloat16_rn(v);
+    }
+}
+
+// 2x2x2 mean pool (BF16, C channels): fine n = 2^lg -> coarse
+__global__ void k_pool(const bf16 *__restrict__ in, bf16 *__restrict__ out, int C, int lgc, int Vc)
+{
+    const int nc = 1 << lgc, m = nc - 1, lgf = lgc + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Vc * C; e += gridDim.x * blockDim.x) {
+        const int c = e % C, v = e / C;
+        const int x = v & m, y = (v >> lgc) & m, z = (v >> (2 * lgc)) & m, b = v >> (3 * lgc);
+        float s = 0.f;
+        for (int k = 0; k < 8; k++) {
+            const int fz = 2 * z + (k >> 2), fy = 2 * y + ((k >> 1) & 1), fx = 2 * x + (k & 1);
+            s += __bfloat162float(in[(size_t)((((b << lgf | fz) << lgf | fy) << lgf) | fx) * C + c]);
+        }
+        out[e] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+
+// pool backward, added: dIn[fine] += dOut[coarse] / 8
+__global__ void k_pool_bwd_add(const float *__restrict__ dout, float *__restrict__ din, int C, int lgf, int Vf)
+{
+    const int nf = 1 << lgf, m = nf - 1, lgc = lgf - 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Vf * C; e += gridDim.x * blockDim.x) {
+        const int c = e % C, v = e / C;
+        const int x = v & m, y = (v >> lgf) & m, z = (v >> (2 * lgf)) & m, b = v >> (3 * lgf);
+        din[e] += 0.125f * dout[(size_t)((((b << lgc | (z >> 1)) << lgc | (y >> 1)) << lgc) | (x >> 1)) * C + c];
+    }
+}
+
+// [up(low), skip] at the fine level: channels 0..Cu-1 from the parent, Cu..Cu+Cs-1 from skip
+__global__ void k_upcat(const bf16 *__restrict__ low, int Cu, const bf16 *__restrict__ skip, int Cs,
+                        bf16 *__restrict__ out, int lgf, int Vf)
+{
+    const int nf = 1 << lgf, m = nf - 1, lgc = lgf - 1, C = Cu + Cs;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Vf * C; e += gridDim.x * blockDim.x) {
+        const int c = e % C, v = e / C;
+        if (c < Cu) {
+            const int x = v & m, y = (v >> lgf) & m, z = (v >> (2 * lgf)) & m, b = v >> (3 * lgf);
+            out[e] = low[(size_t)((((b << lgc | (z >> 1)) << lgc | (y >> 1)) << lgc) | (x >> 1)) * Cu + c];
+        } else {
+            out[e] = skip[(size_t)v * Cs + c - Cu];
+        }
+    }
+}
+
+// backward of k_upcat: dLow[coarse] = sum of the 8 children's channels 0..Cu-1; dSkip = channels Cu.. (written)
+__global__ void k_upcat_bwd(const float *__restrict__ dout, int Cu, int Cs, float *__restrict__ dlow,
+                            float *__restrict__ dskip, int lgc, int Vc)
+{
+    const int nc = 1 << lgc, m = nc - 1, lgf = lgc + 1, C = Cu + Cs;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Vc * Cu; e += gridDim.x * blockDim.x) {
+        const int c = e % Cu, v = e / Cu;
+        const int x = v & m, y = (v >> lgc) & m, z = (v >> (2 * lgc)) & m, b = v >> (3 * lgc);
+        float s = 0.f;
+        for (int k = 0; k < 8; k++) {
+            const int fz = 2 * z + (k >> 2), fy = 2 * y + ((k >> 1) & 1), fx = 2 * x + (k & 1);
+            s += dout[(size_t)((((b << lgf | fz) << lgf | fy) << lgf) | fx) * C + c];
+        }
+        dlow[e] = s;
+    }
+    const int Vf = Vc * 8;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Vf * Cs; e += gridDim.x * blockDim.x) {
+        const int c = e % Cs, v = e / Cs;
+        dskip[e] = dout[(size_t)v * C + Cu + c];
+    }
+}
+
+// d *= (act > 0)
+__global__ void k_relu_mask(float *__restrict__ d, const bf16 *__restrict__ act, long n)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(act[e]) > 0.f))
+            d[e] = 0.f;
+}
+
+// y[v] = sum_c d0[v][c] w[c] + b
+__global__ void k_out1(const bf16 *__restrict__ d0, const float *__restrict__ w, const float *__restrict__ b,
+                       float *__restrict__ y, int V)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        float s = b[0];
+        for (int c = 0; c < 16; c++)
+            s += __bfloat162float(d0[(size_t)v * 16 + c]) * w[c];
+        y[v] = s;
+    }
+}
+
+// loss = mean (y - t)^2 per element; dy = 2 (y - t) / V; dd0 = dy w; dw, db of the 1x1 layer
+__global__ void k_out1_bwd(const float *__restrict__ y, const float *__restrict__ tgt, const bf16 *__restrict__ d0,
+                           const float *__restrict__ w, float *__restrict__ dd0, float *__restrict__ dw,
+                           float *__restrict__ db, float *__restrict__ loss, int V)
+{
+    float accw[16], accb = 0.f, accl = 0.f;
+    for (int c = 0; c < 16; c++)
+        accw[c] = 0.f;
+    const float inv = 1.f / (float)V;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        const float r = y[v] - tgt[v];
+        const float dy = 2.f * r * inv;
+        accl += r * r * inv;
+        accb += dy;
+        for (int c = 0; c < 16; c++) {
+            accw[c] += dy * __bfloat162float(d0[(size_t)v * 16 + c]);
+            dd0[(size_t)v * 16 + c] = dy * w[c];
+        }
+    }
+    // block reductions of the 16 weight gradients, the bias gradient and the loss
+    float vals[18];
+    for (int c = 0; c < 16; c++)
+        vals[c] = accw[c];
+    vals[16] = accb;
+    vals[17] = accl;
+    for (int q = 0; q < 18; q++) {
+        float v = vals[q];
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_down_sync(0xffffffffu, v, o);
+        vals[q] = v;
+    }
+    __shared__ float red2[18][kT / 32];
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 18; q++)
+            red2[q][threadIdx.x >> 5] = vals[q];
+    __syncthreads();
+    if (threadIdx.x < 18) {
+        float s = 0.f;
+        for (int wv = 0; wv < kT / 32; wv++)
+            s += red2[threadIdx.x][wv];
+        if (threadIdx.x < 16)
+            atomicAdd(&dw[threadIdx.x], s);
+        else if (threadIdx.x == 16)
+            atomicAdd(db, s);
+        else
+            atomicAdd(loss, s);
+    }
+}
+
+// AdamW on FP32 master weights
+__global__ void k_adamw(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m, float *__restrict__ v,
+                        long n, float lr, float b1, float b2, float eps, float wd, float c1, float c2)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float gg = gr[e];
+        const float mm = b1 * m[e] + (1.f - b1) * gg;
+        const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+        m[e] = mm;
+        v[e] = vv;
+        p[e] -= lr * ((mm / c1) / (sqrtf(vv / c2) + eps) + wd * p[e]);
+    }
+}
+
+// network input from Omega of an (n+4)^3 block pair, or from dense Omega
+// arrays (stride_blk = 0): x0[v] = {frho * rho / s, phi / s, 0...}, s = scale[b]
+__global__ void k_max_abs(const double *__restrict__ phi, int n, int blk, int lg, int B, float *__restrict__ scale)
+{
+    // one block per sample
+    __shared__ float red[kT / 32];
+    const int b = blockIdx.x;
+    const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
+    float mx = 0.f;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        const int x = v & m, y = (v >> lg) & m, z = v >> (2 * lg);
+        const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + y + 2) * E + x + 2 : (size_t)b * V + v;
+        mx = fmaxf(mx, fabsf((float)phi[q]));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < kT / 32; w++)
+            s = fmaxf(s, red[w]);
+        scale[b] = s > 0.f ? s : 1.f;
+    }
+}
+
+__global__ void k_make_input(const double *__restrict__ rho, const double *__restrict__ phi, int n, int blk, int lg,
+                             int B, const double *__restrict__ frho, const float *__restrict__ scale,
+                             bf16 *__restrict__ x0)
+{
+    const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x) {
+        const int b = e / V, v = e - b * V;
+        const int x = v & m, y = (v >> lg) & m, z = v >> (2 * lg);
+        const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + y + 2) * E + x + 2 : (size_t)e;
+        const float s = scale[b];
+        bf16 *o = x0 + (size_t)e * 16;
+        o[0] = __float2bfloat16_rn((float)(frho[b] * rho[q]) / s);
+        o[1] = __float2bfloat16_rn((float)phi[q] / s);
+        for (int c = 2; c < 16; c++)
+            o[c] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// target of training: (phi_true - phi_interp) / s
+__global__ void k_make_target(const double *__restrict__ phi_t, const double *__restrict__ phi_i,
+                              const float *__restrict__ scale, int V, int B, float *__restrict__ tgt)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x)
+        tgt[e] = (float)((phi_t[e] - phi_i[e]) / scale[e / V]);
+}
+
+// Phi += s * y on Omega (block or dense layout)
+__global__ void k_apply(double *__restrict__ phi, int n, int blk, int lg, int B, const float *__restrict__ scale,
+                        const float *__restrict__ y)
+{
+    const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x) {
+        const int b = e / V, v = e - b * V;
+        const int x = v & m, yy = (v >> lg) & m, z = v >> (2 * lg);
+        const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + yy + 2) * E + x + 2 : (size_t)e;
+        phi[q] += (double)scale[b] * (double)y[e];
+    }
+}
+
+__global__ void k_fill(float *p, long n, float v)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        p[e] = v;
+}
+
+// ---------------------------------------------------------------------------
+// layers
+// ---------------------------------------------------------------------------
+struct Conv {
+    int cin, ckin, cout;     // real input channels, padded K channels, outputs
+    long woff, boff;         // offsets into the parameter vector
+};
+
+// the nine 3x3x3 convolutions, then the 1x1 output (16 weights + bias)
+const int kConvDims[9][2] = {{2, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64}, {128, 32}, {64, 16}, {32, 16}};
+
+int pad16(int c) { return (c + 15) / 16 * 16; }
+
+}  // namespace
+
+struct mg_unet {
+    int nmax = 0, bmax = 0;
+    Conv conv[9];
+    long nparam = 0;
+    float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // FP32 master parameters and AdamW state
+    bf16 *wf[9] = {}, *wd[9] = {};                                     // packed BF16 weights
+    // activations (BF16) and gradients (FP32), sized for bmax * nmax^3
+    bf16 *x0 = nullptr, *a0 = nullptr, *s0 = nullptr, *p0 = nullptr, *a1 = nullptr, *s1 = nullptr, *p1 = nullptr,
+         *s2 = nullptr, *p2 = nullptr, *a3 = nullptr, *u2 = nullptr, *d2 = nullptr, *u1 = nullptr, *d1 = nullptr,
+         *u0 = nullptr, *d0 = nullptr;
+    float *y = nullptr, *tgt = nullptr, *scale = nullptr, *loss = nullptr, *gA = nullptr, *gB = nullptr, *gC = nullptr;
+    double *frho = nullptr;
+    char *mem = nullptr;
+    long step = 0;
+    cudaStream_t stream = nullptr;
+    bool packed = false;
+};
+
+namespace {
+
+template <int NT, bool FLIP, typename TIn>
+cudaError_t conv_launch(const TIn *in, int CK, const bf16 *W, const float *bias, void *out, int out_bf16, int relu,
+                        int lg, int V, cudaStream_t s)
+{
+    k_conv3<NT, FLIP, TIn><<<(V + 63) / 64, 128, 0, s>>>(in, CK, W, bias, out, out_bf16, relu, lg, V);
+    return cudaGetLastError();
+}
+
+template <bool FLIP, typename TIn>
+cudaError_t conv_any(const TIn *in, int CK, const bf16 *W, const float *bias, int N, void *out, int out_bf16, int relu,
+                     int lg, int V, cudaStream_t s)
+{
+    switch (N) {
+    case 16: return conv_launch<2, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
+    case 32: return conv_launch<4, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
+    case 64: return conv_launch<8, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
+    case 128: return conv_launch<16, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int ilog2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n)
+        l++;
+    return l;
+}
+
+cudaError_t pack_all(mg_unet *u)
+{
+    for (int i = 0; i < 9; i++) {
+        const Conv &c = u->conv[i];
+        k_pack_weights<<<blocks_for(27L * c.ckin * c.cout), kT, 0, u->stream>>>(u->p + c.woff, c.cin, c.ckin, c.cout,
+                                                                              u->wf[i], u->wd[i]);
+    }
+    u->packed = true;
+    return cudaGetLastError();
+}
+
+// forward through the network for B samples of edge n = 2^lg (x0 ready)
+cudaError_t forward(mg_unet *u, int B, int lg)
+{
+    cudaStream_t s = u->stream;
+    const int V0 = B << (3 * lg), V1 = V0 >> 3, V2 = V1 >> 3, V3 = V2 >> 3;
+    cudaError_t e;
+    auto C = [&](int i) -> const Conv & { return u->conv[i]; };
+    float *P = u->p;
+#define FWD(i, in, out, lgv, V)                                                                                   \
+    if ((e = conv_any<false, bf16>(in, C(i).ckin, u->wf[i], P + C(i).boff, C(i).cout, out, 1, 1, lgv, V, s))) \
+        return e;
+    FWD(0, u->x0, u->a0, lg, V0);
+    FWD(1, u->a0, u->s0, lg, V0);
+    k_pool<<<blocks_for((long)V1 * 16), kT, 0, s>>>(u->s0, u->p0, 16, lg - 1, V1);
+    FWD(2, u->p0, u->a1, lg - 1, V1);
+    FWD(3, u->a1, u->s1, lg - 1, V1);
+    k_pool<<<blocks_for((long)V2 * 32), kT, 0, s>>>(u->s1, u->p1, 32, lg - 2, V2);
+    FWD(4, u->p1, u->s2, lg - 2, V2);
+    k_pool<<<blocks_for((long)V3 * 64), kT, 0, s>>>(u->s2, u->p2, 64, lg - 3, V3);
+    FWD(5, u->p2, u->a3, lg - 3, V3);
+    k_upcat<<<blocks_for((long)V2 * 128), kT, 0, s>>>(u->a3, 64, u->s2, 64, u->u2, lg - 2, V2);
+    FWD(6, u->u2, u->d2, lg - 2, V2);
+    k_upcat<<<blocks_for((long)V1 * 64), kT, 0, s>>>(u->d2, 32, u->s1, 32, u->u1, lg - 1, V1);
+    FWD(7, u->u1, u->d1, lg - 1, V1);
+    k_upcat<<<blocks_for((long)V0 * 32), kT, 0, s>>>(u->d1, 16, u->s0, 16, u->u0, lg, V0);
+    FWD(8, u->u0, u->d0, lg, V0);
+#undef FWD
+    k_out1<<<blocks_for(V0), kT, 0, s>>>(u->d0, P + u->nparam - 17, P + u->nparam - 1, u->y, V0);
+    return cudaGetLastError();
+}
+
+// weight gradients of conv i from its input activation and output gradient g (FP32, N channels)
+cudaError_t wgrad(mg_unet *u, int i, const bf16 *in, const float *g, int lg, int V)
+{
+    const Conv &c = u->conv[i];
+    const int vpb = 4096;
+    dim3 grid((V + vpb - 1) / vpb, 27);
+    k_wgrad<<<grid, kT, 0, u->stream>>>(in, c.ckin, c.cin, g, c.cout, u->grad + c.woff, u->grad + c.boff, lg, V, vpb);
+    return cudaGetLastError();
+}
+
+cudaError_t dgrad(mg_unet *u, int i, const float *g, float *out, int lg, int V)
+{
+    const Conv &c = u->conv[i];
+    return conv_any<true, float>(g, c.cout, u->wd[i], nullptr, c.ckin, out, 0, 0, lg, V, u->stream);
+}
+
+cudaError_t mask(mg_unet *u, float *g, const bf16 *act, long n)
+{
+    k_relu_mask<<<blocks_for(n), kT, 0, u->stream>>>(g, act, n);
+    return cudaGetLastError();
+}
+
+// backward pass (loss gradient from y vs tgt), accumulating into u->grad
+cudaError_t backward(mg_unet *u, int B, int lg)
+{
+    cudaStream_t s = u->stream;
+    const int V0 = B << (3 * lg), V1 = V0 >> 3, V2 = V1 >> 3, V3 = V2 >> 3;
+    float *gA = u->gA, *gB = u->gB, *gC = u->gC;
+    cudaError_t e;
+    k_out1_bwd<<<blocks_for(V0, 152 * 4), kT, 0, s>>>(u->y, u->tgt, u->d0, u->p + u->nparam - 17, gA,
+                                                     u->grad + u->nparam - 17, u->grad + u->nparam - 1, u->loss, V0);
+    // D0 (u0 -> d0), gA = dd0 [V0][16]
+    if ((e = mask(u, gA, u->d0, (long)V0 * 16)) || (e = wgrad(u, 8, u->u0, gA, lg, V0)) ||
+        (e = dgrad(u, 8, gA, gB, lg, V0)))
+        return e;                                                        // gB = du0 [V0][32]
+    // split du0 -> dd1 (coarse) and ds0 (gC)
+    k_upcat_bwd<<<blocks_for((long)V0 * 16), kT, 0, s>>>(gB, 16, 16, gA, gC, lg - 1, V1);   // gA = dd1 [V1][16], gC = ds0 [V0][16]
+    if ((e = mask(u, gA, u->d1, (long)V1 * 16)) || (e = wgrad(u, 7, u->u1, gA, lg - 1, V1)) ||
+        (e = dgrad(u, 7, gA, gB, lg - 1, V1)))
+        return e;                                                        // gB = du1 [V1][64]
+    // ds1 lives behind ds0 in gC
+    float *ds1 = gC + (size_t)V0 * 16;
+    k_upcat_bwd<<<blocks_for((long)V1 * 32), kT, 0, s>>>(gB, 32, 32, gA, ds1, lg - 2, V2);  // gA = dd2 [V2][32]
+    if ((e = mask(u, gA, u->d2, (long)V2 * 32)) || (e = wgrad(u, 6, u->u2, gA, lg - 2, V2)) ||
+        (e = dgrad(u, 6, gA, gB, lg - 2, V2)))
+        return e;                                                        // gB = du2 [V2][128]
+    float *ds2 = ds1 + (size_t)V1 * 32;
+    k_upcat_bwd<<<blocks_for((long)V2 * 64), kT, 0, s>>>(gB, 64, 64, gA, ds2, lg - 3, V3);  // gA = da3 [V3][64]
+    if ((e = mask(u, gA, u->a3, (long)V3 * 64)) || (e = wgrad(u, 5, u->p2, gA, lg - 3, V3)) ||
+        (e = dgrad(u, 5, gA, gB, lg - 3, V3)))
+        return e;                                                        // gB = dp2 [V3][64]
+    k_pool_bwd_add<<<blocks_for((long)V2 * 64), kT, 0, s>>>(gB, ds2, 64, lg - 2, V2);
+    if ((e = mask(u, ds2, u->s2, (long)V2 * 64)) || (e = wgrad(u, 4, u->p1, ds2, lg - 2, V2)) ||
+        (e = dgrad(u, 4, ds2, gB, lg - 2, V2)))
+        return e;                                                        // gB = dp1 [V2][32]
+    k_pool_bwd_add<<<blocks_for((long)V1 * 32), kT, 0, s>>>(gB, ds1, 32, lg - 1, V1);
+    if ((e = mask(u, ds1, u->s1, (long)V1 * 32)) || (e = wgrad(u, 3, u->a1, ds1, lg - 1, V1)) ||
+        (e = dgrad(u, 3, ds1, gB, lg - 1, V1)))
+        return e;                                                        // gB = da1 [V1][32]
+    if ((e = mask(u, gB, u->a1, (long)V1 * 32)) || (e = wgrad(u, 2, u->p0, gB, lg - 1, V1)) ||
+        (e = dgrad(u, 2, gB, gA, lg - 1, V1)))
+        return e;                                                        // gA = dp0 [V1][16]
+    float *ds0 = gC;
+    k_pool_bwd_add<<<blocks_for((long)V0 * 16), kT, 0, s>>>(gA, ds0, 16, lg, V0);
+    if ((e = mask(u, ds0, u->s0, (long)V0 * 16)) || (e = wgrad(u, 1, u->a0, ds0, lg, V0)) ||
+        (e = dgrad(u, 1, ds0, gB, lg, V0)))
+        return e;                                                        // gB = da0 [V0][16]
+    if ((e = mask(u, gB, u->a0, (long)V0 * 16)) || (e = wgrad(u, 0, u->x0, gB, lg, V0)))
+        return e;
+    return cudaGetLastError();
+}
+
+// He-style initialisation from a counter-based hash (deterministic per seed)
+float hash_uniform(unsigned long long seed, unsigned long long i)
+{
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)((z >> 11) * (1.0 / 9007199254740992.0));
+}
+
+}  // namespace
+
+extern "C" {
+
+long mg_unet_param_count(void)
+{
+    long n = 0;
+    for (int i = 0; i < 9; i++)
+        n += 27L * kConvDims[i][0] * kConvDims[i][1] + kConvDims[i][1];
+    return n + 17;
+}
+
+int mg_unet_create(int nmax, int bmax, unsigned long long seed, void *stream, mg_unet **out)
+{
+    if (!out)
+        return 1;
+    *out = nullptr;
+    if (nmax < 8 || (nmax & (nmax - 1)) || bmax < 1)
+        return 1;
+    mg_unet *u = new (std::nothrow) mg_unet();
+    if (!u)
+        return 2;
+    u->nmax = nmax;
+    u->bmax = bmax;
+    u->stream = (cudaStream_t)stream;
+    long off = 0;
+    for (int i = 0; i < 9; i++) {
+        Conv &c = u->conv[i];
+        c.cin = kConvDims[i][0];
+        c.ckin = pad16(c.cin);
+        c.cout = kConvDims[i][1];
+        c.woff = off;
+        off += 27L * c.cin * c.cout;
+        c.boff = off;
+        off += c.cout;
+    }
+    u->nparam = off + 17;
+    const long V0 = (long)bmax * nmax * nmax * nmax;
+    // arena
+    std::vector<std::pair<void **, size_t>> sl;
+    auto A = [&](void **p, size_t b) { sl.push_back({p, (b + 255) & ~(size_t)255}); };
+    for (void **pp : {(void **)&u->p, (void **)&u->grad, (void **)&u->m, (void **)&u->v})
+        A(pp, u->nparam * sizeof(float));
+    for (int i = 0; i < 9; i++) {
+        A((void **)&u->wf[i], 27L * u->conv[i].ckin * u->conv[i].cout * sizeof(bf16));
+        A((void **)&u->wd[i], 27L * u->conv[i].ckin * u->conv[i].cout * sizeof(bf16));
+    }
+    const long V1 = V0 / 8, V2 = V1 / 8, V3 = V2 / 8;
+    A((void **)&u->x0, V0 * 16 * sizeof(bf16));
+    A((void **)&u->a0, V0 * 16 * sizeof(bf16));
+    A((void **)&u->s0, V0 * 16 * sizeof(bf16));
+    A((void **)&u->p0, V1 * 16 * sizeof(bf16));
+    A((void **)&u->a1, V1 * 32 * sizeof(bf16));
+    A((void **)&u->s1, V1 * 32 * sizeof(bf16));
+    A((void **)&u->p1, V2 * 32 * sizeof(bf16));
+    A((void **)&u->s2, V2 * 64 * sizeof(bf16));
+    A((void **)&u->p2, V3 * 64 * sizeof(bf16));
+    A((void **)&u->a3, V3 * 64 * sizeof(bf16));
+    A((void **)&u->u2, V2 * 128 * sizeof(bf16));
+    A((void **)&u->d2, V2 * 32 * sizeof(bf16));
+    A((void **)&u->u1, V1 * 64 * sizeof(bf16));
+    A((void **)&u->d1, V1 * 16 * sizeof(bf16));
+    A((void **)&u->u0, V0 * 32 * sizeof(bf16));
+    A((void **)&u->d0, V0 * 16 * sizeof(bf16));
+    A((void **)&u->y, V0 * sizeof(float));
+    A((void **)&u->tgt, V0 * sizeof(float));
+    A((void **)&u->scale, 1024 * sizeof(float));
+    A((void **)&u->loss, 256);
+    A((void **)&u->frho, bmax * sizeof(double));
+    A((void **)&u->gA, V0 * 32 * sizeof(float));
+    A((void **)&u->gB, V0 * 32 * sizeof(float));
+    A((void **)&u->gC, (V0 * 16 + V1 * 32 + V2 * 64) * sizeof(float));
+    size_t bytes = 0;
+    for (auto &x : sl)
+        bytes += x.second;
+    if (cudaMalloc((void **)&u->mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete u;
+        return 2;
+    }
+    size_t pos = 0;
+    for (auto &x : sl) {
+        *x.first = u->mem + pos;
+        pos += x.second;
+    }
+    cudaMemsetAsync(u->mem, 0, bytes, u->stream);
+    // initial parameters: uniform(-a, a), a = sqrt(6 / fan_in); zero biases
+    std::vector<float> h(u->nparam, 0.f);
+    for (int i = 0; i < 9; i++) {
+        const Conv &c = u->conv[i];
+        const float a = std::sqrt(6.f / (27.f * c.cin));
+        for (long k = 0; k < 27L * c.cin * c.cout; k++)
+            h[c.woff + k] = a * (2.f * hash_uniform(seed, c.woff + k) - 1.f);
+    }
+    for (int c = 0; c < 16; c++)
+        h[u->nparam - 17 + c] = 0.01f * (2.f * hash_uniform(seed, u->nparam + c) - 1.f);
+    cudaMemcpyAsync(u->p, h.data(), u->nparam * sizeof(float), cudaMemcpyHostToDevice, u->stream);
+    if (cudaStreamSynchronize(u->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(u->mem);
+        delete u;
+        return 3;
+    }
+    *out = u;
+    return 0;
+}
+
+int mg_unet_destroy(mg_unet *u)
+{
+    if (!u)
+        return 0;
+    cudaStreamSynchronize(u->stream);
+    cudaFree(u->mem);
+    cudaGetLastError();
+    delete u;
+    return 0;
+}
+
+int mg_unet_get_params(mg_unet *u, float *out)
+{
+    if (!u || !out)
+        return 1;
+    if (cudaMemcpyAsync(out, u->p, u->nparam * sizeof(float), cudaMemcpyDeviceToHost, u->stream) ||
+        cudaStreamSynchronize(u->stream))
+        return 3;
+    return 0;
+}
+
+int mg_unet_set_params(mg_unet *u, const float *in)
+{
+    if (!u || !in)
+        return 1;
+    if (cudaMemcpyAsync(u->p, in, u->nparam * sizeof(float), cudaMemcpyHostToDevice, u->stream) ||
+        cudaStreamSynchronize(u->stream))
+        return 3;
+    u->packed = false;
+    u->step = 0;
+    return 0;
+}
+
+// Pack the BF16 weight copies now (before a solve graph captures inference).
+int mg_unet_pack(mg_unet *u)
+{
+    if (!u)
+        return 1;
+    if (pack_all(u) || cudaStreamSynchronize(u->stream))
+        return 3;
+    return 0;
+}
+
+int mg_unet_get_grad(mg_unet *u, float *out)
+{
+    if (!u || !out)
+        return 1;
+    if (cudaMemcpyAsync(out, u->grad, u->nparam * sizeof(float), cudaMemcpyDeviceToHost, u->stream) ||
+        cudaStreamSynchronize(u->stream))
+        return 3;
+    return 0;
+}
+
+// Internal entry used by the solver and by the public calls: from (n+4)^3
+// blocks (blk = 1) or dense n^3 arrays (blk = 0) of B samples, predict y and
+// (apply = 1) add scale * y to phi on Omega.
+int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, double *phi, const double *frho_dev,
+                        int apply, void *stream)
+{
+    if (!u || B < 1 || B > u->bmax || n < 8 || n > u->nmax || (n & (n - 1)))
+        return 1;
+    cudaStream_t s = stream ? (cudaStream_t)stream : u->stream;
+    cudaStream_t keep = u->stream;
+    u->stream = s;
+    const int lg = ilog2(n);
+    const int V0 = B << (3 * lg);
+    if (!u->packed && pack_all(u)) {
+        u->stream = keep;
+        return 3;
+    }
+    k_max_abs<<<B, kT, 0, s>>>(phi, n, blk, lg, B, u->scale);
+    k_make_input<<<blocks_for(V0), kT, 0, s>>>(rho, phi, n, blk, lg, B, frho_dev, u->scale, u->x0);
+    cudaError_t e = forward(u, B, lg);
+    if (!e && apply) {
+        k_apply<<<blocks_for(V0), kT, 0, s>>>(phi, n, blk, lg, B, u->scale, u->y);
+        e = cudaGetLastError();
+    }
+    u->stream = keep;
+    return e ? 3 : 0;
+}
+
+int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *phi_interp, const double *frho,
+                    float *y_out)
+{
+    if (!u || !frho || B > u->bmax)
+        return 1;
+    if (cudaMemcpyAsync(u->frho, frho, B * sizeof(double), cudaMemcpyHostToDevice, u->stream))
+        return 3;
+    int r = mg_unet_predict_dev(u, B, n, 0, rho, const_cast<double *>(phi_interp), u->frho, 0, nullptr);
+    if (r)
+        return r;
+    const long V0 = (long)B * n * n * n;
+    if (y_out && (cudaMemcpyAsync(y_out, u->y, V0 * sizeof(float), cudaMemcpyDeviceToHost, u->stream) ||
+                  cudaStreamSynchronize(u->stream)))
+        return 3;
+    return 0;
+}
+
+int mg_unet_train_step(mg_unet *u, int B, int n, const double *rho, const double *phi_interp,
+                       const double *phi_true, const double *frho, float lr, float wd, int update, float *loss_out)
+{
+    if (!u || !frho || B > u->bmax || n < 8 || n > u->nmax || (n & (n - 1)))
+        return 1;
+    cudaStream_t s = u->stream;
+    const int lg = ilog2(n);
+    const int V0 = B << (3 * lg);
+    if (cudaMemcpyAsync(u->frho, frho, B * sizeof(double), cudaMemcpyHostToDevice, s))
+        return 3;
+    int r = mg_unet_predict_dev(u, B, n, 0, rho, const_cast<double *>(phi_interp), u->frho, 0, nullptr);
+    if (r)
+        return r;
+    k_make_target<<<blocks_for(V0), kT, 0, s>>>(phi_true, phi_interp, u->scale, 1 << (3 * lg), B, u->tgt);
+    k_fill<<<blocks_for(u->nparam), kT, 0, s>>>(u->grad, u->nparam, 0.f);
+    k_fill<<<1, 32, 0, s>>>(u->loss, 1, 0.f);
+    if (backward(u, B, lg))
+        return 3;
+    if (update) {
+        u->step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)u->step), c2 = 1.f - std::pow(b2, (float)u->step);
+        k_adamw<<<blocks_for(u->nparam), kT, 0, s>>>(u->p, u->grad, u->m, u->v, u->nparam, lr, b1, b2, 1e-8f, wd, c1, c2);
+        u->packed = false;
+    }
+    float l = 0.f;
+    if (cudaMemcpyAsync(&l, u->loss, sizeof(float), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s))
+        return 3;
+    if (loss_out)
+        *loss_out = l;
+    return cudaGetLastError() ? 3 : 0;
+}
+
+}  // extern "C"
