@@ -188,9 +188,10 @@ mg_status mg_set_unet(mg_hierarchy *h, struct mg_unet *net);
 
 /* After mg_solve: the initial potential level `level` (> 0) of hierarchy b
  * started from under MG_GUESS_INTERP -- the parent's solution interpolated
- * onto the level (Sec. 2.4) -- on Omega, n^d values into out (device or
- * host).  Used to build training data for the learned guess. */
-mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out);
+ * onto the level (Sec. 2.4) -- on Omega, n^d values into out, and (resid_out
+ * not NULL) its h^2-scaled residual h^2 (4 pi G rho - lap_h Phi) there (device
+ * or host pointers).  Used to build training data for the learned guess. */
+mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out, double *resid_out);
 
 /* Autotuner of the mixed-precision V-cycle (not part of the method; it picks
  * among equivalent launch plans).  For each distinct level size it times, on

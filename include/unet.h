@@ -12,10 +12,13 @@
  * nearest upsampling with concatenated skips, a 1x1x1 output; 367k FP32 master
  * parameters, BF16 tensor-core convolutions with FP32 accumulation.
  * Inputs per sample, on Omega (n^3, C order, x fastest):
- *   rho, phi_interp (FP64) and frho = 4 pi G h^2 (the factor that turns rho
- *   into the right-hand side of the 7-point stencil times h^2).
- * With s = max |phi_interp| the network sees (frho * rho / s, phi_interp / s)
- * and predicts y; the guess is phi_interp + s * y.
+ *   rho, phi_interp (FP64), resid = h^2 (4 pi G rho - lap_h(phi_interp)) (the
+ *   7-point residual of the interpolated potential, scaled by h^2) and
+ *   frho = 4 pi G h^2.
+ * With s = max |phi_interp| and s_r = max |resid| the network sees
+ * (frho * rho / s, phi_interp / s, resid / s_r) and predicts y; the guess is
+ * phi_interp + (s_r n^2 / 16) y (the inverse Laplacian amplifies smooth
+ * residuals by about n^2; the factor keeps y of order one for every n).
  * All array pointers are device pointers unless stated.  Return values: 0 ok,
  * 1 bad argument, 2 out of memory, 3 CUDA error.
  */
@@ -45,26 +48,28 @@ int mg_unet_get_grad(mg_unet *u, float *host_out);
 
 /* Forward pass on B dense samples: y_out (host, may be NULL) receives
  * B * n^3 network outputs.  frho: host array of B factors. */
-int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *phi_interp, const double *frho,
-                    float *y_out);
+int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *phi_interp, const double *resid,
+                    const double *frho, float *y_out);
 
 /* One training step: loss = mean over the B * n^3 cells of
- * (y - (phi_true - phi_interp) / s)^2, backward pass into the parameter
+ * (y - (phi_true - phi_interp) / (s_r n^2 / 16))^2, backward pass into the parameter
  * gradient and, if update, one AdamW step (lr, decoupled weight decay wd).
  * loss_out (host) receives the loss before the update. */
 int mg_unet_train_step(mg_unet *u, int B, int n, const double *rho, const double *phi_interp,
-                       const double *phi_true, const double *frho, float lr, float wd, int update, float *loss_out);
+                       const double *resid, const double *phi_true, const double *frho, float lr, float wd, int update,
+                       float *loss_out);
 
 /* Convert the FP32 parameters into the BF16 copies the convolutions read
  * (done lazily otherwise); call before a solve graph records inference. */
 int mg_unet_pack(mg_unet *u);
 
 /* Solver hook: predict for B samples laid out as (n+4)^3 level blocks
- * (blk = 1, Omega at storage indices 2..n+1) or dense n^3 arrays (blk = 0),
- * frho_dev a device array of B factors, and (apply = 1) add s * y to phi on
+ * (blk = 1, Omega at storage indices 2..n+1; the residual is formed from the
+ * blocks, resid unused) or dense n^3 arrays (blk = 0, resid given), frho_dev a
+ * device array of B factors, and (apply = 1) add the correction to phi on
  * Omega, all on `stream`. */
-int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, double *phi, const double *frho_dev,
-                        int apply, void *stream);
+int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, double *phi, const double *resid,
+                        const double *frho_dev, int apply, void *stream);
 
 #ifdef __cplusplus
 }

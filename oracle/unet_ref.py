@@ -12,7 +12,7 @@ import numpy as np
 import torch
 import torch.nn.functional as Fn
 
-CONV_DIMS = [(2, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (128, 32), (64, 16), (32, 16)]
+CONV_DIMS = [(3, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (128, 32), (64, 16), (32, 16)]
 
 
 def param_count():
@@ -36,16 +36,24 @@ def unpack(p):
     return out, (wo, bo)
 
 
-def forward(p, rho, phi_interp, frho):
-    """rho, phi_interp: (B, n, n, n) float64 tensors; frho: (B,) factors.
-    Returns (y (B,n,n,n), scale (B,))."""
+def _max_abs(t):
+    B = t.shape[0]
+    s = t.abs().reshape(B, -1).max(dim=1).values
+    return torch.where(s > 0, s, torch.ones_like(s))
+
+
+def forward(p, rho, phi_interp, resid, frho):
+    """rho, phi_interp, resid: (B, n, n, n) float64 tensors (resid = the
+    h^2-scaled residual of phi_interp); frho: (B,) factors 4 pi G h^2.
+    Returns (y (B,n,n,n), output scale (B,)): the correction is scale * y with
+    scale = max|resid| n^2 / 16."""
     convs, (wo, bo) = unpack(p)
-    B = rho.shape[0]
-    s = torch.clamp(phi_interp.abs().reshape(B, -1).max(dim=1).values, min=0.0)
-    s = torch.where(s > 0, s, torch.ones_like(s))
-    sv = s.reshape(B, 1, 1, 1)
+    B, n = rho.shape[0], rho.shape[1]
+    s = _max_abs(phi_interp)
+    sr = _max_abs(resid)
+    sv, srv = s.reshape(B, 1, 1, 1), sr.reshape(B, 1, 1, 1)
     fr = torch.as_tensor(frho, dtype=rho.dtype).reshape(B, 1, 1, 1)
-    x = torch.stack([fr * rho / sv, phi_interp / sv], dim=1)            # (B, 2, n, n, n)
+    x = torch.stack([fr * rho / sv, phi_interp / sv, resid / srv], dim=1)   # (B, 3, n, n, n)
 
     def c3(t, i):
         return torch.relu(Fn.conv3d(t, convs[i][0], convs[i][1], padding=1))
@@ -61,13 +69,25 @@ def forward(p, rho, phi_interp, frho):
     d1 = c3(torch.cat([up(d2), s1], dim=1), 7)
     d0 = c3(torch.cat([up(d1), s0], dim=1), 8)
     y = torch.einsum("bcxyz,c->bxyz", d0, wo) + bo
-    return y, s
+    return y, sr * (n * n / 16.0)
 
 
-def loss_and_grad(p, rho, phi_interp, phi_true, frho):
-    """Loss mean((y - (phi_true - phi_interp)/s)^2) and its gradient (float64)."""
+def residual_h2(phi, rho, frho):
+    """h^2 (4 pi G rho - lap_h phi) on the interior of dense (B, n, n, n)
+    arrays (the 7-point Laplacian of Eq. 4; edge cells are left zero)."""
+    fr = torch.as_tensor(frho, dtype=rho.dtype).reshape(-1, 1, 1, 1)
+    r = torch.zeros_like(phi)
+    c = phi[:, 1:-1, 1:-1, 1:-1]
+    nb = (phi[:, :-2, 1:-1, 1:-1] + phi[:, 2:, 1:-1, 1:-1] + phi[:, 1:-1, :-2, 1:-1] + phi[:, 1:-1, 2:, 1:-1]
+          + phi[:, 1:-1, 1:-1, :-2] + phi[:, 1:-1, 1:-1, 2:])
+    r[:, 1:-1, 1:-1, 1:-1] = fr * rho[:, 1:-1, 1:-1, 1:-1] - (nb - 6.0 * c)
+    return r
+
+
+def loss_and_grad(p, rho, phi_interp, resid, phi_true, frho):
+    """Loss mean((y - (phi_true - phi_interp)/scale)^2) and its gradient (float64)."""
     pt = torch.tensor(np.asarray(p, dtype=np.float64), requires_grad=True)
-    y, s = forward(pt, rho, phi_interp, frho)
+    y, s = forward(pt, rho, phi_interp, resid, frho)
     tgt = (phi_true - phi_interp) / s.reshape(-1, 1, 1, 1)
     loss = ((y - tgt) ** 2).mean()
     loss.backward()

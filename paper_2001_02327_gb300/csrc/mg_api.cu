@@ -467,7 +467,7 @@ cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
             return e;
         if (o.guess == MG_GUESS_LEARNED && h->unet && dim == 3 && (ld.n & (ld.n - 1)) == 0) {
             // network correction of the interpolated potential on Omega
-            const int r = mg_unet_predict_dev(h->unet, 1, ld.n, 1, ld.rho, ld.phi[0],
+            const int r = mg_unet_predict_dev(h->unet, 1, ld.n, 1, ld.rho, ld.phi[0], nullptr,
                                               h->frho + (size_t)b * MG_MAX_LEVELS + l, 1, s);
             if (r == 3)
                 return cudaErrorLaunchFailure;
@@ -1558,7 +1558,7 @@ mg_status mg_set_unet(mg_hierarchy *h, struct mg_unet *net)
     return MG_OK;
 }
 
-mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out)
+mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out, double *resid_out)
 {
     if (!h || !out)
         return MG_EINVAL;
@@ -1572,15 +1572,22 @@ mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out)
     const LevelData &pd = h->lev[b][level - 1];
     const int dim = h->dim;
     const size_t nr = (size_t)cells(ld.n, dim), nb = (size_t)cells(ld.n + 4, dim);
-    double *blk = h->stage, *dense = h->stage + nb;
+    double *blk = h->stage, *dense = h->stage + nb, *dres = h->stage + nb + nr;
     // the interface rewrites the inner-ring density and f with the values it
     // already holds; the potential goes to the staging block
+    const double fourpiG = 4.0 * M_PI * h->desc[b].G;
     CK(h, mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2], blk, ld.rho,
-                              ld.f[0], 4.0 * M_PI * h->desc[b].G, 0, nullptr, h->stream));
+                              ld.f[0], fourpiG, 0, nullptr, h->stream));
     const bool dev = is_device_ptr(out);
     CK(h, mg_launch_extract(dim, ld.n, blk, dev ? out : dense, h->stream));
     if (!dev)
         CK(h, cudaMemcpyAsync(out, dense, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (resid_out) {
+        const bool rdev = is_device_ptr(resid_out);
+        CK(h, mg_launch_resid_h2(dim, ld.n, blk, ld.rho, fourpiG * ld.h * ld.h, rdev ? resid_out : dres, h->stream));
+        if (!rdev)
+            CK(h, cudaMemcpyAsync(resid_out, dres, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     return MG_OK;
 }

@@ -145,6 +145,8 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
 
 cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s);
 cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cudaStream_t s);
+cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const double *rho_blk, double frho,
+                               double *out, cudaStream_t s);
 
 // Device-side state of one level solve, updated by the control kernels that
 // close every iteration of the solve graph.

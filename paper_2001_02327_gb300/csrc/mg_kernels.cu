@@ -1122,6 +1122,27 @@ __global__ void __launch_bounds__(kThreads) k_extract(int n, const double *__res
     }
 }
 
+// h^2 r = frho rho - (sum of the 2d neighbours - 2d Phi) on Omega of (n+4)^d blocks
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_resid_h2(int n, const double *__restrict__ phi,
+                                                       const double *__restrict__ rho, double frho,
+                                                       double *__restrict__ out)
+{
+    const int E = n + 4;
+    const int total = n * n * (DIM == 3 ? n : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / n;
+        const int i = t - r * n + 2;
+        const int j = DIM == 3 ? r % n + 2 : r + 2;
+        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int p = lin<DIM>(i, j, k, E);
+        double nb = phi[p - 1] + phi[p + 1] + phi[p - E] + phi[p + E];
+        if (DIM == 3)
+            nb += phi[p - E * E] + phi[p + E * E];
+        out[t] = frho * rho[p] - (nb - 2.0 * DIM * phi[p]);
+    }
+}
+
 __global__ void k_zero(uint4 *p, size_t n16)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n16; t += (size_t)gridDim.x * blockDim.x)
@@ -1690,6 +1711,17 @@ cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cu
         k_extract<3><<<grid, kThreads, 0, s>>>(n, blk, out);
     else
         k_extract<2><<<grid, kThreads, 0, s>>>(n, blk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const double *rho_blk, double frho,
+                               double *out, cudaStream_t s)
+{
+    const int grid = grid_for(cube(n, dim));
+    if (dim == 3)
+        k_resid_h2<3><<<grid, kThreads, 0, s>>>(n, phi_blk, rho_blk, frho, out);
+    else
+        k_resid_h2<2><<<grid, kThreads, 0, s>>>(n, phi_blk, rho_blk, frho, out);
     return cudaGetLastError();
 }
 

@@ -4,15 +4,19 @@
 // pass, AdamW training and the hook into the solver.
 //
 // Network (channels-last BF16 activations, n = 2^k spatial edge, 4 scales):
-//   x0 = [4 pi G rho h^2 / s, Phi_interp / s]           (s = max |Phi_interp| on Omega)
-//   a0 = relu(c3(x0; 2->16))      s0 = relu(c3(a0; 16->16))          n
+//   x0 = [4 pi G rho h^2 / s, Phi_interp / s, h^2 r / s_r]   on Omega, with
+//        r = 4 pi G rho - lap(Phi_interp) the residual of the interpolated
+//        potential, s = max |Phi_interp|, s_r = max |h^2 r|
+//   a0 = relu(c3(x0; 3->16))      s0 = relu(c3(a0; 16->16))          n
 //   a1 = relu(c3(pool s0; 16->32)) s1 = relu(c3(a1; 32->32))         n/2
 //   s2 = relu(c3(pool s1; 32->64))                                   n/4
 //   a3 = relu(c3(pool s2; 64->64))                                   n/8
 //   d2 = relu(c3([up a3, s2]; 128->32))                              n/4
 //   d1 = relu(c3([up d2, s1]; 64->16))                               n/2
 //   d0 = relu(c3([up d1, s0]; 32->16))                               n
-//   y  = c1(d0; 16->1);   Phi_guess = Phi_interp + s * y  on Omega
+//   y  = c1(d0; 16->1);   Phi_guess = Phi_interp + (s_r n^2 / 16) y  on Omega
+// (the inverse 7-point Laplacian amplifies smooth residuals by ~n^2: the
+// factor keeps y of order one across level sizes).
 // c3: 3x3x3 convolution, zero padding, bias; pool: 2x2x2 mean; up: nearest.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -385,60 +389,95 @@ __global__ void k_adamw(float *__restrict__ p, const float *__restrict__ gr, flo
     }
 }
 
-// network input from Omega of an (n+4)^3 block pair, or from dense Omega
-// arrays (stride_blk = 0): x0[v] = {frho * rho / s, phi / s, 0...}, s = scale[b]
-__global__ void k_max_abs(const double *__restrict__ phi, int n, int blk, int lg, int B, float *__restrict__ scale)
+// h^2 r = 4 pi G rho h^2 - (sum of the 6 neighbours - 6 Phi) on Omega, from
+// (n+4)^3 level blocks (blk = 1) or copied from a dense array (blk = 0).
+__global__ void k_resid_in(const double *__restrict__ rho, const double *__restrict__ phi,
+                           const double *__restrict__ resid, int n, int blk, int lg, int B,
+                           const double *__restrict__ frho, double *__restrict__ rh2)
 {
-    // one block per sample
-    __shared__ float red[kT / 32];
+    const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x) {
+        if (!blk) {
+            rh2[e] = resid[e];
+            continue;
+        }
+        const int b = e / V, v = e - b * V;
+        const int x = v & m, y = (v >> lg) & m, z = v >> (2 * lg);
+        const size_t q = (size_t)b * E * E * E + ((size_t)(z + 2) * E + y + 2) * E + x + 2;
+        const size_t s1 = 1, s2 = E, s3 = (size_t)E * E;
+        const double nb = phi[q - s1] + phi[q + s1] + phi[q - s2] + phi[q + s2] + phi[q - s3] + phi[q + s3];
+        rh2[e] = frho[b] * rho[q] - (nb - 6.0 * phi[q]);
+    }
+}
+
+// per sample: scale[2b] = max |Phi| on Omega, scale[2b+1] = max |h^2 r| (one block per sample)
+__global__ void k_scales(const double *__restrict__ phi, const double *__restrict__ rh2, int n, int blk, int lg,
+                         float *__restrict__ scale)
+{
+    __shared__ float red[2][kT / 32];
     const int b = blockIdx.x;
     const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
-    float mx = 0.f;
+    float mx = 0.f, mr = 0.f;
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
         const int x = v & m, y = (v >> lg) & m, z = v >> (2 * lg);
         const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + y + 2) * E + x + 2 : (size_t)b * V + v;
         mx = fmaxf(mx, fabsf((float)phi[q]));
+        mr = fmaxf(mr, fabsf((float)rh2[(size_t)b * V + v]));
     }
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = 16; o > 0; o >>= 1) {
         mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0)
-        red[threadIdx.x >> 5] = mx;
+        mr = fmaxf(mr, __shfl_down_sync(0xffffffffu, mr, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = mx;
+        red[1][threadIdx.x >> 5] = mr;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < kT / 32; w++)
-            s = fmaxf(s, red[w]);
-        scale[b] = s > 0.f ? s : 1.f;
+        float s = 0.f, sr = 0.f;
+        for (int w = 0; w < kT / 32; w++) {
+            s = fmaxf(s, red[0][w]);
+            sr = fmaxf(sr, red[1][w]);
+        }
+        scale[2 * b] = s > 0.f ? s : 1.f;
+        scale[2 * b + 1] = sr > 0.f ? sr : 1.f;
     }
 }
 
-__global__ void k_make_input(const double *__restrict__ rho, const double *__restrict__ phi, int n, int blk, int lg,
-                             int B, const double *__restrict__ frho, const float *__restrict__ scale,
-                             bf16 *__restrict__ x0)
+__global__ void k_make_input(const double *__restrict__ rho, const double *__restrict__ phi,
+                             const double *__restrict__ rh2, int n, int blk, int lg, int B,
+                             const double *__restrict__ frho, const float *__restrict__ scale, bf16 *__restrict__ x0)
 {
     const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x) {
         const int b = e / V, v = e - b * V;
         const int x = v & m, y = (v >> lg) & m, z = v >> (2 * lg);
         const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + y + 2) * E + x + 2 : (size_t)e;
-        const float s = scale[b];
+        const float s = scale[2 * b], sr = scale[2 * b + 1];
         bf16 *o = x0 + (size_t)e * 16;
         o[0] = __float2bfloat16_rn((float)(frho[b] * rho[q]) / s);
         o[1] = __float2bfloat16_rn((float)phi[q] / s);
-        for (int c = 2; c < 16; c++)
+        o[2] = __float2bfloat16_rn((float)rh2[e] / sr);
+        for (int c = 3; c < 16; c++)
             o[c] = __float2bfloat16_rn(0.f);
     }
 }
 
-// target of training: (phi_true - phi_interp) / s
-__global__ void k_make_target(const double *__restrict__ phi_t, const double *__restrict__ phi_i,
-                              const float *__restrict__ scale, int V, int B, float *__restrict__ tgt)
+// output scale of sample b: s_r n^2 / 16
+__device__ __forceinline__ double out_scale(const float *scale, int b, int n)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x)
-        tgt[e] = (float)((phi_t[e] - phi_i[e]) / scale[e / V]);
+    return (double)scale[2 * b + 1] * (double)n * (double)n / 16.0;
 }
 
-// Phi += s * y on Omega (block or dense layout)
+// training target: (phi_true - phi_interp) / out_scale
+__global__ void k_make_target(const double *__restrict__ phi_t, const double *__restrict__ phi_i,
+                              const float *__restrict__ scale, int n, int V, int B, float *__restrict__ tgt)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * V; e += gridDim.x * blockDim.x)
+        tgt[e] = (float)((phi_t[e] - phi_i[e]) / out_scale(scale, e / V, n));
+}
+
+// Phi += out_scale * y on Omega (block or dense layout)
 __global__ void k_apply(double *__restrict__ phi, int n, int blk, int lg, int B, const float *__restrict__ scale,
                         const float *__restrict__ y)
 {
@@ -447,7 +486,7 @@ __global__ void k_apply(double *__restrict__ phi, int n, int blk, int lg, int B,
         const int b = e / V, v = e - b * V;
         const int x = v & m, yy = (v >> lg) & m, z = v >> (2 * lg);
         const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + yy + 2) * E + x + 2 : (size_t)e;
-        phi[q] += (double)scale[b] * (double)y[e];
+        phi[q] += out_scale(scale, b, n) * (double)y[e];
     }
 }
 
@@ -466,7 +505,7 @@ struct Conv {
 };
 
 // the nine 3x3x3 convolutions, then the 1x1 output (16 weights + bias)
-const int kConvDims[9][2] = {{2, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64}, {128, 32}, {64, 16}, {32, 16}};
+const int kConvDims[9][2] = {{3, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64}, {128, 32}, {64, 16}, {32, 16}};
 
 int pad16(int c) { return (c + 15) / 16 * 16; }
 
@@ -483,7 +522,7 @@ struct mg_unet {
          *s2 = nullptr, *p2 = nullptr, *a3 = nullptr, *u2 = nullptr, *d2 = nullptr, *u1 = nullptr, *d1 = nullptr,
          *u0 = nullptr, *d0 = nullptr;
     float *y = nullptr, *tgt = nullptr, *scale = nullptr, *loss = nullptr, *gA = nullptr, *gB = nullptr, *gC = nullptr;
-    double *frho = nullptr;
+    double *frho = nullptr, *rh2 = nullptr;
     char *mem = nullptr;
     long step = 0;
     cudaStream_t stream = nullptr;
@@ -662,7 +701,7 @@ int mg_unet_create(int nmax, int bmax, unsigned long long seed, void *stream, mg
     if (!out)
         return 1;
     *out = nullptr;
-    if (nmax < 8 || (nmax & (nmax - 1)) || bmax < 1)
+    if (nmax < 8 || (nmax & (nmax - 1)) || bmax < 1 || bmax > 1024)
         return 1;
     mg_unet *u = new (std::nothrow) mg_unet();
     if (!u)
@@ -711,7 +750,8 @@ int mg_unet_create(int nmax, int bmax, unsigned long long seed, void *stream, mg
     A((void **)&u->d0, V0 * 16 * sizeof(bf16));
     A((void **)&u->y, V0 * sizeof(float));
     A((void **)&u->tgt, V0 * sizeof(float));
-    A((void **)&u->scale, 1024 * sizeof(float));
+    A((void **)&u->scale, 2048 * sizeof(float));
+    A((void **)&u->rh2, V0 * sizeof(double));
     A((void **)&u->loss, 256);
     A((void **)&u->frho, bmax * sizeof(double));
     A((void **)&u->gA, V0 * 32 * sizeof(float));
@@ -808,10 +848,10 @@ int mg_unet_get_grad(mg_unet *u, float *out)
 // Internal entry used by the solver and by the public calls: from (n+4)^3
 // blocks (blk = 1) or dense n^3 arrays (blk = 0) of B samples, predict y and
 // (apply = 1) add scale * y to phi on Omega.
-int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, double *phi, const double *frho_dev,
-                        int apply, void *stream)
+int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, double *phi, const double *resid,
+                        const double *frho_dev, int apply, void *stream)
 {
-    if (!u || B < 1 || B > u->bmax || n < 8 || n > u->nmax || (n & (n - 1)))
+    if (!u || B < 1 || B > u->bmax || n < 8 || n > u->nmax || (n & (n - 1)) || (!blk && !resid))
         return 1;
     cudaStream_t s = stream ? (cudaStream_t)stream : u->stream;
     cudaStream_t keep = u->stream;
@@ -822,8 +862,9 @@ int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, do
         u->stream = keep;
         return 3;
     }
-    k_max_abs<<<B, kT, 0, s>>>(phi, n, blk, lg, B, u->scale);
-    k_make_input<<<blocks_for(V0), kT, 0, s>>>(rho, phi, n, blk, lg, B, frho_dev, u->scale, u->x0);
+    k_resid_in<<<blocks_for(V0), kT, 0, s>>>(rho, phi, resid, n, blk, lg, B, frho_dev, u->rh2);
+    k_scales<<<B, kT, 0, s>>>(phi, u->rh2, n, blk, lg, u->scale);
+    k_make_input<<<blocks_for(V0), kT, 0, s>>>(rho, phi, u->rh2, n, blk, lg, B, frho_dev, u->scale, u->x0);
     cudaError_t e = forward(u, B, lg);
     if (!e && apply) {
         k_apply<<<blocks_for(V0), kT, 0, s>>>(phi, n, blk, lg, B, u->scale, u->y);
@@ -833,14 +874,14 @@ int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, do
     return e ? 3 : 0;
 }
 
-int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *phi_interp, const double *frho,
-                    float *y_out)
+int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *phi_interp, const double *resid,
+                    const double *frho, float *y_out)
 {
     if (!u || !frho || B > u->bmax)
         return 1;
     if (cudaMemcpyAsync(u->frho, frho, B * sizeof(double), cudaMemcpyHostToDevice, u->stream))
         return 3;
-    int r = mg_unet_predict_dev(u, B, n, 0, rho, const_cast<double *>(phi_interp), u->frho, 0, nullptr);
+    int r = mg_unet_predict_dev(u, B, n, 0, rho, const_cast<double *>(phi_interp), resid, u->frho, 0, nullptr);
     if (r)
         return r;
     const long V0 = (long)B * n * n * n;
@@ -851,7 +892,8 @@ int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *p
 }
 
 int mg_unet_train_step(mg_unet *u, int B, int n, const double *rho, const double *phi_interp,
-                       const double *phi_true, const double *frho, float lr, float wd, int update, float *loss_out)
+                       const double *resid, const double *phi_true, const double *frho, float lr, float wd, int update,
+                       float *loss_out)
 {
     if (!u || !frho || B > u->bmax || n < 8 || n > u->nmax || (n & (n - 1)))
         return 1;
@@ -860,10 +902,10 @@ int mg_unet_train_step(mg_unet *u, int B, int n, const double *rho, const double
     const int V0 = B << (3 * lg);
     if (cudaMemcpyAsync(u->frho, frho, B * sizeof(double), cudaMemcpyHostToDevice, s))
         return 3;
-    int r = mg_unet_predict_dev(u, B, n, 0, rho, const_cast<double *>(phi_interp), u->frho, 0, nullptr);
+    int r = mg_unet_predict_dev(u, B, n, 0, rho, const_cast<double *>(phi_interp), resid, u->frho, 0, nullptr);
     if (r)
         return r;
-    k_make_target<<<blocks_for(V0), kT, 0, s>>>(phi_true, phi_interp, u->scale, 1 << (3 * lg), B, u->tgt);
+    k_make_target<<<blocks_for(V0), kT, 0, s>>>(phi_true, phi_interp, u->scale, n, 1 << (3 * lg), B, u->tgt);
     k_fill<<<blocks_for(u->nparam), kT, 0, s>>>(u->grad, u->nparam, 0.f);
     k_fill<<<1, 32, 0, s>>>(u->loss, 1, 0.f);
     if (backward(u, B, lg))

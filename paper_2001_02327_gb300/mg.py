@@ -18,7 +18,7 @@ from . import build as _build
 MG_MAX_LEVELS = 8
 MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ESTATE, MG_ENOCONV, MG_EDIVERGED, MG_ETIMEOUT = range(8)
 MG_FP64, MG_MIXED = 0, 1
-MG_GUESS_INTERP, MG_GUESS_ZERO, MG_GUESS_USER = 0, 1, 2
+MG_GUESS_INTERP, MG_GUESS_ZERO, MG_GUESS_USER, MG_GUESS_LEARNED = 0, 1, 2, 3
 MG_FORCE_EQ2, MG_FORCE_CD2 = 0, 1
 
 

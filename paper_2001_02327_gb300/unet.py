@@ -19,12 +19,12 @@ _SIGS = {
     "mg_unet_set_params": (C.c_int, [_vp, _vp]),
     "mg_unet_get_grad": (C.c_int, [_vp, _vp]),
     "mg_unet_pack": (C.c_int, [_vp]),
-    "mg_unet_forward": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
-    "mg_unet_train_step": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_int,
-                                     C.POINTER(C.c_float)]),
-    "mg_unet_predict_dev": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
+    "mg_unet_forward": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "mg_unet_train_step": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_float, C.c_float,
+                                     C.c_int, C.POINTER(C.c_float)]),
+    "mg_unet_predict_dev": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "mg_set_unet": (C.c_int, [_vp, _vp]),
-    "mg_interp_guess": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    "mg_interp_guess": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(LIB, _name)
@@ -78,19 +78,21 @@ def mg_unet_pack(u):
     _ok(LIB.mg_unet_pack(u), "mg_unet_pack")
 
 
-def mg_unet_forward(u, B, n, rho, phi_interp, frho):
-    """rho, phi_interp: contiguous float64 CUDA tensors (B, n, n, n); frho: B floats."""
+def mg_unet_forward(u, B, n, rho, phi_interp, resid, frho):
+    """rho, phi_interp, resid: contiguous float64 CUDA tensors (B, n, n, n);
+    frho: B floats.  Returns y (B, n, n, n)."""
     fr = np.ascontiguousarray(frho, dtype=np.float64)
     y = np.zeros(B * n ** 3, dtype=np.float32)
-    _ok(LIB.mg_unet_forward(u, B, n, _mg._addr(rho), _mg._addr(phi_interp), fr.ctypes.data, y.ctypes.data),
-        "mg_unet_forward")
+    _ok(LIB.mg_unet_forward(u, B, n, _mg._addr(rho), _mg._addr(phi_interp), _mg._addr(resid), fr.ctypes.data,
+                            y.ctypes.data), "mg_unet_forward")
     return y.reshape((B, n, n, n))
 
 
-def mg_unet_train_step(u, B, n, rho, phi_interp, phi_true, frho, lr=1e-3, wd=0.0, update=True):
+def mg_unet_train_step(u, B, n, rho, phi_interp, resid, phi_true, frho, lr=1e-3, wd=0.0, update=True):
     fr = np.ascontiguousarray(frho, dtype=np.float64)
     loss = C.c_float(0.0)
-    _ok(LIB.mg_unet_train_step(u, B, n, _mg._addr(rho), _mg._addr(phi_interp), _mg._addr(phi_true),
+    _ok(LIB.mg_unet_train_step(u, B, n, _mg._addr(rho), _mg._addr(phi_interp), _mg._addr(resid),
+                               _mg._addr(phi_true),
                                fr.ctypes.data, float(lr), float(wd), 1 if update else 0, C.byref(loss)),
         "mg_unet_train_step")
     return float(loss.value)
@@ -100,12 +102,13 @@ def mg_set_unet(h, u):
     return _mg._check(h, LIB.mg_set_unet(h, u))
 
 
-def mg_interp_guess(h, b, level, out):
-    return _mg._check(h, LIB.mg_interp_guess(h, b, level, _mg._addr(out)))
+def mg_interp_guess(h, b, level, out, resid_out=None):
+    return _mg._check(h, LIB.mg_interp_guess(h, b, level, _mg._addr(out), _mg._addr(resid_out)))
 
 
-def mg_unet_predict_dev(u, B, n, blk, rho, phi, frho_dev, apply=True, stream=None):
-    """Solver-hook form: device arrays only (phi updated in place when apply)."""
+def mg_unet_predict_dev(u, B, n, blk, rho, phi, frho_dev, resid=None, apply=True, stream=None):
+    """Solver-hook form: device arrays only (phi updated in place when apply;
+    resid needed for dense layouts, blk = 0)."""
     st = stream.cuda_stream if (stream is not None and not isinstance(stream, int)) else stream
-    _ok(LIB.mg_unet_predict_dev(u, B, n, blk, _mg._addr(rho), _mg._addr(phi), _mg._addr(frho_dev),
+    _ok(LIB.mg_unet_predict_dev(u, B, n, blk, _mg._addr(rho), _mg._addr(phi), _mg._addr(resid), _mg._addr(frho_dev),
                                 1 if apply else 0, st), "mg_unet_predict_dev")

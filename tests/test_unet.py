@@ -16,7 +16,10 @@ def _sample(B, n, seed):
                     for c in rng.uniform(-0.2, 0.2, size=B)])
     tru = phi + 0.02 * np.sin(3 * x) * np.cos(2 * y) + 0.01 * rng.standard_normal((B, n, n, n))
     frho = rng.uniform(0.5, 2.0, size=B) * 0.01
-    return rho, phi, tru, frho
+    import torch
+    from oracle import unet_ref as R
+    res = R.residual_h2(torch.from_numpy(phi), torch.from_numpy(rho), frho).numpy()
+    return rho, phi, res, tru, frho
 
 
 # --------------------------------------------------------------------------
@@ -24,7 +27,9 @@ def _sample(B, n, seed):
 # --------------------------------------------------------------------------
 def test_reference_param_count():
     from oracle import unet_ref as R
-    assert R.param_count() == 367505
+    # nine 3x3x3 convolutions (3->16, 16->16, 16->32, 32->32, 32->64, 64->64,
+    # 128->32, 64->16, 32->16) with biases, then a 1x1 16->1 output
+    assert R.param_count() == 367937
 
 
 def test_reference_gradient_by_finite_differences():
@@ -32,18 +37,18 @@ def test_reference_gradient_by_finite_differences():
     from oracle import unet_ref as R
     rng = np.random.default_rng(3)
     p = rng.standard_normal(R.param_count()) * 0.2
-    rho, phi, tru, frho = _sample(1, 8, 0)
+    rho, phi, res, tru, frho = _sample(1, 8, 0)
     T = lambda a: torch.from_numpy(a)
-    L, g = R.loss_and_grad(p, T(rho), T(phi), T(tru), frho)
+    L, g = R.loss_and_grad(p, T(rho), T(phi), T(res), T(tru), frho)
     # parameters spread over the layers, including biases and the output layer
-    idx = [0, 100, 900, 9000, 30000, 60000, 150000, 250000, 330000, 367490, 367504]
+    idx = [0, 100, 900, 1295, 9000, 30000, 60000, 150000, 250000, 330000, 367920, 367936]
     for i in idx:
         e = 1e-4      # the loss is O(1e3): smaller steps lose digits to round-off
         pp, pm = p.copy(), p.copy()
         pp[i] += e
         pm[i] -= e
-        lp, _ = R.loss_and_grad(pp, T(rho), T(phi), T(tru), frho)
-        lm, _ = R.loss_and_grad(pm, T(rho), T(phi), T(tru), frho)
+        lp, _ = R.loss_and_grad(pp, T(rho), T(phi), T(res), T(tru), frho)
+        lm, _ = R.loss_and_grad(pm, T(rho), T(phi), T(res), T(tru), frho)
         fd = (lp - lm) / (2 * e)
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd)) + 1e-7, (i, fd, g[i])
 
@@ -74,10 +79,11 @@ def test_forward_matches_reference(un, n, B):
     u = un.mg_unet_create(16, 2, seed=7)
     try:
         p = un.mg_unet_get_params(u).astype(np.float64)
-        rho, phi, tru, frho = _sample(B, n, 1)
+        rho, phi, res, tru, frho = _sample(B, n, 1)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-        y = un.mg_unet_forward(u, B, n, dev(rho), dev(phi), frho)
-        yr, _ = R.forward(torch.from_numpy(p), torch.from_numpy(rho), torch.from_numpy(phi), frho)
+        y = un.mg_unet_forward(u, B, n, dev(rho), dev(phi), dev(res), frho)
+        T = torch.from_numpy
+        yr, _ = R.forward(T(p), T(rho), T(phi), T(res), frho)
         # BF16 operands with FP32 accumulation through nine layers
         assert _rel(y, yr.detach().numpy()) < 3e-2
     finally:
@@ -91,12 +97,12 @@ def test_gradient_matches_reference(un):
     u = un.mg_unet_create(16, 2, seed=11)
     try:
         p = un.mg_unet_get_params(u).astype(np.float64)
-        rho, phi, tru, frho = _sample(2, 16, 2)
+        rho, phi, res, tru, frho = _sample(2, 16, 2)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-        loss = un.mg_unet_train_step(u, 2, 16, dev(rho), dev(phi), dev(tru), frho, update=False)
+        loss = un.mg_unet_train_step(u, 2, 16, dev(rho), dev(phi), dev(res), dev(tru), frho, update=False)
         g = un.mg_unet_get_grad(u).astype(np.float64)
         T = lambda a: torch.from_numpy(a)
-        lr, gr = R.loss_and_grad(p, T(rho), T(phi), T(tru), frho)
+        lr, gr = R.loss_and_grad(p, T(rho), T(phi), T(res), T(tru), frho)
         assert abs(loss / lr - 1) < 3e-2
         off = 0
         for cin, cout in R.CONV_DIMS:
@@ -114,12 +120,12 @@ def test_training_reduces_loss(un):
     import torch
     u = un.mg_unet_create(16, 4, seed=5)
     try:
-        rho, phi, tru, frho = _sample(4, 16, 4)
+        rho, phi, res, tru, frho = _sample(4, 16, 4)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-        r, p_, t = dev(rho), dev(phi), dev(tru)
-        first = un.mg_unet_train_step(u, 4, 16, r, p_, t, frho, lr=2e-3, update=True)
+        r, p_, q, t = dev(rho), dev(phi), dev(res), dev(tru)
+        first = un.mg_unet_train_step(u, 4, 16, r, p_, q, t, frho, lr=2e-3, update=True)
         for _ in range(150):
-            last = un.mg_unet_train_step(u, 4, 16, r, p_, t, frho, lr=2e-3, update=True)
+            last = un.mg_unet_train_step(u, 4, 16, r, p_, q, t, frho, lr=2e-3, update=True)
         assert last < 0.5 * first, (first, last)
     finally:
         un.mg_unet_destroy(u)
@@ -155,8 +161,10 @@ def test_learned_guess_in_solver_keeps_accuracy(un):
                     out.append((phi.cpu().numpy(), st[0][l]["rel_res"]))
                 if mode == mg.MG_GUESS_INTERP:
                     g = torch.zeros((32,) * 3, dtype=torch.float64, device="cuda")
-                    un.mg_interp_guess(h, 0, 1, g)
+                    r = np.zeros((32,) * 3)
+                    un.mg_interp_guess(h, 0, 1, g, r)
                     res["guess1"] = g.cpu().numpy()
+                    res["resid1"] = r
                 res[mode] = out
             finally:
                 mg.mg_destroy(h)
@@ -168,3 +176,16 @@ def test_learned_guess_in_solver_keeps_accuracy(un):
     # the exported guess is the parent solution interpolated: close to the level's solution
     sol1 = res[mg.MG_GUESS_INTERP][1][0]
     assert _rel(res["guess1"], sol1) < 0.05
+    # the exported residual is that of the guess: on cells away from the
+    # buffer ring it equals the 7-point residual of the dense guess array
+    from oracle import unet_ref as R
+    g = res["guess1"]
+    h1 = H.h(1)
+    fr = [4 * np.pi * H.G * h1 * h1]
+    rr = R.residual_h2(torch.from_numpy(g[None]), torch.from_numpy(inp[1]["rho"][None]), fr).numpy()[0]
+    inner = (slice(1, -1),) * 3
+    assert np.abs(res["resid1"][inner] - rr[inner]).max() <= 1e-12 * max(np.abs(rr).max(), 1e-30) + 1e-15
+    # and vanishes (to round-off) for the converged solution: it is a real residual
+    assert np.abs(rr[inner]).max() > 1e3 * np.abs(R.residual_h2(torch.from_numpy(sol1[None]),
+                                                               torch.from_numpy(inp[1]["rho"][None]), fr)
+                                                  .numpy()[0][inner]).max()
