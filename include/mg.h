@@ -65,6 +65,16 @@ enum { MG_GUESS_INTERP = 0,  /* initial potential interpolated from the parent (
 enum { MG_FORCE_EQ2 = 0,     /* fourth-order difference of Eq. 2 (default) */
        MG_FORCE_CD2 = 1 };   /* two-point central difference */
 
+/* Treatment of the buffer rings of levels l > 0. */
+enum { MG_IFACE_BUFFER = 0,  /* Sec. 2.1 (default): the outer ring holds potential
+                                interpolated from level l-1, the inner ring holds
+                                interpolated density and its potential is solved
+                                together with the patch (M = n + 2 active cells) */
+       MG_IFACE_FROZEN = 1 };/* the scheme Sec. 4 and Fig. 4 compare against, as an
+                                ablation: both rings hold interpolated potential and
+                                multigrid solves Omega alone with the inner ring as
+                                its Dirichlet boundary (M = n active cells) */
+
 /* Geometry of one hierarchy (Sec. 2.1).  Level l has n[l] cells per edge
  * (>= 2; even above level 0; at most 1286 in 3D), lower corner lo[l] and
  * cell size h0 / 2^l.  For l > 0 the
@@ -92,6 +102,7 @@ typedef struct {
     int inner_cycles;    /* MIXED: FP32 V-cycles per FP64 defect-correction step (>= 1) */
     int guess;           /* MG_GUESS_* for levels > 0 (level 0 starts from zero, or USER) */
     int force_stencil;   /* MG_FORCE_EQ2 | MG_FORCE_CD2 */
+    int interface;       /* MG_IFACE_BUFFER | MG_IFACE_FROZEN */
     void *stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
 } mg_options;
 

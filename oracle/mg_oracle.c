@@ -309,8 +309,30 @@ static void vcycle(int dim, int nL, const or_mglev *lv, double **phi, double **f
  *   max_cycles.  hist[c] receives that ratio after c cycles (hist[0] for the
  *   initial guess; max_cycles+1 entries).  Returns the cycles performed.
  * ------------------------------------------------------------------------- */
+void or_forces(int dim, int n, double h, const double *phi, double *F, int stencil);
+
+/* max over Omega of |F_a - F_b| (Euclidean length of the difference vector) */
+static double max_force_change(int dim, long nd, const double *Fa, const double *Fb)
+{
+    double m = 0.0;
+    for (long p = 0; p < nd; p++) {
+        double s = 0.0;
+        for (int a = 0; a < dim; a++) {
+            double d = Fa[(long)a * nd + p] - Fb[(long)a * nd + p];
+            s += d * d;
+        }
+        if (s > m)
+            m = s;
+    }
+    return sqrt(m);
+}
+
+/* Stopping rules: stop = 0 -- ||b - A Phi||_2 / ||b||_2 < tol over Gamma;
+ * stop = 1 -- the convergence test of Sec. 3.1/3.2: the acceleration on Omega
+ * (force stencil `stencil`) changes by less than tol between two cycles,
+ * measured as the largest length of the change vector over the cells. */
 int or_level_solve(int dim, int n, double h, double *phi, const double *rho, double fourpiG,
-                   int nu_pre, int nu_post, int max_cycles, double rel_tol, double *hist)
+                   int nu_pre, int nu_post, int max_cycles, double rel_tol, double *hist, int stop, int stencil)
 {
     or_mglev lv[OR_MAX_MG];
     int nL;
@@ -346,6 +368,14 @@ int or_level_solve(int dim, int n, double h, double *phi, const double *rho, dou
 
     residual(dim, &lv[0], phi, fs[0], r);
     double rel = bnorm > 0.0 ? norm2_active(dim, M, r) / bnorm : 0.0;
+    const long nd = cells(dim, n);
+    double *Fp = 0, *Fc = 0;
+    if (stop == 1) {
+        Fp = (double *)calloc((size_t)dim * nd, sizeof(double));
+        Fc = (double *)calloc((size_t)dim * nd, sizeof(double));
+        or_forces(dim, n, h, phi, Fp, stencil);
+        rel = HUGE_VAL;                 /* no previous iterate: at least one cycle */
+    }
     if (hist)
         hist[0] = rel;
     int c = 0;
@@ -355,11 +385,21 @@ int or_level_solve(int dim, int n, double h, double *phi, const double *rho, dou
         else
             smooth(dim, &lv[0], phis[0], fs[0], nu_pre + nu_post);
         c++;
-        residual(dim, &lv[0], phi, fs[0], r);
-        rel = norm2_active(dim, M, r) / bnorm;
+        if (stop == 1) {
+            or_forces(dim, n, h, phi, Fc, stencil);
+            rel = max_force_change(dim, nd, Fc, Fp);
+            double *t = Fp;
+            Fp = Fc;
+            Fc = t;
+        } else {
+            residual(dim, &lv[0], phi, fs[0], r);
+            rel = norm2_active(dim, M, r) / bnorm;
+        }
         if (hist)
             hist[c] = rel;
     }
+    free(Fp);
+    free(Fc);
     free(r);
     free(fs[0]);
     for (int L = 1; L < nL; L++) {

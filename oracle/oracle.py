@@ -49,7 +49,7 @@ def lib():
         L.or_mg_sizes.argtypes = [C.c_int, ip, C.c_int]
         L.or_mg_sizes.restype = C.c_int
         L.or_level_solve.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, C.c_double,
-                                     C.c_int, C.c_int, C.c_int, C.c_double, dp]
+                                     C.c_int, C.c_int, C.c_int, C.c_double, dp, C.c_int, C.c_int]
         L.or_level_solve.restype = C.c_int
         L.or_residual_norm.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, C.c_double]
         L.or_residual_norm.restype = C.c_double
@@ -72,11 +72,15 @@ def mg_sizes(M):
     return [int(v) for v in buf[:k]]
 
 
-def level_solve(dim, n, h, phi, rho, fourpiG, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10):
-    """Solve one refinement level in place; returns (cycles, residual history)."""
+def level_solve(dim, n, h, phi, rho, fourpiG, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10, stop=0,
+                stencil=0):
+    """Solve one refinement level in place; returns (cycles, history of the
+    stopping quantity).  stop=0: relative residual over Gamma; stop=1: the
+    largest change of the acceleration on Omega between cycles (Sec. 3)."""
     assert phi.shape == (n + 4,) * dim and rho.shape == (n + 4,) * dim
     hist = np.zeros(max_cycles + 1, dtype=np.float64)
-    c = lib().or_level_solve(dim, n, h, phi, rho, fourpiG, nu_pre, nu_post, max_cycles, rel_tol, hist)
+    c = lib().or_level_solve(dim, n, h, phi, rho, fourpiG, nu_pre, nu_post, max_cycles, rel_tol, hist, stop,
+                             stencil)
     return c, hist[:c + 1]
 
 
@@ -114,13 +118,26 @@ def pad_into(block, interior, width):
 
 
 def solve_hierarchy(H, inputs, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10, guess="interp",
-                    force_stencil=0):
+                    force_stencil=0, interface="buffer", stop="residual"):
     """Solve a nested hierarchy coarse to fine.
 
     ``inputs`` is the per-level list from ``inputs.level_inputs``.  Returns a
     list of dicts with ``phi`` ((n+4)^d block after the solve), ``rho``
     ((n+4)^d block actually used), ``F`` ((dim, n^d)), ``cycles``, ``hist``.
+
+    ``interface="buffer"`` is the method of Sec. 2.1: the inner buffer ring is
+    solved with the patch.  ``interface="frozen"`` is the scheme Sec. 4 and
+    Fig. 4 compare against: on levels l > 0 both buffer rings hold potential
+    linearly interpolated from level l-1, and multigrid solves Omega alone
+    with the inner ring as its Dirichlet boundary (M = n active cells).
+
+    ``stop="residual"`` ends a level when ||b - A Phi|| / ||b|| < rel_tol;
+    ``stop="force"`` when the acceleration on Omega changes by less than
+    rel_tol between cycles (the test of Sec. 3.1 and 3.2).
     """
+    assert interface in ("buffer", "frozen") and stop in ("residual", "force")
+    assert not (interface == "frozen" and stop == "force")
+    sflag = 1 if stop == "force" else 0
     dim = H.dim
     fourpiG = 4.0 * pi * H.G
     out = []
@@ -140,7 +157,21 @@ def solve_hierarchy(H, inputs, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10
             interface_fill(dim, H.n[l - 1], P["phi"], P["rho"], n, H.offset(l), phi, rho,
                            guess=(guess == "interp"))
         pad_into(rho, inputs[l]["rho"], 2)
-        cyc, hist = level_solve(dim, n, h, phi, rho, fourpiG, nu_pre, nu_post, max_cycles, rel_tol)
+        if l > 0 and interface == "frozen":
+            # inner-ring potential by the same linear interpolation as the outer ring
+            ring_phi, ring_rho = np.zeros_like(phi), np.zeros_like(rho)
+            interface_fill(dim, H.n[l - 1], P["phi"], P["rho"], n, H.offset(l), ring_phi, ring_rho, guess=True)
+            gam = tuple(slice(1, n + 3) for _ in range(dim))
+            om = tuple(slice(2, n + 2) for _ in range(dim))
+            keep = phi[om].copy()
+            phi[gam] = ring_phi[gam]
+            phi[om] = keep
+            sub_phi, sub_rho = phi[gam].copy(), rho[gam].copy()
+            cyc, hist = level_solve(dim, n - 2, h, sub_phi, sub_rho, fourpiG, nu_pre, nu_post, max_cycles, rel_tol)
+            phi[gam] = sub_phi
+        else:
+            cyc, hist = level_solve(dim, n, h, phi, rho, fourpiG, nu_pre, nu_post, max_cycles, rel_tol, sflag,
+                                    force_stencil)
         F = forces(dim, n, h, phi, force_stencil)
         out.append({"phi": phi, "rho": rho, "F": F, "cycles": cyc, "hist": hist})
     return out

@@ -26,8 +26,12 @@ struct LevelData {
     int off[3] = {0, 0, 0};
     double h = 0.0;
     MgGeom g[MG_MAX_MG];
-    double *phi[MG_MAX_MG] = {};   // phi[0]: the (n+4)^d level block
-    double *f[MG_MAX_MG] = {};     // f[0]:   4 pi G rho on the same block
+    double *phi[MG_MAX_MG] = {};   // multigrid level arrays, (N^L+2)^d
+    double *f[MG_MAX_MG] = {};
+    double *blk = nullptr;         // the (n+4)^d level block of potential ...
+    double *fblk = nullptr;        // ... and of 4 pi G rho; phi[0] / f[0] themselves
+                                   // except on frozen-interface levels
+    bool frozen = false;           // MG_IFACE_FROZEN level: multigrid on Omega only
     float *phi32[MG_MAX_MG] = {};  // mixed precision correction, all multigrid levels
     float *phi32b[MG_MAX_MG] = {}; // second FP32 buffer of the temporally blocked levels
     int tile[MG_MAX_MG] = {};      // FP32 temporal-blocking tile per level (0: one kernel per phase)
@@ -117,7 +121,7 @@ int level_sizes(int M, int *N, int cap)
 void build_geometry(LevelData &ld, int dim)
 {
     int N[MG_MAX_MG];
-    ld.M = ld.n + 2;
+    ld.M = ld.frozen ? ld.n : ld.n + 2;
     ld.nmg = level_sizes(ld.M, N, MG_MAX_MG);
     (void)dim;
     for (int L = 0; L < ld.nmg; L++) {
@@ -308,7 +312,8 @@ mg_status check_options(const mg_options &o)
     if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 || !(o.rel_tol >= 0.0) ||
         (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 ||
         o.guess < MG_GUESS_INTERP || o.guess > MG_GUESS_LEARNED ||
-        (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2))
+        (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2) ||
+        (o.interface != MG_IFACE_BUFFER && o.interface != MG_IFACE_FROZEN))
         return MG_EINVAL;
     return MG_OK;
 }
@@ -460,23 +465,38 @@ cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
         const int gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
         const double by = 8.0 * cells_d(ld.n + 4, dim) + 16.0 * (cells_d(ld.n + 2, dim) - cells_d(ld.n, dim));
         e = timed(h, KK_IFACE, by, [&] {
-            return mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2],
-                                       ld.phi[0], ld.rho, ld.f[0], fourpiG, gmode, ld.guess, s);
+            return mg_launch_interface(dim, pd.n, pd.blk, pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2], ld.blk,
+                                       ld.rho, ld.fblk, fourpiG, gmode, ld.guess, ld.frozen, s);
         });
         if (e)
             return e;
         if (o.guess == MG_GUESS_LEARNED && h->unet && dim == 3 && (ld.n & (ld.n - 1)) == 0) {
             // network correction of the interpolated potential on Omega
-            const int r = mg_unet_predict_dev(h->unet, 1, ld.n, 1, ld.rho, ld.phi[0], nullptr,
+            const int r = mg_unet_predict_dev(h->unet, 1, ld.n, 1, ld.rho, ld.blk, nullptr,
                                               h->frho + (size_t)b * MG_MAX_LEVELS + l, 1, s);
             if (r == 3)
                 return cudaErrorLaunchFailure;
         }
+        if (ld.frozen) {
+            // the (n+2)^d box of Omega and the inner ring into the multigrid arrays
+            if ((e = mg_launch_copy_box(dim, ld.n + 2, ld.blk, ld.n + 4, 1, ld.phi[0], ld.n + 2, 0, s)) ||
+                (e = mg_launch_copy_box(dim, ld.n + 2, ld.fblk, ld.n + 4, 1, ld.f[0], ld.n + 2, 0, s)))
+                return e;
+        }
     } else if (ld.guess_set) {
-        if ((e = mg_launch_copy_guess(dim, ld.n, ld.guess, ld.phi[0], s)))
+        if ((e = mg_launch_copy_guess(dim, ld.n, ld.guess, ld.blk, s)))
             return e;
     }
     return norms(h, ld, 3, ds, s, branch);
+}
+
+// After the iterations of a frozen-interface level: Omega back into the level block.
+cudaError_t level_epilogue(mg_hierarchy *h, int b, int l, cudaStream_t s)
+{
+    const LevelData &ld = h->lev[b][l];
+    if (!ld.frozen)
+        return cudaSuccess;
+    return mg_launch_copy_box(h->dim, ld.n, ld.phi[0], ld.n + 2, 1, ld.blk, ld.n + 4, 2, s);
 }
 
 // One iteration of a level's loop (Sec. 2.3 step 14): an FP64 V-cycle, or in
@@ -546,6 +566,7 @@ mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
         if (!std::isfinite(c.rel))
             c.status = 1;
     }
+    CK(h, level_epilogue(h, b, l, s));
     fill_stats(h, c, st);
     return (mg_status)st->status;
 }
@@ -615,7 +636,9 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
                                 o.max_cycles, hc, h->body_stream);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(h->body_stream, &out);
-    return eb ? eb : e;
+    if (eb || e)
+        return eb ? eb : e;
+    return level_epilogue(h, b, l, s);
 }
 
 // Plan of the batched mixed-precision solve: per refinement level the parts
@@ -909,7 +932,7 @@ mg_status build_graph(mg_hierarchy *h)
             CK(h, cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
     }
     h->batched = false;
-    if (h->opt.precision == MG_MIXED && h->batch > 1) {
+    if (h->opt.precision == MG_MIXED && h->batch > 1 && h->opt.interface == MG_IFACE_BUFFER) {
         // measured on 64 uneven hierarchies: graph branches 105 ms, batched
         // launches 143 ms (each batched block first loads its part's
         // descriptor); MG_BATCHED=1 selects the batched launches
@@ -1178,6 +1201,7 @@ mg_status mg_default_options(mg_options *opt)
     opt->inner_cycles = 3;
     opt->guess = MG_GUESS_INTERP;
     opt->force_stencil = MG_FORCE_EQ2;
+    opt->interface = MG_IFACE_BUFFER;
     opt->stream = nullptr;
     return MG_OK;
 }
@@ -1259,6 +1283,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
             LevelData &ld = h->lev[b][l];
             ld.n = d.n[l];
             ld.h = d.h0 / (double)(1L << l);
+            ld.frozen = l > 0 && o.interface == MG_IFACE_FROZEN;
             if (l > 0) {
                 const double hp = d.h0 / (double)(1L << (l - 1));
                 for (int a = 0; a < dim; a++)
@@ -1278,6 +1303,10 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
             for (int L = 1; L < ld.nmg; L++) {
                 slots.push_back({(void **)&ld.tab64[L], align256(128 * sizeof(double))});
                 slots.push_back({(void **)&ld.tab32[L], align256(128 * sizeof(float))});
+            }
+            if (ld.frozen) {
+                slots.push_back({(void **)&ld.blk, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
+                slots.push_back({(void **)&ld.fblk, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
             }
             slots.push_back({(void **)&ld.rho, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
             slots.push_back({(void **)&ld.guess, align256((size_t)cells(ld.n + 2, dim) * sizeof(double))});
@@ -1306,6 +1335,12 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
         *sl.dst = h->arena + pos;
         pos += sl.bytes;
     }
+    for (auto &hl : h->lev)
+        for (auto &ld : hl)
+            if (!ld.frozen) {
+                ld.blk = ld.phi[0];
+                ld.fblk = ld.f[0];
+            }
     e = cudaMallocHost((void **)&h->hscal, (size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double));
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&h->hctl, (size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl));
@@ -1407,7 +1442,7 @@ mg_status mg_set_density(mg_hierarchy *h, int b, int level, const double *rho, c
     }
     const double fourpiG = 4.0 * M_PI * h->desc[b].G;
     CK(h, timed(h, KK_SETDENS, 24.0 * (double)nr, [&] {
-           return mg_launch_set_density(dim, ld.n, d_rho, d_bcr, d_bcp, ld.rho, ld.f[0], ld.phi[0], fourpiG,
+           return mg_launch_set_density(dim, ld.n, d_rho, d_bcr, d_bcp, ld.rho, ld.fblk, ld.blk, fourpiG,
                                         h->stream);
        }));
     if (d_rho == stage || d_bcr == stage + np || d_bcp == stage + 2 * np)
@@ -1493,7 +1528,7 @@ mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *
             dP = h->stage + (size_t)dim * nr;
     }
     CK(h, timed(h, KK_FORCES, 8.0 * (cells_d(ld.n + 4, dim) + (dim + 1) * (double)nr), [&] {
-           return mg_launch_forces(dim, ld.n, ld.h, ld.phi[0], dF, dP, h->opt.force_stencil, h->stream);
+           return mg_launch_forces(dim, ld.n, ld.h, ld.blk, dF, dP, h->opt.force_stencil, h->stream);
        }));
     bool sync = false;
     if (F_out && !F_dev) {
@@ -1576,8 +1611,8 @@ mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out, double
     // the interface rewrites the inner-ring density and f with the values it
     // already holds; the potential goes to the staging block
     const double fourpiG = 4.0 * M_PI * h->desc[b].G;
-    CK(h, mg_launch_interface(dim, pd.n, pd.phi[0], pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2], blk, ld.rho,
-                              ld.f[0], fourpiG, 0, nullptr, h->stream));
+    CK(h, mg_launch_interface(dim, pd.n, pd.blk, pd.rho, ld.n, ld.off[0], ld.off[1], ld.off[2], blk, ld.rho,
+                              ld.fblk, fourpiG, 0, nullptr, ld.frozen, h->stream));
     const bool dev = is_device_ptr(out);
     CK(h, mg_launch_extract(dim, ld.n, blk, dev ? out : dense, h->stream));
     if (!dev)
@@ -1604,6 +1639,8 @@ mg_status mg_autotune(mg_hierarchy *h, const char *cache_path)
     std::vector<TuneEntry> fresh;
     for (int b = 0; b < h->batch; b++)
         for (auto &ld : h->lev[b]) {
+            if (ld.frozen)
+                continue;             // the ablation keeps the default plan
             const TuneEntry *hit = nullptr;
             for (auto *v : {&cache, &fresh})
                 for (auto &te : *v)

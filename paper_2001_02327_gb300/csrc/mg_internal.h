@@ -135,7 +135,7 @@ cudaError_t mg_launch_set_density(int dim, int n, const double *rho, const doubl
 // interpolation, 1: zero, 2: copy of guess_src ((nc+2)^d)).
 cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const double *rho_p, int nc, int ox, int oy,
                                 int oz, double *phi_c, double *rho_c, double *f_c, double fourpiG, int guess,
-                                const double *guess_src, cudaStream_t s);
+                                const double *guess_src, int frozen, cudaStream_t s);
 cudaError_t mg_launch_copy_guess(int dim, int n, const double *guess_src, double *phi_blk, cudaStream_t s);
 
 // Forces F = -grad(Phi) on Omega ((n+4)^d block in, dim * n^d out) and the
@@ -145,6 +145,8 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
 
 cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s);
 cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cudaStream_t s);
+cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os, double *dst, int Ed, int od,
+                              cudaStream_t s);
 cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const double *rho_blk, double frho,
                                double *out, cudaStream_t s);
 

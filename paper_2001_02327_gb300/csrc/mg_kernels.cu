@@ -1026,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
                                                         const double *__restrict__ rho_p, int nc, int ox, int oy, int oz,
                                                         double *__restrict__ phi_c, double *__restrict__ rho_c,
                                                         double *__restrict__ f_c, double fourpiG, int guess,
-                                                        const double *__restrict__ guess_src)
+                                                        const double *__restrict__ guess_src, int frozen)
 {
     const int E = nc + 4, Ep = np + 4;
     const int total = E * E * (DIM == 3 ? E : 1);
@@ -1056,6 +1056,11 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
             const double rv = interp<DIM>(rho_p, Ep, p0, w);
             rho_c[t] = rv;
             f_c[t] = fourpiG * rv;
+            if (frozen) {
+                // frozen-interface ablation: interpolated potential held fixed
+                phi_c[t] = interp<DIM>(phi_p, Ep, p0, w);
+                continue;
+            }
         }
         if (guess == 0)
             phi_c[t] = interp<DIM>(phi_p, Ep, p0, w);
@@ -1063,6 +1068,21 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
             phi_c[t] = 0.0;
         else
             phi_c[t] = guess_src[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+    }
+}
+
+// dst[c + od] = src[c + os] for the c-box [0, e)^d, arrays of edges Es / Ed
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_copy_box(int e, const double *__restrict__ src, int Es, int os,
+                                                       double *__restrict__ dst, int Ed, int od)
+{
+    const int total = e * e * (DIM == 3 ? e : 1);
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / e;
+        const int i = t - r * e;
+        const int j = DIM == 3 ? r % e : r;
+        const int k = DIM == 3 ? r / e : 0;
+        dst[lin<DIM>(i + od, j + od, DIM == 3 ? k + od : 0, Ed)] = src[lin<DIM>(i + os, j + os, DIM == 3 ? k + os : 0, Es)];
     }
 }
 
@@ -1657,15 +1677,15 @@ cudaError_t mg_launch_set_density(int dim, int n, const double *rho, const doubl
 
 cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const double *rho_p, int nc, int ox, int oy,
                                 int oz, double *phi_c, double *rho_c, double *f_c, double fourpiG, int guess,
-                                const double *guess_src, cudaStream_t s)
+                                const double *guess_src, int frozen, cudaStream_t s)
 {
     const int grid = grid_for(cube(nc + 4, dim));
     if (dim == 3)
         k_interface<3><<<grid, kThreads, 0, s>>>(np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
-                                                 guess_src);
+                                                 guess_src, frozen);
     else
         k_interface<2><<<grid, kThreads, 0, s>>>(np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
-                                                 guess_src);
+                                                 guess_src, frozen);
     return cudaGetLastError();
 }
 
@@ -1711,6 +1731,17 @@ cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cu
         k_extract<3><<<grid, kThreads, 0, s>>>(n, blk, out);
     else
         k_extract<2><<<grid, kThreads, 0, s>>>(n, blk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os, double *dst, int Ed, int od,
+                              cudaStream_t s)
+{
+    const int grid = grid_for(cube(e, dim));
+    if (dim == 3)
+        k_copy_box<3><<<grid, kThreads, 0, s>>>(e, src, Es, os, dst, Ed, od);
+    else
+        k_copy_box<2><<<grid, kThreads, 0, s>>>(e, src, Es, os, dst, Ed, od);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,40 @@ def test_hierarchy_zero_guess(mg, oracle, guess):
     check_parity(H, g, ref)
 
 
+# --------------------------------------------------------------------------
+# frozen-interface ablation (the scheme Sec. 4 compares against)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("make", [lambda: I.config_2d_disk(64, 3), lambda: I.config_3d_offset_sphere(32, 4),
+                                  lambda: I.random_hierarchy(5)])
+def test_frozen_interface_fixed_cycles(mg, oracle, make):
+    H = make()
+    inp = I.level_inputs(H)
+    _, g = gpu_solve(mg, H, inp, max_cycles=3, rel_tol=0.0, interface=mg.MG_IFACE_FROZEN)
+    ref = oracle.solve_hierarchy(H, inp, 2, 1, 3, 0.0, interface="frozen")
+    check_parity(H, g, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_frozen_interface_converged(mg, oracle, precision):
+    """Converged frozen-interface solve: same cycle counts (FP64) and results
+    as the oracle, and really different from the buffer-ring method."""
+    H = I.config_3d_offset_sphere(32, 3)
+    inp = I.level_inputs(H)
+    p = mg.MG_FP64 if precision == "fp64" else mg.MG_MIXED
+    kw = dict(nu_pre=2, nu_post=2, max_cycles=60, rel_tol=1e-10, allow_noconv=False, precision=p)
+    _, g = gpu_solve(mg, H, inp, interface=mg.MG_IFACE_FROZEN, **kw)
+    _, gb = gpu_solve(mg, H, inp, **kw)
+    ref = oracle.solve_hierarchy(H, inp, 2, 2, 60, 1e-10, interface="frozen")
+    for l in range(H.num_levels):
+        assert g[l]["rel_res"] < 1e-10
+        if p == mg.MG_FP64:
+            assert g[l]["cycles"] == ref[l]["cycles"], (l, g[l]["cycles"], ref[l]["cycles"])
+    check_parity(H, g, ref, tol=TOL if p == mg.MG_FP64 else 1e-8)
+    assert relmax(g[0]["phi"], gb[0]["phi"]) == 0.0          # level 0 has no interface
+    for l in range(1, H.num_levels):
+        assert relmax(g[l]["phi"], gb[l]["phi"]) > 1e-6
+
+
 def test_full_size_config_fixed_cycles(mg, oracle):
     """The benchmark workload (4 nested 64^3 levels), element by element."""
     H = I.config_3d_offset_sphere(64, 4)
