@@ -65,6 +65,15 @@ enum { MG_GUESS_INTERP = 0,  /* initial potential interpolated from the parent (
 enum { MG_FORCE_EQ2 = 0,     /* fourth-order difference of Eq. 2 (default) */
        MG_FORCE_CD2 = 1 };   /* two-point central difference */
 
+/* When a level stops iterating (besides max_cycles). */
+enum { MG_STOP_RESIDUAL = 0, /* ||b - A Phi||_2 / ||b||_2 < rel_tol over Gamma (default) */
+       MG_STOP_FORCE = 1 };  /* the test of Sec. 3.1 / 3.2: the acceleration on Omega
+                                (force_stencil) changes by less than rel_tol between
+                                two iterations, measured as the largest length of the
+                                change vector over the cells; at least one iteration.
+                                mg_level_stats.rel_res then holds that change.  Only
+                                with MG_IFACE_BUFFER. */
+
 /* Treatment of the buffer rings of levels l > 0. */
 enum { MG_IFACE_BUFFER = 0,  /* Sec. 2.1 (default): the outer ring holds potential
                                 interpolated from level l-1, the inner ring holds
@@ -103,6 +112,7 @@ typedef struct {
     int guess;           /* MG_GUESS_* for levels > 0 (level 0 starts from zero, or USER) */
     int force_stencil;   /* MG_FORCE_EQ2 | MG_FORCE_CD2 */
     int interface;       /* MG_IFACE_BUFFER | MG_IFACE_FROZEN */
+    int stop;            /* MG_STOP_RESIDUAL | MG_STOP_FORCE */
     void *stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
 } mg_options;
 
@@ -235,7 +245,8 @@ int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap);
  *         potential and the solved region the initial guess; on return the
  *         solved region holds the solution.
  *   h, G  cell size and gravitational constant; opt as for mg_solve (NULL =
- *         defaults); precision must be MG_FP64; opt->stream is used.
+ *         defaults); precision must be MG_FP64 and stop MG_STOP_RESIDUAL;
+ *         opt->stream is used.
  *   stats host, may be NULL.
  * Working memory is one library-owned device array of 4 MiB (every GPU that
  * loads the library holds it until the process exits): n <= 64 in 3D and

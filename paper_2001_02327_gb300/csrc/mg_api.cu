@@ -32,6 +32,7 @@ struct LevelData {
     double *fblk = nullptr;        // ... and of 4 pi G rho; phi[0] / f[0] themselves
                                    // except on frozen-interface levels
     bool frozen = false;           // MG_IFACE_FROZEN level: multigrid on Omega only
+    double *prev = nullptr;        // MG_STOP_FORCE: the (n+4)^d block before the iteration
     float *phi32[MG_MAX_MG] = {};  // mixed precision correction, all multigrid levels
     float *phi32b[MG_MAX_MG] = {}; // second FP32 buffer of the temporally blocked levels
     int tile[MG_MAX_MG] = {};      // FP32 temporal-blocking tile per level (0: one kernel per phase)
@@ -180,6 +181,7 @@ struct mg_hierarchy {
     size_t stage_elems = 0;
     double *partials = nullptr;     // MG_BRANCHES * 2 * MG_NORM_BLOCKS_MAX reduction scratch
     unsigned *counters = nullptr;   // MG_BRANCHES block counters of the norm kernel
+    unsigned long long *fmax = nullptr; // MG_BRANCHES maxima of the force-change test
     double *scal = nullptr;         // device scalars: [b][l][2] = ||b||^2, ||r||^2
     double *hscal = nullptr;        // pinned mirror
     MgSolveCtl *ctl = nullptr;      // device loop state per (b, l)
@@ -313,7 +315,9 @@ mg_status check_options(const mg_options &o)
         (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 ||
         o.guess < MG_GUESS_INTERP || o.guess > MG_GUESS_LEARNED ||
         (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2) ||
-        (o.interface != MG_IFACE_BUFFER && o.interface != MG_IFACE_FROZEN))
+        (o.interface != MG_IFACE_BUFFER && o.interface != MG_IFACE_FROZEN) ||
+        (o.stop != MG_STOP_RESIDUAL && o.stop != MG_STOP_FORCE) ||
+        (o.stop == MG_STOP_FORCE && o.interface != MG_IFACE_BUFFER))
         return MG_EINVAL;
     return MG_OK;
 }
@@ -487,7 +491,11 @@ cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
         if ((e = mg_launch_copy_guess(dim, ld.n, ld.guess, ld.blk, s)))
             return e;
     }
-    return norms(h, ld, 3, ds, s, branch);
+    if ((e = norms(h, ld, 3, ds, s, branch)))
+        return e;
+    if (o.stop == MG_STOP_FORCE)
+        e = mg_launch_force_stop(0, dim, ld.n, ld.h, nullptr, nullptr, 0, nullptr, ds, s);
+    return e;
 }
 
 // After the iterations of a frozen-interface level: Omega back into the level block.
@@ -508,6 +516,10 @@ cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int b
     const int dim = h->dim;
     const mg_options &o = h->opt;
     cudaError_t e;
+    unsigned long long *cmax = h->fmax + branch;
+    if (o.stop == MG_STOP_FORCE &&
+        (e = mg_launch_force_stop(1, dim, ld.n, ld.h, ld.blk, ld.prev, 0, cmax, nullptr, s)))
+        return e;
     if (o.precision != MG_MIXED) {
         if ((e = vcycle(h, ld, false, s)))
             return e;
@@ -525,6 +537,8 @@ cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int b
         if (e)
             return e;
     }
+    if (o.stop == MG_STOP_FORCE)
+        return mg_launch_force_stop(2, dim, ld.n, ld.h, ld.blk, ld.prev, o.force_stencil, cmax, level_scal(h, b, l), s);
     return norms(h, ld, 2, level_scal(h, b, l), s, branch);
 }
 
@@ -932,7 +946,8 @@ mg_status build_graph(mg_hierarchy *h)
             CK(h, cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
     }
     h->batched = false;
-    if (h->opt.precision == MG_MIXED && h->batch > 1 && h->opt.interface == MG_IFACE_BUFFER) {
+    if (h->opt.precision == MG_MIXED && h->batch > 1 && h->opt.interface == MG_IFACE_BUFFER &&
+        h->opt.stop == MG_STOP_RESIDUAL) {
         // measured on 64 uneven hierarchies: graph branches 105 ms, batched
         // launches 143 ms (each batched block first loads its part's
         // descriptor); MG_BATCHED=1 selects the batched launches
@@ -1202,6 +1217,7 @@ mg_status mg_default_options(mg_options *opt)
     opt->guess = MG_GUESS_INTERP;
     opt->force_stencil = MG_FORCE_EQ2;
     opt->interface = MG_IFACE_BUFFER;
+    opt->stop = MG_STOP_RESIDUAL;
     opt->stream = nullptr;
     return MG_OK;
 }
@@ -1304,6 +1320,8 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 slots.push_back({(void **)&ld.tab64[L], align256(128 * sizeof(double))});
                 slots.push_back({(void **)&ld.tab32[L], align256(128 * sizeof(float))});
             }
+            if (o.stop == MG_STOP_FORCE)
+                slots.push_back({(void **)&ld.prev, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
             if (ld.frozen) {
                 slots.push_back({(void **)&ld.blk, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
                 slots.push_back({(void **)&ld.fblk, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
@@ -1318,6 +1336,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     slots.push_back({(void **)&h->stage, align256(stage * sizeof(double))});
     slots.push_back({(void **)&h->partials, align256((size_t)MG_BRANCHES * 2 * MG_NORM_BLOCKS_MAX * sizeof(double))});
     slots.push_back({(void **)&h->counters, align256((size_t)MG_BRANCHES * sizeof(unsigned))});
+    slots.push_back({(void **)&h->fmax, align256((size_t)MG_BRANCHES * sizeof(unsigned long long))});
     slots.push_back({(void **)&h->ctl, align256((size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl))});
     slots.push_back({(void **)&h->frho, align256((size_t)batch * MG_MAX_LEVELS * sizeof(double))});
     slots.push_back({(void **)&h->scal, align256((size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double))});

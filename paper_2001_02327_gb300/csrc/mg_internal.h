@@ -145,6 +145,10 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
 
 cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s);
 cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cudaStream_t s);
+// Force-change stopping test (Sec. 3): phase 0 before the first iteration,
+// 1 before each iteration (save phi), 2 after it (scal[1] from the change).
+cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const double *phi_blk, double *prev,
+                                 int stencil, unsigned long long *cmax, double *scal, cudaStream_t s);
 cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os, double *dst, int Ed, int od,
                               cudaStream_t s);
 cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const double *rho_blk, double frho,

@@ -11,6 +11,8 @@
 // is 32-bit.
 #include <algorithm>
 
+#include <math_constants.h>
+
 #include "mg_internal.h"
 
 namespace {
@@ -1127,6 +1129,66 @@ __global__ void __launch_bounds__(kThreads) k_forces(int n, double h, const doub
     }
 }
 
+// Stopping test of Sec. 3: max over Omega of |F(phi) - F(prev)|^2 into *cmax
+// (non-negative doubles order like their bit patterns, so the atomic maximum
+// is exact and independent of the order of the blocks).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_force_change(int n, double h, const double *__restrict__ phi,
+                                                           const double *__restrict__ prev, int stencil,
+                                                           unsigned long long *__restrict__ cmax)
+{
+    const int E = n + 4;
+    const int total = n * n * (DIM == 3 ? n : 1);
+    const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * h) : 1.0 / (2.0 * h);
+    const double c2 = stencil == 0 ? (1.0 / 3.0) / (4.0 * h) : 0.0;
+    double m = 0.0;
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = t / n;
+        const int i = t - r * n + 2;
+        const int j = DIM == 3 ? r % n + 2 : r + 2;
+        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int p = lin<DIM>(i, j, k, E);
+        const int st[3] = {1, E, E * E};
+        double s2 = 0.0;
+        for (int a = 0; a < DIM; a++) {
+            const double ga = c1 * (phi[p + st[a]] - phi[p - st[a]]) - c2 * (phi[p + 2 * st[a]] - phi[p - 2 * st[a]]);
+            const double gb =
+                c1 * (prev[p + st[a]] - prev[p - st[a]]) - c2 * (prev[p + 2 * st[a]] - prev[p - 2 * st[a]]);
+            const double d = ga - gb;
+            s2 += d * d;
+        }
+        m = fmax(m, s2);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(cmax, (unsigned long long)__double_as_longlong(m));
+}
+
+// prev = phi over the whole (n+4)^d block; resets the maximum of k_force_change
+__global__ void k_save_prev(long total, const double *__restrict__ phi, double *__restrict__ prev,
+                            unsigned long long *__restrict__ cmax)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *cmax = 0ull;
+    for (long t = gtid(); t < total; t += gstride())
+        prev[t] = phi[t];
+}
+
+// scal[1] = max|dF|^2 ||b||^2, so that the control kernels' sqrt(scal[1]) / ||b||
+// is the change of the acceleration
+__global__ void k_force_finish(double *scal, const unsigned long long *cmax)
+{
+    scal[1] = __longlong_as_double((long long)*cmax) * scal[0];
+}
+
+// before the first iteration under the force test: an infinite change
+__global__ void k_force_start(double *scal)
+{
+    if (scal[0] > 0.0)
+        scal[1] = CUDART_INF;
+}
+
 // copy Omega of an (n+4)^d block into a dense n^d array
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_extract(int n, const double *__restrict__ blk, double *__restrict__ out)
@@ -1707,6 +1769,25 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
         k_forces<3><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
     else
         k_forces<2><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const double *phi_blk, double *prev,
+                                 int stencil, unsigned long long *cmax, double *scal, cudaStream_t s)
+{
+    if (phase == 0) {
+        k_force_start<<<1, 1, 0, s>>>(scal);
+    } else if (phase == 1) {
+        const long total = cube(n + 4, dim);
+        k_save_prev<<<grid_for(total), kThreads, 0, s>>>(total, phi_blk, prev, cmax);
+    } else {
+        const int grid = grid_for(cube(n, dim));
+        if (dim == 3)
+            k_force_change<3><<<grid, kThreads, 0, s>>>(n, h, phi_blk, prev, stencil, cmax);
+        else
+            k_force_change<2><<<grid, kThreads, 0, s>>>(n, h, phi_blk, prev, stencil, cmax);
+        k_force_finish<<<1, 1, 0, s>>>(scal, cmax);
+    }
     return cudaGetLastError();
 }
 

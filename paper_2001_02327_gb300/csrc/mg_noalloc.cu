@@ -164,8 +164,9 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
     if ((dim != 2 && dim != 3) || n < 2 || !(h > 0.0) || !std::isfinite(G) || !rho || !phi)
         return reject(MG_EINVAL, "bad dim, n, h, G or NULL array");
     if (o.precision != MG_FP64 || o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 ||
-        !(o.rel_tol >= 0.0))
-        return reject(MG_EINVAL, "options: FP64 only, nu_pre + nu_post >= 1, max_cycles >= 0, rel_tol >= 0");
+        !(o.rel_tol >= 0.0) || o.stop != MG_STOP_RESIDUAL)
+        return reject(MG_EINVAL, "options: FP64 only, nu_pre + nu_post >= 1, max_cycles >= 0, rel_tol >= 0, "
+                                 "residual stopping rule");
     if (n + 2 > (1 << (MG_MAX_MG - 1)))
         return reject(MG_EINVAL, "n too large");
 

@@ -21,6 +21,7 @@ MG_FP64, MG_MIXED = 0, 1
 MG_GUESS_INTERP, MG_GUESS_ZERO, MG_GUESS_USER, MG_GUESS_LEARNED = 0, 1, 2, 3
 MG_FORCE_EQ2, MG_FORCE_CD2 = 0, 1
 MG_IFACE_BUFFER, MG_IFACE_FROZEN = 0, 1
+MG_STOP_RESIDUAL, MG_STOP_FORCE = 0, 1
 
 
 class mg_hierarchy_desc(C.Structure):
@@ -32,7 +33,7 @@ class mg_options(C.Structure):
     _fields_ = [("nu_pre", C.c_int), ("nu_post", C.c_int), ("max_cycles", C.c_int), ("rel_tol", C.c_double),
                 ("precision", C.c_int), ("inner_cycles", C.c_int), ("guess", C.c_int),
                 ("force_stencil", C.c_int), ("interface", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stop", C.c_int), ("stream", C.c_void_p)]
 
 
 class mg_level_stats(C.Structure):

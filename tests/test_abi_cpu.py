@@ -69,7 +69,8 @@ def _desc(mg, **kw):
     return d
 
 
-@pytest.mark.parametrize("bad", ["dim", "levels", "n_odd", "offset", "h0", "opt"])
+@pytest.mark.parametrize("bad", ["dim", "levels", "n_odd", "offset", "h0", "opt", "interface", "stop",
+                                 "stop_frozen"])
 def test_invalid_arguments_rejected_on_host(mg, bad):
     d = _desc(mg)
     opt = None
@@ -85,6 +86,13 @@ def test_invalid_arguments_rejected_on_host(mg, bad):
         d.h0 = -1.0
     elif bad == "opt":
         opt = mg.options(nu_pre=0, nu_post=0)
+    elif bad == "interface":
+        opt = mg.options(interface=2)
+    elif bad == "stop":
+        opt = mg.options(stop=2)
+    elif bad == "stop_frozen":
+        # the force-change test is defined on the buffer-ring method only
+        opt = mg.options(stop=mg.MG_STOP_FORCE, interface=mg.MG_IFACE_FROZEN)
     with pytest.raises(mg.MGError) as e:
         mg.mg_create_hierarchy([d], opt)
     assert e.value.status == mg.MG_EINVAL

@@ -176,6 +176,37 @@ def test_frozen_interface_converged(mg, oracle, precision):
         assert relmax(g[l]["phi"], gb[l]["phi"]) > 1e-6
 
 
+# --------------------------------------------------------------------------
+# the force-change stopping test of Sec. 3
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("make,stencil", [(lambda: I.paper_3d(16), 0), (lambda: I.paper_2d(64), 0),
+                                          (lambda: I.config_3d_offset_sphere(32, 3), 1)])
+def test_force_stop_rule(mg, oracle, make, stencil):
+    H = make()
+    inp = I.level_inputs(H)
+    _, g = gpu_solve(mg, H, inp, max_cycles=60, rel_tol=1e-10, stop=mg.MG_STOP_FORCE, force_stencil=stencil,
+                     allow_noconv=False)
+    ref = oracle.solve_hierarchy(H, inp, 2, 1, 60, 1e-10, stop="force", force_stencil=stencil)
+    for l in range(H.num_levels):
+        assert g[l]["cycles"] == ref[l]["cycles"], (l, g[l]["cycles"], ref[l]["cycles"])
+        assert g[l]["rel_res"] < 1e-10
+        assert abs(g[l]["rel_res"] / ref[l]["hist"][-1] - 1) < 1e-3, (l, g[l]["rel_res"], ref[l]["hist"][-1])
+    check_parity(H, g, ref)
+
+
+def test_force_stop_mixed_and_invalid_combination(mg):
+    H = I.paper_3d(16)
+    inp = I.level_inputs(H)
+    _, g = gpu_solve(mg, H, inp, max_cycles=60, rel_tol=1e-10, stop=mg.MG_STOP_FORCE, precision=mg.MG_MIXED,
+                     allow_noconv=False)
+    _, f = gpu_solve(mg, H, inp, max_cycles=60, rel_tol=1e-10, stop=mg.MG_STOP_FORCE, allow_noconv=False)
+    for l in range(H.num_levels):
+        assert g[l]["rel_res"] < 1e-10
+        assert relmax(g[l]["F"], f[l]["F"]) < 1e-8
+    with pytest.raises(mg.MGError):
+        mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(stop=mg.MG_STOP_FORCE, interface=mg.MG_IFACE_FROZEN))
+
+
 def test_full_size_config_fixed_cycles(mg, oracle):
     """The benchmark workload (4 nested 64^3 levels), element by element."""
     H = I.config_3d_offset_sphere(64, 4)
