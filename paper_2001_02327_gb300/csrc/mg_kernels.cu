@@ -378,6 +378,50 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_
     op_prolong<T, DIM>(phi_c, gc, phi_f, gf, gtid(), gstride());
 }
 
+// Residual and restriction inside one block in two stages: every thread takes
+// fine cells (residual into the dense scratch `r`), then every thread takes
+// coarse cells (sum of the children in the order of op_resid_restrict, so the
+// result is the same).  Spreads the FP64 work over all warps instead of 2^d
+// serial residuals per coarse cell.
+template <typename T, int DIM>
+__device__ __forceinline__ void op_resid_restrict_staged(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                         const MgGeom &gf, T *__restrict__ phi_c, T *__restrict__ f_c,
+                                                         const MgGeom &gc, T *__restrict__ r, int t0, int stride)
+{
+    const int Nc = gc.N, Nf = gf.N;
+    const int totf = Nf * Nf * (DIM == 3 ? Nf : 1);
+    Walk3 wf(t0, stride, Nf, DIM == 3 ? Nf : totf);
+    for (int t = t0; t < totf; t += stride, wf.next())
+        r[t] = residual_at<T, DIM>(phi_f, f_f, gf, wf.x + 1, wf.y + 1, DIM == 3 ? wf.z + 1 : 0);
+    __syncthreads();
+    const int total = Nc * Nc * (DIM == 3 ? Nc : 1);
+    const T w = DIM == 3 ? T(0.125) : T(0.25);
+    Walk3 wk(t0, stride, Nc, DIM == 3 ? Nc : total);
+    for (int t = t0; t < total; t += stride, wk.next()) {
+        const int I = wk.x + 1, J = wk.y + 1, K = DIM == 3 ? wk.z + 1 : 0;
+        T s = T(0);
+        for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++) {
+            const int k = DIM == 3 ? 2 * K - 1 + dk : 0;
+            if (DIM == 3 && k > Nf)
+                continue;
+            for (int dj = 0; dj < 2; dj++) {
+                const int j = 2 * J - 1 + dj;
+                if (j > Nf)
+                    continue;
+                for (int di = 0; di < 2; di++) {
+                    const int i = 2 * I - 1 + di;
+                    if (i > Nf)
+                        continue;
+                    s += r[((DIM == 3 ? (k - 1) * Nf : 0) + (j - 1)) * Nf + (i - 1)];
+                }
+            }
+        }
+        const int pc = lin<DIM>(I, J, K, gc.E);
+        f_c[pc] = w * s;
+        phi_c[pc] = T(0);
+    }
+}
+
 // The part of the V-cycle at and below multigrid level Ls (Sec. 2.3 steps
 // 6-11 restricted to those levels) in one thread block, every array of those
 // levels in shared memory: pre-smoothing at Ls, restriction and smoothing
@@ -419,8 +463,10 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ phi_g, const T *__re
     };
     smooth(0, bt.g[0].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
     int q = 0;
+    T *scratch = sm + offs[bt.nlev];      // residuals of the finest level of the block
     while (bt.g[q].N > 1 && q + 1 < bt.nlev) {
-        op_resid_restrict<T, DIM>(PHI(q), F(q), bt.g[q], PHI(q + 1), F(q + 1), bt.g[q + 1], tid, nth);
+        op_resid_restrict_staged<T, DIM>(PHI(q), F(q), bt.g[q], PHI(q + 1), F(q + 1), bt.g[q + 1], scratch, tid,
+                                         nth);
         __syncthreads();
         smooth(q + 1, bt.g[q + 1].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
         q++;
@@ -1561,6 +1607,7 @@ size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt)
     size_t c = 0;
     for (int q = 0; q < bt.nlev; q++)
         c += 2 * (size_t)cube(bt.g[q].E, dim);
+    c += (size_t)cube(bt.g[0].N, dim);      // residual scratch of the first level
     return c * (fp32 ? 4 : 8);
 }
 
