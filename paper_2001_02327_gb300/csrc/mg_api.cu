@@ -43,6 +43,9 @@ struct LevelData {
     double *tab64[MG_MAX_MG] = {}; // boundary diagonal tables of the coarse levels (device)
     float *tab32[MG_MAX_MG] = {};
     int Ls[2] = {0, 0};            // first level handled by the one-block kernel [fp64, fp32]
+    int Lc[2] = {0, 0};            // first level handled by the cluster kernel (-1: none)
+    int Lcb[2] = {0, 0};           // first level the cluster kernel runs in its CTA 0
+    MgBottom cbt[2];               // that part's one-block plan
     MgBottom bt[2];
 };
 
@@ -106,6 +109,63 @@ void plan_bottom(LevelData &ld, int dim, int lim32 = -1)
 
 long cells(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
 
+// Largest multigrid level (cells per edge) handed to the cluster kernel, per
+// precision; 0 disables it.  MG_CLUSTER_N64 / MG_CLUSTER_N32 override.
+int cluster_limit(bool fp32)
+{
+    const char *v = std::getenv(fp32 ? "MG_CLUSTER_N32" : "MG_CLUSTER_N64");
+    if (v && *v)
+        return std::atoi(v);
+    return 0;
+}
+
+// Largest multigrid level (cells per edge) the cluster kernel leaves to its
+// CTA 0 (one block, shared memory, block barriers): levels this small are
+// latency-bound phases either way, and a block barrier is cheaper than a
+// cluster barrier.  MG_CLUSTER_BOTTOM overrides.
+int cluster_bottom_limit()
+{
+    const char *v = std::getenv("MG_CLUSTER_BOTTOM");
+    if (v && *v)
+        return std::atoi(v);
+    return 2;
+}
+
+// The cluster kernel's part of the V-cycle per precision: from the first
+// multigrid level of at most `lim` cells per edge down; Lc = -1 when off.
+void plan_cluster(LevelData &ld, int dim, int csize, int lim64 = -1, int lim32 = -1)
+{
+    const int cb = cluster_bottom_limit();
+    for (int w = 0; w < 2; w++) {
+        const int lim = w ? (lim32 >= 0 ? lim32 : cluster_limit(true)) : (lim64 >= 0 ? lim64 : cluster_limit(false));
+        ld.Lc[w] = -1;
+        if (csize <= 0 || lim <= 0 || ld.nmg < 2)
+            continue;
+        int Lc = -1, Lcb = ld.nmg - 1;
+        for (int L = 0; L < ld.nmg - 1; L++)
+            if (ld.g[L].N <= lim) {
+                Lc = L;
+                break;
+            }
+        if (Lc < 0)
+            continue;
+        for (int L = Lc + 1; L < ld.nmg; L++)
+            if (ld.g[L].N <= cb) {
+                Lcb = L;
+                break;
+            }
+        MgBottom bt;
+        bt.nlev = ld.nmg - Lcb;
+        for (int q = 0; q < bt.nlev; q++)
+            bt.g[q] = ld.g[Lcb + q];
+        if (bt.nlev > MG_BOTTOM_MAX || mg_bottom_smem(dim, w == 1, bt) > MG_BOTTOM_SMEM_MAX)
+            continue;
+        ld.Lc[w] = Lc;
+        ld.Lcb[w] = Lcb;
+        ld.cbt[w] = bt;
+    }
+}
+
 // Sec. 2.2: N^L = round(M / 2^L), halves rounded up, until N^L = 1.
 int level_sizes(int M, int *N, int cap)
 {
@@ -149,10 +209,11 @@ void build_geometry(LevelData &ld, int dim)
 #define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
 
 enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
-                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_COUNT };
+                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_CLUSTER, KK_COUNT };
 const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
                                          "defect",        "accumulate",     "interface",       "forces",
-                                         "set_density",   "bottom",         "tb_pre",          "tb_post"};
+                                         "set_density",   "bottom",         "tb_pre",          "tb_post",
+                                         "cluster_vcycle"};
 
 // Per-launch CUDA-event timing on the hierarchy's stream (mg_profile).
 struct Profiler {
@@ -193,6 +254,7 @@ struct mg_hierarchy {
     Profiler prof;
     // solve graph
     bool use_graph = true;          // MG_SOLVE_GRAPH=0: host-driven loop (for kernel profilers)
+    int csize = 0;                  // CTAs per cluster of the cluster kernel (0: unavailable)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<char> graph_sig;
@@ -378,9 +440,10 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     return cudaSuccess;
 }
 
-// the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level;
-// the levels from Ls down run in the one-block kernel
-cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t s)
+// the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level,
+// `ncyc` times; the levels from Lc down run in the cluster kernel (when
+// Lc < Ls), those from Ls down in the one-block kernel
+cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t s, int ncyc = 1)
 {
     const int dim = h->dim;
     const mg_options &o = h->opt;
@@ -389,17 +452,46 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     auto F = [&](int L) -> void * { return fp32 ? (void *)ld.f32[L] : (void *)ld.f[L]; };
     const int Ls = ld.Ls[fp32 ? 1 : 0];
     const MgBottom &bt = ld.bt[fp32 ? 1 : 0];
+    const int Lc = ld.Lc[fp32 ? 1 : 0];
+    const bool clu = Lc >= 0 && h->csize > 0;
+    const int Lstop = clu ? Lc : Ls;
     auto bottom = [&]() {
         return timed(h, KK_BOTTOM, 3.0 * w * cells_d(ld.g[Ls].E, dim),
                      [&] { return mg_launch_bottom(dim, fp32, P(Ls), F(Ls), bt, o.nu_pre, o.nu_post, s); });
     };
+    auto cluster = [&](int cycles) {
+        MgClusterPlan p{};
+        const int Lcb = ld.Lcb[fp32 ? 1 : 0];
+        p.nlev = ld.nmg - Lc;
+        p.nclu = Lcb - Lc;
+        p.cycles = cycles;
+        p.nu_pre = o.nu_pre;
+        p.nu_post = o.nu_post;
+        double by = 3.0 * w * cells_d(ld.g[Lcb].E, dim);
+        for (int q = 0; q < p.nlev; q++) {
+            p.g[q] = ld.g[Lc + q];
+            p.phi[q] = P(Lc + q);
+            p.f[q] = F(Lc + q);
+            if (q < p.nclu)   // smoothing sweeps, residual + restriction, prolongation
+                by += w * cells_d(ld.g[Lc + q].N, dim) * (4.0 * (o.nu_pre + o.nu_post) + 5.0);
+        }
+        p.bt = ld.cbt[fp32 ? 1 : 0];
+        return timed(h, KK_CLUSTER, by * cycles, [&] { return mg_launch_cluster(dim, fp32, p, h->csize, s); });
+    };
     cudaError_t e;
-    if (Ls == 0)
-        return bottom();                                                                  // whole cycle
-    // descent: at each level above Ls, nu_pre sweeps then residual and
+    if (Lstop == 0) {                                                                     // whole cycle
+        if (clu)
+            return cluster(ncyc);
+        for (int c = 0; c < ncyc; c++)
+            if ((e = bottom()))
+                return e;
+        return cudaSuccess;
+    }
+    for (int cyc = 0; cyc < ncyc; cyc++) {
+    // descent: at each level above Lstop, nu_pre sweeps then residual and
     // restriction (steps 2/6, 4, 5) -- one temporally blocked kernel per
     // level in FP32 when the level has a tile, else one kernel per phase
-    for (int L = 0; L < Ls; L++) {
+    for (int L = 0; L < Lstop; L++) {
         const double nf = cells_d(ld.g[L].N, dim), nc = cells_d(ld.g[L + 1].N, dim);
         if (fp32 && ld.tile[L]) {
             e = timed(h, KK_TB_PRE, w * (3.0 * nf + 2.0 * nc), [&] {
@@ -418,10 +510,10 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
         if (e)
             return e;
     }
-    if ((e = bottom()))                                                                   // steps 6-11, L >= Ls
+    if ((e = clu ? cluster(1) : bottom()))                                                // steps 6-11, L >= Lstop
         return e;
     // ascent: prolongation + correction, then nu_post sweeps (steps 10-11)
-    for (int L = Ls; L > 0; L--) {
+    for (int L = Lstop; L > 0; L--) {
         const double nf = cells_d(ld.g[L - 1].N, dim), nc = cells_d(ld.g[L].N, dim);
         if (fp32 && ld.tile[L - 1]) {
             e = timed(h, KK_TB_POST, w * (3.0 * nf + nc), [&] {
@@ -437,6 +529,7 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
             return e;
         if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s)))
             return e;
+    }
     }
     return cudaSuccess;
 }
@@ -530,9 +623,8 @@ cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int b
         });
         if (e)
             return e;
-        for (int c = 0; c < o.inner_cycles; c++)
-            if ((e = vcycle(h, ld, true, s)))
-                return e;
+        if ((e = vcycle(h, ld, true, s, o.inner_cycles)))
+            return e;
         e = timed(h, KK_ACCUM, 20.0 * nd, [&] { return mg_launch_accumulate(dim, ld.phi[0], ld.phi32[0], ld.g[0], s); });
         if (e)
             return e;
@@ -1100,6 +1192,7 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     for (int nb : nbs) {
         plan_bottom(ld, dim, nb);
         plan_tiles(ld, dim, o.nu_pre, o.nu_post);
+        plan_cluster(ld, h->dim, h->csize);
         const float ms = time_ms(h, 10, [&](cudaStream_t cs) { return vcycle(h, ld, true, cs); }, err);
         if (err)
             return false;
@@ -1109,6 +1202,7 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
         }
     }
     plan_bottom(ld, dim, bestnb);
+    plan_cluster(ld, h->dim, h->csize);
     te.bottom_n = bestnb;
     // 2. per level above the bottom: the tile of its pre/post pair
     const int Ls = ld.Ls[1];
@@ -1168,6 +1262,7 @@ void apply_entry(mg_hierarchy *h, LevelData &ld, const TuneEntry &te)
     plan_bottom(ld, h->dim, te.bottom_n);
     for (int L = 0; L < ld.nmg; L++)
         ld.tile[L] = L < ld.Ls[1] ? te.tile[L] : 0;
+    plan_cluster(ld, h->dim, h->csize);
 }
 
 std::vector<TuneEntry> read_cache(const char *path)
@@ -1382,6 +1477,8 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     if (e == cudaSuccess)
         e = mg_batch_prepare();
     if (e == cudaSuccess)
+        h->csize = mg_cluster_prepare();
+    if (e == cudaSuccess)
         e = mg_launch_zero(h->arena, bytes, h->stream);
     // boundary-diagonal tables of the coarse multigrid levels, then the plan
     // of the one-block kernel (which copies the level descriptions)
@@ -1401,6 +1498,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
             }
             plan_bottom(ld, dim);
             plan_tiles(ld, dim, o.nu_pre, o.nu_post);
+            plan_cluster(ld, h->dim, h->csize);
         }
     if (e == cudaSuccess) {
         std::vector<double> fr((size_t)batch * MG_MAX_LEVELS, 0.0);

@@ -80,6 +80,20 @@ struct MgBottom {
     int nlev;                   // levels Ls .. Ls+nlev-1 (the last one has one cell)
     MgGeom g[MG_BOTTOM_MAX];
 };
+
+// One thread-block cluster running the V-cycle from a multigrid level Lc down
+// (levels Lc + q, q = 0..nlev-1): levels q < nclu phase by phase over all
+// CTAs of the cluster with cluster barriers between phases, levels from nclu
+// down in CTA 0 (the one-block path, plan `bt`).  nclu < nlev.
+#define MG_CLUSTER_THREADS 1024
+struct MgClusterPlan {
+    int nlev, nclu, cycles, nu_pre, nu_post;
+    MgGeom g[MG_MAX_MG];
+    void *phi[MG_MAX_MG];
+    void *f[MG_MAX_MG];
+    MgBottom bt;
+};
+
 size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt);
 cudaError_t mg_bottom_prepare();   // once per device before the first launch
 cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const MgBottom &bt, int nu_pre,
@@ -149,6 +163,10 @@ cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cu
 // 1 before each iteration (save phi), 2 after it (scal[1] from the change).
 cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const double *phi_blk, double *prev,
                                  int stencil, unsigned long long *cmax, double *scal, cudaStream_t s);
+// Cluster V-cycle: mg_cluster_prepare picks the cluster size (16 CTAs where
+// the device can co-schedule them, else 8; 0 if neither) once per process.
+int mg_cluster_prepare();
+cudaError_t mg_launch_cluster(int dim, bool fp32, const MgClusterPlan &p, int csize, cudaStream_t s);
 cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os, double *dst, int Ed, int od,
                               cudaStream_t s);
 cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const double *rho_blk, double frho,

@@ -38,21 +38,36 @@ __device__ __forceinline__ int lin(int i, int j, int k, int E)
     return DIM == 3 ? (k * E + j) * E + i : j * E + i;
 }
 
+// floor(x / d) for 0 <= x < 2^31, d >= 1 and a quotient below 2^21 (every
+// index here: at most (1286 + 4)^2): the FP32 value of x, the reciprocal of d
+// and their product, each rounded toward zero, underestimate x/d by less than
+// 3 * 2^-23 relative, i.e. by less than 1, so truncation gives floor(x/d) or
+// one less, and one exact remainder test corrects it.  A few instructions
+// instead of the long dependent sequence of a general integer division --
+// this sits at the start of every phase of every kernel, where it is latency.
+__device__ __forceinline__ int div_small(int x, int d)
+{
+    int q = __float2int_rz(__fmul_rz(__int2float_rz(x), __frcp_rz(__int2float_rz(d))));
+    if (x - q * d >= d)
+        q++;
+    return q;
+}
+
 // Walk t = t0, t0 + S, t0 + 2S, ... over an nx * ny * nz box (x fastest) with
 // the coordinates advanced incrementally: the divisions happen once, not per
-// cell (integer division is tens of instructions).
+// cell.
 struct Walk3 {
     int x, y, z, dx, dy, dz, nx, ny;
     __device__ __forceinline__ Walk3(int t0, int S, int nx_, int ny_) : nx(nx_), ny(ny_)
     {
-        const int r = t0 / nx;
+        const int r = div_small(t0, nx);
         x = t0 - r * nx;
-        y = r % ny;
-        z = r / ny;
-        const int q = S / nx;
+        z = div_small(r, ny);
+        y = r - z * ny;
+        const int q = div_small(S, nx);
         dx = S - q * nx;
-        dy = q % ny;
-        dz = q / ny;
+        dz = div_small(q, ny);
+        dy = q - dz * ny;
     }
     __device__ __forceinline__ void next()
     {
@@ -333,31 +348,33 @@ __global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi,
     op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
 }
 
-// Residual and restriction with one fine cell per thread: a block computes the
-// residuals of a fine tile (16x8x2 in 3D, 32x8 in 2D) into shared memory and
-// its first threads average the children of the coarse cells of the tile
-// (8x4x1 in 3D, 16x4 in 2D).
+// Residual and restriction with one fine cell per thread: 256 threads compute
+// the residuals of a fine tile (16x8x2 in 3D, 32x8 in 2D) into shared memory
+// `r` and the first of them average the children of the coarse cells of the
+// tile (8x4x1 in 3D, 16x4 in 2D).  Tile (bx, by, bz) of the level; `lt` the
+// thread's index in the tile; contains a __syncthreads (every thread of the
+// block must call it, `ok` false for threads without a tile).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
-                                                             MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
-                                                             MgGeom gc)
+__device__ __forceinline__ void resid_restrict_tile(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                    const MgGeom &gf, T *__restrict__ phi_c, T *__restrict__ f_c,
+                                                    const MgGeom &gc, int bx, int by, int bz, int lt, bool ok,
+                                                    T *__restrict__ r)
 {
-    __shared__ T r[kThreads];
     const int Nf = gf.N, Nc = gc.N;
     constexpr int FX = DIM == 3 ? 16 : 32, FY = 8;
-    const int tx = threadIdx.x % FX, ty = (threadIdx.x / FX) % FY, tz = DIM == 3 ? threadIdx.x / (FX * FY) : 0;
-    const int i = 1 + FX * blockIdx.x + tx, j = 1 + FY * blockIdx.y + ty;
-    const int k = DIM == 3 ? 1 + 2 * blockIdx.z + tz : 0;
+    const int tx = lt % FX, ty = (lt / FX) % FY, tz = DIM == 3 ? lt / (FX * FY) : 0;
+    const int i = 1 + FX * bx + tx, j = 1 + FY * by + ty;
+    const int k = DIM == 3 ? 1 + 2 * bz + tz : 0;
     T v = T(0);
-    if (i <= Nf && j <= Nf && (DIM == 2 || k <= Nf))
+    if (ok && i <= Nf && j <= Nf && (DIM == 2 || k <= Nf))
         v = residual_at<T, DIM>(phi_f, f_f, gf, i, j, k);
-    r[threadIdx.x] = v;
+    r[lt] = v;
     __syncthreads();
     constexpr int CX = FX / 2, CY = FY / 2;
-    if (threadIdx.x < CX * CY) {
-        const int cx = threadIdx.x % CX, cy = threadIdx.x / CX;
-        const int I = 1 + CX * blockIdx.x + cx, J = 1 + CY * blockIdx.y + cy;
-        const int K = DIM == 3 ? 1 + blockIdx.z : 0;
+    if (ok && lt < CX * CY) {
+        const int cx = lt % CX, cy = lt / CX;
+        const int I = 1 + CX * bx + cx, J = 1 + CY * by + cy;
+        const int K = DIM == 3 ? 1 + bz : 0;
         if (I <= Nc && J <= Nc && (DIM == 2 || K <= Nc)) {
             T s = T(0);
             for (int dz = 0; dz < (DIM == 3 ? 2 : 1); dz++)
@@ -369,6 +386,24 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict
             phi_c[pc] = T(0);
         }
     }
+}
+
+// tiles of a restriction from a level of Nc coarse cells per edge
+__host__ __device__ inline void resid_restrict_tiles(int dim, int Nc, int &nx, int &ny, int &nz)
+{
+    nx = dim == 3 ? (Nc + 7) / 8 : (Nc + 15) / 16;
+    ny = (Nc + 3) / 4;
+    nz = dim == 3 ? Nc : 1;
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                             MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
+                                                             MgGeom gc)
+{
+    __shared__ T r[kThreads];
+    resid_restrict_tile<T, DIM>(phi_f, f_f, gf, phi_c, f_c, gc, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, true,
+                                r);
 }
 
 template <typename T, int DIM>
@@ -487,6 +522,84 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     bottom_body<T, DIM>(phi_g, f_g, bt, nu_pre, nu_post, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Cluster V-cycle: one thread-block cluster runs every phase of the levels
+// from Lc down (Sec. 2.3 steps 2-13 restricted to those levels), phases
+// separated by cluster barriers instead of kernel launches.  The arrays stay
+// where they are (global memory, L2-resident at these sizes); the barrier's
+// release/acquire at cluster scope orders each phase's writes before the next
+// phase's reads in every CTA.  Same per-cell arithmetic and phase order as
+// the one-kernel-per-phase path; the levels from nclu down run in CTA 0
+// through the one-block path while the other CTAs wait at the barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_ctas()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// every thread of every CTA of the cluster, from converged code
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(MG_CLUSTER_THREADS, 1) k_cluster_vcycle(const __grid_constant__ MgClusterPlan P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T rbuf[MG_CLUSTER_THREADS];
+    const int rank = (int)cluster_rank(), C = (int)cluster_ctas();
+    const int tid = threadIdx.x;
+    // work items: consecutive warps go to different CTAs (each warp keeps 32
+    // consecutive items), so that even a small level is spread over every SM
+    const int t0 = (((tid >> 5) * C + rank) << 5) + (tid & 31), stride = C * blockDim.x;
+    const int grp = tid >> 8, lt = tid & 255, ngrp = blockDim.x >> 8;   // 256-thread restriction tiles
+    auto PHI = [&](int q) { return static_cast<T *>(P.phi[q]); };
+    auto F = [&](int q) { return static_cast<T *>(P.f[q]); };
+    auto smooth = [&](int q, int sweeps) {
+        for (int sw = 0; sw < sweeps; sw++)
+            for (int c = 0; c < 2; c++) {
+                op_smooth_colour<T, DIM>(PHI(q), F(q), P.g[q], c, t0, stride);
+                cluster_barrier();
+            }
+    };
+    for (int cyc = 0; cyc < P.cycles; cyc++) {
+        for (int q = 0; q < P.nclu; q++) {
+            smooth(q, P.nu_pre);
+            int nx, ny, nz;
+            resid_restrict_tiles(DIM, P.g[q + 1].N, nx, ny, nz);
+            const int ntile = nx * ny * nz, per = ngrp * C;
+            for (int base = 0; base < ntile; base += per) {
+                const int tile = base + grp * C + rank;
+                const bool ok = tile < ntile;
+                const int tt = ok ? tile : 0;
+                const int ty = div_small(tt, nx), tz = div_small(ty, ny);
+                resid_restrict_tile<T, DIM>(PHI(q), F(q), P.g[q], PHI(q + 1), F(q + 1), P.g[q + 1], tt - ty * nx,
+                                            ty - tz * ny, tz, lt, ok, rbuf + (grp << 8));
+                __syncthreads();
+            }
+            cluster_barrier();
+        }
+        if (rank == 0)
+            bottom_body<T, DIM>(PHI(P.nclu), F(P.nclu), P.bt, P.nu_pre, P.nu_post, smem_raw);
+        cluster_barrier();
+        for (int q = P.nclu - 1; q >= 0; q--) {
+            op_prolong<T, DIM>(PHI(q + 1), P.g[q + 1], PHI(q), P.g[q], t0, stride);
+            cluster_barrier();
+            smooth(q, P.nu_post);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -849,11 +962,11 @@ __device__ __forceinline__ void norm_terms(const double *__restrict__ phi, const
                                            const MgGeom &g, int t, int which, double &b2, double &r2)
 {
     const int N = g.N, E = g.E;
-    const int r = t / N;
+    const int r = div_small(t, N);
     const int i = t - r * N + 1;
     int j, k;
     if (DIM == 3) {
-        k = r / N;
+        k = div_small(r, N);
         j = r - k * N + 1;
         k += 1;
     } else {
@@ -962,11 +1075,11 @@ __global__ void __launch_bounds__(kThreads) k_defect(const double *__restrict__ 
     const int N = g.N;
     const int total = N * N * (DIM == 3 ? N : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / N;
+        const int r = div_small(t, N);
         const int i = t - r * N + 1;
         int j, k;
         if (DIM == 3) {
-            k = r / N;
+            k = div_small(r, N);
             j = r - k * N + 1;
             k += 1;
         } else {
@@ -986,11 +1099,11 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(double *__restrict__ ph
     const int N = g.N;
     const int total = N * N * (DIM == 3 ? N : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / N;
+        const int r = div_small(t, N);
         const int i = t - r * N + 1;
         int j, k;
         if (DIM == 3) {
-            k = r / N;
+            k = div_small(r, N);
             j = r - k * N + 1;
             k += 1;
         } else {
@@ -1012,10 +1125,11 @@ __global__ void __launch_bounds__(kThreads) k_set_density(int n, const double *_
     const int E = n + 4;
     const int total = E * E * (DIM == 3 ? E : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / E;
+        const int r = div_small(t, E);
         const int i = t - r * E;
-        const int j = DIM == 3 ? r % E : r;
-        const int k = DIM == 3 ? r / E : 2;
+        const int rq = DIM == 3 ? div_small(r, E) : 0;
+        const int j = DIM == 3 ? r - rq * E : r;
+        const int k = DIM == 3 ? rq : 2;
         const bool outer = i == 0 || i == n + 3 || j == 0 || j == n + 3 || (DIM == 3 && (k == 0 || k == n + 3));
         const bool omega = i >= 2 && i <= n + 1 && j >= 2 && j <= n + 1 && (DIM == 2 || (k >= 2 && k <= n + 1));
         if (omega) {
@@ -1080,10 +1194,11 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
     const int total = E * E * (DIM == 3 ? E : 1);
     for (int t = gtid(); t < total; t += gstride()) {
         int s[3];
-        const int r = t / E;
+        const int r = div_small(t, E);
         s[0] = t - r * E;
-        s[1] = DIM == 3 ? r % E : r;
-        s[2] = DIM == 3 ? r / E : 2;
+        const int rq = DIM == 3 ? div_small(r, E) : 0;
+        s[1] = DIM == 3 ? r - rq * E : r;
+        s[2] = DIM == 3 ? rq : 2;
         bool outer = false, inner = false;
         for (int a = 0; a < DIM; a++) {
             if (s[a] == 0 || s[a] == nc + 3)
@@ -1126,10 +1241,11 @@ __global__ void __launch_bounds__(kThreads) k_copy_box(int e, const double *__re
 {
     const int total = e * e * (DIM == 3 ? e : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / e;
+        const int r = div_small(t, e);
         const int i = t - r * e;
-        const int j = DIM == 3 ? r % e : r;
-        const int k = DIM == 3 ? r / e : 0;
+        const int rq = DIM == 3 ? div_small(r, e) : 0;
+        const int j = DIM == 3 ? r - rq * e : r;
+        const int k = DIM == 3 ? rq : 0;
         dst[lin<DIM>(i + od, j + od, DIM == 3 ? k + od : 0, Ed)] = src[lin<DIM>(i + os, j + os, DIM == 3 ? k + os : 0, Es)];
     }
 }
@@ -1141,10 +1257,11 @@ __global__ void __launch_bounds__(kThreads) k_copy_guess(int n, const double *__
     const int M = n + 2;
     const int total = M * M * (DIM == 3 ? M : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / M;
+        const int r = div_small(t, M);
         const int i = t - r * M;
-        const int j = DIM == 3 ? r % M : r;
-        const int k = DIM == 3 ? r / M : 0;
+        const int rq = DIM == 3 ? div_small(r, M) : 0;
+        const int j = DIM == 3 ? r - rq * M : r;
+        const int k = DIM == 3 ? rq : 0;
         phi_blk[lin<DIM>(i + 1, j + 1, DIM == 3 ? k + 1 : 0, n + 4)] = src[t];
     }
 }
@@ -1159,10 +1276,11 @@ __global__ void __launch_bounds__(kThreads) k_forces(int n, double h, const doub
     const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * h) : 1.0 / (2.0 * h);
     const double c2 = stencil == 0 ? (1.0 / 3.0) / (4.0 * h) : 0.0;
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / n;
+        const int r = div_small(t, n);
         const int i = t - r * n + 2;
-        const int j = DIM == 3 ? r % n + 2 : r + 2;
-        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int rq = DIM == 3 ? div_small(r, n) : 0;
+        const int j = DIM == 3 ? r - rq * n + 2 : r + 2;
+        const int k = DIM == 3 ? rq + 2 : 0;
         const int p = lin<DIM>(i, j, k, E);
         const int st[3] = {1, E, E * E};
         for (int a = 0; a < DIM; a++) {
@@ -1189,10 +1307,11 @@ __global__ void __launch_bounds__(kThreads) k_force_change(int n, double h, cons
     const double c2 = stencil == 0 ? (1.0 / 3.0) / (4.0 * h) : 0.0;
     double m = 0.0;
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / n;
+        const int r = div_small(t, n);
         const int i = t - r * n + 2;
-        const int j = DIM == 3 ? r % n + 2 : r + 2;
-        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int rq = DIM == 3 ? div_small(r, n) : 0;
+        const int j = DIM == 3 ? r - rq * n + 2 : r + 2;
+        const int k = DIM == 3 ? rq + 2 : 0;
         const int p = lin<DIM>(i, j, k, E);
         const int st[3] = {1, E, E * E};
         double s2 = 0.0;
@@ -1242,10 +1361,11 @@ __global__ void __launch_bounds__(kThreads) k_extract(int n, const double *__res
     const int E = n + 4;
     const int total = n * n * (DIM == 3 ? n : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / n;
+        const int r = div_small(t, n);
         const int i = t - r * n + 2;
-        const int j = DIM == 3 ? r % n + 2 : r + 2;
-        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int rq = DIM == 3 ? div_small(r, n) : 0;
+        const int j = DIM == 3 ? r - rq * n + 2 : r + 2;
+        const int k = DIM == 3 ? rq + 2 : 0;
         out[t] = blk[lin<DIM>(i, j, k, E)];
     }
 }
@@ -1259,10 +1379,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_h2(int n, const double *__re
     const int E = n + 4;
     const int total = n * n * (DIM == 3 ? n : 1);
     for (int t = gtid(); t < total; t += gstride()) {
-        const int r = t / n;
+        const int r = div_small(t, n);
         const int i = t - r * n + 2;
-        const int j = DIM == 3 ? r % n + 2 : r + 2;
-        const int k = DIM == 3 ? r / n + 2 : 0;
+        const int rq = DIM == 3 ? div_small(r, n) : 0;
+        const int j = DIM == 3 ? r - rq * n + 2 : r + 2;
+        const int k = DIM == 3 ? rq + 2 : 0;
         const int p = lin<DIM>(i, j, k, E);
         double nb = phi[p - 1] + phi[p + 1] + phi[p - E] + phi[p + E];
         if (DIM == 3)
@@ -1397,10 +1518,10 @@ template <int DIM>
 __device__ __forceinline__ void active_cell(const MgGeom &g, int t, int &i, int &j, int &k)
 {
     const int N = g.N;
-    const int r = t / N;
+    const int r = div_small(t, N);
     i = t - r * N + 1;
     if (DIM == 3) {
-        k = r / N;
+        k = div_small(r, N);
         j = r - k * N + 1;
         k += 1;
     } else {
@@ -1507,10 +1628,11 @@ __global__ void __launch_bounds__(kThreads) kb_interface(const MgBPart *__restri
     const int total = E * E * (DIM == 3 ? E : 1);
     for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_blk * kThreads) {
         int s[3];
-        const int r = t / E;
+        const int r = div_small(t, E);
         s[0] = t - r * E;
-        s[1] = DIM == 3 ? r % E : r;
-        s[2] = DIM == 3 ? r / E : 2;
+        const int rq = DIM == 3 ? div_small(r, E) : 0;
+        s[1] = DIM == 3 ? r - rq * E : r;
+        s[2] = DIM == 3 ? rq : 2;
         bool outer = false, inner = false;
         for (int a = 0; a < DIM; a++) {
             if (s[a] == 0 || s[a] == nc + 3)
@@ -1643,6 +1765,77 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
     return cudaGetLastError();
 }
 
+template <typename T, int DIM>
+static cudaError_t cluster_attrs(int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_cluster_vcycle<T, DIM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (!e)
+        e = cudaFuncSetAttribute(k_cluster_vcycle<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+static cudaLaunchConfig_t cluster_config(int csize, size_t smem, cudaStream_t s, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize, 1, 1);
+    cfg.blockDim = dim3(MG_CLUSTER_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int mg_cluster_prepare()
+{
+    static int dev_done = -1, chosen = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (dev_done == dev)
+        return chosen;
+    const int smem = MG_BOTTOM_SMEM_MAX;
+    if (cluster_attrs<float, 3>(smem) || cluster_attrs<double, 3>(smem) || cluster_attrs<float, 2>(smem) ||
+        cluster_attrs<double, 2>(smem)) {
+        cudaGetLastError();
+        dev_done = dev;
+        chosen = 0;
+        return 0;
+    }
+    chosen = 0;
+    for (int cs : {16, 8}) {
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = cluster_config(cs, smem, nullptr, at);
+        int n64 = 0, n32 = 0;
+        if (cudaOccupancyMaxActiveClusters(&n64, k_cluster_vcycle<double, 3>, &cfg) == cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&n32, k_cluster_vcycle<float, 3>, &cfg) == cudaSuccess && n64 > 0 &&
+            n32 > 0) {
+            chosen = cs;
+            break;
+        }
+        cudaGetLastError();
+    }
+    dev_done = dev;
+    return chosen;
+}
+
+cudaError_t mg_launch_cluster(int dim, bool fp32, const MgClusterPlan &p, int csize, cudaStream_t s)
+{
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = cluster_config(csize, mg_bottom_smem(dim, fp32, p.bt), s, at);
+    if (dim == 3)
+        return fp32 ? cudaLaunchKernelEx(&cfg, k_cluster_vcycle<float, 3>, p)
+                    : cudaLaunchKernelEx(&cfg, k_cluster_vcycle<double, 3>, p);
+    return fp32 ? cudaLaunchKernelEx(&cfg, k_cluster_vcycle<float, 2>, p)
+                : cudaLaunchKernelEx(&cfg, k_cluster_vcycle<double, 2>, p);
+}
+
 size_t mg_tb_smem(int dim, bool fp32, int tile, int halo)
 {
     const size_t P = tile + 2 * halo;
@@ -1690,9 +1883,10 @@ cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, cons
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
                                      void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s)
 {
-    const int Nc = gc.N;
+    int nx, ny, nz;
+    resid_restrict_tiles(dim, gc.N, nx, ny, nz);
+    const dim3 grid(nx, ny, nz);
     if (dim == 3) {
-        const dim3 grid((Nc + 7) / 8, (Nc + 3) / 4, Nc);
         if (fp32)
             k_resid_restrict<float, 3><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
@@ -1700,7 +1894,6 @@ cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, cons
             k_resid_restrict<double, 3><<<grid, kThreads, 0, s>>>((const double *)phi_f, (const double *)f_f, gf,
                                                                   (double *)phi_c, (double *)f_c, gc);
     } else {
-        const dim3 grid((Nc + 15) / 16, (Nc + 3) / 4, 1);
         if (fp32)
             k_resid_restrict<float, 2><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);

@@ -473,3 +473,59 @@ def test_autotune_keeps_results_and_caches(mg, tmp_path):
             mg.mg_destroy(h)
     assert plans[0] == plans[1]
     assert len(open(cache).read().strip().splitlines()) == 1
+
+
+# --------------------------------------------------------------------------
+# the cluster V-cycle (levels from Lc down in one thread-block cluster)
+# --------------------------------------------------------------------------
+def _solve_profiled(mg, H, inp, **kw):
+    """gpu_solve plus the per-kernel launch counts of the same solve."""
+    import torch
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(**kw))
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        for l in range(H.num_levels):
+            if l == 0:
+                mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            else:
+                mg.mg_set_density(h, 0, l, dev(inp[l]["rho"]))
+        mg.mg_profile(h, 1)
+        mg.mg_solve(h, 1, allow_noconv=True)
+        prof = mg.mg_profile_read(h)
+        out = []
+        for l in range(H.num_levels):
+            n = H.n[l]
+            phi = torch.zeros((n,) * H.dim, dtype=torch.float64, device="cuda")
+            F = torch.zeros((H.dim,) + (n,) * H.dim, dtype=torch.float64, device="cuda")
+            mg.mg_forces(h, 0, l, phi, F)
+            torch.cuda.synchronize()
+            out.append((phi.cpu().numpy(), F.cpu().numpy()))
+        return out, prof
+    finally:
+        mg.mg_destroy(h)
+
+
+@pytest.mark.parametrize("make,prec,lim", [
+    (lambda: I.config_3d_offset_sphere(64, 4), "mixed", 66),
+    (lambda: I.config_3d_offset_sphere(64, 4), "mixed", 33),
+    (lambda: I.config_3d_offset_sphere(64, 4), "fp64", 17),
+    (lambda: I.config_3d_offset_sphere(64, 4), "fp64", 33),
+    (lambda: I.config_3d_offset_sphere(32, 3), "mixed", 34),
+    (lambda: I.config_2d_disk(64, 3), "fp64", 33),
+    (lambda: I.config_2d_disk(64, 3), "mixed", 66),
+    (lambda: I.random_hierarchy(7), "mixed", 130)])
+def test_cluster_vcycle_matches_one_kernel_per_phase(mg, make, prec, lim, monkeypatch):
+    H = make()
+    inp = I.level_inputs(H)
+    p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
+    kw = dict(nu_pre=2, nu_post=2, max_cycles=4, rel_tol=0.0, precision=p, inner_cycles=2)
+    var = "MG_CLUSTER_N64" if prec == "fp64" else "MG_CLUSTER_N32"
+    monkeypatch.setenv("MG_CLUSTER_N64", "0")
+    monkeypatch.setenv("MG_CLUSTER_N32", "0")
+    a, pa = _solve_profiled(mg, H, inp, **kw)
+    monkeypatch.setenv(var, str(lim))
+    b, pb = _solve_profiled(mg, H, inp, **kw)
+    assert "cluster_vcycle" not in pa and pb["cluster_vcycle"][0] > 0, pb
+    for l in range(H.num_levels):
+        assert np.array_equal(a[l][0], b[l][0]), (l, relmax(b[l][0], a[l][0]))
+        assert np.array_equal(a[l][1], b[l][1]), l
