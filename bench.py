@@ -429,29 +429,103 @@ def run_batch_case(args):
             inp = I.level_inputs(H)
             ins.append([{k: dev(v) for k, v in d.items()} for d in inp])
 
+        nmax = max(max(H.n) for H in Hs)
+        F = torch.empty((3,) + (nmax,) * 3, dtype=torch.float64, device="cuda")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
         def step():
+            """inputs (device-resident) into the hierarchies, solve, forces of every level"""
             for b, H in enumerate(Hs):
                 d = ins[b]
                 mg.mg_set_density(h, b, 0, d[0]["rho"], d[0]["bc_rho"], d[0]["bc_phi"])
                 for l in range(1, H.num_levels):
                     mg.mg_set_density(h, b, l, d[l]["rho"])
-            return mg.mg_solve(h, len(Hs))[1]
+            st = mg.mg_solve(h, len(Hs))[1]
+            for b, H in enumerate(Hs):
+                for l in range(H.num_levels):
+                    mg.mg_forces(h, b, l, None, F)
+            return st
 
         for _ in range(args.warmup):
             st = step()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ms = []
         for _ in range(args.steps):
+            ev0.record()
             st = step()
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.steps
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        dt = sum(ms) / len(ms) * 1e-3
         worst = max(st[b][l]["rel_res"] for b, H in enumerate(Hs) for l in range(H.num_levels))
         cyc = sum(st[b][l]["cycles"] for b, H in enumerate(Hs) for l in range(H.num_levels))
         print(json.dumps({"case": f"batch of {len(Hs)} uneven hierarchies", "zones": zones, "ms_per_solve": dt * 1e3,
                           "zones_per_s": zones / dt, "worst_rel_res": worst, "fp32_cycles_total": cyc,
-                          "autotune": bool(args.autotune)}))
+                          "autotune": bool(args.autotune), "batched_kernels": os.environ.get("MG_BATCHED", "0") == "1",
+                          "timing": "CUDA events around set_density + mg_solve + mg_forces of every level"}))
     finally:
         mg.mg_destroy(h)
+
+
+def run_scale_case(args):
+    """4 nested 256^3 levels on [-1,1]^3, 8 compact spheres (m = 3) with centres
+    in the finest box, radii U[0.02,0.1] x 2, masses U[0.5,2]; V(2,2) to 1e-10,
+    FP64 and mixed.  Prints one line per form (zones/s of set_density + solve +
+    forces, CUDA events; max errors of potential and force against the closed
+    form), not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    H = I.config_3d_spheres(args.level_n if args.level_n != 254 else 256, 4, 8)
+    inp = I.level_inputs(H)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_in = [{k: dev(v) for k, v in d.items()} for d in inp]
+    n = H.n[0]
+    F = [torch.empty((3,) + (m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
+    P = [torch.empty((m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
+    for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60,
+                                                                 rel_tol=TOL, precision=prec, inner_cycles=3))
+        try:
+            if prec == mg.MG_MIXED:
+                mg.mg_autotune(h, args.tune_cache)
+
+            def step():
+                mg.mg_set_density(h, 0, 0, d_in[0]["rho"], d_in[0]["bc_rho"], d_in[0]["bc_phi"])
+                for l in range(1, H.num_levels):
+                    mg.mg_set_density(h, 0, l, d_in[l]["rho"])
+                st = mg.mg_solve(h, 1)[1]
+                for l in range(H.num_levels):
+                    mg.mg_forces(h, 0, l, P[l], F[l])
+                return st
+
+            for _ in range(args.warmup):
+                st = step()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                ev0.record()
+                st = step()
+                ev1.record()
+                torch.cuda.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+            ep = ef = 0.0
+            for l in range(H.num_levels):
+                X = H.centres(l, 0)
+                pa, fa = H.potential(X), H.force(X)
+                ep = max(ep, float(np.max(np.abs(P[l].cpu().numpy() - pa)) / np.max(np.abs(pa))))
+                ef = max(ef, float(np.max(np.abs(np.moveaxis(F[l].cpu().numpy(), 0, -1) - fa)) / np.max(np.abs(fa))))
+            t = statistics.median(ms)
+            print(json.dumps({"case": f"4 nested {n}^3 levels, 8 spheres", "form": name, "zones": H.zones(),
+                              "ms_per_solve": t, "zones_per_s": H.zones() / (t * 1e-3),
+                              "cycles_per_level": [st[0][l]["cycles"] for l in range(H.num_levels)],
+                              "max_rel_res": max(st[0][l]["rel_res"] for l in range(H.num_levels)),
+                              "max_rel_err_phi": ep, "max_rel_err_F": ef,
+                              "timing": "CUDA events around set_density + mg_solve + mg_forces, median"}), flush=True)
+        finally:
+            mg.mg_destroy(h)
 
 
 def main():
@@ -461,7 +535,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch"],
+    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale"],
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
@@ -476,6 +550,8 @@ def main():
         run_level_case(args)
     elif args.case == "batch":
         run_batch_case(args)
+    elif args.case == "scale":
+        run_scale_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
