@@ -208,12 +208,15 @@ def profile_pass(runner, torch, steps):
     return prof
 
 
-def measured_peaks():
+def measured_peaks(key="hbm_gbs"):
+    """A measured peak (HBM copy GB/s or dense bf16 TFLOP/s) and its source."""
+    fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}[key]
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), "measured"
-    return 6800.0, "fallback"
+        if key in d:
+            return d[key], "measured"
+    return fallback, "fallback"
 
 
 def kernel_traffic(name, form):
@@ -528,6 +531,53 @@ def run_scale_case(args):
             mg.mg_destroy(h)
 
 
+def run_unet_case(args):
+    """The learned guess's 3D U-Net on a batch of 4 samples of 64^3: one
+    forward pass and one training step (forward, backward, AdamW) timed with
+    CUDA events; FLOPs counted from the architecture (2 x 27 x C_in x C_out
+    per output voxel of every 3x3x3 convolution; the backward pass counts
+    twice that: data and weight gradients).  Prints one line, not the
+    benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import unet as U
+    n, B = 64, 4
+    # (C_in, C_out, resolution divisor) of the nine convolutions
+    convs = [(3, 16, 1), (16, 16, 1), (16, 32, 2), (32, 32, 2), (32, 64, 4), (64, 64, 8), (128, 32, 4), (64, 16, 2),
+             (32, 16, 1)]
+    fwd = sum(2.0 * 27 * ci * co * B * (n // dv) ** 3 for ci, co, dv in convs)
+    rng = np.random.default_rng(I.BASE_SEED + 64)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rho, phi, res, tru = (dev(rng.standard_normal((B, n, n, n))) for _ in range(4))
+    frho = np.full(B, 1e-3)
+    u = U.mg_unet_create(n, B, seed=3)
+    try:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = {}
+        for name, fn, flops in (("forward", lambda: U.mg_unet_forward(u, B, n, rho, phi, res, frho), fwd),
+                                ("train_step", lambda: U.mg_unet_train_step(u, B, n, rho, phi, res, tru, frho,
+                                                                           lr=1e-4), 3 * fwd)):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                ev0.record()
+                fn()
+                ev1.record()
+                torch.cuda.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+            t = statistics.median(ms)
+            out[name] = {"ms": t, "tflops": flops / (t * 1e-3) / 1e12}
+        peak, src = measured_peaks(key="bf16_tflops")
+        print(json.dumps({"case": f"U-Net, batch {B} x {n}^3", "conv_flops_forward": fwd, **out,
+                          "bf16_peak_tflops": peak, "peak_source": src,
+                          "note": "times include host<->device copies of y / loss made by these calls"}))
+    finally:
+        U.mg_unet_destroy(u)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,7 +585,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale"],
+    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale", "unet"],
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
@@ -552,6 +602,8 @@ def main():
         run_batch_case(args)
     elif args.case == "scale":
         run_scale_case(args)
+    elif args.case == "unet":
+        run_unet_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

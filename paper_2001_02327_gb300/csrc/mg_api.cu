@@ -43,9 +43,8 @@ struct LevelData {
     double *tab64[MG_MAX_MG] = {}; // boundary diagonal tables of the coarse levels (device)
     float *tab32[MG_MAX_MG] = {};
     int Ls[2] = {0, 0};            // first level handled by the one-block kernel [fp64, fp32]
-    int Lc[2] = {0, 0};            // first level handled by the cluster kernel (-1: none)
-    int Lcb[2] = {0, 0};           // first level the cluster kernel runs in its CTA 0
-    MgBottom cbt[2];               // that part's one-block plan
+    int Lc[2] = {-1, -1};          // first level handled by the cluster kernel (-1: none)
+    int Llim[2] = {0, 0};          // the level-size limit that chose it
     MgBottom bt[2];
 };
 
@@ -120,49 +119,67 @@ int cluster_limit(bool fp32)
 }
 
 // Largest multigrid level (cells per edge) the cluster kernel leaves to its
-// CTA 0 (one block, shared memory, block barriers): levels this small are
-// latency-bound phases either way, and a block barrier is cheaper than a
-// cluster barrier.  MG_CLUSTER_BOTTOM overrides.
+// CTA 0 and the one-block path.  MG_CLUSTER_BOTTOM overrides.
 int cluster_bottom_limit()
 {
     const char *v = std::getenv("MG_CLUSTER_BOTTOM");
     if (v && *v)
         return std::atoi(v);
-    return 2;
+    return 8;
 }
 
-// The cluster kernel's part of the V-cycle per precision: from the first
-// multigrid level of at most `lim` cells per edge down; Lc = -1 when off.
-void plan_cluster(LevelData &ld, int dim, int csize, int lim64 = -1, int lim32 = -1)
+// The cluster kernel's plan for levels from Lc on (3D): Lc the first level of
+// at most `lim` cells per edge, Lcb the first after it of at most the cluster
+// bottom limit; false when it does not apply or does not fit.
+bool cluster_plan(const LevelData &ld, int dim, int csize, bool fp32, int lim, const mg_options &o, MgClusterPlan &p,
+                  size_t *smem, int *Lc_out)
 {
+    if (dim != 3 || csize <= 0 || lim <= 0 || ld.nmg < 3)
+        return false;
+    int Lc = -1, Lcb = ld.nmg - 1;
+    for (int L = 0; L < ld.nmg - 1; L++)
+        if (ld.g[L].N <= lim) {
+            Lc = L;
+            break;
+        }
+    if (Lc < 0)
+        return false;
     const int cb = cluster_bottom_limit();
+    for (int L = Lc + 1; L < ld.nmg; L++)
+        if (ld.g[L].N <= cb) {
+            Lcb = L;
+            break;
+        }
+    if (Lcb <= Lc)
+        return false;
+    p = MgClusterPlan{};
+    p.nlev = ld.nmg - Lc;
+    p.nclu = Lcb - Lc;
+    p.cycles = 1;
+    p.nu_pre = o.nu_pre;
+    p.nu_post = o.nu_post;
+    for (int q = 0; q < p.nlev; q++)
+        p.g[q] = ld.g[Lc + q];
+    p.bt.nlev = ld.nmg - Lcb;
+    if (p.bt.nlev > MG_BOTTOM_MAX)
+        return false;
+    for (int q = 0; q < p.bt.nlev; q++)
+        p.bt.g[q] = ld.g[Lcb + q];
+    if (!mg_cluster_layout(fp32, csize, p, smem))
+        return false;
+    *Lc_out = Lc;
+    return true;
+}
+
+void plan_cluster(LevelData &ld, int dim, int csize, const mg_options &o, int lim64 = -1, int lim32 = -1)
+{
     for (int w = 0; w < 2; w++) {
         const int lim = w ? (lim32 >= 0 ? lim32 : cluster_limit(true)) : (lim64 >= 0 ? lim64 : cluster_limit(false));
-        ld.Lc[w] = -1;
-        if (csize <= 0 || lim <= 0 || ld.nmg < 2)
-            continue;
-        int Lc = -1, Lcb = ld.nmg - 1;
-        for (int L = 0; L < ld.nmg - 1; L++)
-            if (ld.g[L].N <= lim) {
-                Lc = L;
-                break;
-            }
-        if (Lc < 0)
-            continue;
-        for (int L = Lc + 1; L < ld.nmg; L++)
-            if (ld.g[L].N <= cb) {
-                Lcb = L;
-                break;
-            }
-        MgBottom bt;
-        bt.nlev = ld.nmg - Lcb;
-        for (int q = 0; q < bt.nlev; q++)
-            bt.g[q] = ld.g[Lcb + q];
-        if (bt.nlev > MG_BOTTOM_MAX || mg_bottom_smem(dim, w == 1, bt) > MG_BOTTOM_SMEM_MAX)
-            continue;
-        ld.Lc[w] = Lc;
-        ld.Lcb[w] = Lcb;
-        ld.cbt[w] = bt;
+        MgClusterPlan p;
+        size_t smem = 0;
+        int Lc = -1;
+        ld.Lc[w] = cluster_plan(ld, dim, csize, w == 1, lim, o, p, &smem, &Lc) ? Lc : -1;
+        ld.Llim[w] = lim;
     }
 }
 
@@ -460,23 +477,19 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
                      [&] { return mg_launch_bottom(dim, fp32, P(Ls), F(Ls), bt, o.nu_pre, o.nu_post, s); });
     };
     auto cluster = [&](int cycles) {
-        MgClusterPlan p{};
-        const int Lcb = ld.Lcb[fp32 ? 1 : 0];
-        p.nlev = ld.nmg - Lc;
-        p.nclu = Lcb - Lc;
+        MgClusterPlan p;
+        size_t smem = 0;
+        int L0 = -1;
+        if (!cluster_plan(ld, dim, h->csize, fp32, ld.Llim[fp32 ? 1 : 0], o, p, &smem, &L0) ||
+            L0 != Lc)
+            return cudaErrorInvalidValue;
         p.cycles = cycles;
-        p.nu_pre = o.nu_pre;
-        p.nu_post = o.nu_post;
-        double by = 3.0 * w * cells_d(ld.g[Lcb].E, dim);
-        for (int q = 0; q < p.nlev; q++) {
-            p.g[q] = ld.g[Lc + q];
-            p.phi[q] = P(Lc + q);
-            p.f[q] = F(Lc + q);
-            if (q < p.nclu)   // smoothing sweeps, residual + restriction, prolongation
-                by += w * cells_d(ld.g[Lc + q].N, dim) * (4.0 * (o.nu_pre + o.nu_post) + 5.0);
-        }
-        p.bt = ld.cbt[fp32 ? 1 : 0];
-        return timed(h, KK_CLUSTER, by * cycles, [&] { return mg_launch_cluster(dim, fp32, p, h->csize, s); });
+        p.phi0 = P(Lc);
+        p.f0 = F(Lc);
+        double by = 3.0 * w * cells_d(ld.g[Lc].E, dim);
+        for (int q = 0; q < p.nclu; q++)   // smoothing sweeps, residual + restriction, prolongation (on chip)
+            by += w * cells_d(ld.g[Lc + q].N, dim) * (4.0 * (o.nu_pre + o.nu_post) + 5.0);
+        return timed(h, KK_CLUSTER, by * cycles, [&] { return mg_launch_cluster(fp32, p, h->csize, smem, s); });
     };
     cudaError_t e;
     if (Lstop == 0) {                                                                     // whole cycle
@@ -1192,7 +1205,7 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     for (int nb : nbs) {
         plan_bottom(ld, dim, nb);
         plan_tiles(ld, dim, o.nu_pre, o.nu_post);
-        plan_cluster(ld, h->dim, h->csize);
+        plan_cluster(ld, h->dim, h->csize, h->opt);
         const float ms = time_ms(h, 10, [&](cudaStream_t cs) { return vcycle(h, ld, true, cs); }, err);
         if (err)
             return false;
@@ -1202,7 +1215,7 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
         }
     }
     plan_bottom(ld, dim, bestnb);
-    plan_cluster(ld, h->dim, h->csize);
+    plan_cluster(ld, h->dim, h->csize, h->opt);
     te.bottom_n = bestnb;
     // 2. per level above the bottom: the tile of its pre/post pair
     const int Ls = ld.Ls[1];
@@ -1262,7 +1275,7 @@ void apply_entry(mg_hierarchy *h, LevelData &ld, const TuneEntry &te)
     plan_bottom(ld, h->dim, te.bottom_n);
     for (int L = 0; L < ld.nmg; L++)
         ld.tile[L] = L < ld.Ls[1] ? te.tile[L] : 0;
-    plan_cluster(ld, h->dim, h->csize);
+    plan_cluster(ld, h->dim, h->csize, h->opt);
 }
 
 std::vector<TuneEntry> read_cache(const char *path)
@@ -1498,7 +1511,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
             }
             plan_bottom(ld, dim);
             plan_tiles(ld, dim, o.nu_pre, o.nu_post);
-            plan_cluster(ld, h->dim, h->csize);
+            plan_cluster(ld, h->dim, h->csize, h->opt);
         }
     if (e == cudaSuccess) {
         std::vector<double> fr((size_t)batch * MG_MAX_LEVELS, 0.0);

@@ -82,15 +82,25 @@ struct MgBottom {
 };
 
 // One thread-block cluster running the V-cycle from a multigrid level Lc down
-// (levels Lc + q, q = 0..nlev-1): levels q < nclu phase by phase over all
-// CTAs of the cluster with cluster barriers between phases, levels from nclu
-// down in CTA 0 (the one-block path, plan `bt`).  nclu < nlev.
-#define MG_CLUSTER_THREADS 1024
+// (levels Lc + q, q = 0..nlev-1) with every array in the shared memory of the
+// cluster's CTAs (3D): levels q < nclu are split by z-planes over the CTAs
+// (CTA r owns planes [ceil(r E / C), ceil((r+1) E / C))), level nclu lives in
+// CTA 0, and the levels below it are the one-block path (plan `bt`) of CTA 0.
+// In every CTA, level q's Phi planes start at element off[q] and its f planes
+// pmax[q] planes later; the one-block scratch starts at byte `scratch`.
+// phi[0] / f[0]: the global arrays of level Lc, loaded at the start (both)
+// and stored at the end (Phi).  nclu >= 1, nclu < nlev.
+#define MG_CLUSTER_THREADS 512
+#define MG_CLUSTER_PLANES 256
+#define MG_CLUSTER_SMEM_MAX (220 * 1024)
 struct MgClusterPlan {
     int nlev, nclu, cycles, nu_pre, nu_post;
     MgGeom g[MG_MAX_MG];
-    void *phi[MG_MAX_MG];
-    void *f[MG_MAX_MG];
+    void *phi0;
+    const void *f0;
+    int pmax[MG_MAX_MG];
+    int off[MG_MAX_MG + 1];
+    int scratch;
     MgBottom bt;
 };
 
@@ -164,9 +174,12 @@ cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cu
 cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const double *phi_blk, double *prev,
                                  int stencil, unsigned long long *cmax, double *scal, cudaStream_t s);
 // Cluster V-cycle: mg_cluster_prepare picks the cluster size (16 CTAs where
-// the device can co-schedule them, else 8; 0 if neither) once per process.
+// the device can co-schedule them, else 8; 0 if neither) once per process;
+// mg_cluster_layout fills the shared-memory layout of a plan (false if it
+// does not fit) and returns its dynamic shared memory in *smem.
 int mg_cluster_prepare();
-cudaError_t mg_launch_cluster(int dim, bool fp32, const MgClusterPlan &p, int csize, cudaStream_t s);
+bool mg_cluster_layout(bool fp32, int csize, MgClusterPlan &p, size_t *smem);
+cudaError_t mg_launch_cluster(bool fp32, const MgClusterPlan &p, int csize, size_t smem, cudaStream_t s);
 cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os, double *dst, int Ed, int od,
                               cudaStream_t s);
 cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const double *rho_blk, double frho,

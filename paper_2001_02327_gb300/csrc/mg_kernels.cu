@@ -119,17 +119,18 @@ __device__ __forceinline__ const float *tab_of<float>(const MgGeom &g) { return 
 // touches no multigrid boundary, always 0 on the finest level where the outer
 // ring holds Dirichlet data).
 template <typename T, int DIM>
-__device__ __forceinline__ T neighbour_sum_s(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, int p,
-                                            int sy, int sz, int &cls)
+__device__ __forceinline__ T neighbour_sum_ptr(const T *c, const T *d, const T *u, const MgGeom &g, int i, int j,
+                                              int k, int sy, int &cls)
 {
+    // c: the cell; d, u: the same cell in the planes k-1 and k+1 (3D)
     const int N = g.N;
     const bool coarse = g.L > 0;
     const bool inner = !coarse || (i > 1 && i < N && j > 1 && j < N && (DIM == 2 || (k > 1 && k < N)));
     if (inner) {
         cls = 0;
-        T s = (phi[p - 1] + phi[p + 1]) + (phi[p - sy] + phi[p + sy]);
+        T s = (c[-1] + c[1]) + (c[-sy] + c[sy]);
         if (DIM == 3)
-            s += phi[p - sz] + phi[p + sz];
+            s += d[0] + u[0];
         return s;
     }
     // left neighbour dropped at index 1 (ghost = -self: goes to the diagonal)
@@ -137,17 +138,26 @@ __device__ __forceinline__ T neighbour_sum_s(const T *__restrict__ phi, const Mg
     // neighbour dropped at index N (ghost cR Phi_N: diagonal)
     const bool tieN = g.tie && N >= 2;
     cls = 0;
-    auto axis = [&](int c, int st, int shift) -> T {
-        const bool lo = c == 1, hi = c == N;
+    auto axis = [&](int a, const T *lp, const T *rp, int shift) -> T {
+        const bool lo = a == 1, hi = a == N;
         cls |= ((lo ? 1 : 0) | (hi ? 2 : 0)) << shift;
-        const T l = (!lo && !(hi && tieN)) ? phi[p - st] : T(0);
-        const T r = !hi ? phi[p + st] : T(0);
+        const T l = (!lo && !(hi && tieN)) ? *lp : T(0);
+        const T r = !hi ? *rp : T(0);
         return l + r;
     };
-    T s = axis(i, 1, 0) + axis(j, sy, 2);
+    T s = axis(i, c - 1, c + 1, 0) + axis(j, c - sy, c + sy, 2);
     if (DIM == 3)
-        s += axis(k, sz, 4);
+        s += axis(k, d, u, 4);
     return s;
+}
+
+// Ghost-folded neighbour sum at index p of an array with strides (1, sy, sz)
+template <typename T, int DIM>
+__device__ __forceinline__ T neighbour_sum_s(const T *__restrict__ phi, const MgGeom &g, int i, int j, int k, int p,
+                                            int sy, int sz, int &cls)
+{
+    return neighbour_sum_ptr<T, DIM>(phi + p, phi + p - (DIM == 3 ? sz : 0), phi + p + (DIM == 3 ? sz : 0), g, i, j,
+                                     k, sy, cls);
 }
 
 // the same on a level array of edge g.E
@@ -208,14 +218,23 @@ __device__ __forceinline__ void op_smooth_colour(T *__restrict__ phi, const T *_
     }
 }
 
+// f - lap(Phi) at a cell given by pointers to it and to it in the planes k-1, k+1
+template <typename T, int DIM>
+__device__ __forceinline__ T residual_ptr(const T *c, const T *d, const T *u, T fv, const MgGeom &g, int i, int j,
+                                          int k)
+{
+    int cls;
+    const T other = neighbour_sum_ptr<T, DIM>(c, d, u, g, i, j, k, g.E, cls);
+    return fv - (other + diag_of<T, DIM>(g, cls) * c[0]) * geo_inv_h2<T>(g);
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g, int i,
                                          int j, int k)
 {
     const int p = lin<DIM>(i, j, k, g.E);
-    int cls;
-    const T other = neighbour_sum<T, DIM>(phi, g, i, j, k, p, cls);
-    return f[p] - (other + diag_of<T, DIM>(g, cls) * phi[p]) * geo_inv_h2<T>(g);
+    const int sz = DIM == 3 ? g.E * g.E : 0;
+    return residual_ptr<T, DIM>(phi + p, phi + p - sz, phi + p + sz, f[p], g, i, j, k);
 }
 
 // Residual (Sec. 2.3 step 4) restricted to the next coarser level by the
@@ -284,9 +303,10 @@ __device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, T &
 // Prolongation and correction (Sec. 2.3 step 10; bi/trilinear 3/4-1/4
 // weights per axis, i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse
 // ghosts by the rule, evaluated one axis at a time.
-// P(Phi_c) at fine active cell f (Sec. 2.3 step 10)
-template <typename T, int DIM>
-__device__ __forceinline__ T prolong_value(const T *__restrict__ phi_c, const MgGeom &gc, const int *f)
+// P(Phi_c) at fine active cell f (Sec. 2.3 step 10); plane(kz) returns the
+// coarse plane kz (the whole array in 2D)
+template <typename T, int DIM, typename Planes>
+__device__ __forceinline__ T prolong_value_pl(const Planes &plane, const MgGeom &gc, const int *f)
 {
     const int Ec = gc.E;
     int idx[3][2];
@@ -303,23 +323,32 @@ __device__ __forceinline__ T prolong_value(const T *__restrict__ phi_c, const Mg
     if (DIM == 3) {
         T zsum = T(0);
         for (int c = 0; c < 2; c++) {
+            const T *pl = plane(idx[2][c]);
             T ysum = T(0);
             for (int b = 0; b < 2; b++) {
-                const int row = (idx[2][c] * Ec + idx[1][b]) * Ec;
-                const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
+                const int row = idx[1][b] * Ec;
+                const T xv = w[0][0] * pl[row + idx[0][0]] + w[0][1] * pl[row + idx[0][1]];
                 ysum += w[1][b] * xv;
             }
             zsum += w[2][c] * ysum;
         }
         return zsum;
     }
+    const T *pl = plane(0);
     T ysum = T(0);
     for (int b = 0; b < 2; b++) {
         const int row = idx[1][b] * Ec;
-        const T xv = w[0][0] * phi_c[row + idx[0][0]] + w[0][1] * phi_c[row + idx[0][1]];
+        const T xv = w[0][0] * pl[row + idx[0][0]] + w[0][1] * pl[row + idx[0][1]];
         ysum += w[1][b] * xv;
     }
     return ysum;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T prolong_value(const T *__restrict__ phi_c, const MgGeom &gc, const int *f)
+{
+    const int E2 = gc.E * gc.E;
+    return prolong_value_pl<T, DIM>([&](int kz) { return phi_c + (DIM == 3 ? kz * E2 : 0); }, gc, f);
 }
 
 // Prolongation and correction (Sec. 2.3 step 10; bi/trilinear 3/4-1/4
@@ -525,14 +554,14 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g
 }
 
 // ---------------------------------------------------------------------------
-// Cluster V-cycle: one thread-block cluster runs every phase of the levels
-// from Lc down (Sec. 2.3 steps 2-13 restricted to those levels), phases
-// separated by cluster barriers instead of kernel launches.  The arrays stay
-// where they are (global memory, L2-resident at these sizes); the barrier's
-// release/acquire at cluster scope orders each phase's writes before the next
-// phase's reads in every CTA.  Same per-cell arithmetic and phase order as
-// the one-kernel-per-phase path; the levels from nclu down run in CTA 0
-// through the one-block path while the other CTAs wait at the barrier.
+// Cluster V-cycle with the levels in distributed shared memory (3D).  One
+// thread-block cluster holds the multigrid levels from Lc down: each of the
+// larger ones split by z-planes over the CTAs, read across CTAs through
+// shared::cluster addresses, the smallest in CTA 0.  Phases are separated by
+// cluster barriers (release/acquire at cluster scope); no phase touches global
+// memory except the load of level Lc at the start and the store of its Phi at
+// the end.  Same per-cell arithmetic and order of phases as the
+// one-kernel-per-phase path.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned cluster_rank()
 {
@@ -554,52 +583,160 @@ __device__ __forceinline__ void cluster_barrier()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-template <typename T, int DIM>
+// generic address of the same shared-memory location in CTA `rank` of the cluster
+template <typename T>
+__device__ __forceinline__ T *cluster_map(T *p, unsigned rank)
+{
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((unsigned long long)p), "r"(rank));
+    return reinterpret_cast<T *>(out);
+}
+
+// first z-plane of CTA r when E planes are split over C CTAs
+__host__ __device__ __forceinline__ int cluster_first_plane(int r, int E, int C) { return (r * E + C - 1) / C; }
+
+template <typename T>
 __global__ void __launch_bounds__(MG_CLUSTER_THREADS, 1) k_cluster_vcycle(const __grid_constant__ MgClusterPlan P)
 {
+    constexpr int DIM = 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T rbuf[MG_CLUSTER_THREADS];
+    __shared__ T *tabP[MG_CLUSTER_PLANES];
+    __shared__ T *tabF[MG_CLUSTER_PLANES];
+    __shared__ int tbo[MG_MAX_MG + 1];
+    T *sm = reinterpret_cast<T *>(smem_raw);
     const int rank = (int)cluster_rank(), C = (int)cluster_ctas();
-    const int tid = threadIdx.x;
-    // work items: consecutive warps go to different CTAs (each warp keeps 32
-    // consecutive items), so that even a small level is spread over every SM
-    const int t0 = (((tid >> 5) * C + rank) << 5) + (tid & 31), stride = C * blockDim.x;
-    const int grp = tid >> 8, lt = tid & 255, ngrp = blockDim.x >> 8;   // 256-thread restriction tiles
-    auto PHI = [&](int q) { return static_cast<T *>(P.phi[q]); };
-    auto F = [&](int q) { return static_cast<T *>(P.f[q]); };
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int nl = P.nclu + 1;                       // levels held as planes (the last one in CTA 0)
+    auto owner = [&](int q, int k) { return q < P.nclu ? (k * C) / P.g[q].E : 0; };
+    auto first = [&](int q, int r) { return q < P.nclu ? cluster_first_plane(r, P.g[q].E, C) : (r == 0 ? 0 : P.g[q].E); };
+    if (tid == 0) {
+        tbo[0] = 0;
+        for (int q = 0; q < nl; q++)
+            tbo[q + 1] = tbo[q] + P.g[q].E;
+    }
+    __syncthreads();
+    // plane pointer tables (shared::cluster addresses as generic pointers)
+    for (int q = 0; q < nl; q++) {
+        const int E = P.g[q].E, E2 = E * E;
+        for (int k = tid; k < E; k += nth) {
+            const int o = owner(q, k), lk = k - first(q, o);
+            tabP[tbo[q] + k] = cluster_map(sm + P.off[q] + lk * E2, o);
+            tabF[tbo[q] + k] = cluster_map(sm + P.off[q] + (P.pmax[q] + lk) * E2, o);
+        }
+    }
+    // own planes start at zero (ghost layers and rings stay zero); level Lc from global
+    for (int t = tid; t < P.off[nl]; t += nth)
+        sm[t] = T(0);
+    __syncthreads();
+    {
+        const int E = P.g[0].E, E2 = E * E;
+        const int z0 = first(0, rank), z1 = first(0, rank + 1);
+        const T *gp = static_cast<const T *>(P.phi0), *gf = static_cast<const T *>(P.f0);
+        for (int t = tid; t < (z1 - z0) * E2; t += nth) {
+            sm[P.off[0] + t] = gp[z0 * E2 + t];
+            sm[P.off[0] + P.pmax[0] * E2 + t] = gf[z0 * E2 + t];
+        }
+    }
+    cluster_barrier();
+    auto PL = [&](int q, int k) { return tabP[tbo[q] + k]; };
+    auto FL = [&](int q, int k) { return tabF[tbo[q] + k]; };
+    // interior planes [kl, kh) of level q owned by this CTA
+    auto own = [&](int q, int &kl, int &kh) {
+        kl = max(first(q, rank), 1);
+        kh = min(first(q, rank + 1), P.g[q].N + 1);
+    };
     auto smooth = [&](int q, int sweeps) {
+        const MgGeom &g = P.g[q];
+        const int N = g.N, E = g.E, half = (N + 1) >> 1;
+        const T h2 = geo_h2<T>(g);
+        int kl, kh;
+        own(q, kl, kh);
+        const int total = half * N * max(kh - kl, 0);
         for (int sw = 0; sw < sweeps; sw++)
-            for (int c = 0; c < 2; c++) {
-                op_smooth_colour<T, DIM>(PHI(q), F(q), P.g[q], c, t0, stride);
+            for (int colour = 0; colour < 2; colour++) {
+                Walk3 w(tid, nth, half, N);
+                for (int t = tid; t < total; t += nth, w.next()) {
+                    const int j = w.y + 1, k = w.z + kl;
+                    const int i = ((((1 + j + k) & 1) == colour) ? 1 : 2) + 2 * w.x;
+                    if (i > N)
+                        continue;
+                    const int p = j * E + i;
+                    T *c = PL(q, k) + p;
+                    int cls;
+                    const T other = neighbour_sum_ptr<T, DIM>(c, PL(q, k - 1) + p, PL(q, k + 1) + p, g, i, j, k, E, cls);
+                    c[0] = (other - h2 * FL(q, k)[p]) * neg_inv_diag<T, DIM>(g, cls);
+                }
                 cluster_barrier();
             }
     };
     for (int cyc = 0; cyc < P.cycles; cyc++) {
         for (int q = 0; q < P.nclu; q++) {
             smooth(q, P.nu_pre);
-            int nx, ny, nz;
-            resid_restrict_tiles(DIM, P.g[q + 1].N, nx, ny, nz);
-            const int ntile = nx * ny * nz, per = ngrp * C;
-            for (int base = 0; base < ntile; base += per) {
-                const int tile = base + grp * C + rank;
-                const bool ok = tile < ntile;
-                const int tt = ok ? tile : 0;
-                const int ty = div_small(tt, nx), tz = div_small(ty, ny);
-                resid_restrict_tile<T, DIM>(PHI(q), F(q), P.g[q], PHI(q + 1), F(q + 1), P.g[q + 1], tt - ty * nx,
-                                            ty - tz * ny, tz, lt, ok, rbuf + (grp << 8));
-                __syncthreads();
+            // residual and restriction into level q + 1: coarse cells of own planes
+            const MgGeom &gf = P.g[q], &gc = P.g[q + 1];
+            const int Nf = gf.N, Ef = gf.E, Nc = gc.N, Ec = gc.E;
+            const T wgt = T(0.125);
+            int kl, kh;
+            own(q + 1, kl, kh);
+            const int total = Nc * Nc * max(kh - kl, 0);
+            Walk3 w(tid, nth, Nc, Nc);
+            for (int t = tid; t < total; t += nth, w.next()) {
+                const int I = w.x + 1, J = w.y + 1, K = w.z + kl;
+                T s = T(0);
+                for (int dk = 0; dk < 2; dk++) {
+                    const int k = 2 * K - 1 + dk;
+                    if (k > Nf)
+                        continue;
+                    for (int dj = 0; dj < 2; dj++) {
+                        const int j = 2 * J - 1 + dj;
+                        if (j > Nf)
+                            continue;
+                        for (int di = 0; di < 2; di++) {
+                            const int i = 2 * I - 1 + di;
+                            if (i > Nf)
+                                continue;
+                            const int p = j * Ef + i;
+                            s += residual_ptr<T, DIM>(PL(q, k) + p, PL(q, k - 1) + p, PL(q, k + 1) + p, FL(q, k)[p],
+                                                      gf, i, j, k);
+                        }
+                    }
+                }
+                const int pc = J * Ec + I;
+                FL(q + 1, K)[pc] = wgt * s;
+                PL(q + 1, K)[pc] = T(0);
             }
             cluster_barrier();
         }
-        if (rank == 0)
-            bottom_body<T, DIM>(PHI(P.nclu), F(P.nclu), P.bt, P.nu_pre, P.nu_post, smem_raw);
+        if (rank == 0) {
+            const int E = P.g[P.nclu].E;
+            T *pb = sm + P.off[P.nclu];
+            bottom_body<T, DIM>(pb, pb + E * E * E, P.bt, P.nu_pre, P.nu_post, smem_raw + P.scratch);
+        }
         cluster_barrier();
         for (int q = P.nclu - 1; q >= 0; q--) {
-            op_prolong<T, DIM>(PHI(q + 1), P.g[q + 1], PHI(q), P.g[q], t0, stride);
+            const MgGeom &gf = P.g[q], &gc = P.g[q + 1];
+            const int Nf = gf.N, Ef = gf.E;
+            int kl, kh;
+            own(q, kl, kh);
+            const int total = Nf * Nf * max(kh - kl, 0);
+            Walk3 w(tid, nth, Nf, Nf);
+            for (int t = tid; t < total; t += nth, w.next()) {
+                const int f[3] = {w.x + 1, w.y + 1, w.z + kl};
+                const T v = prolong_value_pl<T, DIM>([&](int kz) { return (const T *)PL(q + 1, kz); }, gc, f);
+                PL(q, f[2])[f[1] * Ef + f[0]] += v;
+            }
             cluster_barrier();
             smooth(q, P.nu_post);
         }
     }
+    {
+        const int E = P.g[0].E, E2 = E * E;
+        const int z0 = first(0, rank), z1 = first(0, rank + 1);
+        T *gp = static_cast<T *>(P.phi0);
+        for (int t = tid; t < (z1 - z0) * E2; t += nth)
+            gp[z0 * E2 + t] = sm[P.off[0] + t];
+    }
+    cluster_barrier();   // no CTA leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -1765,12 +1902,12 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
     return cudaGetLastError();
 }
 
-template <typename T, int DIM>
-static cudaError_t cluster_attrs(int smem)
+template <typename T>
+static cudaError_t cluster_attrs()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_cluster_vcycle<T, DIM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute(k_cluster_vcycle<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (!e)
-        e = cudaFuncSetAttribute(k_cluster_vcycle<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(k_cluster_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MG_CLUSTER_SMEM_MAX);
     return e;
 }
 
@@ -1800,40 +1937,54 @@ int mg_cluster_prepare()
     }
     if (dev_done == dev)
         return chosen;
-    const int smem = MG_BOTTOM_SMEM_MAX;
-    if (cluster_attrs<float, 3>(smem) || cluster_attrs<double, 3>(smem) || cluster_attrs<float, 2>(smem) ||
-        cluster_attrs<double, 2>(smem)) {
+    dev_done = dev;
+    chosen = 0;
+    if (cluster_attrs<float>() || cluster_attrs<double>()) {
         cudaGetLastError();
-        dev_done = dev;
-        chosen = 0;
         return 0;
     }
-    chosen = 0;
     for (int cs : {16, 8}) {
         cudaLaunchAttribute at[1];
-        cudaLaunchConfig_t cfg = cluster_config(cs, smem, nullptr, at);
+        cudaLaunchConfig_t cfg = cluster_config(cs, MG_CLUSTER_SMEM_MAX, nullptr, at);
         int n64 = 0, n32 = 0;
-        if (cudaOccupancyMaxActiveClusters(&n64, k_cluster_vcycle<double, 3>, &cfg) == cudaSuccess &&
-            cudaOccupancyMaxActiveClusters(&n32, k_cluster_vcycle<float, 3>, &cfg) == cudaSuccess && n64 > 0 &&
-            n32 > 0) {
+        if (cudaOccupancyMaxActiveClusters(&n64, k_cluster_vcycle<double>, &cfg) == cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&n32, k_cluster_vcycle<float>, &cfg) == cudaSuccess && n64 > 0 && n32 > 0) {
             chosen = cs;
             break;
         }
         cudaGetLastError();
     }
-    dev_done = dev;
     return chosen;
 }
 
-cudaError_t mg_launch_cluster(int dim, bool fp32, const MgClusterPlan &p, int csize, cudaStream_t s)
+bool mg_cluster_layout(bool fp32, int csize, MgClusterPlan &p, size_t *smem)
+{
+    if (csize <= 0 || p.nclu < 1 || p.nclu >= p.nlev)
+        return false;
+    const size_t w = fp32 ? 4 : 8;
+    long planes = 0, off = 0;
+    for (int q = 0; q <= p.nclu; q++) {
+        const int E = p.g[q].E;
+        p.pmax[q] = q < p.nclu ? (E + csize - 1) / csize : E;
+        p.off[q] = (int)off;
+        off += 2L * p.pmax[q] * E * E;
+        planes += E;
+    }
+    p.off[p.nclu + 1] = (int)off;
+    const size_t sb = (off * w + 15) / 16 * 16;
+    p.scratch = (int)sb;
+    const size_t total = sb + mg_bottom_smem(3, fp32, p.bt);
+    if (planes > MG_CLUSTER_PLANES || total > MG_CLUSTER_SMEM_MAX)
+        return false;
+    *smem = total;
+    return true;
+}
+
+cudaError_t mg_launch_cluster(bool fp32, const MgClusterPlan &p, int csize, size_t smem, cudaStream_t s)
 {
     cudaLaunchAttribute at[1];
-    const cudaLaunchConfig_t cfg = cluster_config(csize, mg_bottom_smem(dim, fp32, p.bt), s, at);
-    if (dim == 3)
-        return fp32 ? cudaLaunchKernelEx(&cfg, k_cluster_vcycle<float, 3>, p)
-                    : cudaLaunchKernelEx(&cfg, k_cluster_vcycle<double, 3>, p);
-    return fp32 ? cudaLaunchKernelEx(&cfg, k_cluster_vcycle<float, 2>, p)
-                : cudaLaunchKernelEx(&cfg, k_cluster_vcycle<double, 2>, p);
+    const cudaLaunchConfig_t cfg = cluster_config(csize, smem, s, at);
+    return fp32 ? cudaLaunchKernelEx(&cfg, k_cluster_vcycle<float>, p) : cudaLaunchKernelEx(&cfg, k_cluster_vcycle<double>, p);
 }
 
 size_t mg_tb_smem(int dim, bool fp32, int tile, int halo)

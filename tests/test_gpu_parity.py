@@ -506,15 +506,16 @@ def _solve_profiled(mg, H, inp, **kw):
 
 
 @pytest.mark.parametrize("make,prec,lim", [
-    (lambda: I.config_3d_offset_sphere(64, 4), "mixed", 66),
     (lambda: I.config_3d_offset_sphere(64, 4), "mixed", 33),
+    (lambda: I.config_3d_offset_sphere(64, 4), "mixed", 17),
     (lambda: I.config_3d_offset_sphere(64, 4), "fp64", 17),
     (lambda: I.config_3d_offset_sphere(64, 4), "fp64", 33),
     (lambda: I.config_3d_offset_sphere(32, 3), "mixed", 34),
-    (lambda: I.config_2d_disk(64, 3), "fp64", 33),
-    (lambda: I.config_2d_disk(64, 3), "mixed", 66),
-    (lambda: I.random_hierarchy(7), "mixed", 130)])
+    (lambda: I.paper_3d(48), "fp64", 25),
+    (lambda: I.random_hierarchy(7), "mixed", 50)])
 def test_cluster_vcycle_matches_one_kernel_per_phase(mg, make, prec, lim, monkeypatch):
+    """The V-cycle from a level down in one cluster with the levels in
+    distributed shared memory gives bit-identical results."""
     H = make()
     inp = I.level_inputs(H)
     p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
@@ -529,3 +530,12 @@ def test_cluster_vcycle_matches_one_kernel_per_phase(mg, make, prec, lim, monkey
     for l in range(H.num_levels):
         assert np.array_equal(a[l][0], b[l][0]), (l, relmax(b[l][0], a[l][0]))
         assert np.array_equal(a[l][1], b[l][1]), l
+
+
+def test_cluster_vcycle_is_3d_only(mg, monkeypatch):
+    H = I.config_2d_disk(64, 3)
+    inp = I.level_inputs(H)
+    monkeypatch.setenv("MG_CLUSTER_N64", "33")
+    monkeypatch.setenv("MG_CLUSTER_N32", "33")
+    b, pb = _solve_profiled(mg, H, inp, max_cycles=3, rel_tol=0.0)
+    assert "cluster_vcycle" not in pb
