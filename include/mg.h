@@ -84,19 +84,27 @@ enum { MG_IFACE_BUFFER = 0,  /* Sec. 2.1 (default): the outer ring holds potenti
                                 multigrid solves Omega alone with the inner ring as
                                 its Dirichlet boundary (M = n active cells) */
 
-/* Geometry of one hierarchy (Sec. 2.1).  Level l has n[l] cells per edge
- * (>= 2; even above level 0; at most 1286 in 3D), lower corner lo[l] and
- * cell size h0 / 2^l.  For l > 0 the
- * patch must sit on parent cell faces, its lower corner o[a] whole parent
- * cells above the parent's, with 1 <= o[a] <= n[l-1] - n[l]/2 - 1 so that
- * every buffer cell interpolates from cells the parent solves for. */
+/* Geometry of one hierarchy (Sec. 2.1): num_levels patches, patch 0 the
+ * base.  Patch l has n[l] cells per edge (>= 2; even for l > 0; at most 1286
+ * in 3D) and lower corner lo[l].  Its parent is patch l-1 (tree = 0: a chain
+ * of nested levels, one patch per refinement level) or patch parent[l] <
+ * l (tree = 1: several patches may share a parent, the patch-based refinement
+ * of Sec. 5); a patch's cell size is h0 / 2^depth, depth = the number of
+ * steps to the base.  Every "level" argument of the calls below is a patch
+ * index.  A child must sit on parent cell faces, its lower corner o[a] whole
+ * parent cells above the parent's, with 1 <= o[a] <= n[parent] - n[l]/2 - 1
+ * so that every buffer cell interpolates from cells the parent solves for.
+ * Sibling patches are solved independently (each from its parent); their
+ * overlap, if any, is not reconciled. */
 typedef struct {
     int dim;                          /* 2 or 3 */
-    int num_levels;                   /* 1..MG_MAX_LEVELS, level 0 is the base */
+    int num_levels;                   /* 1..MG_MAX_LEVELS patches, patch 0 is the base */
     int n[MG_MAX_LEVELS];
     double lo[MG_MAX_LEVELS][3];
-    double h0;                        /* cell size of level 0 (> 0) */
+    double h0;                        /* cell size of patch 0 (> 0) */
     double G;                         /* gravitational constant of Eq. 1 */
+    int tree;                         /* 0: parent of patch l is l-1; 1: parent[l] */
+    int parent[MG_MAX_LEVELS];        /* tree = 1: parent patch of l > 0, < l */
 } mg_hierarchy_desc;
 
 /* Solver options; mg_default_options fills the paper's choices. */

@@ -12,12 +12,12 @@ import numpy as np
 
 
 def covered_mask(H, l):
-    """True on the cells of Omega^l (n^d) that Omega^{l+1} covers."""
+    """True on the cells of Omega^l (n^d) that a child patch covers."""
     n = H.n[l]
     mask = np.zeros((n,) * H.dim, dtype=bool)
-    if l + 1 < H.num_levels:
-        o = H.offset(l + 1)
-        w = H.n[l + 1] // 2
+    for c in H.children(l):
+        o = H.offset(c)
+        w = H.n[c] // 2
         sl = tuple(slice(o[a], o[a] + w) for a in reversed(range(H.dim)))  # C order (z,y,x)
         mask[sl] = True
     return mask

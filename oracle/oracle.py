@@ -153,14 +153,14 @@ def solve_hierarchy(H, inputs, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10
             inner = tuple(slice(1, n + 3) for _ in range(dim))
             phi[inner] = 0.0
         else:
-            P = out[l - 1]
-            interface_fill(dim, H.n[l - 1], P["phi"], P["rho"], n, H.offset(l), phi, rho,
+            P = out[H.parent(l)]
+            interface_fill(dim, H.n[H.parent(l)], P["phi"], P["rho"], n, H.offset(l), phi, rho,
                            guess=(guess == "interp"))
         pad_into(rho, inputs[l]["rho"], 2)
         if l > 0 and interface == "frozen":
             # inner-ring potential by the same linear interpolation as the outer ring
             ring_phi, ring_rho = np.zeros_like(phi), np.zeros_like(rho)
-            interface_fill(dim, H.n[l - 1], P["phi"], P["rho"], n, H.offset(l), ring_phi, ring_rho, guess=True)
+            interface_fill(dim, H.n[H.parent(l)], P["phi"], P["rho"], n, H.offset(l), ring_phi, ring_rho, guess=True)
             gam = tuple(slice(1, n + 3) for _ in range(dim))
             om = tuple(slice(2, n + 2) for _ in range(dim))
             keep = phi[om].copy()

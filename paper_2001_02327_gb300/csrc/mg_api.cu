@@ -23,6 +23,7 @@ namespace {
 
 struct LevelData {
     int n = 0, M = 0, nmg = 0;
+    int parent = -1;               // parent patch (-1 for the base)
     int off[3] = {0, 0, 0};
     double h = 0.0;
     MgGeom g[MG_MAX_MG];
@@ -401,6 +402,18 @@ mg_status check_options(const mg_options &o)
     return MG_OK;
 }
 
+// parent patch of patch l > 0, and the refinement depth of a patch
+int desc_parent(const mg_hierarchy_desc &d, int l) { return d.tree ? d.parent[l] : l - 1; }
+int desc_depth(const mg_hierarchy_desc &d, int l)
+{
+    int k = 0;
+    while (l > 0 && k <= MG_MAX_LEVELS) {
+        l = desc_parent(d, l);
+        k++;
+    }
+    return k;
+}
+
 mg_status check_desc(const mg_hierarchy_desc &d, int b, int dim0)
 {
     if (d.dim != 2 && d.dim != 3)
@@ -411,6 +424,11 @@ mg_status check_desc(const mg_hierarchy_desc &d, int b, int dim0)
         return fail(nullptr, MG_EINVAL, "hierarchy %d: num_levels %d out of range", b, d.num_levels);
     if (!(d.h0 > 0.0) || !std::isfinite(d.h0) || !std::isfinite(d.G))
         return fail(nullptr, MG_EINVAL, "hierarchy %d: h0 must be positive and G finite", b);
+    if (d.tree != 0 && d.tree != 1)
+        return fail(nullptr, MG_EINVAL, "hierarchy %d: tree must be 0 or 1", b);
+    for (int l = 1; l < d.num_levels; l++)
+        if (d.tree && (d.parent[l] < 0 || d.parent[l] >= l))
+            return fail(nullptr, MG_EINVAL, "hierarchy %d patch %d: parent %d not in [0, %d)", b, l, d.parent[l], l);
     for (int l = 0; l < d.num_levels; l++) {
         const int n = d.n[l];
         if (n < 2 || n + 2 > (1 << (MG_MAX_MG - 1)) || (l > 0 && (n & 1)))
@@ -419,16 +437,17 @@ mg_status check_desc(const mg_hierarchy_desc &d, int b, int dim0)
             return fail(nullptr, MG_EINVAL, "hierarchy %d level %d: n=%d exceeds 1286 in 3D", b, l, n);
         if (l == 0)
             continue;
-        const double hp = d.h0 / (double)(1L << (l - 1));
+        const int pl = desc_parent(d, l);
+        const double hp = d.h0 / (double)(1L << desc_depth(d, pl));
         for (int a = 0; a < d.dim; a++) {
-            const double o = (d.lo[l][a] - d.lo[l - 1][a]) / hp;
+            const double o = (d.lo[l][a] - d.lo[pl][a]) / hp;
             const double r = std::floor(o + 0.5);
             if (std::fabs(o - r) > 1e-6)
                 return fail(nullptr, MG_EINVAL, "hierarchy %d level %d axis %d: patch not on parent cell faces", b, l, a);
-            if (r < 1.0 || r > (double)(d.n[l - 1] - n / 2 - 1))
+            if (r < 1.0 || r > (double)(d.n[pl] - n / 2 - 1))
                 return fail(nullptr, MG_EINVAL,
                             "hierarchy %d level %d axis %d: offset %g outside [1, %d] parent cells", b, l, a, r,
-                            d.n[l - 1] - n / 2 - 1);
+                            d.n[pl] - n / 2 - 1);
         }
     }
     return MG_OK;
@@ -571,7 +590,7 @@ cudaError_t level_prelude(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
     double *ds = level_scal(h, b, l);
     cudaError_t e;
     if (l > 0) {
-        const LevelData &pd = h->lev[b][l - 1];
+        const LevelData &pd = h->lev[b][ld.parent];
         const int gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
         const double by = 8.0 * cells_d(ld.n + 4, dim) + 16.0 * (cells_d(ld.n + 2, dim) - cells_d(ld.n, dim));
         e = timed(h, KK_IFACE, by, [&] {
@@ -814,7 +833,7 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
             if (l == 0) {
                 P.gmode = ld.guess_set ? 2 : -1;
             } else {
-                const LevelData &pd = h->lev[b][l - 1];
+                const LevelData &pd = h->lev[b][ld.parent];
                 P.np = pd.n;
                 P.phi_p = pd.phi[0];
                 P.rho_p = pd.rho;
@@ -1406,12 +1425,13 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
         for (int l = 0; l < d.num_levels; l++) {
             LevelData &ld = h->lev[b][l];
             ld.n = d.n[l];
-            ld.h = d.h0 / (double)(1L << l);
+            ld.h = d.h0 / (double)(1L << desc_depth(d, l));
             ld.frozen = l > 0 && o.interface == MG_IFACE_FROZEN;
             if (l > 0) {
-                const double hp = d.h0 / (double)(1L << (l - 1));
+                ld.parent = desc_parent(d, l);
+                const double hp = d.h0 / (double)(1L << desc_depth(d, ld.parent));
                 for (int a = 0; a < dim; a++)
-                    ld.off[a] = (int)std::floor((d.lo[l][a] - d.lo[l - 1][a]) / hp + 0.5);
+                    ld.off[a] = (int)std::floor((d.lo[l][a] - d.lo[ld.parent][a]) / hp + 0.5);
             }
             build_geometry(ld, dim);
             for (int L = 0; L < ld.nmg; L++) {
@@ -1517,7 +1537,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
         std::vector<double> fr((size_t)batch * MG_MAX_LEVELS, 0.0);
         for (int b = 0; b < batch; b++)
             for (int l = 0; l < descs[b].num_levels; l++) {
-                const double hl = descs[b].h0 / (double)(1L << l);
+                const double hl = h->lev[b][l].h;
                 fr[(size_t)b * MG_MAX_LEVELS + l] = 4.0 * M_PI * descs[b].G * hl * hl;
             }
         e = cudaMemcpy(h->frho, fr.data(), fr.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -1734,7 +1754,7 @@ mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out, double
     if (!h->solved)
         return fail(h, MG_ESTATE, "mg_interp_guess before mg_solve");
     LevelData &ld = h->lev[b][level];
-    const LevelData &pd = h->lev[b][level - 1];
+    const LevelData &pd = h->lev[b][ld.parent];
     const int dim = h->dim;
     const size_t nr = (size_t)cells(ld.n, dim), nb = (size_t)cells(ld.n + 4, dim);
     double *blk = h->stage, *dense = h->stage + nb, *dres = h->stage + nb + nr;

@@ -163,17 +163,33 @@ class Hierarchy:
     G: float
     sources: list = field(default_factory=list)
     name: str = ""
+    parents: list = None   # parent patch of each patch (None: a chain, parent of l is l-1)
 
     @property
     def num_levels(self):
+        """Number of patches (in a chain: refinement levels)."""
         return len(self.n)
 
+    def parent(self, l):
+        return l - 1 if self.parents is None else self.parents[l]
+
+    def children(self, l):
+        return [c for c in range(1, self.num_levels) if self.parent(c) == l]
+
+    def depth(self, l):
+        k = 0
+        while l > 0:
+            l = self.parent(l)
+            k += 1
+        return k
+
     def h(self, l):
-        return self.h0 / 2.0 ** l
+        return self.h0 / 2.0 ** self.depth(l)
 
     def offset(self, l):
-        """Lower corner of level l in parent cells (integer, Sec. 2.1 nesting)."""
-        off = [(self.lo[l][a] - self.lo[l - 1][a]) / self.h(l - 1) for a in range(self.dim)]
+        """Lower corner of patch l in parent cells (integer, Sec. 2.1 nesting)."""
+        p = self.parent(l)
+        off = [(self.lo[l][a] - self.lo[p][a]) / self.h(p) for a in range(self.dim)]
         ioff = [int(round(o)) for o in off]
         assert all(abs(o - i) < 1e-9 for o, i in zip(off, ioff)), "patch not aligned to parent faces"
         return ioff
@@ -183,8 +199,9 @@ class Hierarchy:
 
     def validate(self):
         for l in range(1, self.num_levels):
+            assert 0 <= self.parent(l) < l, l
             o = self.offset(l)
-            nl, np_ = self.n[l], self.n[l - 1]
+            nl, np_ = self.n[l], self.n[self.parent(l)]
             assert nl % 2 == 0
             for a in range(self.dim):
                 assert 1 <= o[a] <= np_ - nl // 2 - 1, (l, a, o[a])
@@ -263,6 +280,28 @@ def config_3d_spheres(n=256, levels=4, count=8, seed=BASE_SEED):
     w = 2.0 ** (-(levels - 1))
     sph = random_spheres(rng, count, -w, w)
     return nested_centred(3, levels, n, 1.0, 1.0, sph, f"spheres3d_{levels}x{n}_s{seed}")
+
+
+def config_3d_patches(n=64, m=32, seed=BASE_SEED):
+    """Patch-based refinement: base n^3 on [-1,1]^3, two disjoint m^3 patches
+    on level 1 (one per compact sphere), and an m^3 patch inside the first.
+    Patches are listed parents first."""
+    h0 = 2.0 / n
+    w = m // 2                               # patch width in parent cells
+    o1 = (n // 8, n // 2 - w // 2, n // 2 - w // 2)
+    o2 = (n - n // 8 - w, n // 2 - w // 2, n // 2 - w // 2)
+    lo1 = tuple(-1.0 + o * h0 for o in o1)
+    lo2 = tuple(-1.0 + o * h0 for o in o2)
+    h1 = h0 / 2
+    o3 = (m // 4,) * 3
+    lo3 = tuple(l + o * h1 for l, o in zip(lo1, o3))
+    c1 = tuple(l + (w * h0) / 2 for l in lo1)
+    c2 = tuple(l + (w * h0) / 2 for l in lo2)
+    sph = [PolySphere(c1, 0.2, 1.0, 3), PolySphere(c2, 0.18, 1.5, 3)]
+    H = Hierarchy(3, [n, m, m, m], [(-1.0,) * 3, lo1, lo2, lo3], h0, 1.0, sph, f"patches3d_{n}_{m}",
+                  parents=[-1, 0, 0, 1])
+    H.validate()
+    return H
 
 
 EDGES = (32, 48, 64, 96, 128)

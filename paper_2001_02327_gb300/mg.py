@@ -26,7 +26,8 @@ MG_STOP_RESIDUAL, MG_STOP_FORCE = 0, 1
 
 class mg_hierarchy_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("num_levels", C.c_int), ("n", C.c_int * MG_MAX_LEVELS),
-                ("lo", (C.c_double * 3) * MG_MAX_LEVELS), ("h0", C.c_double), ("G", C.c_double)]
+                ("lo", (C.c_double * 3) * MG_MAX_LEVELS), ("h0", C.c_double), ("G", C.c_double),
+                ("tree", C.c_int), ("parent", C.c_int * MG_MAX_LEVELS)]
 
 
 class mg_options(C.Structure):
@@ -216,6 +217,10 @@ def desc_from(H):
             d.lo[l][a] = H.lo[l][a]
     d.h0 = H.h0
     d.G = H.G
+    if getattr(H, "parents", None) is not None:
+        d.tree = 1
+        for l in range(1, H.num_levels):
+            d.parent[l] = H.parent(l)
     return d
 
 

@@ -70,7 +70,7 @@ def _desc(mg, **kw):
 
 
 @pytest.mark.parametrize("bad", ["dim", "levels", "n_odd", "offset", "h0", "opt", "interface", "stop",
-                                 "stop_frozen"])
+                                 "stop_frozen", "parent", "tree_flag"])
 def test_invalid_arguments_rejected_on_host(mg, bad):
     d = _desc(mg)
     opt = None
@@ -90,6 +90,11 @@ def test_invalid_arguments_rejected_on_host(mg, bad):
         opt = mg.options(interface=2)
     elif bad == "stop":
         opt = mg.options(stop=2)
+    elif bad == "parent":
+        d.tree = 1
+        d.parent[1] = 1                   # a patch cannot be its own parent
+    elif bad == "tree_flag":
+        d.tree = 2
     elif bad == "stop_frozen":
         # the force-change test is defined on the buffer-ring method only
         opt = mg.options(stop=mg.MG_STOP_FORCE, interface=mg.MG_IFACE_FROZEN)

@@ -177,6 +177,36 @@ def test_frozen_interface_converged(mg, oracle, precision):
 
 
 # --------------------------------------------------------------------------
+# patch-based refinement: several patches per level (a tree of patches)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_patch_tree(mg, oracle, prec):
+    H = I.config_3d_patches(64, 32)
+    inp = I.level_inputs(H)
+    p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
+    _, g = gpu_solve(mg, H, inp, max_cycles=3, rel_tol=0.0, precision=mg.MG_FP64)
+    check_parity(H, g, oracle.solve_hierarchy(H, inp, 2, 1, 3, 0.0))
+    _, gc = gpu_solve(mg, H, inp, nu_pre=2, nu_post=2, max_cycles=60, rel_tol=1e-10, precision=p,
+                      allow_noconv=False)
+    ref = oracle.solve_hierarchy(H, inp, 2, 2, 60, 1e-10)
+    for l in range(H.num_levels):
+        assert gc[l]["rel_res"] < 1e-10
+        if p == mg.MG_FP64:
+            assert gc[l]["cycles"] == ref[l]["cycles"], l
+    check_parity(H, gc, ref, tol=TOL if p == mg.MG_FP64 else 1e-8)
+
+
+def test_patch_tree_equals_chains_on_gpu(mg):
+    H = I.config_3d_patches(64, 32)
+    _, g = gpu_solve(mg, H, I.level_inputs(H), max_cycles=4, rel_tol=0.0)
+    for path in ([0, 1, 3], [0, 2]):
+        Hc = I.Hierarchy(3, [H.n[l] for l in path], [H.lo[l] for l in path], H.h0, H.G, H.sources)
+        _, gc = gpu_solve(mg, Hc, I.level_inputs(Hc), max_cycles=4, rel_tol=0.0)
+        for k, l in enumerate(path):
+            assert np.array_equal(gc[k]["phi"], g[l]["phi"]) and np.array_equal(gc[k]["F"], g[l]["F"]), (path, l)
+
+
+# --------------------------------------------------------------------------
 # the force-change stopping test of Sec. 3
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("make,stencil", [(lambda: I.paper_3d(16), 0), (lambda: I.paper_2d(64), 0),
