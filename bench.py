@@ -208,6 +208,24 @@ def profile_pass(runner, torch, steps):
     return prof
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest x over all ranks of the process group (the job takes as
+    long as its slowest rank); x itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ms, world_size):
+    """Whole-job units per second: every rank processes units_per_rank
+    (replicas, weak scaling) in ms milliseconds of the slowest rank."""
+    return world_size * units_per_rank / (ms * 1e-3)
+
+
 def measured_peaks(key="hbm_gbs"):
     """A measured peak (HBM copy GB/s or dense bf16 TFLOP/s) and its source."""
     fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}[key]
@@ -279,17 +297,13 @@ def run_ours(args):
                 sampler.start()
             times = time_device(r, torch, args.steps, args.warmup, flush)
             clocks = sampler.stop() if sampler else None
-            total = sum(times)
-            if ws > 1:
-                t = torch.tensor([total], dtype=torch.float64, device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                total = float(t.item())
+            total = max_over_ranks(sum(times), device="cuda")
             ms = total / args.steps
-            e2e_ms = time_e2e(r, torch, max(3, args.steps // 2))
+            e2e_ms = max_over_ranks(time_e2e(r, torch, max(3, args.steps // 2)), device="cuda")
             h2d, d2h = r.io_bytes()
             prof = profile_pass(r, torch, max(3, min(args.steps, 10)))
             nprof = max(3, min(args.steps, 10))
-            forms[name] = {"value": ws * H.zones() / (ms * 1e-3), "ms_per_step": ms,
+            forms[name] = {"value": job_throughput(H.zones(), ms, ws), "ms_per_step": ms,
                            "ms_min": min(times), "cycles": cyc, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h,
                            "prof": {k: (v[0] / nprof, v[1] / nprof, v[2] / nprof) for k, v in prof.items()},
                            "clocks": clocks}
@@ -336,7 +350,7 @@ def run_ours(args):
                       "kernels": {kk: {"launches": round(vv[0], 1), "ms": round(vv[1], 4)} for kk, vv in v["prof"].items()}}
                   for k, v in forms.items()},
         "mixed_error_vs_fp64_over_discretisation": worst,
-        "e2e": {"value": ws * H.zones() / (fb["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": fb["h2d"],
+        "e2e": {"value": job_throughput(H.zones(), fb["e2e_ms"], ws), "unit": UNIT, "h2d_bytes_per_step": fb["h2d"],
                 "d2h_bytes_per_step": fb["d2h"]},
         "gpu_launches": launches,
         "roofline": roofline,
