@@ -18,9 +18,13 @@
  * Conventions common to every call
  *   - Arrays are C order with x fastest: 3D index (k*n + j)*n + i, 2D j*n + i.
  *   - Array pointers may be host or device memory; the library inspects each
- *     pointer (cudaPointerGetAttributes) and copies on the hierarchy's stream.
- *     It never keeps a caller pointer after a call returns.  Host pointers make
- *     the call synchronous with respect to that stream.
+ *     pointer (cudaPointerGetAttributes).  Page-locked host memory that CUDA
+ *     maps into the device address space (cudaMallocHost, cudaHostAlloc,
+ *     cudaHostRegister; torch pin_memory) is read and written by the kernels
+ *     in place over the host link; other host memory is copied through a
+ *     library staging area on the hierarchy's stream.  The library never keeps
+ *     a caller pointer after a call returns.  Host pointers make the call
+ *     synchronous with respect to that stream.
  *   - The library owns all its device memory (allocated in
  *     mg_create_hierarchy, freed in mg_destroy) and runs on one GPU, the
  *     current device at creation.

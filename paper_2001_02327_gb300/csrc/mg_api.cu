@@ -389,6 +389,20 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory that CUDA maps into the device address space: the
+// device address through which kernels read or write it directly over the
+// host link (no staging copy); nullptr for any other memory.
+template <typename P>
+P *mapped_host_view(P *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<P *>(a.devicePointer) : nullptr;
+}
+
 mg_status check_options(const mg_options &o)
 {
     if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 || !(o.rel_tol >= 0.0) ||
@@ -1576,27 +1590,32 @@ mg_status mg_set_density(mg_hierarchy *h, int b, int level, const double *rho, c
     const size_t nr = (size_t)cells(ld.n, dim), nb = (size_t)cells(ld.n + 2, dim), np = (size_t)cells(ld.n + 4, dim);
     const double *d_rho = rho, *d_bcr = bc_rho, *d_bcp = bc_phi;
     double *stage = h->stage;
-    if (!is_device_ptr(rho)) {
-        CK(h, cudaMemcpyAsync(stage, rho, nr * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        d_rho = stage;
-    }
+    bool host_in = false;
+    // host arrays: read in place by the kernel when mapped (page-locked),
+    // else copied to the staging area first
+    auto take = [&](const double *src, const double *&dst, double *st, size_t count) -> cudaError_t {
+        if (is_device_ptr(src))
+            return cudaSuccess;
+        host_in = true;
+        if (const double *m = mapped_host_view(src)) {
+            dst = m;
+            return cudaSuccess;
+        }
+        dst = st;
+        return cudaMemcpyAsync(st, src, count * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    };
+    CK(h, take(rho, d_rho, stage, nr));
     if (level == 0) {
-        if (!is_device_ptr(bc_rho)) {
-            CK(h, cudaMemcpyAsync(stage + np, bc_rho, nb * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            d_bcr = stage + np;
-        }
-        if (!is_device_ptr(bc_phi)) {
-            CK(h, cudaMemcpyAsync(stage + 2 * np, bc_phi, np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            d_bcp = stage + 2 * np;
-        }
+        CK(h, take(bc_rho, d_bcr, stage + np, nb));
+        CK(h, take(bc_phi, d_bcp, stage + 2 * np, np));
     }
     const double fourpiG = 4.0 * M_PI * h->desc[b].G;
     CK(h, timed(h, KK_SETDENS, 24.0 * (double)nr, [&] {
            return mg_launch_set_density(dim, ld.n, d_rho, d_bcr, d_bcp, ld.rho, ld.fblk, ld.blk, fourpiG,
                                         h->stream);
        }));
-    if (d_rho == stage || d_bcr == stage + np || d_bcp == stage + 2 * np)
-        CK(h, cudaStreamSynchronize(h->stream));   // the staging area is reused by the next call
+    if (host_in)   // the caller may reuse its host arrays (and the staging area is reused) on return
+        CK(h, cudaStreamSynchronize(h->stream));
     ld.density_set = true;
     ld.guess_set = false;
     h->solved = false;
@@ -1667,10 +1686,14 @@ mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *
     const LevelData &ld = h->lev[b][level];
     const int dim = h->dim;
     const size_t nr = (size_t)cells(ld.n, dim);
-    const bool phi_dev = phi_out && is_device_ptr(phi_out);
-    const bool F_dev = F_out && is_device_ptr(F_out);
-    double *dF = F_out ? (F_dev ? F_out : h->stage) : nullptr;
-    double *dP = phi_out ? (phi_dev ? phi_out : h->stage + (size_t)dim * nr) : nullptr;
+    // device arrays and mapped page-locked host arrays are written by the
+    // kernel itself; other host arrays get a copy from the staging area
+    double *mF = F_out && !is_device_ptr(F_out) ? mapped_host_view(F_out) : nullptr;
+    double *mP = phi_out && !is_device_ptr(phi_out) ? mapped_host_view(phi_out) : nullptr;
+    const bool phi_dev = phi_out && (mP || is_device_ptr(phi_out));
+    const bool F_dev = F_out && (mF || is_device_ptr(F_out));
+    double *dF = F_out ? (F_dev ? (mF ? mF : F_out) : h->stage) : nullptr;
+    double *dP = phi_out ? (phi_dev ? (mP ? mP : phi_out) : h->stage + (size_t)dim * nr) : nullptr;
     if (!dF) {
         // potential only: the kernel still needs somewhere to write forces
         dF = h->stage;
@@ -1689,6 +1712,8 @@ mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *
         CK(h, cudaMemcpyAsync(phi_out, dP, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         sync = true;
     }
+    if (mF || mP)
+        sync = true;   // host memory written by the kernel: complete before returning
     if (sync)
         CK(h, cudaStreamSynchronize(h->stream));
     return MG_OK;
