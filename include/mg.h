@@ -52,7 +52,7 @@ typedef enum {
     MG_ECUDA = 3,       /* a CUDA call failed; handle poisoned */
     MG_ESTATE = 4,      /* call out of order, or handle poisoned */
     MG_ENOCONV = 5,     /* max_cycles reached above rel_tol (results are valid, unconverged) */
-    MG_EDIVERGED = 6,   /* residual became NaN/Inf */
+    MG_EDIVERGED = 6,   /* the right-hand side or the residual is NaN/Inf */
     MG_ETIMEOUT = 7     /* a bounded device-side wait gave up */
 } mg_status;
 

@@ -708,6 +708,8 @@ mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
     MgSolveCtl c{};
     c.bnorm = std::sqrt(hs[0]);
     c.rel = c.bnorm > 0.0 ? std::sqrt(hs[1]) / c.bnorm : 0.0;
+    if (!std::isfinite(c.bnorm))
+        c.status = 1;
     while (c.bnorm > 0.0 && c.status == 0 && c.cycles < o.max_cycles && !(c.rel < o.rel_tol)) {
         CK(h, level_iteration(h, b, l, s, 0));
         CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -1548,7 +1548,7 @@ __global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int 
     c.rel = c.bnorm > 0.0 ? sqrt(scal[1]) / c.bnorm : 0.0;
     c.cycles = 0;
     c.outer = 0;
-    c.status = 0;
+    c.status = isfinite(c.bnorm) ? 0 : 6;   // non-finite input: diverged, not "nothing to do"
     c.go = keep_going(c, tol, max_cycles);
     *ctl = c;
     cudaGraphSetConditional(hc, c.go);
@@ -1817,7 +1817,7 @@ __global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts
             c.rel = c.bnorm > 0.0 ? sqrt(P.scal[1]) / c.bnorm : 0.0;
             c.cycles = 0;
             c.outer = 0;
-            c.status = 0;
+            c.status = isfinite(c.bnorm) ? 0 : 6;
         } else {
             c = *P.ctl;
             if (!active[p])

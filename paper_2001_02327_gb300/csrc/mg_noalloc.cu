@@ -237,8 +237,8 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
         return reject(MG_ECUDA, cudaGetErrorString(e));
     const double bn = std::sqrt(hs[0]);
     double rel = bn > 0.0 ? std::sqrt(hs[1]) / bn : 0.0;
-    int cycles = 0, status = MG_OK;
-    while (bn > 0.0 && cycles < o.max_cycles && !(rel < o.rel_tol)) {
+    int cycles = 0, status = std::isfinite(bn) ? MG_OK : MG_EDIVERGED;
+    while (status == MG_OK && bn > 0.0 && cycles < o.max_cycles && !(rel < o.rel_tol)) {
         if ((e = vcycle(dim, nmg, g, phis, fs, o.nu_pre, o.nu_post, s)) ||
             (e = mg_launch_resid_norm2(dim, phi, fs[0], g[0], false, partials, scal + 1, s)) ||
             (e = cudaMemcpyAsync(hs + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) ||

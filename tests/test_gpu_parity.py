@@ -365,6 +365,44 @@ def test_state_errors(mg):
         mg.mg_destroy(h)
 
 
+@pytest.mark.parametrize("graph", ["1", "0"])
+def test_too_few_cycles_reports_enoconv(mg, graph, monkeypatch):
+    monkeypatch.setenv("MG_SOLVE_GRAPH", graph)
+    H = I.config_3d_offset_sphere(32, 3)
+    status, g = gpu_solve(mg, H, I.level_inputs(H), max_cycles=2, rel_tol=1e-10)
+    assert status == mg.MG_ENOCONV
+    for l in range(H.num_levels):
+        assert g[l]["cycles"] == 2 and g[l]["status"] == mg.MG_ENOCONV and g[l]["rel_res"] > 1e-10
+
+
+@pytest.mark.parametrize("graph", ["1", "0"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_non_finite_density_reports_ediverged(mg, graph, prec, monkeypatch):
+    """A NaN in the density is reported as MG_EDIVERGED (not as a converged
+    level), and the handle solves the next, finite input normally."""
+    import torch
+    monkeypatch.setenv("MG_SOLVE_GRAPH", graph)
+    H = I.config_3d_offset_sphere(16, 2)
+    inp = I.level_inputs(H)
+    p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    bad = inp[0]["rho"].copy()
+    bad[3, 4, 5] = np.nan
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(precision=p))
+    try:
+        mg.mg_set_density(h, 0, 0, dev(bad), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+        mg.mg_set_density(h, 0, 1, dev(inp[1]["rho"]))
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_solve(h, 1)
+        assert e.value.status == mg.MG_EDIVERGED
+        mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+        mg.mg_set_density(h, 0, 1, dev(inp[1]["rho"]))
+        status, st = mg.mg_solve(h, 1)
+        assert status == mg.MG_OK and all(st[0][l]["rel_res"] < 1e-10 for l in range(2))
+    finally:
+        mg.mg_destroy(h)
+
+
 def test_second_order_on_gpu(mg):
     """Second order in L1, L2 and L-infinity for potential and force, from
     the GPU results (composite-grid norms as in Tables 1-2)."""
