@@ -10,6 +10,7 @@
 // selects rather than multiplies, separable interpolation.  Index arithmetic
 // is 32-bit.
 #include <algorithm>
+#include <cstdlib>
 
 #include <math_constants.h>
 
@@ -36,6 +37,16 @@ template <int DIM>
 __device__ __forceinline__ int lin(int i, int j, int k, int E)
 {
     return DIM == 3 ? (k * E + j) * E + i : j * E + i;
+}
+
+// Programmatic dependent launch: every kernel first waits until the kernel
+// before it in the stream has completed and its writes are visible, then
+// lets the next kernel start launching, so that launch latency overlaps the
+// running kernel.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // floor(x / d) for 0 <= x < 2^31, d >= 1 and a quotient below 2^21 (every
@@ -374,6 +385,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
                                                             int colour)
 {
+    pdl_begin();
     op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
 }
 
@@ -430,6 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict
                                                              MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
                                                              MgGeom gc)
 {
+    pdl_begin();
     __shared__ T r[kThreads];
     resid_restrict_tile<T, DIM>(phi_f, f_f, gf, phi_c, f_c, gc, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, true,
                                 r);
@@ -439,6 +452,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_prolong(const T *__restrict__ phi_c, MgGeom gc, T *__restrict__ phi_f,
                                                       MgGeom gf)
 {
+    pdl_begin();
     op_prolong<T, DIM>(phi_c, gc, phi_f, gf, gtid(), gstride());
 }
 
@@ -549,6 +563,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g, const T *__restrict__ f_g,
                                                            MgBottom bt, int nu_pre, int nu_post)
 {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     bottom_body<T, DIM>(phi_g, f_g, bt, nu_pre, nu_post, smem_raw);
 }
@@ -598,6 +613,7 @@ __host__ __device__ __forceinline__ int cluster_first_plane(int r, int E, int C)
 template <typename T>
 __global__ void __launch_bounds__(MG_CLUSTER_THREADS, 1) k_cluster_vcycle(const __grid_constant__ MgClusterPlan P)
 {
+    pdl_begin();
     constexpr int DIM = 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T *tabP[MG_CLUSTER_PLANES];
@@ -1055,6 +1071,7 @@ __global__ void __launch_bounds__(512) k_tb_pre(const T *__restrict__ phi_in, T 
                                                 const T *__restrict__ f, MgGeom g, T *__restrict__ phi_c,
                                                 T *__restrict__ f_c, MgGeom gc, int tile, int nu)
 {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int blk[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
     tb_pre_body<T, DIM>(phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu, blk, smem_raw);
@@ -1065,6 +1082,7 @@ __global__ void __launch_bounds__(512) k_tb_post(const T *__restrict__ phi_in, T
                                                  const T *__restrict__ f, MgGeom g, const T *__restrict__ phi_c,
                                                  MgGeom gc, int tile, int nu)
 {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int blk[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
     tb_post_body<T, DIM>(phi_in, phi_out, f, g, phi_c, gc, tile, nu, blk, smem_raw);
@@ -1135,6 +1153,7 @@ __global__ void __launch_bounds__(kThreads) k_norms2(const double *__restrict__ 
                                                      MgGeom g, int which, double *__restrict__ partials,
                                                      unsigned *__restrict__ counter, double *__restrict__ out2)
 {
+    pdl_begin();
     __shared__ double sm[kThreads / 32];
     __shared__ bool last;
     const int N = g.N;
@@ -1180,6 +1199,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_resid_norm2(const double *__restrict__ phi, const double *__restrict__ f,
                                                           MgGeom g, int zero_inside, double *__restrict__ partials)
 {
+    pdl_begin();
     __shared__ double sm[kThreads / 32];
     const int N = g.N;
     const int total = N * N * (DIM == 3 ? N : 1);
@@ -1194,6 +1214,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_norm2(const double *__restri
 __global__ void __launch_bounds__(kThreads) k_sum_partials(const double *__restrict__ partials, int n,
                                                            double *__restrict__ out)
 {
+    pdl_begin();
     __shared__ double sm[kThreads / 32];
     double acc = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x)
@@ -1209,6 +1230,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_defect(const double *__restrict__ phi, const double *__restrict__ f,
                                                      MgGeom g, float *__restrict__ r32, float *__restrict__ e32)
 {
+    pdl_begin();
     const int N = g.N;
     const int total = N * N * (DIM == 3 ? N : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1233,6 +1255,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_accumulate(double *__restrict__ phi, const float *__restrict__ e32,
                                                          MgGeom g)
 {
+    pdl_begin();
     const int N = g.N;
     const int total = N * N * (DIM == 3 ? N : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1259,6 +1282,7 @@ __global__ void __launch_bounds__(kThreads) k_set_density(int n, const double *_
                                                           double *__restrict__ f_blk, double *__restrict__ phi_blk,
                                                           double fourpiG)
 {
+    pdl_begin();
     const int E = n + 4;
     const int total = E * E * (DIM == 3 ? E : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1327,6 +1351,7 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
                                                         double *__restrict__ f_c, double fourpiG, int guess,
                                                         const double *__restrict__ guess_src, int frozen)
 {
+    pdl_begin();
     const int E = nc + 4, Ep = np + 4;
     const int total = E * E * (DIM == 3 ? E : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1376,6 +1401,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_copy_box(int e, const double *__restrict__ src, int Es, int os,
                                                        double *__restrict__ dst, int Ed, int od)
 {
+    pdl_begin();
     const int total = e * e * (DIM == 3 ? e : 1);
     for (int t = gtid(); t < total; t += gstride()) {
         const int r = div_small(t, e);
@@ -1391,6 +1417,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_copy_guess(int n, const double *__restrict__ src,
                                                          double *__restrict__ phi_blk)
 {
+    pdl_begin();
     const int M = n + 2;
     const int total = M * M * (DIM == 3 ? M : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1408,6 +1435,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_forces(int n, double h, const double *__restrict__ phi,
                                                      double *__restrict__ F, double *__restrict__ phi_out, int stencil)
 {
+    pdl_begin();
     const int E = n + 4;
     const int total = n * n * (DIM == 3 ? n : 1);
     const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * h) : 1.0 / (2.0 * h);
@@ -1438,6 +1466,7 @@ __global__ void __launch_bounds__(kThreads) k_force_change(int n, double h, cons
                                                            const double *__restrict__ prev, int stencil,
                                                            unsigned long long *__restrict__ cmax)
 {
+    pdl_begin();
     const int E = n + 4;
     const int total = n * n * (DIM == 3 ? n : 1);
     const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * h) : 1.0 / (2.0 * h);
@@ -1471,6 +1500,7 @@ __global__ void __launch_bounds__(kThreads) k_force_change(int n, double h, cons
 __global__ void k_save_prev(long total, const double *__restrict__ phi, double *__restrict__ prev,
                             unsigned long long *__restrict__ cmax)
 {
+    pdl_begin();
     if (blockIdx.x == 0 && threadIdx.x == 0)
         *cmax = 0ull;
     for (long t = gtid(); t < total; t += gstride())
@@ -1481,12 +1511,14 @@ __global__ void k_save_prev(long total, const double *__restrict__ phi, double *
 // is the change of the acceleration
 __global__ void k_force_finish(double *scal, const unsigned long long *cmax)
 {
+    pdl_begin();
     scal[1] = __longlong_as_double((long long)*cmax) * scal[0];
 }
 
 // before the first iteration under the force test: an infinite change
 __global__ void k_force_start(double *scal)
 {
+    pdl_begin();
     if (scal[0] > 0.0)
         scal[1] = CUDART_INF;
 }
@@ -1495,6 +1527,7 @@ __global__ void k_force_start(double *scal)
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_extract(int n, const double *__restrict__ blk, double *__restrict__ out)
 {
+    pdl_begin();
     const int E = n + 4;
     const int total = n * n * (DIM == 3 ? n : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1513,6 +1546,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_h2(int n, const double *__re
                                                        const double *__restrict__ rho, double frho,
                                                        double *__restrict__ out)
 {
+    pdl_begin();
     const int E = n + 4;
     const int total = n * n * (DIM == 3 ? n : 1);
     for (int t = gtid(); t < total; t += gstride()) {
@@ -1531,6 +1565,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_h2(int n, const double *__re
 
 __global__ void k_zero(uint4 *p, size_t n16)
 {
+    pdl_begin();
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n16; t += (size_t)gridDim.x * blockDim.x)
         p[t] = make_uint4(0, 0, 0, 0);
 }
@@ -1543,6 +1578,7 @@ __device__ __forceinline__ int keep_going(const MgSolveCtl &c, double tol, int m
 __global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
                            cudaGraphConditionalHandle hc)
 {
+    pdl_begin();
     MgSolveCtl c;
     c.bnorm = sqrt(scal[0]);
     c.rel = c.bnorm > 0.0 ? sqrt(scal[1]) / c.bnorm : 0.0;
@@ -1557,6 +1593,7 @@ __global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int 
 __global__ void k_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
                            cudaGraphConditionalHandle hc)
 {
+    pdl_begin();
     MgSolveCtl c = *ctl;
     c.cycles += inc;
     c.outer += 1;
@@ -1576,6 +1613,7 @@ template <int DIM>
 __global__ void __launch_bounds__(512) kb_tb_pre(const MgBPart *__restrict__ parts, const MgBTask *__restrict__ tasks,
                                                  const int *__restrict__ active, int L, int nu)
 {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MgBTask tk = tasks[blockIdx.x];
     if (!active[tk.part])
@@ -1590,6 +1628,7 @@ template <int DIM>
 __global__ void __launch_bounds__(512) kb_tb_post(const MgBPart *__restrict__ parts, const MgBTask *__restrict__ tasks,
                                                   const int *__restrict__ active, int L, int nu)
 {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MgBTask tk = tasks[blockIdx.x];
     if (!active[tk.part])
@@ -1604,6 +1643,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBottomThreads) kb_bottom(const MgBPart *__restrict__ parts,
                                                             const int *__restrict__ active, int nu_pre, int nu_post)
 {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!active[blockIdx.x])
         return;
@@ -1617,6 +1657,7 @@ __global__ void __launch_bounds__(kThreads) kb_smooth(const MgBPart *__restrict_
                                                       const MgBCell *__restrict__ cells, const int *__restrict__ active,
                                                       int L, int colour)
 {
+    pdl_begin();
     const MgBCell c = cells[blockIdx.x];
     if (!active[c.part])
         return;
@@ -1630,6 +1671,7 @@ __global__ void __launch_bounds__(kThreads) kb_restrict(const MgBPart *__restric
                                                         const MgBCell *__restrict__ cells,
                                                         const int *__restrict__ active, int L)
 {
+    pdl_begin();
     const MgBCell c = cells[blockIdx.x];
     if (!active[c.part])
         return;
@@ -1643,6 +1685,7 @@ __global__ void __launch_bounds__(kThreads) kb_prolong(const MgBPart *__restrict
                                                        const MgBCell *__restrict__ cells,
                                                        const int *__restrict__ active, int L)
 {
+    pdl_begin();
     const MgBCell c = cells[blockIdx.x];
     if (!active[c.part])
         return;
@@ -1671,6 +1714,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) kb_defect(const MgBPart *__restrict__ parts,
                                                       const MgBCell *__restrict__ cells, const int *__restrict__ active)
 {
+    pdl_begin();
     const MgBCell c = cells[blockIdx.x];
     if (!active[c.part])
         return;
@@ -1691,6 +1735,7 @@ __global__ void __launch_bounds__(kThreads) kb_accumulate(const MgBPart *__restr
                                                           const MgBCell *__restrict__ cells,
                                                           const int *__restrict__ active)
 {
+    pdl_begin();
     const MgBCell c = cells[blockIdx.x];
     if (!active[c.part])
         return;
@@ -1710,6 +1755,7 @@ __global__ void __launch_bounds__(kThreads) kb_norms2(const MgBPart *__restrict_
                                                       const MgBCell *__restrict__ cells, const int *__restrict__ active,
                                                       int which)
 {
+    pdl_begin();
     __shared__ double sm[kThreads / 32];
     __shared__ bool last;
     const MgBCell c = cells[blockIdx.x];
@@ -1757,6 +1803,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) kb_interface(const MgBPart *__restrict__ parts,
                                                          const MgBCell *__restrict__ cells)
 {
+    pdl_begin();
     const MgBCell c = cells[blockIdx.x];
     const MgBPart &P = parts[c.part];
     if (P.gmode < 0)
@@ -1808,6 +1855,7 @@ __global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts
                                                int init, int inc, double tol, int max_cycles,
                                                cudaGraphConditionalHandle hc)
 {
+    pdl_begin();
     int any = 0;
     for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
         const MgBPart &P = parts[p];
@@ -1843,20 +1891,48 @@ __global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Every kernel is launched with programmatic dependent launch (the kernels
+// begin with pdl_begin) unless MG_PDL=0.  Errors are left for
+// cudaGetLastError, as with the triple-chevron launch.
+static bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("MG_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+static void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int c, cudaStream_t s)
 {
     const long work = (long)((g.N + 1) / 2) * g.N * (dim == 3 ? g.N : 1);
     const int grid = grid_for(work);
     if (dim == 3) {
         if (fp32)
-            k_smooth_colour<float, 3><<<grid, kThreads, 0, s>>>((float *)phi, (const float *)f, g, c);
+            launch(k_smooth_colour<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
         else
-            k_smooth_colour<double, 3><<<grid, kThreads, 0, s>>>((double *)phi, (const double *)f, g, c);
+            launch(k_smooth_colour<double, 3>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c);
     } else {
         if (fp32)
-            k_smooth_colour<float, 2><<<grid, kThreads, 0, s>>>((float *)phi, (const float *)f, g, c);
+            launch(k_smooth_colour<float, 2>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
         else
-            k_smooth_colour<double, 2><<<grid, kThreads, 0, s>>>((double *)phi, (const double *)f, g, c);
+            launch(k_smooth_colour<double, 2>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c);
     }
     return cudaGetLastError();
 }
@@ -1890,14 +1966,14 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
     const size_t smem = mg_bottom_smem(dim, fp32, bt);
     if (dim == 3) {
         if (fp32)
-            k_bottom<float, 3><<<1, kBottomThreads, smem, s>>>((float *)phi, (const float *)f, bt, nu_pre, nu_post);
+            launch(k_bottom<float, 3>, 1, kBottomThreads, smem, s, (float *)phi, (const float *)f, bt, nu_pre, nu_post);
         else
-            k_bottom<double, 3><<<1, kBottomThreads, smem, s>>>((double *)phi, (const double *)f, bt, nu_pre, nu_post);
+            launch(k_bottom<double, 3>, 1, kBottomThreads, smem, s, (double *)phi, (const double *)f, bt, nu_pre, nu_post);
     } else {
         if (fp32)
-            k_bottom<float, 2><<<1, kBottomThreads, smem, s>>>((float *)phi, (const float *)f, bt, nu_pre, nu_post);
+            launch(k_bottom<float, 2>, 1, kBottomThreads, smem, s, (float *)phi, (const float *)f, bt, nu_pre, nu_post);
         else
-            k_bottom<double, 2><<<1, kBottomThreads, smem, s>>>((double *)phi, (const double *)f, bt, nu_pre, nu_post);
+            launch(k_bottom<double, 2>, 1, kBottomThreads, smem, s, (double *)phi, (const double *)f, bt, nu_pre, nu_post);
     }
     return cudaGetLastError();
 }
@@ -2013,9 +2089,9 @@ cudaError_t mg_launch_tb_pre(int dim, const float *phi_in, float *phi_out, const
     const int nb = (g.N + tile - 1) / tile;
     const size_t smem = mg_tb_smem(dim, true, tile, 2 * nu + 1);
     if (dim == 3)
-        k_tb_pre<float, 3><<<dim3(nb, nb, nb), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
+        launch(k_tb_pre<float, 3>, dim3(nb, nb, nb), 512, smem, s, phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
     else
-        k_tb_pre<float, 2><<<dim3(nb, nb, 1), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
+        launch(k_tb_pre<float, 2>, dim3(nb, nb, 1), 512, smem, s, phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
     return cudaGetLastError();
 }
 
@@ -2025,9 +2101,9 @@ cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, cons
     const int nb = (g.N + tile - 1) / tile;
     const size_t smem = mg_tb_smem(dim, true, tile, 2 * nu);
     if (dim == 3)
-        k_tb_post<float, 3><<<dim3(nb, nb, nb), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, gc, tile, nu);
+        launch(k_tb_post<float, 3>, dim3(nb, nb, nb), 512, smem, s, phi_in, phi_out, f, g, phi_c, gc, tile, nu);
     else
-        k_tb_post<float, 2><<<dim3(nb, nb, 1), 512, smem, s>>>(phi_in, phi_out, f, g, phi_c, gc, tile, nu);
+        launch(k_tb_post<float, 2>, dim3(nb, nb, 1), 512, smem, s, phi_in, phi_out, f, g, phi_c, gc, tile, nu);
     return cudaGetLastError();
 }
 
@@ -2039,17 +2115,17 @@ cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, cons
     const dim3 grid(nx, ny, nz);
     if (dim == 3) {
         if (fp32)
-            k_resid_restrict<float, 3><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
+            launch(k_resid_restrict<float, 3>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
         else
-            k_resid_restrict<double, 3><<<grid, kThreads, 0, s>>>((const double *)phi_f, (const double *)f_f, gf,
+            launch(k_resid_restrict<double, 3>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
                                                                   (double *)phi_c, (double *)f_c, gc);
     } else {
         if (fp32)
-            k_resid_restrict<float, 2><<<grid, kThreads, 0, s>>>((const float *)phi_f, (const float *)f_f, gf,
+            launch(k_resid_restrict<float, 2>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
         else
-            k_resid_restrict<double, 2><<<grid, kThreads, 0, s>>>((const double *)phi_f, (const double *)f_f, gf,
+            launch(k_resid_restrict<double, 2>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
                                                                   (double *)phi_c, (double *)f_c, gc);
     }
     return cudaGetLastError();
@@ -2061,14 +2137,14 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
     const int grid = grid_for(cube(gf.N, dim));
     if (dim == 3) {
         if (fp32)
-            k_prolong<float, 3><<<grid, kThreads, 0, s>>>((const float *)phi_c, gc, (float *)phi_f, gf);
+            launch(k_prolong<float, 3>, grid, kThreads, 0, s, (const float *)phi_c, gc, (float *)phi_f, gf);
         else
-            k_prolong<double, 3><<<grid, kThreads, 0, s>>>((const double *)phi_c, gc, (double *)phi_f, gf);
+            launch(k_prolong<double, 3>, grid, kThreads, 0, s, (const double *)phi_c, gc, (double *)phi_f, gf);
     } else {
         if (fp32)
-            k_prolong<float, 2><<<grid, kThreads, 0, s>>>((const float *)phi_c, gc, (float *)phi_f, gf);
+            launch(k_prolong<float, 2>, grid, kThreads, 0, s, (const float *)phi_c, gc, (float *)phi_f, gf);
         else
-            k_prolong<double, 2><<<grid, kThreads, 0, s>>>((const double *)phi_c, gc, (double *)phi_f, gf);
+            launch(k_prolong<double, 2>, grid, kThreads, 0, s, (const double *)phi_c, gc, (double *)phi_f, gf);
     }
     return cudaGetLastError();
 }
@@ -2079,9 +2155,9 @@ cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const 
     // about four cells per thread: fewer block reductions on the FP64 pipe
     const int grid = std::max(1, std::min<int>((int)((cube(g.N, dim) + 4 * kThreads - 1) / (4 * kThreads)), MG_NORM_BLOCKS_MAX));
     if (dim == 3)
-        k_norms2<3><<<grid, kThreads, 0, s>>>(phi, f, g, which, partials, counter, out2);
+        launch(k_norms2<3>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2);
     else
-        k_norms2<2><<<grid, kThreads, 0, s>>>(phi, f, g, which, partials, counter, out2);
+        launch(k_norms2<2>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2);
     return cudaGetLastError();
 }
 
@@ -2089,10 +2165,10 @@ cudaError_t mg_launch_resid_norm2(int dim, const double *phi, const double *f, c
                                   double *partials, double *out, cudaStream_t s)
 {
     if (dim == 3)
-        k_resid_norm2<3><<<MG_NORM_BLOCKS, kThreads, 0, s>>>(phi, f, g, zero_inside ? 1 : 0, partials);
+        launch(k_resid_norm2<3>, MG_NORM_BLOCKS, kThreads, 0, s, phi, f, g, zero_inside ? 1 : 0, partials);
     else
-        k_resid_norm2<2><<<MG_NORM_BLOCKS, kThreads, 0, s>>>(phi, f, g, zero_inside ? 1 : 0, partials);
-    k_sum_partials<<<1, kThreads, 0, s>>>(partials, MG_NORM_BLOCKS, out);
+        launch(k_resid_norm2<2>, MG_NORM_BLOCKS, kThreads, 0, s, phi, f, g, zero_inside ? 1 : 0, partials);
+    launch(k_sum_partials, 1, kThreads, 0, s, partials, MG_NORM_BLOCKS, out);
     return cudaGetLastError();
 }
 
@@ -2101,9 +2177,9 @@ cudaError_t mg_launch_defect(int dim, const double *phi, const double *f, const 
 {
     const int grid = grid_for(cube(g.N, dim));
     if (dim == 3)
-        k_defect<3><<<grid, kThreads, 0, s>>>(phi, f, g, r32, e32);
+        launch(k_defect<3>, grid, kThreads, 0, s, phi, f, g, r32, e32);
     else
-        k_defect<2><<<grid, kThreads, 0, s>>>(phi, f, g, r32, e32);
+        launch(k_defect<2>, grid, kThreads, 0, s, phi, f, g, r32, e32);
     return cudaGetLastError();
 }
 
@@ -2111,9 +2187,9 @@ cudaError_t mg_launch_accumulate(int dim, double *phi, const float *e32, const M
 {
     const int grid = grid_for(cube(g.N, dim));
     if (dim == 3)
-        k_accumulate<3><<<grid, kThreads, 0, s>>>(phi, e32, g);
+        launch(k_accumulate<3>, grid, kThreads, 0, s, phi, e32, g);
     else
-        k_accumulate<2><<<grid, kThreads, 0, s>>>(phi, e32, g);
+        launch(k_accumulate<2>, grid, kThreads, 0, s, phi, e32, g);
     return cudaGetLastError();
 }
 
@@ -2122,9 +2198,9 @@ cudaError_t mg_launch_set_density(int dim, int n, const double *rho, const doubl
 {
     const int grid = grid_for(cube(n + 4, dim));
     if (dim == 3)
-        k_set_density<3><<<grid, kThreads, 0, s>>>(n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
+        launch(k_set_density<3>, grid, kThreads, 0, s, n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
     else
-        k_set_density<2><<<grid, kThreads, 0, s>>>(n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
+        launch(k_set_density<2>, grid, kThreads, 0, s, n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
     return cudaGetLastError();
 }
 
@@ -2134,10 +2210,10 @@ cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const doub
 {
     const int grid = grid_for(cube(nc + 4, dim));
     if (dim == 3)
-        k_interface<3><<<grid, kThreads, 0, s>>>(np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
+        launch(k_interface<3>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
                                                  guess_src, frozen);
     else
-        k_interface<2><<<grid, kThreads, 0, s>>>(np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
+        launch(k_interface<2>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
                                                  guess_src, frozen);
     return cudaGetLastError();
 }
@@ -2146,9 +2222,9 @@ cudaError_t mg_launch_copy_guess(int dim, int n, const double *guess_src, double
 {
     const int grid = grid_for(cube(n + 2, dim));
     if (dim == 3)
-        k_copy_guess<3><<<grid, kThreads, 0, s>>>(n, guess_src, phi_blk);
+        launch(k_copy_guess<3>, grid, kThreads, 0, s, n, guess_src, phi_blk);
     else
-        k_copy_guess<2><<<grid, kThreads, 0, s>>>(n, guess_src, phi_blk);
+        launch(k_copy_guess<2>, grid, kThreads, 0, s, n, guess_src, phi_blk);
     return cudaGetLastError();
 }
 
@@ -2157,9 +2233,9 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
 {
     const int grid = grid_for(cube(n, dim));
     if (dim == 3)
-        k_forces<3><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
+        launch(k_forces<3>, grid, kThreads, 0, s, n, h, phi_blk, F, phi_out, stencil);
     else
-        k_forces<2><<<grid, kThreads, 0, s>>>(n, h, phi_blk, F, phi_out, stencil);
+        launch(k_forces<2>, grid, kThreads, 0, s, n, h, phi_blk, F, phi_out, stencil);
     return cudaGetLastError();
 }
 
@@ -2167,17 +2243,17 @@ cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const doub
                                  int stencil, unsigned long long *cmax, double *scal, cudaStream_t s)
 {
     if (phase == 0) {
-        k_force_start<<<1, 1, 0, s>>>(scal);
+        launch(k_force_start, 1, 1, 0, s, scal);
     } else if (phase == 1) {
         const long total = cube(n + 4, dim);
-        k_save_prev<<<grid_for(total), kThreads, 0, s>>>(total, phi_blk, prev, cmax);
+        launch(k_save_prev, grid_for(total), kThreads, 0, s, total, phi_blk, prev, cmax);
     } else {
         const int grid = grid_for(cube(n, dim));
         if (dim == 3)
-            k_force_change<3><<<grid, kThreads, 0, s>>>(n, h, phi_blk, prev, stencil, cmax);
+            launch(k_force_change<3>, grid, kThreads, 0, s, n, h, phi_blk, prev, stencil, cmax);
         else
-            k_force_change<2><<<grid, kThreads, 0, s>>>(n, h, phi_blk, prev, stencil, cmax);
-        k_force_finish<<<1, 1, 0, s>>>(scal, cmax);
+            launch(k_force_change<2>, grid, kThreads, 0, s, n, h, phi_blk, prev, stencil, cmax);
+        launch(k_force_finish, 1, 1, 0, s, scal, cmax);
     }
     return cudaGetLastError();
 }
@@ -2185,14 +2261,14 @@ cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const doub
 cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
                                cudaGraphConditionalHandle hc, cudaStream_t s)
 {
-    k_ctl_init<<<1, 1, 0, s>>>(ctl, scal, tol, max_cycles, hc);
+    launch(k_ctl_init, 1, 1, 0, s, ctl, scal, tol, max_cycles, hc);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
                                cudaGraphConditionalHandle hc, cudaStream_t s)
 {
-    k_ctl_step<<<1, 1, 0, s>>>(ctl, scal, inc, tol, max_cycles, hc);
+    launch(k_ctl_step, 1, 1, 0, s, ctl, scal, inc, tol, max_cycles, hc);
     return cudaGetLastError();
 }
 
@@ -2200,9 +2276,9 @@ cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cu
 {
     const int grid = grid_for(cube(n, dim));
     if (dim == 3)
-        k_extract<3><<<grid, kThreads, 0, s>>>(n, blk, out);
+        launch(k_extract<3>, grid, kThreads, 0, s, n, blk, out);
     else
-        k_extract<2><<<grid, kThreads, 0, s>>>(n, blk, out);
+        launch(k_extract<2>, grid, kThreads, 0, s, n, blk, out);
     return cudaGetLastError();
 }
 
@@ -2211,9 +2287,9 @@ cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os
 {
     const int grid = grid_for(cube(e, dim));
     if (dim == 3)
-        k_copy_box<3><<<grid, kThreads, 0, s>>>(e, src, Es, os, dst, Ed, od);
+        launch(k_copy_box<3>, grid, kThreads, 0, s, e, src, Es, os, dst, Ed, od);
     else
-        k_copy_box<2><<<grid, kThreads, 0, s>>>(e, src, Es, os, dst, Ed, od);
+        launch(k_copy_box<2>, grid, kThreads, 0, s, e, src, Es, os, dst, Ed, od);
     return cudaGetLastError();
 }
 
@@ -2222,9 +2298,9 @@ cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const doub
 {
     const int grid = grid_for(cube(n, dim));
     if (dim == 3)
-        k_resid_h2<3><<<grid, kThreads, 0, s>>>(n, phi_blk, rho_blk, frho, out);
+        launch(k_resid_h2<3>, grid, kThreads, 0, s, n, phi_blk, rho_blk, frho, out);
     else
-        k_resid_h2<2><<<grid, kThreads, 0, s>>>(n, phi_blk, rho_blk, frho, out);
+        launch(k_resid_h2<2>, grid, kThreads, 0, s, n, phi_blk, rho_blk, frho, out);
     return cudaGetLastError();
 }
 
@@ -2233,7 +2309,7 @@ cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s)
     // callers pass 256-byte aligned sub-allocations whose sizes are multiples of 16
     const size_t n16 = bytes / 16;
     if (n16)
-        k_zero<<<grid_for((long)n16), kThreads, 0, s>>>((uint4 *)p, n16);
+        launch(k_zero, grid_for((long)n16), kThreads, 0, s, (uint4 *)p, n16);
     return cudaGetLastError();
 }
 
@@ -2263,9 +2339,9 @@ cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tas
     if (ntasks <= 0)
         return cudaSuccess;
     if (dim == 3)
-        kb_tb_pre<3><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+        launch(kb_tb_pre<3>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     else
-        kb_tb_pre<2><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+        launch(kb_tb_pre<2>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     return cudaGetLastError();
 }
 
@@ -2275,9 +2351,9 @@ cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *ta
     if (ntasks <= 0)
         return cudaSuccess;
     if (dim == 3)
-        kb_tb_post<3><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+        launch(kb_tb_post<3>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     else
-        kb_tb_post<2><<<ntasks, 512, smem, s>>>(parts, tasks, active, depth, nu);
+        launch(kb_tb_post<2>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     return cudaGetLastError();
 }
 
@@ -2287,9 +2363,9 @@ cudaError_t mg_launch_b_smooth(int dim, const MgBPart *parts, const MgBCell *cel
     if (ncells <= 0)
         return cudaSuccess;
     if (dim == 3)
-        kb_smooth<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, L, colour);
+        launch(kb_smooth<3>, ncells, kThreads, 0, s, parts, cells, active, L, colour);
     else
-        kb_smooth<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, L, colour);
+        launch(kb_smooth<2>, ncells, kThreads, 0, s, parts, cells, active, L, colour);
     return cudaGetLastError();
 }
 
@@ -2299,9 +2375,9 @@ cudaError_t mg_launch_b_restrict(int dim, const MgBPart *parts, const MgBCell *c
     if (ncells <= 0)
         return cudaSuccess;
     if (dim == 3)
-        kb_restrict<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+        launch(kb_restrict<3>, ncells, kThreads, 0, s, parts, cells, active, L);
     else
-        kb_restrict<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+        launch(kb_restrict<2>, ncells, kThreads, 0, s, parts, cells, active, L);
     return cudaGetLastError();
 }
 
@@ -2311,9 +2387,9 @@ cudaError_t mg_launch_b_prolong(int dim, const MgBPart *parts, const MgBCell *ce
     if (ncells <= 0)
         return cudaSuccess;
     if (dim == 3)
-        kb_prolong<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+        launch(kb_prolong<3>, ncells, kThreads, 0, s, parts, cells, active, L);
     else
-        kb_prolong<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, L);
+        launch(kb_prolong<2>, ncells, kThreads, 0, s, parts, cells, active, L);
     return cudaGetLastError();
 }
 
@@ -2321,9 +2397,9 @@ cudaError_t mg_launch_b_bottom(int dim, const MgBPart *parts, int nparts, const 
                                size_t smem, cudaStream_t s)
 {
     if (dim == 3)
-        kb_bottom<3><<<nparts, kBottomThreads, smem, s>>>(parts, active, nu_pre, nu_post);
+        launch(kb_bottom<3>, nparts, kBottomThreads, smem, s, parts, active, nu_pre, nu_post);
     else
-        kb_bottom<2><<<nparts, kBottomThreads, smem, s>>>(parts, active, nu_pre, nu_post);
+        launch(kb_bottom<2>, nparts, kBottomThreads, smem, s, parts, active, nu_pre, nu_post);
     return cudaGetLastError();
 }
 
@@ -2331,9 +2407,9 @@ cudaError_t mg_launch_b_defect(int dim, const MgBPart *parts, const MgBCell *cel
                                cudaStream_t s)
 {
     if (dim == 3)
-        kb_defect<3><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+        launch(kb_defect<3>, ncells, kThreads, 0, s, parts, cells, active);
     else
-        kb_defect<2><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+        launch(kb_defect<2>, ncells, kThreads, 0, s, parts, cells, active);
     return cudaGetLastError();
 }
 
@@ -2341,9 +2417,9 @@ cudaError_t mg_launch_b_accumulate(int dim, const MgBPart *parts, const MgBCell 
                                    const int *active, cudaStream_t s)
 {
     if (dim == 3)
-        kb_accumulate<3><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+        launch(kb_accumulate<3>, ncells, kThreads, 0, s, parts, cells, active);
     else
-        kb_accumulate<2><<<ncells, kThreads, 0, s>>>(parts, cells, active);
+        launch(kb_accumulate<2>, ncells, kThreads, 0, s, parts, cells, active);
     return cudaGetLastError();
 }
 
@@ -2351,24 +2427,24 @@ cudaError_t mg_launch_b_norms2(int dim, const MgBPart *parts, const MgBCell *cel
                                int which, cudaStream_t s)
 {
     if (dim == 3)
-        kb_norms2<3><<<ncells, kThreads, 0, s>>>(parts, cells, active, which);
+        launch(kb_norms2<3>, ncells, kThreads, 0, s, parts, cells, active, which);
     else
-        kb_norms2<2><<<ncells, kThreads, 0, s>>>(parts, cells, active, which);
+        launch(kb_norms2<2>, ncells, kThreads, 0, s, parts, cells, active, which);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_b_interface(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, cudaStream_t s)
 {
     if (dim == 3)
-        kb_interface<3><<<ncells, kThreads, 0, s>>>(parts, cells);
+        launch(kb_interface<3>, ncells, kThreads, 0, s, parts, cells);
     else
-        kb_interface<2><<<ncells, kThreads, 0, s>>>(parts, cells);
+        launch(kb_interface<2>, ncells, kThreads, 0, s, parts, cells);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_b_ctl(const MgBPart *parts, int nparts, int *active, int init, int inc, double tol,
                             int max_cycles, cudaGraphConditionalHandle hc, cudaStream_t s)
 {
-    kb_ctl<<<1, 1024, 0, s>>>(parts, nparts, active, init, inc, tol, max_cycles, hc);
+    launch(kb_ctl, 1, 1024, 0, s, parts, nparts, active, init, inc, tol, max_cycles, hc);
     return cudaGetLastError();
 }
