@@ -580,13 +580,20 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     return cudaSuccess;
 }
 
+// True when the residual norm also writes the next defect-correction step's
+// FP32 right-hand side (mixed precision under the residual stopping rule):
+// the residual is then computed once per step instead of twice.
+bool fused_defect(const mg_hierarchy *h) { return h->opt.precision == MG_MIXED && h->opt.stop == MG_STOP_RESIDUAL; }
+
 // ||b||^2 (which & 1) and ||r||^2 (which & 2) of a level into scal[0..1];
 // `branch` selects the reduction scratch of a parallel graph branch.
 cudaError_t norms(mg_hierarchy *h, const LevelData &ld, int which, double *scal, cudaStream_t s, int branch)
 {
-    return timed(h, KK_NORM, 16.0 * cells_d(ld.g[0].N, h->dim), [&] {
+    const bool fd = (which & 2) && fused_defect(h);
+    return timed(h, KK_NORM, (fd ? 24.0 : 16.0) * cells_d(ld.g[0].N, h->dim), [&] {
         return mg_launch_norms2(h->dim, ld.phi[0], ld.f[0], ld.g[0], which,
-                                h->partials + (size_t)branch * 2 * MG_NORM_BLOCKS_MAX, h->counters + branch, scal, s);
+                                h->partials + (size_t)branch * 2 * MG_NORM_BLOCKS_MAX, h->counters + branch, scal, s,
+                                fd ? ld.f32[0] : nullptr, fd ? ld.phi32[0] : nullptr);
     });
 }
 
@@ -647,7 +654,8 @@ cudaError_t level_epilogue(mg_hierarchy *h, int b, int l, cudaStream_t s)
 }
 
 // One iteration of a level's loop (Sec. 2.3 step 14): an FP64 V-cycle, or in
-// mixed precision an FP64 defect, inner_cycles FP32 V-cycles on the
+// mixed precision an FP64 defect (already written by the previous residual
+// norm under the residual stopping rule), inner_cycles FP32 V-cycles on the
 // correction and its FP64 accumulation; then ||r||^2.
 cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int branch)
 {
@@ -664,11 +672,13 @@ cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int b
             return e;
     } else {
         const double nd = cells_d(ld.g[0].N, dim);
-        e = timed(h, KK_DEFECT, 24.0 * nd, [&] {
-            return mg_launch_defect(dim, ld.phi[0], ld.f[0], ld.g[0], ld.f32[0], ld.phi32[0], s);
-        });
-        if (e)
-            return e;
+        if (!fused_defect(h)) {   // else the previous residual norm wrote it
+            e = timed(h, KK_DEFECT, 24.0 * nd, [&] {
+                return mg_launch_defect(dim, ld.phi[0], ld.f[0], ld.g[0], ld.f32[0], ld.phi32[0], s);
+            });
+            if (e)
+                return e;
+        }
         if ((e = vcycle(h, ld, true, s, o.inner_cycles)))
             return e;
         e = timed(h, KK_ACCUM, 20.0 * nd, [&] { return mg_launch_accumulate(dim, ld.phi[0], ld.phi32[0], ld.g[0], s); });

@@ -136,8 +136,12 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
 // (MG_NORM_BLOCKS_MAX doubles) in a fixed order; counter (one unsigned, zero
 // between launches) tracks finished blocks.
 #define MG_NORM_BLOCKS_MAX 1216
+// ||b||^2 / ||r||^2 of a finest level; with r32 set, also the FP32 right-hand
+// side r32 = f - A Phi and a zero correction e32 of the next defect-correction
+// step (what mg_launch_defect writes), from the same residual values.
 cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const MgGeom &g, int which,
-                             double *partials, unsigned *counter, double *out2, cudaStream_t s);
+                             double *partials, unsigned *counter, double *out2, cudaStream_t s,
+                             float *r32 = nullptr, float *e32 = nullptr);
 cudaError_t mg_launch_resid_norm2(int dim, const double *phi, const double *f, const MgGeom &g, bool zero_inside,
                                   double *partials, double *out, cudaStream_t s);
 

@@ -1114,7 +1114,8 @@ __device__ __forceinline__ double block_sum(double v, double *sm)
 // zero potential inside (only the outer-ring neighbours count).
 template <int DIM>
 __device__ __forceinline__ void norm_terms(const double *__restrict__ phi, const double *__restrict__ f,
-                                           const MgGeom &g, int t, int which, double &b2, double &r2)
+                                           const MgGeom &g, int t, int which, double &b2, double &r2,
+                                           float *__restrict__ r32, float *__restrict__ e32)
 {
     const int N = g.N, E = g.E;
     const int r = div_small(t, N);
@@ -1145,13 +1146,18 @@ __device__ __forceinline__ void norm_terms(const double *__restrict__ phi, const
     if (which & 2) {
         const double v = residual_at<double, DIM>(phi, f, g, i, j, k);
         r2 += v * v;
+        if (r32) {   // the next defect-correction step's right-hand side (k_defect's values)
+            r32[p] = (float)v;
+            e32[p] = 0.0f;
+        }
     }
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_norms2(const double *__restrict__ phi, const double *__restrict__ f,
                                                      MgGeom g, int which, double *__restrict__ partials,
-                                                     unsigned *__restrict__ counter, double *__restrict__ out2)
+                                                     unsigned *__restrict__ counter, double *__restrict__ out2,
+                                                     float *__restrict__ r32, float *__restrict__ e32)
 {
     pdl_begin();
     __shared__ double sm[kThreads / 32];
@@ -1160,7 +1166,7 @@ __global__ void __launch_bounds__(kThreads) k_norms2(const double *__restrict__ 
     const int total = N * N * (DIM == 3 ? N : 1);
     double b2 = 0.0, r2 = 0.0;
     for (int t = gtid(); t < total; t += gstride())
-        norm_terms<DIM>(phi, f, g, t, which, b2, r2);
+        norm_terms<DIM>(phi, f, g, t, which, b2, r2, r32, e32);
     // FP64 reductions cost FP64-pipe time: reduce only what was asked for
     if (which & 1)
         b2 = block_sum(b2, sm);
@@ -1205,7 +1211,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_norm2(const double *__restri
     const int total = N * N * (DIM == 3 ? N : 1);
     double b2 = 0.0, r2 = 0.0;
     for (int t = gtid(); t < total; t += gstride())
-        norm_terms<DIM>(phi, f, g, t, zero_inside ? 1 : 2, b2, r2);
+        norm_terms<DIM>(phi, f, g, t, zero_inside ? 1 : 2, b2, r2, nullptr, nullptr);
     const double acc = block_sum(zero_inside ? b2 : r2, sm);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = acc;
@@ -1766,7 +1772,7 @@ __global__ void __launch_bounds__(kThreads) kb_norms2(const MgBPart *__restrict_
     const int total = g.N * g.N * (DIM == 3 ? g.N : 1);
     double b2 = 0.0, r2 = 0.0;
     for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_act * kThreads)
-        norm_terms<DIM>(P.phi, P.f, g, t, which, b2, r2);
+        norm_terms<DIM>(P.phi, P.f, g, t, which, b2, r2, nullptr, nullptr);
     if (which & 1)
         b2 = block_sum(b2, sm);
     if (which & 2)
@@ -2150,14 +2156,14 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
 }
 
 cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const MgGeom &g, int which,
-                             double *partials, unsigned *counter, double *out2, cudaStream_t s)
+                             double *partials, unsigned *counter, double *out2, cudaStream_t s, float *r32, float *e32)
 {
     // about four cells per thread: fewer block reductions on the FP64 pipe
     const int grid = std::max(1, std::min<int>((int)((cube(g.N, dim) + 4 * kThreads - 1) / (4 * kThreads)), MG_NORM_BLOCKS_MAX));
     if (dim == 3)
-        launch(k_norms2<3>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2);
+        launch(k_norms2<3>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2, r32, e32);
     else
-        launch(k_norms2<2>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2);
+        launch(k_norms2<2>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2, r32, e32);
     return cudaGetLastError();
 }
 
