@@ -1,7 +1,7 @@
 """Seeded synthetic inputs for the nested-grid Poisson solver.
 
 This module builds the *inputs* of the method and the analytic references
-its results are judged against; it holds none of the method's own arithmetic
+its results are checked against; it holds none of the method's own arithmetic
 (no smoother, transfer, interface or force stencil).  Both the CUDA path and
 the CPU oracle are fed from here.
 
