@@ -622,6 +622,45 @@ def run_unet_case(args):
         U.mg_unet_destroy(u)
 
 
+def run_learned_case(args):
+    """The learned initial guess end to end: training samples generated by the
+    solver (hierarchies of 64^3 levels with 1-8 random compact spheres), the
+    network trained on them, then V-cycles, wall time and difference from the
+    zero-guess solution with the zero, interpolated and learned guesses on
+    held-out hierarchies of 3 levels of 64^3 and of 128^3.  Prints one line,
+    not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import learned as LR
+    from paper_2001_02327_gb300 import unet as U
+    t0 = time.perf_counter()
+    train = LR.make_samples(torch, args.samples, n=64, seed0=1000)
+    val = LR.make_samples(torch, 32, n=64, seed0=90000)
+    t_gen = time.perf_counter() - t0
+    net = U.mg_unet_create(64, 4, seed=1)
+    nets = []
+    try:
+        v0 = LR.validation_loss(torch, net, val)
+        t0 = time.perf_counter()
+        losses = LR.train(torch, net, train, steps=args.train_steps, batch=4, lr=1e-3)
+        t_train = time.perf_counter() - t0
+        v1 = LR.validation_loss(torch, net, val)
+        p = U.mg_unet_get_params(net)
+        out = {"case": "learned initial guess", "samples": args.samples, "train_steps": args.train_steps,
+               "gen_s": t_gen, "train_s": t_train, "val_loss_before": v0, "val_loss_after": v1,
+               "train_loss_last50": float(np.mean(losses[-50:]))}
+        for n, count, seed in ((64, 4, 200000), (128, 2, 300000)):
+            e = U.mg_unet_create(n, 1, seed=0)
+            nets.append(e)
+            U.mg_unet_set_params(e, p)
+            out[f"eval_{n}"] = LR.evaluate(torch, e, [LR.random_nested(seed + k, n, 3) for k in range(count)])
+        print(json.dumps(out), flush=True)
+    finally:
+        for e in [net] + nets:
+            U.mg_unet_destroy(e)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -630,7 +669,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="leave out the mixed + learned-guess form")
-    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale", "unet"],
+    ap.add_argument("--samples", type=int, default=256, help="learned case: training samples")
+    ap.add_argument("--train-steps", type=int, default=1500, help="learned case: training steps")
+    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale", "unet", "learned"],
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
@@ -649,6 +690,8 @@ def main():
         run_scale_case(args)
     elif args.case == "unet":
         run_unet_case(args)
+    elif args.case == "learned":
+        run_learned_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
