@@ -622,6 +622,57 @@ def run_unet_case(args):
         U.mg_unet_destroy(u)
 
 
+def run_2d_case(args):
+    """2D workloads: 3 nested 64^2 levels (density (1 - r^2/0.25)^4, closed-form
+    outer boundary, V(2,2)) and the model of Sec. 3.1 at N = 1024 (4 levels,
+    V(2,1)); FP64 and mixed, solved to 1e-10 with forces.  Prints one line per
+    workload and form (zones/s of set_density + solve + forces, CUDA events,
+    median), not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for H, nu in ((I.config_2d_disk(64, 3), (2, 2)), (I.paper_2d(1024), (2, 1))):
+        inp = I.level_inputs(H)
+        d = [{k: dev(v) for k, v in x.items()} for x in inp]
+        F = [torch.empty((2, n, n), dtype=torch.float64, device="cuda") for n in H.n]
+        for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+            h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=nu[0], nu_post=nu[1], max_cycles=60,
+                                                                     rel_tol=TOL, precision=prec, inner_cycles=3))
+            try:
+                if prec == mg.MG_MIXED:
+                    mg.mg_autotune(h, args.tune_cache)
+
+                def step():
+                    mg.mg_set_density(h, 0, 0, d[0]["rho"], d[0]["bc_rho"], d[0]["bc_phi"])
+                    for l in range(1, H.num_levels):
+                        mg.mg_set_density(h, 0, l, d[l]["rho"])
+                    st = mg.mg_solve(h, 1)[1]
+                    for l in range(H.num_levels):
+                        mg.mg_forces(h, 0, l, None, F[l])
+                    return st
+
+                for _ in range(args.warmup):
+                    st = step()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ms = []
+                for _ in range(args.steps):
+                    torch.cuda.synchronize()
+                    ev0.record()
+                    st = step()
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    ms.append(ev0.elapsed_time(ev1))
+                t = statistics.median(ms)
+                print(json.dumps({"case": H.name, "form": name, "zones": H.zones(), "ms_per_solve": t,
+                                  "zones_per_s": H.zones() / (t * 1e-3),
+                                  "cycles_per_level": [st[0][l]["cycles"] for l in range(H.num_levels)],
+                                  "max_rel_res": max(st[0][l]["rel_res"] for l in range(H.num_levels))}), flush=True)
+            finally:
+                mg.mg_destroy(h)
+
+
 def run_learned_case(args):
     """The learned initial guess end to end: training samples generated by the
     solver (hierarchies of 64^3 levels with 1-8 random compact spheres), the
@@ -671,7 +722,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="leave out the mixed + learned-guess form")
     ap.add_argument("--samples", type=int, default=256, help="learned case: training samples")
     ap.add_argument("--train-steps", type=int, default=1500, help="learned case: training steps")
-    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale", "unet", "learned"],
+    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale", "unet", "learned", "2d"],
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
@@ -692,6 +743,8 @@ def main():
         run_unet_case(args)
     elif args.case == "learned":
         run_learned_case(args)
+    elif args.case == "2d":
+        run_2d_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
