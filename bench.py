@@ -370,6 +370,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": fb["d2h"]},
         "gpu_launches": launches,
         "roofline": roofline,
+        "roofline_dram_resident": dram_resident_roofline(mg, torch),
         "clocks": forms["fp64"]["clocks"],
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -395,6 +396,39 @@ def train_guess_network(torch):
     LR.train(torch, net, data, steps=300, batch=4, lr=1e-3)
     torch.cuda.synchronize()
     return net
+
+
+def dram_resident_roofline(mg, torch):
+    """Bandwidth of the FP32 smoothing kernel where it meets DRAM: one 3D level
+    of n = 254 (258^3 arrays, 69 MB each in FP32: beyond L2), two mixed-
+    precision cycles under the library's per-launch CUDA-event profile;
+    algorithmic bytes (2 words per active cell and colour) over the summed
+    times of the finest multigrid level's smoothing launches."""
+    n = 254
+    rng = np.random.default_rng(I.BASE_SEED + 254)
+    H = I.Hierarchy(3, [n], [(0.0, 0.0, 0.0)], 1.0 / n, 1.0, [], f"level{n}")
+    dev = lambda a: torch.from_numpy(a).cuda()
+    rho, bcr, bcp = (dev(rng.standard_normal((k,) * 3)) for k in (n, n + 2, n + 4))
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(max_cycles=2, rel_tol=0.0, precision=mg.MG_MIXED,
+                                                             inner_cycles=1))
+    try:
+        mg.mg_set_density(h, 0, 0, rho, bcr, bcp)
+        mg.mg_solve(h, 1, allow_noconv=True)                    # warm-up
+        mg.mg_set_density(h, 0, 0, rho, bcr, bcp)
+        mg.mg_profile(h, 1)
+        mg.mg_solve(h, 1, allow_noconv=True)
+        prof = mg.mg_profile_read(h)
+        mg.mg_profile(h, 0)
+    finally:
+        mg.mg_destroy(h)
+    launches, ms, nbytes = prof["smooth_colour_finest"]
+    peak, src = measured_peaks()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": "smooth_colour_finest (FP32)", "workload": "one 3D level n=254, 2 mixed cycles", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "launches": launches, "traffic": kernel_traffic("smooth_colour_finest", "level254_mixed"),
+            "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+            "timing": "per-launch CUDA events (each pair adds about 1 us to a launch of about 43 us)"}
 
 
 def run_reference(args):

@@ -227,11 +227,11 @@ void build_geometry(LevelData &ld, int dim)
 #define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
 
 enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
-                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_CLUSTER, KK_COUNT };
+                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_CLUSTER, KK_SMOOTH0, KK_COUNT };
 const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
                                          "defect",        "accumulate",     "interface",       "forces",
                                          "set_density",   "bottom",         "tb_pre",          "tb_post",
-                                         "cluster_vcycle"};
+                                         "cluster_vcycle", "smooth_colour_finest"};
 
 // Per-launch CUDA-event timing on the hierarchy's stream (mg_profile).
 struct Profiler {
@@ -483,7 +483,9 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     const double bytes = 2.0 * (fp32 ? 4 : 8) * cells_d(g.N, dim);   // read Phi, read/write one colour
     for (int sw = 0; sw < sweeps; sw++)
         for (int c = 0; c < 2; c++) {
-            cudaError_t e = timed(h, KK_SMOOTH, bytes, [&] { return mg_launch_smooth(dim, fp32, phi, f, g, c, s); });
+            // the finest multigrid level is profiled apart from the coarser ones
+            cudaError_t e = timed(h, L == 0 ? KK_SMOOTH0 : KK_SMOOTH, bytes,
+                                  [&] { return mg_launch_smooth(dim, fp32, phi, f, g, c, s); });
             if (e)
                 return e;
         }
