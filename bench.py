@@ -340,8 +340,13 @@ def run_ours(args):
         U.mg_unet_destroy(net)
     fb = forms[best]
 
-    # roofline of the dominant kernel of the reported form
-    kname, (kl, kms, kbytes) = max(fb["prof"].items(), key=lambda kv: kv[1][1])
+    # roofline of the dominant kernel of the reported form: the profiler keeps
+    # the finest multigrid level's smoothing apart, the kernel is the same one
+    by_kernel = {}
+    for k, v in fb["prof"].items():
+        k = "smooth_colour" if k == "smooth_colour_finest" else k
+        by_kernel[k] = [a + b for a, b in zip(by_kernel.get(k, (0, 0.0, 0.0)), v)]
+    kname, (kl, kms, kbytes) = max(by_kernel.items(), key=lambda kv: kv[1][1])
     launch_ms = kms / kl
     per_launch_bytes = kbytes / kl
     peak, peak_src = measured_peaks()
