@@ -500,6 +500,90 @@ __device__ __forceinline__ void op_resid_restrict_staged(const T *__restrict__ p
     }
 }
 
+// Smoothing plan of the one-block kernel: entry t of colour c of a level
+// (t over the half-rows of op_smooth_colour's walk, so the same cells in the
+// same order) holds the cell's index in the level array (bits 0-19) and which
+// of its six neighbours the ghost rule drops (bits 20-25: x-, x+, y-, y+, z-,
+// z+), or -1 when the half-row has no cell of that colour; a second array
+// holds the cell's negated reciprocal diagonal.  Built once per launch, it
+// leaves each smoothing phase with loads, five additions and the update.
+constexpr int kPlanCellBits = 20;
+
+template <int DIM>
+__host__ __device__ __forceinline__ int bottom_plan_count(int N)
+{
+    return ((N + 1) >> 1) * N * (DIM == 3 ? N : 1);   // entries per colour
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void bottom_plan_build(const MgGeom &g, int *__restrict__ pidx, T *__restrict__ pnid,
+                                                  int t0, int stride)
+{
+    const int N = g.N, half = (N + 1) >> 1, cnt = bottom_plan_count<DIM>(N);
+    const bool coarse = g.L > 0, tieN = g.tie && N >= 2;
+    for (int t = t0; t < 2 * cnt; t += stride) {
+        const int c = t >= cnt ? 1 : 0, r = t - c * cnt;
+        const int x = r % half, y = (r / half) % N, z = DIM == 3 ? r / (half * N) : 0;
+        const int j = y + 1, k = DIM == 3 ? z + 1 : 0;
+        const int i = ((((1 + j + k) & 1) == c) ? 1 : 2) + 2 * x;
+        if (i > N) {
+            pidx[t] = -1;
+            pnid[t] = T(0);
+            continue;
+        }
+        int e = lin<DIM>(i, j, k, g.E), cls = 0;
+        if (coarse) {
+            // the drops and boundary classes of neighbour_sum_ptr
+            auto axis = [&](int a, int shift, int bit) {
+                const bool lo = a == 1, hi = a == N;
+                cls |= ((lo ? 1 : 0) | (hi ? 2 : 0)) << shift;
+                if (lo || (hi && tieN))
+                    e |= 1 << bit;
+                if (hi)
+                    e |= 1 << (bit + 1);
+            };
+            axis(i, 0, kPlanCellBits);
+            axis(j, 2, kPlanCellBits + 2);
+            if (DIM == 3)
+                axis(k, 4, kPlanCellBits + 4);
+        }
+        pidx[t] = e;
+        pnid[t] = neg_inv_diag<T, DIM>(g, cls);
+    }
+}
+
+// One colour of a red-black sweep from the plan: the arithmetic of
+// op_smooth_colour (the same neighbour sum, association included, and the
+// same update), dropped neighbours read from a zero in shared memory.
+template <typename T, int DIM>
+__device__ __forceinline__ void bottom_plan_smooth(T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g,
+                                                   const int *__restrict__ pidx, const T *__restrict__ pnid,
+                                                   const T *zero, int t0, int stride)
+{
+    const int cnt = bottom_plan_count<DIM>(g.N);
+    const int sy = g.E, sz = DIM == 3 ? g.E * g.E : 0;
+    const T h2 = geo_h2<T>(g);
+    constexpr int B = kPlanCellBits;
+    for (int t = t0; t < cnt; t += stride) {
+        const int e = pidx[t];
+        if (e < 0)
+            continue;
+        const int p = e & ((1 << B) - 1);
+        T *c = phi + p;
+        const T *a0 = (e >> B) & 1 ? zero : c - 1;
+        const T *a1 = (e >> (B + 1)) & 1 ? zero : c + 1;
+        const T *a2 = (e >> (B + 2)) & 1 ? zero : c - sy;
+        const T *a3 = (e >> (B + 3)) & 1 ? zero : c + sy;
+        T s = (*a0 + *a1) + (*a2 + *a3);
+        if (DIM == 3) {
+            const T *a4 = (e >> (B + 4)) & 1 ? zero : c - sz;
+            const T *a5 = (e >> (B + 5)) & 1 ? zero : c + sz;
+            s += *a4 + *a5;
+        }
+        *c = (s - h2 * f[p]) * pnid[t];
+    }
+}
+
 // The part of the V-cycle at and below multigrid level Ls (Sec. 2.3 steps
 // 6-11 restricted to those levels) in one thread block, every array of those
 // levels in shared memory: pre-smoothing at Ls, restriction and smoothing
@@ -507,25 +591,38 @@ __device__ __forceinline__ void op_resid_restrict_staged(const T *__restrict__ p
 // Phi and f of level Ls come from global memory (f written by the
 // restriction from Ls-1, Phi zero; or the finest level itself when Ls = 0);
 // the smoothed Phi of level Ls goes back.  Same per-cell arithmetic and the
-// same order of phases as the one-kernel-per-phase path.
+// same order of phases as the one-kernel-per-phase path.  Shared memory, in
+// elements of T: Phi and f of every level, the residual scratch of level Ls,
+// the plans' diagonals and one zero; then the plans' cell entries (int).
 template <typename T, int DIM>
 __device__ __forceinline__ void bottom_body(T *__restrict__ phi_g, const T *__restrict__ f_g, const MgBottom &bt,
                                             int nu_pre, int nu_post, unsigned char *smem_raw)
 {
     T *sm = reinterpret_cast<T *>(smem_raw);
-    int offs[MG_BOTTOM_MAX + 1];
+    int offs[MG_BOTTOM_MAX + 1], poffs[MG_BOTTOM_MAX + 1];
     offs[0] = 0;
+    poffs[0] = 0;
     for (int q = 0; q < bt.nlev; q++) {
         const int c = DIM == 3 ? bt.g[q].E * bt.g[q].E * bt.g[q].E : bt.g[q].E * bt.g[q].E;
         offs[q + 1] = offs[q] + 2 * c;
+        poffs[q + 1] = poffs[q] + 2 * bottom_plan_count<DIM>(bt.g[q].N);
     }
     auto PHI = [&](int q) { return sm + offs[q]; };
     auto F = [&](int q) { return sm + offs[q] + (offs[q + 1] - offs[q]) / 2; };
     const int tid = threadIdx.x, nth = blockDim.x;
     const int total = offs[bt.nlev];
     const int c0 = (offs[1] - offs[0]) / 2;
+    const int n0 = DIM == 3 ? bt.g[0].N * bt.g[0].N * bt.g[0].N : bt.g[0].N * bt.g[0].N;
+    T *scratch = sm + total;              // residuals of the finest level of the block
+    T *pnid = scratch + n0;
+    T *zero = pnid + poffs[bt.nlev];
+    int *pidx = reinterpret_cast<int *>(zero + 1);
     for (int t = tid; t < total; t += nth)
         sm[t] = T(0);
+    if (tid == 0)
+        *zero = T(0);
+    for (int q = 0; q < bt.nlev; q++)
+        bottom_plan_build<T, DIM>(bt.g[q], pidx + poffs[q], pnid + poffs[q], tid, nth);
     __syncthreads();
     for (int t = tid; t < c0; t += nth) {
         PHI(0)[t] = phi_g[t];
@@ -533,15 +630,16 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ phi_g, const T *__re
     }
     __syncthreads();
     auto smooth = [&](int q, int sweeps) {
+        const int cnt = bottom_plan_count<DIM>(bt.g[q].N);
         for (int sw = 0; sw < sweeps; sw++)
             for (int c = 0; c < 2; c++) {
-                op_smooth_colour<T, DIM>(PHI(q), F(q), bt.g[q], c, tid, nth);
+                bottom_plan_smooth<T, DIM>(PHI(q), F(q), bt.g[q], pidx + poffs[q] + c * cnt,
+                                           pnid + poffs[q] + c * cnt, zero, tid, nth);
                 __syncthreads();
             }
     };
     smooth(0, bt.g[0].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
     int q = 0;
-    T *scratch = sm + offs[bt.nlev];      // residuals of the finest level of the block
     while (bt.g[q].N > 1 && q + 1 < bt.nlev) {
         op_resid_restrict_staged<T, DIM>(PHI(q), F(q), bt.g[q], PHI(q + 1), F(q + 1), bt.g[q + 1], scratch, tid,
                                          nth);
@@ -1945,11 +2043,14 @@ cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const
 
 size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt)
 {
-    size_t c = 0;
-    for (int q = 0; q < bt.nlev; q++)
+    size_t c = 0, plan = 0;
+    for (int q = 0; q < bt.nlev; q++) {
         c += 2 * (size_t)cube(bt.g[q].E, dim);
+        plan += 2 * (size_t)(dim == 3 ? bottom_plan_count<3>(bt.g[q].N) : bottom_plan_count<2>(bt.g[q].N));
+    }
     c += (size_t)cube(bt.g[0].N, dim);      // residual scratch of the first level
-    return c * (fp32 ? 4 : 8);
+    c += plan + 1;                          // plan diagonals and the zero
+    return c * (fp32 ? 4 : 8) + plan * sizeof(int);
 }
 
 cudaError_t mg_bottom_prepare()

@@ -627,6 +627,33 @@ def test_cluster_vcycle_matches_one_kernel_per_phase(mg, make, prec, lim, monkey
         assert np.array_equal(a[l][1], b[l][1]), l
 
 
+@pytest.mark.parametrize("make,prec,lim", [
+    (lambda: I.config_3d_offset_sphere(64, 3), "fp64", 8),
+    (lambda: I.config_3d_offset_sphere(64, 3), "mixed", 8),
+    (lambda: I.config_3d_offset_sphere(32, 3), "fp64", 17),
+    (lambda: I.paper_3d(48), "mixed", 13),
+    (lambda: I.config_2d_disk(64, 3), "fp64", 33),
+    (lambda: I.config_2d_disk(64, 3), "mixed", 17)])
+def test_one_block_bottom_matches_one_kernel_per_phase(mg, make, prec, lim, monkeypatch):
+    """The multigrid levels from N <= lim down in the one-block kernel (every
+    array in shared memory, smoothing from its per-cell plan) give results
+    bit-identical to one kernel per phase on every level but the last."""
+    H = make()
+    inp = I.level_inputs(H)
+    p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
+    kw = dict(nu_pre=2, nu_post=2, max_cycles=4, rel_tol=0.0, precision=p, inner_cycles=2)
+    for v in ("MG_BOTTOM_N64", "MG_BOTTOM_N32", "MG_CLUSTER_N64", "MG_CLUSTER_N32"):
+        monkeypatch.setenv(v, "0")
+    a, pa = _solve_profiled(mg, H, inp, **kw)
+    monkeypatch.setenv("MG_BOTTOM_N64", str(lim))
+    monkeypatch.setenv("MG_BOTTOM_N32", str(lim))
+    b, pb = _solve_profiled(mg, H, inp, **kw)
+    assert pb.get("smooth_colour", (0,))[0] < pa["smooth_colour"][0], (pa, pb)
+    for l in range(H.num_levels):
+        assert np.array_equal(a[l][0], b[l][0]), (l, relmax(b[l][0], a[l][0]))
+        assert np.array_equal(a[l][1], b[l][1]), l
+
+
 def test_cluster_vcycle_is_3d_only(mg, monkeypatch):
     H = I.config_2d_disk(64, 3)
     inp = I.level_inputs(H)
