@@ -47,6 +47,10 @@ struct LevelData {
     int Lc[2] = {-1, -1};          // first level handled by the cluster kernel (-1: none)
     int Llim[2] = {0, 0};          // the level-size limit that chose it
     MgBottom bt[2];
+    // device image of the one-block kernel's plan for the precision the
+    // V-cycles run in, sized for the largest bottom the level admits
+    void *bplan = nullptr;
+    size_t bplan_bytes = 0;
 };
 
 // Largest multigrid level (cells per edge) given to the one-block bottom
@@ -104,7 +108,25 @@ void plan_bottom(LevelData &ld, int dim, int lim32 = -1)
         ld.bt[w].nlev = ld.nmg - Ls;
         for (int q = 0; q < ld.bt[w].nlev; q++)
             ld.bt[w].g[q] = ld.g[Ls + q];
+        ld.bt[w].plan = nullptr;   // until refresh_bottom_plan writes the image for these levels
     }
+}
+
+// Bytes of the largest plan image a one-block kernel of this level can use
+// (the first level from which the kernel's shared memory fits).
+size_t max_bottom_plan_bytes(const LevelData &ld, int dim, bool fp32)
+{
+    for (int L = 0; L < ld.nmg; L++) {
+        if (ld.nmg - L > MG_BOTTOM_MAX)
+            continue;
+        MgBottom bt;
+        bt.nlev = ld.nmg - L;
+        for (int q = 0; q < bt.nlev; q++)
+            bt.g[q] = ld.g[L + q];
+        if (mg_bottom_smem(dim, fp32, bt) <= MG_BOTTOM_SMEM_MAX)
+            return mg_bottom_plan_bytes(dim, fp32, bt);
+    }
+    return 0;
 }
 
 long cells(int e, int dim) { return dim == 3 ? (long)e * e * e : (long)e * e; }
@@ -490,6 +512,24 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
                 return e;
         }
     return cudaSuccess;
+}
+
+// Writes the one-block kernel's plan image for the levels plan_bottom chose
+// (precision of the V-cycles) and hands it to the kernel; until then the
+// kernel builds the plan itself.  Synchronous: runs at creation and tuning.
+cudaError_t refresh_bottom_plan(mg_hierarchy *h, LevelData &ld)
+{
+    const bool fp32 = h->opt.precision == MG_MIXED;
+    MgBottom &bt = ld.bt[fp32 ? 1 : 0];
+    bt.plan = nullptr;
+    if (!ld.bplan || mg_bottom_plan_bytes(h->dim, fp32, bt) > ld.bplan_bytes)
+        return cudaSuccess;
+    cudaError_t e = mg_launch_bottom_plan(h->dim, fp32, bt, ld.bplan, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess)
+        bt.plan = ld.bplan;
+    return e;
 }
 
 // the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level,
@@ -1251,6 +1291,8 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     int bestnb = 8;
     for (int nb : nbs) {
         plan_bottom(ld, dim, nb);
+        if ((err = refresh_bottom_plan(h, ld)))
+            return false;
         plan_tiles(ld, dim, o.nu_pre, o.nu_post);
         plan_cluster(ld, h->dim, h->csize, h->opt);
         const float ms = time_ms(h, 10, [&](cudaStream_t cs) { return vcycle(h, ld, true, cs); }, err);
@@ -1262,6 +1304,8 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
         }
     }
     plan_bottom(ld, dim, bestnb);
+    if ((err = refresh_bottom_plan(h, ld)))
+        return false;
     plan_cluster(ld, h->dim, h->csize, h->opt);
     te.bottom_n = bestnb;
     // 2. per level above the bottom: the tile of its pre/post pair
@@ -1317,12 +1361,14 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     return true;
 }
 
-void apply_entry(mg_hierarchy *h, LevelData &ld, const TuneEntry &te)
+cudaError_t apply_entry(mg_hierarchy *h, LevelData &ld, const TuneEntry &te)
 {
     plan_bottom(ld, h->dim, te.bottom_n);
+    const cudaError_t e = refresh_bottom_plan(h, ld);
     for (int L = 0; L < ld.nmg; L++)
         ld.tile[L] = L < ld.Ls[1] ? te.tile[L] : 0;
     plan_cluster(ld, h->dim, h->csize, h->opt);
+    return e;
 }
 
 std::vector<TuneEntry> read_cache(const char *path)
@@ -1476,6 +1522,9 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 slots.push_back({(void **)&ld.tab64[L], align256(128 * sizeof(double))});
                 slots.push_back({(void **)&ld.tab32[L], align256(128 * sizeof(float))});
             }
+            ld.bplan_bytes = max_bottom_plan_bytes(ld, dim, o.precision == MG_MIXED);
+            if (ld.bplan_bytes)
+                slots.push_back({(void **)&ld.bplan, align256(ld.bplan_bytes)});
             if (o.stop == MG_STOP_FORCE)
                 slots.push_back({(void **)&ld.prev, align256((size_t)cells(ld.n + 4, dim) * sizeof(double))});
             if (ld.frozen) {
@@ -1541,8 +1590,11 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
         h->csize = mg_cluster_prepare();
     if (e == cudaSuccess)
         e = mg_launch_zero(h->arena, bytes, h->stream);
+    if (e == cudaSuccess)   // the table copies below do not run on the caller's stream
+        e = cudaStreamSynchronize(h->stream);
     // boundary-diagonal tables of the coarse multigrid levels, then the plan
-    // of the one-block kernel (which copies the level descriptions)
+    // of the one-block kernel (which copies the level descriptions) and its
+    // image
     for (int b = 0; b < batch && e == cudaSuccess; b++)
         for (auto &ld : h->lev[b]) {
             for (int L = 1; L < ld.nmg && e == cudaSuccess; L++) {
@@ -1558,6 +1610,8 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 ld.g[L].tab32 = ld.tab32[L];
             }
             plan_bottom(ld, dim);
+            if (e == cudaSuccess)
+                e = refresh_bottom_plan(h, ld);
             plan_tiles(ld, dim, o.nu_pre, o.nu_post);
             plan_cluster(ld, h->dim, h->csize, h->opt);
         }
@@ -1837,7 +1891,8 @@ mg_status mg_autotune(mg_hierarchy *h, const char *cache_path)
                         te.nu_post == h->opt.nu_post)
                         hit = &te;
             if (hit) {
-                apply_entry(h, ld, *hit);
+                if (cudaError_t e = apply_entry(h, ld, *hit))
+                    return fail_cuda(h, e, "bottom plan");
                 continue;
             }
             TuneEntry te{};

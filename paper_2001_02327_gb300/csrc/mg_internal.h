@@ -79,6 +79,9 @@ cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const
 struct MgBottom {
     int nlev;                   // levels Ls .. Ls+nlev-1 (the last one has one cell)
     MgGeom g[MG_BOTTOM_MAX];
+    // device image of the kernel's per-cell plan for exactly these levels
+    // (mg_launch_bottom_plan), or NULL: the kernel then builds it itself
+    const void *plan = nullptr;
 };
 
 // One thread-block cluster running the V-cycle from a multigrid level Lc down
@@ -105,6 +108,9 @@ struct MgClusterPlan {
 };
 
 size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt);
+size_t mg_bottom_plan_bytes(int dim, bool fp32, const MgBottom &bt);
+// writes the per-cell plan of bt's levels to `img` (mg_bottom_plan_bytes)
+cudaError_t mg_launch_bottom_plan(int dim, bool fp32, const MgBottom &bt, void *img, cudaStream_t s);
 cudaError_t mg_bottom_prepare();   // once per device before the first launch
 cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const MgBottom &bt, int nu_pre,
                              int nu_post, cudaStream_t s);

@@ -311,26 +311,14 @@ __device__ __forceinline__ void ghost_map(int q, const MgGeom &gc, int &idx, T &
     }
 }
 
-// Prolongation and correction (Sec. 2.3 step 10; bi/trilinear 3/4-1/4
-// weights per axis, i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse
-// ghosts by the rule, evaluated one axis at a time.
-// P(Phi_c) at fine active cell f (Sec. 2.3 step 10); plane(kz) returns the
-// coarse plane kz (the whole array in 2D)
+// Prolongation (Sec. 2.3 step 10; bi/trilinear 3/4-1/4 weights per axis,
+// i.e. 9/3/3/1 in 2D and 27/9/9/9/3/3/3/1 in 3D), coarse ghosts by the rule,
+// evaluated one axis at a time: the interpolation from per-axis coarse
+// indices and weights; plane(kz) returns the coarse plane kz (the whole
+// array in 2D)
 template <typename T, int DIM, typename Planes>
-__device__ __forceinline__ T prolong_value_pl(const Planes &plane, const MgGeom &gc, const int *f)
+__device__ __forceinline__ T prolong_combine(const Planes &plane, int Ec, const int (&idx)[3][2], const T (&w)[3][2])
 {
-    const int Ec = gc.E;
-    int idx[3][2];
-    T w[3][2];
-    for (int a = 0; a < DIM; a++) {
-        const int near = (f[a] + 1) >> 1;
-        const int far = (f[a] & 1) ? near - 1 : near + 1;
-        T c0, c1;
-        ghost_map<T>(near, gc, idx[a][0], c0);
-        ghost_map<T>(far, gc, idx[a][1], c1);
-        w[a][0] = T(0.75) * c0;
-        w[a][1] = T(0.25) * c1;
-    }
     if (DIM == 3) {
         T zsum = T(0);
         for (int c = 0; c < 2; c++) {
@@ -353,6 +341,30 @@ __device__ __forceinline__ T prolong_value_pl(const Planes &plane, const MgGeom 
         ysum += w[1][b] * xv;
     }
     return ysum;
+}
+
+// the two coarse indices and weights along one axis for fine index v
+template <typename T>
+__device__ __forceinline__ void prolong_axis(int v, const MgGeom &gc, int &i0, int &i1, T &w0, T &w1)
+{
+    const int near = (v + 1) >> 1;
+    const int far = (v & 1) ? near - 1 : near + 1;
+    T c0, c1;
+    ghost_map<T>(near, gc, i0, c0);
+    ghost_map<T>(far, gc, i1, c1);
+    w0 = T(0.75) * c0;
+    w1 = T(0.25) * c1;
+}
+
+// P(Phi_c) at fine active cell f
+template <typename T, int DIM, typename Planes>
+__device__ __forceinline__ T prolong_value_pl(const Planes &plane, const MgGeom &gc, const int *f)
+{
+    int idx[3][2] = {};
+    T w[3][2] = {};
+    for (int a = 0; a < DIM; a++)
+        prolong_axis<T>(f[a], gc, idx[a][0], idx[a][1], w[a][0], w[a][1]);
+    return prolong_combine<T, DIM>(plane, gc.E, idx, w);
 }
 
 template <typename T, int DIM>
@@ -500,13 +512,16 @@ __device__ __forceinline__ void op_resid_restrict_staged(const T *__restrict__ p
     }
 }
 
-// Smoothing plan of the one-block kernel: entry t of colour c of a level
-// (t over the half-rows of op_smooth_colour's walk, so the same cells in the
-// same order) holds the cell's index in the level array (bits 0-19) and which
-// of its six neighbours the ghost rule drops (bits 20-25: x-, x+, y-, y+, z-,
-// z+), or -1 when the half-row has no cell of that colour; a second array
-// holds the cell's negated reciprocal diagonal.  Built once per launch, it
-// leaves each smoothing phase with loads, five additions and the update.
+// Per-cell plan of the one-block kernel, built once per launch so that its
+// phases are loads, the arithmetic and a barrier.  Entry t of colour c of a
+// level (t over the half-rows of op_smooth_colour's walk: the same cells in
+// the same order; the two colours together cover every active cell once)
+// holds in `idx` the cell's index in the level array (bits 0-19) and which of
+// its six neighbours the ghost rule drops (bits 20-25: x-, x+, y-, y+, z-, z+),
+// or -1 when the half-row has no cell of that colour; in `ijk` its indices
+// (i | j << 8 | k << 16); in `nid` and `dg` its negated reciprocal diagonal and
+// its diagonal.  Per fine level, for each index v = 1..N along an axis, the
+// prolongation's two coarse indices and weights (ghost rule applied).
 constexpr int kPlanCellBits = 20;
 
 template <int DIM>
@@ -515,9 +530,15 @@ __host__ __device__ __forceinline__ int bottom_plan_count(int N)
     return ((N + 1) >> 1) * N * (DIM == 3 ? N : 1);   // entries per colour
 }
 
+template <typename T>
+struct BottomPlan {
+    int *idx, *ijk;
+    T *nid, *dg;
+};
+
 template <typename T, int DIM>
-__device__ __forceinline__ void bottom_plan_build(const MgGeom &g, int *__restrict__ pidx, T *__restrict__ pnid,
-                                                  int t0, int stride)
+__device__ __forceinline__ void bottom_plan_build(const MgGeom &g, const BottomPlan<T> &P, const T *stab, int t0,
+                                                  int stride)
 {
     const int N = g.N, half = (N + 1) >> 1, cnt = bottom_plan_count<DIM>(N);
     const bool coarse = g.L > 0, tieN = g.tie && N >= 2;
@@ -527,8 +548,10 @@ __device__ __forceinline__ void bottom_plan_build(const MgGeom &g, int *__restri
         const int j = y + 1, k = DIM == 3 ? z + 1 : 0;
         const int i = ((((1 + j + k) & 1) == c) ? 1 : 2) + 2 * x;
         if (i > N) {
-            pidx[t] = -1;
-            pnid[t] = T(0);
+            P.idx[t] = -1;
+            P.ijk[t] = 0;
+            P.nid[t] = T(0);
+            P.dg[t] = T(0);
             continue;
         }
         int e = lin<DIM>(i, j, k, g.E), cls = 0;
@@ -547,14 +570,40 @@ __device__ __forceinline__ void bottom_plan_build(const MgGeom &g, int *__restri
             if (DIM == 3)
                 axis(k, 4, kPlanCellBits + 4);
         }
-        pidx[t] = e;
-        pnid[t] = neg_inv_diag<T, DIM>(g, cls);
+        P.idx[t] = e;
+        P.ijk[t] = i | (j << 8) | (k << 16);
+        // the values of neg_inv_diag and diag_of, the level's table read from
+        // its copy in shared memory
+        if (cls == 0 || !stab) {
+            P.nid[t] = neg_inv_diag<T, DIM>(g, cls);
+            P.dg[t] = diag_of<T, DIM>(g, cls);
+        } else {
+            P.nid[t] = stab[64 + cls];
+            P.dg[t] = stab[cls];
+        }
     }
 }
 
-// One colour of a red-black sweep from the plan: the arithmetic of
-// op_smooth_colour (the same neighbour sum, association included, and the
-// same update), dropped neighbours read from a zero in shared memory.
+// the ghost-folded neighbour sum of neighbour_sum_ptr (same association) of
+// the cell of plan entry e at c, dropped neighbours read from `zero`
+template <typename T, int DIM>
+__device__ __forceinline__ T bottom_plan_nsum(const T *c, int e, int sy, int sz, const T *zero)
+{
+    constexpr int B = kPlanCellBits;
+    const T *a0 = (e >> B) & 1 ? zero : c - 1;
+    const T *a1 = (e >> (B + 1)) & 1 ? zero : c + 1;
+    const T *a2 = (e >> (B + 2)) & 1 ? zero : c - sy;
+    const T *a3 = (e >> (B + 3)) & 1 ? zero : c + sy;
+    T s = (*a0 + *a1) + (*a2 + *a3);
+    if (DIM == 3) {
+        const T *a4 = (e >> (B + 4)) & 1 ? zero : c - sz;
+        const T *a5 = (e >> (B + 5)) & 1 ? zero : c + sz;
+        s += *a4 + *a5;
+    }
+    return s;
+}
+
+// one colour of a red-black sweep (the arithmetic of op_smooth_colour)
 template <typename T, int DIM>
 __device__ __forceinline__ void bottom_plan_smooth(T *__restrict__ phi, const T *__restrict__ f, const MgGeom &g,
                                                    const int *__restrict__ pidx, const T *__restrict__ pnid,
@@ -563,26 +612,119 @@ __device__ __forceinline__ void bottom_plan_smooth(T *__restrict__ phi, const T 
     const int cnt = bottom_plan_count<DIM>(g.N);
     const int sy = g.E, sz = DIM == 3 ? g.E * g.E : 0;
     const T h2 = geo_h2<T>(g);
-    constexpr int B = kPlanCellBits;
     for (int t = t0; t < cnt; t += stride) {
         const int e = pidx[t];
         if (e < 0)
             continue;
-        const int p = e & ((1 << B) - 1);
+        const int p = e & ((1 << kPlanCellBits) - 1);
         T *c = phi + p;
-        const T *a0 = (e >> B) & 1 ? zero : c - 1;
-        const T *a1 = (e >> (B + 1)) & 1 ? zero : c + 1;
-        const T *a2 = (e >> (B + 2)) & 1 ? zero : c - sy;
-        const T *a3 = (e >> (B + 3)) & 1 ? zero : c + sy;
-        T s = (*a0 + *a1) + (*a2 + *a3);
-        if (DIM == 3) {
-            const T *a4 = (e >> (B + 4)) & 1 ? zero : c - sz;
-            const T *a5 = (e >> (B + 5)) & 1 ? zero : c + sz;
-            s += *a4 + *a5;
-        }
+        const T s = bottom_plan_nsum<T, DIM>(c, e, sy, sz, zero);
         *c = (s - h2 * f[p]) * pnid[t];
     }
 }
+
+// Residual (Sec. 2.3 step 4) of every active cell of level gf into r at the
+// cell's own index (r's ghost positions stay zero), then the 2^d-child
+// average into level gc (step 5): the arithmetic and order of
+// op_resid_restrict_staged, children beyond N read as a zero.  Contains a
+// __syncthreads.
+template <typename T, int DIM>
+__device__ __forceinline__ void bottom_plan_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
+                                                     const MgGeom &gf, const BottomPlan<T> &Pf,
+                                                     T *__restrict__ phi_c, T *__restrict__ f_c, const MgGeom &gc,
+                                                     const BottomPlan<T> &Pc, T *__restrict__ r, const T *zero,
+                                                     int t0, int stride)
+{
+    constexpr int M = (1 << kPlanCellBits) - 1;
+    const int Ef = gf.E, sz = DIM == 3 ? Ef * Ef : 0;
+    const int nf = 2 * bottom_plan_count<DIM>(gf.N);
+    const T ih2 = geo_inv_h2<T>(gf);
+    for (int t = t0; t < nf; t += stride) {
+        const int e = Pf.idx[t];
+        if (e < 0)
+            continue;
+        const int p = e & M;
+        const T *c = phi_f + p;
+        const T other = bottom_plan_nsum<T, DIM>(c, e, Ef, sz, zero);
+        r[p] = f_f[p] - (other + Pf.dg[t] * c[0]) * ih2;
+    }
+    __syncthreads();
+    const int nc = 2 * bottom_plan_count<DIM>(gc.N);
+    const T w = DIM == 3 ? T(0.125) : T(0.25);
+    for (int t = t0; t < nc; t += stride) {
+        const int e = Pc.idx[t];
+        if (e < 0)
+            continue;
+        const int ijk = Pc.ijk[t];
+        const int I = ijk & 255, J = (ijk >> 8) & 255, K = ijk >> 16;
+        const T *b = r + lin<DIM>(2 * I - 1, 2 * J - 1, DIM == 3 ? 2 * K - 1 : 0, Ef);
+        T s = T(0);
+        for (int dk = 0; dk < (DIM == 3 ? 2 : 1); dk++)
+            for (int dj = 0; dj < 2; dj++)
+                for (int di = 0; di < 2; di++)
+                    s += b[dk * sz + dj * Ef + di];
+        f_c[e & M] = w * s;
+        phi_c[e & M] = T(0);
+    }
+}
+
+// Prolongation and correction (Sec. 2.3 step 10) into every active cell of
+// level gf, the per-axis indices and weights from the tables ix, wt (entries
+// 2(v-1), 2(v-1)+1 for fine index v): the arithmetic of op_prolong.
+template <typename T, int DIM>
+__device__ __forceinline__ void bottom_plan_prolong(const T *__restrict__ phi_c, const MgGeom &gc,
+                                                    T *__restrict__ phi_f, const MgGeom &gf,
+                                                    const BottomPlan<T> &Pf, const int *__restrict__ ix,
+                                                    const T *__restrict__ wt, int t0, int stride)
+{
+    constexpr int M = (1 << kPlanCellBits) - 1;
+    const int nf = 2 * bottom_plan_count<DIM>(gf.N);
+    const int E2 = gc.E * gc.E;
+    for (int t = t0; t < nf; t += stride) {
+        const int e = Pf.idx[t];
+        if (e < 0)
+            continue;
+        const int ijk = Pf.ijk[t];
+        const int f[3] = {ijk & 255, (ijk >> 8) & 255, ijk >> 16};
+        int idx[3][2] = {};
+        T w[3][2] = {};
+        for (int a = 0; a < DIM; a++) {
+            const int v = 2 * (f[a] - 1);
+            idx[a][0] = ix[v];
+            idx[a][1] = ix[v + 1];
+            w[a][0] = wt[v];
+            w[a][1] = wt[v + 1];
+        }
+        phi_f[e & M] += prolong_combine<T, DIM>([&](int kz) { return phi_c + (DIM == 3 ? kz * E2 : 0); }, gc.E,
+                                                idx, w);
+    }
+}
+
+// Shared-memory layout of the one-block kernel, in elements: T region - Phi
+// and f of every level, each level's residual (in its own layout), the
+// plans' nid and dg, the prolongation weights, a copy of each level's
+// boundary-diagonal table (128 entries), one zero; int region - the plans'
+// idx and ijk, the prolongation indices.
+struct BottomLayout {
+    int lev[MG_BOTTOM_MAX + 1], res[MG_BOTTOM_MAX + 1], plan[MG_BOTTOM_MAX + 1], tab[MG_BOTTOM_MAX + 1];
+    __host__ __device__ BottomLayout(const MgBottom &bt, int dim)
+    {
+        lev[0] = res[0] = plan[0] = tab[0] = 0;
+        for (int q = 0; q < bt.nlev; q++) {
+            const int E = bt.g[q].E, N = bt.g[q].N;
+            const int vol = dim == 3 ? E * E * E : E * E;
+            lev[q + 1] = lev[q] + 2 * vol;
+            res[q + 1] = res[q] + vol;
+            plan[q + 1] = plan[q] + 2 * (dim == 3 ? bottom_plan_count<3>(N) : bottom_plan_count<2>(N));
+            tab[q + 1] = tab[q] + 2 * N;
+        }
+    }
+    __host__ __device__ size_t t_elems(int n) const
+    {
+        return (size_t)lev[n] + res[n] + 2 * plan[n] + tab[n] + 128 * (size_t)n + 1;
+    }
+    __host__ __device__ size_t i_elems(int n) const { return 2 * (size_t)plan[n] + tab[n]; }
+};
 
 // The part of the V-cycle at and below multigrid level Ls (Sec. 2.3 steps
 // 6-11 restricted to those levels) in one thread block, every array of those
@@ -591,64 +733,89 @@ __device__ __forceinline__ void bottom_plan_smooth(T *__restrict__ phi, const T 
 // Phi and f of level Ls come from global memory (f written by the
 // restriction from Ls-1, Phi zero; or the finest level itself when Ls = 0);
 // the smoothed Phi of level Ls goes back.  Same per-cell arithmetic and the
-// same order of phases as the one-kernel-per-phase path.  Shared memory, in
-// elements of T: Phi and f of every level, the residual scratch of level Ls,
-// the plans' diagonals and one zero; then the plans' cell entries (int).
+// same order of phases as the one-kernel-per-phase path, every phase from
+// the per-cell plan.
 template <typename T, int DIM>
 __device__ __forceinline__ void bottom_body(T *__restrict__ phi_g, const T *__restrict__ f_g, const MgBottom &bt,
                                             int nu_pre, int nu_post, unsigned char *smem_raw)
 {
+    const int n = bt.nlev;
+    const BottomLayout lay(bt, DIM);
     T *sm = reinterpret_cast<T *>(smem_raw);
-    int offs[MG_BOTTOM_MAX + 1], poffs[MG_BOTTOM_MAX + 1];
-    offs[0] = 0;
-    poffs[0] = 0;
-    for (int q = 0; q < bt.nlev; q++) {
-        const int c = DIM == 3 ? bt.g[q].E * bt.g[q].E * bt.g[q].E : bt.g[q].E * bt.g[q].E;
-        offs[q + 1] = offs[q] + 2 * c;
-        poffs[q + 1] = poffs[q] + 2 * bottom_plan_count<DIM>(bt.g[q].N);
-    }
-    auto PHI = [&](int q) { return sm + offs[q]; };
-    auto F = [&](int q) { return sm + offs[q] + (offs[q + 1] - offs[q]) / 2; };
+    T *res = sm + lay.lev[n];
+    T *nid = res + lay.res[n];
+    T *dg = nid + lay.plan[n];
+    T *wt = dg + lay.plan[n];
+    T *stab = wt + lay.tab[n];
+    T *zero = stab + 128 * n;
+    int *idx = reinterpret_cast<int *>(zero + 1);
+    int *ijk = idx + lay.plan[n];
+    int *ix = ijk + lay.plan[n];
+    auto PHI = [&](int q) { return sm + lay.lev[q]; };
+    auto F = [&](int q) { return sm + lay.lev[q] + (lay.lev[q + 1] - lay.lev[q]) / 2; };
+    auto plan = [&](int q) {
+        return BottomPlan<T>{idx + lay.plan[q], ijk + lay.plan[q], nid + lay.plan[q], dg + lay.plan[q]};
+    };
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int total = offs[bt.nlev];
-    const int c0 = (offs[1] - offs[0]) / 2;
-    const int n0 = DIM == 3 ? bt.g[0].N * bt.g[0].N * bt.g[0].N : bt.g[0].N * bt.g[0].N;
-    T *scratch = sm + total;              // residuals of the finest level of the block
-    T *pnid = scratch + n0;
-    T *zero = pnid + poffs[bt.nlev];
-    int *pidx = reinterpret_cast<int *>(zero + 1);
-    for (int t = tid; t < total; t += nth)
-        sm[t] = T(0);
-    if (tid == 0)
-        *zero = T(0);
-    for (int q = 0; q < bt.nlev; q++)
-        bottom_plan_build<T, DIM>(bt.g[q], pidx + poffs[q], pnid + poffs[q], tid, nth);
-    __syncthreads();
+    // 1. level Ls from global memory, every other array to zero, the plan's
+    // image (or the boundary-diagonal tables to build it from) to shared
+    // memory: the global loads in one phase
+    const int c0 = (lay.lev[1] - lay.lev[0]) / 2;
     for (int t = tid; t < c0; t += nth) {
         PHI(0)[t] = phi_g[t];
         F(0)[t] = f_g[t];
     }
+    for (int t = lay.lev[1] + tid; t < lay.lev[n] + lay.res[n]; t += nth)
+        sm[t] = T(0);
+    if (bt.plan) {
+        const int nimg = 2 * lay.plan[n] + lay.tab[n];   // nid, dg, wt and idx, ijk, ix are contiguous
+        const T *imgT = static_cast<const T *>(bt.plan);
+        const int *imgI = reinterpret_cast<const int *>(imgT + nimg);
+        for (int t = tid; t < nimg; t += nth) {
+            nid[t] = imgT[t];
+            idx[t] = imgI[t];
+        }
+    } else {
+        for (int t = tid; t < 128 * n; t += nth) {
+            const T *tb = tab_of<T>(bt.g[t >> 7]);
+            stab[t] = tb ? tb[t & 127] : T(0);
+        }
+    }
+    if (tid == 0)
+        *zero = T(0);
     __syncthreads();
+    // 2. the plans, when there is no image (bt.plan is the same for the block)
+    if (!bt.plan) {
+        for (int q = 0; q < n; q++)
+            bottom_plan_build<T, DIM>(bt.g[q], plan(q), tab_of<T>(bt.g[q]) ? stab + 128 * q : nullptr, tid, nth);
+        for (int q = 0; q + 1 < n; q++)
+            for (int v = 1 + tid; v <= bt.g[q].N; v += nth) {
+                const int o = lay.tab[q] + 2 * (v - 1);
+                prolong_axis<T>(v, bt.g[q + 1], ix[o], ix[o + 1], wt[o], wt[o + 1]);
+            }
+        __syncthreads();
+    }
     auto smooth = [&](int q, int sweeps) {
         const int cnt = bottom_plan_count<DIM>(bt.g[q].N);
+        const BottomPlan<T> P = plan(q);
         for (int sw = 0; sw < sweeps; sw++)
             for (int c = 0; c < 2; c++) {
-                bottom_plan_smooth<T, DIM>(PHI(q), F(q), bt.g[q], pidx + poffs[q] + c * cnt,
-                                           pnid + poffs[q] + c * cnt, zero, tid, nth);
+                bottom_plan_smooth<T, DIM>(PHI(q), F(q), bt.g[q], P.idx + c * cnt, P.nid + c * cnt, zero, tid, nth);
                 __syncthreads();
             }
     };
     smooth(0, bt.g[0].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
     int q = 0;
-    while (bt.g[q].N > 1 && q + 1 < bt.nlev) {
-        op_resid_restrict_staged<T, DIM>(PHI(q), F(q), bt.g[q], PHI(q + 1), F(q + 1), bt.g[q + 1], scratch, tid,
-                                         nth);
+    while (bt.g[q].N > 1 && q + 1 < n) {
+        bottom_plan_restrict<T, DIM>(PHI(q), F(q), bt.g[q], plan(q), PHI(q + 1), F(q + 1), bt.g[q + 1], plan(q + 1),
+                                     res + lay.res[q], zero, tid, nth);
         __syncthreads();
         smooth(q + 1, bt.g[q + 1].N == 1 ? (nu_pre > 0 ? 1 : 0) : nu_pre);
         q++;
     }
     while (q > 0) {
-        op_prolong<T, DIM>(PHI(q), bt.g[q], PHI(q - 1), bt.g[q - 1], tid, nth);
+        bottom_plan_prolong<T, DIM>(PHI(q), bt.g[q], PHI(q - 1), bt.g[q - 1], plan(q - 1), ix + lay.tab[q - 1],
+                                    wt + lay.tab[q - 1], tid, nth);
         __syncthreads();
         smooth(q - 1, nu_post);
         q--;
@@ -664,6 +831,30 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ phi_g
     pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     bottom_body<T, DIM>(phi_g, f_g, bt, nu_pre, nu_post, smem_raw);
+}
+
+// The plan image of the one-block kernel (one block, global memory): the
+// values bottom_body builds itself, in its shared-memory order - T part nid,
+// dg, wt, then int part idx, ijk, ix.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom_plan(MgBottom bt, T *__restrict__ img)
+{
+    pdl_begin();
+    const int n = bt.nlev;
+    const BottomLayout lay(bt, DIM);
+    T *nid = img, *dg = nid + lay.plan[n], *wt = dg + lay.plan[n];
+    int *idx = reinterpret_cast<int *>(wt + lay.tab[n]);
+    int *ijk = idx + lay.plan[n], *ix = ijk + lay.plan[n];
+    for (int q = 0; q < n; q++)
+        bottom_plan_build<T, DIM>(bt.g[q],
+                                  BottomPlan<T>{idx + lay.plan[q], ijk + lay.plan[q], nid + lay.plan[q],
+                                                dg + lay.plan[q]},
+                                  nullptr, threadIdx.x, blockDim.x);
+    for (int q = 0; q + 1 < n; q++)
+        for (int v = 1 + (int)threadIdx.x; v <= bt.g[q].N; v += blockDim.x) {
+            const int o = lay.tab[q] + 2 * (v - 1);
+            prolong_axis<T>(v, bt.g[q + 1], ix[o], ix[o + 1], wt[o], wt[o + 1]);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -2043,14 +2234,31 @@ cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const
 
 size_t mg_bottom_smem(int dim, bool fp32, const MgBottom &bt)
 {
-    size_t c = 0, plan = 0;
-    for (int q = 0; q < bt.nlev; q++) {
-        c += 2 * (size_t)cube(bt.g[q].E, dim);
-        plan += 2 * (size_t)(dim == 3 ? bottom_plan_count<3>(bt.g[q].N) : bottom_plan_count<2>(bt.g[q].N));
+    const BottomLayout lay(bt, dim);
+    return lay.t_elems(bt.nlev) * (fp32 ? 4 : 8) + lay.i_elems(bt.nlev) * sizeof(int);
+}
+
+size_t mg_bottom_plan_bytes(int dim, bool fp32, const MgBottom &bt)
+{
+    const BottomLayout lay(bt, dim);
+    const size_t nimg = 2 * (size_t)lay.plan[bt.nlev] + lay.tab[bt.nlev];
+    return nimg * ((fp32 ? 4 : 8) + sizeof(int));
+}
+
+cudaError_t mg_launch_bottom_plan(int dim, bool fp32, const MgBottom &bt, void *img, cudaStream_t s)
+{
+    if (dim == 3) {
+        if (fp32)
+            launch(k_bottom_plan<float, 3>, 1, kBottomThreads, 0, s, bt, (float *)img);
+        else
+            launch(k_bottom_plan<double, 3>, 1, kBottomThreads, 0, s, bt, (double *)img);
+    } else {
+        if (fp32)
+            launch(k_bottom_plan<float, 2>, 1, kBottomThreads, 0, s, bt, (float *)img);
+        else
+            launch(k_bottom_plan<double, 2>, 1, kBottomThreads, 0, s, bt, (double *)img);
     }
-    c += (size_t)cube(bt.g[0].N, dim);      // residual scratch of the first level
-    c += plan + 1;                          // plan diagonals and the zero
-    return c * (fp32 ? 4 : 8) + plan * sizeof(int);
+    return cudaGetLastError();
 }
 
 cudaError_t mg_bottom_prepare()
