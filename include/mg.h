@@ -111,6 +111,8 @@ typedef struct {
     int parent[MG_MAX_LEVELS];        /* tree = 1: parent patch of l > 0, < l */
 } mg_hierarchy_desc;
 
+#define MG_INNER_MAX 32   /* largest mg_options.inner_max */
+
 /* Solver options; mg_default_options fills the paper's choices. */
 typedef struct {
     int nu_pre;          /* Gauss-Seidel sweeps before restriction (paper: 2, Sec. 3) */
@@ -126,6 +128,12 @@ typedef struct {
     int interface;       /* MG_IFACE_BUFFER | MG_IFACE_FROZEN */
     int stop;            /* MG_STOP_RESIDUAL | MG_STOP_FORCE */
     void *stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
+    int inner_max;       /* MIXED under MG_STOP_RESIDUAL, 0..MG_INNER_MAX: 0 runs inner_cycles
+                            FP32 V-cycles in every defect-correction step; > 0 runs inner_cycles in
+                            the first step and lets each later step choose its count, 1..inner_max:
+                            the cycles that the per-cycle residual contraction of the step before
+                            predicts for reaching rel_tol (decided on the device, in the graph).
+                            Not part of the paper's method, whose V-cycles are all FP64. */
 } mg_options;
 
 /* Per (hierarchy, level) result of mg_solve. */
@@ -139,7 +147,7 @@ typedef struct {
 
 /* Fill *opt with nu_pre = 2, nu_post = 1 (Sec. 3), max_cycles = 50,
  * rel_tol = 1e-10, MG_FP64, inner_cycles = 3, MG_GUESS_INTERP, MG_FORCE_EQ2,
- * stream NULL.  Returns MG_EINVAL if opt is NULL. */
+ * stream NULL, inner_max = 0.  Returns MG_EINVAL if opt is NULL. */
 mg_status mg_default_options(mg_options *opt);
 
 /* Create `batch` independent hierarchies (Sec. 2.1 data structure) with

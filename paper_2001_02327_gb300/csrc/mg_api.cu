@@ -318,6 +318,7 @@ struct mg_hierarchy {
     char *batch_mem = nullptr;
     bool batched = false;
     cudaStream_t body_stream = nullptr;
+    cudaStream_t inner_stream = nullptr;   // captures the nested loop of an adaptive step
     cudaEvent_t ev_fork = nullptr, ev_join[MG_BRANCHES] = {};
 };
 
@@ -428,7 +429,8 @@ P *mapped_host_view(P *p)
 mg_status check_options(const mg_options &o)
 {
     if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 || !(o.rel_tol >= 0.0) ||
-        (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 ||
+        (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 || o.inner_max < 0 ||
+        o.inner_max > MG_INNER_MAX ||
         o.guess < MG_GUESS_INTERP || o.guess > MG_GUESS_LEARNED ||
         (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2) ||
         (o.interface != MG_IFACE_BUFFER && o.interface != MG_IFACE_FROZEN) ||
@@ -496,7 +498,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // --------------------------------------------------------------------------
 double cells_d(int N, int dim) { return dim == 3 ? (double)N * N * N : (double)N * N; }
 
-cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int sweeps, cudaStream_t s)
+// sweeps red-black sweeps on level L; ctl != NULL: the last launch also
+// counts one V-cycle of an adaptive step's nested loop (condition hi)
+cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int sweeps, cudaStream_t s,
+                   MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0)
 {
     const int dim = h->dim;
     const MgGeom &g = ld.g[L];
@@ -506,8 +511,10 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     for (int sw = 0; sw < sweeps; sw++)
         for (int c = 0; c < 2; c++) {
             // the finest multigrid level is profiled apart from the coarser ones
-            cudaError_t e = timed(h, L == 0 ? KK_SMOOTH0 : KK_SMOOTH, bytes,
-                                  [&] { return mg_launch_smooth(dim, fp32, phi, f, g, c, s); });
+            const bool last = sw == sweeps - 1 && c == 1;
+            cudaError_t e = timed(h, L == 0 ? KK_SMOOTH0 : KK_SMOOTH, bytes, [&] {
+                return mg_launch_smooth(dim, fp32, phi, f, g, c, s, last ? ctl : nullptr, hi);
+            });
             if (e)
                 return e;
         }
@@ -535,7 +542,11 @@ cudaError_t refresh_bottom_plan(mg_hierarchy *h, LevelData &ld)
 // the V-cycle of Sec. 2.3 (steps 2-13) on the arrays of one refinement level,
 // `ncyc` times; the levels from Lc down run in the cluster kernel (when
 // Lc < Ls), those from Ls down in the one-block kernel
-cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t s, int ncyc = 1)
+// ctl != NULL (one V-cycle of an adaptive step's nested loop): when the
+// cycle ends with a smoothing launch of level 0, that launch also counts the
+// cycle and sets the loop condition hi, and *counted is set.
+cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t s, int ncyc = 1,
+                   MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0, bool *counted = nullptr)
 {
     const int dim = h->dim;
     const mg_options &o = h->opt;
@@ -615,8 +626,11 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
         e = timed(h, KK_PROLONG, w * (nc + 2.0 * nf), [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
         if (e)
             return e;
-        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s)))
+        const bool fold = ctl && ncyc == 1 && L == 1 && o.nu_post > 0;
+        if ((e = smooth(h, ld, L - 1, fp32, o.nu_post, s, fold ? ctl : nullptr, hi)))
             return e;
+        if (fold && counted)
+            *counted = true;
     }
     }
     return cudaSuccess;
@@ -699,7 +713,58 @@ cudaError_t level_epilogue(mg_hierarchy *h, int b, int l, cudaStream_t s)
 // mixed precision an FP64 defect (already written by the previous residual
 // norm under the residual stopping rule), inner_cycles FP32 V-cycles on the
 // correction and its FP64 accumulation; then ||r||^2.
-cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int branch)
+// True when each mixed-precision step chooses its FP32 V-cycles (options
+// inner_max > 0, residual stopping rule).
+bool adaptive_inner(const mg_hierarchy *h)
+{
+    return h->opt.precision == MG_MIXED && h->opt.stop == MG_STOP_RESIDUAL && h->opt.inner_max > 0;
+}
+
+// The FP32 V-cycles of an adaptive step while s captures a graph: a nested
+// WHILE node whose body is one V-cycle and the kernel that counts it down
+// (ctl.left); its condition *hi starts at 1 and ctl_step re-arms it.
+cudaError_t capture_inner_loop(mg_hierarchy *h, const LevelData &ld, MgSolveCtl *ctl, cudaStream_t s,
+                               cudaGraphConditionalHandle *hi)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+    if (e)
+        return e;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    if ((e = cudaGraphConditionalHandleCreate(hi, g, 1, cudaGraphCondAssignDefault)))
+        return e;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = *hi;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &p)))
+        return e;
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)))
+        return e;
+    if (!h->inner_stream && (e = cudaStreamCreateWithFlags(&h->inner_stream, cudaStreamNonBlocking)))
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(h->inner_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+        return e;
+    bool counted = false;
+    cudaError_t eb = vcycle(h, ld, true, h->inner_stream, 1, ctl, *hi, &counted);
+    if (!eb && !counted)
+        eb = mg_launch_inner_step(ctl, *hi, h->inner_stream);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(h->inner_stream, &out);
+    return eb ? eb : e;
+}
+
+// One step of level l: ncyc V-cycles (FP32 in mixed mode, where hi != NULL
+// captures an adaptive step's nested loop instead), then the norms that
+// decide the next.
+cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int branch, int ncyc = -1,
+                            cudaGraphConditionalHandle *hi = nullptr)
 {
     const LevelData &ld = h->lev[b][l];
     const int dim = h->dim;
@@ -721,7 +786,11 @@ cudaError_t level_iteration(mg_hierarchy *h, int b, int l, cudaStream_t s, int b
             if (e)
                 return e;
         }
-        if ((e = vcycle(h, ld, true, s, o.inner_cycles)))
+        if (hi)
+            e = capture_inner_loop(h, ld, level_ctl(h, b, l), s, hi);
+        else
+            e = vcycle(h, ld, true, s, ncyc > 0 ? ncyc : o.inner_cycles);
+        if (e)
             return e;
         e = timed(h, KK_ACCUM, 20.0 * nd, [&] { return mg_launch_accumulate(dim, ld.phi[0], ld.phi32[0], ld.g[0], s); });
         if (e)
@@ -762,15 +831,21 @@ mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
     c.rel = c.bnorm > 0.0 ? std::sqrt(hs[1]) / c.bnorm : 0.0;
     if (!std::isfinite(c.bnorm))
         c.status = 1;
+    const bool adapt = adaptive_inner(h);
+    int inner = o.inner_cycles;   // adaptive: FP32 V-cycles of the next step, as the graph's ctl kernels choose
     while (c.bnorm > 0.0 && c.status == 0 && c.cycles < o.max_cycles && !(c.rel < o.rel_tol)) {
-        CK(h, level_iteration(h, b, l, s, 0));
+        const int ncyc = adapt ? std::min(inner, o.max_cycles - c.cycles) : cycles_per_iteration(h);
+        CK(h, level_iteration(h, b, l, s, 0, ncyc));
         CK(h, cudaMemcpyAsync(hs, ds, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(h, cudaStreamSynchronize(s));
-        c.cycles += cycles_per_iteration(h);
+        const double before = c.rel;
+        c.cycles += ncyc;
         c.outer++;
         c.rel = std::sqrt(hs[1]) / c.bnorm;
         if (!std::isfinite(c.rel))
             c.status = 1;
+        if (adapt)
+            inner = mg_next_inner(before, c.rel, ncyc, o.rel_tol, o.inner_max);
     }
     CK(h, level_epilogue(h, b, l, s));
     fill_stats(h, c, st);
@@ -816,7 +891,8 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
         return e;
     if ((e = level_prelude(h, b, l, s, branch)))
         return e;
-    if ((e = mg_launch_ctl_init(level_ctl(h, b, l), level_scal(h, b, l), o.rel_tol, o.max_cycles, hc, s)))
+    if ((e = mg_launch_ctl_init(level_ctl(h, b, l), level_scal(h, b, l), o.rel_tol, o.max_cycles, o.inner_cycles,
+                                hc, s)))
         return e;
     const cudaGraphNode_t *deps = nullptr;
     size_t nd = 0;
@@ -836,10 +912,12 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
         return e;
     if ((e = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
         return e;
-    cudaError_t eb = level_iteration(h, b, l, h->body_stream, branch);
+    const bool adapt = adaptive_inner(h);
+    cudaGraphConditionalHandle hi = 0;
+    cudaError_t eb = level_iteration(h, b, l, h->body_stream, branch, -1, adapt ? &hi : nullptr);
     if (!eb)
-        eb = mg_launch_ctl_step(level_ctl(h, b, l), level_scal(h, b, l), cycles_per_iteration(h), o.rel_tol,
-                                o.max_cycles, hc, h->body_stream);
+        eb = mg_launch_ctl_step(level_ctl(h, b, l), level_scal(h, b, l), adapt ? 0 : cycles_per_iteration(h),
+                                o.rel_tol, o.max_cycles, adapt ? o.inner_max : 0, hc, hi, h->body_stream);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(h->body_stream, &out);
     if (eb || e)
@@ -1415,6 +1493,7 @@ mg_status mg_default_options(mg_options *opt)
     opt->rel_tol = 1e-10;
     opt->precision = MG_FP64;
     opt->inner_cycles = 3;
+    opt->inner_max = 0;
     opt->guess = MG_GUESS_INTERP;
     opt->force_stencil = MG_FORCE_EQ2;
     opt->interface = MG_IFACE_BUFFER;
@@ -1948,6 +2027,8 @@ mg_status mg_destroy(mg_hierarchy *h)
     }
     if (h->body_stream)
         cudaStreamDestroy(h->body_stream);
+    if (h->inner_stream)
+        cudaStreamDestroy(h->inner_stream);
     if (h->ev_fork)
         cudaEventDestroy(h->ev_fork);
     if (h->hscal)

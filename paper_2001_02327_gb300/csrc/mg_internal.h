@@ -69,9 +69,12 @@ inline void mg_fill_diag_table(const MgGeom &g, int dim, double *tab)
 // geometry is the same.  All launches go to stream s and return the launch
 // error (cudaGetLastError).
 // ---------------------------------------------------------------------------
-// One colour (0 = red, (i+j[+k]) even; 1 = black) of a Gauss-Seidel sweep.
+struct MgSolveCtl;
+// One colour (0 = red, (i+j[+k]) even; 1 = black) of a Gauss-Seidel sweep;
+// ctl != NULL: the launch also counts one V-cycle of an adaptive step's
+// nested loop (ctl->cycles, ctl->left) and sets that loop's condition hi.
 cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int colour,
-                             cudaStream_t s);
+                             cudaStream_t s, MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0);
 // The levels at and below a multigrid level Ls, run by one thread block with
 // all their arrays in shared memory (k_bottom).
 #define MG_BOTTOM_MAX 12
@@ -204,15 +207,43 @@ struct MgSolveCtl {
     int go;          // last value given to the loop condition
     double rel;      // ||r|| / ||b||
     double bnorm;    // ||b||
+    int inner;       // adaptive mixed mode: FP32 V-cycles of the current step
+    int left;        //   of them not run yet
+    int cyc0;        //   cycles when the current step began
 };
+
+// Adaptive mixed mode: FP32 V-cycles of the next defect-correction step.
+// The last step took the relative residual from rel_before to rel_after in
+// `ran` V-cycles; at that per-cycle contraction, the cycles still needed to
+// reach tol, between 1 and inner_max (inner_max when the step did not
+// contract or there is no tolerance to aim at).
+__host__ __device__ inline int mg_next_inner(double rel_before, double rel_after, int ran, double tol, int inner_max)
+{
+    if (!(tol > 0.0) || !(rel_after > 0.0) || !(rel_after < rel_before) || ran < 1)
+        return inner_max;
+    if (rel_after < tol)
+        return 1;
+    const double per_cycle = log(rel_after / rel_before) / ran;   // < 0
+    const double need = log(tol / rel_after) / per_cycle;          // > 0
+    if (!(need < inner_max))
+        return inner_max;
+    const int k = (int)ceil(need);
+    return k < 1 ? 1 : k;
+}
 
 // ctl_init: from scal = {||b||^2, ||r||^2} start the counters and set the
 // loop condition (handle) to 1 iff another iteration is needed.
 // ctl_step: after one iteration of `inc` V-cycles, with scal[1] = ||r||^2.
-cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
+// inner0 / inner_max: first step's FP32 V-cycles and the adaptive cap
+// (inner_max 0: fixed steps of `inc` cycles, counted by ctl_step; > 0: the
+// nested loop of the step counts its cycles in inner_step, ctl_step sets the
+// next step's count and re-arms that loop's condition hi).
+cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles, int inner0,
                                cudaGraphConditionalHandle hc, cudaStream_t s);
 cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
-                               cudaGraphConditionalHandle hc, cudaStream_t s);
+                               int inner_max, cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hi,
+                               cudaStream_t s);
+cudaError_t mg_launch_inner_step(MgSolveCtl *ctl, cudaGraphConditionalHandle hi, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batched mixed-precision solve: one launch per phase over every hierarchy

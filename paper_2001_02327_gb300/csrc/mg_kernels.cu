@@ -393,11 +393,36 @@ __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const Mg
 __device__ __forceinline__ int gtid() { return blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int gstride() { return gridDim.x * blockDim.x; }
 
+// One FP32 V-cycle of an adaptive defect-correction step done (the step's
+// nested graph loop): count it and let the loop go on while cycles are left.
+// One thread.
+__device__ __forceinline__ void inner_step_count(MgSolveCtl *ctl, cudaGraphConditionalHandle hi)
+{
+    MgSolveCtl c = *ctl;
+    c.cycles += 1;
+    c.left -= 1;
+    *ctl = c;
+    cudaGraphSetConditional(hi, c.left > 0);
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
                                                             int colour)
 {
     pdl_begin();
+    op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
+}
+
+// The same colour, when it is the last launch of a V-cycle in an adaptive
+// step's nested loop: one thread also counts the cycle (inner_step_count).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_smooth_colour_counted(T *__restrict__ phi, const T *__restrict__ f,
+                                                                    MgGeom g, int colour, MgSolveCtl *ctl,
+                                                                    cudaGraphConditionalHandle hi)
+{
+    pdl_begin();
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        inner_step_count(ctl, hi);
     op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
 }
 
@@ -1870,7 +1895,7 @@ __device__ __forceinline__ int keep_going(const MgSolveCtl &c, double tol, int m
     return c.bnorm > 0.0 && c.status == 0 && c.cycles < max_cycles && !(c.rel < tol);
 }
 
-__global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
+__global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles, int inner0,
                            cudaGraphConditionalHandle hc)
 {
     pdl_begin();
@@ -1880,24 +1905,43 @@ __global__ void k_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int 
     c.cycles = 0;
     c.outer = 0;
     c.status = isfinite(c.bnorm) ? 0 : 6;   // non-finite input: diverged, not "nothing to do"
+    c.inner = inner0;
+    c.left = min(inner0, max_cycles);
+    c.cyc0 = 0;
     c.go = keep_going(c, tol, max_cycles);
     *ctl = c;
     cudaGraphSetConditional(hc, c.go);
 }
 
-__global__ void k_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
-                           cudaGraphConditionalHandle hc)
+__global__ void k_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles, int inner_max,
+                           cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hi)
 {
     pdl_begin();
     MgSolveCtl c = *ctl;
+    const double before = c.rel;
     c.cycles += inc;
     c.outer += 1;
     c.rel = sqrt(scal[1]) / c.bnorm;
     if (!isfinite(c.rel))
         c.status = 6;
+    if (inner_max > 0) {
+        c.inner = mg_next_inner(before, c.rel, c.cycles - c.cyc0, tol, inner_max);
+        c.left = min(c.inner, max_cycles - c.cycles);
+        c.cyc0 = c.cycles;
+    }
     c.go = keep_going(c, tol, max_cycles);
     *ctl = c;
     cudaGraphSetConditional(hc, c.go);
+    if (inner_max > 0)
+        cudaGraphSetConditional(hi, 1);   // the next step's nested loop runs at least once
+}
+
+// end of one FP32 V-cycle of an adaptive step's nested loop (when the
+// V-cycle's last launch is not a smoothing colour that counts it)
+__global__ void k_inner_step(MgSolveCtl *ctl, cudaGraphConditionalHandle hi)
+{
+    pdl_begin();
+    inner_step_count(ctl, hi);
 }
 
 
@@ -2214,10 +2258,24 @@ static void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int c, cudaStream_t s)
+cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int c, cudaStream_t s,
+                             MgSolveCtl *ctl, cudaGraphConditionalHandle hi)
 {
     const long work = (long)((g.N + 1) / 2) * g.N * (dim == 3 ? g.N : 1);
     const int grid = grid_for(work);
+    if (ctl) {
+        if (dim == 3 && fp32)
+            launch(k_smooth_colour_counted<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c, ctl, hi);
+        else if (dim == 3)
+            launch(k_smooth_colour_counted<double, 3>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c, ctl,
+                   hi);
+        else if (fp32)
+            launch(k_smooth_colour_counted<float, 2>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c, ctl, hi);
+        else
+            launch(k_smooth_colour_counted<double, 2>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c, ctl,
+                   hi);
+        return cudaGetLastError();
+    }
     if (dim == 3) {
         if (fp32)
             launch(k_smooth_colour<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
@@ -2573,17 +2631,24 @@ cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const doub
     return cudaGetLastError();
 }
 
-cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles,
+cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles, int inner0,
                                cudaGraphConditionalHandle hc, cudaStream_t s)
 {
-    launch(k_ctl_init, 1, 1, 0, s, ctl, scal, tol, max_cycles, hc);
+    launch(k_ctl_init, 1, 1, 0, s, ctl, scal, tol, max_cycles, inner0, hc);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, double tol, int max_cycles,
-                               cudaGraphConditionalHandle hc, cudaStream_t s)
+                               int inner_max, cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hi,
+                               cudaStream_t s)
 {
-    launch(k_ctl_step, 1, 1, 0, s, ctl, scal, inc, tol, max_cycles, hc);
+    launch(k_ctl_step, 1, 1, 0, s, ctl, scal, inc, tol, max_cycles, inner_max, hc, hi);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_inner_step(MgSolveCtl *ctl, cudaGraphConditionalHandle hi, cudaStream_t s)
+{
+    launch(k_inner_step, 1, 1, 0, s, ctl, hi);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ class mg_options(C.Structure):
     _fields_ = [("nu_pre", C.c_int), ("nu_post", C.c_int), ("max_cycles", C.c_int), ("rel_tol", C.c_double),
                 ("precision", C.c_int), ("inner_cycles", C.c_int), ("guess", C.c_int),
                 ("force_stencil", C.c_int), ("interface", C.c_int),
-                ("stop", C.c_int), ("stream", C.c_void_p)]
+                ("stop", C.c_int), ("stream", C.c_void_p), ("inner_max", C.c_int)]
 
 
 class mg_level_stats(C.Structure):

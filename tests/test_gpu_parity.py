@@ -456,6 +456,62 @@ def test_graph_path_equals_host_loop(mg):
         assert ca == cb and np.array_equal(a, b)
 
 
+def _solve_with(mg, H, inp, prof, **kw):
+    """Solve on the GPU with the graph (prof False) or the host-driven loop
+    (prof True); per level the potential, the stats and (host loop) the
+    one-block kernel's launch count."""
+    import torch
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(**kw))
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+        for l in range(1, H.num_levels):
+            mg.mg_set_density(h, 0, l, dev(inp[l]["rho"]))
+        mg.mg_profile(h, prof)
+        status, st = mg.mg_solve(h, 1, allow_noconv=True)
+        bottoms = mg.mg_profile_read(h).get("bottom", (0,))[0] if prof else None
+        out = []
+        for l in range(H.num_levels):
+            phi = torch.zeros((H.n[l],) * H.dim, dtype=torch.float64, device="cuda")
+            F = torch.zeros((H.dim,) + (H.n[l],) * H.dim, dtype=torch.float64, device="cuda")
+            mg.mg_forces(h, 0, l, phi, F)
+            torch.cuda.synchronize()
+            out.append((phi.cpu().numpy(), F.cpu().numpy(), dict(st[0][l])))
+        return status, out, bottoms
+    finally:
+        mg.mg_destroy(h)
+
+
+@pytest.mark.parametrize("make", [lambda: I.config_3d_offset_sphere(64, 4), lambda: I.random_hierarchy(11),
+                                  lambda: I.config_2d_disk(64, 3)])
+def test_adaptive_inner_cycles(mg, make):
+    """Mixed precision with each defect-correction step choosing its FP32
+    V-cycles (inner_max > 0): converges to the tolerance, stays within the
+    mixed form's bar against FP64, counts exactly the V-cycles it ran (one
+    one-block launch per V-cycle), takes no more outer steps than fixed steps
+    of inner_cycles, and the graph's device-side choices equal the host
+    loop's."""
+    H = make()
+    inp = I.level_inputs(H)
+    kw = dict(nu_pre=2, nu_post=2, max_cycles=60, rel_tol=1e-10, precision=mg.MG_MIXED, inner_cycles=3)
+    s64, r64, _ = _solve_with(mg, H, inp, False, **dict(kw, precision=mg.MG_FP64))
+    sfx, rfx, _ = _solve_with(mg, H, inp, False, **kw)
+    sg, rg, _ = _solve_with(mg, H, inp, False, inner_max=6, **kw)
+    sh, rh, bottoms = _solve_with(mg, H, inp, True, inner_max=6, **kw)
+    assert s64 == sfx == sg == sh == mg.MG_OK
+    X = [H.centres(l, 0) for l in range(H.num_levels)]
+    for l in range(H.num_levels):
+        phi, F, st = rg[l]
+        assert st["rel_res"] < 1e-10, (l, st)
+        assert st["outer_steps"] <= rfx[l][2]["outer_steps"], (l, st, rfx[l][2])
+        disc = np.max(np.abs(r64[l][0] - H.potential(X[l])))
+        assert np.max(np.abs(phi - r64[l][0])) < 1e-2 * disc, l
+        assert relmax(phi, r64[l][0]) < 1e-7 and relmax(F, r64[l][1]) < 1e-7, l
+        assert np.array_equal(phi, rh[l][0]) and np.array_equal(F, rh[l][1]), l
+        assert st["cycles"] == rh[l][2]["cycles"] and st["outer_steps"] == rh[l][2]["outer_steps"], l
+    assert bottoms == sum(rh[l][2]["cycles"] for l in range(H.num_levels))
+
+
 def test_heterogeneous_batch(mg):
     """Uneven hierarchies solved together (parallel branches of the solve
     graph) give the same results as each solved alone."""
