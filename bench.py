@@ -509,7 +509,8 @@ def run_batch_case(args):
     from paper_2001_02327_gb300 import mg
     Hs = [I.random_hierarchy(I.BASE_SEED + b) for b in range(args.batch)]
     zones = sum(H.zones() for H in Hs)
-    opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED, inner_cycles=3)
+    opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED, inner_cycles=3,
+                     inner_max=args.inner_max)
     h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], opt)
     try:
         if args.autotune:
@@ -577,7 +578,8 @@ def run_scale_case(args):
     P = [torch.empty((m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
     for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
         h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60,
-                                                                 rel_tol=TOL, precision=prec, inner_cycles=3))
+                                                                 rel_tol=TOL, precision=prec, inner_cycles=3,
+                                                                 inner_max=args.inner_max))
         try:
             if prec == mg.MG_MIXED:
                 mg.mg_autotune(h, args.tune_cache)
@@ -683,7 +685,8 @@ def run_2d_case(args):
         F = [torch.empty((2, n, n), dtype=torch.float64, device="cuda") for n in H.n]
         for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
             h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=nu[0], nu_post=nu[1], max_cycles=60,
-                                                                     rel_tol=TOL, precision=prec, inner_cycles=3))
+                                                                     rel_tol=TOL, precision=prec, inner_cycles=3,
+                                                                     inner_max=args.inner_max))
             try:
                 if prec == mg.MG_MIXED:
                     mg.mg_autotune(h, args.tune_cache)

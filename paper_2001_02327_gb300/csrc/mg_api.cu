@@ -1217,7 +1217,7 @@ mg_status build_graph(mg_hierarchy *h)
     }
     h->batched = false;
     if (h->opt.precision == MG_MIXED && h->batch > 1 && h->opt.interface == MG_IFACE_BUFFER &&
-        h->opt.stop == MG_STOP_RESIDUAL) {
+        h->opt.stop == MG_STOP_RESIDUAL && h->opt.inner_max == 0) {   // the batched kernels run fixed steps
         // measured on 64 uneven hierarchies: graph branches 105 ms, batched
         // launches 143 ms (each batched block first loads its part's
         // descriptor); MG_BATCHED=1 selects the batched launches
