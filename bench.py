@@ -115,12 +115,13 @@ class ClockSampler:
 class Runner:
     """One hierarchy resident on the GPU plus its inputs and outputs."""
 
-    def __init__(self, mg, torch, H, inp, stream, precision, tune_cache=None, unet=None, autotune=True, inner_max=0):
+    def __init__(self, mg, torch, H, inp, stream, precision, tune_cache=None, unet=None, autotune=True, inner_max=0,
+                 inner_cycles=3):
         self.mg, self.torch, self.H = mg, torch, H
         self.stream = stream
         guess = mg.MG_GUESS_LEARNED if unet is not None else mg.MG_GUESS_INTERP
         self.opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=precision,
-                              inner_cycles=3, inner_max=inner_max, guess=guess, stream=stream)
+                              inner_cycles=inner_cycles, inner_max=inner_max, guess=guess, stream=stream)
         self.h = mg.mg_create_hierarchy([mg.desc_from(H)], self.opt)
         if unet is not None:
             from paper_2001_02327_gb300 import unet as U
@@ -290,7 +291,8 @@ def run_ours(args):
         net = train_guess_network(torch)
         plans.append(("mixed_learned", mg.MG_MIXED, net))
     for name, prec, unet in plans:
-        r = Runner(mg, torch, H, inp, stream, prec, args.tune_cache, unet, not args.no_autotune, args.inner_max)
+        r = Runner(mg, torch, H, inp, stream, prec, args.tune_cache, unet, not args.no_autotune, args.inner_max,
+                   args.inner_cycles)
         try:
             # the first solve of each form carries an NVTX range, so that a
             # profiler can select exactly one solve's launches
@@ -369,8 +371,8 @@ def run_ours(args):
                    "nu": list(NU), "rel_tol": TOL, "form": best, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}",
                    "launch_plan": "default" if args.no_autotune else "mg_autotune (timed at setup)",
-                   "mixed_inner_cycles": f"3, then chosen per step up to {args.inner_max}" if args.inner_max
-                   else "3 per step"},
+                   "mixed_inner_cycles": f"{args.inner_cycles}, then chosen per step up to {args.inner_max}"
+                   if args.inner_max else f"{args.inner_cycles} per step"},
         "forms": {k: {"zones_per_s": v["value"], "ms_per_step": v["ms_per_step"], "cycles_per_level": v["cycles"],
                       "kernels": {kk: {"launches": round(vv[0], 1), "ms": round(vv[1], 4)} for kk, vv in v["prof"].items()}}
                   for k, v in forms.items()},
@@ -509,8 +511,8 @@ def run_batch_case(args):
     from paper_2001_02327_gb300 import mg
     Hs = [I.random_hierarchy(I.BASE_SEED + b) for b in range(args.batch)]
     zones = sum(H.zones() for H in Hs)
-    opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED, inner_cycles=3,
-                     inner_max=args.inner_max)
+    opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED,
+                     inner_cycles=args.inner_cycles, inner_max=args.inner_max)
     h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], opt)
     try:
         if args.autotune:
@@ -578,7 +580,8 @@ def run_scale_case(args):
     P = [torch.empty((m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
     for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
         h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60,
-                                                                 rel_tol=TOL, precision=prec, inner_cycles=3,
+                                                                 rel_tol=TOL, precision=prec,
+                                                                 inner_cycles=args.inner_cycles,
                                                                  inner_max=args.inner_max))
         try:
             if prec == mg.MG_MIXED:
@@ -685,7 +688,8 @@ def run_2d_case(args):
         F = [torch.empty((2, n, n), dtype=torch.float64, device="cuda") for n in H.n]
         for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
             h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=nu[0], nu_post=nu[1], max_cycles=60,
-                                                                     rel_tol=TOL, precision=prec, inner_cycles=3,
+                                                                     rel_tol=TOL, precision=prec,
+                                                                     inner_cycles=args.inner_cycles,
                                                                      inner_max=args.inner_max))
             try:
                 if prec == mg.MG_MIXED:
@@ -767,6 +771,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="leave out the mixed + learned-guess form")
+    ap.add_argument("--inner-cycles", type=int, default=3,
+                    help="mixed forms: FP32 V-cycles of the first defect-correction step (of every step "
+                         "with --inner-max 0)")
     ap.add_argument("--inner-max", type=int, default=8,
                     help="mixed forms: cap of the FP32 V-cycles each defect-correction step after the first "
                          "may choose (0: three in every step)")
