@@ -139,9 +139,23 @@ class Runner:
         self.h_phi = [torch.zeros((n,) * 3, dtype=torch.float64).pin_memory().numpy() for n in H.n]
         self.h_F = [torch.zeros((3,) + (n,) * 3, dtype=torch.float64).pin_memory().numpy() for n in H.n]
         self.stats = None
+        self.outputs(False)
+
+    def outputs(self, host):
+        """Where mg_solve writes each level's potential and forces: the device
+        arrays or the page-locked host arrays (a change rebuilds the solve
+        graph once, at the next solve)."""
+        phi, F = (self.h_phi, self.h_F) if host else (self.d_phi, self.d_F)
+        for l in range(self.H.num_levels):
+            self.mg.mg_set_outputs(self.h, 0, l, phi[l], F[l])
+        self.out_host = host
 
     def step(self, host=False):
+        """One step: the inputs into the hierarchy, the solve, which also
+        writes every level's potential and forces (Eq. 2) to the outputs."""
         mg = self.mg
+        if host != self.out_host:
+            self.outputs(host)
         src = self.h_in if host else self.d_in
         for l in range(self.H.num_levels):
             if l == 0:
@@ -149,11 +163,6 @@ class Runner:
             else:
                 mg.mg_set_density(self.h, 0, l, src[l]["rho"])
         _, self.stats = mg.mg_solve(self.h, 1)
-        for l in range(self.H.num_levels):
-            if host:
-                mg.mg_forces(self.h, 0, l, self.h_phi[l], self.h_F[l])
-            else:
-                mg.mg_forces(self.h, 0, l, self.d_phi[l], self.d_F[l])
 
     def io_bytes(self):
         h2d = sum(a.nbytes for d in self.h_in for a in d.values())
@@ -197,6 +206,7 @@ def time_device(runner, torch, steps, warmup, flush):
 
 
 def time_e2e(runner, torch, steps):
+    runner.step(host=True)          # untimed: switches the outputs to the host arrays
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):

@@ -196,6 +196,17 @@ mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats);
  * Errors: MG_EINVAL, MG_ESTATE (no solve yet), MG_ECUDA. */
 mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out);
 
+/* Register where mg_solve itself writes the results of hierarchy b on
+ * `level` (the values mg_forces would give, same layouts): F_out (required
+ * for phi_out) and phi_out, each device memory or page-locked host memory
+ * (written in place); NULL, NULL unregisters.  mg_solve then computes them
+ * as soon as the level has converged, beside the solves of the levels after
+ * it, and returns with them complete.  The pointers are kept until changed
+ * (a change rebuilds the solve graph once).  Not part of the paper: the
+ * results of Sec. 2 (Eq. 2) without a call per level.  Errors: MG_EINVAL
+ * (range, phi without F, pageable host memory). */
+mg_status mg_set_outputs(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out);
+
 /* Release everything; NULL-safe; always MG_OK. */
 mg_status mg_destroy(mg_hierarchy *h);
 

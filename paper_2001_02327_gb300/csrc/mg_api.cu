@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -51,6 +52,9 @@ struct LevelData {
     // V-cycles run in, sized for the largest bottom the level admits
     void *bplan = nullptr;
     size_t bplan_bytes = 0;
+    // outputs mg_solve writes once the level has converged (mg_set_outputs):
+    // device pointers or device views of page-locked host arrays
+    double *out_F = nullptr, *out_phi = nullptr;
 };
 
 // Largest multigrid level (cells per edge) given to the one-block bottom
@@ -320,6 +324,11 @@ struct mg_hierarchy {
     cudaStream_t body_stream = nullptr;
     cudaStream_t inner_stream = nullptr;   // captures the nested loop of an adaptive step
     cudaEvent_t ev_fork = nullptr, ev_join[MG_BRANCHES] = {};
+    // registered outputs: per branch a side stream that writes them while the
+    // next levels solve
+    cudaStream_t side[MG_BRANCHES] = {};
+    cudaEvent_t ev_side = nullptr, ev_side_join[MG_BRANCHES] = {};
+    bool side_used[MG_BRANCHES] = {};
 };
 
 namespace {
@@ -815,6 +824,19 @@ void fill_stats(const mg_hierarchy *h, const MgSolveCtl &c, mg_level_stats *st)
     st->status = status;
 }
 
+// Potential and forces (Eq. 2) of a converged level into its registered
+// outputs, on stream s.
+cudaError_t launch_outputs(mg_hierarchy *h, const LevelData &ld, cudaStream_t s)
+{
+    if (!ld.out_F)
+        return cudaSuccess;
+    const int dim = h->dim;
+    const double nr = cells_d(ld.n, dim);
+    return timed(h, KK_FORCES, 8.0 * (cells_d(ld.n + 4, dim) + (dim + 1) * nr), [&] {
+        return mg_launch_forces(dim, ld.n, ld.h, ld.blk, ld.out_F, ld.out_phi, h->opt.force_stencil, s);
+    });
+}
+
 // Host-driven loop (used while per-kernel profiling is on): the same
 // launches as the graph, with the loop decision taken on the host.
 mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
@@ -848,6 +870,7 @@ mg_status solve_level_host(mg_hierarchy *h, int b, int l, mg_level_stats *st)
             inner = mg_next_inner(before, c.rel, ncyc, o.rel_tol, o.inner_max);
     }
     CK(h, level_epilogue(h, b, l, s));
+    CK(h, launch_outputs(h, h->lev[b][l], s));
     fill_stats(h, c, st);
     return (mg_status)st->status;
 }
@@ -873,8 +896,14 @@ std::vector<char> graph_signature(const mg_hierarchy *h)
     std::vector<char> sig;
     sig.push_back(h->unet ? 1 : 0);
     for (const auto &hl : h->lev)
-        for (const auto &ld : hl)
+        for (const auto &ld : hl) {
             sig.push_back(ld.guess_set ? 1 : 0);
+            for (const double *p : {ld.out_F, ld.out_phi}) {
+                const uintptr_t v = (uintptr_t)p;
+                for (size_t k = 0; k < sizeof v; k++)
+                    sig.push_back((char)(v >> (8 * k)));
+            }
+        }
     return sig;
 }
 
@@ -922,7 +951,17 @@ cudaError_t capture_level(mg_hierarchy *h, int b, int l, cudaStream_t s, int bra
     e = cudaStreamEndCapture(h->body_stream, &out);
     if (eb || e)
         return eb ? eb : e;
-    return level_epilogue(h, b, l, s);
+    if ((e = level_epilogue(h, b, l, s)))
+        return e;
+    const LevelData &ld = h->lev[b][l];
+    if (!ld.out_F)
+        return cudaSuccess;
+    // the outputs on the branch's side stream, beside the next levels' solves
+    // (which only read this level's potential)
+    if ((e = cudaEventRecord(h->ev_side, s)) || (e = cudaStreamWaitEvent(h->side[branch], h->ev_side, 0)))
+        return e;
+    h->side_used[branch] = true;
+    return launch_outputs(h, ld, h->side[branch]);
 }
 
 // Plan of the batched mixed-precision solve: per refinement level the parts
@@ -1215,6 +1254,16 @@ mg_status build_graph(mg_hierarchy *h)
         for (int i = 0; i < MG_BRANCHES; i++)
             CK(h, cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
     }
+    if (!h->ev_side) {
+        CK(h, cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming));
+        for (int i = 0; i < MG_BRANCHES; i++)
+            CK(h, cudaEventCreateWithFlags(&h->ev_side_join[i], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < nbr; i++) {
+        if (!h->side[i])
+            CK(h, cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
+        h->side_used[i] = false;
+    }
     h->batched = false;
     if (h->opt.precision == MG_MIXED && h->batch > 1 && h->opt.interface == MG_IFACE_BUFFER &&
         h->opt.stop == MG_STOP_RESIDUAL && h->opt.inner_max == 0) {   // the batched kernels run fixed steps
@@ -1234,6 +1283,9 @@ mg_status build_graph(mg_hierarchy *h)
         cudaError_t e = cudaSuccess;
         for (int l = 0; l < (int)h->bl.size() && !e; l++)
             e = capture_batched_level(h, l, h->cap[0], h->body_stream);
+        for (int b = 0; b < h->batch && !e; b++)       // registered outputs, after the batched solve
+            for (int l = 0; l < h->desc[b].num_levels && !e; l++)
+                e = launch_outputs(h, h->lev[b][l], h->cap[0]);
         cudaGraph_t g = nullptr;
         cudaError_t ee = cudaStreamEndCapture(h->cap[0], &g);
         if (e || ee) {
@@ -1258,6 +1310,12 @@ mg_status build_graph(mg_hierarchy *h)
         if (!e)
             e = cudaStreamWaitEvent(h->cap[0], h->ev_join[i], 0);
     }
+    for (int i = 0; i < nbr && !e; i++)
+        if (h->side_used[i]) {
+            e = cudaEventRecord(h->ev_side_join[i], h->side[i]);
+            if (!e)
+                e = cudaStreamWaitEvent(h->cap[0], h->ev_side_join[i], 0);
+        }
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(h->cap[0], &g);
     if (e || ee) {
@@ -1815,9 +1873,36 @@ mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats)
                 if (s == MG_EDIVERGED || (s == MG_ENOCONV && worst == MG_OK))
                     worst = s;
             }
+        CK(h, cudaStreamSynchronize(h->stream));   // registered outputs complete on return
     }
     h->solved = true;
     return worst;
+}
+
+mg_status mg_set_outputs(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out)
+{
+    if (!h)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (b < 0 || b >= h->batch || level < 0 || level >= h->desc[b].num_levels)
+        return fail(h, MG_EINVAL, "hierarchy %d level %d out of range", b, level);
+    if (!F_out && phi_out)
+        return fail(h, MG_EINVAL, "a potential output needs a force output");
+    auto usable = [](double *p) -> double * {
+        if (!p)
+            return nullptr;
+        if (is_device_ptr(p))
+            return p;
+        return mapped_host_view(p);   // page-locked host memory, else NULL
+    };
+    double *F = usable(F_out), *P = usable(phi_out);
+    if ((F_out && !F) || (phi_out && !P))
+        return fail(h, MG_EINVAL, "outputs must be device memory or page-locked host memory");
+    LevelData &ld = h->lev[b][level];
+    ld.out_F = F;
+    ld.out_phi = P;
+    return MG_OK;
 }
 
 mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out)
@@ -2029,6 +2114,14 @@ mg_status mg_destroy(mg_hierarchy *h)
         cudaStreamDestroy(h->body_stream);
     if (h->inner_stream)
         cudaStreamDestroy(h->inner_stream);
+    for (int i = 0; i < MG_BRANCHES; i++) {
+        if (h->side[i])
+            cudaStreamDestroy(h->side[i]);
+        if (h->ev_side_join[i])
+            cudaEventDestroy(h->ev_side_join[i]);
+    }
+    if (h->ev_side)
+        cudaEventDestroy(h->ev_side);
     if (h->ev_fork)
         cudaEventDestroy(h->ev_fork);
     if (h->hscal)

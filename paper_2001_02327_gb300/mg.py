@@ -54,6 +54,7 @@ _SIGS = {
     "mg_set_guess": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
     "mg_solve": (C.c_int, [_vp, C.POINTER(mg_level_stats)]),
     "mg_forces": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
+    "mg_set_outputs": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
     "mg_destroy": (C.c_int, [_vp]),
     "mg_status_str": (C.c_char_p, [C.c_int]),
     "mg_error_message": (C.c_char_p, [_vp]),
@@ -165,6 +166,12 @@ def mg_solve(h, batch, allow_noconv=False):
 
 def mg_forces(h, b, level, phi_out=None, F_out=None):
     return _check(h, LIB.mg_forces(h, b, level, _addr(phi_out), _addr(F_out)))
+
+
+def mg_set_outputs(h, b, level, phi_out=None, F_out=None):
+    """Arrays (device or page-locked host) that mg_solve fills with the
+    level's potential and forces; None, None unregisters."""
+    return _check(h, LIB.mg_set_outputs(h, b, level, _addr(phi_out), _addr(F_out)))
 
 
 def mg_profile(h, enable):

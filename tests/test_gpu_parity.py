@@ -512,6 +512,62 @@ def test_adaptive_inner_cycles(mg, make):
     assert bottoms == sum(rh[l][2]["cycles"] for l in range(H.num_levels))
 
 
+@pytest.mark.parametrize("prof", [False, True])
+def test_registered_outputs_equal_mg_forces(mg, prof):
+    """mg_solve writes the registered outputs (device and page-locked host,
+    potential with forces or forces alone) with the values mg_forces gives,
+    in the solve graph (two hierarchies as branches) and in the host-driven
+    loop; an unregistered level is left alone; pageable host memory and a
+    potential without forces are refused."""
+    import torch
+    Hs = [I.config_3d_offset_sphere(32, 3), I.random_hierarchy(4)]
+    h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], mg.options(nu_pre=2, nu_post=2))
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        for b, H in enumerate(Hs):
+            inp = I.level_inputs(H)
+            mg.mg_set_density(h, b, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            for l in range(1, H.num_levels):
+                mg.mg_set_density(h, b, l, dev(inp[l]["rho"]))
+        shp = lambda H, l: ((H.n[l],) * 3, (3,) + (H.n[l],) * 3)
+        outs = {}
+        for b, H in enumerate(Hs):
+            for l in range(H.num_levels):
+                ps, fs = shp(H, l)
+                if (b, l) == (0, 1):                      # page-locked host
+                    P = torch.full(ps, 7.0, dtype=torch.float64).pin_memory()
+                    F = torch.full(fs, 7.0, dtype=torch.float64).pin_memory()
+                elif (b, l) == (0, 2):                    # forces alone
+                    P, F = None, torch.full(fs, 7.0, dtype=torch.float64, device="cuda")
+                else:
+                    P, F = (torch.full(ps, 7.0, dtype=torch.float64, device="cuda"),
+                            torch.full(fs, 7.0, dtype=torch.float64, device="cuda"))
+                mg.mg_set_outputs(h, b, l, P, F)
+                outs[(b, l)] = (P, F)
+        # registered, then unregistered: stays untouched
+        mg.mg_set_outputs(h, 1, 1, None, None)
+        with pytest.raises(mg.MGError):
+            mg.mg_set_outputs(h, 0, 0, np.zeros(shp(Hs[0], 0)[0]), np.zeros(shp(Hs[0], 0)[1]))
+        with pytest.raises(mg.MGError):
+            mg.mg_set_outputs(h, 0, 0, torch.zeros(shp(Hs[0], 0)[0], dtype=torch.float64, device="cuda"), None)
+        mg.mg_profile(h, prof)
+        mg.mg_solve(h, 2, allow_noconv=True)
+        for (b, l), (P, F) in outs.items():
+            ps, fs = shp(Hs[b], l)
+            rp = torch.zeros(ps, dtype=torch.float64, device="cuda")
+            rf = torch.zeros(fs, dtype=torch.float64, device="cuda")
+            mg.mg_forces(h, b, l, rp, rf)
+            torch.cuda.synchronize()
+            if (b, l) == (1, 1):
+                assert torch.all(P.cpu() == 7.0) and torch.all(F.cpu() == 7.0)
+                continue
+            assert np.array_equal(F.cpu().numpy(), rf.cpu().numpy()), (b, l)
+            if P is not None:
+                assert np.array_equal(P.cpu().numpy(), rp.cpu().numpy()), (b, l)
+    finally:
+        mg.mg_destroy(h)
+
+
 def test_heterogeneous_batch(mg):
     """Uneven hierarchies solved together (parallel branches of the solve
     graph) give the same results as each solved alone."""
