@@ -116,7 +116,7 @@ class Runner:
     """One hierarchy resident on the GPU plus its inputs and outputs."""
 
     def __init__(self, mg, torch, H, inp, stream, precision, tune_cache=None, unet=None, autotune=True, inner_max=0,
-                 inner_cycles=3):
+                 inner_cycles=3, forces_call=False):
         self.mg, self.torch, self.H = mg, torch, H
         self.stream = stream
         guess = mg.MG_GUESS_LEARNED if unet is not None else mg.MG_GUESS_INTERP
@@ -139,7 +139,10 @@ class Runner:
         self.h_phi = [torch.zeros((n,) * 3, dtype=torch.float64).pin_memory().numpy() for n in H.n]
         self.h_F = [torch.zeros((3,) + (n,) * 3, dtype=torch.float64).pin_memory().numpy() for n in H.n]
         self.stats = None
-        self.outputs(False)
+        self.forces_call = forces_call
+        self.out_host = False
+        if not forces_call:
+            self.outputs(False)
 
     def outputs(self, host):
         """Where mg_solve writes each level's potential and forces: the device
@@ -154,7 +157,7 @@ class Runner:
         """One step: the inputs into the hierarchy, the solve, which also
         writes every level's potential and forces (Eq. 2) to the outputs."""
         mg = self.mg
-        if host != self.out_host:
+        if host != self.out_host and not self.forces_call:
             self.outputs(host)
         src = self.h_in if host else self.d_in
         for l in range(self.H.num_levels):
@@ -163,6 +166,10 @@ class Runner:
             else:
                 mg.mg_set_density(self.h, 0, l, src[l]["rho"])
         _, self.stats = mg.mg_solve(self.h, 1)
+        if self.forces_call:       # the same results through one mg_forces call per level
+            phi, F = (self.h_phi, self.h_F) if host else (self.d_phi, self.d_F)
+            for l in range(self.H.num_levels):
+                mg.mg_forces(self.h, 0, l, phi[l], F[l])
 
     def io_bytes(self):
         h2d = sum(a.nbytes for d in self.h_in for a in d.values())
@@ -302,7 +309,7 @@ def run_ours(args):
         plans.append(("mixed_learned", mg.MG_MIXED, net))
     for name, prec, unet in plans:
         r = Runner(mg, torch, H, inp, stream, prec, args.tune_cache, unet, not args.no_autotune, args.inner_max,
-                   args.inner_cycles)
+                   args.inner_cycles, args.forces_call)
         try:
             # the first solve of each form carries an NVTX range, so that a
             # profiler can select exactly one solve's launches
@@ -533,21 +540,26 @@ def run_batch_case(args):
             inp = I.level_inputs(H)
             ins.append([{k: dev(v) for k, v in d.items()} for d in inp])
 
-        nmax = max(max(H.n) for H in Hs)
-        F = torch.empty((3,) + (nmax,) * 3, dtype=torch.float64, device="cuda")
+        # every level's forces, written by mg_solve once the level has converged
+        Fs = [[torch.empty((3,) + (n,) * 3, dtype=torch.float64, device="cuda") for n in H.n] for H in Hs]
+        for b, H in enumerate(Hs):
+            for l in range(H.num_levels):
+                if not args.forces_call:
+                    mg.mg_set_outputs(h, b, l, None, Fs[b][l])
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
         def step():
-            """inputs (device-resident) into the hierarchies, solve, forces of every level"""
+            """inputs (device-resident) into the hierarchies, solve (forces of every level included)"""
             for b, H in enumerate(Hs):
                 d = ins[b]
                 mg.mg_set_density(h, b, 0, d[0]["rho"], d[0]["bc_rho"], d[0]["bc_phi"])
                 for l in range(1, H.num_levels):
                     mg.mg_set_density(h, b, l, d[l]["rho"])
             st = mg.mg_solve(h, len(Hs))[1]
-            for b, H in enumerate(Hs):
-                for l in range(H.num_levels):
-                    mg.mg_forces(h, b, l, None, F)
+            if args.forces_call:
+                for b, H in enumerate(Hs):
+                    for l in range(H.num_levels):
+                        mg.mg_forces(h, b, l, None, Fs[b][l])
             return st
 
         for _ in range(args.warmup):
@@ -566,7 +578,7 @@ def run_batch_case(args):
         print(json.dumps({"case": f"batch of {len(Hs)} uneven hierarchies", "zones": zones, "ms_per_solve": dt * 1e3,
                           "zones_per_s": zones / dt, "worst_rel_res": worst, "fp32_cycles_total": cyc,
                           "autotune": bool(args.autotune), "batched_kernels": os.environ.get("MG_BATCHED", "0") == "1",
-                          "timing": "CUDA events around set_density + mg_solve + mg_forces of every level"}))
+                          "timing": "CUDA events around set_density + mg_solve (writing every level's forces)"}))
     finally:
         mg.mg_destroy(h)
 
@@ -597,14 +609,14 @@ def run_scale_case(args):
             if prec == mg.MG_MIXED:
                 mg.mg_autotune(h, args.tune_cache)
 
+            for l in range(H.num_levels):
+                mg.mg_set_outputs(h, 0, l, P[l], F[l])
+
             def step():
                 mg.mg_set_density(h, 0, 0, d_in[0]["rho"], d_in[0]["bc_rho"], d_in[0]["bc_phi"])
                 for l in range(1, H.num_levels):
                     mg.mg_set_density(h, 0, l, d_in[l]["rho"])
-                st = mg.mg_solve(h, 1)[1]
-                for l in range(H.num_levels):
-                    mg.mg_forces(h, 0, l, P[l], F[l])
-                return st
+                return mg.mg_solve(h, 1)[1]
 
             for _ in range(args.warmup):
                 st = step()
@@ -629,7 +641,8 @@ def run_scale_case(args):
                               "cycles_per_level": [st[0][l]["cycles"] for l in range(H.num_levels)],
                               "max_rel_res": max(st[0][l]["rel_res"] for l in range(H.num_levels)),
                               "max_rel_err_phi": ep, "max_rel_err_F": ef,
-                              "timing": "CUDA events around set_density + mg_solve + mg_forces, median"}), flush=True)
+                              "timing": "CUDA events around set_density + mg_solve (writing potential and forces), "
+                                        "median"}), flush=True)
         finally:
             mg.mg_destroy(h)
 
@@ -705,14 +718,14 @@ def run_2d_case(args):
                 if prec == mg.MG_MIXED:
                     mg.mg_autotune(h, args.tune_cache)
 
+                for l in range(H.num_levels):
+                    mg.mg_set_outputs(h, 0, l, None, F[l])
+
                 def step():
                     mg.mg_set_density(h, 0, 0, d[0]["rho"], d[0]["bc_rho"], d[0]["bc_phi"])
                     for l in range(1, H.num_levels):
                         mg.mg_set_density(h, 0, l, d[l]["rho"])
-                    st = mg.mg_solve(h, 1)[1]
-                    for l in range(H.num_levels):
-                        mg.mg_forces(h, 0, l, None, F[l])
-                    return st
+                    return mg.mg_solve(h, 1)[1]
 
                 for _ in range(args.warmup):
                     st = step()
@@ -787,6 +800,9 @@ def main():
     ap.add_argument("--inner-max", type=int, default=8,
                     help="mixed forms: cap of the FP32 V-cycles each defect-correction step after the first "
                          "may choose (0: three in every step)")
+    ap.add_argument("--forces-call", action="store_true",
+                    help="results through one mg_forces call per level after mg_solve instead of the outputs "
+                         "mg_solve fills itself (mg_set_outputs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch plan (a fixed plan for profiler captures)")
     ap.add_argument("--samples", type=int, default=256, help="learned case: training samples")

@@ -200,8 +200,9 @@ mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *
  * `level` (the values mg_forces would give, same layouts): F_out (required
  * for phi_out) and phi_out, each device memory or page-locked host memory
  * (written in place); NULL, NULL unregisters.  mg_solve then computes them
- * as soon as the level has converged, beside the solves of the levels after
- * it, and returns with them complete.  The pointers are kept until changed
+ * after the solves, inside its own graph launch, and returns with them
+ * complete (no synchronisation per level, as mg_forces needs for host
+ * arrays).  The pointers are kept until changed
  * (a change rebuilds the solve graph once).  Not part of the paper: the
  * results of Sec. 2 (Eq. 2) without a call per level.  Errors: MG_EINVAL
  * (range, phi without F, pageable host memory). */
