@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cmath>
 
 #define MG_MAX_MG 16          // multigrid levels per refinement level (n+2 <= 2^15)
 
@@ -227,7 +228,7 @@ __host__ __device__ inline int mg_next_inner(double rel_before, double rel_after
     const double need = log(tol / rel_after) / per_cycle;          // > 0
     if (!(need < inner_max))
         return inner_max;
-    const int k = (int)ceil(need);
+    const int k = (int)ceil(need - 1e-9);   // a whole number of cycles stays whole under rounding
     return k < 1 ? 1 : k;
 }
 
