@@ -152,22 +152,33 @@ def residual(lv, phi, f):
 
 
 def restrict(fine, r, coarse):
-    """f of the coarse level from the fine residual (A3)."""
-    fc = np.zeros(coarse.shape())
+    """f of the coarse level from the fine residual (A3): along a coarsened
+    axis coarse cell I sums fine cells 2I-1 and 2I (cells beyond the fine N
+    count zero, a fine cell beyond 2 N_coarse has no parent), along the others
+    it takes cell I; the sum is divided by 2^k, k the coarsened axes."""
     dim = fine.dim
-    coars = [coarse.la[a] > fine.la[a] for a in range(dim)]
-    k = sum(coars)
-    it = np.ndindex(*tuple(coarse.N[::-1]))
-    for I_rev in it:
-        I = [v + 1 for v in reversed(I_rev)]            # (I, J[, K]) 1-based, x first
-        offs = [(0, 1) if coars[a] else (0,) for a in range(dim)]
-        s = 0.0
-        for d in np.ndindex(*[len(o) for o in offs]):
-            q = [2 * I[a] - 1 + d[a] if coars[a] else I[a] for a in range(dim)]
-            if any(q[a] > fine.N[a] for a in range(dim)):
-                continue
-            s += r[tuple(reversed(q))]
-        fc[tuple(reversed(I))] = s / 2.0 ** k
+    act = tuple(slice(1, n + 1) for n in reversed(fine.N))
+    v = r[act]
+    k = 0
+    for a in range(dim):
+        if coarse.la[a] <= fine.la[a]:
+            continue
+        k += 1
+        ax = dim - 1 - a
+        Nc, Nf = coarse.N[a], fine.N[a]
+        if 2 * Nc > Nf:
+            pad = [(0, 0)] * dim
+            pad[ax] = (0, 2 * Nc - Nf)
+            v = np.pad(v, pad)
+        else:
+            sl = [slice(None)] * dim
+            sl[ax] = slice(0, 2 * Nc)
+            v = v[tuple(sl)]
+        shp = list(v.shape)
+        shp[ax:ax + 1] = [Nc, 2]
+        v = v.reshape(shp).sum(axis=ax + 1)
+    fc = np.zeros(coarse.shape())
+    fc[tuple(slice(1, n + 1) for n in reversed(coarse.N))] = v / 2.0 ** k
     return fc
 
 
@@ -191,30 +202,24 @@ def fill_ghosts(lv, phi):
 
 
 def prolong_add(coarse, phic, fine, phif):
-    """Phi_fine += P(Phi_coarse) (A4; Sec. 2.3 step 10 weights per coarsened axis)."""
+    """Phi_fine += P(Phi_coarse) (A4; Sec. 2.3 step 10): axis after axis, the
+    fine centre of cell i a quarter coarse cell from coarse cell ceil(i/2)
+    towards cell ceil(i/2) - 1 (i odd) or + 1 (i even), weights 3/4 and 1/4,
+    along coarsened axes (coarse ghosts by the rule of Sec. 2.4); the coarse
+    value of cell i along the others."""
     dim = fine.dim
     fill_ghosts(coarse, phic)
-    coars = [coarse.la[a] > fine.la[a] for a in range(dim)]
-    for F_rev in np.ndindex(*tuple(fine.N[::-1])):
-        f = [v + 1 for v in reversed(F_rev)]
-        taps = []
-        for a in range(dim):
-            if coars[a]:
-                near = (f[a] + 1) // 2
-                far = near - 1 if f[a] & 1 else near + 1
-                taps.append(((near, 0.75), (far, 0.25)))
-            else:
-                taps.append(((f[a], 1.0),))
-        v = 0.0
-        for choice in np.ndindex(*[len(t) for t in taps]):
-            w = 1.0
-            q = []
-            for a in range(dim):
-                idx, wa = taps[a][choice[a]]
-                w *= wa
-                q.append(idx)
-            v += w * phic[tuple(reversed(q))]
-        phif[tuple(reversed(f))] += v
+    v = phic
+    for a in range(dim):
+        ax = dim - 1 - a
+        i = np.arange(1, fine.N[a] + 1)
+        if coarse.la[a] > fine.la[a]:
+            near = (i + 1) // 2
+            far = np.where(i & 1, near - 1, near + 1)
+            v = 0.75 * np.take(v, near, axis=ax) + 0.25 * np.take(v, far, axis=ax)
+        else:
+            v = np.take(v, i, axis=ax)
+    phif[tuple(slice(1, n + 1) for n in reversed(fine.N))] += v
 
 
 def vcycle(lvs, phi, f, nu_pre, nu_post):
@@ -267,3 +272,102 @@ def level_solve(n, h, phi, rho, fourpiG, nu_pre=2, nu_post=1, max_cycles=50, rel
         hist.append(rel())
     phi[act] = phis[0][act]
     return c, np.array(hist)
+
+
+# ---------------------------------------------------------------------------
+# A hierarchy of box patches (Sec. 2.1): interface, forces, the coarse-to-fine solve
+# ---------------------------------------------------------------------------
+def interface_fill(n_p, phi_p, rho_p, n_c, off, phi_c, rho_c, guess=True):
+    """Buffer rings of a child patch from its parent (Sec. 2.1; Appendix A
+    weights): bi/trilinear interpolation from the 2^d parent centres around
+    each child centre -- potential into the outer ring, density into the
+    inner ring, and (guess) the interpolated potential as the initial value
+    of Gamma; the parent's centre of storage index p sits at coordinate p,
+    the child's storage index s at off + 1.5 + (s - 1.5) / 2."""
+    dim = len(n_c)
+    shape_c = tuple(m + 4 for m in reversed(n_c))
+    p0, t = [], []
+    for a in range(dim):
+        s = np.arange(n_c[a] + 4)
+        q = off[a] + 1.5 + (s - 1.5) * 0.5
+        f = np.floor(q).astype(int)
+        p0.append(f)
+        t.append(q - f)
+
+    def interp(src):
+        v = np.zeros(shape_c)
+        for corner in np.ndindex(*([2] * dim)):
+            w = np.ones(shape_c)
+            idx = []
+            for a in range(dim):
+                ax = dim - 1 - a
+                wa = t[a] if corner[a] else 1.0 - t[a]
+                w = w * wa.reshape([-1 if k == ax else 1 for k in range(dim)])
+                idx.append(p0[a] + corner[a])
+            v += w * src[np.ix_(*reversed(idx))]
+        return v
+
+    outer = np.zeros(shape_c, dtype=bool)
+    inner = np.zeros(shape_c, dtype=bool)
+    for a in range(dim):
+        ax = dim - 1 - a
+        s = np.arange(n_c[a] + 4).reshape([-1 if k == ax else 1 for k in range(dim)])
+        outer |= (s == 0) | (s == n_c[a] + 3)
+        inner |= (s == 1) | (s == n_c[a] + 2)
+    inner &= ~outer
+    vphi = interp(phi_p)
+    vrho = interp(rho_p)
+    phi_c[outer] = vphi[outer]
+    rho_c[inner] = vrho[inner]
+    phi_c[~outer] = vphi[~outer] if guess else 0.0
+
+
+def forces(n, h, phi, stencil=0):
+    """F = -grad(Phi) on the patch cells by Eq. 2 (stencil 0) or the two-point
+    central difference (stencil 1); shape (dim,) + patch shape ((z,) y, x)."""
+    dim = len(n)
+    om = [slice(2, m + 2) for m in reversed(n)]
+    F = np.zeros((dim,) + tuple(reversed(n)))
+    for a in range(dim):
+        ax = dim - 1 - a
+
+        def sh(d):
+            sl = list(om)
+            sl[ax] = slice(2 + d, n[a] + 2 + d)
+            return phi[tuple(sl)]
+
+        d1 = sh(1) - sh(-1)
+        d2 = sh(2) - sh(-2)
+        g = (4.0 / 3.0) * d1 / (2.0 * h) - (1.0 / 3.0) * d2 / (4.0 * h) if stencil == 0 else d1 / (2.0 * h)
+        F[a] = -g
+    return F
+
+
+def solve_hierarchy(H, inputs, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10, force_stencil=0):
+    """Solve a nested hierarchy of box patches coarse to fine (Sec. 2.1 one-way
+    scheme): the base level from the caller's boundary data (outer-ring
+    potential, inner-ring density) and a zero start, every finer patch from
+    its parent's converged solution (interpolated rings and initial guess).
+    Returns per patch dicts with phi (the n_a + 4 block), rho, F, cycles, hist."""
+    from math import pi
+    dim = H.dim
+    fourpiG = 4.0 * pi * H.G
+    out = []
+    for l in range(H.num_levels):
+        n, h = tuple(H.n[l]), H.h(l)
+        shape = tuple(m + 4 for m in reversed(n))
+        phi = np.zeros(shape)
+        rho = np.zeros(shape)
+        gam = tuple(slice(1, m + 3) for m in reversed(n))
+        om = tuple(slice(2, m + 2) for m in reversed(n))
+        if l == 0:
+            phi[...] = inputs[0]["bc_phi"]
+            rho[gam] = inputs[0]["bc_rho"]
+            phi[gam] = 0.0
+        else:
+            P = out[H.parent(l)]
+            interface_fill(tuple(H.n[H.parent(l)]), P["phi"], P["rho"], n, H.offset(l), phi, rho, guess=True)
+        rho[om] = inputs[l]["rho"]
+        cyc, hist = level_solve(n, h, phi, rho, fourpiG, nu_pre, nu_post, max_cycles, rel_tol)
+        out.append({"phi": phi, "rho": rho, "F": forces(n, h, phi, force_stencil), "cycles": cyc, "hist": hist})
+    return out

@@ -224,6 +224,63 @@ class Hierarchy:
         return sum(s.force(X, self.G) for s in self.sources)
 
 
+class BoxHierarchy(Hierarchy):
+    """A hierarchy of box (non-cubic) patches: n[l] is a tuple of cells per
+    axis (x, y[, z]); everything else as in Hierarchy."""
+
+    def centres(self, l, pad):
+        """Cell centres of patch l over a block of n_a + 2 pad cells per axis;
+        shape (..., dim), C order (z, y, x)."""
+        h = self.h(l)
+        ax = [self.lo[l][a] + (np.arange(-pad, self.n[l][a] + pad) + 0.5) * h for a in range(self.dim)]
+        grids = np.meshgrid(*ax[::-1], indexing="ij")
+        return np.stack(grids[::-1], axis=-1)
+
+    def zones(self):
+        return sum(int(np.prod(n)) for n in self.n)
+
+    def validate(self):
+        for l in range(1, self.num_levels):
+            assert 0 <= self.parent(l) < l, l
+            o = self.offset(l)
+            nl, np_ = self.n[l], self.n[self.parent(l)]
+            for a in range(self.dim):
+                assert nl[a] % 2 == 0
+                assert 1 <= o[a] <= np_[a] - nl[a] // 2 - 1, (l, a, o[a])
+
+
+def nested_boxes(dim, n_levels, n, half_widths, G, sources, name="", centre=0.0):
+    """Base box [c - w_a, c + w_a] with n = (n_x, n_y[, n_z]) cells of one size;
+    each finer patch halves the box about the centre (same cell counts)."""
+    h0 = 2.0 * half_widths[0] / n[0]
+    assert all(abs(2.0 * half_widths[a] / n[a] - h0) < 1e-12 * h0 for a in range(dim)), "cells must be cubes"
+    lo = []
+    for l in range(n_levels):
+        hl = h0 / 2 ** l
+        lo.append(tuple(centre - n[a] * hl / 2.0 for a in range(dim)))
+    H = BoxHierarchy(dim, [tuple(n)] * n_levels, lo, h0, G, list(sources), name)
+    H.validate()
+    return H
+
+
+def box_3d_sphere(n=(24, 32, 16), levels=3):
+    """3D box patches: base of n cells (one cell size) centred on an offset
+    compact sphere rho = (1 - r^2/R^2)^3, R = 0.3 at (0.05, 0.03, 0.02); G = 1;
+    each finer patch halves the box."""
+    h0 = 2.0 / max(n)
+    hw = [0.5 * na * h0 for na in n]
+    return nested_boxes(3, levels, n, hw, 1.0, [PolySphere((0.05, 0.03, 0.02), 0.3, 1.0, 3)],
+                        f"box3d_{levels}x{'x'.join(map(str, n))}")
+
+
+def box_2d_disk(n=(48, 24), levels=3):
+    """2D box patches around the compact disk rho = (1 - r^2/R^2)^4, R = 0.5."""
+    h0 = 2.0 / max(n)
+    hw = [0.5 * na * h0 for na in n]
+    return nested_boxes(2, levels, n, hw, 1.0, [PolyDisk((0.0, 0.0), 0.5, 1.0, 4)],
+                        f"box2d_{levels}x{'x'.join(map(str, n))}")
+
+
 def nested_centred(dim, n_levels, n, half_width, G, sources, name="", centre=0.0):
     """Base [c-w, c+w]^d with n cells; each finer level halves the box (same n)."""
     ns = [n] * n_levels if np.isscalar(n) else list(n)

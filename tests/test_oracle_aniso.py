@@ -7,7 +7,11 @@
   by its own tests) after a fixed number of V-cycles;
 - for patches whose axes differ, the fixed point: the direct solution of the
   level's 5/7-point system with the Dirichlet outer ring;
-- the contraction of a working multigrid cycle on those patches.
+- the contraction of a working multigrid cycle on those patches;
+- for hierarchies of box patches: the cubic case equals the cubic oracle's
+  hierarchy solve, the buffer fill is exact on multilinear fields, Eq. 2 is
+  exact on quartics, and the error against the closed forms falls at second
+  order.
 """
 import numpy as np
 import pytest
@@ -15,6 +19,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from oracle import aniso as A
+from paper_2001_02327_gb300 import inputs as I
 
 
 def test_axis_sizes_and_semi_coarsening():
@@ -96,3 +101,108 @@ def test_non_cubic_cycles_contract(n):
     c, hist = A.level_solve(n, 1.0 / max(n), phi, rho, 1.0, 2, 1, 10, 0.0)
     rates = hist[4:] / hist[3:-1]
     assert np.all(rates < 0.3), rates
+
+
+# --------------------------------------------------------------------------
+# hierarchies of box patches: interface, forces, the coarse-to-fine solve
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("dim,n", [(3, 16), (2, 32)])
+def test_box_hierarchy_cubic_case_equals_cubic_oracle(oracle, dim, n):
+    Hc = I.config_3d_offset_sphere(n, 3) if dim == 3 else I.config_2d_disk(n, 3)
+    Hb = I.nested_boxes(dim, 3, (n,) * dim, [1.0] * dim, Hc.G, Hc.sources)
+    ic, ib = I.level_inputs(Hc), I.level_inputs(Hb)
+    rc = oracle.solve_hierarchy(Hc, ic, 2, 1, 3, 0.0)
+    rb = A.solve_hierarchy(Hb, ib, 2, 1, 3, 0.0)
+    for l in range(3):
+        for key in ("phi", "F"):
+            ref = rc[l][key]
+            assert np.max(np.abs(rb[l][key] - ref)) <= 1e-12 * np.max(np.abs(ref)), (l, key)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_box_interface_exact_on_multilinear_fields(dim):
+    """Appendix A: the bi/trilinear buffer fill reproduces any multilinear
+    field; parent centre of storage index p at coordinate p, child storage
+    index s at off + 1.5 + (s - 1.5) / 2, per axis."""
+    rng = np.random.default_rng(dim)
+    n_p = (20, 14, 18)[:dim]
+    n_c = (12, 8, 10)[:dim]
+    off = (3, 2, 5)[:dim]
+    coef = rng.standard_normal(2 ** dim)
+
+    def field(coords):                                   # sum over subsets of the product of coordinates
+        v = 0.0
+        for m, c in zip(np.ndindex(*([2] * dim)), coef):
+            term = c
+            for a in range(dim):
+                if m[a]:
+                    term = term * coords[a]
+            v = v + term
+        return v
+
+    def grid(n, to_coord):
+        ax = [to_coord(a, np.arange(n[a] + 4)) for a in range(dim)]
+        g = np.meshgrid(*ax[::-1], indexing="ij")
+        return g[::-1]                                   # x, y[, z] arrays in (z,) y, x order
+
+    phi_p = field(grid(n_p, lambda a, p: p.astype(float)))
+    rho_p = 2.0 * phi_p + 1.0
+    phi_c = np.full(tuple(m + 4 for m in reversed(n_c)), np.nan)
+    rho_c = np.full_like(phi_c, np.nan)
+    A.interface_fill(n_p, phi_p, rho_p, n_c, off, phi_c, rho_c, guess=True)
+    want = field(grid(n_c, lambda a, s: off[a] + 1.5 + (s - 1.5) * 0.5))
+    assert np.allclose(phi_c, want, rtol=0, atol=1e-12 * np.max(np.abs(want)))
+    inner = np.zeros(phi_c.shape, dtype=bool)
+    outer = np.zeros(phi_c.shape, dtype=bool)
+    for a in range(dim):
+        ax = dim - 1 - a
+        s = np.arange(n_c[a] + 4).reshape([-1 if k == ax else 1 for k in range(dim)])
+        outer |= (s == 0) | (s == n_c[a] + 3)
+        inner |= (s == 1) | (s == n_c[a] + 2)
+    inner &= ~outer
+    assert np.allclose(rho_c[inner], 2.0 * want[inner] + 1.0, rtol=0, atol=1e-12 * np.max(np.abs(want)))
+    assert np.all(np.isnan(rho_c[~inner]))              # density only into the inner ring
+
+
+@pytest.mark.parametrize("n", [(10, 7, 12), (9, 15)])
+def test_box_forces_exact_on_quartics(n):
+    """Eq. 2 is exact for polynomials of degree four along each axis."""
+    dim = len(n)
+    h = 0.37
+    ax = [(np.arange(n[a] + 4) - 1.5) * h for a in range(dim)]
+    g = np.meshgrid(*ax[::-1], indexing="ij")[::-1]
+    polys = [(0.3, -1.1, 0.7, 2.0, -0.4), (1.5, 0.2, -0.9, 0.1, 0.8), (-0.6, 0.5, 0.3, -1.2, 0.05)][:dim]
+    phi = sum(np.polyval(p, g[a]) for a, p in enumerate(polys))
+    F = A.forces(n, h, phi, 0)
+    for a, p in enumerate(polys):
+        om = tuple(slice(2, m + 2) for m in reversed(n))
+        want = -np.polyval(np.polyder(p), g[a][om])
+        assert np.allclose(F[a], want, rtol=0, atol=1e-10 * np.max(np.abs(want))), a
+
+
+def _errors(H, res):
+    ep = ef = 0.0
+    for l in range(H.num_levels):
+        X = H.centres(l, 0)
+        om = tuple(slice(2, m + 2) for m in reversed(H.n[l]))
+        pa, fa = H.potential(X), H.force(X)
+        ep = max(ep, np.max(np.abs(res[l]["phi"][om] - pa)) / np.max(np.abs(pa)))
+        ef = max(ef, np.max(np.abs(np.moveaxis(res[l]["F"], 0, -1) - fa)) / np.max(np.abs(fa)))
+    return ep, ef
+
+
+@pytest.mark.parametrize("make", [lambda k: I.box_3d_sphere((12 * k, 16 * k, 8 * k), 3),
+                                  lambda k: I.box_2d_disk((24 * k, 12 * k), 3)])
+def test_box_hierarchy_second_order(make):
+    """Potential and forces of a nested box hierarchy against the closed form:
+    the largest error over all patches falls by more than 3 when the cells
+    halve (second order across the refinement interfaces)."""
+    e = []
+    for k in (1, 2):
+        H = make(k)
+        res = A.solve_hierarchy(H, I.level_inputs(H), 2, 2, 40, 1e-10)
+        assert all(r["hist"][-1] < 1e-10 for r in res)
+        e.append(_errors(H, res))
+    assert e[0][0] / e[1][0] > 3.0 and e[0][1] / e[1][1] > 3.0, e
