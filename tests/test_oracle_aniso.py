@@ -35,6 +35,52 @@ def test_axis_sizes_and_semi_coarsening():
     assert lv[2].tie[0] and not lv[1].tie[0]
 
 
+def test_restriction_averages_on_a_semi_coarsened_level():
+    """A3: the restriction is an average -- a constant residual restricts to
+    the same constant where every child exists, also where one axis no longer
+    coarsens (M = (4, 34), levels 2 -> 3: x stays at one cell, y halves)."""
+    lv = A.levels([4, 34], 1.0)
+    fine, coarse = lv[2], lv[3]
+    assert fine.N == [1, 9] and coarse.N == [1, 4]
+    r = np.zeros(fine.shape())
+    r[1:-1, 1:-1] = 1.0
+    fc = A.restrict(fine, r, coarse)
+    assert np.allclose(fc[1:5, 1], 1.0)                 # coarse cells J = 1..4 (children 1..8)
+
+
+def test_operator_on_a_semi_coarsened_level():
+    """A2 on level 3 of M = (4, 34) (h0 = 1): one cell along x of size 4
+    (its left ghost -Phi_1 and its right ghost -Phi_1, since x_N + h/2 = 1),
+    four cells along y of size 8.  For Phi = y^2 the interior cells give
+    r = 0 - (x part + y part) = -((-1 - 1 - 2) Phi / 16 + 2) = Phi / 4 - 2."""
+    lv = A.levels([4, 34], 1.0)[3]
+    assert lv.N == [1, 4] and lv.h == [4.0, 8.0]
+    y = (np.arange(6) - 0.5) * 8.0                      # storage 0..5 along y
+    phi = np.zeros(lv.shape())
+    phi[:, 1] = y ** 2
+    r = A.residual(lv, phi, np.zeros_like(phi))
+    for j in (2, 3):
+        assert r[j, 1] == pytest.approx(phi[j, 1] / 4.0 - 2.0, rel=1e-14), j
+
+
+def test_right_ghost_rule_per_axis():
+    """Sec. 2.4 per axis on level 2 of M = (9, 11): x has 2 cells with right
+    ghost -Phi_2 / 3, y 3 cells with right ghost -3 Phi_3 (linear
+    extrapolation through zero at x_MG = 1 on each axis's own grid).  A field
+    linear in y vanishing at y_MG = 1 has no y part at j = 2, 3, so the
+    residual there is minus the x part: Phi / 8 at i = 1 and Phi / 12 at
+    i = 2 (cell size 4)."""
+    lv = A.levels([9, 11], 1.0)[2]
+    assert lv.N == [2, 3] and lv.cR == pytest.approx([-1.0 / 3.0, -3.0])
+    yn = (np.arange(5) - 0.5) * 4.0 / 11.0               # normalised centres, storage 0..4
+    phi = np.zeros(lv.shape())
+    phi[:, 1:3] = (1.0 - yn)[:, None]
+    r = A.residual(lv, phi, np.zeros_like(phi))
+    for j in (2, 3):
+        assert r[j, 1] == pytest.approx(phi[j, 1] / 8.0, rel=1e-13), j
+        assert r[j, 2] == pytest.approx(phi[j, 2] / 12.0, rel=1e-13), j
+
+
 @pytest.mark.parametrize("dim,n", [(3, 12), (3, 8), (3, 9), (2, 20), (2, 8), (2, 13)])
 def test_cubic_case_equals_the_cubic_oracle(oracle, dim, n):
     rng = np.random.default_rng(100 + 10 * dim + n)
