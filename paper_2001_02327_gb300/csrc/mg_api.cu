@@ -725,8 +725,9 @@ bool adaptive_inner(const mg_hierarchy *h)
 }
 
 // The FP32 V-cycles of an adaptive step while s captures a graph: a nested
-// WHILE node whose body is one V-cycle and the kernel that counts it down
-// (ctl.left); its condition *hi starts at 1 and ctl_step re-arms it.
+// WHILE node whose body is one V-cycle, counted down in ctl.left by its last
+// launch (the counted smoothing variant, else a separate kernel after it);
+// the condition *hi starts at 1 and ctl_step re-arms it for the next step.
 cudaError_t capture_inner_loop(mg_hierarchy *h, const LevelData &ld, MgSolveCtl *ctl, cudaStream_t s,
                                cudaGraphConditionalHandle *hi)
 {
