@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB: 3D n <= 64, 2D n <= 540
+constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB: 3D n <= 69, 2D n <= 554 (the byte count below decides)
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t ncells(int e, int dim) { return dim == 3 ? (size_t)e * e * e : (size_t)e * e; }
@@ -181,9 +181,21 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
     need += up256(MG_NORM_BLOCKS * sizeof(double)) + up256(2 * sizeof(double));
     if (need > kNoAllocScratchBytes) {
         char buf[160];
-        std::snprintf(buf, sizeof buf, "n=%d in %dD needs %zu bytes of scratch, the limit is %zu (3D n <= 64, 2D n <= 540)",
+        std::snprintf(buf, sizeof buf, "n=%d in %dD needs %zu bytes of scratch, the limit is %zu (3D n <= 69, 2D n <= 554)",
                       n, dim, need, kNoAllocScratchBytes);
         return reject(MG_EINVAL, buf);
+    }
+    cudaStream_t s = (cudaStream_t)o.stream;
+    {
+        // the call waits for its own norms on the host: a capturing stream
+        // would have its capture invalidated, so it is refused up front
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return reject(MG_EINVAL, "opt->stream is not a valid stream");
+        }
+        if (cs != cudaStreamCaptureStatusNone)
+            return reject(MG_EINVAL, "opt->stream is capturing a graph; this call synchronises and cannot be captured");
     }
     for (const void *p : {(const void *)rho, (const void *)phi}) {
         cudaPointerAttributes a;
@@ -198,7 +210,6 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess)
         return reject(MG_ECUDA, cudaGetErrorString(e));
-    cudaStream_t s = (cudaStream_t)o.stream;
     double *phis[MG_MAX_MG], *fs[MG_MAX_MG];
     size_t pos = 0;
     phis[0] = phi;
@@ -213,10 +224,18 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
     double *partials = (double *)(base + part_off);
     double *scal = partials + up256(MG_NORM_BLOCKS * sizeof(double)) / sizeof(double);
 
+    // once work is queued, a failing call waits for the stream before it
+    // returns, so that no kernel of it still writes the shared array when the
+    // caller's next call starts
+    auto fail_queued = [&](cudaError_t err) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        return reject(MG_ECUDA, cudaGetErrorString(err));
+    };
     // the array keeps the previous call's contents: ghost layers of the
     // coarse levels must read as zero, so clear the part this call uses
     if ((e = mg_launch_zero(base, need, s)))
-        return reject(MG_ECUDA, cudaGetErrorString(e));
+        return fail_queued(e);
     const double fourpiG = 4.0 * M_PI * G;
     const int E = n + 4;
     const long tot = (long)ncells(E, dim);
@@ -226,7 +245,7 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
     else
         k_rhs_from_block<2><<<grid, 256, 0, s>>>(n, rho, fs[0], fourpiG);
     if ((e = cudaGetLastError()))
-        return reject(MG_ECUDA, cudaGetErrorString(e));
+        return fail_queued(e);
 
     // loop of Sec. 2.3 with the stopping rule of mg_options (host-side test;
     // the two norms come back through a pageable host copy, no allocation)
@@ -234,7 +253,7 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
     if ((e = mg_launch_resid_norm2(dim, phi, fs[0], g[0], true, partials, scal, s)) ||
         (e = mg_launch_resid_norm2(dim, phi, fs[0], g[0], false, partials, scal + 1, s)) ||
         (e = cudaMemcpyAsync(hs, scal, sizeof hs, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
-        return reject(MG_ECUDA, cudaGetErrorString(e));
+        return fail_queued(e);
     const double bn = std::sqrt(hs[0]);
     double rel = bn > 0.0 ? std::sqrt(hs[1]) / bn : 0.0;
     int cycles = 0, status = std::isfinite(bn) ? MG_OK : MG_EDIVERGED;
@@ -243,7 +262,7 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
             (e = mg_launch_resid_norm2(dim, phi, fs[0], g[0], false, partials, scal + 1, s)) ||
             (e = cudaMemcpyAsync(hs + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) ||
             (e = cudaStreamSynchronize(s)))
-            return reject(MG_ECUDA, cudaGetErrorString(e));
+            return fail_queued(e);
         cycles++;
         rel = std::sqrt(hs[1]) / bn;
         if (!std::isfinite(rel)) {
