@@ -251,19 +251,41 @@ mg_status mg_interp_guess(mg_hierarchy *h, int b, int level, double *out, double
  * among equivalent launch plans).  For each distinct level size it times, on
  * the level's own FP32 correction arrays, (1) the size limit of the one-block
  * kernel for the coarse multigrid levels (4, 8 or 17 cells per edge) and
- * (2) for every multigrid level above it, the temporal-blocking tile of its
- * pre-/post-smoothing kernels (8, 12, 16, or 0 = one kernel per phase).
+ * (2) for every multigrid level above it, how its smoothing runs: one
+ * kernel per colour and phase (0), the temporally blocked legs (tile 8, 12 or
+ * 16), or the plane-marching sweeps (3D, 1-2 sweeps per stint: every stint one
+ * launch, two tile shapes and three splits of z each).
  * Every choice computes the same result.  cache_path (may be NULL) is a text
  * file of earlier choices keyed by (dim, n, nu_pre, nu_post); new choices are
  * appended.  No-op for MG_FP64.  Call after mg_create_hierarchy, before
  * mg_solve.  Errors: MG_EINVAL, MG_ESTATE, MG_ECUDA. */
 mg_status mg_autotune(mg_hierarchy *h, const char *cache_path);
 
-/* The current FP32 plan of hierarchy b's level: writes the tile of each
- * multigrid level (0 = one kernel per phase) into tiles[0..cap) and returns
+/* The current FP32 plan of hierarchy b's level: writes the plan of each
+ * multigrid level into tiles[0..cap) (0 = one kernel per phase, > 0 the
+ * blocked legs' tile, < 0 the plane-marching sweeps: -(256 * tile shape +
+ * z-chunks), tile shape 0 = 56 x 10, 1 = 56 x 6) and returns
  * the edge of the first level run by the one-block kernel (-1 on bad
  * arguments). */
 int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap);
+
+/* Time multigrid level L of hierarchy b's refinement level `level` as the
+ * solve graph launches it (measurement, not part of the method; MG_MIXED
+ * only, L above the one-block kernel).  `launches` smoothing launches of the
+ * level's current FP32 plan are captured back to back into one CUDA graph with
+ * programmatic dependent launch, as in mg_solve, and the graph is replayed on
+ * the handle's stream between CUDA events (one warm-up replay, then five;
+ * with MG_SOLVE_GRAPH=0 the launches run and are timed without a graph).
+ * Plane-marching plan: one launch = nu_pre complete red-black sweeps, the FP32
+ * correction arrays ping-ponged; one-kernel-per-phase plan: one launch = one
+ * colour in place.  Writes the mean time per launch in microseconds and the
+ * algorithmic bytes per launch, the least DRAM traffic the launch must move:
+ * 3 words per active cell for a plane-marching launch (Phi and f read once,
+ * Phi written once), 1.5 for one colour (Phi read, half of f read, half of
+ * Phi written).  Overwrites the level's FP32 correction arrays, which the next
+ * mg_solve rewrites.  Errors: MG_EINVAL, MG_ESTATE, MG_ECUDA. */
+mg_status mg_time_smoothing(mg_hierarchy *h, int b, int level, int L, int launches, double *us_per_launch,
+                            double *bytes_per_launch);
 
 /* Allocation-free solve of one refinement level, for callers that cannot
  * allocate device memory: codes that give all of the GPU's memory to their
@@ -282,14 +304,17 @@ int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap);
  *         opt->stream is used.
  *   stats host, may be NULL.
  * Working memory is one library-owned device array of 4 MiB (every GPU that
- * loads the library holds it until the process exits): n <= 64 in 3D and
- * n <= 540 in 2D; larger n is rejected with MG_EINVAL before any GPU work.
+ * loads the library holds it until the process exits): n <= 69 in 3D and
+ * n <= 554 in 2D; larger n is rejected with MG_EINVAL before any GPU work.
  * The array is shared by every call and keeps the previous call's contents
  * (the call clears the part it uses): calls whose GPU work overlaps race and
  * must not be issued concurrently.  The first call on each device looks the
  * array's device address up once (cudaGetSymbolAddress with that device
- * current); make that first call before any stream capture.  Errors:
- * MG_EINVAL (message on stderr), MG_ECUDA, and MG_ENOCONV / MG_EDIVERGED as
+ * current).  Every call waits on the host for its residual norms, so it must
+ * never be issued on a stream that is capturing a graph: such a stream is
+ * refused with MG_EINVAL before any work.  Errors: MG_EINVAL (message on
+ * stderr), MG_ECUDA (the call first waits for the work it queued, so that
+ * nothing of it runs on when it returns), and MG_ENOCONV / MG_EDIVERGED as
  * for mg_solve.  The call returns after the solve has finished. */
 mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, const double *rho, double *phi,
                                  const mg_options *opt, mg_level_stats *stats);

@@ -70,22 +70,59 @@ int bottom_limit(bool fp32)
     return 8;
 }
 
-// FP32 temporal-blocking tile of each level above the bottom kernel.  The
-// default is 0 (one kernel per phase): on L2-resident levels the halo
-// recomputation of a blocked leg (about 4x the updates at tile 16 and halo 5)
-// costs more than the launches it saves; mg_autotune picks tiles where they
-// pay.  MG_TB_TILE forces one tile for every level.  Tiles are even and fit
-// the shared-memory limit.
+// Launch plan of an FP32 multigrid level above the bottom kernel, one int per
+// level (LevelData::tile): 0 = one kernel per colour and phase; t > 0 = the
+// temporally blocked legs with tile t; t < 0 = the plane-marching sweeps
+// (mg_wave.cu: every smoothing stint one launch, phi32 -> phi32b before the
+// restriction, phi32b + prolongation -> phi32 after it), encoded as
+// -(variant * 256 + z-chunks).
+int wave_code(int variant, int zchunks) { return -(variant * 256 + zchunks); }
+int wave_variant(int code) { return (-code) >> 8; }
+int wave_zchunks(int code) { return (-code) & 255; }
+
+bool wave_ok(int dim, int nu_pre, int nu_post, int N)
+{
+    return mg_wave_applies(dim, nu_pre, N) && mg_wave_applies(dim, nu_post, N);
+}
+
+// The default plane-marching plan of a level of N cells per edge: 56 x 10
+// tiles from 100 cells up, 56 x 6 below (two blocks per SM either way);
+// z-chunks so that the blocks fill the SMs once.
+int wave_default(int N)
+{
+    const int variant = N >= 100 ? 0 : 1;
+    const int ty = variant == 0 ? 10 : 6;
+    const int xy = (N / 56 + 1) * (N / ty + 1);
+    int zc = std::max(1, 152 * 2 / xy);
+    zc = std::min(zc, std::max(1, N / 8));
+    return wave_code(variant, std::min(zc, 255));
+}
+
+// FP32 launch plan of each level above the bottom kernel.  Without tuning:
+// one kernel per phase (measured fastest on every level but the largest,
+// where the plane-marching sweeps are about even); MG_WAVE=1 selects the
+// plane-marching sweeps wherever they apply (3D, 1-2 sweeps per stint),
+// MG_WAVE_PLAN="variant,zchunks" fixes their tile shape and z split (for
+// measurement); MG_TB_TILE forces one blocked-leg tile for every level (even,
+// fitting the shared-memory limit).  mg_autotune times all the candidates.
 void plan_tiles(LevelData &ld, int dim, int nu_pre, int nu_post)
 {
     const char *v = std::getenv("MG_TB_TILE");
     const int forced = (v && *v) ? std::atoi(v) : -1;
+    const char *wv = std::getenv("MG_WAVE");
+    const bool wave = wv && wv[0] == '1';
+    int wvar = -1, wzc = -1;
+    if (const char *wp = std::getenv("MG_WAVE_PLAN"))
+        if (std::sscanf(wp, "%d,%d", &wvar, &wzc) != 2 || wvar < 0 || wvar > 1 || wzc < 1 || wzc > 255)
+            wvar = wzc = -1;
     for (int L = 0; L < ld.nmg; L++) {
         int t = forced >= 0 ? forced : 0;
         t &= ~1;
         while (t > 0 && (mg_tb_smem(dim, true, t, 2 * nu_pre + 1) > MG_TB_SMEM_MAX ||
                          mg_tb_smem(dim, true, t, 2 * nu_post) > MG_TB_SMEM_MAX))
             t -= 2;
+        if (forced < 0 && wave && wave_ok(dim, nu_pre, nu_post, ld.g[L].N))
+            t = wvar >= 0 ? wave_code(wvar, std::min(wzc, ld.g[L].N)) : wave_default(ld.g[L].N);
         ld.tile[L] = t;
     }
 }
@@ -253,11 +290,12 @@ void build_geometry(LevelData &ld, int dim)
 #define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
 
 enum KernelKind { KK_SMOOTH, KK_RESTRICT, KK_PROLONG, KK_NORM, KK_DEFECT, KK_ACCUM, KK_IFACE, KK_FORCES,
-                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_CLUSTER, KK_SMOOTH0, KK_COUNT };
+                  KK_SETDENS, KK_BOTTOM, KK_TB_PRE, KK_TB_POST, KK_CLUSTER, KK_SMOOTH0, KK_WAVE, KK_WAVE0, KK_COUNT };
 const char *const kKindName[KK_COUNT] = {"smooth_colour", "resid_restrict", "prolong_correct", "resid_norm",
                                          "defect",        "accumulate",     "interface",       "forces",
                                          "set_density",   "bottom",         "tb_pre",          "tb_post",
-                                         "cluster_vcycle", "smooth_colour_finest"};
+                                         "cluster_vcycle", "smooth_colour_finest", "smooth_wave",
+                                         "smooth_wave_finest"};
 
 // Per-launch CUDA-event timing on the hierarchy's stream (mg_profile).
 struct Profiler {
@@ -293,6 +331,8 @@ struct mg_hierarchy {
     double *frho = nullptr;         // device 4 pi G h_l^2 per (b, l) (input scaling of the learned guess)
     mg_unet *unet = nullptr;        // learned initial guess (MG_GUESS_LEARNED)
     MgSolveCtl *hctl = nullptr;     // pinned mirror
+    int *werr = nullptr;            // device word: MG_ETIMEOUT once a plane-marching load wait gave up
+    int wfault = 0;                 // MG_FAULT_WAVE_WAIT=1: those waits are made to run out (test of that path)
     bool poisoned = false, solved = false;
     std::string err;
     Profiler prof;
@@ -497,6 +537,23 @@ mg_status check_desc(const mg_hierarchy_desc &d, int b, int dim0)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// After device work that ran plane-marching sweeps: MG_ETIMEOUT (and the
+// handle poisoned) when one of their bounded load waits gave up.
+mg_status wave_status(mg_hierarchy *h)
+{
+    int w = 0;
+    cudaError_t e = cudaMemcpyAsync(&w, h->werr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess)
+        return fail_cuda(h, e, "reading the device error word");
+    if (w) {
+        h->poisoned = true;
+        return fail(h, MG_ETIMEOUT, "a plane-marching sweep's load wait ran out of its clock budget");
+    }
+    return MG_OK;
+}
+
 // --------------------------------------------------------------------------
 // the V-cycle of Sec. 2.3 on the arrays of one refinement level
 // --------------------------------------------------------------------------
@@ -596,7 +653,23 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     // level in FP32 when the level has a tile, else one kernel per phase
     for (int L = 0; L < Lstop; L++) {
         const double nf = cells_d(ld.g[L].N, dim), nc = cells_d(ld.g[L + 1].N, dim);
-        if (fp32 && ld.tile[L]) {
+        if (fp32 && ld.tile[L] < 0) {
+            const int code = ld.tile[L];
+            e = timed(h, L == 0 ? KK_WAVE0 : KK_WAVE, 3.0 * w * nf, [&] {
+                return mg_launch_wave(ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], o.nu_pre, wave_variant(code),
+                                      wave_zchunks(code), s, nullptr, 0, h->werr, h->wfault);
+            });
+            if (e)
+                return e;
+            e = timed(h, KK_RESTRICT, w * (2.0 * nf + 2.0 * nc), [&] {
+                return mg_launch_resid_restrict(dim, true, ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
+                                                ld.f32[L + 1], ld.g[L + 1], s);
+            });
+            if (e)
+                return e;
+            continue;
+        }
+        if (fp32 && ld.tile[L] > 0) {
             e = timed(h, KK_TB_PRE, w * (3.0 * nf + 2.0 * nc), [&] {
                 return mg_launch_tb_pre(dim, ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
                                         ld.f32[L + 1], ld.g[L + 1], ld.tile[L], o.nu_pre, s);
@@ -618,7 +691,26 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     // ascent: prolongation + correction, then nu_post sweeps (steps 10-11)
     for (int L = Lstop; L > 0; L--) {
         const double nf = cells_d(ld.g[L - 1].N, dim), nc = cells_d(ld.g[L].N, dim);
-        if (fp32 && ld.tile[L - 1]) {
+        if (fp32 && ld.tile[L - 1] < 0) {
+            const int code = ld.tile[L - 1];
+            e = timed(h, KK_PROLONG, w * (nc + 2.0 * nf), [&] {
+                return mg_launch_prolong(dim, true, ld.phi32[L], ld.g[L], ld.phi32b[L - 1], ld.g[L - 1], s);
+            });
+            if (e)
+                return e;
+            const bool fold = ctl && ncyc == 1 && L == 1;
+            e = timed(h, L == 1 ? KK_WAVE0 : KK_WAVE, 3.0 * w * nf, [&] {
+                return mg_launch_wave(ld.phi32b[L - 1], ld.phi32[L - 1], ld.f32[L - 1], ld.g[L - 1], o.nu_post,
+                                      wave_variant(code), wave_zchunks(code), s, fold ? ctl : nullptr, hi, h->werr,
+                                      h->wfault);
+            });
+            if (e)
+                return e;
+            if (fold && counted)
+                *counted = true;
+            continue;
+        }
+        if (fp32 && ld.tile[L - 1] > 0) {
             e = timed(h, KK_TB_POST, w * (3.0 * nf + nc), [&] {
                 return mg_launch_tb_post(dim, ld.phi32b[L - 1], ld.phi32[L - 1], ld.f32[L - 1], ld.g[L - 1],
                                          ld.phi32[L], ld.g[L], ld.tile[L - 1], o.nu_post, s);
@@ -984,7 +1076,7 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
             P.Ls = ld.Ls[1];
             for (int L = 0; L < ld.nmg; L++) {
                 P.g[L] = ld.g[L];
-                P.tile[L] = ld.tile[L];
+                P.tile[L] = ld.tile[L] > 0 ? ld.tile[L] : 0;   // batched kernels: blocked legs or one kernel per phase
                 P.phi32[L] = ld.phi32[L];
                 P.phi32b[L] = ld.phi32b[L];
                 P.f32[L] = ld.f32[L];
@@ -1020,7 +1112,7 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
                 H.pr.resize(P.Ls);
             }
             for (int L = 0; L < P.Ls; L++) {
-                if (ld.tile[L]) {
+                if (ld.tile[L] > 0) {
                     const int nb = (ld.g[L].N + ld.tile[L] - 1) / ld.tile[L];
                     for (int z = 0; z < (dim == 3 ? nb : 1); z++)
                         for (int y = 0; y < nb; y++)
@@ -1342,10 +1434,36 @@ struct TuneEntry {
 
 // Mean time of one replay of the launches of fn, captured into a CUDA graph
 // (the solve runs as a graph: timing plain launches would favour plans with
-// fewer launches for the wrong reason).
+// fewer launches for the wrong reason).  With the solve graph off
+// (MG_SOLVE_GRAPH=0) the launches are timed as plain launches, as the solve
+// then runs them.
 float time_ms(mg_hierarchy *h, int reps, const std::function<cudaError_t(cudaStream_t)> &fn, cudaError_t &err)
 {
     err = cudaSuccess;
+    if (!h->use_graph) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        err = fn(h->stream);                                // warm-up
+        if (!err)
+            err = cudaEventCreate(&a);
+        if (!err)
+            err = cudaEventCreate(&b);
+        if (!err)
+            err = cudaEventRecord(a, h->stream);
+        for (int r = 0; r < reps && !err; r++)
+            err = fn(h->stream);
+        if (!err)
+            err = cudaEventRecord(b, h->stream);
+        if (!err)
+            err = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (!err)
+            err = cudaEventElapsedTime(&ms, a, b);
+        if (a)
+            cudaEventDestroy(a);
+        if (b)
+            cudaEventDestroy(b);
+        return ms / reps;
+    }
     if (!h->cap[0] && (err = cudaStreamCreateWithFlags(&h->cap[0], cudaStreamNonBlocking)))
         return 0.f;
     cudaStream_t cs = h->cap[0];
@@ -1423,17 +1541,39 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     const int Ls = ld.Ls[1];
     for (int L = 0; L < MG_MAX_MG; L++)
         te.tile[L] = 0;
-    const int cands[4] = {0, 8, 12, 16};
     for (int L = 0; L < Ls; L++) {
         float bl = 1e30f;
         int bt = 0;
+        std::vector<int> cands = {0, 8, 12, 16};
+        if (wave_ok(dim, o.nu_pre, o.nu_post, ld.g[L].N)) {
+            // plane-marching sweeps: both tiles, z-chunks around the default
+            const int N = ld.g[L].N;
+            const int zd = wave_zchunks(wave_default(N));
+            for (int v = 0; v < 2; v++)
+                for (int zc : {std::max(1, zd / 2), zd, std::min(2 * zd, std::max(1, N / 4))})
+                    if (std::find(cands.begin(), cands.end(), wave_code(v, zc)) == cands.end())
+                        cands.push_back(wave_code(v, zc));
+        }
         for (int t : cands) {
-            if (t && (mg_tb_smem(dim, true, t, 2 * o.nu_pre + 1) > MG_TB_SMEM_MAX ||
-                      mg_tb_smem(dim, true, t, 2 * o.nu_post) > MG_TB_SMEM_MAX))
+            if (t > 0 && (mg_tb_smem(dim, true, t, 2 * o.nu_pre + 1) > MG_TB_SMEM_MAX ||
+                          mg_tb_smem(dim, true, t, 2 * o.nu_post) > MG_TB_SMEM_MAX))
                 continue;
             ld.tile[L] = t;
             const float ms = time_ms(h, 10, [&](cudaStream_t s) {
                 cudaError_t e;
+                if (t < 0) {
+                    e = mg_launch_wave(ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], o.nu_pre, wave_variant(t),
+                                       wave_zchunks(t), s, nullptr, 0, h->werr, h->wfault);
+                    if (!e)
+                        e = mg_launch_resid_restrict(dim, true, ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
+                                                     ld.f32[L + 1], ld.g[L + 1], s);
+                    if (!e)
+                        e = mg_launch_prolong(dim, true, ld.phi32[L + 1], ld.g[L + 1], ld.phi32b[L], ld.g[L], s);
+                    if (!e)
+                        e = mg_launch_wave(ld.phi32b[L], ld.phi32[L], ld.f32[L], ld.g[L], o.nu_post, wave_variant(t),
+                                           wave_zchunks(t), s, nullptr, 0, h->werr, h->wfault);
+                    return e;
+                }
                 if (t) {
                     e = mg_launch_tb_pre(dim, ld.phi32[L], ld.phi32b[L], ld.f32[L], ld.g[L], ld.phi32[L + 1],
                                          ld.f32[L + 1], ld.g[L + 1], t, o.nu_pre, s);
@@ -1657,6 +1797,7 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     slots.push_back({(void **)&h->ctl, align256((size_t)batch * MG_MAX_LEVELS * sizeof(MgSolveCtl))});
     slots.push_back({(void **)&h->frho, align256((size_t)batch * MG_MAX_LEVELS * sizeof(double))});
     slots.push_back({(void **)&h->scal, align256((size_t)batch * MG_MAX_LEVELS * 2 * sizeof(double))});
+    slots.push_back({(void **)&h->werr, align256(sizeof(int))});
     for (auto &sl : slots)
         bytes += sl.bytes;
     cudaError_t e = cudaMalloc((void **)&h->arena, bytes);
@@ -1691,11 +1832,15 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
     {
         const char *v = std::getenv("MG_SOLVE_GRAPH");
         h->use_graph = !(v && v[0] == '0');
+        const char *fw = std::getenv("MG_FAULT_WAVE_WAIT");
+        h->wfault = fw && fw[0] == '1';
     }
     // ghost layers and rings start at zero
     e = mg_bottom_prepare();
     if (e == cudaSuccess)
         e = mg_tb_prepare();
+    if (e == cudaSuccess)
+        e = mg_wave_prepare();
     if (e == cudaSuccess)
         e = mg_batch_prepare();
     if (e == cudaSuccess)
@@ -1850,6 +1995,8 @@ mg_status mg_solve(mg_hierarchy *h, mg_level_stats *stats)
             }
         CK(h, cudaStreamSynchronize(h->stream));   // registered outputs complete on return
     }
+    if (mg_status ws = wave_status(h))
+        return ws;
     h->solved = true;
     return worst;
 }
@@ -2053,6 +2200,50 @@ mg_status mg_autotune(mg_hierarchy *h, const char *cache_path)
         }
     }
     destroy_graph(h);                 // the solve graph is rebuilt with the new plan
+    return wave_status(h);
+}
+
+mg_status mg_time_smoothing(mg_hierarchy *h, int b, int level, int L, int launches, double *us_per_launch,
+                            double *bytes_per_launch)
+{
+    if (!h || !us_per_launch || !bytes_per_launch)
+        return MG_EINVAL;
+    if (h->poisoned)
+        return fail(h, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (h->opt.precision != MG_MIXED)
+        return fail(h, MG_EINVAL, "mg_time_smoothing times the FP32 plan of MG_MIXED");
+    if (b < 0 || b >= h->batch || level < 0 || level >= h->desc[b].num_levels)
+        return fail(h, MG_EINVAL, "hierarchy %d level %d out of range", b, level);
+    LevelData &ld = h->lev[b][level];
+    if (L < 0 || L >= ld.Ls[1] || ld.Lc[1] >= 0 || launches < 1 || launches > 4096)
+        return fail(h, MG_EINVAL, "multigrid level %d is not run by per-level launches, or launches %d out of 1..4096",
+                    L, launches);
+    const int dim = h->dim, code = ld.tile[L];
+    if (code > 0)
+        return fail(h, MG_EINVAL, "multigrid level %d runs the temporally blocked legs", L);
+    const mg_options &o = h->opt;
+    cudaError_t err = cudaSuccess;
+    const float ms = time_ms(h, 5, [&](cudaStream_t s) {
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r < launches && !e; r++) {
+            if (code < 0) {
+                const bool fwd = (r & 1) == 0;
+                e = mg_launch_wave(fwd ? ld.phi32[L] : ld.phi32b[L], fwd ? ld.phi32b[L] : ld.phi32[L], ld.f32[L],
+                                   ld.g[L], o.nu_pre, wave_variant(code), wave_zchunks(code), s, nullptr, 0,
+                                   h->werr, h->wfault);
+            } else {
+                e = mg_launch_smooth(dim, true, ld.phi32[L], ld.f32[L], ld.g[L], r & 1, s);
+            }
+        }
+        return e;
+    }, err);
+    if (err)
+        return fail_cuda(h, err, "smoothing timing");
+    if (mg_status ws = wave_status(h))
+        return ws;
+    const double nc = cells_d(ld.g[L].N, dim);
+    *us_per_launch = 1e3 * (double)ms / launches;
+    *bytes_per_launch = (code < 0 ? 3.0 : 1.5) * sizeof(float) * nc;
     return MG_OK;
 }
 

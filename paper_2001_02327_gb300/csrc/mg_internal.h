@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <cmath>
+#include <cstdlib>
 
 #define MG_MAX_MG 16          // multigrid levels per refinement level (n+2 <= 2^15)
 
@@ -131,6 +132,20 @@ cudaError_t mg_launch_tb_pre(int dim, const float *phi_in, float *phi_out, const
 cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, const float *f, const MgGeom &g,
                               const float *phi_c, const MgGeom &gc, int tile, int nu, cudaStream_t s);
 
+// Plane-marching red-black sweeps of an FP32 3D level (mg_wave.cu): nsw (1 or
+// 2) complete sweeps phi_in -> phi_out (distinct arrays whose ghost layers
+// hold the same values), bit-identical to 2 nsw mg_launch_smooth colours in
+// place.  variant 0: 56 x 10 tiles, 1: 56 x 6 tiles; the z extent is split
+// into zchunks ranges.  ctl != NULL: as mg_launch_smooth.  A load wait that
+// runs out of its clock budget (about 2 s) writes MG_ETIMEOUT to *err (if
+// err is not NULL) and ends the block; fault != 0 leaves one load group of
+// every block unissued with a budget of about 1 ms (a test of that path).
+cudaError_t mg_wave_prepare();   // once per device before the first launch
+bool mg_wave_applies(int dim, int nsw, int N);
+cudaError_t mg_launch_wave(const float *phi_in, float *phi_out, const float *f, const MgGeom &g, int nsw, int variant,
+                           int zchunks, cudaStream_t s, MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0,
+                           int *err = nullptr, int fault = 0);
+
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
                                      void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s);
 cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeom &gc, void *phi_f, const MgGeom &gf,
@@ -231,6 +246,59 @@ __host__ __device__ inline int mg_next_inner(double rel_before, double rel_after
     const int k = (int)ceil(need - 1e-9);   // a whole number of cycles stays whole under rounding
     return k < 1 ? 1 : k;
 }
+
+#ifdef __CUDACC__
+// Programmatic dependent launch: every kernel first waits until the kernel
+// before it in the stream has completed and its writes are visible, then
+// lets the next kernel start launching, so that launch latency overlaps the
+// running kernel.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// One FP32 V-cycle of an adaptive defect-correction step done (the step's
+// nested graph loop): count it and let the loop go on while cycles are left.
+// One thread.
+__device__ __forceinline__ void inner_step_count(MgSolveCtl *ctl, cudaGraphConditionalHandle hi)
+{
+    MgSolveCtl c = *ctl;
+    c.cycles += 1;
+    c.left -= 1;
+    *ctl = c;
+    cudaGraphSetConditional(hi, c.left > 0);
+}
+
+// Every kernel is launched with programmatic dependent launch (the kernels
+// begin with pdl_begin) unless MG_PDL=0.  Errors are left for
+// cudaGetLastError, as with the triple-chevron launch.
+inline bool mg_pdl_enabled()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("MG_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+inline void mg_launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = mg_pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+#endif
 
 // ctl_init: from scal = {||b||^2, ||r||^2} start the counters and set the
 // loop condition (handle) to 1 iff another iteration is needed.

@@ -39,16 +39,6 @@ __device__ __forceinline__ int lin(int i, int j, int k, int E)
     return DIM == 3 ? (k * E + j) * E + i : j * E + i;
 }
 
-// Programmatic dependent launch: every kernel first waits until the kernel
-// before it in the stream has completed and its writes are visible, then
-// lets the next kernel start launching, so that launch latency overlaps the
-// running kernel.  Without the launch attribute both instructions are no-ops.
-__device__ __forceinline__ void pdl_begin()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // floor(x / d) for 0 <= x < 2^31, d >= 1 and a quotient below 2^21 (every
 // index here: at most (1286 + 4)^2): the FP32 value of x, the reciprocal of d
 // and their product, each rounded toward zero, underestimate x/d by less than
@@ -392,18 +382,6 @@ __device__ __forceinline__ void op_prolong(const T *__restrict__ phi_c, const Mg
 
 __device__ __forceinline__ int gtid() { return blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int gstride() { return gridDim.x * blockDim.x; }
-
-// One FP32 V-cycle of an adaptive defect-correction step done (the step's
-// nested graph loop): count it and let the loop go on while cycles are left.
-// One thread.
-__device__ __forceinline__ void inner_step_count(MgSolveCtl *ctl, cudaGraphConditionalHandle hi)
-{
-    MgSolveCtl c = *ctl;
-    c.cycles += 1;
-    c.left -= 1;
-    *ctl = c;
-    cudaGraphSetConditional(hi, c.left > 0);
-}
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_smooth_colour(T *__restrict__ phi, const T *__restrict__ f, MgGeom g,
@@ -2230,34 +2208,6 @@ __global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// Every kernel is launched with programmatic dependent launch (the kernels
-// begin with pdl_begin) unless MG_PDL=0.  Errors are left for
-// cudaGetLastError, as with the triple-chevron launch.
-static bool pdl_enabled()
-{
-    static const bool on = [] {
-        const char *v = std::getenv("MG_PDL");
-        return !(v && v[0] == '0');
-    }();
-    return on;
-}
-
-template <typename... KArgs, typename... Args>
-static void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const MgGeom &g, int c, cudaStream_t s,
                              MgSolveCtl *ctl, cudaGraphConditionalHandle hi)
 {
@@ -2265,27 +2215,27 @@ cudaError_t mg_launch_smooth(int dim, bool fp32, void *phi, const void *f, const
     const int grid = grid_for(work);
     if (ctl) {
         if (dim == 3 && fp32)
-            launch(k_smooth_colour_counted<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c, ctl, hi);
+            mg_launch_kernel(k_smooth_colour_counted<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c, ctl, hi);
         else if (dim == 3)
-            launch(k_smooth_colour_counted<double, 3>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c, ctl,
+            mg_launch_kernel(k_smooth_colour_counted<double, 3>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c, ctl,
                    hi);
         else if (fp32)
-            launch(k_smooth_colour_counted<float, 2>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c, ctl, hi);
+            mg_launch_kernel(k_smooth_colour_counted<float, 2>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c, ctl, hi);
         else
-            launch(k_smooth_colour_counted<double, 2>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c, ctl,
+            mg_launch_kernel(k_smooth_colour_counted<double, 2>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c, ctl,
                    hi);
         return cudaGetLastError();
     }
     if (dim == 3) {
         if (fp32)
-            launch(k_smooth_colour<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
+            mg_launch_kernel(k_smooth_colour<float, 3>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
         else
-            launch(k_smooth_colour<double, 3>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c);
+            mg_launch_kernel(k_smooth_colour<double, 3>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c);
     } else {
         if (fp32)
-            launch(k_smooth_colour<float, 2>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
+            mg_launch_kernel(k_smooth_colour<float, 2>, grid, kThreads, 0, s, (float *)phi, (const float *)f, g, c);
         else
-            launch(k_smooth_colour<double, 2>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c);
+            mg_launch_kernel(k_smooth_colour<double, 2>, grid, kThreads, 0, s, (double *)phi, (const double *)f, g, c);
     }
     return cudaGetLastError();
 }
@@ -2307,14 +2257,14 @@ cudaError_t mg_launch_bottom_plan(int dim, bool fp32, const MgBottom &bt, void *
 {
     if (dim == 3) {
         if (fp32)
-            launch(k_bottom_plan<float, 3>, 1, kBottomThreads, 0, s, bt, (float *)img);
+            mg_launch_kernel(k_bottom_plan<float, 3>, 1, kBottomThreads, 0, s, bt, (float *)img);
         else
-            launch(k_bottom_plan<double, 3>, 1, kBottomThreads, 0, s, bt, (double *)img);
+            mg_launch_kernel(k_bottom_plan<double, 3>, 1, kBottomThreads, 0, s, bt, (double *)img);
     } else {
         if (fp32)
-            launch(k_bottom_plan<float, 2>, 1, kBottomThreads, 0, s, bt, (float *)img);
+            mg_launch_kernel(k_bottom_plan<float, 2>, 1, kBottomThreads, 0, s, bt, (float *)img);
         else
-            launch(k_bottom_plan<double, 2>, 1, kBottomThreads, 0, s, bt, (double *)img);
+            mg_launch_kernel(k_bottom_plan<double, 2>, 1, kBottomThreads, 0, s, bt, (double *)img);
     }
     return cudaGetLastError();
 }
@@ -2339,14 +2289,14 @@ cudaError_t mg_launch_bottom(int dim, bool fp32, void *phi, const void *f, const
     const size_t smem = mg_bottom_smem(dim, fp32, bt);
     if (dim == 3) {
         if (fp32)
-            launch(k_bottom<float, 3>, 1, kBottomThreads, smem, s, (float *)phi, (const float *)f, bt, nu_pre, nu_post);
+            mg_launch_kernel(k_bottom<float, 3>, 1, kBottomThreads, smem, s, (float *)phi, (const float *)f, bt, nu_pre, nu_post);
         else
-            launch(k_bottom<double, 3>, 1, kBottomThreads, smem, s, (double *)phi, (const double *)f, bt, nu_pre, nu_post);
+            mg_launch_kernel(k_bottom<double, 3>, 1, kBottomThreads, smem, s, (double *)phi, (const double *)f, bt, nu_pre, nu_post);
     } else {
         if (fp32)
-            launch(k_bottom<float, 2>, 1, kBottomThreads, smem, s, (float *)phi, (const float *)f, bt, nu_pre, nu_post);
+            mg_launch_kernel(k_bottom<float, 2>, 1, kBottomThreads, smem, s, (float *)phi, (const float *)f, bt, nu_pre, nu_post);
         else
-            launch(k_bottom<double, 2>, 1, kBottomThreads, smem, s, (double *)phi, (const double *)f, bt, nu_pre, nu_post);
+            mg_launch_kernel(k_bottom<double, 2>, 1, kBottomThreads, smem, s, (double *)phi, (const double *)f, bt, nu_pre, nu_post);
     }
     return cudaGetLastError();
 }
@@ -2462,9 +2412,9 @@ cudaError_t mg_launch_tb_pre(int dim, const float *phi_in, float *phi_out, const
     const int nb = (g.N + tile - 1) / tile;
     const size_t smem = mg_tb_smem(dim, true, tile, 2 * nu + 1);
     if (dim == 3)
-        launch(k_tb_pre<float, 3>, dim3(nb, nb, nb), 512, smem, s, phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
+        mg_launch_kernel(k_tb_pre<float, 3>, dim3(nb, nb, nb), 512, smem, s, phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
     else
-        launch(k_tb_pre<float, 2>, dim3(nb, nb, 1), 512, smem, s, phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
+        mg_launch_kernel(k_tb_pre<float, 2>, dim3(nb, nb, 1), 512, smem, s, phi_in, phi_out, f, g, phi_c, f_c, gc, tile, nu);
     return cudaGetLastError();
 }
 
@@ -2474,9 +2424,9 @@ cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, cons
     const int nb = (g.N + tile - 1) / tile;
     const size_t smem = mg_tb_smem(dim, true, tile, 2 * nu);
     if (dim == 3)
-        launch(k_tb_post<float, 3>, dim3(nb, nb, nb), 512, smem, s, phi_in, phi_out, f, g, phi_c, gc, tile, nu);
+        mg_launch_kernel(k_tb_post<float, 3>, dim3(nb, nb, nb), 512, smem, s, phi_in, phi_out, f, g, phi_c, gc, tile, nu);
     else
-        launch(k_tb_post<float, 2>, dim3(nb, nb, 1), 512, smem, s, phi_in, phi_out, f, g, phi_c, gc, tile, nu);
+        mg_launch_kernel(k_tb_post<float, 2>, dim3(nb, nb, 1), 512, smem, s, phi_in, phi_out, f, g, phi_c, gc, tile, nu);
     return cudaGetLastError();
 }
 
@@ -2488,17 +2438,17 @@ cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, cons
     const dim3 grid(nx, ny, nz);
     if (dim == 3) {
         if (fp32)
-            launch(k_resid_restrict<float, 3>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
+            mg_launch_kernel(k_resid_restrict<float, 3>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
         else
-            launch(k_resid_restrict<double, 3>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
+            mg_launch_kernel(k_resid_restrict<double, 3>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
                                                                   (double *)phi_c, (double *)f_c, gc);
     } else {
         if (fp32)
-            launch(k_resid_restrict<float, 2>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
+            mg_launch_kernel(k_resid_restrict<float, 2>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
                                                                  (float *)phi_c, (float *)f_c, gc);
         else
-            launch(k_resid_restrict<double, 2>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
+            mg_launch_kernel(k_resid_restrict<double, 2>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
                                                                   (double *)phi_c, (double *)f_c, gc);
     }
     return cudaGetLastError();
@@ -2510,14 +2460,14 @@ cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeo
     const int grid = grid_for(cube(gf.N, dim));
     if (dim == 3) {
         if (fp32)
-            launch(k_prolong<float, 3>, grid, kThreads, 0, s, (const float *)phi_c, gc, (float *)phi_f, gf);
+            mg_launch_kernel(k_prolong<float, 3>, grid, kThreads, 0, s, (const float *)phi_c, gc, (float *)phi_f, gf);
         else
-            launch(k_prolong<double, 3>, grid, kThreads, 0, s, (const double *)phi_c, gc, (double *)phi_f, gf);
+            mg_launch_kernel(k_prolong<double, 3>, grid, kThreads, 0, s, (const double *)phi_c, gc, (double *)phi_f, gf);
     } else {
         if (fp32)
-            launch(k_prolong<float, 2>, grid, kThreads, 0, s, (const float *)phi_c, gc, (float *)phi_f, gf);
+            mg_launch_kernel(k_prolong<float, 2>, grid, kThreads, 0, s, (const float *)phi_c, gc, (float *)phi_f, gf);
         else
-            launch(k_prolong<double, 2>, grid, kThreads, 0, s, (const double *)phi_c, gc, (double *)phi_f, gf);
+            mg_launch_kernel(k_prolong<double, 2>, grid, kThreads, 0, s, (const double *)phi_c, gc, (double *)phi_f, gf);
     }
     return cudaGetLastError();
 }
@@ -2528,9 +2478,9 @@ cudaError_t mg_launch_norms2(int dim, const double *phi, const double *f, const 
     // about four cells per thread: fewer block reductions on the FP64 pipe
     const int grid = std::max(1, std::min<int>((int)((cube(g.N, dim) + 4 * kThreads - 1) / (4 * kThreads)), MG_NORM_BLOCKS_MAX));
     if (dim == 3)
-        launch(k_norms2<3>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2, r32, e32);
+        mg_launch_kernel(k_norms2<3>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2, r32, e32);
     else
-        launch(k_norms2<2>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2, r32, e32);
+        mg_launch_kernel(k_norms2<2>, grid, kThreads, 0, s, phi, f, g, which, partials, counter, out2, r32, e32);
     return cudaGetLastError();
 }
 
@@ -2538,10 +2488,10 @@ cudaError_t mg_launch_resid_norm2(int dim, const double *phi, const double *f, c
                                   double *partials, double *out, cudaStream_t s)
 {
     if (dim == 3)
-        launch(k_resid_norm2<3>, MG_NORM_BLOCKS, kThreads, 0, s, phi, f, g, zero_inside ? 1 : 0, partials);
+        mg_launch_kernel(k_resid_norm2<3>, MG_NORM_BLOCKS, kThreads, 0, s, phi, f, g, zero_inside ? 1 : 0, partials);
     else
-        launch(k_resid_norm2<2>, MG_NORM_BLOCKS, kThreads, 0, s, phi, f, g, zero_inside ? 1 : 0, partials);
-    launch(k_sum_partials, 1, kThreads, 0, s, partials, MG_NORM_BLOCKS, out);
+        mg_launch_kernel(k_resid_norm2<2>, MG_NORM_BLOCKS, kThreads, 0, s, phi, f, g, zero_inside ? 1 : 0, partials);
+    mg_launch_kernel(k_sum_partials, 1, kThreads, 0, s, partials, MG_NORM_BLOCKS, out);
     return cudaGetLastError();
 }
 
@@ -2550,9 +2500,9 @@ cudaError_t mg_launch_defect(int dim, const double *phi, const double *f, const 
 {
     const int grid = grid_for(cube(g.N, dim));
     if (dim == 3)
-        launch(k_defect<3>, grid, kThreads, 0, s, phi, f, g, r32, e32);
+        mg_launch_kernel(k_defect<3>, grid, kThreads, 0, s, phi, f, g, r32, e32);
     else
-        launch(k_defect<2>, grid, kThreads, 0, s, phi, f, g, r32, e32);
+        mg_launch_kernel(k_defect<2>, grid, kThreads, 0, s, phi, f, g, r32, e32);
     return cudaGetLastError();
 }
 
@@ -2560,9 +2510,9 @@ cudaError_t mg_launch_accumulate(int dim, double *phi, const float *e32, const M
 {
     const int grid = grid_for(cube(g.N, dim));
     if (dim == 3)
-        launch(k_accumulate<3>, grid, kThreads, 0, s, phi, e32, g);
+        mg_launch_kernel(k_accumulate<3>, grid, kThreads, 0, s, phi, e32, g);
     else
-        launch(k_accumulate<2>, grid, kThreads, 0, s, phi, e32, g);
+        mg_launch_kernel(k_accumulate<2>, grid, kThreads, 0, s, phi, e32, g);
     return cudaGetLastError();
 }
 
@@ -2571,9 +2521,9 @@ cudaError_t mg_launch_set_density(int dim, int n, const double *rho, const doubl
 {
     const int grid = grid_for(cube(n + 4, dim));
     if (dim == 3)
-        launch(k_set_density<3>, grid, kThreads, 0, s, n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
+        mg_launch_kernel(k_set_density<3>, grid, kThreads, 0, s, n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
     else
-        launch(k_set_density<2>, grid, kThreads, 0, s, n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
+        mg_launch_kernel(k_set_density<2>, grid, kThreads, 0, s, n, rho, bc_rho, bc_phi, rho_blk, f_blk, phi_blk, fourpiG);
     return cudaGetLastError();
 }
 
@@ -2583,10 +2533,10 @@ cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const doub
 {
     const int grid = grid_for(cube(nc + 4, dim));
     if (dim == 3)
-        launch(k_interface<3>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
+        mg_launch_kernel(k_interface<3>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
                                                  guess_src, frozen);
     else
-        launch(k_interface<2>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
+        mg_launch_kernel(k_interface<2>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
                                                  guess_src, frozen);
     return cudaGetLastError();
 }
@@ -2595,9 +2545,9 @@ cudaError_t mg_launch_copy_guess(int dim, int n, const double *guess_src, double
 {
     const int grid = grid_for(cube(n + 2, dim));
     if (dim == 3)
-        launch(k_copy_guess<3>, grid, kThreads, 0, s, n, guess_src, phi_blk);
+        mg_launch_kernel(k_copy_guess<3>, grid, kThreads, 0, s, n, guess_src, phi_blk);
     else
-        launch(k_copy_guess<2>, grid, kThreads, 0, s, n, guess_src, phi_blk);
+        mg_launch_kernel(k_copy_guess<2>, grid, kThreads, 0, s, n, guess_src, phi_blk);
     return cudaGetLastError();
 }
 
@@ -2606,9 +2556,9 @@ cudaError_t mg_launch_forces(int dim, int n, double h, const double *phi_blk, do
 {
     const int grid = grid_for(cube(n, dim));
     if (dim == 3)
-        launch(k_forces<3>, grid, kThreads, 0, s, n, h, phi_blk, F, phi_out, stencil);
+        mg_launch_kernel(k_forces<3>, grid, kThreads, 0, s, n, h, phi_blk, F, phi_out, stencil);
     else
-        launch(k_forces<2>, grid, kThreads, 0, s, n, h, phi_blk, F, phi_out, stencil);
+        mg_launch_kernel(k_forces<2>, grid, kThreads, 0, s, n, h, phi_blk, F, phi_out, stencil);
     return cudaGetLastError();
 }
 
@@ -2616,17 +2566,17 @@ cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const doub
                                  int stencil, unsigned long long *cmax, double *scal, cudaStream_t s)
 {
     if (phase == 0) {
-        launch(k_force_start, 1, 1, 0, s, scal);
+        mg_launch_kernel(k_force_start, 1, 1, 0, s, scal);
     } else if (phase == 1) {
         const long total = cube(n + 4, dim);
-        launch(k_save_prev, grid_for(total), kThreads, 0, s, total, phi_blk, prev, cmax);
+        mg_launch_kernel(k_save_prev, grid_for(total), kThreads, 0, s, total, phi_blk, prev, cmax);
     } else {
         const int grid = grid_for(cube(n, dim));
         if (dim == 3)
-            launch(k_force_change<3>, grid, kThreads, 0, s, n, h, phi_blk, prev, stencil, cmax);
+            mg_launch_kernel(k_force_change<3>, grid, kThreads, 0, s, n, h, phi_blk, prev, stencil, cmax);
         else
-            launch(k_force_change<2>, grid, kThreads, 0, s, n, h, phi_blk, prev, stencil, cmax);
-        launch(k_force_finish, 1, 1, 0, s, scal, cmax);
+            mg_launch_kernel(k_force_change<2>, grid, kThreads, 0, s, n, h, phi_blk, prev, stencil, cmax);
+        mg_launch_kernel(k_force_finish, 1, 1, 0, s, scal, cmax);
     }
     return cudaGetLastError();
 }
@@ -2634,7 +2584,7 @@ cudaError_t mg_launch_force_stop(int phase, int dim, int n, double h, const doub
 cudaError_t mg_launch_ctl_init(MgSolveCtl *ctl, const double *scal, double tol, int max_cycles, int inner0,
                                cudaGraphConditionalHandle hc, cudaStream_t s)
 {
-    launch(k_ctl_init, 1, 1, 0, s, ctl, scal, tol, max_cycles, inner0, hc);
+    mg_launch_kernel(k_ctl_init, 1, 1, 0, s, ctl, scal, tol, max_cycles, inner0, hc);
     return cudaGetLastError();
 }
 
@@ -2642,13 +2592,13 @@ cudaError_t mg_launch_ctl_step(MgSolveCtl *ctl, const double *scal, int inc, dou
                                int inner_max, cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hi,
                                cudaStream_t s)
 {
-    launch(k_ctl_step, 1, 1, 0, s, ctl, scal, inc, tol, max_cycles, inner_max, hc, hi);
+    mg_launch_kernel(k_ctl_step, 1, 1, 0, s, ctl, scal, inc, tol, max_cycles, inner_max, hc, hi);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_inner_step(MgSolveCtl *ctl, cudaGraphConditionalHandle hi, cudaStream_t s)
 {
-    launch(k_inner_step, 1, 1, 0, s, ctl, hi);
+    mg_launch_kernel(k_inner_step, 1, 1, 0, s, ctl, hi);
     return cudaGetLastError();
 }
 
@@ -2656,9 +2606,9 @@ cudaError_t mg_launch_extract(int dim, int n, const double *blk, double *out, cu
 {
     const int grid = grid_for(cube(n, dim));
     if (dim == 3)
-        launch(k_extract<3>, grid, kThreads, 0, s, n, blk, out);
+        mg_launch_kernel(k_extract<3>, grid, kThreads, 0, s, n, blk, out);
     else
-        launch(k_extract<2>, grid, kThreads, 0, s, n, blk, out);
+        mg_launch_kernel(k_extract<2>, grid, kThreads, 0, s, n, blk, out);
     return cudaGetLastError();
 }
 
@@ -2667,9 +2617,9 @@ cudaError_t mg_launch_copy_box(int dim, int e, const double *src, int Es, int os
 {
     const int grid = grid_for(cube(e, dim));
     if (dim == 3)
-        launch(k_copy_box<3>, grid, kThreads, 0, s, e, src, Es, os, dst, Ed, od);
+        mg_launch_kernel(k_copy_box<3>, grid, kThreads, 0, s, e, src, Es, os, dst, Ed, od);
     else
-        launch(k_copy_box<2>, grid, kThreads, 0, s, e, src, Es, os, dst, Ed, od);
+        mg_launch_kernel(k_copy_box<2>, grid, kThreads, 0, s, e, src, Es, os, dst, Ed, od);
     return cudaGetLastError();
 }
 
@@ -2678,9 +2628,9 @@ cudaError_t mg_launch_resid_h2(int dim, int n, const double *phi_blk, const doub
 {
     const int grid = grid_for(cube(n, dim));
     if (dim == 3)
-        launch(k_resid_h2<3>, grid, kThreads, 0, s, n, phi_blk, rho_blk, frho, out);
+        mg_launch_kernel(k_resid_h2<3>, grid, kThreads, 0, s, n, phi_blk, rho_blk, frho, out);
     else
-        launch(k_resid_h2<2>, grid, kThreads, 0, s, n, phi_blk, rho_blk, frho, out);
+        mg_launch_kernel(k_resid_h2<2>, grid, kThreads, 0, s, n, phi_blk, rho_blk, frho, out);
     return cudaGetLastError();
 }
 
@@ -2689,7 +2639,7 @@ cudaError_t mg_launch_zero(void *p, size_t bytes, cudaStream_t s)
     // callers pass 256-byte aligned sub-allocations whose sizes are multiples of 16
     const size_t n16 = bytes / 16;
     if (n16)
-        launch(k_zero, grid_for((long)n16), kThreads, 0, s, (uint4 *)p, n16);
+        mg_launch_kernel(k_zero, grid_for((long)n16), kThreads, 0, s, (uint4 *)p, n16);
     return cudaGetLastError();
 }
 
@@ -2719,9 +2669,9 @@ cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tas
     if (ntasks <= 0)
         return cudaSuccess;
     if (dim == 3)
-        launch(kb_tb_pre<3>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
+        mg_launch_kernel(kb_tb_pre<3>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     else
-        launch(kb_tb_pre<2>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
+        mg_launch_kernel(kb_tb_pre<2>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     return cudaGetLastError();
 }
 
@@ -2731,9 +2681,9 @@ cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *ta
     if (ntasks <= 0)
         return cudaSuccess;
     if (dim == 3)
-        launch(kb_tb_post<3>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
+        mg_launch_kernel(kb_tb_post<3>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     else
-        launch(kb_tb_post<2>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
+        mg_launch_kernel(kb_tb_post<2>, ntasks, 512, smem, s, parts, tasks, active, depth, nu);
     return cudaGetLastError();
 }
 
@@ -2743,9 +2693,9 @@ cudaError_t mg_launch_b_smooth(int dim, const MgBPart *parts, const MgBCell *cel
     if (ncells <= 0)
         return cudaSuccess;
     if (dim == 3)
-        launch(kb_smooth<3>, ncells, kThreads, 0, s, parts, cells, active, L, colour);
+        mg_launch_kernel(kb_smooth<3>, ncells, kThreads, 0, s, parts, cells, active, L, colour);
     else
-        launch(kb_smooth<2>, ncells, kThreads, 0, s, parts, cells, active, L, colour);
+        mg_launch_kernel(kb_smooth<2>, ncells, kThreads, 0, s, parts, cells, active, L, colour);
     return cudaGetLastError();
 }
 
@@ -2755,9 +2705,9 @@ cudaError_t mg_launch_b_restrict(int dim, const MgBPart *parts, const MgBCell *c
     if (ncells <= 0)
         return cudaSuccess;
     if (dim == 3)
-        launch(kb_restrict<3>, ncells, kThreads, 0, s, parts, cells, active, L);
+        mg_launch_kernel(kb_restrict<3>, ncells, kThreads, 0, s, parts, cells, active, L);
     else
-        launch(kb_restrict<2>, ncells, kThreads, 0, s, parts, cells, active, L);
+        mg_launch_kernel(kb_restrict<2>, ncells, kThreads, 0, s, parts, cells, active, L);
     return cudaGetLastError();
 }
 
@@ -2767,9 +2717,9 @@ cudaError_t mg_launch_b_prolong(int dim, const MgBPart *parts, const MgBCell *ce
     if (ncells <= 0)
         return cudaSuccess;
     if (dim == 3)
-        launch(kb_prolong<3>, ncells, kThreads, 0, s, parts, cells, active, L);
+        mg_launch_kernel(kb_prolong<3>, ncells, kThreads, 0, s, parts, cells, active, L);
     else
-        launch(kb_prolong<2>, ncells, kThreads, 0, s, parts, cells, active, L);
+        mg_launch_kernel(kb_prolong<2>, ncells, kThreads, 0, s, parts, cells, active, L);
     return cudaGetLastError();
 }
 
@@ -2777,9 +2727,9 @@ cudaError_t mg_launch_b_bottom(int dim, const MgBPart *parts, int nparts, const 
                                size_t smem, cudaStream_t s)
 {
     if (dim == 3)
-        launch(kb_bottom<3>, nparts, kBottomThreads, smem, s, parts, active, nu_pre, nu_post);
+        mg_launch_kernel(kb_bottom<3>, nparts, kBottomThreads, smem, s, parts, active, nu_pre, nu_post);
     else
-        launch(kb_bottom<2>, nparts, kBottomThreads, smem, s, parts, active, nu_pre, nu_post);
+        mg_launch_kernel(kb_bottom<2>, nparts, kBottomThreads, smem, s, parts, active, nu_pre, nu_post);
     return cudaGetLastError();
 }
 
@@ -2787,9 +2737,9 @@ cudaError_t mg_launch_b_defect(int dim, const MgBPart *parts, const MgBCell *cel
                                cudaStream_t s)
 {
     if (dim == 3)
-        launch(kb_defect<3>, ncells, kThreads, 0, s, parts, cells, active);
+        mg_launch_kernel(kb_defect<3>, ncells, kThreads, 0, s, parts, cells, active);
     else
-        launch(kb_defect<2>, ncells, kThreads, 0, s, parts, cells, active);
+        mg_launch_kernel(kb_defect<2>, ncells, kThreads, 0, s, parts, cells, active);
     return cudaGetLastError();
 }
 
@@ -2797,9 +2747,9 @@ cudaError_t mg_launch_b_accumulate(int dim, const MgBPart *parts, const MgBCell 
                                    const int *active, cudaStream_t s)
 {
     if (dim == 3)
-        launch(kb_accumulate<3>, ncells, kThreads, 0, s, parts, cells, active);
+        mg_launch_kernel(kb_accumulate<3>, ncells, kThreads, 0, s, parts, cells, active);
     else
-        launch(kb_accumulate<2>, ncells, kThreads, 0, s, parts, cells, active);
+        mg_launch_kernel(kb_accumulate<2>, ncells, kThreads, 0, s, parts, cells, active);
     return cudaGetLastError();
 }
 
@@ -2807,24 +2757,24 @@ cudaError_t mg_launch_b_norms2(int dim, const MgBPart *parts, const MgBCell *cel
                                int which, cudaStream_t s)
 {
     if (dim == 3)
-        launch(kb_norms2<3>, ncells, kThreads, 0, s, parts, cells, active, which);
+        mg_launch_kernel(kb_norms2<3>, ncells, kThreads, 0, s, parts, cells, active, which);
     else
-        launch(kb_norms2<2>, ncells, kThreads, 0, s, parts, cells, active, which);
+        mg_launch_kernel(kb_norms2<2>, ncells, kThreads, 0, s, parts, cells, active, which);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_b_interface(int dim, const MgBPart *parts, const MgBCell *cells, int ncells, cudaStream_t s)
 {
     if (dim == 3)
-        launch(kb_interface<3>, ncells, kThreads, 0, s, parts, cells);
+        mg_launch_kernel(kb_interface<3>, ncells, kThreads, 0, s, parts, cells);
     else
-        launch(kb_interface<2>, ncells, kThreads, 0, s, parts, cells);
+        mg_launch_kernel(kb_interface<2>, ncells, kThreads, 0, s, parts, cells);
     return cudaGetLastError();
 }
 
 cudaError_t mg_launch_b_ctl(const MgBPart *parts, int nparts, int *active, int init, int inc, double tol,
                             int max_cycles, cudaGraphConditionalHandle hc, cudaStream_t s)
 {
-    launch(kb_ctl, 1, 1024, 0, s, parts, nparts, active, init, inc, tol, max_cycles, hc);
+    mg_launch_kernel(kb_ctl, 1, 1024, 0, s, parts, nparts, active, init, inc, tol, max_cycles, hc);
     return cudaGetLastError();
 }

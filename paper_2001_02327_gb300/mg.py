@@ -62,6 +62,8 @@ _SIGS = {
     "mg_profile": (C.c_int, [_vp, C.c_int]),
     "mg_autotune": (C.c_int, [_vp, C.c_char_p]),
     "mg_tuning": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "mg_time_smoothing": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     "mg_solve_level_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
                                          C.POINTER(mg_options), C.POINTER(mg_level_stats)]),
     "mg_profile_read": (C.c_int, [_vp, C.POINTER(mg_kernel_stat), C.c_int]),
@@ -204,6 +206,14 @@ def mg_tuning(h, b, level):
     buf = (C.c_int * 16)()
     nb = LIB.mg_tuning(h, b, level, buf, 16)
     return [buf[i] for i in range(16)], nb
+
+
+def mg_time_smoothing(h, b, level, L, launches):
+    """(microseconds per launch, algorithmic bytes per launch) of multigrid
+    level L's smoothing, timed as the solve graph launches it."""
+    us, by = C.c_double(), C.c_double()
+    _check(h, LIB.mg_time_smoothing(h, b, level, L, launches, C.byref(us), C.byref(by)))
+    return us.value, by.value
 
 
 def mg_destroy(h):

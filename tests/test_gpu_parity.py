@@ -754,7 +754,7 @@ def test_one_block_bottom_matches_one_kernel_per_phase(mg, make, prec, lim, monk
     inp = I.level_inputs(H)
     p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
     kw = dict(nu_pre=2, nu_post=2, max_cycles=4, rel_tol=0.0, precision=p, inner_cycles=2)
-    for v in ("MG_BOTTOM_N64", "MG_BOTTOM_N32", "MG_CLUSTER_N64", "MG_CLUSTER_N32"):
+    for v in ("MG_BOTTOM_N64", "MG_BOTTOM_N32", "MG_CLUSTER_N64", "MG_CLUSTER_N32", "MG_WAVE"):
         monkeypatch.setenv(v, "0")
     a, pa = _solve_profiled(mg, H, inp, **kw)
     monkeypatch.setenv("MG_BOTTOM_N64", str(lim))
@@ -773,3 +773,95 @@ def test_cluster_vcycle_is_3d_only(mg, monkeypatch):
     monkeypatch.setenv("MG_CLUSTER_N32", "33")
     b, pb = _solve_profiled(mg, H, inp, max_cycles=3, rel_tol=0.0)
     assert "cluster_vcycle" not in pb
+
+
+# --------------------------------------------------------------------------
+# plane-marching FP32 sweeps (all colour passes of a smoothing stint in one
+# launch, out of place) against one launch per colour
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("make,nu", [
+    (lambda: I.config_3d_offset_sphere(64, 3), (2, 2)),
+    (lambda: I.config_3d_offset_sphere(64, 2), (2, 1)),
+    (lambda: I.config_3d_offset_sphere(32, 3), (1, 1)),
+    (lambda: I.paper_3d(48), (2, 2)),
+    (lambda: I.paper_3d(48), (1, 2)),
+    (lambda: I.random_hierarchy(7), (2, 2)),
+    (lambda: I.random_hierarchy(3), (2, 1))])
+def test_wave_sweeps_match_one_colour_kernels(mg, make, nu, monkeypatch):
+    """Every multigrid level above the one-block kernel smoothed by the
+    plane-marching kernel (tile ring recomputed per block, ping-pong arrays)
+    gives potential and forces bit-identical to one launch per colour; the
+    multigrid sizes include odd, tie (x_N = 1) and non-tie levels."""
+    H = make()
+    inp = I.level_inputs(H)
+    kw = dict(nu_pre=nu[0], nu_post=nu[1], max_cycles=4, rel_tol=0.0, precision=mg.MG_MIXED, inner_cycles=2)
+    monkeypatch.setenv("MG_WAVE", "0")
+    a, pa = _solve_profiled(mg, H, inp, **kw)
+    monkeypatch.setenv("MG_WAVE", "1")
+    b, pb = _solve_profiled(mg, H, inp, **kw)
+    assert "smooth_wave" not in pa and "smooth_wave_finest" not in pa
+    assert pb["smooth_wave_finest"][0] > 0 and "smooth_colour_finest" not in pb, pb
+    for l in range(H.num_levels):
+        assert np.array_equal(a[l][0], b[l][0]), (l, relmax(b[l][0], a[l][0]))
+        assert np.array_equal(a[l][1], b[l][1]), l
+
+
+@pytest.mark.parametrize("zc", ["1", "5"])
+def test_wave_converged_adaptive_equals_one_colour(mg, zc, monkeypatch):
+    """Converged mixed solve with adaptive correction steps (the last sweep
+    launch of each FP32 V-cycle counts it in the nested graph loop): same
+    cycle counts and bit-identical results with and without the sweeps."""
+    H = I.config_3d_offset_sphere(64, 4)
+    inp = I.level_inputs(H)
+    kw = dict(nu_pre=2, nu_post=2, precision=mg.MG_MIXED, inner_max=8, allow_noconv=False)
+    monkeypatch.setenv("MG_WAVE", "0")
+    _, a = gpu_solve(mg, H, inp, **kw)
+    monkeypatch.setenv("MG_WAVE", "1")
+    monkeypatch.setenv("MG_WAVE_PLAN", f"1,{zc}")
+    _, b = gpu_solve(mg, H, inp, **kw)
+    for l in range(H.num_levels):
+        assert a[l]["cycles"] == b[l]["cycles"] and b[l]["rel_res"] < 1e-10
+        assert np.array_equal(a[l]["phi"], b[l]["phi"]) and np.array_equal(a[l]["F"], b[l]["F"])
+
+
+def test_time_smoothing_reports_plan_bytes(mg, monkeypatch):
+    """mg_time_smoothing times the level's smoothing in its plan's launch
+    form and states the algorithmic bytes of one launch (3 words per cell for
+    a plane-marching launch, 1.5 for one colour)."""
+    H = I.config_3d_offset_sphere(64, 2)
+    for wave in ("1", "0"):
+        monkeypatch.setenv("MG_WAVE", wave)
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=2, nu_post=2, precision=mg.MG_MIXED))
+        try:
+            tiles, _ = mg.mg_tuning(h, 0, 0)
+            us, by = mg.mg_time_smoothing(h, 0, 0, 0, 8)
+            N = 66
+            assert us > 0.0
+            assert by == (3.0 if wave == "1" else 1.5) * 4 * N ** 3
+            assert (tiles[0] < 0) == (wave == "1")
+            with pytest.raises(mg.MGError):
+                mg.mg_time_smoothing(h, 0, 0, 12, 8)   # the one-block kernel's levels are not per-level launches
+        finally:
+            mg.mg_destroy(h)
+
+
+def test_wave_load_wait_timeout_reports_etimeout(mg, monkeypatch):
+    """Every mbarrier wait of the plane-marching kernel has a clock budget.
+    With MG_FAULT_WAVE_WAIT=1 one load group of every block is never issued
+    (a wait nothing completes; budget about 1 ms): the blocks record the
+    timeout and return, mg_solve reports MG_ETIMEOUT and the handle refuses
+    further work; the GPU stays usable and a new handle solves normally."""
+    H = I.config_3d_offset_sphere(32, 2)
+    inp = I.level_inputs(H)
+    kw = dict(nu_pre=2, nu_post=2, max_cycles=2, rel_tol=0.0, precision=mg.MG_MIXED, inner_cycles=1)
+    monkeypatch.setenv("MG_WAVE", "1")
+    monkeypatch.setenv("MG_FAULT_WAVE_WAIT", "1")
+    with pytest.raises(mg.MGError) as ei:
+        gpu_solve(mg, H, inp, **kw)
+    assert ei.value.status == mg.MG_ETIMEOUT, ei.value
+    monkeypatch.delenv("MG_FAULT_WAVE_WAIT")
+    _, good = gpu_solve(mg, H, inp, **kw)
+    monkeypatch.setenv("MG_WAVE", "0")
+    _, plain = gpu_solve(mg, H, inp, **kw)
+    for l in range(H.num_levels):
+        assert np.array_equal(good[l]["phi"], plain[l]["phi"])
