@@ -14,8 +14,16 @@ timed events.  Forms: plain FP64, and FP32 V-cycles inside FP64 defect
 correction ("mixed").  `value` is the fastest form whose results stay within
 1e-2 of the discretisation error of the FP64 result.
 
---impl reference times the CPU FP64 oracle on the same workload (one full
-solve per step) on the host.
+Beside the headline: the finest multigrid level's FP32 smoothing timed as
+the solve graph launches it (mg_time_smoothing) against the measured HBM
+copy bandwidth, with its algorithmic bytes, and the whole step's algorithmic
+bytes over its time -- for this workload (L2-resident) and for the
+DRAM-resident one of 4 nested 256^3 levels with 8 compact spheres, whose
+zones/s are measured in the same run (--no-scale leaves it out).
+
+--impl reference times the CPU FP64 oracle, as it stands, on every host
+core: one full solve of the workload per core per step, in parallel
+processes.
 """
 from __future__ import annotations
 
@@ -261,19 +269,52 @@ def measured_peaks(key="hbm_gbs"):
     return fallback, "fallback"
 
 
-def kernel_traffic(name, form):
-    """DRAM bytes per launch of kernel `name` in form `form` from a committed
-    ncu summary, if it was taken on the current kernel source."""
+def kernel_traffic(key):
+    """DRAM bytes per launch of the kernel `key` from the committed ncu
+    summary (profiles/ncu_traffic.json), if it was taken on the current
+    kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = os.path.join(ROOT, "paper_2001_02327_gb300", "csrc", "mg_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    ent = d.get(f"{form}/{name}")
-    if not ent or ent.get("csrc_sha256") != sha:
+    ent = d.get(key)
+    if not ent or ent.get("csrc_sha256") != kernel_source_sha():
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+def kernel_source_sha():
+    """sha256 over the CUDA sources of the solver (sorted file names)."""
+    import glob
+    hs = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2001_02327_gb300", "csrc", "mg_*.cu"))):
+        hs.update(open(f, "rb").read())
+    return hs.hexdigest()
+
+
+def _oracle_solve(args):
+    """One oracle solve of the benchmark workload (a worker of the all-core
+    baseline; builds its own inputs, returns its wall time)."""
+    from oracle import oracle as O
+    H, inp = make_workload()
+    t0 = time.perf_counter()
+    O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(procs):
+    """Throughput of the oracle on every host core: `procs` independent solves
+    of the workload at once, one per process (spawned, so that no process
+    inherits a CUDA context).  Returns (zones/s, wall seconds)."""
+    import multiprocessing as mp
+    H, _ = make_workload()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_solve, range(procs))           # warm-up: imports, library load
+        t0 = time.perf_counter()
+        pool.map(_oracle_solve, range(procs))
+        wall = time.perf_counter() - t0
+    return procs * H.zones() / wall, wall
 
 
 def cpu_baseline(H, inp):
@@ -282,8 +323,145 @@ def cpu_baseline(H, inp):
     t0 = time.perf_counter()
     O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
     dt = time.perf_counter() - t0
+    procs = os.cpu_count() or 1
+    v_all, wall = oracle_all_cores(procs)
     return {"value": H.zones() / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full solve of the workload (all 4 levels, forces included), {dt:.2f} s, single thread"}
+            "sample": f"one full solve of the workload (all 4 levels, forces included), {dt:.2f} s, single thread",
+            "all_cores": {"value": v_all, "unit": UNIT, "cores": procs,
+                          "sample": f"{procs} independent full solves at once, one process per core, {wall:.2f} s"}}
+
+
+# ---------------------------------------------------------------------------
+# measured rooflines: the finest multigrid level's smoothing, timed as the
+# solve graph launches it, and the whole solve's algorithmic bytes
+# ---------------------------------------------------------------------------
+SMOOTH_KINDS = ("smooth_colour_finest", "smooth_wave_finest")
+
+
+def kernel_roofline(mg, h, level, prof_per_step, ms_per_step, workload, traffic_key, sustained):
+    """Roofline of the finest multigrid level's FP32 smoothing of refinement
+    level `level`: per-launch time from mg_time_smoothing (launches captured
+    back to back in one CUDA graph with programmatic dependent launch, as the
+    solve runs them), algorithmic bytes from the library (1.5 words per
+    active cell per one-colour launch, 3 per plane-marching launch), the
+    launches per step from the host-loop profile of the same plan."""
+    us, by = mg.mg_time_smoothing(h, 0, level, 0, 20)
+    kind = next((k for k in SMOOTH_KINDS if k in prof_per_step), None)
+    per_step = prof_per_step[kind][0] if kind else 0.0
+    peak, src = measured_peaks()
+    achieved = by / (us * 1e-6) / 1e9
+    traffic = kernel_traffic(f"{traffic_key}/{kind}") if kind else None
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_over_algorithmic": round(traffic / by, 3) if traffic else None,
+            "kernel": kind or "smooth", "workload": workload, "launch_us": round(us, 3), "bytes_per_launch": by,
+            "byte_model": "active cells x 4 B x (1.5 per one-colour launch: Phi read, half of f read, half of Phi "
+                          "written; 3 per plane-marching launch of nu sweeps: Phi and f read once, Phi written once)",
+            "timing": "mg_time_smoothing: 20 launches in one CUDA graph with programmatic dependent launch, "
+                      "CUDA events around 5 replays on the solver's stream",
+            "launches_per_step": per_step, "kernel_ms_per_step": round(per_step * us * 1e-3, 4),
+            "ms_per_step": round(ms_per_step, 4),
+            "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" + ("; timed alone" if not sustained else "")}
+
+
+def solve_bytes(H, stats, precision):
+    """Algorithmic DRAM bytes of one step (set_density + solve + potential and
+    forces out): per refinement level, 7.1 words per active cell per V-cycle
+    (Phi and f read and Phi written going down and coming up, a quarter word
+    of transfer, 8/7 for the coarse multigrid levels), 40 B per cell per FP64
+    defect-correction step of the mixed form (residual and accumulation), and
+    64 B per cell of the level for the density in and the outputs."""
+    w = 4 if precision == "mixed" else 8
+    total = 0.0
+    for l in range(H.num_levels):
+        M3 = float(H.n[l] + 2) ** H.dim
+        st = stats[0][l]
+        total += 7.1 * w * M3 * st["cycles"] + 64.0 * float(H.n[l]) ** H.dim
+        if precision == "mixed":
+            total += 40.0 * M3 * st["outer_steps"]
+    return total
+
+
+def whole_solve_roofline(H, stats, precision, ms):
+    by = solve_bytes(H, stats, precision)
+    peak, src = measured_peaks()
+    achieved = by / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "bytes_per_step": by, "ms_per_step": round(ms, 4),
+            "byte_model": "per level: 7.1 words x active cells x V-cycles (FP32 words in the mixed form) + 40 B x "
+                          "active cells x defect-correction steps (mixed) + 64 B x cells of Omega (density in, "
+                          "potential and forces out)", "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}
+
+
+def scale_case(mg, torch, stream, flush, steps, warmup, tune_cache, inner_cycles, inner_max):
+    """The DRAM-resident workload: 4 nested 256^3 levels, 8 compact spheres;
+    mixed form (the reported one) and FP64, set_density + solve (potential
+    and forces written by mg_solve), CUDA events, L2 flushed between steps."""
+    H = I.config_3d_spheres(256, 4, 8)
+    inp = I.level_inputs(H)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_in = [{k: dev(v) for k, v in d.items()} for d in inp]
+    F = [torch.empty((3,) + (m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
+    P = [torch.empty((m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
+    out = {}
+    for name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60,
+                                                                 rel_tol=TOL, precision=prec,
+                                                                 inner_cycles=inner_cycles,
+                                                                 inner_max=inner_max, stream=stream))
+        try:
+            if prec == mg.MG_MIXED:
+                mg.mg_autotune(h, tune_cache)
+            for l in range(H.num_levels):
+                mg.mg_set_outputs(h, 0, l, P[l], F[l])
+
+            def step():
+                mg.mg_set_density(h, 0, 0, d_in[0]["rho"], d_in[0]["bc_rho"], d_in[0]["bc_phi"])
+                for l in range(1, H.num_levels):
+                    mg.mg_set_density(h, 0, l, d_in[l]["rho"])
+                return mg.mg_solve(h, 1)[1]
+
+            for _ in range(warmup):
+                st = step()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                a.record(stream)
+                st = step()
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(b) for a, b in ev]
+            t = statistics.median(ms)
+            ep = ef = 0.0
+            for l in range(H.num_levels):
+                X = H.centres(l, 0)
+                pa, fa = H.potential(X), H.force(X)
+                ep = max(ep, float(np.max(np.abs(P[l].cpu().numpy() - pa)) / np.max(np.abs(pa))))
+                ef = max(ef, float(np.max(np.abs(np.moveaxis(F[l].cpu().numpy(), 0, -1) - fa)) / np.max(np.abs(fa))))
+            res = {"zones_per_s": H.zones() / (t * 1e-3), "ms_per_step": t, "ms_min": min(ms),
+                   "cycles_per_level": [st[0][l]["cycles"] for l in range(H.num_levels)],
+                   "outer_steps_per_level": [st[0][l]["outer_steps"] for l in range(H.num_levels)],
+                   "max_rel_res": max(st[0][l]["rel_res"] for l in range(H.num_levels)),
+                   "max_rel_err_phi_vs_closed_form": ep, "max_rel_err_F_vs_closed_form": ef,
+                   "whole_solve_roofline": whole_solve_roofline(H, st, name, t)}
+            if prec == mg.MG_MIXED:
+                res["plan_finest"] = mg.mg_tuning(h, 0, 0)[0][:8]
+                mg.mg_profile(h, 1)
+                step()
+                prof = mg.mg_profile_read(h)
+                mg.mg_profile(h, 0)
+                res["kernel_roofline"] = kernel_roofline(mg, h, 0, prof, t, "4 nested 256^3 levels (finest "
+                                                         "multigrid level 258^3, 69 MB per FP32 array)",
+                                                         "scale_4x256cubed", sustained=True)
+            out[name] = res
+        finally:
+            mg.mg_destroy(h)
+    out["workload"] = ("3D, 4 nested 256^3 levels on [-1,1]^3, 8 compact spheres (m=3) with centres in the finest "
+                       "box, radii U[0.02,0.1]x2, masses U[0.5,2]; V(2,2) to 1e-10; Eq. 2 forces")
+    out["zones_per_solve"] = H.zones()
+    return out
 
 
 def run_ours(args):
@@ -307,6 +485,7 @@ def run_ours(args):
     if not args.no_learned:
         net = train_guess_network(torch)
         plans.append(("mixed_learned", mg.MG_MIXED, net))
+    kroof = None
     for name, prec, unet in plans:
         r = Runner(mg, torch, H, inp, stream, prec, args.tune_cache, unet, not args.no_autotune, args.inner_max,
                    args.inner_cycles, args.forces_call)
@@ -319,24 +498,30 @@ def run_ours(args):
             torch.cuda.nvtx.range_pop()
             results[name] = r.results()
             cyc = [r.stats[0][l]["cycles"] for l in range(H.num_levels)]
+            stats = r.stats
             if ws > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
-            sampler = ClockSampler(gpu_ident(torch, local)) if name == "fp64" else None
-            if sampler:
-                sampler.start()
+            sampler = ClockSampler(gpu_ident(torch, local))
+            sampler.start()
             times = time_device(r, torch, args.steps, args.warmup, flush)
-            clocks = sampler.stop() if sampler else None
+            clocks = sampler.stop()
             total = max_over_ranks(sum(times), device="cuda")
             ms = total / args.steps
             e2e_ms = max_over_ranks(time_e2e(r, torch, max(3, args.steps // 2)), device="cuda")
             h2d, d2h = r.io_bytes()
-            prof = profile_pass(r, torch, max(3, min(args.steps, 10)))
             nprof = max(3, min(args.steps, 10))
+            prof = profile_pass(r, torch, nprof)
+            per_step = {k: (v[0] / nprof, v[1] / nprof, v[2] / nprof) for k, v in prof.items()}
             forms[name] = {"value": job_throughput(H.zones(), ms, ws), "ms_per_step": ms,
                            "ms_min": min(times), "cycles": cyc, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h,
-                           "prof": {k: (v[0] / nprof, v[1] / nprof, v[2] / nprof) for k, v in prof.items()},
-                           "clocks": clocks}
+                           "prof": per_step, "clocks": clocks,
+                           "whole_solve": whole_solve_roofline(H, stats, "fp64" if prec == mg.MG_FP64 else "mixed",
+                                                               ms)}
+            if name == "mixed":
+                kroof = kernel_roofline(mg, r.h, 0, per_step, ms, "4 nested 64^3 levels (finest multigrid level "
+                                        "66^3, 1.1 MB per FP32 array: L2-resident, launch-latency bound)",
+                                        "bench_4x64cubed", sustained=True)
         finally:
             r.close()
 
@@ -361,22 +546,9 @@ def run_ours(args):
         U.mg_unet_destroy(net)
     fb = forms[best]
 
-    # roofline of the dominant kernel of the reported form: the profiler keeps
-    # the finest multigrid level's smoothing apart, the kernel is the same one
-    by_kernel = {}
-    for k, v in fb["prof"].items():
-        k = "smooth_colour" if k == "smooth_colour_finest" else k
-        by_kernel[k] = [a + b for a, b in zip(by_kernel.get(k, (0, 0.0, 0.0)), v)]
-    kname, (kl, kms, kbytes) = max(by_kernel.items(), key=lambda kv: kv[1][1])
-    launch_ms = kms / kl
-    per_launch_bytes = kbytes / kl
-    peak, peak_src = measured_peaks()
-    achieved = per_launch_bytes / (launch_ms * 1e-3) / 1e9
-    traffic = kernel_traffic(kname, best)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
-                "launch_us": round(launch_ms * 1e3, 2), "bytes_per_launch": per_launch_bytes,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
+    # the DRAM-resident workload, where a fraction of the HBM roofline means something
+    scale = None if args.no_scale else scale_case(mg, torch, stream, flush, max(3, min(args.steps, 10)), 2,
+                                                    args.tune_cache, args.inner_cycles, args.inner_max)
 
     launches = int(round(sum(v[0] for v in fb["prof"].values()))) * args.steps
     out = {
@@ -391,17 +563,21 @@ def run_ours(args):
                    "mixed_inner_cycles": f"{args.inner_cycles}, then chosen per step up to {args.inner_max}"
                    if args.inner_max else f"{args.inner_cycles} per step"},
         "forms": {k: {"zones_per_s": v["value"], "ms_per_step": v["ms_per_step"], "cycles_per_level": v["cycles"],
-                      "kernels": {kk: {"launches": round(vv[0], 1), "ms": round(vv[1], 4)} for kk, vv in v["prof"].items()}}
+                      "whole_solve_roofline": v["whole_solve"],
+                      "kernels_host_loop_profile": {kk: {"launches": round(vv[0], 1), "ms": round(vv[1], 4)}
+                                                    for kk, vv in v["prof"].items()}}
                   for k, v in forms.items()},
         "mixed_error_vs_fp64_over_discretisation": worst,
         "form_error_vs_fp64_over_discretisation": errors,
         "e2e": {"value": job_throughput(H.zones(), fb["e2e_ms"], ws), "unit": UNIT, "h2d_bytes_per_step": fb["h2d"],
                 "d2h_bytes_per_step": fb["d2h"]},
         "gpu_launches": launches,
-        "roofline": roofline,
-        "roofline_dram_resident": dram_resident_roofline(mg, torch),
-        "clocks": forms["fp64"]["clocks"],
+        "roofline": kroof,
+        "clocks": fb["clocks"],
     }
+    if scale is not None:
+        out["scale_4x256cubed"] = scale
+        out["roofline_dram_resident"] = scale["mixed"].get("kernel_roofline")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(H, inp)
     if rank == 0:
@@ -427,61 +603,36 @@ def train_guess_network(torch):
     return net
 
 
-def dram_resident_roofline(mg, torch):
-    """Bandwidth of the FP32 smoothing kernel where it meets DRAM: one 3D level
-    of n = 254 (258^3 arrays, 69 MB each in FP32: beyond L2), two mixed-
-    precision cycles under the library's per-launch CUDA-event profile;
-    algorithmic bytes (2 words per active cell and colour) over the summed
-    times of the finest multigrid level's smoothing launches."""
-    n = 254
-    rng = np.random.default_rng(I.BASE_SEED + 254)
-    H = I.Hierarchy(3, [n], [(0.0, 0.0, 0.0)], 1.0 / n, 1.0, [], f"level{n}")
-    dev = lambda a: torch.from_numpy(a).cuda()
-    rho, bcr, bcp = (dev(rng.standard_normal((k,) * 3)) for k in (n, n + 2, n + 4))
-    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(max_cycles=2, rel_tol=0.0, precision=mg.MG_MIXED,
-                                                             inner_cycles=1))
-    try:
-        mg.mg_set_density(h, 0, 0, rho, bcr, bcp)
-        mg.mg_solve(h, 1, allow_noconv=True)                    # warm-up
-        mg.mg_set_density(h, 0, 0, rho, bcr, bcp)
-        mg.mg_profile(h, 1)
-        mg.mg_solve(h, 1, allow_noconv=True)
-        prof = mg.mg_profile_read(h)
-        mg.mg_profile(h, 0)
-    finally:
-        mg.mg_destroy(h)
-    launches, ms, nbytes = prof["smooth_colour_finest"]
-    peak, src = measured_peaks()
-    achieved = nbytes / (ms * 1e-3) / 1e9
-    return {"kernel": "smooth_colour_finest (FP32)", "workload": "one 3D level n=254, 2 mixed cycles", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "launches": launches, "traffic": kernel_traffic("smooth_colour_finest", "level254_mixed"),
-            "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
-            "timing": "per-launch CUDA events (each pair adds about 1 us to a launch of about 43 us)"}
-
-
 def run_reference(args):
+    """The CPU FP64 oracle, as it stands, on every host core: each step is
+    one full solve of the workload per core, in parallel processes
+    (independent solves; the oracle itself is single-threaded)."""
+    import multiprocessing as mp
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
-    H, inp = make_workload()
-    for _ in range(args.warmup):
-        O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.solve_hierarchy(H, inp, NU[0], NU[1], 60, TOL)
-    dt = (time.perf_counter() - t0) / args.steps
-    v = H.zones() / dt
-    sample = "one full solve of the workload per step (all 4 levels, forces included), single thread"
+    H, _ = make_workload()
+    procs = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_solve, range(procs))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_solve, range(procs))
+        dt = (time.perf_counter() - t0) / args.steps
+    v = procs * H.zones() / dt
+    sample = (f"{procs} independent full solves of the workload per step (all 4 levels, forces included), one "
+              f"single-threaded process per host core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form density and boundary potential)",
         "config": {"workload": WORKLOAD, "zones_per_solve": H.zones(), "levels": H.num_levels, "n": 64,
-                   "nu": list(NU), "rel_tol": TOL, "form": "oracle"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                   "nu": list(NU), "rel_tol": TOL, "form": "oracle", "solves_per_step": procs},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -513,6 +664,28 @@ def run_level_case(args):
             dt = time.perf_counter() - t0
         print(json.dumps({"case": f"level n={n}", "precision": args.precision, "cycles": st[0][0]["cycles"],
                           "ms": dt * 1e3, "rel_res": st[0][0]["rel_res"]}))
+    finally:
+        mg.mg_destroy(h)
+
+
+def run_smoothing_case(args):
+    """The finest multigrid level's FP32 smoothing of one 3D level of n cells
+    per edge (mixed precision, the library's default plan unless MG_WAVE /
+    MG_WAVE_PLAN choose the plane-marching sweeps), timed by mg_time_smoothing
+    with `--launches` launches.  For profiler captures (under MG_SOLVE_GRAPH=0
+    the launches run without a graph, where a profiler sees them); prints one
+    line, not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    n = args.level_n
+    H = I.Hierarchy(3, [n], [(0.0, 0.0, 0.0)], 1.0 / n, 1.0, [], f"level{n}")
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=NU[0], nu_post=NU[1], precision=mg.MG_MIXED))
+    try:
+        us, by = mg.mg_time_smoothing(h, 0, 0, 0, args.launches)
+        print(json.dumps({"case": f"smoothing, finest multigrid level of a {n}^3 level", "plan": mg.mg_tuning(h, 0, 0)[0][0],
+                          "us_per_launch": us, "bytes_per_launch": by, "GB_per_s": by / us / 1e3}))
     finally:
         mg.mg_destroy(h)
 
@@ -794,6 +967,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="leave out the mixed + learned-guess form")
+    ap.add_argument("--no-scale", action="store_true", help="leave out the 4x256^3 DRAM-resident workload")
     ap.add_argument("--inner-cycles", type=int, default=3,
                     help="mixed forms: FP32 V-cycles of the first defect-correction step (of every step "
                          "with --inner-max 0)")
@@ -807,7 +981,9 @@ def main():
                     help="keep the default launch plan (a fixed plan for profiler captures)")
     ap.add_argument("--samples", type=int, default=256, help="learned case: training samples")
     ap.add_argument("--train-steps", type=int, default=1500, help="learned case: training steps")
-    ap.add_argument("--case", default="bench", choices=["bench", "level", "batch", "scale", "unet", "learned", "2d"],
+    ap.add_argument("--launches", type=int, default=4, help="smoothing case: launches per timing")
+    ap.add_argument("--case", default="bench",
+                    choices=["bench", "level", "smoothing", "batch", "scale", "unet", "learned", "2d"],
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
@@ -820,6 +996,8 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.case == "level":
         run_level_case(args)
+    elif args.case == "smoothing":
+        run_smoothing_case(args)
     elif args.case == "batch":
         run_batch_case(args)
     elif args.case == "scale":
