@@ -563,3 +563,33 @@ int or_mg_residual(int dim, int M, int L, const double *phi, const double *f, do
     residual(dim, &lv[L], phi, f, r);
     return lv[L].N;
 }
+
+/* Test hook: the restriction of Sec. 2.3 step 5 from multigrid level L to
+ * L + 1 of a Gamma of M cells per edge: rf is (N^L+2)^d, fc (N^{L+1}+2)^d (its
+ * active cells are written).  Returns N^{L+1}, or -1 if there is no level
+ * L + 1. */
+int or_mg_restrict(int dim, int M, int L, const double *rf, double *fc)
+{
+    or_mglev lv[OR_MAX_MG];
+    int nL;
+    make_levels(M, 1.0, lv, &nL);
+    if (L < 0 || L + 1 >= nL)
+        return -1;
+    restrict_avg(dim, &lv[L], rf, &lv[L + 1], fc);
+    return lv[L + 1].N;
+}
+
+/* Test hook: the prolongation and correction of Sec. 2.3 step 10 from
+ * multigrid level L + 1 to L: the ghost layer of phic ((N^{L+1}+2)^d) is
+ * filled by the rule of Sec. 2.4, then P(phic) is added to the active cells of
+ * phif ((N^L+2)^d).  Returns N^{L+1}, or -1 if there is no level L + 1. */
+int or_mg_prolong(int dim, int M, int L, double *phic, double *phif)
+{
+    or_mglev lv[OR_MAX_MG];
+    int nL;
+    make_levels(M, 1.0, lv, &nL);
+    if (L < 0 || L + 1 >= nL)
+        return -1;
+    prolong_add(dim, &lv[L + 1], phic, &lv[L], phif);
+    return lv[L + 1].N;
+}

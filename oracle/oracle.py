@@ -61,6 +61,10 @@ def lib():
         L.or_fill_ghosts.restype = C.c_int
         L.or_mg_residual.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
         L.or_mg_residual.restype = C.c_int
+        L.or_mg_restrict.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+        L.or_mg_restrict.restype = C.c_int
+        L.or_mg_prolong.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+        L.or_mg_prolong.restype = C.c_int
         _lib = L
     return _lib
 
@@ -70,6 +74,22 @@ def mg_sizes(M):
     buf = np.zeros(64, dtype=np.int32)
     k = lib().or_mg_sizes(int(M), buf, 64)
     return [int(v) for v in buf[:k]]
+
+
+def mg_restrict(dim, M, L, rf):
+    """The restriction of Sec. 2.3 step 5 from multigrid level L to L+1 of a
+    Gamma of M cells (test hook): returns the (N^{L+1}+2)^d coarse array."""
+    Nc = mg_sizes(M)[L + 1]
+    fc = np.zeros((Nc + 2,) * dim)
+    assert lib().or_mg_restrict(dim, M, L, np.ascontiguousarray(rf, dtype=np.float64), fc) == Nc
+    return fc
+
+
+def mg_prolong(dim, M, L, phic, phif):
+    """Prolongation and correction of Sec. 2.3 step 10 from level L+1 to L
+    (test hook): phic's ghost layer is filled by the rule of Sec. 2.4, then
+    phif (modified in place) += P(phic) on its active cells."""
+    assert lib().or_mg_prolong(dim, M, L, phic, phif) == phic.shape[0] - 2
 
 
 def level_solve(dim, n, h, phi, rho, fourpiG, nu_pre=2, nu_post=1, max_cycles=50, rel_tol=1e-10, stop=0,

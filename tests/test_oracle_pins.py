@@ -636,3 +636,90 @@ def test_patch_tree_validation():
     bad = I.Hierarchy(3, H.n, H.lo, H.h0, H.G, H.sources, parents=[-1, 0, 0, 3])
     with pytest.raises(AssertionError):
         bad.validate()
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3 steps 5 and 10 / Appendix A: restriction and prolongation, directly
+# --------------------------------------------------------------------------
+def _centres(M, L, N):
+    """Cell centres of multigrid level L (ghosts included) in the normalised
+    coordinate of Sec. 2.2 (Gamma = [0, 1])."""
+    return (np.arange(N + 2) - 0.5) * (2.0 ** L / M)
+
+
+def _grid_field(dim, x, fn):
+    g = np.meshgrid(*([x] * dim), indexing="ij")   # g[0] slowest (z in 3D) ... g[-1] = x
+    return fn(*g[::-1])                               # fn(x, y[, z])
+
+
+@pytest.mark.parametrize("M,L", [(66, 0), (66, 1), (66, 2), (10, 1), (50, 1), (34, 2), (99, 0), (65, 0)])
+def test_restriction_of_multilinear_fields(oracle, M, L):
+    """The 2^d children of a coarse cell sit symmetrically about its centre,
+    so their average of a multilinear field is the field at the coarse centre
+    (Appendix A); a coarse cell whose children run past the fine level's last
+    cell gets 2^-d times the children it has (reading R9: a constant field
+    gives 1/2 per missing direction)."""
+    sizes = oracle.mg_sizes(M)
+    Nf, Nc = sizes[L], sizes[L + 1]
+    xf, xc = _centres(M, L, Nf), _centres(M, L + 1, Nc)
+    rng = _rng(60 + L)
+    for dim in (2, 3):
+        a = rng.standard_normal(8)
+        if dim == 2:
+            fn = lambda x, y: a[0] + a[1] * x + a[2] * y + a[3] * x * y
+        else:
+            fn = lambda x, y, z: (a[0] + a[1] * x + a[2] * y + a[3] * z + a[4] * x * y + a[5] * y * z
+                                  + a[6] * x * z + a[7] * x * y * z)
+        fc = oracle.mg_restrict(dim, M, L, _grid_field(dim, xf, fn))
+        want = _grid_field(dim, xc, fn)
+        full = min(Nc, Nf // 2)                        # coarse cells 1..full have both children per axis
+        inner = (slice(1, full + 1),) * dim
+        assert np.allclose(fc[inner], want[inner], rtol=0, atol=1e-13)
+        if full < Nc:                                  # Nf odd: the last coarse cell has one child per axis
+            one = oracle.mg_restrict(dim, M, L, np.ones((Nf + 2,) * dim))
+            last = (Nc,) * dim
+            assert one[last] == 0.5 ** dim
+            edge = tuple([1] * (dim - 1) + [Nc])
+            assert one[edge] == 0.5
+
+
+@pytest.mark.parametrize("M,L", [(66, 0), (66, 1), (66, 2), (10, 0), (10, 1), (50, 1), (34, 2), (99, 0)])
+def test_prolongation_exact_on_trilinear_fields_through_the_ghost_rule(oracle, M, L):
+    """Prolongation and correction add the bi/trilinear interpolation with the
+    3/4-1/4 weights of Appendix A, coarse ghosts filled by the rule of Sec.
+    2.4 first: exact for multilinear fields, at the left faces for x y [z]
+    (zero on x_MG = 0: the odd reflection is exact) and at the right faces for
+    (1-x)(1-y)[(1-z)] (zero on x_MG = 1: the linear extrapolation, or the
+    tie rule -Phi_{N-1}, is exact); (66, 1) and (10, 1) prolong from a tie
+    level, (66, 2) has a fine cell beyond the last coarse cell's children."""
+    sizes = oracle.mg_sizes(M)
+    Nf, Nc = sizes[L], sizes[L + 1]
+    xf, xc = _centres(M, L, Nf), _centres(M, L + 1, Nc)
+    rng = _rng(70 + L)
+    i = np.arange(1, Nf + 1)
+    near = (i + 1) // 2
+    far = np.where(i % 2 == 1, near - 1, near + 1)
+    for dim in (2, 3):
+        for side, g, bad in (("left", lambda t: t, Nc + 1), ("right", lambda t: 1.0 - t, 0)):
+            fn = (lambda x, y: g(x) * g(y)) if dim == 2 else (lambda x, y, z: g(x) * g(y) * g(z))
+            phic = _grid_field(dim, xc, fn)
+            ring = np.ones(phic.shape, dtype=bool)
+            ring[(slice(1, Nc + 1),) * dim] = False
+            phic[ring] = 12345.0                         # the rule must overwrite every ghost
+            phif0 = rng.standard_normal((Nf + 2,) * dim)
+            phif = phif0.copy()
+            oracle.mg_prolong(dim, M, L, phic, phif)
+            ok1 = (near != bad) & (far != bad)           # stencil away from the other side's ghosts
+            ok = np.ones((Nf,) * dim, dtype=bool)
+            for a in range(dim):
+                shape = [1] * dim
+                shape[dim - 1 - a] = Nf
+                ok &= ok1.reshape(shape)
+            act = (slice(1, Nf + 1),) * dim
+            got = (phif - phif0)[act]
+            want = _grid_field(dim, xf, fn)[act]
+            assert ok.sum() > 0.25 * ok.size
+            assert np.allclose(got[ok], want[ok], rtol=0, atol=1e-13), (side, dim)
+            # cells next to the exact side use its ghosts: they are among the checked ones
+            first = (0,) * dim if side == "left" else (Nf - 1,) * dim
+            assert ok[first]
