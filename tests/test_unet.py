@@ -53,6 +53,108 @@ def test_reference_gradient_by_finite_differences():
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd)) + 1e-7, (i, fd, g[i])
 
 
+def test_reference_tap_layout_by_hand():
+    """Flat weights [27][Cin][Cout], tap = (dz+1)*9 + (dy+1)*3 + (dx+1), the
+    input read at voxel + (dz, dy, dx) (arrays indexed [z][y][x]): a unit
+    weight at one tap moves a point input to the voxel that reads it."""
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as Fn
+    from oracle import unet_ref as R
+    n = 6
+    for (dz, dy, dx) in ((0, 0, 1), (1, 0, 0), (0, -1, 0), (-1, 1, -1)):
+        tap = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+        p = np.zeros(R.param_count())
+        p[tap * 3 * 16 + 1 * 16 + 5] = 1.0          # conv 0: tap, cin 1 -> cout 5
+        (w, b), = R.unpack(p)[0][:1]
+        x = torch.zeros(1, 3, n, n, n, dtype=torch.float64)
+        x[0, 1, 3, 3, 3] = 1.0                      # point input at (z, y, x) = (3, 3, 3), channel 1
+        y = Fn.conv3d(x, w, b, padding=1)
+        nz = torch.nonzero(y)
+        assert nz.shape[0] == 1
+        assert tuple(nz[0].tolist()) == (0, 5, 3 - dz, 3 - dy, 3 - dx)
+
+
+def _routing_params(skip_channel):
+    """Every convolution passes one input channel through its centre tap to
+    output channel 0 (zero biases, unit 1x1 output on channel 0): the input
+    channel of the decoder convolutions picks the upsampled path (0) or the
+    skip path (skip_channel)."""
+    from oracle import unet_ref as R
+    p = np.zeros(R.param_count())
+    off = 0
+    for i, (cin, cout) in enumerate(R.CONV_DIMS):
+        ci = skip_channel(i) if i >= 6 else 0
+        p[off + 13 * cin * cout + ci * cout + 0] = 1.0
+        off += 27 * cin * cout + cout
+    p[off + 0] = 1.0                                 # 1x1 output weight of channel 0
+    return p
+
+
+def test_reference_wiring_by_hand():
+    """Through the whole network with pass-through weights: taking channel 0
+    of every decoder input (the upsampled coarse path) gives each voxel the
+    mean of its 8x8x8 block (three 2x pools, three nearest 2x upsamplings);
+    taking the skip channels instead gives the input itself at every scale."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet_ref as R
+    n = 16
+    rng = np.random.default_rng(21)
+    rho = torch.from_numpy(rng.uniform(0.5, 1.5, size=(1, n, n, n)))
+    phi = torch.from_numpy(rng.uniform(-1, 1, size=(1, n, n, n)))
+    res = torch.from_numpy(rng.uniform(-1, 1, size=(1, n, n, n)))
+    x0 = rho / phi.abs().max()                        # channel 0 as the network sees it (frho = 1)
+    # decoder inputs: [up(low) (Cu channels), skip]: Cu = 64, 32, 16 for convs 6, 7, 8
+    y_up, _ = R.forward(torch.from_numpy(_routing_params(lambda i: 0)), rho, phi, res, [1.0])
+    blk = x0[0].reshape(2, 8, 2, 8, 2, 8).mean(dim=(1, 3, 5))
+    want = blk.repeat_interleave(8, 0).repeat_interleave(8, 1).repeat_interleave(8, 2)
+    assert torch.allclose(y_up[0], want, rtol=0, atol=1e-14)
+    # conv 8 from the first skip channel (index 16): s0, the input at full resolution
+    y_skip, _ = R.forward(torch.from_numpy(_routing_params(lambda i: {6: 64, 7: 32, 8: 16}[i])), rho, phi, res, [1.0])
+    assert torch.allclose(y_skip[0], x0[0], rtol=0, atol=1e-14)
+
+
+def _dyadic_case(seed, n=8, B=1):
+    """Inputs and parameters on coarse dyadic grids (integers, eighths) whose
+    every sum the module forms is exact in FP32: max |phi| = max |resid| = 8
+    (power-of-two scales), frho = 1, targets (phi_true - phi)/(8 n^2/16)
+    integer; sparse integer weights and biases."""
+    from oracle import unet_ref as R
+    rng = np.random.default_rng(I.BASE_SEED + 700 + seed)
+    sh = (B, n, n, n)
+    rho = rng.integers(-4, 5, size=sh).astype(np.float64)
+    phi = rng.integers(-7, 8, size=sh).astype(np.float64)
+    phi[:, 0, 0, 0] = 8.0
+    res = rng.integers(-7, 8, size=sh).astype(np.float64)
+    res[:, 1, 2, 3] = -8.0
+    scale = 8.0 * n * n / 16.0
+    tru = phi + scale * rng.integers(-2, 3, size=sh)
+    frho = np.ones(B)
+    p = np.zeros(R.param_count(), dtype=np.float32)
+    off = 0
+    for cin, cout in R.CONV_DIMS:
+        nw = 27 * cin * cout
+        d = min(0.5, 2.5 / (27 * cin))
+        p[off:off + nw] = rng.choice([-1.0, 0.0, 1.0], size=nw, p=[d / 2, 1 - d, d / 2])
+        p[off + nw:off + nw + cout] = rng.choice([0.0, 1.0], size=cout)
+        off += nw + cout
+    p[off:off + 16] = rng.choice([-1.0, 1.0], size=16)
+    return rho, phi, res, tru, frho, p
+
+
+def test_dyadic_case_is_exact_in_fp32():
+    """The emulated forward pass of the dyadic case gives the same values in
+    float32 as in float64: every sum it forms is exact, so any order of
+    summation (the module's FP32 tensor-core accumulation) gives them too."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet_ref as R
+    rho, phi, res, tru, frho, p = _dyadic_case(0)
+    T = torch.from_numpy
+    y64, _ = R.forward(T(p.astype(np.float64)), T(rho), T(phi), T(res), frho, emulate=True)
+    y32, _ = R.forward(T(p), T(rho).float(), T(phi).float(), T(res).float(), frho, emulate=True)
+    assert torch.equal(y64.float(), y32)
+    assert (y64 != 0).float().mean() > 0.2          # the case exercises the network, not a zero output
+
+
 # --------------------------------------------------------------------------
 # GPU
 # --------------------------------------------------------------------------
@@ -189,3 +291,67 @@ def test_learned_guess_in_solver_keeps_accuracy(un):
     assert np.abs(rr[inner]).max() > 1e3 * np.abs(R.residual_h2(torch.from_numpy(sol1[None]),
                                                                torch.from_numpy(inp[1]["rho"][None]), fr)
                                                   .numpy()[0][inner]).max()
+
+
+@pytest.mark.gpu
+def test_forward_and_gradient_elementwise_dyadic(un):
+    """Element-wise parity on the dyadic case: the forward output equals the
+    BF16-emulating float64 reference bit for bit (every sum exact, so only a
+    wrong tap, layout, rounding point or wiring could differ); every weight
+    and bias gradient lies within the FP32 summation bound of its terms,
+    |g - g_ref| <= V 2^-24 sum |terms| (V = voxels summed), and the loss
+    within the same bound."""
+    import torch
+    from oracle import unet_ref as R
+    B, n = 1, 8
+    rho, phi, res, tru, frho, p = _dyadic_case(0, n, B)
+    u = un.mg_unet_create(n, B, seed=0)
+    try:
+        un.mg_unet_set_params(u, p)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        y = un.mg_unet_forward(u, B, n, dev(rho), dev(phi), dev(res), frho)
+        T = torch.from_numpy
+        p64 = p.astype(np.float64)
+        yr, _ = R.forward(T(p64), T(rho), T(phi), T(res), frho, emulate=True)
+        yr = yr.detach().numpy().astype(np.float32)
+        assert np.array_equal(np.asarray(y).reshape(yr.shape), yr), np.abs(np.asarray(y).reshape(yr.shape) - yr).max()
+        loss = un.mg_unet_train_step(u, B, n, dev(rho), dev(phi), dev(res), dev(tru), frho, update=False)
+        g = un.mg_unet_get_grad(u).astype(np.float64)
+        lr, gr = R.loss_and_grad(p64, T(rho), T(phi), T(res), T(tru), frho, emulate=True)
+        mag = R.weight_grad_magnitude(p64, T(rho), T(phi), T(res), T(tru), frho)
+        V = B * n ** 3
+        bound = V * 2.0 ** -24 * mag
+        bad = np.abs(g - gr) > bound
+        assert not bad.any(), (int(bad.sum()), np.flatnonzero(bad)[:10], (np.abs(g - gr) / np.maximum(mag, 1e-300)).max())
+        assert (gr != 0).mean() > 0.01                 # gradients reach the parameters
+        assert abs(loss - lr) <= V * 2.0 ** -24 * lr + 1e-30
+    finally:
+        un.mg_unet_destroy(u)
+
+
+@pytest.mark.gpu
+def test_learned_guess_gain_measured(un, capsys):
+    """What the trained network gains: trained on solver-generated samples
+    (32 samples from 16 hierarchies of three 32^3 levels with 1-8 random
+    spheres), then held-out hierarchies solved to 1e-10 in mixed precision
+    from the zero, the interpolated (Sec. 2.4) and the learned initial guess.
+    Asserted: every form converges to the same solution, and the learned
+    guess needs fewer V-cycles than the zero guess; printed: V-cycles and wall
+    time of all three (the measured comparison with the interpolated guess)."""
+    import torch
+    from paper_2001_02327_gb300 import learned as LR
+    data = LR.make_samples(torch, 32, n=32, seed0=I.BASE_SEED + 6000, levels=3)
+    net = un.mg_unet_create(32, 4, seed=3)
+    try:
+        losses = LR.train(torch, net, data, steps=300, batch=4, lr=1e-3)
+        assert np.mean(losses[-30:]) < 0.5 * np.mean(losses[:30])
+        held = [LR.random_nested(I.BASE_SEED + 9000 + k, 32, 3) for k in range(3)]
+        ev = LR.evaluate(torch, net, held, reps=3)
+    finally:
+        un.mg_unet_destroy(net)
+    with capsys.disabled():
+        print("\nlearned-guess evaluation (3 held-out hierarchies of 3 x 32^3, mixed, to 1e-10): " +
+              ", ".join(f"{k}: {v['cycles']} V-cycles, {v['ms']:.2f} ms" for k, v in ev.items()))
+    for k in ("interp", "learned"):
+        assert ev[k]["max_rel_diff_vs_zero_guess"] < 1e-8, (k, ev[k])
+    assert ev["learned"]["cycles"] < ev["zero"]["cycles"], ev
