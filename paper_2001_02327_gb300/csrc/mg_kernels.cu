@@ -622,7 +622,17 @@ __device__ __forceinline__ void bottom_plan_smooth(T *__restrict__ phi, const T 
         const int p = e & ((1 << kPlanCellBits) - 1);
         T *c = phi + p;
         const T s = bottom_plan_nsum<T, DIM>(c, e, sy, sz, zero);
-        *c = (s - h2 * f[p]) * pnid[t];
+        if (sizeof(T) < sizeof(double) && g.N == 1) {
+            // the coarsest level's one unknown (Sec. 2.3 step 8, an exact
+            // solve) in FP64 even inside an FP32 V-cycle: its diagonal from
+            // the ghost rule on every axis (first and last cell at once)
+            double d = mg_axis_diag(3, g) + mg_axis_diag(3, g);
+            if (DIM == 3)
+                d += mg_axis_diag(3, g);
+            *c = T(((double)s - g.h2 * (double)f[p]) / (-d));
+        } else {
+            *c = (s - h2 * f[p]) * pnid[t];
+        }
     }
 }
 
