@@ -1,0 +1,1297 @@
+// mg_box.cu -- the nested-grid multigrid solve on box (non-cubic) patches:
+// per-axis multigrid sizes with semi-coarsening (Sec. 2.2 applied to each
+// axis), the per-axis ghost rule of Sec. 2.4, the child-average restriction
+// and the 3/4-1/4 prolongation of Appendix A along the axes that coarsened,
+// the interface of Sec. 2.1 and the forces of Eq. 2.  The C ABI is in
+// include/mg_box.h; this file holds the kernels and the host engine.
+//
+// Storage: every array of a multigrid level is one block of
+// (N_z+2) x (N_y+2) x (N_x+2) cells (2D: no z), x fastest, one ghost layer per
+// side.  Multigrid level 0 of a patch is its solved region Gamma (n_a + 2
+// cells) with the outer buffer ring as the ghost layer, so its potential is
+// the patch's (n+4) block itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mg_box.h"
+#include "mg_internal.h"
+
+namespace {
+
+// Geometry of one multigrid level of a box patch, per axis (x, y, z).
+struct BoxGeom {
+    int N[3];         // active cells (z: 1 in 2D)
+    int E[3];         // storage extent N + 2 (z: 1 in 2D)
+    int L;            // multigrid level; 0: the ghost layer holds boundary data
+    int tie[3];       // centre of cell N at x_MG = 1 along this axis
+    double cR[3];     // right ghost = cR Phi_N when !tie (Sec. 2.4)
+    double ih2[3];    // 1 / h_a^2, h_a this axis's cell size on this level
+    float cRf[3], ih2f[3];
+};
+
+template <typename T> __device__ __forceinline__ T gsel(double d, float f);
+template <> __device__ __forceinline__ double gsel<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float gsel<float>(double, float f) { return f; }
+
+__device__ __forceinline__ long long box_index(const BoxGeom &g, int i, int j, int k)
+{
+    return ((long long)k * g.E[1] + j) * g.E[0] + i;
+}
+
+// The off-diagonal sum and the diagonal of cell (i, j, k)'s equation (Sec.
+// 2.3 stencil, per-axis cell sizes): per axis the two neighbours, except on
+// coarse levels where a neighbour in the ghost layer is replaced by the ghost
+// rule of Sec. 2.4 folded into the cell's own coefficient (left ghost
+// -Phi_1: -1; right ghost cR Phi_N: +cR; at a tie -Phi_{N-1}, which cancels
+// the left neighbour, or +Phi_1 when N = 1).  Axis order x, y, z.
+template <typename T, int DIM>
+__device__ __forceinline__ void box_terms(const T *__restrict__ phi, const BoxGeom &g, int i, int j, int k,
+                                          long long p, T &other, T &diag)
+{
+    const long long st[3] = {1, g.E[0], (long long)g.E[0] * g.E[1]};
+    const int id[3] = {i, j, k};
+    other = T(0);
+    diag = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const T left = phi[p - st[a]], right = phi[p + st[a]];
+        T o, self;
+        if (g.L == 0) {
+            o = left + right;
+            self = T(0);
+        } else {
+            const bool lo = id[a] == 1, hi = id[a] == g.N[a];
+            o = lo ? T(0) : left;
+            self = lo ? T(-1) : T(0);
+            if (hi) {
+                if (g.tie[a]) {
+                    if (g.N[a] >= 2)
+                        o = o + (-left);
+                    else
+                        self = self + T(1);
+                } else {
+                    self = self + gsel<T>(g.cR[a], g.cRf[a]);
+                }
+            } else {
+                o = o + right;
+            }
+        }
+        const T ih2 = gsel<T>(g.ih2[a], g.ih2f[a]);
+        other = other + o * ih2;
+        diag = diag + (self - T(2)) * ih2;
+    }
+}
+
+// cell (i, j, k) of the t-th work item of a colour pass: cells with
+// (i + j + k) & 1 == colour (2D: i + j), 1-based, x in pairs
+template <int DIM>
+__device__ __forceinline__ bool colour_cell(const BoxGeom &g, int colour, long long t, int &i, int &j, int &k)
+{
+    const int half = (g.N[0] + 1) >> 1;
+    const long long r = t / half;
+    const int ih = (int)(t - r * half);
+    j = (int)(r % g.N[1]) + 1;
+    k = DIM == 3 ? (int)(r / g.N[1]) + 1 : 0;
+    const int par = (colour - j - k) & 1;   // parity of i
+    i = 2 * ih + (par ? 1 : 2);
+    return i <= g.N[0];
+}
+
+__host__ __device__ inline long long colour_items(const BoxGeom &g, int dim)
+{
+    return (long long)((g.N[0] + 1) >> 1) * g.N[1] * (dim == 3 ? g.N[2] : 1);
+}
+
+// Red-black Gauss-Seidel, one colour (Sec. 2.3 steps 2, 6, 11): each cell of
+// the colour solves its own equation for the current neighbours.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) kx_smooth(T *__restrict__ phi, const T *__restrict__ f, BoxGeom g, int colour)
+{
+    pdl_begin();
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= colour_items(g, DIM))
+        return;
+    int i, j, k;
+    if (!colour_cell<DIM>(g, colour, t, i, j, k))
+        return;
+    const long long p = box_index(g, i, j, k);
+    T other, diag;
+    box_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
+    phi[p] = (f[p] - other) / diag;
+}
+
+// r = f - A Phi at cell (i, j, k)
+template <typename T, int DIM>
+__device__ __forceinline__ T box_resid(const T *__restrict__ phi, const T *__restrict__ f, const BoxGeom &g, int i,
+                                       int j, int k)
+{
+    const long long p = box_index(g, i, j, k);
+    T other, diag;
+    box_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
+    return f[p] - (other + diag * phi[p]);
+}
+
+// Residual of the fine level restricted to the coarse right-hand side (Sec.
+// 2.3 steps 4-5; Appendix A): coarse cell I sums the residuals of fine cells
+// 2I-1 and 2I along each axis that coarsened (a child past the fine level's
+// last cell counts zero) and of cell I along the others, x pairs first, then
+// y, then z, times 2^-k (k the coarsened axes, bit a of cmask).  Also starts
+// the coarse potential at zero (Sec. 2.3 step 6).  One thread per coarse cell.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) kx_resid_restrict(const T *__restrict__ phi, const T *__restrict__ f,
+                                                         BoxGeom gf, T *__restrict__ fc, T *__restrict__ phic,
+                                                         BoxGeom gc, int cmask, T wk)
+{
+    pdl_begin();
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long tot = (long long)gc.N[0] * gc.N[1] * (DIM == 3 ? gc.N[2] : 1);
+    if (t >= tot)
+        return;
+    const long long r = t / gc.N[0];
+    const int I = (int)(t - r * gc.N[0]) + 1;
+    const int J = (int)(r % gc.N[1]) + 1;
+    const int K = DIM == 3 ? (int)(r / gc.N[1]) + 1 : 0;
+    int c0[3], nc[3];
+    const int C[3] = {I, J, K};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (a < DIM && (cmask >> a) & 1) {
+            c0[a] = 2 * C[a] - 1;
+            nc[a] = 2 * C[a] <= gf.N[a] ? 2 : 1;
+        } else {
+            c0[a] = C[a];
+            nc[a] = 1;
+        }
+    }
+    T sz = T(0);
+    for (int dz = 0; dz < (DIM == 3 ? nc[2] : 1); dz++) {
+        T sy = T(0);
+        for (int dy = 0; dy < nc[1]; dy++) {
+            T sx = T(0);
+            for (int dx = 0; dx < nc[0]; dx++)
+                sx = sx + box_resid<T, DIM>(phi, f, gf, c0[0] + dx, c0[1] + dy, c0[2] + dz);
+            sy = sy + sx;
+        }
+        sz = sz + sy;
+    }
+    const long long pc = box_index(gc, I, J, K);
+    fc[pc] = sz * wk;
+    phic[pc] = T(0);
+}
+
+// A coarse value read through the ghost rule of Sec. 2.4, applied axis after
+// axis (x, y, z) as a ghost fill would: index 0 -> -Phi_1; N+1 -> cR Phi_N,
+// or at a tie -Phi_{N-1} (+Phi_1 when N = 1).
+template <typename T, int DIM>
+__device__ __forceinline__ T ghost_read(const T *__restrict__ phic, const BoxGeom &g, int i, int j, int k)
+{
+    int id[3] = {i, j, k};
+    T c[3] = {T(1), T(1), T(1)};
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const int N = g.N[a];
+        if (id[a] == 0) {
+            id[a] = 1;
+            c[a] = T(-1);
+        } else if (id[a] == N + 1) {
+            if (g.tie[a]) {
+                id[a] = N >= 2 ? N - 1 : 1;
+                c[a] = N >= 2 ? T(-1) : T(1);
+            } else {
+                id[a] = N;
+                c[a] = gsel<T>(g.cR[a], g.cRf[a]);
+            }
+        }
+    }
+    T v = phic[box_index(g, id[0], id[1], id[2])];
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+        v = v * c[a];
+    return v;
+}
+
+// Phi_fine += P Phi_coarse (Sec. 2.3 step 10; Appendix A): along an axis that
+// coarsened, fine cell i lies a quarter coarse cell from coarse cell
+// ceil(i/2) towards ceil(i/2) - 1 (i odd) or + 1 (i even): weights 3/4 and
+// 1/4; along the others it takes coarse cell i.  Interpolated x first, then
+// y, then z.  One thread per fine cell.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom gf, const T *__restrict__ phic,
+                                                  BoxGeom gc, int cmask)
+{
+    pdl_begin();
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long tot = (long long)gf.N[0] * gf.N[1] * (DIM == 3 ? gf.N[2] : 1);
+    if (t >= tot)
+        return;
+    const long long r = t / gf.N[0];
+    const int i = (int)(t - r * gf.N[0]) + 1;
+    const int j = (int)(r % gf.N[1]) + 1;
+    const int k = DIM == 3 ? (int)(r / gf.N[1]) + 1 : 0;
+    const int F[3] = {i, j, k};
+    int ix[3][2], nt[3];
+    T w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (a < DIM && (cmask >> a) & 1) {
+            const int near = (F[a] + 1) >> 1;
+            ix[a][0] = near;
+            ix[a][1] = (F[a] & 1) ? near - 1 : near + 1;
+            w[a][0] = T(0.75);
+            w[a][1] = T(0.25);
+            nt[a] = 2;
+        } else {
+            ix[a][0] = ix[a][1] = F[a];
+            w[a][0] = T(1);
+            w[a][1] = T(0);
+            nt[a] = 1;
+        }
+    }
+    T vz = T(0);
+    for (int cz = 0; cz < (DIM == 3 ? nt[2] : 1); cz++) {
+        T vy = T(0);
+        for (int cy = 0; cy < nt[1]; cy++) {
+            T vx = T(0);
+            for (int cx = 0; cx < nt[0]; cx++)
+                vx = vx + w[0][cx] * ghost_read<T, DIM>(phic, gc, ix[0][cx], ix[1][cy], ix[2][cz]);
+            vy = vy + (nt[1] == 2 ? w[1][cy] * vx : vx);
+        }
+        vz = vz + (DIM == 3 && nt[2] == 2 ? w[2][cz] * vy : vy);
+    }
+    phif[box_index(gf, i, j, k)] += vz;
+}
+
+constexpr int kNormBlocks = 152 * 4;   // fixed grid of the norm reduction: the same partial sums every call
+constexpr int kNormThreads = 256;
+
+// block sum in a fixed order (warp shuffles, then the warps in order)
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double ws[kNormThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0)
+        ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kNormThreads / 32; w++)
+            s += ws[w];
+    return s;
+}
+
+// ||f - A Phi||^2 over the active cells of multigrid level 0 in FP64 (Sec.
+// 2.3 step 14), per block into part[blockIdx.x].  zero_inside: the potential
+// taken as zero on the active cells (the ghost layer as stored), for ||b||.
+// Mixed precision (f32 != NULL): the residual is also the next defect, written
+// as FP32 into f32, with the FP32 correction e32 cleared.
+template <int DIM>
+__global__ void __launch_bounds__(kNormThreads) kx_resid_norm(const double *__restrict__ phi,
+                                                               const double *__restrict__ f, BoxGeom g, int zero_inside,
+                                                               double *__restrict__ part, float *__restrict__ f32,
+                                                               float *__restrict__ e32)
+{
+    pdl_begin();
+    const long long tot = (long long)g.N[0] * g.N[1] * (DIM == 3 ? g.N[2] : 1);
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / g.N[0];
+        const int i = (int)(t - r * g.N[0]) + 1;
+        const int j = (int)(r % g.N[1]) + 1;
+        const int k = DIM == 3 ? (int)(r / g.N[1]) + 1 : 0;
+        const long long p = box_index(g, i, j, k);
+        double res;
+        if (zero_inside) {
+            // only the ghost-layer neighbours (level 0: boundary data) remain
+            const long long st[3] = {1, g.E[0], (long long)g.E[0] * g.E[1]};
+            const int id[3] = {i, j, k};
+            double other = 0.0;
+            for (int a = 0; a < DIM; a++) {
+                const double left = id[a] == 1 ? phi[p - st[a]] : 0.0;
+                const double right = id[a] == g.N[a] ? phi[p + st[a]] : 0.0;
+                other = other + (left + right) * g.ih2[a];
+            }
+            res = f[p] - other;
+        } else {
+            res = box_resid<double, DIM>(phi, f, g, i, j, k);
+        }
+        if (f32) {
+            f32[p] = (float)res;
+            e32[p] = 0.0f;
+        }
+        acc += res * res;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = s;
+}
+
+// out = sum of part[0..n-1] in a fixed order; one block
+__global__ void __launch_bounds__(kNormThreads) kx_sum(const double *__restrict__ part, int n, double *out)
+{
+    pdl_begin();
+    double v = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x)
+        v += part[q];
+    const double s = block_sum(v);
+    if (threadIdx.x == 0)
+        *out = s;
+}
+
+// Phi += e on the active cells of level 0 (mixed precision: the FP32
+// correction accumulated in FP64)
+template <int DIM>
+__global__ void __launch_bounds__(256) kx_accumulate(double *__restrict__ phi, const float *__restrict__ e32, BoxGeom g)
+{
+    pdl_begin();
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long tot = (long long)g.N[0] * g.N[1] * (DIM == 3 ? g.N[2] : 1);
+    if (t >= tot)
+        return;
+    const long long r = t / g.N[0];
+    const int i = (int)(t - r * g.N[0]) + 1;
+    const int j = (int)(r % g.N[1]) + 1;
+    const int k = DIM == 3 ? (int)(r / g.N[1]) + 1 : 0;
+    const long long p = box_index(g, i, j, k);
+    phi[p] += (double)e32[p];
+}
+
+// Patch geometry for the kernels that work on the (n+4) blocks.
+struct PatchDims {
+    int n[3];     // Omega cells per axis (z: 1 in 2D)
+    int B[3];     // (n+4) block extents (z: 1 in 2D)
+};
+
+__device__ __forceinline__ void block_coords(const PatchDims &d, int dim, long long t, int s[3])
+{
+    const long long r = t / d.B[0];
+    s[0] = (int)(t - r * d.B[0]);
+    s[1] = (int)(r % d.B[1]);
+    s[2] = dim == 3 ? (int)(r / d.B[1]) : 0;
+}
+
+// ring of a storage index of the (n+4) block: 2 for Omega, 1 for the inner
+// buffer ring (Gamma minus Omega), 0 for the outer ring
+__device__ __forceinline__ int block_ring(const PatchDims &d, int dim, const int s[3])
+{
+    int ring = 2;
+    for (int a = 0; a < dim; a++) {
+        const int m = min(s[a], d.n[a] + 3 - s[a]);
+        ring = min(ring, m);
+    }
+    return ring;
+}
+
+// mg_box_set_density: Omega density into the patch's density block; patch 0
+// also the inner-ring density (from the (n+2) block bc_rho) and the outer-ring
+// potential (from the (n+4) block bc_phi), the outer ring's density zero.
+__global__ void __launch_bounds__(256) kx_place(PatchDims d, int dim, const double *__restrict__ rho,
+                                                const double *__restrict__ bc_rho, const double *__restrict__ bc_phi,
+                                                double *__restrict__ rho_blk, double *__restrict__ phi_blk)
+{
+    pdl_begin();
+    const long long tot = (long long)d.B[0] * d.B[1] * d.B[2];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= tot)
+        return;
+    int s[3];
+    block_coords(d, dim, t, s);
+    const int ring = block_ring(d, dim, s);
+    if (ring == 2) {
+        const long long q = dim == 3 ? (((long long)(s[2] - 2) * d.n[1] + (s[1] - 2)) * d.n[0] + (s[0] - 2))
+                                     : ((long long)(s[1] - 2) * d.n[0] + (s[0] - 2));
+        rho_blk[t] = rho[q];
+    } else if (ring == 1) {
+        if (bc_rho) {
+            const int e0 = d.n[0] + 2, e1 = d.n[1] + 2;
+            const long long q = dim == 3 ? (((long long)(s[2] - 1) * e1 + (s[1] - 1)) * e0 + (s[0] - 1))
+                                         : ((long long)(s[1] - 1) * e0 + (s[0] - 1));
+            rho_blk[t] = bc_rho[q];
+        }
+    } else if (bc_phi) {
+        phi_blk[t] = bc_phi[t];
+        rho_blk[t] = 0.0;
+    }
+}
+
+// Buffer rings of a child patch from its parent (Sec. 2.1; Appendix A
+// weights): bi/trilinear interpolation from the 2^d parent centres around
+// each child centre.  The parent's centre of block index p sits at
+// coordinate p, the child's block index s at off + 1.5 + (s - 1.5) / 2.
+// mode 0: potential of the outer ring, density of the inner ring, and zero
+// on Gamma (the start from which ||b|| is taken); mode 1: the interpolated
+// potential on Gamma only (the initial guess of Sec. 2.4).
+__global__ void __launch_bounds__(256) kx_interface(PatchDims dc, PatchDims dp, int dim, int o0, int o1, int o2,
+                                                    const double *__restrict__ phi_p, const double *__restrict__ rho_p,
+                                                    double *__restrict__ phi_c, double *__restrict__ rho_c, int mode)
+{
+    pdl_begin();
+    const long long tot = (long long)dc.B[0] * dc.B[1] * dc.B[2];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= tot)
+        return;
+    int s[3];
+    block_coords(dc, dim, t, s);
+    const int ring = block_ring(dc, dim, s);
+    if (mode == 1 && ring == 0)
+        return;
+    const int off[3] = {o0, o1, o2};
+    int p0[3];
+    double tw[3];
+    for (int a = 0; a < 3; a++) {
+        if (a < dim) {
+            const double q = off[a] + 1.5 + (s[a] - 1.5) * 0.5;
+            p0[a] = (int)floor(q);
+            tw[a] = q - p0[a];
+        } else {
+            p0[a] = 0;
+            tw[a] = 0.0;
+        }
+    }
+    auto interp = [&](const double *src) {
+        double v = 0.0;
+        const int nz = dim == 3 ? 2 : 1;
+        for (int cx = 0; cx < 2; cx++)
+            for (int cy = 0; cy < 2; cy++)
+                for (int cz = 0; cz < nz; cz++) {
+                    double w = 1.0;
+                    w = w * (cx ? tw[0] : 1.0 - tw[0]);
+                    w = w * (cy ? tw[1] : 1.0 - tw[1]);
+                    if (dim == 3)
+                        w = w * (cz ? tw[2] : 1.0 - tw[2]);
+                    const long long q = ((long long)(p0[2] + cz) * dp.B[1] + (p0[1] + cy)) * dp.B[0] + (p0[0] + cx);
+                    v += w * src[q];
+                }
+        return v;
+    };
+    if (mode == 1) {
+        phi_c[t] = interp(phi_p);
+        return;
+    }
+    if (ring == 0)
+        phi_c[t] = interp(phi_p);
+    else
+        phi_c[t] = 0.0;
+    if (ring == 1)
+        rho_c[t] = interp(rho_p);
+}
+
+// The right-hand side of multigrid level 0: 4 pi G rho on Gamma (Eq. 1)
+__global__ void __launch_bounds__(256) kx_rhs(PatchDims d, int dim, const double *__restrict__ rho,
+                                              double *__restrict__ f, double fourpiG)
+{
+    pdl_begin();
+    const long long tot = (long long)d.B[0] * d.B[1] * d.B[2];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= tot)
+        return;
+    int s[3];
+    block_coords(d, dim, t, s);
+    f[t] = block_ring(d, dim, s) >= 1 ? fourpiG * rho[t] : 0.0;
+}
+
+// Potential zero on Gamma (patch 0's start), the outer ring kept
+__global__ void __launch_bounds__(256) kx_zero_gamma(PatchDims d, int dim, double *__restrict__ phi)
+{
+    pdl_begin();
+    const long long tot = (long long)d.B[0] * d.B[1] * d.B[2];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= tot)
+        return;
+    int s[3];
+    block_coords(d, dim, t, s);
+    if (block_ring(d, dim, s) >= 1)
+        phi[t] = 0.0;
+}
+
+// F = -grad Phi on Omega (Eq. 2: 4/3 of the centred difference over 2h minus
+// 1/3 of the one over 4h; stencil 1: the two-point centred difference), and
+// the potential on Omega.  Component a at F[a * cells + cell].
+__global__ void __launch_bounds__(256) kx_forces(PatchDims d, int dim, double h, const double *__restrict__ phi,
+                                                 double *__restrict__ F, double *__restrict__ phi_out, int stencil)
+{
+    pdl_begin();
+    const long long cells = (long long)d.n[0] * d.n[1] * (dim == 3 ? d.n[2] : 1);
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cells)
+        return;
+    const long long r = t / d.n[0];
+    const int i = (int)(t - r * d.n[0]) + 2;
+    const int j = (int)(r % d.n[1]) + 2;
+    const int k = dim == 3 ? (int)(r / d.n[1]) + 2 : 0;
+    const long long st[3] = {1, d.B[0], (long long)d.B[0] * d.B[1]};
+    const long long p = ((long long)k * d.B[1] + j) * d.B[0] + i;
+    for (int a = 0; a < dim; a++) {
+        const double d1 = phi[p + st[a]] - phi[p - st[a]];
+        double gr;
+        if (stencil == 0) {
+            const double d2 = phi[p + 2 * st[a]] - phi[p - 2 * st[a]];
+            gr = (4.0 / 3.0) * d1 / (2.0 * h) - (1.0 / 3.0) * d2 / (4.0 * h);
+        } else {
+            gr = d1 / (2.0 * h);
+        }
+        if (F)
+            F[a * cells + t] = -gr;
+    }
+    if (phi_out)
+        phi_out[t] = phi[p];
+}
+
+}  // namespace
+
+// ==========================================================================
+// Host engine
+// ==========================================================================
+namespace {
+
+// One multigrid level of a patch.
+struct BoxLevel {
+    BoxGeom g;
+    size_t cells = 0;            // storage cells
+    double *phi64 = nullptr;     // FP64 potential and right-hand side (level 0: the patch's blocks)
+    double *f64 = nullptr;
+    float *phi32 = nullptr;      // mixed precision: FP32 correction and defect
+    float *f32 = nullptr;
+    int cmask = 0;               // axes (bit a) that coarsen from this level to the next
+    int ncoars = 0;
+};
+
+struct BoxPatch {
+    int n[3] = {1, 1, 1};
+    int off[3] = {0, 0, 0};      // lower corner in parent cells
+    int parent = -1;
+    double h = 0.0;              // cell size
+    PatchDims d{};
+    std::vector<BoxLevel> lv;
+    double *phi = nullptr, *rho = nullptr, *f0 = nullptr;   // (n+4) blocks
+    double *scal = nullptr;      // device: ||b||^2, ||r||^2
+    bool density_set = false;
+    std::map<int, cudaGraphExec_t> step;   // one iteration, keyed by its FP32 V-cycles (FP64: 1)
+};
+
+std::vector<int> axis_sizes(int M)
+{
+    // Sec. 2.2: N^L = M / 2^L rounded half up, until one cell
+    std::vector<int> N{M};
+    for (int L = 1; N.back() > 1; L++)
+        N.push_back((M + (1 << (L - 1))) >> L);
+    return N;
+}
+
+BoxGeom level_geom(const int n[3], int dim, double h, int L)
+{
+    BoxGeom g{};
+    g.L = L;
+    for (int a = 0; a < 3; a++) {
+        if (a >= dim) {
+            g.N[a] = 1;
+            g.E[a] = 1;
+            continue;
+        }
+        const int M = n[a] + 2;
+        const std::vector<int> seq = axis_sizes(M);
+        const int la = std::min(L, (int)seq.size() - 1);
+        const int N = seq[la];
+        g.N[a] = N;
+        g.E[a] = N + 2;
+        const long long twoM = 2LL * M, xN2 = (2LL * N - 1) << la, hL2 = 2LL << la;
+        g.tie[a] = xN2 == twoM;
+        g.cR[a] = g.tie[a] ? 0.0 : (double)(twoM - xN2 - hL2) / (double)(twoM - xN2);
+        const double ha = std::ldexp(h, la);
+        g.ih2[a] = 1.0 / (ha * ha);
+        g.cRf[a] = (float)g.cR[a];
+        g.ih2f[a] = (float)g.ih2[a];
+    }
+    return g;
+}
+
+int level_count(const int n[3], int dim)
+{
+    int depth = 1;
+    for (int a = 0; a < dim; a++)
+        depth = std::max(depth, (int)axis_sizes(n[a] + 2).size());
+    return depth;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+thread_local std::string g_create_msg;
+
+}  // namespace
+
+struct mg_box {
+    mg_box_desc desc{};
+    mg_options opt{};
+    int dim = 3;
+    int device = 0;
+    std::vector<BoxPatch> p;
+    cudaStream_t stream = nullptr;    // the caller's stream (NULL: legacy default)
+    cudaStream_t cap = nullptr;       // capture stream of the iteration graphs
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    char *arena = nullptr;
+    double *part = nullptr;           // norm partial sums
+    double *stage = nullptr;          // staging for host arrays
+    size_t stage_doubles = 0;
+    double *hscal = nullptr;          // page-locked: 2 per patch
+    bool solved = false;
+    bool poisoned = false;
+    std::string msg;
+};
+
+namespace {
+
+mg_status bfail(mg_box *b, mg_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    (b ? b->msg : g_create_msg) = buf;
+    return s;
+}
+
+mg_status bfail_cuda(mg_box *b, cudaError_t e, const char *what)
+{
+    if (b)
+        b->poisoned = true;
+    return bfail(b, MG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BCK(b, call)                                   \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess)                         \
+            return bfail_cuda((b), e_, #call);         \
+    } while (0)
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kernel)(KArgs...), long long items, cudaStream_t s, Args... args)
+{
+    if (items <= 0)
+        return cudaSuccess;
+    mg_launch_kernel(kernel, dim3((unsigned)((items + 255) / 256)), dim3(256), 0, s, args...);
+    return cudaGetLastError();
+}
+
+long long level_cells(const BoxGeom &g, int dim) { return (long long)g.N[0] * g.N[1] * (dim == 3 ? g.N[2] : 1); }
+long long block_cells(const PatchDims &d) { return (long long)d.B[0] * d.B[1] * d.B[2]; }
+
+template <typename T> T *lphi(const BoxLevel &l);
+template <typename T> T *lf(const BoxLevel &l);
+template <> double *lphi<double>(const BoxLevel &l) { return l.phi64; }
+template <> double *lf<double>(const BoxLevel &l) { return l.f64; }
+template <> float *lphi<float>(const BoxLevel &l) { return l.phi32; }
+template <> float *lf<float>(const BoxLevel &l) { return l.f32; }
+
+template <typename T>
+cudaError_t smooth(const mg_box *b, const BoxLevel &l, int sweeps, cudaStream_t s)
+{
+    const long long items = colour_items(l.g, b->dim);
+    for (int sw = 0; sw < sweeps; sw++)
+        for (int c = 0; c < 2; c++) {
+            cudaError_t e = b->dim == 3 ? launch(kx_smooth<T, 3>, items, s, lphi<T>(l), (const T *)lf<T>(l), l.g, c)
+                                        : launch(kx_smooth<T, 2>, items, s, lphi<T>(l), (const T *)lf<T>(l), l.g, c);
+            if (e)
+                return e;
+        }
+    return cudaSuccess;
+}
+
+// One V-cycle (Sec. 2.3 steps 2-13) over every multigrid level of patch P in
+// precision T: pre-smoothing and restriction down to the level where every
+// axis has one cell (smoothed nu_pre times there), then prolongation,
+// correction and post-smoothing back up.
+template <typename T>
+cudaError_t vcycle(const mg_box *b, const BoxPatch &P, cudaStream_t s)
+{
+    const int dim = b->dim;
+    const int Lc = (int)P.lv.size() - 1;
+    cudaError_t e = smooth<T>(b, P.lv[0], b->opt.nu_pre, s);
+    for (int L = 0; L < Lc && !e; L++) {
+        const BoxLevel &fl = P.lv[L], &cl = P.lv[L + 1];
+        const T wk = (T)std::ldexp(1.0, -fl.ncoars);
+        const long long items = level_cells(cl.g, dim);
+        e = dim == 3 ? launch(kx_resid_restrict<T, 3>, items, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl), fl.g,
+                              lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk)
+                     : launch(kx_resid_restrict<T, 2>, items, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl), fl.g,
+                              lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk);
+        if (!e)
+            e = smooth<T>(b, cl, b->opt.nu_pre, s);
+    }
+    for (int L = Lc; L > 0 && !e; L--) {
+        const BoxLevel &cl = P.lv[L], &fl = P.lv[L - 1];
+        const long long items = level_cells(fl.g, dim);
+        e = dim == 3 ? launch(kx_prolong<T, 3>, items, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask)
+                     : launch(kx_prolong<T, 2>, items, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask);
+        if (!e)
+            e = smooth<T>(b, fl, b->opt.nu_post, s);
+    }
+    return e;
+}
+
+// ||f - A Phi||^2 of level 0 into *out (zero_inside: Phi zero on Gamma);
+// mixed precision with write32: the residual also becomes the FP32 defect
+cudaError_t resid_norm(const mg_box *b, const BoxPatch &P, int zero_inside, bool write32, double *out, cudaStream_t s)
+{
+    const BoxLevel &l = P.lv[0];
+    float *f32 = write32 ? l.f32 : nullptr, *e32 = write32 ? l.phi32 : nullptr;
+    const long long tot = level_cells(l.g, b->dim);
+    const int blocks = (int)std::min<long long>(kNormBlocks, (tot + kNormThreads - 1) / kNormThreads);
+    if (b->dim == 3)
+        mg_launch_kernel(kx_resid_norm<3>, dim3(blocks), dim3(kNormThreads), 0, s, (const double *)l.phi64,
+                         (const double *)l.f64, l.g, zero_inside, b->part, f32, e32);
+    else
+        mg_launch_kernel(kx_resid_norm<2>, dim3(blocks), dim3(kNormThreads), 0, s, (const double *)l.phi64,
+                         (const double *)l.f64, l.g, zero_inside, b->part, f32, e32);
+    cudaError_t e = cudaGetLastError();
+    if (e)
+        return e;
+    mg_launch_kernel(kx_sum, dim3(1), dim3(kNormThreads), 0, s, (const double *)b->part, blocks, out);
+    return cudaGetLastError();
+}
+
+bool mixed(const mg_box *b) { return b->opt.precision == MG_MIXED; }
+
+// One iteration of patch pi's loop (Sec. 2.3 step 14): an FP64 V-cycle, or
+// ncyc FP32 V-cycles on the correction of the stored defect and their FP64
+// accumulation; then ||r||^2 (in mixed precision also the next defect), copied
+// to the page-locked host slot.
+cudaError_t iteration(mg_box *b, int pi, int ncyc, cudaStream_t s)
+{
+    BoxPatch &P = b->p[pi];
+    cudaError_t e;
+    if (!mixed(b)) {
+        e = vcycle<double>(b, P, s);
+    } else {
+        e = cudaSuccess;
+        for (int c = 0; c < ncyc && !e; c++)
+            e = vcycle<float>(b, P, s);
+        if (!e)
+            e = launch(b->dim == 3 ? kx_accumulate<3> : kx_accumulate<2>, level_cells(P.lv[0].g, b->dim), s,
+                       P.lv[0].phi64, (const float *)P.lv[0].phi32, P.lv[0].g);
+    }
+    if (!e)
+        e = resid_norm(b, P, 0, mixed(b), P.scal + 1, s);
+    if (!e)
+        e = cudaMemcpyAsync(b->hscal + 2 * pi + 1, P.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+// The iteration as a CUDA graph (captured once per FP32 V-cycle count)
+cudaError_t iteration_graph(mg_box *b, int pi, int ncyc, cudaGraphExec_t *out)
+{
+    BoxPatch &P = b->p[pi];
+    auto it = P.step.find(ncyc);
+    if (it != P.step.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e)
+        return e;
+    const cudaError_t eb = iteration(b, pi, ncyc, b->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (eb || e) {
+        if (g)
+            cudaGraphDestroy(g);
+        return eb ? eb : e;
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e)
+        return e;
+    P.step[ncyc] = x;
+    *out = x;
+    return cudaSuccess;
+}
+
+// The start of patch pi's solve: its buffer rings (from the parent, or the
+// caller's boundary data), the right-hand side, ||b|| from a zero Gamma, the
+// initial guess and the starting residual
+cudaError_t prelude(mg_box *b, int pi, cudaStream_t s)
+{
+    BoxPatch &P = b->p[pi];
+    const int dim = b->dim;
+    const long long nb = block_cells(P.d);
+    cudaError_t e;
+    if (pi == 0) {
+        e = launch(kx_zero_gamma, nb, s, P.d, dim, P.phi);
+    } else {
+        const BoxPatch &Q = b->p[P.parent];
+        e = launch(kx_interface, nb, s, P.d, Q.d, dim, P.off[0], P.off[1], P.off[2], (const double *)Q.phi,
+                   (const double *)Q.rho, P.phi, P.rho, 0);
+    }
+    if (!e)
+        e = launch(kx_rhs, nb, s, P.d, dim, (const double *)P.rho, P.f0, 4.0 * M_PI * b->desc.G);
+    if (!e)
+        e = resid_norm(b, P, 1, false, P.scal, s);
+    if (!e && pi > 0 && b->opt.guess == MG_GUESS_INTERP) {
+        const BoxPatch &Q = b->p[P.parent];
+        e = launch(kx_interface, nb, s, P.d, Q.d, dim, P.off[0], P.off[1], P.off[2], (const double *)Q.phi,
+                   (const double *)Q.rho, P.phi, P.rho, 1);
+    }
+    if (!e)
+        e = resid_norm(b, P, 0, mixed(b), P.scal + 1, s);
+    if (!e)
+        e = cudaMemcpyAsync(b->hscal + 2 * pi, P.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+mg_status check_box_options(const mg_options &o)
+{
+    if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.max_cycles < 0 || !(o.rel_tol >= 0.0) ||
+        (o.precision != MG_FP64 && o.precision != MG_MIXED) || o.inner_cycles < 1 || o.inner_max < 0 ||
+        o.inner_max > MG_INNER_MAX || (o.guess != MG_GUESS_INTERP && o.guess != MG_GUESS_ZERO) ||
+        (o.force_stencil != MG_FORCE_EQ2 && o.force_stencil != MG_FORCE_CD2) || o.interface != MG_IFACE_BUFFER ||
+        o.stop != MG_STOP_RESIDUAL)
+        return MG_EINVAL;
+    return MG_OK;
+}
+
+int box_parent(const mg_box_desc &d, int l) { return d.tree ? d.parent[l] : l - 1; }
+
+mg_status check_box_desc(const mg_box_desc &d)
+{
+    if (d.dim != 2 && d.dim != 3)
+        return bfail(nullptr, MG_EINVAL, "dim must be 2 or 3");
+    if (d.num_patches < 1 || d.num_patches > MG_MAX_LEVELS)
+        return bfail(nullptr, MG_EINVAL, "num_patches %d out of range", d.num_patches);
+    if (!(d.h0 > 0.0) || !std::isfinite(d.h0) || !std::isfinite(d.G))
+        return bfail(nullptr, MG_EINVAL, "h0 must be positive and G finite");
+    if (d.tree != 0 && d.tree != 1)
+        return bfail(nullptr, MG_EINVAL, "tree must be 0 or 1");
+    for (int l = 1; l < d.num_patches; l++)
+        if (d.tree && (d.parent[l] < 0 || d.parent[l] >= l))
+            return bfail(nullptr, MG_EINVAL, "patch %d: parent %d not in [0, %d)", l, d.parent[l], l);
+    for (int l = 0; l < d.num_patches; l++) {
+        double cells = 1.0;
+        for (int a = 0; a < d.dim; a++) {
+            const int n = d.n[l][a];
+            if (n < 2 || n > (1 << 20) || (l > 0 && (n & 1)))
+                return bfail(nullptr, MG_EINVAL, "patch %d axis %d: n=%d (need >= 2, even above patch 0)", l, a, n);
+            cells *= (double)(n + 4);
+        }
+        if (cells > 2147483647.0)
+            return bfail(nullptr, MG_EINVAL, "patch %d: (n+4) block of %.0f cells exceeds 2^31", l, cells);
+        if (l == 0)
+            continue;
+        const int pl = box_parent(d, l);
+        int depth = 0;
+        for (int q = pl; q > 0; q = box_parent(d, q))
+            depth++;
+        const double hp = std::ldexp(d.h0, -depth);
+        for (int a = 0; a < d.dim; a++) {
+            const double o = (d.lo[l][a] - d.lo[pl][a]) / hp;
+            const double r = std::floor(o + 0.5);
+            if (std::fabs(o - r) > 1e-6)
+                return bfail(nullptr, MG_EINVAL, "patch %d axis %d: not on parent cell faces", l, a);
+            const int hi = d.n[pl][a] - d.n[l][a] / 2 - 1;
+            if (r < 1.0 || r > (double)hi)
+                return bfail(nullptr, MG_EINVAL, "patch %d axis %d: offset %g outside [1, %d] parent cells", l, a, r, hi);
+        }
+    }
+    return MG_OK;
+}
+
+void destroy_box(mg_box *b)
+{
+    if (!b)
+        return;
+    for (auto &P : b->p)
+        for (auto &kv : P.step)
+            cudaGraphExecDestroy(kv.second);
+    if (b->arena)
+        cudaFree(b->arena);
+    if (b->hscal)
+        cudaFreeHost(b->hscal);
+    if (b->ev0)
+        cudaEventDestroy(b->ev0);
+    if (b->ev1)
+        cudaEventDestroy(b->ev1);
+    if (b->cap)
+        cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_box_create(const mg_box_desc *desc, const mg_options *opt, mg_box **out)
+{
+    if (!out)
+        return bfail(nullptr, MG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!desc)
+        return bfail(nullptr, MG_EINVAL, "desc is NULL");
+    mg_options o;
+    mg_default_options(&o);
+    if (opt)
+        o = *opt;
+    if (check_box_options(o) != MG_OK)
+        return bfail(nullptr, MG_EINVAL,
+                     "options: box patches take FP64 or MIXED, guess INTERP or ZERO, interface BUFFER, stop RESIDUAL");
+    mg_status st = check_box_desc(*desc);
+    if (st != MG_OK)
+        return st;
+    mg_box *b = new mg_box;
+    b->desc = *desc;
+    b->opt = o;
+    b->dim = desc->dim;
+    b->stream = (cudaStream_t)o.stream;
+    cudaError_t e = cudaGetDevice(&b->device);
+    const int dim = b->dim;
+    b->p.resize(desc->num_patches);
+    // layout of the arena
+    size_t bytes = up256(kNormBlocks * sizeof(double));
+    size_t stage = 0;
+    std::vector<std::vector<size_t>> offs(desc->num_patches);
+    for (int l = 0; l < desc->num_patches; l++) {
+        BoxPatch &P = b->p[l];
+        for (int a = 0; a < 3; a++)
+            P.n[a] = a < dim ? desc->n[l][a] : 1;
+        P.parent = l > 0 ? box_parent(*desc, l) : -1;
+        int depth = 0;
+        for (int q = l; q > 0; q = box_parent(*desc, q))
+            depth++;
+        P.h = std::ldexp(desc->h0, -depth);
+        for (int a = 0; a < 3; a++) {
+            P.d.n[a] = P.n[a];
+            P.d.B[a] = a < dim ? P.n[a] + 4 : 1;
+            if (l > 0 && a < dim) {
+                const double hp = 2.0 * P.h;
+                P.off[a] = (int)std::floor((desc->lo[l][a] - desc->lo[P.parent][a]) / hp + 0.5);
+            }
+        }
+        const int depthL = level_count(P.n, dim);
+        P.lv.resize(depthL);
+        for (int L = 0; L < depthL; L++) {
+            BoxLevel &v = P.lv[L];
+            v.g = level_geom(P.n, dim, P.h, L);
+            v.cells = (size_t)v.g.E[0] * v.g.E[1] * v.g.E[2];
+        }
+        for (int L = 0; L + 1 < depthL; L++) {
+            const BoxGeom &f = P.lv[L].g, &c = P.lv[L + 1].g;
+            int m = 0, k = 0;
+            for (int a = 0; a < dim; a++) {
+                // an axis coarsens when its own level index grows: its cell count changes, or
+                // it stays at one cell (then la is capped and nothing changes)
+                const std::vector<int> seq = axis_sizes(P.n[a] + 2);
+                const int laf = std::min(L, (int)seq.size() - 1), lac = std::min(L + 1, (int)seq.size() - 1);
+                if (lac > laf) {
+                    m |= 1 << a;
+                    k++;
+                }
+            }
+            (void)f;
+            (void)c;
+            P.lv[L].cmask = m;
+            P.lv[L].ncoars = k;
+        }
+        const size_t nb = (size_t)block_cells(P.d);
+        std::vector<size_t> &of = offs[l];
+        of.push_back(bytes);   // phi
+        bytes += up256(nb * 8);
+        of.push_back(bytes);   // rho
+        bytes += up256(nb * 8);
+        of.push_back(bytes);   // f0
+        bytes += up256(nb * 8);
+        of.push_back(bytes);   // scal
+        bytes += 256;
+        for (int L = 0; L < depthL; L++) {
+            const size_t c = P.lv[L].cells;
+            if (!mixed(b)) {
+                if (L > 0) {
+                    of.push_back(bytes);
+                    bytes += up256(c * 8);
+                    of.push_back(bytes);
+                    bytes += up256(c * 8);
+                }
+            } else {
+                of.push_back(bytes);
+                bytes += up256(c * 4);
+                of.push_back(bytes);
+                bytes += up256(c * 4);
+            }
+        }
+        long long om = 1;
+        for (int a = 0; a < dim; a++)
+            om *= P.n[a];
+        stage = std::max(stage, std::max((size_t)nb * 3, (size_t)om * (dim + 1)));
+    }
+    const size_t stage_off = bytes;
+    bytes += up256(stage * 8);
+    if (!e)
+        e = cudaMalloc(&b->arena, bytes);
+    if (e) {
+        cudaGetLastError();
+        destroy_box(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA, "device memory (%zu bytes): %s",
+                     bytes, cudaGetErrorString(e));
+    }
+    b->part = (double *)b->arena;
+    b->stage = (double *)(b->arena + stage_off);
+    b->stage_doubles = stage;
+    for (int l = 0; l < desc->num_patches; l++) {
+        BoxPatch &P = b->p[l];
+        const std::vector<size_t> &of = offs[l];
+        size_t q = 0;
+        P.phi = (double *)(b->arena + of[q++]);
+        P.rho = (double *)(b->arena + of[q++]);
+        P.f0 = (double *)(b->arena + of[q++]);
+        P.scal = (double *)(b->arena + of[q++]);
+        for (int L = 0; L < (int)P.lv.size(); L++) {
+            BoxLevel &v = P.lv[L];
+            if (L == 0) {
+                v.phi64 = P.phi;
+                v.f64 = P.f0;
+            }
+            if (!mixed(b)) {
+                if (L > 0) {
+                    v.phi64 = (double *)(b->arena + of[q++]);
+                    v.f64 = (double *)(b->arena + of[q++]);
+                }
+            } else {
+                v.phi32 = (float *)(b->arena + of[q++]);
+                v.f32 = (float *)(b->arena + of[q++]);
+            }
+        }
+    }
+    if (!e)
+        e = cudaMemsetAsync(b->arena, 0, bytes, b->stream);
+    if (!e)
+        e = cudaMallocHost(&b->hscal, 2 * sizeof(double) * desc->num_patches);
+    if (!e)
+        e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (!e)
+        e = cudaEventCreate(&b->ev0);
+    if (!e)
+        e = cudaEventCreate(&b->ev1);
+    if (!e)
+        e = cudaStreamSynchronize(b->stream);
+    if (e) {
+        cudaGetLastError();
+        destroy_box(b);
+        return bfail(nullptr, MG_ECUDA, "setup: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return MG_OK;
+}
+
+mg_status mg_box_set_density(mg_box *b, int patch, const double *rho, const double *bc_rho, const double *bc_phi)
+{
+    if (!b)
+        return MG_EINVAL;
+    if (b->poisoned)
+        return bfail(b, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (patch < 0 || patch >= (int)b->p.size())
+        return bfail(b, MG_EINVAL, "patch %d out of range", patch);
+    if (!rho)
+        return bfail(b, MG_EINVAL, "rho is NULL");
+    if (patch == 0 && (!bc_rho || !bc_phi))
+        return bfail(b, MG_EINVAL, "patch 0 needs bc_rho and bc_phi");
+    if (patch > 0 && (bc_rho || bc_phi))
+        return bfail(b, MG_EINVAL, "bc_rho/bc_phi must be NULL above patch 0 (the interface fills them)");
+    BoxPatch &P = b->p[patch];
+    const int dim = b->dim;
+    const size_t nb = (size_t)block_cells(P.d);
+    size_t nr = 1, ng = 1;
+    for (int a = 0; a < dim; a++) {
+        nr *= (size_t)P.n[a];
+        ng *= (size_t)P.n[a] + 2;
+    }
+    const double *d_rho = rho, *d_bcr = bc_rho, *d_bcp = bc_phi;
+    bool host_in = false;
+    auto take = [&](const double *src, const double *&dst, double *st, size_t count) -> cudaError_t {
+        if (device_ptr(src))
+            return cudaSuccess;
+        host_in = true;
+        dst = st;
+        return cudaMemcpyAsync(st, src, count * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    };
+    BCK(b, take(rho, d_rho, b->stage, nr));
+    if (patch == 0) {
+        BCK(b, take(bc_rho, d_bcr, b->stage + nb, ng));
+        BCK(b, take(bc_phi, d_bcp, b->stage + 2 * nb, nb));
+    }
+    BCK(b, launch(kx_place, (long long)nb, b->stream, P.d, dim, d_rho, d_bcr, d_bcp, P.rho, P.phi));
+    if (host_in)
+        BCK(b, cudaStreamSynchronize(b->stream));
+    P.density_set = true;
+    b->solved = false;
+    return MG_OK;
+}
+
+mg_status mg_box_solve(mg_box *b, mg_level_stats *stats)
+{
+    if (!b)
+        return MG_EINVAL;
+    if (b->poisoned)
+        return bfail(b, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    for (size_t l = 0; l < b->p.size(); l++)
+        if (!b->p[l].density_set)
+            return bfail(b, MG_ESTATE, "patch %zu has no density", l);
+    const mg_options &o = b->opt;
+    const bool adapt = mixed(b) && o.inner_max > 0;
+    mg_status worst = MG_OK;
+    for (int pi = 0; pi < (int)b->p.size(); pi++) {
+        BCK(b, prelude(b, pi, b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        const double *hs = b->hscal + 2 * pi;
+        const double bn = std::sqrt(hs[0]);
+        double rel = bn > 0.0 ? std::sqrt(hs[1]) / bn : 0.0;
+        int status = std::isfinite(bn) && std::isfinite(rel) ? 0 : 1;
+        int cycles = 0, outer = 0, inner = o.inner_cycles;
+        while (bn > 0.0 && !status && cycles < o.max_cycles && !(rel < o.rel_tol)) {
+            const int ncyc = !mixed(b) ? 1 : adapt ? std::min(inner, o.max_cycles - cycles) : o.inner_cycles;
+            cudaGraphExec_t x;
+            BCK(b, iteration_graph(b, pi, ncyc, &x));
+            BCK(b, cudaGraphLaunch(x, b->stream));
+            BCK(b, cudaStreamSynchronize(b->stream));
+            const double before = rel;
+            cycles += ncyc;
+            outer++;
+            rel = std::sqrt(hs[1]) / bn;
+            if (!std::isfinite(rel))
+                status = 1;
+            if (adapt)
+                inner = mg_next_inner(before, rel, ncyc, o.rel_tol, o.inner_max);
+        }
+        int s = status ? MG_EDIVERGED : MG_OK;
+        if (s == MG_OK && bn > 0.0 && o.rel_tol > 0.0 && !(rel < o.rel_tol))
+            s = MG_ENOCONV;
+        if (stats) {
+            stats[pi].cycles = cycles;
+            stats[pi].outer_steps = outer;
+            stats[pi].rel_res = rel;
+            stats[pi].b_norm = bn;
+            stats[pi].status = s;
+        }
+        if (s == MG_EDIVERGED)
+            worst = MG_EDIVERGED;
+        else if (s == MG_ENOCONV && worst == MG_OK)
+            worst = MG_ENOCONV;
+    }
+    b->solved = true;
+    return worst;
+}
+
+mg_status mg_box_forces(mg_box *b, int patch, double *phi_out, double *F_out)
+{
+    if (!b)
+        return MG_EINVAL;
+    if (b->poisoned)
+        return bfail(b, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (patch < 0 || patch >= (int)b->p.size())
+        return bfail(b, MG_EINVAL, "patch %d out of range", patch);
+    if (!b->solved)
+        return bfail(b, MG_ESTATE, "mg_box_forces before mg_box_solve");
+    const BoxPatch &P = b->p[patch];
+    const int dim = b->dim;
+    size_t nr = 1;
+    for (int a = 0; a < dim; a++)
+        nr *= (size_t)P.n[a];
+    const bool F_dev = F_out && device_ptr(F_out), P_dev = phi_out && device_ptr(phi_out);
+    double *dF = F_out ? (F_dev ? F_out : b->stage) : nullptr;
+    double *dP = phi_out ? (P_dev ? phi_out : b->stage + (size_t)dim * nr) : nullptr;
+    BCK(b, launch(kx_forces, (long long)nr, b->stream, P.d, dim, P.h, (const double *)P.phi, dF, dP,
+                  b->opt.force_stencil));
+    bool sync = false;
+    if (F_out && !F_dev) {
+        BCK(b, cudaMemcpyAsync(F_out, dF, (size_t)dim * nr * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        sync = true;
+    }
+    if (phi_out && !P_dev) {
+        BCK(b, cudaMemcpyAsync(phi_out, dP, nr * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        sync = true;
+    }
+    if (sync)
+        BCK(b, cudaStreamSynchronize(b->stream));
+    return MG_OK;
+}
+
+int mg_box_level_sizes(const mg_box *b, int patch, int *N, int cap)
+{
+    if (!b || patch < 0 || patch >= (int)b->p.size() || cap < 0 || (cap > 0 && !N))
+        return -1;
+    const BoxPatch &P = b->p[patch];
+    const int k = (int)P.lv.size();
+    for (int L = 0; L < std::min(k, cap); L++)
+        for (int a = 0; a < 3; a++)
+            N[3 * L + a] = P.lv[L].g.N[a];
+    return k;
+}
+
+mg_status mg_box_time_smoothing(mg_box *b, int patch, int L, int launches, double *us_per_launch,
+                                double *bytes_per_launch)
+{
+    if (!b)
+        return MG_EINVAL;
+    if (b->poisoned)
+        return bfail(b, MG_ESTATE, "handle poisoned by an earlier CUDA error");
+    if (patch < 0 || patch >= (int)b->p.size() || launches < 1)
+        return bfail(b, MG_EINVAL, "patch %d / launches %d out of range", patch, launches);
+    const BoxPatch &P = b->p[patch];
+    if (L < 0 || L >= (int)P.lv.size())
+        return bfail(b, MG_EINVAL, "multigrid level %d out of range", L);
+    const BoxLevel &v = P.lv[L];
+    auto pass = [&](int c) -> cudaError_t {
+        const long long items = colour_items(v.g, b->dim);
+        if (mixed(b))
+            return b->dim == 3 ? launch(kx_smooth<float, 3>, items, b->stream, v.phi32, (const float *)v.f32, v.g, c)
+                               : launch(kx_smooth<float, 2>, items, b->stream, v.phi32, (const float *)v.f32, v.g, c);
+        return b->dim == 3 ? launch(kx_smooth<double, 3>, items, b->stream, v.phi64, (const double *)v.f64, v.g, c)
+                           : launch(kx_smooth<double, 2>, items, b->stream, v.phi64, (const double *)v.f64, v.g, c);
+    };
+    for (int w = 0; w < 3; w++)
+        BCK(b, pass(w & 1));
+    BCK(b, cudaEventRecord(b->ev0, b->stream));
+    for (int r = 0; r < launches; r++)
+        BCK(b, pass(r & 1));
+    BCK(b, cudaEventRecord(b->ev1, b->stream));
+    BCK(b, cudaEventSynchronize(b->ev1));
+    float ms = 0.0f;
+    BCK(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    const double cells = (double)v.g.N[0] * v.g.N[1] * v.g.N[2];
+    if (us_per_launch)
+        *us_per_launch = 1e3 * ms / launches;
+    if (bytes_per_launch)
+        *bytes_per_launch = 1.5 * cells * (mixed(b) ? 4.0 : 8.0);
+    b->solved = false;
+    return MG_OK;
+}
+
+const char *mg_box_error_message(const mg_box *b) { return b ? b->msg.c_str() : g_create_msg.c_str(); }
+
+mg_status mg_box_destroy(mg_box *b)
+{
+    if (b)
+        cudaSetDevice(b->device);
+    destroy_box(b);
+    return MG_OK;
+}
+
+}  // extern "C"

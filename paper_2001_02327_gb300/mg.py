@@ -1,4 +1,4 @@
-"""ctypes binding of the C ABI declared in include/mg.h.
+"""ctypes binding of the C ABI declared in include/mg.h and include/mg_box.h.
 
 The functions below carry the C names and only marshal arguments; every step
 of the solve runs in libmg.so.  Arrays may be torch tensors (CUDA or CPU),
@@ -42,6 +42,12 @@ class mg_level_stats(C.Structure):
                 ("status", C.c_int)]
 
 
+class mg_box_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("num_patches", C.c_int), ("n", (C.c_int * 3) * MG_MAX_LEVELS),
+                ("lo", (C.c_double * 3) * MG_MAX_LEVELS), ("h0", C.c_double), ("G", C.c_double),
+                ("tree", C.c_int), ("parent", C.c_int * MG_MAX_LEVELS)]
+
+
 class mg_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_long), ("ms", C.c_double), ("bytes", C.c_double)]
 
@@ -67,6 +73,15 @@ _SIGS = {
     "mg_solve_level_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
                                          C.POINTER(mg_options), C.POINTER(mg_level_stats)]),
     "mg_profile_read": (C.c_int, [_vp, C.POINTER(mg_kernel_stat), C.c_int]),
+    "mg_box_create": (C.c_int, [C.POINTER(mg_box_desc), C.POINTER(mg_options), C.POINTER(_vp)]),
+    "mg_box_set_density": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "mg_box_solve": (C.c_int, [_vp, C.POINTER(mg_level_stats)]),
+    "mg_box_forces": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "mg_box_level_sizes": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "mg_box_time_smoothing": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
+    "mg_box_error_message": (C.c_char_p, [_vp]),
+    "mg_box_destroy": (C.c_int, [_vp]),
 }
 
 
@@ -220,6 +235,63 @@ def mg_destroy(h):
     return LIB.mg_destroy(h)
 
 
+# box (non-cubic) patches, include/mg_box.h
+def mg_box_error_message(b=None):
+    return LIB.mg_box_error_message(b).decode()
+
+
+def _bcheck(b, s, ok=(MG_OK,)):
+    if s not in ok:
+        raise MGError(s, mg_box_error_message(b))
+    return s
+
+
+def mg_box_create(desc, opt=None):
+    """desc: mg_box_desc; returns the opaque handle (int)."""
+    b = _vp()
+    s = LIB.mg_box_create(C.byref(desc), C.byref(opt) if opt is not None else None, C.byref(b))
+    if s != MG_OK:
+        raise MGError(s, mg_box_error_message(None))
+    return b.value
+
+
+def mg_box_set_density(b, patch, rho, bc_rho=None, bc_phi=None):
+    return _bcheck(b, LIB.mg_box_set_density(b, patch, _addr(rho), _addr(bc_rho), _addr(bc_phi)))
+
+
+def mg_box_solve(b, num_patches, allow_noconv=False):
+    """Returns (status, stats) with stats a list of one dict per patch."""
+    st = (mg_level_stats * num_patches)()
+    s = LIB.mg_box_solve(b, st)
+    _bcheck(b, s, (MG_OK, MG_ENOCONV) if allow_noconv else (MG_OK,))
+    return s, [{"cycles": st[l].cycles, "outer_steps": st[l].outer_steps, "rel_res": st[l].rel_res,
+                "b_norm": st[l].b_norm, "status": st[l].status} for l in range(num_patches)]
+
+
+def mg_box_forces(b, patch, phi_out=None, F_out=None):
+    return _bcheck(b, LIB.mg_box_forces(b, patch, _addr(phi_out), _addr(F_out)))
+
+
+def mg_box_level_sizes(b, patch):
+    """[(N_x, N_y, N_z)] per multigrid level of the patch."""
+    buf = (C.c_int * (3 * 64))()
+    k = LIB.mg_box_level_sizes(b, patch, buf, 64)
+    if k < 0:
+        raise MGError(MG_EINVAL, "mg_box_level_sizes")
+    return [tuple(buf[3 * L + a] for a in range(3)) for L in range(k)]
+
+
+def mg_box_time_smoothing(b, patch, L, launches):
+    """(microseconds per colour pass, algorithmic bytes per pass) on multigrid level L."""
+    us, by = C.c_double(), C.c_double()
+    _bcheck(b, LIB.mg_box_time_smoothing(b, patch, L, launches, C.byref(us), C.byref(by)))
+    return us.value, by.value
+
+
+def mg_box_destroy(b):
+    return LIB.mg_box_destroy(b)
+
+
 # ---------------------------------------------------------------------------
 # marshalling helpers
 # ---------------------------------------------------------------------------
@@ -231,6 +303,24 @@ def desc_from(H):
     for l in range(H.num_levels):
         d.n[l] = H.n[l]
         for a in range(H.dim):
+            d.lo[l][a] = H.lo[l][a]
+    d.h0 = H.h0
+    d.G = H.G
+    if getattr(H, "parents", None) is not None:
+        d.tree = 1
+        for l in range(1, H.num_levels):
+            d.parent[l] = H.parent(l)
+    return d
+
+
+def box_desc_from(H):
+    """mg_box_desc from an inputs.BoxHierarchy."""
+    d = mg_box_desc()
+    d.dim = H.dim
+    d.num_patches = H.num_levels
+    for l in range(H.num_levels):
+        for a in range(H.dim):
+            d.n[l][a] = H.n[l][a]
             d.lo[l][a] = H.lo[l][a]
     d.h0 = H.h0
     d.G = H.G

@@ -1,6 +1,7 @@
 """The C ABI library builds, loads and answers its host-only calls (no GPU).
 
-Checks that libmg.so exports every function include/mg.h declares, that the
+Checks that libmg.so exports every function include/mg.h, include/mg_box.h
+and include/unet.h declare, that the
 multigrid level sizes it computes agree with the oracle's for many sizes,
 and that argument validation happens on the host before any CUDA call.
 """
@@ -21,7 +22,7 @@ def mg():
     return M
 
 
-def _declared(headers=("mg.h", "unet.h")):
+def _declared(headers=("mg.h", "mg_box.h", "unet.h")):
     names = set()
     for hdr in headers:
         src = open(os.path.join(ROOT, "include", hdr)).read()
@@ -104,7 +105,55 @@ def test_invalid_arguments_rejected_on_host(mg, bad):
     assert mg.mg_error_message(None)
 
 
+def _box_desc(mg, **kw):
+    from paper_2001_02327_gb300 import inputs as I
+    return mg.box_desc_from(I.box_3d_sphere(n=(24, 32, 16), levels=3))
+
+
+@pytest.mark.parametrize("bad", ["dim", "patches", "n_odd", "n_small", "offset", "off_grid", "h0", "parent",
+                                 "frozen", "force_stop", "user_guess", "learned_guess", "inner_max"])
+def test_box_invalid_arguments_rejected_on_host(mg, bad):
+    d = _box_desc(mg)
+    opt = None
+    if bad == "dim":
+        d.dim = 1
+    elif bad == "patches":
+        d.num_patches = 0
+    elif bad == "n_odd":
+        d.n[1][2] = 15
+    elif bad == "n_small":
+        d.n[0][1] = 1
+    elif bad == "offset":
+        d.lo[1][1] = d.lo[0][1]             # offset 0 parent cells along y
+    elif bad == "off_grid":
+        d.lo[2][0] += 0.3 * d.h0            # not on a parent cell face
+    elif bad == "h0":
+        d.h0 = 0.0
+    elif bad == "parent":
+        d.tree = 1
+        d.parent[2] = 2
+    elif bad == "frozen":
+        opt = mg.options(interface=mg.MG_IFACE_FROZEN)
+    elif bad == "force_stop":
+        opt = mg.options(stop=mg.MG_STOP_FORCE)
+    elif bad == "user_guess":
+        opt = mg.options(guess=mg.MG_GUESS_USER)
+    elif bad == "learned_guess":
+        opt = mg.options(guess=mg.MG_GUESS_LEARNED)
+    elif bad == "inner_max":
+        opt = mg.options(precision=mg.MG_MIXED, inner_max=99)
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_box_create(d, opt)
+    assert e.value.status == mg.MG_EINVAL
+    assert mg.mg_box_error_message(None)
+
+
 def test_null_handles(mg):
+    assert mg.LIB.mg_box_destroy(None) == mg.MG_OK
+    assert mg.LIB.mg_box_solve(None, None) == mg.MG_EINVAL
+    assert mg.LIB.mg_box_forces(None, 0, None, None) == mg.MG_EINVAL
+    assert mg.LIB.mg_box_set_density(None, 0, None, None, None) == mg.MG_EINVAL
+    assert mg.LIB.mg_box_level_sizes(None, 0, None, 0) == -1
     assert mg.LIB.mg_destroy(None) == mg.MG_OK
     assert mg.LIB.mg_solve(None, None) == mg.MG_EINVAL
     assert mg.LIB.mg_forces(None, 0, 0, None, None) == mg.MG_EINVAL
