@@ -820,6 +820,100 @@ def run_scale_case(args):
             mg.mg_destroy(h)
 
 
+def run_box_case(args):
+    """Box (non-cubic) patches: 3 nested patches of 512 x 256 x 256 cells (each
+    halving the box [-1,1] x [-0.5,0.5]^2 about its centre) around the offset
+    compact sphere; V(2,2) to 1e-10, FP64 and mixed, through include/mg_box.h.
+    One line per form (zones/s of set_density + solve + forces, CUDA events;
+    max errors against the closed form; cycles), then the finest multigrid
+    level's colour pass timed back to back (DRAM-resident: 514 x 258 x 258
+    cells per array) against the measured HBM bandwidth."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    n = tuple(int(v) for v in args.box_n.split("x"))
+    H = I.box_3d_sphere(n=n, levels=3)
+    inp = I.level_inputs(H)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_in = [{k: dev(v) for k, v in d.items()} for d in inp]
+    shape = tuple(reversed(n))
+    F = [torch.empty((3,) + shape, dtype=torch.float64, device="cuda") for _ in range(H.num_levels)]
+    P = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(H.num_levels)]
+    peak, peak_src = measured_peaks("hbm_gbs")
+    for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+        b = mg.mg_box_create(mg.box_desc_from(H), mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60,
+                                                             rel_tol=TOL, precision=prec,
+                                                             inner_cycles=args.inner_cycles,
+                                                             inner_max=args.inner_max))
+        try:
+            def step():
+                mg.mg_box_set_density(b, 0, d_in[0]["rho"], d_in[0]["bc_rho"], d_in[0]["bc_phi"])
+                for l in range(1, H.num_levels):
+                    mg.mg_box_set_density(b, l, d_in[l]["rho"])
+                st = mg.mg_box_solve(b, H.num_levels)[1]
+                for l in range(H.num_levels):
+                    mg.mg_box_forces(b, l, P[l], F[l])
+                return st
+
+            for _ in range(args.warmup):
+                st = step()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                ev0.record()
+                st = step()
+                ev1.record()
+                torch.cuda.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+            ep = ef = 0.0
+            for l in range(H.num_levels):
+                X = H.centres(l, 0)
+                pa, fa = H.potential(X), H.force(X)
+                ep = max(ep, float(np.max(np.abs(P[l].cpu().numpy() - pa)) / np.max(np.abs(pa))))
+                ef = max(ef, float(np.max(np.abs(np.moveaxis(F[l].cpu().numpy(), 0, -1) - fa)) / np.max(np.abs(fa))))
+            t = statistics.median(ms)
+            us, by = mg.mg_box_time_smoothing(b, 0, 0, args.launches)
+            print(json.dumps({"case": f"3 nested box patches of {'x'.join(map(str, n))} cells, offset sphere",
+                              "form": name, "zones": H.zones(), "ms_per_solve": t,
+                              "zones_per_s": H.zones() / (t * 1e-3),
+                              "cycles_per_patch": [s["cycles"] for s in st],
+                              "outer_steps_per_patch": [s["outer_steps"] for s in st],
+                              "max_rel_res": max(s["rel_res"] for s in st),
+                              "max_rel_err_phi": ep, "max_rel_err_F": ef,
+                              "timing": "CUDA events around set_density + mg_box_solve + mg_box_forces, median",
+                              "finest_colour_pass": {"us": us, "bytes": by, "GBps": by / (us * 1e-6) / 1e9,
+                                                     "frac": by / (us * 1e-6) / 1e9 / peak,
+                                                     "peak_GBps": peak, "peak_source": peak_src,
+                                                     "byte_model": "1.5 words per cell (Phi read once, its "
+                                                                   "colour written, f of the colour read)",
+                                                     "timing": f"{args.launches} back-to-back launches, "
+                                                               "CUDA events"}}), flush=True)
+        finally:
+            mg.mg_box_destroy(b)
+
+
+def run_box_smoothing_case(args):
+    """The finest multigrid level's FP32 colour pass of a box patch
+    (--box-n cells; mixed-precision storage) timed alone, `--launches`
+    back-to-back launches: a short command for profiler captures."""
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    n = tuple(int(v) for v in args.box_n.split("x"))
+    H = I.box_3d_sphere(n=n, levels=1)
+    b = mg.mg_box_create(mg.box_desc_from(H), mg.options(precision=mg.MG_MIXED))
+    try:
+        us, by = mg.mg_box_time_smoothing(b, 0, 0, args.launches)
+        peak, src = measured_peaks("hbm_gbs")
+        print(json.dumps({"case": f"box patch {args.box_n}, finest FP32 colour pass", "us": us, "bytes": by,
+                          "GBps": by / (us * 1e-6) / 1e9, "frac": by / (us * 1e-6) / 1e9 / peak,
+                          "peak_source": src, "launches": args.launches}), flush=True)
+    finally:
+        mg.mg_box_destroy(b)
+
+
 def run_unet_case(args):
     """The learned guess's 3D U-Net on a batch of 4 samples of 64^3: one
     forward pass and one training step (forward, backward, AdamW) timed with
@@ -983,9 +1077,11 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1500, help="learned case: training steps")
     ap.add_argument("--launches", type=int, default=4, help="smoothing case: launches per timing")
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "level", "smoothing", "batch", "scale", "unet", "learned", "2d"],
+                    choices=["bench", "level", "smoothing", "batch", "scale", "unet", "learned", "2d", "box",
+                             "box_smoothing"],
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--box-n", default="512x256x256", help="box case: cells per axis of each patch")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--level-n", type=int, default=254)
@@ -1008,6 +1104,10 @@ def main():
         run_learned_case(args)
     elif args.case == "2d":
         run_2d_case(args)
+    elif args.case == "box":
+        run_box_case(args)
+    elif args.case == "box_smoothing":
+        run_box_smoothing_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

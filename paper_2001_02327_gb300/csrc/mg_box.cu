@@ -10,6 +10,10 @@
 // side.  Multigrid level 0 of a patch is its solved region Gamma (n_a + 2
 // cells) with the outer buffer ring as the ghost layer, so its potential is
 // the patch's (n+4) block itself.
+//
+// Launches: every per-cell kernel runs on a 3D grid -- x along the row (in
+// blocks of up to 256 threads), y over rows (several per block when rows are
+// short), z over planes -- so no thread divides to find its cell.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +38,10 @@ struct BoxGeom {
     int tie[3];       // centre of cell N at x_MG = 1 along this axis
     double cR[3];     // right ghost = cR Phi_N when !tie (Sec. 2.4)
     double ih2[3];    // 1 / h_a^2, h_a this axis's cell size on this level
-    float cRf[3], ih2f[3];
+    double d0, inv0;  // diagonal of a cell with no ghost folded in (-2 sum ih2) and its reciprocal
+    int H;            // FP32 colour-split storage: cells of one colour per row, (E_x + 1) / 2
+    long long half;   //   and per colour array, H E_y E_z
+    float cRf[3], ih2f[3], d0f, inv0f;
 };
 
 template <typename T> __device__ __forceinline__ T gsel(double d, float f);
@@ -46,31 +53,84 @@ __device__ __forceinline__ long long box_index(const BoxGeom &g, int i, int j, i
     return ((long long)k * g.E[1] + j) * g.E[0] + i;
 }
 
-// The off-diagonal sum and the diagonal of cell (i, j, k)'s equation (Sec.
-// 2.3 stencil, per-axis cell sizes): per axis the two neighbours, except on
-// coarse levels where a neighbour in the ghost layer is replaced by the ghost
-// rule of Sec. 2.4 folded into the cell's own coefficient (left ghost
-// -Phi_1: -1; right ghost cR Phi_N: +cR; at a tie -Phi_{N-1}, which cancels
-// the left neighbour, or +Phi_1 when N = 1).  Axis order x, y, z.
-template <typename T, int DIM>
-__device__ __forceinline__ void box_terms(const T *__restrict__ phi, const BoxGeom &g, int i, int j, int k,
-                                          long long p, T &other, T &diag)
+// Index of cell (i, j, k) (storage indices, ghost layer included) in a level
+// array of precision T.  FP64 arrays are plain blocks.  FP32 arrays are
+// colour-split: colour (i + j + k) & 1 -- red 0, black 1, as the 1-based
+// active indices give them -- selects one of two arrays of H cells per row,
+// the cell at position i / 2 of its row.  A red cell's six neighbours are all
+// black, so a colour pass reads the other colour's array, writes its own, and
+// consecutive threads touch consecutive words.
+template <typename T> __device__ __forceinline__ long long lidx(const BoxGeom &g, int i, int j, int k);
+template <> __device__ __forceinline__ long long lidx<double>(const BoxGeom &g, int i, int j, int k)
 {
-    const long long st[3] = {1, g.E[0], (long long)g.E[0] * g.E[1]};
+    return box_index(g, i, j, k);
+}
+template <> __device__ __forceinline__ long long lidx<float>(const BoxGeom &g, int i, int j, int k)
+{
+    return ((i + j + k) & 1) * g.half + ((long long)k * g.E[1] + j) * g.H + (i >> 1);
+}
+
+// Division of an unsigned 32-bit n by an invariant d with one multiply-high,
+// an add and shifts (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994, round-up method): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (t + ((n - t) >> min(l, 1))) >>
+// max(l - 1, 0) with t = mulhi(m, n); exact for every n and d >= 1.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+inline FastDiv fast_div(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < d)
+        l++;
+    FastDiv f;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = std::min(l, 1);
+    f.s2 = std::max(l - 1, 0);
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(const FastDiv &f, unsigned n)
+{
+    const unsigned t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// thread coordinates of a 3D launch: x along the row, y over rows, z planes
+__device__ __forceinline__ int gx() { return blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int gy() { return blockIdx.y * blockDim.y + threadIdx.y; }
+__device__ __forceinline__ int gz() { return blockIdx.z; }
+
+// The off-diagonal sum of cell (i, j, k)'s equation and what ghosts add to
+// its diagonal (Sec. 2.3 stencil, per-axis cell sizes): per axis the two
+// neighbours, except on coarse levels where a neighbour in the ghost layer is
+// replaced by the ghost rule of Sec. 2.4 folded into the cell's own
+// coefficient (left ghost -Phi_1: -1; right ghost cR Phi_N: +cR; at a tie
+// -Phi_{N-1}, which cancels the left neighbour, or +Phi_1 when N = 1).  The
+// diagonal is d0 + fold.  Axis order x, y, z.  Returns whether the cell has a
+// ghost neighbour on a coarse level.
+template <typename T, int DIM>
+__device__ __forceinline__ bool box_terms(const T *__restrict__ phi, const BoxGeom &g, int i, int j, int k, T &other,
+                                          T &fold)
+{
     const int id[3] = {i, j, k};
     other = T(0);
-    diag = T(0);
+    fold = T(0);
+    bool folded = false;
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
-        const T left = phi[p - st[a]], right = phi[p + st[a]];
-        T o, self;
+        const T left = phi[lidx<T>(g, i - (a == 0), j - (a == 1), k - (a == 2))];
+        const T right = phi[lidx<T>(g, i + (a == 0), j + (a == 1), k + (a == 2))];
+        const T ih2 = gsel<T>(g.ih2[a], g.ih2f[a]);
+        T o;
         if (g.L == 0) {
             o = left + right;
-            self = T(0);
         } else {
             const bool lo = id[a] == 1, hi = id[a] == g.N[a];
+            T self = lo ? T(-1) : T(0);
             o = lo ? T(0) : left;
-            self = lo ? T(-1) : T(0);
             if (hi) {
                 if (g.tie[a]) {
                     if (g.N[a] >= 2)
@@ -83,49 +143,111 @@ __device__ __forceinline__ void box_terms(const T *__restrict__ phi, const BoxGe
             } else {
                 o = o + right;
             }
+            if (lo || hi) {
+                folded = true;
+                fold = fold + self * ih2;
+            }
         }
-        const T ih2 = gsel<T>(g.ih2[a], g.ih2f[a]);
         other = other + o * ih2;
-        diag = diag + (self - T(2)) * ih2;
     }
+    return folded;
 }
 
-// cell (i, j, k) of the t-th work item of a colour pass: cells with
-// (i + j + k) & 1 == colour (2D: i + j), 1-based, x in pairs
-template <int DIM>
-__device__ __forceinline__ bool colour_cell(const BoxGeom &g, int colour, long long t, int &i, int &j, int &k)
-{
-    const int half = (g.N[0] + 1) >> 1;
-    const long long r = t / half;
-    const int ih = (int)(t - r * half);
-    j = (int)(r % g.N[1]) + 1;
-    k = DIM == 3 ? (int)(r / g.N[1]) + 1 : 0;
-    const int par = (colour - j - k) & 1;   // parity of i
-    i = 2 * ih + (par ? 1 : 2);
-    return i <= g.N[0];
-}
-
-__host__ __device__ inline long long colour_items(const BoxGeom &g, int dim)
-{
-    return (long long)((g.N[0] + 1) >> 1) * g.N[1] * (dim == 3 ? g.N[2] : 1);
-}
-
-// Red-black Gauss-Seidel, one colour (Sec. 2.3 steps 2, 6, 11): each cell of
-// the colour solves its own equation for the current neighbours.
+// Red-black Gauss-Seidel, one colour (Sec. 2.3 steps 2, 6, 11): each cell
+// with (i + j + k) & 1 == colour (2D: i + j; 1-based) solves its own equation
+// for the current neighbours.  Thread x takes the x-th cell of its colour in
+// row (j, k).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) kx_smooth(T *__restrict__ phi, const T *__restrict__ f, BoxGeom g, int colour)
 {
     pdl_begin();
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= colour_items(g, DIM))
+    const int j = gy() + 1, k = DIM == 3 ? gz() + 1 : 0;
+    if (j > g.N[1])
         return;
-    int i, j, k;
-    if (!colour_cell<DIM>(g, colour, t, i, j, k))
+    const int i = 2 * gx() + (((colour - j - k) & 1) ? 1 : 2);
+    if (i > g.N[0])
         return;
-    const long long p = box_index(g, i, j, k);
-    T other, diag;
-    box_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
-    phi[p] = (f[p] - other) / diag;
+    T other, fold;
+    const bool folded = box_terms<T, DIM>(phi, g, i, j, k, other, fold);
+    const long long p = lidx<T>(g, i, j, k);
+    const T rhs = f[p] - other;
+    phi[p] = folded ? rhs / (gsel<T>(g.d0, g.d0f) + fold) : rhs * gsel<T>(g.inv0, g.inv0f);
+}
+
+// The same colour pass on colour-split FP32 storage, four cells of the
+// colour per thread: row (j, k) of this colour holds cell i = 2m + p at
+// position m (p = the colour's parity of i in this row), so cells m0..m0+3
+// need the other colour's positions m0-1..m0+4 of the same row and m0..m0+3
+// of the rows and planes around it -- aligned float4 loads (H is a multiple
+// of 4) and one more word.  Cells next to a ghost on a coarse level take the
+// per-cell form with the ghost rule folded in.
+// Threads run over (row, group of four) linearly -- q groups per row, no
+// idle threads at row ends -- the row and plane found by FastDiv.
+template <int DIM>
+__global__ void __launch_bounds__(256) kx_smooth32(float *__restrict__ phi, const float *__restrict__ f, BoxGeom g,
+                                                   int colour, unsigned total, int q, FastDiv dq, FastDiv dny)
+{
+    pdl_begin();
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const unsigned r = fdiv(dq, t);
+    const unsigned kz = DIM == 3 ? fdiv(dny, r) : 0u;
+    const int j = (int)(r - kz * (unsigned)g.N[1]) + 1, k = DIM == 3 ? (int)kz + 1 : 0;
+    const int par = (colour - j - k) & 1;
+    const int m0 = 4 * (int)(t - r * (unsigned)q);
+    if (2 * m0 + par > g.N[0])
+        return;
+    const int row = (k * g.E[1] + j) * g.H;
+    const float *o = phi + (colour ^ 1) * g.half + row;
+    float *own = phi + colour * g.half + row;
+    const float *fr = f + colour * g.half + row;
+    const float4 c = *reinterpret_cast<const float4 *>(o + m0);
+    const float s = par ? o[m0 + 4] : o[m0 - 1];
+    const float4 yd = *reinterpret_cast<const float4 *>(o + m0 - g.H);
+    const float4 yu = *reinterpret_cast<const float4 *>(o + m0 + g.H);
+    float4 zd = make_float4(0.f, 0.f, 0.f, 0.f), zu = zd;
+    if (DIM == 3) {
+        const int pl = g.E[1] * g.H;
+        zd = *reinterpret_cast<const float4 *>(o + m0 - pl);
+        zu = *reinterpret_cast<const float4 *>(o + m0 + pl);
+    }
+    const float4 fv = *reinterpret_cast<const float4 *>(fr + m0);
+    const float xl[4] = {par ? c.x : s, par ? c.y : c.x, par ? c.z : c.y, par ? c.w : c.z};
+    const float xr[4] = {par ? c.y : c.x, par ? c.z : c.y, par ? c.w : c.z, par ? s : c.w};
+    const float ydv[4] = {yd.x, yd.y, yd.z, yd.w}, yuv[4] = {yu.x, yu.y, yu.z, yu.w};
+    const float zdv[4] = {zd.x, zd.y, zd.z, zd.w}, zuv[4] = {zu.x, zu.y, zu.z, zu.w};
+    const float fvv[4] = {fv.x, fv.y, fv.z, fv.w};
+    float nv[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        float other = (xl[e] + xr[e]) * g.ih2f[0];
+        other = other + (ydv[e] + yuv[e]) * g.ih2f[1];
+        if (DIM == 3)
+            other = other + (zdv[e] + zuv[e]) * g.ih2f[2];
+        nv[e] = (fvv[e] - other) * g.inv0f;
+    }
+    const int i0 = 2 * m0 + par;
+    const bool row_edge = g.L > 0 && (j == 1 || j == g.N[1] || (DIM == 3 && (k == 1 || k == g.N[2])));
+    const bool plain = i0 >= 1 && i0 + 6 <= g.N[0] && (g.L == 0 || (!row_edge && i0 > 1 && i0 + 6 < g.N[0]));
+    if (plain) {
+        *reinterpret_cast<float4 *>(own + m0) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int i = i0 + 2 * e;
+        if (i < 1 || i > g.N[0])
+            continue;
+        if (g.L > 0 && (row_edge || i == 1 || i == g.N[0])) {
+            float other, fold;
+            const bool folded = box_terms<float, DIM>(phi, g, i, j, k, other, fold);
+            const float rhs = fr[m0 + e] - other;
+            own[m0 + e] = folded ? rhs / (g.d0f + fold) : rhs * g.inv0f;
+        } else {
+            own[m0 + e] = nv[e];
+        }
+    }
 }
 
 // r = f - A Phi at cell (i, j, k)
@@ -133,10 +255,10 @@ template <typename T, int DIM>
 __device__ __forceinline__ T box_resid(const T *__restrict__ phi, const T *__restrict__ f, const BoxGeom &g, int i,
                                        int j, int k)
 {
-    const long long p = box_index(g, i, j, k);
-    T other, diag;
-    box_terms<T, DIM>(phi, g, i, j, k, p, other, diag);
-    return f[p] - (other + diag * phi[p]);
+    T other, fold;
+    box_terms<T, DIM>(phi, g, i, j, k, other, fold);
+    const long long p = lidx<T>(g, i, j, k);
+    return f[p] - (other + (gsel<T>(g.d0, g.d0f) + fold) * phi[p]);
 }
 
 // Residual of the fine level restricted to the coarse right-hand side (Sec.
@@ -151,38 +273,34 @@ __global__ void __launch_bounds__(256) kx_resid_restrict(const T *__restrict__ p
                                                          BoxGeom gc, int cmask, T wk)
 {
     pdl_begin();
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long tot = (long long)gc.N[0] * gc.N[1] * (DIM == 3 ? gc.N[2] : 1);
-    if (t >= tot)
+    const int I = gx() + 1, J = gy() + 1, K = DIM == 3 ? gz() + 1 : 0;
+    if (I > gc.N[0] || J > gc.N[1])
         return;
-    const long long r = t / gc.N[0];
-    const int I = (int)(t - r * gc.N[0]) + 1;
-    const int J = (int)(r % gc.N[1]) + 1;
-    const int K = DIM == 3 ? (int)(r / gc.N[1]) + 1 : 0;
-    int c0[3], nc[3];
-    const int C[3] = {I, J, K};
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        if (a < DIM && (cmask >> a) & 1) {
-            c0[a] = 2 * C[a] - 1;
-            nc[a] = 2 * C[a] <= gf.N[a] ? 2 : 1;
-        } else {
-            c0[a] = C[a];
-            nc[a] = 1;
-        }
-    }
+    // first child and child count per axis
+    const bool cx = cmask & 1, cy = (cmask >> 1) & 1, cz = DIM == 3 && ((cmask >> 2) & 1);
+    const int x0 = cx ? 2 * I - 1 : I, y0 = cy ? 2 * J - 1 : J, z0 = cz ? 2 * K - 1 : K;
+    const int nx = cx && 2 * I <= gf.N[0] ? 2 : 1, ny = cy && 2 * J <= gf.N[1] ? 2 : 1,
+              nz = cz && 2 * K <= gf.N[2] ? 2 : 1;
     T sz = T(0);
-    for (int dz = 0; dz < (DIM == 3 ? nc[2] : 1); dz++) {
-        T sy = T(0);
-        for (int dy = 0; dy < nc[1]; dy++) {
-            T sx = T(0);
-            for (int dx = 0; dx < nc[0]; dx++)
-                sx = sx + box_resid<T, DIM>(phi, f, gf, c0[0] + dx, c0[1] + dy, c0[2] + dz);
-            sy = sy + sx;
+#pragma unroll
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); dz++) {
+        if (dz < nz) {
+            T sy = T(0);
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++) {
+                if (dy < ny) {
+                    T sx = T(0);
+#pragma unroll
+                    for (int dx = 0; dx < 2; dx++)
+                        if (dx < nx)
+                            sx = sx + box_resid<T, DIM>(phi, f, gf, x0 + dx, y0 + dy, z0 + dz);
+                    sy = sy + sx;
+                }
+            }
+            sz = sz + sy;
         }
-        sz = sz + sy;
     }
-    const long long pc = box_index(gc, I, J, K);
+    const long long pc = lidx<T>(gc, I, J, K);
     fc[pc] = sz * wk;
     phic[pc] = T(0);
 }
@@ -211,7 +329,7 @@ __device__ __forceinline__ T ghost_read(const T *__restrict__ phic, const BoxGeo
             }
         }
     }
-    T v = phic[box_index(g, id[0], id[1], id[2])];
+    T v = phic[lidx<T>(g, id[0], id[1], id[2])];
 #pragma unroll
     for (int a = 0; a < DIM; a++)
         v = v * c[a];
@@ -228,45 +346,35 @@ __global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom 
                                                   BoxGeom gc, int cmask)
 {
     pdl_begin();
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long tot = (long long)gf.N[0] * gf.N[1] * (DIM == 3 ? gf.N[2] : 1);
-    if (t >= tot)
+    const int i = gx() + 1, j = gy() + 1, k = DIM == 3 ? gz() + 1 : 0;
+    if (i > gf.N[0] || j > gf.N[1])
         return;
-    const long long r = t / gf.N[0];
-    const int i = (int)(t - r * gf.N[0]) + 1;
-    const int j = (int)(r % gf.N[1]) + 1;
-    const int k = DIM == 3 ? (int)(r / gf.N[1]) + 1 : 0;
-    const int F[3] = {i, j, k};
-    int ix[3][2], nt[3];
-    T w[3][2];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        if (a < DIM && (cmask >> a) & 1) {
-            const int near = (F[a] + 1) >> 1;
-            ix[a][0] = near;
-            ix[a][1] = (F[a] & 1) ? near - 1 : near + 1;
-            w[a][0] = T(0.75);
-            w[a][1] = T(0.25);
-            nt[a] = 2;
-        } else {
-            ix[a][0] = ix[a][1] = F[a];
-            w[a][0] = T(1);
-            w[a][1] = T(0);
-            nt[a] = 1;
-        }
+    // per axis: the near and far coarse cells and their weights (one tap of
+    // weight 1 along an axis that did not coarsen)
+    const bool cx = cmask & 1, cy = (cmask >> 1) & 1, cz = DIM == 3 && ((cmask >> 2) & 1);
+    const int ax0 = cx ? (i + 1) >> 1 : i, ay0 = cy ? (j + 1) >> 1 : j, az0 = cz ? (k + 1) >> 1 : k;
+    const int ax1 = (i & 1) ? ax0 - 1 : ax0 + 1, ay1 = (j & 1) ? ay0 - 1 : ay0 + 1, az1 = (k & 1) ? az0 - 1 : az0 + 1;
+    const T w0 = T(0.75), w1 = T(0.25);
+    auto row = [&](int y, int z) {   // interpolated along x
+        if (!cx)
+            return T(0) + T(1) * ghost_read<T, DIM>(phic, gc, ax0, y, z);
+        T v = T(0) + w0 * ghost_read<T, DIM>(phic, gc, ax0, y, z);
+        return v + w1 * ghost_read<T, DIM>(phic, gc, ax1, y, z);
+    };
+    auto plane = [&](int z) {        // then along y
+        if (!cy)
+            return T(0) + row(ay0, z);
+        T v = T(0) + w0 * row(ay0, z);
+        return v + w1 * row(ay1, z);
+    };
+    T vz;                            // then along z
+    if (!cz) {
+        vz = T(0) + plane(az0);
+    } else {
+        vz = T(0) + w0 * plane(az0);
+        vz = vz + w1 * plane(az1);
     }
-    T vz = T(0);
-    for (int cz = 0; cz < (DIM == 3 ? nt[2] : 1); cz++) {
-        T vy = T(0);
-        for (int cy = 0; cy < nt[1]; cy++) {
-            T vx = T(0);
-            for (int cx = 0; cx < nt[0]; cx++)
-                vx = vx + w[0][cx] * ghost_read<T, DIM>(phic, gc, ix[0][cx], ix[1][cy], ix[2][cz]);
-            vy = vy + (nt[1] == 2 ? w[1][cy] * vx : vx);
-        }
-        vz = vz + (DIM == 3 && nt[2] == 2 ? w[2][cz] * vy : vy);
-    }
-    phif[box_index(gf, i, j, k)] += vz;
+    phif[lidx<T>(gf, i, j, k)] += vz;
 }
 
 constexpr int kNormBlocks = 152 * 4;   // fixed grid of the norm reduction: the same partial sums every call
@@ -290,10 +398,11 @@ __device__ __forceinline__ double block_sum(double v)
 }
 
 // ||f - A Phi||^2 over the active cells of multigrid level 0 in FP64 (Sec.
-// 2.3 step 14), per block into part[blockIdx.x].  zero_inside: the potential
-// taken as zero on the active cells (the ghost layer as stored), for ||b||.
-// Mixed precision (f32 != NULL): the residual is also the next defect, written
-// as FP32 into f32, with the FP32 correction e32 cleared.
+// 2.3 step 14), per block into part[blockIdx.x]; block b takes rows b,
+// b + gridDim.x, ...  zero_inside: the potential taken as zero on the active
+// cells (the ghost layer as stored), for ||b||.  Mixed precision (f32 !=
+// NULL): the residual is also the next defect, written as FP32 into f32, with
+// the FP32 correction e32 cleared.
 template <int DIM>
 __global__ void __launch_bounds__(kNormThreads) kx_resid_norm(const double *__restrict__ phi,
                                                                const double *__restrict__ f, BoxGeom g, int zero_inside,
@@ -301,35 +410,35 @@ __global__ void __launch_bounds__(kNormThreads) kx_resid_norm(const double *__re
                                                                float *__restrict__ e32)
 {
     pdl_begin();
-    const long long tot = (long long)g.N[0] * g.N[1] * (DIM == 3 ? g.N[2] : 1);
+    const int rows = g.N[1] * (DIM == 3 ? g.N[2] : 1);
     double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / g.N[0];
-        const int i = (int)(t - r * g.N[0]) + 1;
-        const int j = (int)(r % g.N[1]) + 1;
-        const int k = DIM == 3 ? (int)(r / g.N[1]) + 1 : 0;
-        const long long p = box_index(g, i, j, k);
-        double res;
-        if (zero_inside) {
-            // only the ghost-layer neighbours (level 0: boundary data) remain
-            const long long st[3] = {1, g.E[0], (long long)g.E[0] * g.E[1]};
-            const int id[3] = {i, j, k};
-            double other = 0.0;
-            for (int a = 0; a < DIM; a++) {
-                const double left = id[a] == 1 ? phi[p - st[a]] : 0.0;
-                const double right = id[a] == g.N[a] ? phi[p + st[a]] : 0.0;
-                other = other + (left + right) * g.ih2[a];
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % g.N[1] + 1;
+        const int k = DIM == 3 ? row / g.N[1] + 1 : 0;
+        for (int i = threadIdx.x + 1; i <= g.N[0]; i += blockDim.x) {
+            const long long p = box_index(g, i, j, k);
+            double res;
+            if (zero_inside) {
+                // only the ghost-layer neighbours (level 0: boundary data) remain
+                const long long st[3] = {1, g.E[0], (long long)g.E[0] * g.E[1]};
+                const int id[3] = {i, j, k};
+                double other = 0.0;
+                for (int a = 0; a < DIM; a++) {
+                    const double left = id[a] == 1 ? phi[p - st[a]] : 0.0;
+                    const double right = id[a] == g.N[a] ? phi[p + st[a]] : 0.0;
+                    other = other + (left + right) * g.ih2[a];
+                }
+                res = f[p] - other;
+            } else {
+                res = box_resid<double, DIM>(phi, f, g, i, j, k);
             }
-            res = f[p] - other;
-        } else {
-            res = box_resid<double, DIM>(phi, f, g, i, j, k);
+            if (f32) {
+                const long long q = lidx<float>(g, i, j, k);
+                f32[q] = (float)res;
+                e32[q] = 0.0f;
+            }
+            acc += res * res;
         }
-        if (f32) {
-            f32[p] = (float)res;
-            e32[p] = 0.0f;
-        }
-        acc += res * res;
     }
     const double s = block_sum(acc);
     if (threadIdx.x == 0)
@@ -354,16 +463,10 @@ template <int DIM>
 __global__ void __launch_bounds__(256) kx_accumulate(double *__restrict__ phi, const float *__restrict__ e32, BoxGeom g)
 {
     pdl_begin();
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long tot = (long long)g.N[0] * g.N[1] * (DIM == 3 ? g.N[2] : 1);
-    if (t >= tot)
+    const int i = gx() + 1, j = gy() + 1, k = DIM == 3 ? gz() + 1 : 0;
+    if (i > g.N[0] || j > g.N[1])
         return;
-    const long long r = t / g.N[0];
-    const int i = (int)(t - r * g.N[0]) + 1;
-    const int j = (int)(r % g.N[1]) + 1;
-    const int k = DIM == 3 ? (int)(r / g.N[1]) + 1 : 0;
-    const long long p = box_index(g, i, j, k);
-    phi[p] += (double)e32[p];
+    phi[box_index(g, i, j, k)] += (double)e32[lidx<float>(g, i, j, k)];
 }
 
 // Patch geometry for the kernels that work on the (n+4) blocks.
@@ -371,14 +474,6 @@ struct PatchDims {
     int n[3];     // Omega cells per axis (z: 1 in 2D)
     int B[3];     // (n+4) block extents (z: 1 in 2D)
 };
-
-__device__ __forceinline__ void block_coords(const PatchDims &d, int dim, long long t, int s[3])
-{
-    const long long r = t / d.B[0];
-    s[0] = (int)(t - r * d.B[0]);
-    s[1] = (int)(r % d.B[1]);
-    s[2] = dim == 3 ? (int)(r / d.B[1]) : 0;
-}
 
 // ring of a storage index of the (n+4) block: 2 for Omega, 1 for the inner
 // buffer ring (Gamma minus Omega), 0 for the outer ring
@@ -392,6 +487,19 @@ __device__ __forceinline__ int block_ring(const PatchDims &d, int dim, const int
     return ring;
 }
 
+// block coordinates of this thread (x, y, z over the (n+4) block); false
+// outside it
+__device__ __forceinline__ bool block_cell(const PatchDims &d, int s[3], long long &t)
+{
+    s[0] = gx();
+    s[1] = gy();
+    s[2] = gz();
+    if (s[0] >= d.B[0] || s[1] >= d.B[1])
+        return false;
+    t = ((long long)s[2] * d.B[1] + s[1]) * d.B[0] + s[0];
+    return true;
+}
+
 // mg_box_set_density: Omega density into the patch's density block; patch 0
 // also the inner-ring density (from the (n+2) block bc_rho) and the outer-ring
 // potential (from the (n+4) block bc_phi), the outer ring's density zero.
@@ -400,12 +508,10 @@ __global__ void __launch_bounds__(256) kx_place(PatchDims d, int dim, const doub
                                                 double *__restrict__ rho_blk, double *__restrict__ phi_blk)
 {
     pdl_begin();
-    const long long tot = (long long)d.B[0] * d.B[1] * d.B[2];
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= tot)
-        return;
     int s[3];
-    block_coords(d, dim, t, s);
+    long long t;
+    if (!block_cell(d, s, t))
+        return;
     const int ring = block_ring(d, dim, s);
     if (ring == 2) {
         const long long q = dim == 3 ? (((long long)(s[2] - 2) * d.n[1] + (s[1] - 2)) * d.n[0] + (s[0] - 2))
@@ -436,12 +542,10 @@ __global__ void __launch_bounds__(256) kx_interface(PatchDims dc, PatchDims dp, 
                                                     double *__restrict__ phi_c, double *__restrict__ rho_c, int mode)
 {
     pdl_begin();
-    const long long tot = (long long)dc.B[0] * dc.B[1] * dc.B[2];
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= tot)
-        return;
     int s[3];
-    block_coords(dc, dim, t, s);
+    long long t;
+    if (!block_cell(dc, s, t))
+        return;
     const int ring = block_ring(dc, dim, s);
     if (mode == 1 && ring == 0)
         return;
@@ -491,12 +595,10 @@ __global__ void __launch_bounds__(256) kx_rhs(PatchDims d, int dim, const double
                                               double *__restrict__ f, double fourpiG)
 {
     pdl_begin();
-    const long long tot = (long long)d.B[0] * d.B[1] * d.B[2];
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= tot)
-        return;
     int s[3];
-    block_coords(d, dim, t, s);
+    long long t;
+    if (!block_cell(d, s, t))
+        return;
     f[t] = block_ring(d, dim, s) >= 1 ? fourpiG * rho[t] : 0.0;
 }
 
@@ -504,31 +606,29 @@ __global__ void __launch_bounds__(256) kx_rhs(PatchDims d, int dim, const double
 __global__ void __launch_bounds__(256) kx_zero_gamma(PatchDims d, int dim, double *__restrict__ phi)
 {
     pdl_begin();
-    const long long tot = (long long)d.B[0] * d.B[1] * d.B[2];
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= tot)
-        return;
     int s[3];
-    block_coords(d, dim, t, s);
+    long long t;
+    if (!block_cell(d, s, t))
+        return;
     if (block_ring(d, dim, s) >= 1)
         phi[t] = 0.0;
 }
 
 // F = -grad Phi on Omega (Eq. 2: 4/3 of the centred difference over 2h minus
-// 1/3 of the one over 4h; stencil 1: the two-point centred difference), and
-// the potential on Omega.  Component a at F[a * cells + cell].
-__global__ void __launch_bounds__(256) kx_forces(PatchDims d, int dim, double h, const double *__restrict__ phi,
-                                                 double *__restrict__ F, double *__restrict__ phi_out, int stencil)
+// 1/3 of the one over 4h, i2h = 1/(2h), i4h = 1/(4h); stencil 1: the
+// two-point centred difference), and the potential on Omega.  Component a at
+// F[a * cells + cell].
+__global__ void __launch_bounds__(256) kx_forces(PatchDims d, int dim, double i2h, double i4h,
+                                                 const double *__restrict__ phi, double *__restrict__ F,
+                                                 double *__restrict__ phi_out, int stencil)
 {
     pdl_begin();
-    const long long cells = (long long)d.n[0] * d.n[1] * (dim == 3 ? d.n[2] : 1);
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= cells)
+    const int x = gx(), y = gy(), z = gz();
+    if (x >= d.n[0] || y >= d.n[1])
         return;
-    const long long r = t / d.n[0];
-    const int i = (int)(t - r * d.n[0]) + 2;
-    const int j = (int)(r % d.n[1]) + 2;
-    const int k = dim == 3 ? (int)(r / d.n[1]) + 2 : 0;
+    const long long cells = (long long)d.n[0] * d.n[1] * (dim == 3 ? d.n[2] : 1);
+    const long long t = ((long long)z * d.n[1] + y) * d.n[0] + x;
+    const int i = x + 2, j = y + 2, k = dim == 3 ? z + 2 : 0;
     const long long st[3] = {1, d.B[0], (long long)d.B[0] * d.B[1]};
     const long long p = ((long long)k * d.B[1] + j) * d.B[0] + i;
     for (int a = 0; a < dim; a++) {
@@ -536,9 +636,9 @@ __global__ void __launch_bounds__(256) kx_forces(PatchDims d, int dim, double h,
         double gr;
         if (stencil == 0) {
             const double d2 = phi[p + 2 * st[a]] - phi[p - 2 * st[a]];
-            gr = (4.0 / 3.0) * d1 / (2.0 * h) - (1.0 / 3.0) * d2 / (4.0 * h);
+            gr = (4.0 / 3.0) * d1 * i2h - (1.0 / 3.0) * d2 * i4h;
         } else {
-            gr = d1 / (2.0 * h);
+            gr = d1 * i2h;
         }
         if (F)
             F[a * cells + t] = -gr;
@@ -612,6 +712,15 @@ BoxGeom level_geom(const int n[3], int dim, double h, int L)
         g.cRf[a] = (float)g.cR[a];
         g.ih2f[a] = (float)g.ih2[a];
     }
+    double d = 0.0;
+    for (int a = 0; a < dim; a++)
+        d += -2.0 * g.ih2[a];
+    g.d0 = d;
+    g.inv0 = 1.0 / d;
+    g.d0f = (float)g.d0;
+    g.inv0f = (float)g.inv0;
+    g.H = ((g.E[0] + 1) / 2 + 3) & ~3;   // a multiple of 4: rows start 16-byte aligned
+    g.half = (long long)g.H * g.E[1] * g.E[2];
     return g;
 }
 
@@ -685,17 +794,37 @@ mg_status bfail_cuda(mg_box *b, cudaError_t e, const char *what)
             return bfail_cuda((b), e_, #call);         \
     } while (0)
 
+// A 3D launch over nx x ny x nz threads: blocks of 256 threads, 32..256 of
+// them along x (the width that leaves the fewest idle threads at the row's
+// end, the wider on a tie), the rest of the block over rows.
 template <typename... KArgs, typename... Args>
-cudaError_t launch(void (*kernel)(KArgs...), long long items, cudaStream_t s, Args... args)
+cudaError_t launch3(void (*kernel)(KArgs...), long long nx, long long ny, long long nz, cudaStream_t s, Args... args)
 {
-    if (items <= 0)
+    if (nx <= 0 || ny <= 0 || nz <= 0)
         return cudaSuccess;
-    mg_launch_kernel(kernel, dim3((unsigned)((items + 255) / 256)), dim3(256), 0, s, args...);
+    int bx = 256;
+    for (int w = 128; w >= 32; w /= 2)
+        if ((nx + w - 1) / w * w < (nx + bx - 1) / bx * bx)
+            bx = w;
+    const int by = 256 / bx;
+    mg_launch_kernel(kernel, dim3((unsigned)((nx + bx - 1) / bx), (unsigned)((ny + by - 1) / by), (unsigned)nz),
+                     dim3(bx, by, 1), 0, s, args...);
     return cudaGetLastError();
 }
 
-long long level_cells(const BoxGeom &g, int dim) { return (long long)g.N[0] * g.N[1] * (dim == 3 ? g.N[2] : 1); }
 long long block_cells(const PatchDims &d) { return (long long)d.B[0] * d.B[1] * d.B[2]; }
+
+// a launch over the active cells of a level, or over a patch's (n+4) block
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cells(void (*kernel)(KArgs...), const BoxGeom &g, cudaStream_t s, Args... args)
+{
+    return launch3(kernel, g.N[0], g.N[1], g.N[2], s, args...);
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_block(void (*kernel)(KArgs...), const PatchDims &d, cudaStream_t s, Args... args)
+{
+    return launch3(kernel, d.B[0], d.B[1], d.B[2], s, args...);
+}
 
 template <typename T> T *lphi(const BoxLevel &l);
 template <typename T> T *lf(const BoxLevel &l);
@@ -704,14 +833,33 @@ template <> double *lf<double>(const BoxLevel &l) { return l.f64; }
 template <> float *lphi<float>(const BoxLevel &l) { return l.phi32; }
 template <> float *lf<float>(const BoxLevel &l) { return l.f32; }
 
+// one colour pass: FP64 one cell per thread, FP32 (colour-split) four
+cudaError_t colour_pass(int dim, double *phi, const double *f, const BoxGeom &g, int c, cudaStream_t s)
+{
+    const int half = (g.N[0] + 1) >> 1;
+    return dim == 3 ? launch3(kx_smooth<double, 3>, half, g.N[1], g.N[2], s, phi, f, g, c)
+                    : launch3(kx_smooth<double, 2>, half, g.N[1], 1, s, phi, f, g, c);
+}
+cudaError_t colour_pass(int dim, float *phi, const float *f, const BoxGeom &g, int c, cudaStream_t s)
+{
+    const int q = ((g.N[0] >> 1) + 4) / 4;   // positions 0..N_x/2 in fours
+    const unsigned total = (unsigned)q * (unsigned)g.N[1] * (unsigned)(dim == 3 ? g.N[2] : 1);
+    const dim3 grid((total + 255) / 256);
+    if (dim == 3)
+        mg_launch_kernel(kx_smooth32<3>, grid, dim3(256), 0, s, phi, f, g, c, total, q, fast_div(q),
+                         fast_div(g.N[1]));
+    else
+        mg_launch_kernel(kx_smooth32<2>, grid, dim3(256), 0, s, phi, f, g, c, total, q, fast_div(q),
+                         fast_div(g.N[1]));
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t smooth(const mg_box *b, const BoxLevel &l, int sweeps, cudaStream_t s)
 {
-    const long long items = colour_items(l.g, b->dim);
     for (int sw = 0; sw < sweeps; sw++)
         for (int c = 0; c < 2; c++) {
-            cudaError_t e = b->dim == 3 ? launch(kx_smooth<T, 3>, items, s, lphi<T>(l), (const T *)lf<T>(l), l.g, c)
-                                        : launch(kx_smooth<T, 2>, items, s, lphi<T>(l), (const T *)lf<T>(l), l.g, c);
+            cudaError_t e = colour_pass(b->dim, lphi<T>(l), (const T *)lf<T>(l), l.g, c, s);
             if (e)
                 return e;
         }
@@ -731,19 +879,17 @@ cudaError_t vcycle(const mg_box *b, const BoxPatch &P, cudaStream_t s)
     for (int L = 0; L < Lc && !e; L++) {
         const BoxLevel &fl = P.lv[L], &cl = P.lv[L + 1];
         const T wk = (T)std::ldexp(1.0, -fl.ncoars);
-        const long long items = level_cells(cl.g, dim);
-        e = dim == 3 ? launch(kx_resid_restrict<T, 3>, items, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl), fl.g,
-                              lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk)
-                     : launch(kx_resid_restrict<T, 2>, items, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl), fl.g,
-                              lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk);
+        e = dim == 3 ? launch_cells(kx_resid_restrict<T, 3>, cl.g, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl),
+                                    fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk)
+                     : launch_cells(kx_resid_restrict<T, 2>, cl.g, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl),
+                                    fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk);
         if (!e)
             e = smooth<T>(b, cl, b->opt.nu_pre, s);
     }
     for (int L = Lc; L > 0 && !e; L--) {
         const BoxLevel &cl = P.lv[L], &fl = P.lv[L - 1];
-        const long long items = level_cells(fl.g, dim);
-        e = dim == 3 ? launch(kx_prolong<T, 3>, items, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask)
-                     : launch(kx_prolong<T, 2>, items, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask);
+        e = dim == 3 ? launch_cells(kx_prolong<T, 3>, fl.g, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask)
+                     : launch_cells(kx_prolong<T, 2>, fl.g, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask);
         if (!e)
             e = smooth<T>(b, fl, b->opt.nu_post, s);
     }
@@ -756,8 +902,7 @@ cudaError_t resid_norm(const mg_box *b, const BoxPatch &P, int zero_inside, bool
 {
     const BoxLevel &l = P.lv[0];
     float *f32 = write32 ? l.f32 : nullptr, *e32 = write32 ? l.phi32 : nullptr;
-    const long long tot = level_cells(l.g, b->dim);
-    const int blocks = (int)std::min<long long>(kNormBlocks, (tot + kNormThreads - 1) / kNormThreads);
+    const int blocks = std::min(kNormBlocks, l.g.N[1] * l.g.N[2]);
     if (b->dim == 3)
         mg_launch_kernel(kx_resid_norm<3>, dim3(blocks), dim3(kNormThreads), 0, s, (const double *)l.phi64,
                          (const double *)l.f64, l.g, zero_inside, b->part, f32, e32);
@@ -788,8 +933,8 @@ cudaError_t iteration(mg_box *b, int pi, int ncyc, cudaStream_t s)
         for (int c = 0; c < ncyc && !e; c++)
             e = vcycle<float>(b, P, s);
         if (!e)
-            e = launch(b->dim == 3 ? kx_accumulate<3> : kx_accumulate<2>, level_cells(P.lv[0].g, b->dim), s,
-                       P.lv[0].phi64, (const float *)P.lv[0].phi32, P.lv[0].g);
+            e = launch_cells(b->dim == 3 ? kx_accumulate<3> : kx_accumulate<2>, P.lv[0].g, s, P.lv[0].phi64,
+                             (const float *)P.lv[0].phi32, P.lv[0].g);
     }
     if (!e)
         e = resid_norm(b, P, 0, mixed(b), P.scal + 1, s);
@@ -835,23 +980,22 @@ cudaError_t prelude(mg_box *b, int pi, cudaStream_t s)
 {
     BoxPatch &P = b->p[pi];
     const int dim = b->dim;
-    const long long nb = block_cells(P.d);
     cudaError_t e;
     if (pi == 0) {
-        e = launch(kx_zero_gamma, nb, s, P.d, dim, P.phi);
+        e = launch_block(kx_zero_gamma, P.d, s, P.d, dim, P.phi);
     } else {
         const BoxPatch &Q = b->p[P.parent];
-        e = launch(kx_interface, nb, s, P.d, Q.d, dim, P.off[0], P.off[1], P.off[2], (const double *)Q.phi,
-                   (const double *)Q.rho, P.phi, P.rho, 0);
+        e = launch_block(kx_interface, P.d, s, P.d, Q.d, dim, P.off[0], P.off[1], P.off[2], (const double *)Q.phi,
+                         (const double *)Q.rho, P.phi, P.rho, 0);
     }
     if (!e)
-        e = launch(kx_rhs, nb, s, P.d, dim, (const double *)P.rho, P.f0, 4.0 * M_PI * b->desc.G);
+        e = launch_block(kx_rhs, P.d, s, P.d, dim, (const double *)P.rho, P.f0, 4.0 * M_PI * b->desc.G);
     if (!e)
         e = resid_norm(b, P, 1, false, P.scal, s);
     if (!e && pi > 0 && b->opt.guess == MG_GUESS_INTERP) {
         const BoxPatch &Q = b->p[P.parent];
-        e = launch(kx_interface, nb, s, P.d, Q.d, dim, P.off[0], P.off[1], P.off[2], (const double *)Q.phi,
-                   (const double *)Q.rho, P.phi, P.rho, 1);
+        e = launch_block(kx_interface, P.d, s, P.d, Q.d, dim, P.off[0], P.off[1], P.off[2], (const double *)Q.phi,
+                         (const double *)Q.rho, P.phi, P.rho, 1);
     }
     if (!e)
         e = resid_norm(b, P, 0, mixed(b), P.scal + 1, s);
@@ -890,8 +1034,9 @@ mg_status check_box_desc(const mg_box_desc &d)
         double cells = 1.0;
         for (int a = 0; a < d.dim; a++) {
             const int n = d.n[l][a];
-            if (n < 2 || n > (1 << 20) || (l > 0 && (n & 1)))
-                return bfail(nullptr, MG_EINVAL, "patch %d axis %d: n=%d (need >= 2, even above patch 0)", l, a, n);
+            if (n < 2 || n > 65000 || (l > 0 && (n & 1)))   // launch grids: y and z extents below 2^16
+                return bfail(nullptr, MG_EINVAL, "patch %d axis %d: n=%d (need 2..65000, even above patch 0)", l, a,
+                             n);
             cells *= (double)(n + 4);
         }
         if (cells > 2147483647.0)
@@ -1030,11 +1175,12 @@ mg_status mg_box_create(const mg_box_desc *desc, const mg_options *opt, mg_box *
                     of.push_back(bytes);
                     bytes += up256(c * 8);
                 }
-            } else {
+            } else {   // colour-split: two arrays of `half` cells, and the word past the last row
+                const size_t cs = 2 * (size_t)P.lv[L].g.half + 16;
                 of.push_back(bytes);
-                bytes += up256(c * 4);
+                bytes += up256(cs * 4);
                 of.push_back(bytes);
-                bytes += up256(c * 4);
+                bytes += up256(cs * 4);
             }
         }
         long long om = 1;
@@ -1137,7 +1283,7 @@ mg_status mg_box_set_density(mg_box *b, int patch, const double *rho, const doub
         BCK(b, take(bc_rho, d_bcr, b->stage + nb, ng));
         BCK(b, take(bc_phi, d_bcp, b->stage + 2 * nb, nb));
     }
-    BCK(b, launch(kx_place, (long long)nb, b->stream, P.d, dim, d_rho, d_bcr, d_bcp, P.rho, P.phi));
+    BCK(b, launch_block(kx_place, P.d, b->stream, P.d, dim, d_rho, d_bcr, d_bcp, P.rho, P.phi));
     if (host_in)
         BCK(b, cudaStreamSynchronize(b->stream));
     P.density_set = true;
@@ -1217,8 +1363,8 @@ mg_status mg_box_forces(mg_box *b, int patch, double *phi_out, double *F_out)
     const bool F_dev = F_out && device_ptr(F_out), P_dev = phi_out && device_ptr(phi_out);
     double *dF = F_out ? (F_dev ? F_out : b->stage) : nullptr;
     double *dP = phi_out ? (P_dev ? phi_out : b->stage + (size_t)dim * nr) : nullptr;
-    BCK(b, launch(kx_forces, (long long)nr, b->stream, P.d, dim, P.h, (const double *)P.phi, dF, dP,
-                  b->opt.force_stencil));
+    BCK(b, launch3(kx_forces, P.n[0], P.n[1], P.n[2], b->stream, P.d, dim, 1.0 / (2.0 * P.h), 1.0 / (4.0 * P.h),
+                   (const double *)P.phi, dF, dP, b->opt.force_stencil));
     bool sync = false;
     if (F_out && !F_dev) {
         BCK(b, cudaMemcpyAsync(F_out, dF, (size_t)dim * nr * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
@@ -1259,12 +1405,9 @@ mg_status mg_box_time_smoothing(mg_box *b, int patch, int L, int launches, doubl
         return bfail(b, MG_EINVAL, "multigrid level %d out of range", L);
     const BoxLevel &v = P.lv[L];
     auto pass = [&](int c) -> cudaError_t {
-        const long long items = colour_items(v.g, b->dim);
         if (mixed(b))
-            return b->dim == 3 ? launch(kx_smooth<float, 3>, items, b->stream, v.phi32, (const float *)v.f32, v.g, c)
-                               : launch(kx_smooth<float, 2>, items, b->stream, v.phi32, (const float *)v.f32, v.g, c);
-        return b->dim == 3 ? launch(kx_smooth<double, 3>, items, b->stream, v.phi64, (const double *)v.f64, v.g, c)
-                           : launch(kx_smooth<double, 2>, items, b->stream, v.phi64, (const double *)v.f64, v.g, c);
+            return colour_pass(b->dim, v.phi32, (const float *)v.f32, v.g, c, b->stream);
+        return colour_pass(b->dim, v.phi64, (const double *)v.f64, v.g, c, b->stream);
     };
     for (int w = 0; w < 3; w++)
         BCK(b, pass(w & 1));
