@@ -38,6 +38,7 @@ struct LevelData {
     float *phi32[MG_MAX_MG] = {};  // mixed precision correction, all multigrid levels
     float *phi32b[MG_MAX_MG] = {}; // second FP32 buffer of the temporally blocked levels
     int tile[MG_MAX_MG] = {};      // FP32 temporal-blocking tile per level (0: one kernel per phase)
+    int nsplit = 0;                // FP32 levels 0..nsplit-1 stored colour-split (MgGeom::sH > 0), tile 0
     float *f32[MG_MAX_MG] = {};
     double *rho = nullptr;         // (n+4)^d density (Omega and inner ring)
     double *guess = nullptr;       // (n+2)^d optional initial potential
@@ -125,6 +126,64 @@ void plan_tiles(LevelData &ld, int dim, int nu_pre, int nu_post)
             t = wvar >= 0 ? wave_code(wvar, std::min(wzc, ld.g[L].N)) : wave_default(ld.g[L].N);
         ld.tile[L] = t;
     }
+}
+
+// Colour-split FP32 levels: the first S multigrid levels above the one-block
+// bottom (none with the cluster kernel) keep each colour in its own array and
+// run the box-patch kernels (mg_box.cu), whose colour pass moves exactly its
+// algorithmic bytes; levels below stay plain for the bottom, plane-marching
+// and blocked kernels.  MG_SPLIT=S fixes S; without it (and without tuning)
+// the levels of 64 cells per edge or more are split, unless MG_WAVE,
+// MG_WAVE_PLAN or MG_TB_TILE ask for the plain-layout plans.  mg_autotune
+// times the choices; the batched kernels (MG_BATCHED=1) run plain levels
+// only.  Changing the layout clears the level's FP32 arrays (their ghost
+// layer must read zero in either layout).
+constexpr int kTileSplit = 1 << 16;   // mg_tuning / tuning-cache code of a split level
+constexpr int kSplitMinN = 64;
+
+int split_default(const LevelData &ld)
+{
+    if (ld.Lc[1] >= 0 || ld.frozen)   // the cluster kernel runs plain levels
+        return 0;
+    const int Ls = ld.Ls[1];
+    if (const char *v = std::getenv("MG_SPLIT"))
+        if (*v)
+            return std::max(0, std::min(std::atoi(v), Ls));
+    for (const char *name : {"MG_WAVE", "MG_WAVE_PLAN", "MG_TB_TILE"})
+        if (const char *v = std::getenv(name))
+            if (*v)
+                return 0;
+    int S = 0;
+    while (S < Ls && ld.g[S].N >= kSplitMinN)
+        S++;
+    return S;
+}
+
+cudaError_t plan_split(LevelData &ld, int dim, int S, cudaStream_t s)
+{
+    S = std::max(0, std::min(S, ld.Ls[1]));
+    if (ld.Lc[1] >= 0)
+        S = 0;
+    const bool changed = S != ld.nsplit;
+    for (int L = 0; L < ld.nmg; L++) {
+        MgGeom &g = ld.g[L];
+        if (L < S) {
+            g.sH = mg_split_H(g.E);
+            g.shalf = (long long)g.sH * g.E * (dim == 3 ? g.E : 1);
+            ld.tile[L] = 0;
+        } else {
+            g.sH = 0;
+            g.shalf = 0;
+        }
+    }
+    ld.nsplit = S;
+    if (!changed || !ld.phi32[0])
+        return cudaSuccess;
+    for (int L = 0; L < ld.nmg; L++)
+        for (float *a : {ld.phi32[L], ld.phi32b[L], ld.f32[L]})
+            if (cudaError_t e = cudaMemsetAsync(a, 0, mg_fp32_cells(ld.g[L].E, dim) * sizeof(float), s))
+                return e;
+    return cudaSuccess;
 }
 
 void plan_bottom(LevelData &ld, int dim, int lim32 = -1)
@@ -284,7 +343,10 @@ void build_geometry(LevelData &ld, int dim)
         g.cRf = (float)g.cR;
         g.h2f = (float)g.h2;
         g.inv_h2f = (float)g.inv_h2;
+        g.sH = 0;
+        g.shalf = 0;
     }
+    ld.nsplit = 0;
 }
 
 #define MG_BRANCHES 8   // parallel branches of the solve graph (hierarchies of a batch)
@@ -568,15 +630,20 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     const MgGeom &g = ld.g[L];
     void *phi = fp32 ? (void *)ld.phi32[L] : (void *)ld.phi[L];
     const void *f = fp32 ? (const void *)ld.f32[L] : (const void *)ld.f[L];
-    const double bytes = 2.0 * (fp32 ? 4 : 8) * cells_d(g.N, dim);   // read Phi, read/write one colour
+    const bool split = fp32 && L < ld.nsplit;
+    const double bytes = (split ? 1.5 : 2.0) * (fp32 ? 4 : 8) * cells_d(g.N, dim);   // read Phi, read/write one colour
     for (int sw = 0; sw < sweeps; sw++)
         for (int c = 0; c < 2; c++) {
             // the finest multigrid level is profiled apart from the coarser ones
             const bool last = sw == sweeps - 1 && c == 1;
             cudaError_t e = timed(h, L == 0 ? KK_SMOOTH0 : KK_SMOOTH, bytes, [&] {
+                if (split)
+                    return mg_split_colour(dim, (float *)phi, (const float *)f, g, c, s);
                 return mg_launch_smooth(dim, fp32, phi, f, g, c, s, last ? ctl : nullptr, hi);
             });
             if (e)
+                return e;
+            if (split && last && ctl && (e = mg_launch_inner_step(ctl, hi, s)))
                 return e;
         }
     return cudaSuccess;
@@ -681,6 +748,9 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
         if ((e = smooth(h, ld, L, fp32, o.nu_pre, s)))
             return e;
         e = timed(h, KK_RESTRICT, 2.0 * w * (nf + nc), [&] {
+            if (fp32 && L < ld.nsplit)
+                return mg_split_resid_restrict(dim, ld.phi32[L], ld.f32[L], ld.g[L], ld.phi32[L + 1], ld.f32[L + 1],
+                                               ld.g[L + 1], s);
             return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s);
         });
         if (e)
@@ -719,7 +789,11 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
                 return e;
             continue;
         }
-        e = timed(h, KK_PROLONG, w * (nc + 2.0 * nf), [&] { return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s); });
+        e = timed(h, KK_PROLONG, w * (nc + 2.0 * nf), [&] {
+            if (fp32 && L - 1 < ld.nsplit)
+                return mg_split_prolong(dim, ld.phi32[L], ld.g[L], ld.phi32[L - 1], ld.g[L - 1], s);
+            return mg_launch_prolong(dim, fp32, P(L), ld.g[L], P(L - 1), ld.g[L - 1], s);
+        });
         if (e)
             return e;
         const bool fold = ctl && ncyc == 1 && L == 1 && o.nu_post > 0;
@@ -1340,6 +1414,9 @@ mg_status build_graph(mg_hierarchy *h)
         // descriptor); MG_BATCHED=1 selects the batched launches
         const char *v = std::getenv("MG_BATCHED");
         if (v && v[0] == '1') {
+            for (auto &hl : h->lev)
+                for (auto &ld : hl)
+                    CK(h, plan_split(ld, h->dim, 0, h->stream));
             mg_status perr;
             h->batched = plan_batched(h, perr);
             if (perr)
@@ -1524,6 +1601,8 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
             return false;
         plan_tiles(ld, dim, o.nu_pre, o.nu_post);
         plan_cluster(ld, h->dim, h->csize, h->opt);
+        if ((err = plan_split(ld, dim, 0, h->stream)))
+            return false;
         const float ms = time_ms(h, 10, [&](cudaStream_t cs) { return vcycle(h, ld, true, cs); }, err);
         if (err)
             return false;
@@ -1536,6 +1615,8 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     if ((err = refresh_bottom_plan(h, ld)))
         return false;
     plan_cluster(ld, h->dim, h->csize, h->opt);
+    if ((err = plan_split(ld, dim, 0, h->stream)))
+        return false;
     te.bottom_n = bestnb;
     // 2. per level above the bottom: the tile of its pre/post pair
     const int Ls = ld.Ls[1];
@@ -1609,16 +1690,45 @@ bool tune_level(mg_hierarchy *h, LevelData &ld, TuneEntry &te, cudaError_t &err)
     }
     for (int L = Ls; L < ld.nmg; L++)
         ld.tile[L] = 0;
+    // 3. how many leading levels run colour-split (their tiles give way)
+    if (ld.Lc[1] < 0 && !ld.frozen) {
+        int tiles[MG_MAX_MG];
+        std::copy(ld.tile, ld.tile + MG_MAX_MG, tiles);
+        float bs = 1e30f;
+        int bestS = 0;
+        for (int S = 0; S <= Ls; S++) {
+            std::copy(tiles, tiles + MG_MAX_MG, ld.tile);
+            if ((err = plan_split(ld, dim, S, h->stream)))
+                return false;
+            const float ms = time_ms(h, 10, [&](cudaStream_t cs) { return vcycle(h, ld, true, cs); }, err);
+            if (err)
+                return false;
+            if (ms < bs) {
+                bs = ms;
+                bestS = S;
+            }
+        }
+        std::copy(tiles, tiles + MG_MAX_MG, ld.tile);
+        if ((err = plan_split(ld, dim, bestS, h->stream)))
+            return false;
+        for (int L = 0; L < bestS; L++)
+            te.tile[L] = kTileSplit;
+    }
     return true;
 }
 
 cudaError_t apply_entry(mg_hierarchy *h, LevelData &ld, const TuneEntry &te)
 {
     plan_bottom(ld, h->dim, te.bottom_n);
-    const cudaError_t e = refresh_bottom_plan(h, ld);
+    cudaError_t e = refresh_bottom_plan(h, ld);
+    int S = 0;
+    while (S < ld.Ls[1] && te.tile[S] == kTileSplit)
+        S++;
     for (int L = 0; L < ld.nmg; L++)
-        ld.tile[L] = L < ld.Ls[1] ? te.tile[L] : 0;
+        ld.tile[L] = L < ld.Ls[1] && te.tile[L] != kTileSplit ? te.tile[L] : 0;
     plan_cluster(ld, h->dim, h->csize, h->opt);
+    if (!e)
+        e = plan_split(ld, h->dim, S, h->stream);
     return e;
 }
 
@@ -1764,10 +1874,11 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 const size_t c = (size_t)cells(ld.g[L].E, dim);
                 slots.push_back({(void **)&ld.phi[L], align256(c * sizeof(double))});
                 slots.push_back({(void **)&ld.f[L], align256(c * sizeof(double))});
-                if (o.precision == MG_MIXED) {
-                    slots.push_back({(void **)&ld.phi32[L], align256(c * sizeof(float))});
-                    slots.push_back({(void **)&ld.phi32b[L], align256(c * sizeof(float))});
-                    slots.push_back({(void **)&ld.f32[L], align256(c * sizeof(float))});
+                if (o.precision == MG_MIXED) {   // room for the plain and the colour-split layout
+                    const size_t c32 = mg_fp32_cells(ld.g[L].E, dim);
+                    slots.push_back({(void **)&ld.phi32[L], align256(c32 * sizeof(float))});
+                    slots.push_back({(void **)&ld.phi32b[L], align256(c32 * sizeof(float))});
+                    slots.push_back({(void **)&ld.f32[L], align256(c32 * sizeof(float))});
                 }
             }
             for (int L = 1; L < ld.nmg; L++) {
@@ -1871,6 +1982,8 @@ mg_status mg_create_hierarchy(const mg_hierarchy_desc *descs, int batch, const m
                 e = refresh_bottom_plan(h, ld);
             plan_tiles(ld, dim, o.nu_pre, o.nu_post);
             plan_cluster(ld, h->dim, h->csize, h->opt);
+            if (e == cudaSuccess && o.precision == MG_MIXED)
+                e = plan_split(ld, dim, split_default(ld), h->stream);
         }
     if (e == cudaSuccess) {
         std::vector<double> fr((size_t)batch * MG_MAX_LEVELS, 0.0);
@@ -2231,6 +2344,8 @@ mg_status mg_time_smoothing(mg_hierarchy *h, int b, int level, int L, int launch
                 e = mg_launch_wave(fwd ? ld.phi32[L] : ld.phi32b[L], fwd ? ld.phi32b[L] : ld.phi32[L], ld.f32[L],
                                    ld.g[L], o.nu_pre, wave_variant(code), wave_zchunks(code), s, nullptr, 0,
                                    h->werr, h->wfault);
+            } else if (L < ld.nsplit) {
+                e = mg_split_colour(dim, ld.phi32[L], ld.f32[L], ld.g[L], r & 1, s);
             } else {
                 e = mg_launch_smooth(dim, true, ld.phi32[L], ld.f32[L], ld.g[L], r & 1, s);
             }
@@ -2253,7 +2368,7 @@ int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap)
         return -1;
     const LevelData &ld = h->lev[b][level];
     for (int L = 0; L < cap && L < ld.nmg; L++)
-        tiles[L] = ld.tile[L];
+        tiles[L] = L < ld.nsplit ? kTileSplit : ld.tile[L];
     return ld.g[ld.Ls[1]].N;
 }
 

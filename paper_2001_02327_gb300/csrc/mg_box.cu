@@ -60,14 +60,12 @@ __device__ __forceinline__ long long box_index(const BoxGeom &g, int i, int j, i
 // the cell at position i / 2 of its row.  A red cell's six neighbours are all
 // black, so a colour pass reads the other colour's array, writes its own, and
 // consecutive threads touch consecutive words.
-template <typename T> __device__ __forceinline__ long long lidx(const BoxGeom &g, int i, int j, int k);
-template <> __device__ __forceinline__ long long lidx<double>(const BoxGeom &g, int i, int j, int k)
+template <bool SPLIT>
+__device__ __forceinline__ long long lidx(const BoxGeom &g, int i, int j, int k)
 {
+    if (SPLIT)
+        return ((i + j + k) & 1) * g.half + ((long long)k * g.E[1] + j) * g.H + (i >> 1);
     return box_index(g, i, j, k);
-}
-template <> __device__ __forceinline__ long long lidx<float>(const BoxGeom &g, int i, int j, int k)
-{
-    return ((i + j + k) & 1) * g.half + ((long long)k * g.E[1] + j) * g.H + (i >> 1);
 }
 
 // Division of an unsigned 32-bit n by an invariant d with one multiply-high,
@@ -111,7 +109,7 @@ __device__ __forceinline__ int gz() { return blockIdx.z; }
 // -Phi_{N-1}, which cancels the left neighbour, or +Phi_1 when N = 1).  The
 // diagonal is d0 + fold.  Axis order x, y, z.  Returns whether the cell has a
 // ghost neighbour on a coarse level.
-template <typename T, int DIM>
+template <typename T, int DIM, bool S>
 __device__ __forceinline__ bool box_terms(const T *__restrict__ phi, const BoxGeom &g, int i, int j, int k, T &other,
                                           T &fold)
 {
@@ -121,8 +119,8 @@ __device__ __forceinline__ bool box_terms(const T *__restrict__ phi, const BoxGe
     bool folded = false;
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
-        const T left = phi[lidx<T>(g, i - (a == 0), j - (a == 1), k - (a == 2))];
-        const T right = phi[lidx<T>(g, i + (a == 0), j + (a == 1), k + (a == 2))];
+        const T left = phi[lidx<S>(g, i - (a == 0), j - (a == 1), k - (a == 2))];
+        const T right = phi[lidx<S>(g, i + (a == 0), j + (a == 1), k + (a == 2))];
         const T ih2 = gsel<T>(g.ih2[a], g.ih2f[a]);
         T o;
         if (g.L == 0) {
@@ -168,8 +166,8 @@ __global__ void __launch_bounds__(256) kx_smooth(T *__restrict__ phi, const T *_
     if (i > g.N[0])
         return;
     T other, fold;
-    const bool folded = box_terms<T, DIM>(phi, g, i, j, k, other, fold);
-    const long long p = lidx<T>(g, i, j, k);
+    const bool folded = box_terms<T, DIM, false>(phi, g, i, j, k, other, fold);
+    const long long p = box_index(g, i, j, k);
     const T rhs = f[p] - other;
     phi[p] = folded ? rhs / (gsel<T>(g.d0, g.d0f) + fold) : rhs * gsel<T>(g.inv0, g.inv0f);
 }
@@ -241,7 +239,7 @@ __global__ void __launch_bounds__(256) kx_smooth32(float *__restrict__ phi, cons
             continue;
         if (g.L > 0 && (row_edge || i == 1 || i == g.N[0])) {
             float other, fold;
-            const bool folded = box_terms<float, DIM>(phi, g, i, j, k, other, fold);
+            const bool folded = box_terms<float, DIM, true>(phi, g, i, j, k, other, fold);
             const float rhs = fr[m0 + e] - other;
             own[m0 + e] = folded ? rhs / (g.d0f + fold) : rhs * g.inv0f;
         } else {
@@ -250,14 +248,14 @@ __global__ void __launch_bounds__(256) kx_smooth32(float *__restrict__ phi, cons
     }
 }
 
-// r = f - A Phi at cell (i, j, k)
-template <typename T, int DIM>
+// r = f - A Phi at cell (i, j, k), storage layout S
+template <typename T, int DIM, bool S>
 __device__ __forceinline__ T box_resid(const T *__restrict__ phi, const T *__restrict__ f, const BoxGeom &g, int i,
                                        int j, int k)
 {
     T other, fold;
-    box_terms<T, DIM>(phi, g, i, j, k, other, fold);
-    const long long p = lidx<T>(g, i, j, k);
+    box_terms<T, DIM, S>(phi, g, i, j, k, other, fold);
+    const long long p = lidx<S>(g, i, j, k);
     return f[p] - (other + (gsel<T>(g.d0, g.d0f) + fold) * phi[p]);
 }
 
@@ -267,7 +265,8 @@ __device__ __forceinline__ T box_resid(const T *__restrict__ phi, const T *__res
 // last cell counts zero) and of cell I along the others, x pairs first, then
 // y, then z, times 2^-k (k the coarsened axes, bit a of cmask).  Also starts
 // the coarse potential at zero (Sec. 2.3 step 6).  One thread per coarse cell.
-template <typename T, int DIM>
+// FS / CS: the fine / coarse arrays colour-split (FP32) or plain.
+template <typename T, int DIM, bool FS, bool CS>
 __global__ void __launch_bounds__(256) kx_resid_restrict(const T *__restrict__ phi, const T *__restrict__ f,
                                                          BoxGeom gf, T *__restrict__ fc, T *__restrict__ phic,
                                                          BoxGeom gc, int cmask, T wk)
@@ -293,14 +292,14 @@ __global__ void __launch_bounds__(256) kx_resid_restrict(const T *__restrict__ p
 #pragma unroll
                     for (int dx = 0; dx < 2; dx++)
                         if (dx < nx)
-                            sx = sx + box_resid<T, DIM>(phi, f, gf, x0 + dx, y0 + dy, z0 + dz);
+                            sx = sx + box_resid<T, DIM, FS>(phi, f, gf, x0 + dx, y0 + dy, z0 + dz);
                     sy = sy + sx;
                 }
             }
             sz = sz + sy;
         }
     }
-    const long long pc = lidx<T>(gc, I, J, K);
+    const long long pc = lidx<CS>(gc, I, J, K);
     fc[pc] = sz * wk;
     phic[pc] = T(0);
 }
@@ -308,7 +307,7 @@ __global__ void __launch_bounds__(256) kx_resid_restrict(const T *__restrict__ p
 // A coarse value read through the ghost rule of Sec. 2.4, applied axis after
 // axis (x, y, z) as a ghost fill would: index 0 -> -Phi_1; N+1 -> cR Phi_N,
 // or at a tie -Phi_{N-1} (+Phi_1 when N = 1).
-template <typename T, int DIM>
+template <typename T, int DIM, bool S>
 __device__ __forceinline__ T ghost_read(const T *__restrict__ phic, const BoxGeom &g, int i, int j, int k)
 {
     int id[3] = {i, j, k};
@@ -329,7 +328,7 @@ __device__ __forceinline__ T ghost_read(const T *__restrict__ phic, const BoxGeo
             }
         }
     }
-    T v = phic[lidx<T>(g, id[0], id[1], id[2])];
+    T v = phic[lidx<S>(g, id[0], id[1], id[2])];
 #pragma unroll
     for (int a = 0; a < DIM; a++)
         v = v * c[a];
@@ -340,15 +339,12 @@ __device__ __forceinline__ T ghost_read(const T *__restrict__ phic, const BoxGeo
 // coarsened, fine cell i lies a quarter coarse cell from coarse cell
 // ceil(i/2) towards ceil(i/2) - 1 (i odd) or + 1 (i even): weights 3/4 and
 // 1/4; along the others it takes coarse cell i.  Interpolated x first, then
-// y, then z.  One thread per fine cell.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom gf, const T *__restrict__ phic,
-                                                  BoxGeom gc, int cmask)
+// y, then z.  This is the correction at fine cell (i, j, k), coarse layout CS.
+template <typename T, int DIM, bool CS>
+__device__ __forceinline__ T prolong_value(const BoxGeom &gf, const T *__restrict__ phic, const BoxGeom &gc, int cmask,
+                                           int i, int j, int k)
 {
-    pdl_begin();
-    const int i = gx() + 1, j = gy() + 1, k = DIM == 3 ? gz() + 1 : 0;
-    if (i > gf.N[0] || j > gf.N[1])
-        return;
+    (void)gf;
     // per axis: the near and far coarse cells and their weights (one tap of
     // weight 1 along an axis that did not coarsen)
     const bool cx = cmask & 1, cy = (cmask >> 1) & 1, cz = DIM == 3 && ((cmask >> 2) & 1);
@@ -357,9 +353,9 @@ __global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom 
     const T w0 = T(0.75), w1 = T(0.25);
     auto row = [&](int y, int z) {   // interpolated along x
         if (!cx)
-            return T(0) + T(1) * ghost_read<T, DIM>(phic, gc, ax0, y, z);
-        T v = T(0) + w0 * ghost_read<T, DIM>(phic, gc, ax0, y, z);
-        return v + w1 * ghost_read<T, DIM>(phic, gc, ax1, y, z);
+            return T(0) + T(1) * ghost_read<T, DIM, CS>(phic, gc, ax0, y, z);
+        T v = T(0) + w0 * ghost_read<T, DIM, CS>(phic, gc, ax0, y, z);
+        return v + w1 * ghost_read<T, DIM, CS>(phic, gc, ax1, y, z);
     };
     auto plane = [&](int z) {        // then along y
         if (!cy)
@@ -374,7 +370,149 @@ __global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom 
         vz = T(0) + w0 * plane(az0);
         vz = vz + w1 * plane(az1);
     }
-    phif[lidx<T>(gf, i, j, k)] += vz;
+    return vz;
+}
+
+// One thread per fine cell; CS / FS: the coarse / fine arrays colour-split
+// (FP32) or plain.
+template <typename T, int DIM, bool CS, bool FS>
+__global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom gf, const T *__restrict__ phic,
+                                                  BoxGeom gc, int cmask)
+{
+    pdl_begin();
+    const int i = gx() + 1, j = gy() + 1, k = DIM == 3 ? gz() + 1 : 0;
+    if (i > gf.N[0] || j > gf.N[1])
+        return;
+    phif[lidx<FS>(gf, i, j, k)] += prolong_value<T, DIM, CS>(gf, phic, gc, cmask, i, j, k);
+}
+
+// The same on a colour-split FP32 fine level whose x axis coarsened, four
+// fine cells of one colour per thread (colour = blockIdx.y; threads over
+// (row, group of four) as in kx_smooth32).  Fine cells i = 2m + p, m in
+// m0..m0+3, take their x taps from coarse cells m and m + 1 (near: m + p),
+// so the thread reads coarse cells m0..m0+4 of each of its (up to four)
+// coarse rows once; threads next to a ghost take the per-cell form.
+template <int DIM, bool CS>
+__global__ void __launch_bounds__(256) kx_prolong32(float *__restrict__ phif, BoxGeom gf, const float *__restrict__ phic,
+                                                    BoxGeom gc, int cmask, unsigned total, int q, FastDiv dq,
+                                                    FastDiv dny)
+{
+    pdl_begin();
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int colour = blockIdx.y;
+    const unsigned r = fdiv(dq, t);
+    const unsigned kz = DIM == 3 ? fdiv(dny, r) : 0u;
+    const int j = (int)(r - kz * (unsigned)gf.N[1]) + 1, k = DIM == 3 ? (int)kz + 1 : 0;
+    const int par = (colour - j - k) & 1;
+    const int m0 = 4 * (int)(t - r * (unsigned)q);
+    const int i0 = 2 * m0 + par;
+    if (i0 > gf.N[0])
+        return;
+    float *own = phif + colour * gf.half + (long long)(k * gf.E[1] + j) * gf.H;
+    const bool cy = (cmask >> 1) & 1, cz = DIM == 3 && ((cmask >> 2) & 1);
+    const int J0 = cy ? (j + 1) >> 1 : j, J1 = cy ? ((j & 1) ? J0 - 1 : J0 + 1) : J0;
+    const int K0 = cz ? (k + 1) >> 1 : k, K1 = cz ? ((k & 1) ? K0 - 1 : K0 + 1) : K0;
+    // every coarse index through the ghost rule of Sec. 2.4 as a (cell,
+    // factor) pair -- factor 1 inside, so the products below are exact there
+    // and equal ghost_read's at the ghosts; no thread leaves the common path
+    auto gmap = [&](int a, int I, int &m) -> float {
+        const int N = gc.N[a];
+        if (I <= 0) {
+            m = 1;
+            return -1.0f;
+        }
+        if (I <= N) {
+            m = I;
+            return 1.0f;
+        }
+        if (I > N + 1) {   // past the ghost: only cells outside the level use it
+            m = N;
+            return 0.0f;
+        }
+        if (gc.tie[a]) {
+            m = N >= 2 ? N - 1 : 1;
+            return N >= 2 ? -1.0f : 1.0f;
+        }
+        m = N;
+        return gc.cRf[a];
+    };
+    int jm[2], km[2], im[5];
+    float cj[2], ck[2], ci[5];
+    cj[0] = gmap(1, J0, jm[0]);
+    cj[1] = gmap(1, J1, jm[1]);
+    if (DIM == 3) {
+        ck[0] = gmap(2, K0, km[0]);
+        ck[1] = gmap(2, K1, km[1]);
+    } else {
+        km[0] = km[1] = 0;
+        ck[0] = ck[1] = 1.0f;
+    }
+#pragma unroll
+    for (int x = 0; x < 5; x++)
+        ci[x] = gmap(0, m0 + x, im[x]);
+    // coarse rows (J, K): 0 = (J0, K0), 1 = (J1, K0), 2 = (J0, K1), 3 = (J1, K1)
+    float w[4][5];
+    const int nr = DIM == 3 ? 4 : 2;
+#pragma unroll
+    for (int rr = 0; rr < nr; rr++) {
+        const int Jm = jm[rr & 1], Km = km[rr >> 1];
+        const long long rb = (long long)Km * gc.E[1] + Jm;
+#pragma unroll
+        for (int x = 0; x < 5; x++) {
+            const int I = im[x];
+            float v = CS ? phic[((I + Jm + Km) & 1) * gc.half + rb * gc.H + (I >> 1)] : phic[rb * gc.E[0] + I];
+            v = v * ci[x];
+            v = v * cj[rr & 1];
+            if (DIM == 3)
+                v = v * ck[rr >> 1];
+            w[rr][x] = v;
+        }
+    }
+    const float wn = 0.75f, wf = 0.25f;
+    float nv[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        float vx[4];
+#pragma unroll
+        for (int rr = 0; rr < nr; rr++) {   // near coarse x = m0 + e + par, far = the other of e, e + 1
+            const float cn = par ? w[rr][e + 1] : w[rr][e], cf = par ? w[rr][e] : w[rr][e + 1];
+            const float a = 0.0f + wn * cn;
+            vx[rr] = a + wf * cf;
+        }
+        float vy0, vy1 = 0.0f;
+        if (cy) {
+            vy0 = (0.0f + wn * vx[0]) + wf * vx[1];
+            if (DIM == 3)
+                vy1 = (0.0f + wn * vx[2]) + wf * vx[3];
+        } else {
+            vy0 = 0.0f + vx[0];
+            if (DIM == 3)
+                vy1 = 0.0f + vx[2];
+        }
+        float vz;
+        if (DIM == 3 && cz)
+            vz = (0.0f + wn * vy0) + wf * vy1;
+        else
+            vz = 0.0f + vy0;
+        nv[e] = vz;
+    }
+    if (i0 >= 1 && i0 + 6 <= gf.N[0]) {
+        float4 o = *reinterpret_cast<float4 *>(own + m0);
+        o.x += nv[0];
+        o.y += nv[1];
+        o.z += nv[2];
+        o.w += nv[3];
+        *reinterpret_cast<float4 *>(own + m0) = o;
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int i = i0 + 2 * e;
+        if (i >= 1 && i <= gf.N[0])
+            own[m0 + e] += nv[e];
+    }
 }
 
 constexpr int kNormBlocks = 152 * 4;   // fixed grid of the norm reduction: the same partial sums every call
@@ -430,10 +568,10 @@ __global__ void __launch_bounds__(kNormThreads) kx_resid_norm(const double *__re
                 }
                 res = f[p] - other;
             } else {
-                res = box_resid<double, DIM>(phi, f, g, i, j, k);
+                res = box_resid<double, DIM, false>(phi, f, g, i, j, k);
             }
             if (f32) {
-                const long long q = lidx<float>(g, i, j, k);
+                const long long q = lidx<true>(g, i, j, k);
                 f32[q] = (float)res;
                 e32[q] = 0.0f;
             }
@@ -466,7 +604,7 @@ __global__ void __launch_bounds__(256) kx_accumulate(double *__restrict__ phi, c
     const int i = gx() + 1, j = gy() + 1, k = DIM == 3 ? gz() + 1 : 0;
     if (i > g.N[0] || j > g.N[1])
         return;
-    phi[box_index(g, i, j, k)] += (double)e32[lidx<float>(g, i, j, k)];
+    phi[box_index(g, i, j, k)] += (double)e32[lidx<true>(g, i, j, k)];
 }
 
 // Patch geometry for the kernels that work on the (n+4) blocks.
@@ -719,7 +857,7 @@ BoxGeom level_geom(const int n[3], int dim, double h, int L)
     g.inv0 = 1.0 / d;
     g.d0f = (float)g.d0;
     g.inv0f = (float)g.inv0;
-    g.H = ((g.E[0] + 1) / 2 + 3) & ~3;   // a multiple of 4: rows start 16-byte aligned
+    g.H = mg_split_H(g.E[0]);   // a multiple of 4: rows start 16-byte aligned
     g.half = (long long)g.H * g.E[1] * g.E[2];
     return g;
 }
@@ -854,6 +992,27 @@ cudaError_t colour_pass(int dim, float *phi, const float *f, const BoxGeom &g, i
     return cudaGetLastError();
 }
 
+// Prolongation into a colour-split FP32 fine level: four fine cells per
+// thread where the x axis coarsened, else one
+template <bool CS>
+cudaError_t prolong32(int dim, float *phif, const BoxGeom &gf, const float *phic, const BoxGeom &gc, int cmask,
+                      cudaStream_t s)
+{
+    if (!(cmask & 1))
+        return dim == 3 ? launch_cells(kx_prolong<float, 3, CS, true>, gf, s, phif, gf, phic, gc, cmask)
+                        : launch_cells(kx_prolong<float, 2, CS, true>, gf, s, phif, gf, phic, gc, cmask);
+    const int q = ((gf.N[0] >> 1) + 4) / 4;
+    const unsigned total = (unsigned)q * (unsigned)gf.N[1] * (unsigned)(dim == 3 ? gf.N[2] : 1);
+    const dim3 grid((total + 255) / 256, 2);
+    if (dim == 3)
+        mg_launch_kernel(kx_prolong32<3, CS>, grid, dim3(256), 0, s, phif, gf, phic, gc, cmask, total, q, fast_div(q),
+                         fast_div(gf.N[1]));
+    else
+        mg_launch_kernel(kx_prolong32<2, CS>, grid, dim3(256), 0, s, phif, gf, phic, gc, cmask, total, q, fast_div(q),
+                         fast_div(gf.N[1]));
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t smooth(const mg_box *b, const BoxLevel &l, int sweeps, cudaStream_t s)
 {
@@ -879,17 +1038,23 @@ cudaError_t vcycle(const mg_box *b, const BoxPatch &P, cudaStream_t s)
     for (int L = 0; L < Lc && !e; L++) {
         const BoxLevel &fl = P.lv[L], &cl = P.lv[L + 1];
         const T wk = (T)std::ldexp(1.0, -fl.ncoars);
-        e = dim == 3 ? launch_cells(kx_resid_restrict<T, 3>, cl.g, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl),
-                                    fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk)
-                     : launch_cells(kx_resid_restrict<T, 2>, cl.g, s, (const T *)lphi<T>(fl), (const T *)lf<T>(fl),
-                                    fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk);
+        constexpr bool S = sizeof(T) == 4;   // FP32 levels colour-split, FP64 plain
+        e = dim == 3 ? launch_cells(kx_resid_restrict<T, 3, S, S>, cl.g, s, (const T *)lphi<T>(fl),
+                                    (const T *)lf<T>(fl), fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk)
+                     : launch_cells(kx_resid_restrict<T, 2, S, S>, cl.g, s, (const T *)lphi<T>(fl),
+                                    (const T *)lf<T>(fl), fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk);
         if (!e)
             e = smooth<T>(b, cl, b->opt.nu_pre, s);
     }
     for (int L = Lc; L > 0 && !e; L--) {
         const BoxLevel &cl = P.lv[L], &fl = P.lv[L - 1];
-        e = dim == 3 ? launch_cells(kx_prolong<T, 3>, fl.g, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask)
-                     : launch_cells(kx_prolong<T, 2>, fl.g, s, lphi<T>(fl), fl.g, (const T *)lphi<T>(cl), cl.g, fl.cmask);
+        if constexpr (sizeof(T) == 4)   // FP32 levels colour-split
+            e = prolong32<true>(dim, fl.phi32, fl.g, cl.phi32, cl.g, fl.cmask, s);
+        else
+            e = dim == 3 ? launch_cells(kx_prolong<double, 3, false, false>, fl.g, s, fl.phi64, fl.g,
+                                        (const double *)cl.phi64, cl.g, fl.cmask)
+                         : launch_cells(kx_prolong<double, 2, false, false>, fl.g, s, fl.phi64, fl.g,
+                                        (const double *)cl.phi64, cl.g, fl.cmask);
         if (!e)
             e = smooth<T>(b, fl, b->opt.nu_post, s);
     }
@@ -1082,6 +1247,94 @@ void destroy_box(mg_box *b)
 }
 
 }  // namespace
+
+// --------------------------------------------------------------------------
+// The cubic engine's colour-split FP32 levels (declared in mg_internal.h)
+// --------------------------------------------------------------------------
+namespace {
+
+BoxGeom box_from_mg(const MgGeom &g, int dim)
+{
+    BoxGeom b{};
+    b.L = g.L;
+    for (int a = 0; a < 3; a++) {
+        if (a >= dim) {
+            b.N[a] = 1;
+            b.E[a] = 1;
+            continue;
+        }
+        b.N[a] = g.N;
+        b.E[a] = g.E;
+        b.tie[a] = g.tie;
+        b.cR[a] = g.cR;
+        b.ih2[a] = g.inv_h2;
+        b.cRf[a] = g.cRf;
+        b.ih2f[a] = g.inv_h2f;
+    }
+    b.d0 = -2.0 * dim * g.inv_h2;
+    b.inv0 = 1.0 / b.d0;
+    b.d0f = (float)b.d0;
+    b.inv0f = (float)b.inv0;
+    b.H = g.sH > 0 ? g.sH : mg_split_H(g.E);
+    b.half = (long long)b.H * g.E * (dim == 3 ? g.E : 1);
+    return b;
+}
+
+template <bool FS, bool CS>
+cudaError_t split_restrict(int dim, const float *phi, const float *f, const BoxGeom &bf, float *phic, float *fc,
+                           const BoxGeom &bc, cudaStream_t s)
+{
+    const int cmask = (1 << dim) - 1;
+    const float wk = dim == 3 ? 0.125f : 0.25f;
+    return dim == 3 ? launch_cells(kx_resid_restrict<float, 3, FS, CS>, bc, s, phi, f, bf, fc, phic, bc, cmask, wk)
+                    : launch_cells(kx_resid_restrict<float, 2, FS, CS>, bc, s, phi, f, bf, fc, phic, bc, cmask, wk);
+}
+
+template <bool CS, bool FS>
+cudaError_t split_prolong(int dim, const float *phic, const BoxGeom &bc, float *phif, const BoxGeom &bf, cudaStream_t s)
+{
+    const int cmask = (1 << dim) - 1;
+    return dim == 3 ? launch_cells(kx_prolong<float, 3, CS, FS>, bf, s, phif, bf, phic, bc, cmask)
+                    : launch_cells(kx_prolong<float, 2, CS, FS>, bf, s, phif, bf, phic, bc, cmask);
+}
+
+}  // namespace
+
+cudaError_t mg_split_colour(int dim, float *phi, const float *f, const MgGeom &g, int colour, cudaStream_t s)
+{
+    if (g.sH <= 0)
+        return cudaErrorInvalidValue;
+    return colour_pass(dim, phi, f, box_from_mg(g, dim), colour, s);
+}
+
+cudaError_t mg_split_resid_restrict(int dim, const float *phi, const float *f, const MgGeom &gf, float *phic,
+                                    float *fc, const MgGeom &gc, cudaStream_t s)
+{
+    const BoxGeom bf = box_from_mg(gf, dim), bc = box_from_mg(gc, dim);
+    const bool fs = gf.sH > 0, cs = gc.sH > 0;
+    if (fs && cs)
+        return split_restrict<true, true>(dim, phi, f, bf, phic, fc, bc, s);
+    if (fs)
+        return split_restrict<true, false>(dim, phi, f, bf, phic, fc, bc, s);
+    if (cs)
+        return split_restrict<false, true>(dim, phi, f, bf, phic, fc, bc, s);
+    return split_restrict<false, false>(dim, phi, f, bf, phic, fc, bc, s);
+}
+
+cudaError_t mg_split_prolong(int dim, const float *phic, const MgGeom &gc, float *phif, const MgGeom &gf,
+                             cudaStream_t s)
+{
+    const BoxGeom bf = box_from_mg(gf, dim), bc = box_from_mg(gc, dim);
+    const bool fs = gf.sH > 0, cs = gc.sH > 0;
+    const int cmask = (1 << dim) - 1;
+    if (fs && cs)
+        return prolong32<true>(dim, phif, bf, phic, bc, cmask, s);
+    if (fs)
+        return prolong32<false>(dim, phif, bf, phic, bc, cmask, s);
+    if (cs)
+        return split_prolong<true, false>(dim, phic, bc, phif, bf, s);
+    return split_prolong<false, false>(dim, phic, bc, phif, bf, s);
+}
 
 extern "C" {
 

@@ -31,7 +31,24 @@ struct MgGeom {
     // the diagonal, 64..127 its negated reciprocal.  NULL: computed in place.
     const double *tab64;
     const float *tab32;
+    // FP32 storage of this level: sH = 0 plain; sH > 0 colour-split -- cell
+    // (i, j, k) of colour (i + j + k) & 1 at colour * shalf + (k E + j) sH + i / 2,
+    // sH = mg_split_H(E) words per row of one colour, shalf = sH E^(d-1)
+    int sH;
+    long long shalf;
 };
+
+// Words per row of one colour in colour-split FP32 storage: half the row,
+// rounded up to a multiple of 4 so that every row starts 16-byte aligned.
+__host__ __device__ inline int mg_split_H(int E) { return ((E + 1) / 2 + 3) & ~3; }
+
+// Index of cell (i, j, k) (storage indices) in an FP32 array of level g
+__host__ __device__ inline long long mg_idx32(const MgGeom &g, int dim, int i, int j, int k)
+{
+    if (g.sH > 0)
+        return ((i + j + k) & 1) * g.shalf + ((long long)k * g.E + j) * g.sH + (i >> 1);
+    return dim == 3 ? ((long long)k * g.E + j) * g.E + i : (long long)j * g.E + i;
+}
 
 // Diagonal contribution of one axis for boundary class c (Sec. 2.4 ghost
 // rule folded in): left ghost -Phi_1 adds -1; right ghost cR Phi_N adds cR,
@@ -140,6 +157,23 @@ cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, cons
 // runs out of its clock budget (about 2 s) writes MG_ETIMEOUT to *err (if
 // err is not NULL) and ends the block; fault != 0 leaves one load group of
 // every block unissued with a budget of about 1 ms (a test of that path).
+// Colour-split FP32 levels (MgGeom::sH > 0) of the cubic engine, run by the
+// box-patch kernels of mg_box.cu: one red-black colour pass (the level must
+// be split), and the residual restriction / prolongation between two levels
+// of which either may be split.
+cudaError_t mg_split_colour(int dim, float *phi, const float *f, const MgGeom &g, int colour, cudaStream_t s);
+cudaError_t mg_split_resid_restrict(int dim, const float *phi, const float *f, const MgGeom &gf, float *phic,
+                                    float *fc, const MgGeom &gc, cudaStream_t s);
+cudaError_t mg_split_prolong(int dim, const float *phic, const MgGeom &gc, float *phif, const MgGeom &gf,
+                             cudaStream_t s);
+// FP32 array size (floats) of a level of storage edge E: room for both layouts
+inline size_t mg_fp32_cells(int E, int dim)
+{
+    const size_t plain = dim == 3 ? (size_t)E * E * E : (size_t)E * E;
+    const size_t split = 2 * (size_t)mg_split_H(E) * (dim == 3 ? (size_t)E * E : (size_t)E) + 16;
+    return plain > split ? plain : split;
+}
+
 cudaError_t mg_wave_prepare();   // once per device before the first launch
 bool mg_wave_applies(int dim, int nsw, int N);
 cudaError_t mg_launch_wave(const float *phi_in, float *phi_out, const float *f, const MgGeom &g, int nsw, int variant,

@@ -1449,8 +1449,9 @@ __device__ __forceinline__ void norm_terms(const double *__restrict__ phi, const
         const double v = residual_at<double, DIM>(phi, f, g, i, j, k);
         r2 += v * v;
         if (r32) {   // the next defect-correction step's right-hand side (k_defect's values)
-            r32[p] = (float)v;
-            e32[p] = 0.0f;
+            const long long q = mg_idx32(g, DIM, i, j, k);
+            r32[q] = (float)v;
+            e32[q] = 0.0f;
         }
     }
 }
@@ -1553,9 +1554,9 @@ __global__ void __launch_bounds__(kThreads) k_defect(const double *__restrict__ 
             j = r + 1;
             k = 0;
         }
-        const int p = lin<DIM>(i, j, k, g.E);
-        r32[p] = (float)residual_at<double, DIM>(phi, f, g, i, j, k);
-        e32[p] = 0.0f;
+        const long long q = mg_idx32(g, DIM, i, j, k);
+        r32[q] = (float)residual_at<double, DIM>(phi, f, g, i, j, k);
+        e32[q] = 0.0f;
     }
 }
 
@@ -1579,7 +1580,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(double *__restrict__ ph
             k = 0;
         }
         const int p = lin<DIM>(i, j, k, g.E);
-        phi[p] += (double)e32[p];
+        phi[p] += (double)e32[mg_idx32(g, DIM, i, j, k)];
     }
 }
 
@@ -2051,9 +2052,9 @@ __global__ void __launch_bounds__(kThreads) kb_defect(const MgBPart *__restrict_
     for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_act * kThreads) {
         int i, j, k;
         active_cell<DIM>(g, t, i, j, k);
-        const int p = lin<DIM>(i, j, k, g.E);
-        P.f32[0][p] = (float)residual_at<double, DIM>(P.phi, P.f, g, i, j, k);
-        P.phi32[0][p] = 0.0f;
+        const long long q = mg_idx32(g, DIM, i, j, k);
+        P.f32[0][q] = (float)residual_at<double, DIM>(P.phi, P.f, g, i, j, k);
+        P.phi32[0][q] = 0.0f;
     }
 }
 
@@ -2073,7 +2074,7 @@ __global__ void __launch_bounds__(kThreads) kb_accumulate(const MgBPart *__restr
         int i, j, k;
         active_cell<DIM>(g, t, i, j, k);
         const int p = lin<DIM>(i, j, k, g.E);
-        P.phi[p] += (double)P.phi32[0][p];
+        P.phi[p] += (double)P.phi32[0][mg_idx32(g, DIM, i, j, k)];
     }
 }
 

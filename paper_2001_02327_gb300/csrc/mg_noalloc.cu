@@ -172,7 +172,7 @@ extern "C" mg_status mg_solve_level_noalloc(int dim, int n, double h, double G, 
 
     // layout of the scratch array, checked against its size before any GPU work
     const int M = n + 2;
-    MgGeom g[MG_MAX_MG];
+    MgGeom g[MG_MAX_MG] = {};
     const int nmg = geometry(M, h, g);
     size_t need = up256(ncells(n + 4, dim) * sizeof(double));                       // f on the finest level
     for (int L = 1; L < nmg; L++)

@@ -622,6 +622,7 @@ def test_batched_mixed_equals_per_hierarchy_branches(mg, monkeypatch):
     Hs = [I.random_hierarchy(s) for s in range(12)]
     Hs = [H for H in Hs if max(H.n) <= 96][:5]
     res = {}
+    monkeypatch.setenv("MG_SPLIT", "0")                 # the batched kernels run plain-layout levels
     for mode in ("0", "1"):
         monkeypatch.setenv("MG_BATCHED", mode)
         h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], mg.options(precision=mg.MG_MIXED, nu_pre=2,
@@ -728,6 +729,7 @@ def test_cluster_vcycle_matches_one_kernel_per_phase(mg, make, prec, lim, monkey
     p = mg.MG_FP64 if prec == "fp64" else mg.MG_MIXED
     kw = dict(nu_pre=2, nu_post=2, max_cycles=4, rel_tol=0.0, precision=p, inner_cycles=2)
     var = "MG_CLUSTER_N64" if prec == "fp64" else "MG_CLUSTER_N32"
+    monkeypatch.setenv("MG_SPLIT", "0")             # the cluster kernel runs plain-layout levels
     monkeypatch.setenv("MG_CLUSTER_N64", "0")
     monkeypatch.setenv("MG_CLUSTER_N32", "0")
     a, pa = _solve_profiled(mg, H, inp, **kw)
@@ -865,3 +867,73 @@ def test_wave_load_wait_timeout_reports_etimeout(mg, monkeypatch):
     _, plain = gpu_solve(mg, H, inp, **kw)
     for l in range(H.num_levels):
         assert np.array_equal(good[l]["phi"], plain[l]["phi"])
+
+
+# --------------------------------------------------------------------------
+# colour-split FP32 levels (mixed precision)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("make,split,want", [
+    (lambda: I.config_3d_offset_sphere(64, 3), "", 1),           # default: levels of >= 64 cells per edge
+    (lambda: I.config_3d_offset_sphere(128, 2), "", 2),
+    (lambda: I.config_3d_offset_sphere(64, 3), "9", None),       # every level above the one-block bottom
+    (lambda: I.config_2d_disk(256, 2), "", 3),
+    (lambda: I.config_2d_disk(64, 2), "9", None)])
+def test_split_levels_match_plain_layout(mg, make, split, want, monkeypatch):
+    """FP32 levels stored colour-split and run by the box-patch kernels
+    reach the same tolerance as the plain layout, with cycle counts within
+    one and potentials within 1e-8 of each other (only FP32 rounding
+    differs); mg_tuning reports the split levels as 65536."""
+    import torch
+    H = make()
+    inp = I.level_inputs(H)
+    res, plans = {}, {}
+    for mode in ("0", split):
+        monkeypatch.setenv("MG_SPLIT", mode)
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=2, nu_post=2, precision=mg.MG_MIXED,
+                                                                 inner_max=8))
+        try:
+            plans[mode] = [mg.mg_tuning(h, 0, l) for l in range(H.num_levels)]
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            for l in range(1, H.num_levels):
+                mg.mg_set_density(h, 0, l, dev(inp[l]["rho"]))
+            _, st = mg.mg_solve(h, 1)
+            out = []
+            for l in range(H.num_levels):
+                phi = torch.zeros((H.n[l],) * H.dim, dtype=torch.float64, device="cuda")
+                mg.mg_forces(h, 0, l, phi, None)
+                torch.cuda.synchronize()
+                out.append((phi.cpu().numpy(), st[0][l]["cycles"], st[0][l]["rel_res"]))
+            res[mode] = out
+        finally:
+            mg.mg_destroy(h)
+    for l in range(H.num_levels):
+        tiles0, nb0 = plans["0"][l]
+        tiles, nb = plans[split][l]
+        assert 65536 not in tiles0
+        nsplit = sum(1 for t in tiles if t == 65536)
+        assert tiles[:nsplit] == [65536] * nsplit and 65536 not in tiles[nsplit:]
+        if want is not None:
+            assert nsplit == want, tiles
+        else:
+            # every level above the one-block kernel (edge nb) is split
+            Ns = mg.mg_level_sizes(H.n[l] + 2)
+            assert nsplit == Ns.index(nb), (tiles, nb)
+        (pa, ca, ra), (pb, cb, rb) = res["0"][l], res[split][l]
+        assert ra < 1e-10 and rb < 1e-10
+        assert abs(ca - cb) <= 1, (ca, cb)
+        assert relmax(pb, pa) < 1e-8, relmax(pb, pa)
+
+
+def test_split_smoothing_timed_with_split_bytes(mg, monkeypatch):
+    """mg_time_smoothing times the split colour pass where the plan has one
+    (1.5 words per active cell)."""
+    monkeypatch.setenv("MG_SPLIT", "1")
+    H = I.config_3d_offset_sphere(64, 2)
+    h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(precision=mg.MG_MIXED))
+    try:
+        assert mg.mg_tuning(h, 0, 0)[0][0] == 65536
+        us, by = mg.mg_time_smoothing(h, 0, 0, 0, 8)
+        assert us > 0 and by == 1.5 * 4 * 66 ** 3
+    finally:
+        mg.mg_destroy(h)
