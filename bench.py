@@ -283,12 +283,15 @@ def kernel_traffic(key):
     return ent.get("dram_bytes_per_launch")
 
 
+SMOOTH_SOURCES = ("mg_box.cu", "mg_internal.h", "mg_kernels.cu", "mg_wave.cu")
+
+
 def kernel_source_sha():
-    """sha256 over the CUDA sources of the solver (sorted file names)."""
-    import glob
+    """sha256 over the CUDA sources that define the smoothing kernels
+    (k_smooth_colour, k_wave, kx_smooth32 and their headers), in this order."""
     hs = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2001_02327_gb300", "csrc", "mg_*.cu"))):
-        hs.update(open(f, "rb").read())
+    for f in SMOOTH_SOURCES:
+        hs.update(open(os.path.join(ROOT, "paper_2001_02327_gb300", "csrc", f), "rb").read())
     return hs.hexdigest()
 
 
@@ -350,11 +353,17 @@ def kernel_roofline(mg, h, level, prof_per_step, ms_per_step, workload, traffic_
     per_step = prof_per_step[kind][0] if kind else 0.0
     peak, src = measured_peaks()
     achieved = by / (us * 1e-6) / 1e9
-    traffic = kernel_traffic(f"{traffic_key}/{kind}") if kind else None
+    code = mg.mg_tuning(h, 0, level)[0][0]
+    plan = ("colour-split storage, one colour per launch (kx_smooth32)" if code == 65536 else
+            "plane-marching sweeps (k_wave)" if code < 0 else "temporally blocked legs" if code > 0 else
+            "plain storage, one colour per launch (k_smooth_colour)")
+    key = f"{traffic_key}/{kind}" + ("/split" if code == 65536 else "")
+    traffic = kernel_traffic(key) if kind else None
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_over_algorithmic": round(traffic / by, 3) if traffic else None,
-            "kernel": kind or "smooth", "workload": workload, "launch_us": round(us, 3), "bytes_per_launch": by,
+            "kernel": kind or "smooth", "plan": plan, "workload": workload, "launch_us": round(us, 3),
+            "bytes_per_launch": by,
             "byte_model": "active cells x 4 B x (1.5 per one-colour launch: Phi read, half of f read, half of Phi "
                           "written; 3 per plane-marching launch of nu sweeps: Phi and f read once, Phi written once)",
             "timing": "mg_time_smoothing: 20 launches in one CUDA graph with programmatic dependent launch, "
