@@ -708,7 +708,8 @@ def run_batch_case(args):
     from paper_2001_02327_gb300 import build
     build.build()
     from paper_2001_02327_gb300 import mg
-    Hs = [I.random_hierarchy(I.BASE_SEED + b) for b in range(args.batch)]
+    edges = tuple(int(e) for e in args.batch_edges.split(",")) if args.batch_edges else I.EDGES
+    Hs = [I.random_hierarchy(I.BASE_SEED + b, edges=edges) for b in range(args.batch)]
     zones = sum(H.zones() for H in Hs)
     opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED,
                      inner_cycles=args.inner_cycles, inner_max=args.inner_max)
@@ -757,9 +758,11 @@ def run_batch_case(args):
         dt = sum(ms) / len(ms) * 1e-3
         worst = max(st[b][l]["rel_res"] for b, H in enumerate(Hs) for l in range(H.num_levels))
         cyc = sum(st[b][l]["cycles"] for b, H in enumerate(Hs) for l in range(H.num_levels))
-        print(json.dumps({"case": f"batch of {len(Hs)} uneven hierarchies", "zones": zones, "ms_per_solve": dt * 1e3,
+        print(json.dumps({"case": f"batch of {len(Hs)} uneven hierarchies, edges {edges}", "zones": zones,
+                          "ms_per_solve": dt * 1e3,
                           "zones_per_s": zones / dt, "worst_rel_res": worst, "fp32_cycles_total": cyc,
                           "autotune": bool(args.autotune), "batched_kernels": os.environ.get("MG_BATCHED", "0") == "1",
+                          "persistent": os.environ.get("MG_PERSIST", "model"),
                           "timing": "CUDA events around set_density + mg_solve (writing every level's forces)"}))
     finally:
         mg.mg_destroy(h)
@@ -1091,6 +1094,7 @@ def main():
                     help="level: one DRAM-resident 3D level for profiler captures; batch: uneven hierarchies")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--box-n", default="512x256x256", help="box case: cells per axis of each patch")
+    ap.add_argument("--batch-edges", default="", help="batch case: cells per edge to draw from, e.g. 16,24,32")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--level-n", type=int, default=254)

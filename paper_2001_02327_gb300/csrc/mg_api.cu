@@ -423,6 +423,17 @@ struct mg_hierarchy {
     std::vector<BatchLevel> bl;
     char *batch_mem = nullptr;
     bool batched = false;
+    // persistent batched plan (one launch: a block per hierarchy at a time)
+    bool persist = false;
+    std::vector<char> in_persist;  // per hierarchy: solved by the persistent launch
+    cudaStream_t cap_p = nullptr;  // capture stream of the persistent launch's branch
+    cudaEvent_t ev_pjoin = nullptr;
+    char *persist_mem = nullptr;
+    MgBPart *pparts = nullptr;
+    MgPTask *ptasks = nullptr;
+    unsigned *pnext = nullptr;
+    int nptasks = 0, pgrid = 0;
+    size_t psmem = 0;
     cudaStream_t body_stream = nullptr;
     cudaStream_t inner_stream = nullptr;   // captures the nested loop of an adaptive step
     cudaEvent_t ev_fork = nullptr, ev_join[MG_BRANCHES] = {};
@@ -1313,6 +1324,190 @@ bool plan_batched(mg_hierarchy *h, mg_status &err)
 // One iteration of the batched loop of level l: FP64 defect, inner_cycles
 // FP32 V-cycles over all parts (pre legs by depth, the one-block kernels,
 // post legs), FP64 accumulation, norms and the loop control.
+// The persistent plan: every (hierarchy, level) as a part in level order,
+// the hierarchies ordered by decreasing active cells (the largest start
+// first, so the last block to finish holds a small one), FP32 levels plain.
+// Eligible: mixed precision, buffer interface, residual stopping rule, no
+// learned guess and no cluster levels.
+bool persist_eligible(const mg_hierarchy *h)
+{
+    const mg_options &o = h->opt;
+    if (o.precision != MG_MIXED || h->batch < 2 || o.interface != MG_IFACE_BUFFER || o.stop != MG_STOP_RESIDUAL ||
+        o.guess == MG_GUESS_LEARNED)
+        return false;
+    for (const auto &hl : h->lev)
+        for (const auto &ld : hl)
+            if (ld.Lc[1] >= 0 || ld.frozen)
+                return false;
+    return true;
+}
+
+// Which hierarchies of an eligible batch the persistent launch takes.  Cost
+// model, calibrated on GB300 batches of 512 hierarchies of 16-32 and 32-48
+// cells per edge and of 64 and 512 hierarchies of 32-128: a graph branch
+// costs about 2.3 us per kernel node (Ls (2 nu_pre + 1) + 1 + Ls (2 nu_post
+// + 1) nodes per V-cycle, 12 V-cycles per level assumed, 8 branches at once)
+// plus its cells at 1.5e9 per second; the persistent launch solves 6e6 cells
+// per second per block, 2 blocks per SM, largest hierarchy first.  The whole
+// batch goes to the persistent launch when that estimate is the shorter:
+// run beside graph branches it takes SMs and bandwidth from them (measured:
+// a split of the 512-hierarchy batch of 32-128 took 707 ms against 642 ms
+// with graph branches only).  MG_PERSIST=1 / 0 forces all / none (the
+// batched kernels, MG_BATCHED=1, exclude it); MG_PERSIST_COUNT=k gives the k
+// smallest hierarchies to it and the rest to graph branches in the same
+// graph.
+void choose_persistent(mg_hierarchy *h)
+{
+    const int nb = h->batch;
+    h->in_persist.assign(nb, 0);
+    const char *v = std::getenv("MG_PERSIST");
+    const char *vb = std::getenv("MG_BATCHED");
+    if (!persist_eligible(h) || (v && v[0] == '0') || (vb && vb[0] == '1'))
+        return;
+    if (v && v[0] == '1') {
+        h->in_persist.assign(nb, 1);
+        return;
+    }
+    const mg_options &o = h->opt;
+    std::vector<double> cells(nb, 0.0), lat(nb, 0.0);
+    for (int b = 0; b < nb; b++)
+        for (const auto &ld : h->lev[b]) {
+            cells[b] += cells_d(ld.n, h->dim);
+            const int Ls = ld.Ls[1];
+            lat[b] += 12.0 * (Ls * (2.0 * o.nu_pre + 1) + 1 + Ls * (2.0 * o.nu_post + 1)) * 2.3e-6;
+        }
+    if (const char *kv = std::getenv("MG_PERSIST_COUNT")) {
+        std::vector<int> order(nb);
+        for (int b = 0; b < nb; b++)
+            order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cells[a] < cells[c]; });
+        const int k = std::max(0, std::min(std::atoi(kv), nb));
+        for (int i = 0; i < k; i++)
+            h->in_persist[order[i]] = 1;
+        return;
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    double g_lat = 0.0, all = 0.0, big = 0.0;
+    for (int b = 0; b < nb; b++) {
+        g_lat += lat[b];
+        all += cells[b];
+        big = std::max(big, cells[b]);
+    }
+    const double tg = g_lat / 8.0 + all / 1.5e9;
+    const double tp = std::max(big / 6e6, all / (std::min((double)nb, 2.0 * nsm) * 6e6));
+    if (tp < tg)
+        h->in_persist.assign(nb, 1);
+}
+
+bool plan_persistent(mg_hierarchy *h, mg_status &err)
+{
+    err = MG_OK;
+    const int dim = h->dim;
+    const mg_options &o = h->opt;
+    std::vector<MgBPart> parts;
+    std::vector<MgPTask> tasks;
+    std::vector<double> work;
+    size_t smem = 0;
+    for (int b = 0; b < h->batch; b++) {
+        if (!h->in_persist[b])
+            continue;
+        MgPTask T{(int)parts.size(), h->desc[b].num_levels};
+        double cellsum = 0.0;
+        for (int l = 0; l < h->desc[b].num_levels; l++) {
+            LevelData &ld = h->lev[b][l];
+            if (cudaError_t e = plan_split(ld, dim, 0, h->stream)) {
+                err = fail_cuda(h, e, "persistent plan");
+                return false;
+            }
+            MgBPart P;
+            std::memset(&P, 0, sizeof P);
+            P.b = b;
+            P.l = l;
+            P.nmg = ld.nmg;
+            P.Ls = ld.Ls[1];
+            for (int L = 0; L < ld.nmg; L++) {
+                P.g[L] = ld.g[L];
+                P.phi32[L] = ld.phi32[L];
+                P.phi32b[L] = ld.phi32b[L];
+                P.f32[L] = ld.f32[L];
+            }
+            P.phi = ld.phi[0];
+            P.f = ld.f[0];
+            P.rho = ld.rho;
+            P.scal = level_scal(h, b, l);
+            P.ctl = level_ctl(h, b, l);
+            P.bt = ld.bt[1];
+            P.n = ld.n;
+            P.h = ld.h;
+            P.fourpiG = 4.0 * M_PI * h->desc[b].G;
+            P.guess = ld.guess;
+            P.out_F = ld.out_F;
+            P.out_phi = ld.out_phi;
+            if (l == 0) {
+                P.gmode = ld.guess_set ? 2 : -1;
+            } else {
+                const LevelData &pd = h->lev[b][ld.parent];
+                P.np = pd.n;
+                P.phi_p = pd.phi[0];
+                P.rho_p = pd.rho;
+                for (int a = 0; a < 3; a++)
+                    P.off[a] = ld.off[a];
+                P.gmode = o.guess == MG_GUESS_USER ? (ld.guess_set ? 2 : 0) : (o.guess == MG_GUESS_ZERO ? 1 : 0);
+            }
+            smem = std::max(smem, mg_bottom_smem(dim, true, P.bt));
+            cellsum += cells_d(ld.g[0].N, dim);
+            parts.push_back(P);
+        }
+        tasks.push_back(T);
+        work.push_back(cellsum);
+    }
+    std::vector<int> order(tasks.size());
+    for (size_t i = 0; i < order.size(); i++)
+        order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<MgPTask> sorted;
+    for (int i : order)
+        sorted.push_back(tasks[i]);
+    int per_sm = 0;
+    cudaError_t e = mg_persist_prepare(dim, smem, &per_sm);
+    if (e || per_sm < 1) {
+        err = fail_cuda(h, e ? e : cudaErrorInvalidConfiguration, "persistent kernel occupancy");
+        return false;
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t bytes = align256(parts.size() * sizeof(MgBPart)) + align256(sorted.size() * sizeof(MgPTask)) + 256;
+    if (h->persist_mem)
+        cudaFree(h->persist_mem);
+    h->persist_mem = nullptr;
+    if ((e = cudaMalloc((void **)&h->persist_mem, bytes))) {
+        cudaGetLastError();
+        err = fail(h, MG_ENOMEM, "cudaMalloc of %zu bytes for the persistent plan failed", bytes);
+        return false;
+    }
+    h->pparts = (MgBPart *)h->persist_mem;
+    h->ptasks = (MgPTask *)(h->persist_mem + align256(parts.size() * sizeof(MgBPart)));
+    h->pnext = (unsigned *)(h->persist_mem + align256(parts.size() * sizeof(MgBPart)) +
+                            align256(sorted.size() * sizeof(MgPTask)));
+    h->nptasks = (int)sorted.size();
+    h->psmem = smem;
+    h->pgrid = std::min(h->nptasks, per_sm * nsm);
+    e = cudaMemcpyAsync(h->pparts, parts.data(), parts.size() * sizeof(MgBPart), cudaMemcpyHostToDevice, h->stream);
+    if (!e)
+        e = cudaMemcpyAsync(h->ptasks, sorted.data(), sorted.size() * sizeof(MgPTask), cudaMemcpyHostToDevice,
+                            h->stream);
+    if (!e)
+        e = cudaStreamSynchronize(h->stream);
+    if (e) {
+        err = fail_cuda(h, e, "persistent plan upload");
+        return false;
+    }
+    return true;
+}
+
 cudaError_t capture_batched_level(mg_hierarchy *h, int l, cudaStream_t s, cudaStream_t body)
 {
     const int dim = h->dim;
@@ -1407,6 +1602,19 @@ mg_status build_graph(mg_hierarchy *h)
             CK(h, cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
     }
     h->batched = false;
+    h->persist = false;
+    choose_persistent(h);
+    for (char c : h->in_persist)
+        h->persist |= c != 0;
+    if (h->persist) {
+        mg_status perr;
+        if (!plan_persistent(h, perr))
+            return perr ? perr : MG_ECUDA;
+        if (!h->cap_p)
+            CK(h, cudaStreamCreateWithFlags(&h->cap_p, cudaStreamNonBlocking));
+        if (!h->ev_pjoin)
+            CK(h, cudaEventCreateWithFlags(&h->ev_pjoin, cudaEventDisableTiming));
+    }
     if (h->opt.precision == MG_MIXED && h->batch > 1 && h->opt.interface == MG_IFACE_BUFFER &&
         h->opt.stop == MG_STOP_RESIDUAL && h->opt.inner_max == 0) {   // the batched kernels run fixed steps
         // measured on 64 uneven hierarchies: graph branches 105 ms, batched
@@ -1447,19 +1655,40 @@ mg_status build_graph(mg_hierarchy *h)
     cudaError_t e = cudaEventRecord(h->ev_fork, h->cap[0]);
     for (int i = 1; i < nbr && !e; i++)
         e = cudaStreamWaitEvent(h->cap[i], h->ev_fork, 0);
-    for (int b = 0; b < h->batch && !e; b++)
+    if (h->persist && !e) {   // its own branch: the hierarchies the persistent launch takes
+        const mg_options &o = h->opt;
+        e = cudaStreamWaitEvent(h->cap_p, h->ev_fork, 0);
+        if (!e)
+            e = cudaMemsetAsync(h->pnext, 0, sizeof(unsigned), h->cap_p);
+        if (!e)
+            e = mg_launch_persist(h->dim, h->pparts, h->ptasks, h->nptasks, h->pnext, h->pgrid, h->psmem, o.nu_pre,
+                                  o.nu_post, o.rel_tol, o.max_cycles, o.inner_cycles,
+                                  adaptive_inner(h) ? o.inner_max : 0, o.force_stencil, h->cap_p);
+        if (!e)
+            e = cudaEventRecord(h->ev_pjoin, h->cap_p);
+    }
+    int q = 0;   // graph branches, round robin over the other hierarchies
+    for (int b = 0; b < h->batch && !e; b++) {
+        if (h->persist && h->in_persist[b])
+            continue;
         for (int l = 0; l < h->desc[b].num_levels && !e; l++)
-            e = capture_level(h, b, l, h->cap[b % nbr], b % nbr);
+            e = capture_level(h, b, l, h->cap[q % nbr], q % nbr);
+        q++;
+    }
     for (int i = 1; i < nbr && !e; i++) {
         e = cudaEventRecord(h->ev_join[i], h->cap[i]);
         if (!e)
             e = cudaStreamWaitEvent(h->cap[0], h->ev_join[i], 0);
     }
+    if (h->persist && !e)
+        e = cudaStreamWaitEvent(h->cap[0], h->ev_pjoin, 0);
     // registered outputs after every solve (beside the solves of other
-    // levels or branches they slowed those down: batch of 64, 90 vs 84 ms)
+    // levels or branches they slowed those down: batch of 64, 90 vs 84 ms);
+    // the persistent launch writes its own
     for (int b = 0; b < h->batch && !e; b++)
         for (int l = 0; l < h->desc[b].num_levels && !e; l++)
-            e = launch_outputs(h, h->lev[b][l], h->cap[0]);
+            if (!(h->persist && h->in_persist[b]))
+                e = launch_outputs(h, h->lev[b][l], h->cap[0]);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(h->cap[0], &g);
     if (e || ee) {
@@ -2383,6 +2612,12 @@ mg_status mg_destroy(mg_hierarchy *h)
     for (cudaEvent_t e : h->prof.pool)
         cudaEventDestroy(e);
     destroy_graph(h);
+    if (h->persist_mem)
+        cudaFree(h->persist_mem);
+    if (h->cap_p)
+        cudaStreamDestroy(h->cap_p);
+    if (h->ev_pjoin)
+        cudaEventDestroy(h->ev_pjoin);
     if (h->batch_mem)
         cudaFree(h->batch_mem);
     for (int i = 0; i < MG_BRANCHES; i++) {

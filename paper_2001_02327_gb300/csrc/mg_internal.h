@@ -373,6 +373,12 @@ struct MgBPart {
     int n, np, off[3], gmode;      // gmode: 0 interpolate, 1 zero, 2 copy guess, -1 none (level 0)
     const double *phi_p, *rho_p, *guess;
     double fourpiG;
+    // persistent solve: the level's registered outputs (or NULL) and cell size
+    double *out_F, *out_phi;
+    double h;
+};
+struct MgPTask {                   // persistent solve: one hierarchy, its parts in level order
+    int first, count;
 };
 struct MgBTask {                   // tile task
     int part, bx, by, bz;
@@ -382,6 +388,21 @@ struct MgBCell {                   // cell-chunk task
 };
 
 cudaError_t mg_batch_prepare();
+// Persistent batched mixed-precision solve (one launch for the whole batch):
+// `grid` blocks of mg_persist_threads() threads take hierarchies from
+// tasks[0..ntasks-1] in order through the counter *next (zero at launch) and
+// solve each one's levels coarse to fine, every phase by the block alone
+// (interface, norms with the fused FP32 defect, the FP32 V-cycles of each
+// defect-correction step with the one-block bottom, accumulation, control,
+// registered outputs).  Every level above the bottom must use the plain FP32
+// layout and one kernel per phase.  smem: the largest bottom plan's shared
+// memory.  inner_max > 0: adaptive steps (mg_next_inner), else inner0 cycles
+// per step.
+int mg_persist_threads();
+cudaError_t mg_persist_prepare(int dim, size_t smem, int *blocks_per_sm);
+cudaError_t mg_launch_persist(int dim, const MgBPart *parts, const MgPTask *tasks, int ntasks, unsigned *next,
+                              int grid, size_t smem, int nu_pre, int nu_post, double tol, int max_cycles, int inner0,
+                              int inner_max, int stencil, cudaStream_t s);
 cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,
                                int depth, int nu, size_t smem, cudaStream_t s);
 cudaError_t mg_launch_b_tb_post(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,

@@ -2127,6 +2127,53 @@ __global__ void __launch_bounds__(kThreads) kb_norms2(const MgBPart *__restrict_
     }
 }
 
+// Interface of part P at cell t of its (n+4)^d block (Sec. 2.1, Appendix A):
+// the outer ring's potential and the inner ring's density (and f) by
+// interpolation from the parent, the initial guess inside (gmode 0
+// interpolated, 1 zero, 2 the caller's); on level 0 only a caller's start.
+template <int DIM>
+__device__ __forceinline__ void iface_cell(const MgBPart &P, int t)
+{
+    const int nc = P.n, E = nc + 4, Ep = P.np + 4;
+    int s[3];
+    const int r = div_small(t, E);
+    s[0] = t - r * E;
+    const int rq = DIM == 3 ? div_small(r, E) : 0;
+    s[1] = DIM == 3 ? r - rq * E : r;
+    s[2] = DIM == 3 ? rq : 2;
+    bool outer = false, inner = false;
+    for (int a = 0; a < DIM; a++) {
+        if (s[a] == 0 || s[a] == nc + 3)
+            outer = true;
+        else if (s[a] == 1 || s[a] == nc + 2)
+            inner = true;
+    }
+    if (P.l == 0) {            // level 0: only a caller-supplied start inside
+        if (!outer && P.gmode == 2)
+            P.phi[t] = P.guess[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+        return;
+    }
+    int p0[3] = {0, 0, 0};
+    double w[3] = {0, 0, 0};
+    for (int a = 0; a < DIM; a++)
+        iface_axis(s[a], P.off[a], p0[a], w[a]);
+    if (outer) {
+        P.phi[t] = interp<DIM>(P.phi_p, Ep, p0, w);
+        return;
+    }
+    if (inner) {
+        const double rv = interp<DIM>(P.rho_p, Ep, p0, w);
+        P.rho[t] = rv;
+        P.f[t] = P.fourpiG * rv;
+    }
+    if (P.gmode == 0)
+        P.phi[t] = interp<DIM>(P.phi_p, Ep, p0, w);
+    else if (P.gmode == 1)
+        P.phi[t] = 0.0;
+    else
+        P.phi[t] = P.guess[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) kb_interface(const MgBPart *__restrict__ parts,
                                                          const MgBCell *__restrict__ cells)
@@ -2136,47 +2183,10 @@ __global__ void __launch_bounds__(kThreads) kb_interface(const MgBPart *__restri
     const MgBPart &P = parts[c.part];
     if (P.gmode < 0)
         return;
-    const int nc = P.n, E = nc + 4, Ep = P.np + 4;
+    const int E = P.n + 4;
     const int total = E * E * (DIM == 3 ? E : 1);
-    for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_blk * kThreads) {
-        int s[3];
-        const int r = div_small(t, E);
-        s[0] = t - r * E;
-        const int rq = DIM == 3 ? div_small(r, E) : 0;
-        s[1] = DIM == 3 ? r - rq * E : r;
-        s[2] = DIM == 3 ? rq : 2;
-        bool outer = false, inner = false;
-        for (int a = 0; a < DIM; a++) {
-            if (s[a] == 0 || s[a] == nc + 3)
-                outer = true;
-            else if (s[a] == 1 || s[a] == nc + 2)
-                inner = true;
-        }
-        if (P.l == 0) {            // level 0: only a caller-supplied start inside
-            if (!outer && P.gmode == 2)
-                P.phi[t] = P.guess[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
-            continue;
-        }
-        int p0[3] = {0, 0, 0};
-        double w[3] = {0, 0, 0};
-        for (int a = 0; a < DIM; a++)
-            iface_axis(s[a], P.off[a], p0[a], w[a]);
-        if (outer) {
-            P.phi[t] = interp<DIM>(P.phi_p, Ep, p0, w);
-            continue;
-        }
-        if (inner) {
-            const double rv = interp<DIM>(P.rho_p, Ep, p0, w);
-            P.rho[t] = rv;
-            P.f[t] = P.fourpiG * rv;
-        }
-        if (P.gmode == 0)
-            P.phi[t] = interp<DIM>(P.phi_p, Ep, p0, w);
-        else if (P.gmode == 1)
-            P.phi[t] = 0.0;
-        else
-            P.phi[t] = P.guess[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
-    }
+    for (int t = c.chunk * kThreads + threadIdx.x; t < total; t += P.nblk_blk * kThreads)
+        iface_cell<DIM>(P, t);
 }
 
 __global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts, int nparts, int *__restrict__ active,
@@ -2212,6 +2222,196 @@ __global__ void __launch_bounds__(1024) kb_ctl(const MgBPart *__restrict__ parts
     any = __syncthreads_or(any);
     if (threadIdx.x == 0)
         cudaGraphSetConditional(hc, any ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// persistent batched solve: one block per hierarchy at a time
+// ---------------------------------------------------------------------------
+constexpr int kPersistThreads = 512;
+
+// Fixed-order sum over the block (up to 1024 threads); valid in thread 0.
+__device__ __forceinline__ double block_sum_all(double v, double *sm)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+        sm[w] = v;
+    __syncthreads();
+    v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    if (w == 0)
+        v = warp_sum(v);
+    return v;
+}
+
+// One FP32 V-cycle (Sec. 2.3 steps 2-13) of part P by this block: per level
+// above the bottom, nu_pre sweeps and the residual restriction, the bottom
+// levels from the one-block plan, then prolongation and nu_post sweeps back
+// up.  The same per-cell functions as the one-kernel-per-phase launches.
+template <int DIM>
+__device__ void persist_vcycle(const MgBPart &P, int nu_pre, int nu_post, unsigned char *smem)
+{
+    const int tid = threadIdx.x, nth = blockDim.x, Ls = P.Ls;
+    for (int L = 0; L < Ls; L++) {
+        for (int sw = 0; sw < nu_pre; sw++)
+            for (int col = 0; col < 2; col++) {
+                op_smooth_colour<float, DIM>(P.phi32[L], P.f32[L], P.g[L], col, tid, nth);
+                __syncthreads();
+            }
+        op_resid_restrict<float, DIM>(P.phi32[L], P.f32[L], P.g[L], P.phi32[L + 1], P.f32[L + 1], P.g[L + 1], tid,
+                                      nth);
+        __syncthreads();
+    }
+    bottom_body<float, DIM>(P.phi32[Ls], P.f32[Ls], P.bt, nu_pre, nu_post, smem);
+    __syncthreads();
+    for (int L = Ls; L > 0; L--) {
+        op_prolong<float, DIM>(P.phi32[L], P.g[L], P.phi32[L - 1], P.g[L - 1], tid, nth);
+        __syncthreads();
+        for (int sw = 0; sw < nu_post; sw++)
+            for (int col = 0; col < 2; col++) {
+                op_smooth_colour<float, DIM>(P.phi32[L - 1], P.f32[L - 1], P.g[L - 1], col, tid, nth);
+                __syncthreads();
+            }
+    }
+}
+
+// ||b||^2 and / or ||r||^2 of part P's finest level (which as in
+// norm_terms), writing the next step's FP32 defect with it; the sums land in
+// red[0..1] for every thread.
+template <int DIM>
+__device__ void persist_norms(const MgBPart &P, int which, double *sm, double *red)
+{
+    const MgGeom &g = P.g[0];
+    const int total = g.N * g.N * (DIM == 3 ? g.N : 1);
+    double b2 = 0.0, r2 = 0.0;
+    for (int t = threadIdx.x; t < total; t += blockDim.x)
+        norm_terms<DIM>(P.phi, P.f, g, t, which, b2, r2, P.f32[0], P.phi32[0]);
+    b2 = block_sum_all(b2, sm);
+    r2 = block_sum_all(r2, sm);
+    if (threadIdx.x == 0) {
+        red[0] = b2;
+        red[1] = r2;
+    }
+    __syncthreads();
+}
+
+// The solve of one refinement level (part P) by this block, with the loop
+// control of the graph path (k_ctl_init / k_ctl_step, nested adaptive steps)
+// taken by thread 0.
+template <int DIM>
+__device__ void persist_level(const MgBPart &P, int nu_pre, int nu_post, double tol, int max_cycles, int inner0,
+                              int inner_max, int stencil, unsigned char *smem)
+{
+    __shared__ double sm[32];
+    __shared__ double red[2];
+    __shared__ MgSolveCtl cs;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int E = P.n + 4;
+    if (P.gmode >= 0) {
+        const int total = E * E * (DIM == 3 ? E : 1);
+        for (int t = tid; t < total; t += nth)
+            iface_cell<DIM>(P, t);
+        __syncthreads();
+    }
+    persist_norms<DIM>(P, 3, sm, red);
+    if (tid == 0) {
+        MgSolveCtl c;
+        c.bnorm = sqrt(red[0]);
+        c.rel = c.bnorm > 0.0 ? sqrt(red[1]) / c.bnorm : 0.0;
+        c.cycles = 0;
+        c.outer = 0;
+        c.status = isfinite(c.bnorm) ? 0 : 6;
+        c.inner = inner0;
+        c.left = min(inner0, max_cycles);
+        c.cyc0 = 0;
+        c.go = keep_going(c, tol, max_cycles);
+        cs = c;
+    }
+    __syncthreads();
+    const MgGeom &g0 = P.g[0];
+    const int nact = g0.N * g0.N * (DIM == 3 ? g0.N : 1);
+    while (cs.go) {
+        const int ncyc = inner_max > 0 ? cs.left : inner0;
+        for (int v = 0; v < ncyc; v++)
+            persist_vcycle<DIM>(P, nu_pre, nu_post, smem);
+        for (int t = tid; t < nact; t += nth) {   // Phi += e in FP64
+            int i, j, k;
+            active_cell<DIM>(g0, t, i, j, k);
+            P.phi[lin<DIM>(i, j, k, g0.E)] += (double)P.phi32[0][mg_idx32(g0, DIM, i, j, k)];
+        }
+        __syncthreads();
+        persist_norms<DIM>(P, 2, sm, red);
+        if (tid == 0) {
+            MgSolveCtl c = cs;
+            const double before = c.rel;
+            c.cycles += ncyc;
+            c.outer += 1;
+            c.rel = sqrt(red[1]) / c.bnorm;
+            if (!isfinite(c.rel))
+                c.status = 6;
+            if (inner_max > 0) {
+                c.inner = mg_next_inner(before, c.rel, c.cycles - c.cyc0, tol, inner_max);
+                c.left = min(c.inner, max_cycles - c.cycles);
+                c.cyc0 = c.cycles;
+            }
+            c.go = keep_going(c, tol, max_cycles);
+            cs = c;
+        }
+        __syncthreads();
+    }
+    if (P.out_F) {   // registered outputs: potential and forces of Eq. 2 (or the two-point difference)
+        const int n = P.n;
+        const int total = n * n * (DIM == 3 ? n : 1);
+        const double c1 = stencil == 0 ? (4.0 / 3.0) / (2.0 * P.h) : 1.0 / (2.0 * P.h);
+        const double c2 = stencil == 0 ? (1.0 / 3.0) / (4.0 * P.h) : 0.0;
+        for (int t = tid; t < total; t += nth) {
+            const int r = div_small(t, n);
+            const int i = t - r * n + 2;
+            const int rq = DIM == 3 ? div_small(r, n) : 0;
+            const int j = DIM == 3 ? r - rq * n + 2 : r + 2;
+            const int k = DIM == 3 ? rq + 2 : 0;
+            const int p = lin<DIM>(i, j, k, E);
+            const int st[3] = {1, E, E * E};
+            for (int a = 0; a < DIM; a++) {
+                const double d1 = P.phi[p + st[a]] - P.phi[p - st[a]];
+                const double d2 = P.phi[p + 2 * st[a]] - P.phi[p - 2 * st[a]];
+                P.out_F[(long)a * total + t] = -(c1 * d1 - c2 * d2);
+            }
+            if (P.out_phi)
+                P.out_phi[t] = P.phi[p];
+        }
+    }
+    if (tid == 0)
+        *P.ctl = cs;
+    __syncthreads();
+}
+
+// The whole batch in one launch: each block takes the next hierarchy from
+// the counter (hierarchies ordered largest first on the host) and solves its
+// levels in order; no block waits for another.
+template <int DIM>
+__global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const MgBPart *__restrict__ parts,
+                                                               const MgPTask *__restrict__ tasks, int ntasks,
+                                                               unsigned *__restrict__ next, int nu_pre, int nu_post,
+                                                               double tol, int max_cycles, int inner0, int inner_max,
+                                                               int stencil)
+{
+    pdl_begin();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int task;
+    for (;;) {
+        if (threadIdx.x == 0)
+            task = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int q = task;
+        if (q >= ntasks)
+            return;
+        const MgPTask T = tasks[q];
+        for (int l = 0; l < T.count; l++)
+            persist_level<DIM>(parts[T.first + l], nu_pre, nu_post, tol, max_cycles, inner0, inner_max, stencil,
+                               smem_raw);
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -2672,6 +2872,35 @@ cudaError_t mg_batch_prepare()
     if (!e)
         e = cudaFuncSetAttribute(kb_bottom<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MG_BOTTOM_SMEM_MAX);
     return e;
+}
+
+int mg_persist_threads() { return kPersistThreads; }
+
+cudaError_t mg_persist_prepare(int dim, size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = dim == 3 ? cudaFuncSetAttribute(k_persist<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    MG_BOTTOM_SMEM_MAX)
+                             : cudaFuncSetAttribute(k_persist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    MG_BOTTOM_SMEM_MAX);
+    if (e)
+        return e;
+    return dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persist<3>, kPersistThreads, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persist<2>, kPersistThreads, smem);
+}
+
+cudaError_t mg_launch_persist(int dim, const MgBPart *parts, const MgPTask *tasks, int ntasks, unsigned *next,
+                              int grid, size_t smem, int nu_pre, int nu_post, double tol, int max_cycles, int inner0,
+                              int inner_max, int stencil, cudaStream_t s)
+{
+    if (ntasks <= 0 || grid <= 0)
+        return cudaSuccess;
+    if (dim == 3)
+        mg_launch_kernel(k_persist<3>, grid, kPersistThreads, smem, s, parts, tasks, ntasks, next, nu_pre, nu_post,
+                         tol, max_cycles, inner0, inner_max, stencil);
+    else
+        mg_launch_kernel(k_persist<2>, grid, kPersistThreads, smem, s, parts, tasks, ntasks, next, nu_pre, nu_post,
+                         tol, max_cycles, inner0, inner_max, stencil);
+    return cudaGetLastError();
 }
 
 cudaError_t mg_launch_b_tb_pre(int dim, const MgBPart *parts, const MgBTask *tasks, int ntasks, const int *active,

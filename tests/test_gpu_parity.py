@@ -937,3 +937,105 @@ def test_split_smoothing_timed_with_split_bytes(mg, monkeypatch):
         assert us > 0 and by == 1.5 * 4 * 66 ** 3
     finally:
         mg.mg_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# the persistent batched solve (one launch for the whole batch)
+# --------------------------------------------------------------------------
+def _batch_solve(mg, Hs, outputs=False, **kw):
+    import torch
+    h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], mg.options(**kw))
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        outs = {}
+        for b, H in enumerate(Hs):
+            inp = I.level_inputs(H)
+            mg.mg_set_density(h, b, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            for l in range(1, H.num_levels):
+                mg.mg_set_density(h, b, l, dev(inp[l]["rho"]))
+            if outputs:
+                for l in range(H.num_levels):
+                    shp = (H.n[l],) * H.dim
+                    P = torch.zeros(shp, dtype=torch.float64, device="cuda")
+                    F = torch.zeros((H.dim,) + shp, dtype=torch.float64, device="cuda")
+                    mg.mg_set_outputs(h, b, l, P, F)
+                    outs[b, l] = (P, F)
+        res = []
+        for rep in range(2):                  # the second solve reuses the graph
+            for b, H in enumerate(Hs):
+                inp = I.level_inputs(H)
+                mg.mg_set_density(h, b, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+                for l in range(1, H.num_levels):
+                    mg.mg_set_density(h, b, l, dev(inp[l]["rho"]))
+            _, st = mg.mg_solve(h, len(Hs))
+        for b, H in enumerate(Hs):
+            lev = []
+            for l in range(H.num_levels):
+                shp = (H.n[l],) * H.dim
+                if outputs:
+                    P, F = outs[b, l]
+                else:
+                    P = torch.zeros(shp, dtype=torch.float64, device="cuda")
+                    F = torch.zeros((H.dim,) + shp, dtype=torch.float64, device="cuda")
+                    mg.mg_forces(h, b, l, P, F)
+                torch.cuda.synchronize()
+                lev.append((P.cpu().numpy(), F.cpu().numpy(), st[b][l]))
+            res.append(lev)
+        return res
+    finally:
+        mg.mg_destroy(h)
+
+
+@pytest.mark.parametrize("inner_max,outputs,guess", [(8, False, 0), (0, True, 0), (8, True, 1)])
+def test_persistent_batch_equals_graph_branches(mg, monkeypatch, inner_max, outputs, guess):
+    """One persistent launch over the batch (a block per hierarchy, levels in
+    order) gives the cycle counts and results of the per-hierarchy graph
+    branches: the same per-cell arithmetic, norms summed in another order."""
+    Hs = [I.random_hierarchy(s) for s in range(14)]
+    Hs = [H for H in Hs if max(H.n) <= 96][:6]
+    monkeypatch.setenv("MG_SPLIT", "0")
+    kw = dict(precision=mg.MG_MIXED, nu_pre=2, nu_post=2, inner_max=inner_max, guess=guess)
+    monkeypatch.setenv("MG_PERSIST", "0")
+    a = _batch_solve(mg, Hs, outputs, **kw)
+    monkeypatch.setenv("MG_PERSIST", "1")
+    b = _batch_solve(mg, Hs, outputs, **kw)
+    for ha, hb in zip(a, b):
+        for (pa, Fa, sa), (pb, Fb, sb) in zip(ha, hb):
+            assert sb["status"] == 0 and sb["rel_res"] < 1e-10
+            assert sa["cycles"] == sb["cycles"] and sa["outer_steps"] == sb["outer_steps"], (sa, sb)
+            assert relmax(pb, pa) < 1e-10 and relmax(Fb, Fa) < 1e-9
+
+
+def test_persistent_batch_2d(mg, monkeypatch):
+    Hs = [I.config_2d_disk(n, 3) for n in (32, 64, 48, 64, 96)]
+    monkeypatch.setenv("MG_SPLIT", "0")
+    kw = dict(precision=mg.MG_MIXED, nu_pre=2, nu_post=2, inner_max=8)
+    monkeypatch.setenv("MG_PERSIST", "0")
+    a = _batch_solve(mg, Hs, **kw)
+    monkeypatch.setenv("MG_PERSIST", "1")
+    b = _batch_solve(mg, Hs, **kw)
+    for ha, hb in zip(a, b):
+        for (pa, Fa, sa), (pb, Fb, sb) in zip(ha, hb):
+            assert sa["cycles"] == sb["cycles"] and sb["rel_res"] < 1e-10
+            assert relmax(pb, pa) < 1e-10
+
+
+def test_mixed_persistent_and_graph_branches(mg, monkeypatch):
+    """The smallest hierarchies in the persistent launch, the others as graph
+    branches beside it in the same graph, as the cost model splits a batch:
+    results and cycle counts as with graph branches only."""
+    Hs = [I.random_hierarchy(s, edges=(16, 24, 32)) for s in range(6)] + \
+         [I.random_hierarchy(s) for s in range(20, 24)]
+    monkeypatch.setenv("MG_SPLIT", "0")
+    kw = dict(precision=mg.MG_MIXED, nu_pre=2, nu_post=2, inner_max=8)
+    monkeypatch.setenv("MG_PERSIST", "0")
+    a = _batch_solve(mg, Hs, True, **kw)
+    monkeypatch.delenv("MG_PERSIST")
+    monkeypatch.setenv("MG_PERSIST_COUNT", "6")
+    b = _batch_solve(mg, Hs, True, **kw)
+    monkeypatch.delenv("MG_PERSIST_COUNT")
+    c = _batch_solve(mg, Hs, True, **kw)          # the cost model's own split
+    for ha, hb, hc in zip(a, b, c):
+        for (pa, Fa, sa), (pb, Fb, sb), (pc, Fc, sc) in zip(ha, hb, hc):
+            assert sa["cycles"] == sb["cycles"] == sc["cycles"]
+            assert relmax(pb, pa) < 1e-10 and relmax(pc, pa) < 1e-10 and relmax(Fb, Fa) < 1e-9
