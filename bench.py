@@ -587,6 +587,10 @@ def run_ours(args):
     if scale is not None:
         out["scale_4x256cubed"] = scale
         out["roofline_dram_resident"] = scale["mixed"].get("kernel_roofline")
+    if not args.no_batch:
+        # the uneven batch of 512 hierarchies, and 512 small ones (the persistent launch's case)
+        out["batch_512"] = batch_case(mg, torch, 512, I.EDGES, 2, 2, args.inner_cycles, args.inner_max)
+        out["batch_512_small"] = batch_case(mg, torch, 512, (16, 24, 32), 3, 2, args.inner_cycles, args.inner_max)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(H, inp)
     if rank == 0:
@@ -699,57 +703,50 @@ def run_smoothing_case(args):
         mg.mg_destroy(h)
 
 
-def run_batch_case(args):
-    """Uneven batch: `--batch` seeded hierarchies (2-4 levels, edges from
-    {32,48,64,96,128}, 1-4 compact spheres each), mixed precision, V(2,2) to
-    1e-10, solved together in one graph launch.  Prints one line of timing
-    (zones/s over all hierarchies), not the benchmark record."""
-    import torch
-    from paper_2001_02327_gb300 import build
-    build.build()
-    from paper_2001_02327_gb300 import mg
-    edges = tuple(int(e) for e in args.batch_edges.split(",")) if args.batch_edges else I.EDGES
-    Hs = [I.random_hierarchy(I.BASE_SEED + b, edges=edges) for b in range(args.batch)]
+def batch_case(mg, torch, nb, edges, steps, warmup, inner_cycles, inner_max, autotune=False, forces_call=False):
+    """Uneven batch: nb seeded hierarchies (2-4 levels, edges drawn from
+    `edges`, 1-4 compact spheres each), mixed precision, V(2,2) to 1e-10,
+    solved together in one graph launch (graph branches or the persistent
+    launch, as the library's cost model picks), every level's forces written
+    by mg_solve; CUDA events around set_density + mg_solve, mean of `steps`."""
+    Hs = [I.random_hierarchy(I.BASE_SEED + b, edges=edges) for b in range(nb)]
     zones = sum(H.zones() for H in Hs)
     opt = mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60, rel_tol=TOL, precision=mg.MG_MIXED,
-                     inner_cycles=args.inner_cycles, inner_max=args.inner_max)
+                     inner_cycles=inner_cycles, inner_max=inner_max)
     h = mg.mg_create_hierarchy([mg.desc_from(H) for H in Hs], opt)
     try:
-        if args.autotune:
+        if autotune:
             mg.mg_autotune(h, None)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         ins = []
         for H in Hs:
             inp = I.level_inputs(H)
             ins.append([{k: dev(v) for k, v in d.items()} for d in inp])
-
-        # every level's forces, written by mg_solve once the level has converged
         Fs = [[torch.empty((3,) + (n,) * 3, dtype=torch.float64, device="cuda") for n in H.n] for H in Hs]
         for b, H in enumerate(Hs):
             for l in range(H.num_levels):
-                if not args.forces_call:
+                if not forces_call:
                     mg.mg_set_outputs(h, b, l, None, Fs[b][l])
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
         def step():
-            """inputs (device-resident) into the hierarchies, solve (forces of every level included)"""
             for b, H in enumerate(Hs):
                 d = ins[b]
                 mg.mg_set_density(h, b, 0, d[0]["rho"], d[0]["bc_rho"], d[0]["bc_phi"])
                 for l in range(1, H.num_levels):
                     mg.mg_set_density(h, b, l, d[l]["rho"])
             st = mg.mg_solve(h, len(Hs))[1]
-            if args.forces_call:
+            if forces_call:
                 for b, H in enumerate(Hs):
                     for l in range(H.num_levels):
                         mg.mg_forces(h, b, l, None, Fs[b][l])
             return st
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             st = step()
         torch.cuda.synchronize()
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             ev0.record()
             st = step()
             ev1.record()
@@ -758,14 +755,28 @@ def run_batch_case(args):
         dt = sum(ms) / len(ms) * 1e-3
         worst = max(st[b][l]["rel_res"] for b, H in enumerate(Hs) for l in range(H.num_levels))
         cyc = sum(st[b][l]["cycles"] for b, H in enumerate(Hs) for l in range(H.num_levels))
-        print(json.dumps({"case": f"batch of {len(Hs)} uneven hierarchies, edges {edges}", "zones": zones,
-                          "ms_per_solve": dt * 1e3,
-                          "zones_per_s": zones / dt, "worst_rel_res": worst, "fp32_cycles_total": cyc,
-                          "autotune": bool(args.autotune), "batched_kernels": os.environ.get("MG_BATCHED", "0") == "1",
-                          "persistent": os.environ.get("MG_PERSIST", "model"),
-                          "timing": "CUDA events around set_density + mg_solve (writing every level's forces)"}))
+        npers = mg.mg_persistent_count(h)
+        return {"case": f"batch of {len(Hs)} uneven hierarchies, edges {list(edges)}", "zones": zones,
+                "ms_per_solve": dt * 1e3, "zones_per_s": zones / dt, "worst_rel_res": worst,
+                "fp32_cycles_total": cyc, "autotune": bool(autotune),
+                "batched_kernels": os.environ.get("MG_BATCHED", "0") == "1",
+                "solve_plan": "persistent launch" if npers == len(Hs) else
+                              ("graph branches" if npers == 0 else f"persistent launch for {npers}, graph branches"),
+                "timing": f"CUDA events around set_density + mg_solve (writing every level's forces), mean of {steps}"}
     finally:
         mg.mg_destroy(h)
+
+
+def run_batch_case(args):
+    """Uneven batch of `--batch` hierarchies (edges from {32,48,64,96,128}
+    or `--batch-edges`); prints one line of timing, not the benchmark record."""
+    import torch
+    from paper_2001_02327_gb300 import build
+    build.build()
+    from paper_2001_02327_gb300 import mg
+    edges = tuple(int(e) for e in args.batch_edges.split(",")) if args.batch_edges else I.EDGES
+    print(json.dumps(batch_case(mg, torch, args.batch, edges, args.steps, args.warmup, args.inner_cycles,
+                                args.inner_max, args.autotune, args.forces_call)))
 
 
 def run_scale_case(args):
@@ -1074,6 +1085,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="leave out the mixed + learned-guess form")
     ap.add_argument("--no-scale", action="store_true", help="leave out the 4x256^3 DRAM-resident workload")
+    ap.add_argument("--no-batch", action="store_true", help="leave out the 512-hierarchy batches")
     ap.add_argument("--inner-cycles", type=int, default=3,
                     help="mixed forms: FP32 V-cycles of the first defect-correction step (of every step "
                          "with --inner-max 0)")

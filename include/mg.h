@@ -208,6 +208,15 @@ mg_status mg_forces(mg_hierarchy *h, int b, int level, double *phi_out, double *
  * (range, phi without F, pageable host memory). */
 mg_status mg_set_outputs(mg_hierarchy *h, int b, int level, double *phi_out, double *F_out);
 
+/* How many hierarchies of the batch the solve graph gives to the persistent
+ * launch (one launch, one thread block per hierarchy at a time, solving its
+ * levels with block-wide phases; chosen when a cost model of the two puts it
+ * ahead of one graph branch per hierarchy, which suits many small
+ * hierarchies), 0 when every hierarchy runs as graph branches, -1 before the
+ * first mg_solve builds the graph or with a NULL handle.  Not part of the
+ * paper. */
+int mg_persistent_count(const mg_hierarchy *h);
+
 /* Release everything; NULL-safe; always MG_OK. */
 mg_status mg_destroy(mg_hierarchy *h);
 

@@ -133,13 +133,15 @@ void plan_tiles(LevelData &ld, int dim, int nu_pre, int nu_post)
 // run the box-patch kernels (mg_box.cu), whose colour pass moves exactly its
 // algorithmic bytes; levels below stay plain for the bottom, plane-marching
 // and blocked kernels.  MG_SPLIT=S fixes S; without it (and without tuning)
-// the levels of 64 cells per edge or more are split, unless MG_WAVE,
+// the levels of 192 cells per edge or more are split (measured on 4 nested
+// 256^3 levels: the 258^3 level gains 33.4 -> 28.6 ms, splitting the 129^3
+// level as well costs 0.9 ms, and at 66^3 the tuner keeps plain), unless MG_WAVE,
 // MG_WAVE_PLAN or MG_TB_TILE ask for the plain-layout plans.  mg_autotune
 // times the choices; the batched kernels (MG_BATCHED=1) run plain levels
 // only.  Changing the layout clears the level's FP32 arrays (their ghost
 // layer must read zero in either layout).
 constexpr int kTileSplit = 1 << 16;   // mg_tuning / tuning-cache code of a split level
-constexpr int kSplitMinN = 64;
+constexpr int kSplitMinN = 192;
 
 int split_default(const LevelData &ld)
 {
@@ -2589,6 +2591,17 @@ mg_status mg_time_smoothing(mg_hierarchy *h, int b, int level, int L, int launch
     *us_per_launch = 1e3 * (double)ms / launches;
     *bytes_per_launch = (code < 0 ? 3.0 : 1.5) * sizeof(float) * nc;
     return MG_OK;
+}
+
+int mg_persistent_count(const mg_hierarchy *h)
+{
+    if (!h || !h->gexec)
+        return -1;
+    int k = 0;
+    if (h->persist)
+        for (char c : h->in_persist)
+            k += c != 0;
+    return k;
 }
 
 int mg_tuning(const mg_hierarchy *h, int b, int level, int *tiles, int cap)

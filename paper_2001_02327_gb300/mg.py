@@ -73,6 +73,7 @@ _SIGS = {
     "mg_solve_level_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
                                          C.POINTER(mg_options), C.POINTER(mg_level_stats)]),
     "mg_profile_read": (C.c_int, [_vp, C.POINTER(mg_kernel_stat), C.c_int]),
+    "mg_persistent_count": (C.c_int, [_vp]),
     "mg_box_create": (C.c_int, [C.POINTER(mg_box_desc), C.POINTER(mg_options), C.POINTER(_vp)]),
     "mg_box_set_density": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "mg_box_solve": (C.c_int, [_vp, C.POINTER(mg_level_stats)]),
@@ -229,6 +230,11 @@ def mg_time_smoothing(h, b, level, L, launches):
     us, by = C.c_double(), C.c_double()
     _check(h, LIB.mg_time_smoothing(h, b, level, L, launches, C.byref(us), C.byref(by)))
     return us.value, by.value
+
+
+def mg_persistent_count(h):
+    """Hierarchies the solve graph gives to the persistent launch (-1: no graph yet)."""
+    return LIB.mg_persistent_count(h)
 
 
 def mg_destroy(h):

@@ -873,10 +873,10 @@ def test_wave_load_wait_timeout_reports_etimeout(mg, monkeypatch):
 # colour-split FP32 levels (mixed precision)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("make,split,want", [
-    (lambda: I.config_3d_offset_sphere(64, 3), "", 1),           # default: levels of >= 64 cells per edge
-    (lambda: I.config_3d_offset_sphere(128, 2), "", 2),
+    (lambda: I.config_3d_offset_sphere(64, 3), "1", 1),
+    (lambda: I.config_3d_offset_sphere(128, 2), "2", 2),
     (lambda: I.config_3d_offset_sphere(64, 3), "9", None),       # every level above the one-block bottom
-    (lambda: I.config_2d_disk(256, 2), "", 3),
+    (lambda: I.config_2d_disk(256, 2), "", 1),                   # default: levels of >= 192 cells per edge
     (lambda: I.config_2d_disk(64, 2), "9", None)])
 def test_split_levels_match_plain_layout(mg, make, split, want, monkeypatch):
     """FP32 levels stored colour-split and run by the box-patch kernels
