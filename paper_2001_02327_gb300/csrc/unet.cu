@@ -23,6 +23,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -143,6 +144,287 @@ __global__ void __launch_bounds__(128) k_conv3(const TIn *__restrict__ in, int C
             if (ok1)
                 *reinterpret_cast<float2 *>(o + (size_t)r1 * N + c) = make_float2(v[2], v[3]);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5th-generation tensor cores (tcgen05): the same implicit GEMM with the
+// accumulator in tensor memory.  Inline PTX after the PTX ISA's tcgen05
+// section: TMEM allocation by one warp, tcgen05.mma issued by one thread
+// from shared-memory matrix descriptors, completion through tcgen05.commit
+// on an mbarrier, tcgen05.ld for the epilogue.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_alloc(uint32_t slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy stores to shared memory made visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// D[tmem] (+)= A * B^T, kind::f16 (BF16 operands, FP32 accumulate)
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+// arrive once on the mbarrier when every tcgen05.mma this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_init1(uint32_t mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(ok)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// wait for completion `parity` of the mbarrier; false when the clock budget ran out first
+__device__ __forceinline__ bool mbar_wait_for(uint32_t mbar, uint32_t parity, long long budget)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(mbar, parity))
+        if (clock64() - t0 > budget)
+            return false;
+    return true;
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices adjacent along K), stride-dimension byte
+// offset (between 8-row groups along M or N), the fixed 0b001 at bits 46-48.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Operand tiles in shared memory, K-major without swizzle: K in slabs of 16
+// (one MMA each); within a slab, core matrices of 8 rows x 8 BF16 (128
+// contiguous bytes, rows 16 B apart), the two core matrices of a row group
+// 128 B apart (LBO), row groups 256 B apart (SBO).  Byte offset of the
+// 16-byte chunk holding elements k8*8..k8*8+7 of row m in a tile of `rows`
+// rows:
+__device__ __forceinline__ uint32_t tc_chunk(int rows, int m, int k8)
+{
+    return (uint32_t)((k8 >> 1) * rows * 32 + (m >> 3) * 256 + (k8 & 1) * 128 + (m & 7) * 16);
+}
+
+// 16-byte asynchronous copy global -> shared through L1, zero-filled when
+// `valid` is false (a padding voxel); groups committed and waited on per tap
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+constexpr long long kTcBudget = 1ll << 31;   // clock cycles an mbarrier wait may take (about 1 s)
+constexpr int kTcStages = 4;                  // taps in flight
+
+// 3x3x3 convolution on tcgen05: a block of 128 threads computes 128 voxels
+// (thread m gathers voxel m's rows and owns its outputs) x N output channels.
+// Taps run through kTcStages shared-memory stages: the 128 gathered input
+// rows (CK channels, zero rows at the padding) and the tap's N x CK weights
+// arrive by cp.async kTcStages - 2 taps ahead; once a tap's copies have
+// landed, thread 0 issues CK/16 MMAs into the TMEM accumulator and commits
+// them to the stage's mbarrier, which the stage's next fill (two taps later)
+// waits on.
+// Epilogue: each warp reads its 32 TMEM lanes, adds the bias, applies relu,
+// stores.  FLIP and the operand layouts as in k_conv3 (BF16 input).  A wait
+// that outlasts kTcBudget sets *err and stops issuing; the block still waits
+// (bounded) for what it issued and frees its TMEM.
+template <int N, bool FLIP>
+__global__ void __launch_bounds__(128) k_conv3_tc(const bf16 *__restrict__ in, int CK, const bf16 *__restrict__ W,
+                                                  const float *__restrict__ bias, void *__restrict__ out,
+                                                  int out_bf16, int relu, int lg, int V, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[kTcStages];
+    __shared__ uint32_t tslot;
+    constexpr int NCOL = N < 32 ? 32 : N;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, N);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int abytes = 128 * CK * 2, bbytes = N * CK * 2, sbytes = abytes + bbytes;
+    const uint32_t sm0 = smem_u32(smem), mb0 = smem_u32(&mbar[0]);   // stage s: tiles at sm0 + s sbytes, mbarrier mb0 + 8 s
+    if (warp == 0) {
+        tc_alloc(smem_u32(&tslot), NCOL);
+        tc_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < kTcStages; q++)
+            mbar_init1(mb0 + 8 * q);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int n = 1 << lg, msk = n - 1;
+    const int r = blockIdx.x * 128 + tid;
+    const bool ok = r < V;
+    const int x = r & msk, y = (r >> lg) & msk, z = (r >> (2 * lg)) & msk, b = r >> (3 * lg);
+    const int nk8 = CK >> 3;
+    // the copies of one tap into stage s
+    auto fill = [&](int tap, int s) {
+        int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        if (FLIP) {
+            dz = -dz;
+            dy = -dy;
+            dx = -dx;
+        }
+        const int zz = z + dz, yy = y + dy, xx = x + dx;
+        const bool inside = ok && (unsigned)zz < (unsigned)n && (unsigned)yy < (unsigned)n && (unsigned)xx < (unsigned)n;
+        const bf16 *src = inside ? in + (size_t)((((b << lg | zz) << lg | yy) << lg) | xx) * CK : in;
+        const uint32_t As = sm0 + s * sbytes, Bs = As + abytes;
+        for (int k8 = 0; k8 < nk8; k8++)
+            cp16(As + tc_chunk(128, tid, k8), src + k8 * 8, inside);
+        const bf16 *Wt = W + (size_t)tap * N * CK;
+        for (int e = tid; e < N * nk8; e += 128) {
+            const int row = e / nk8, k8 = e - row * nk8;
+            cp16(Bs + tc_chunk(N, row, k8), Wt + (size_t)row * CK + k8 * 8, true);
+        }
+    };
+    for (int t = 0; t < kTcStages - 2; t++) {
+        fill(t, t);
+        cp_commit();
+    }
+    uint32_t phases = 0u;    // bit s: parity of stage s's next completion
+    int issued = 0;          // taps whose MMAs were issued (uniform)
+    bool bad = false;
+    for (int tap = 0; tap < 27; tap++) {
+        const int s = tap % kTcStages;
+        // refill the stage of tap - 2 with tap + kTcStages - 2, once tap - 2's MMAs are done with it
+        // (a tap's MMAs get one tap of slack; the copies of two taps stay in flight)
+        const int tn = tap + kTcStages - 2;
+        if (tn < 27) {
+            const int sn = tn % kTcStages;
+            if (tap >= 2) {
+                const bool done = mbar_wait_for(mb0 + 8 * sn, (phases >> sn) & 1u, kTcBudget);
+                if (__syncthreads_or(!done)) {   // the final wait covers tap - 2 and what followed it
+                    bad = true;
+                    break;
+                }
+                phases ^= 1u << sn;
+            }
+            fill(tn, sn);
+        }
+        cp_commit();                 // (an empty group past the last tap keeps the count)
+        cp_wait<kTcStages - 2>();    // this thread's copies of `tap` have landed
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t a0 = sm0 + s * sbytes, b0 = a0 + abytes;
+            for (int k = 0; k < CK / 16; k++)
+                tc_mma(tmem, tc_sdesc(a0 + k * 128 * 32, 128, 256), tc_sdesc(b0 + k * N * 32, 128, 256), IDESC,
+                       (tap > 0 || k > 0) ? 1u : 0u);
+            tc_commit(mb0 + 8 * s);
+        }
+        issued = tap + 1;
+    }
+    cp_wait<0>();
+    // the last commit covers every MMA issued before it
+    bool done = true;
+    if (issued > 0) {
+        const int s = (issued - 1) % kTcStages;
+        done = mbar_wait_for(mb0 + 8 * s, (phases >> s) & 1u, kTcBudget);
+    }
+    done = !__syncthreads_or(!done);
+    tc_fence_after();
+    if (done && !bad) {
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc_ld16(lane_base + c0, v);
+            if (bias)
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    v[i] += bias[c0 + i];
+            if (relu)
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    v[i] = fmaxf(v[i], 0.f);
+            if (!ok)
+                continue;
+            if (out_bf16) {
+                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(out) + (size_t)r * N + c0);
+                o[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                o[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
+            } else {
+                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + (size_t)r * N + c0);
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc_dealloc(tmem, NCOL);
+    if ((bad || !done) && tid == 0)
+        atomicExch(err, 1);
+}
+
+// FP32 -> BF16 (round to nearest even), 8 values per thread
+__global__ void k_to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, long n8)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n8; e += (long)gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4 *>(src)[2 * e], c = reinterpret_cast<const float4 *>(src)[2 * e + 1];
+        reinterpret_cast<uint4 *>(dst)[e] =
+            make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(c.x, c.y), pack2(c.z, c.w));
     }
 }
 
@@ -410,15 +692,18 @@ __global__ void k_resid_in(const double *__restrict__ rho, const double *__restr
     }
 }
 
-// per sample: scale[2b] = max |Phi| on Omega, scale[2b+1] = max |h^2 r| (one block per sample)
+// per sample b (blockIdx.y): the maxima of |Phi| on Omega and of |h^2 r| over
+// this block's share of the cells, folded into bits[2b], bits[2b+1] by an
+// atomic max on the float bit patterns (non-negative floats order as their
+// bits: the result is the exact maximum, whatever the order)
 __global__ void k_scales(const double *__restrict__ phi, const double *__restrict__ rh2, int n, int blk, int lg,
-                         float *__restrict__ scale)
+                         unsigned *__restrict__ bits)
 {
     __shared__ float red[2][kT / 32];
-    const int b = blockIdx.x;
+    const int b = blockIdx.y;
     const int V = 1 << (3 * lg), m = (1 << lg) - 1, E = n + 4;
     float mx = 0.f, mr = 0.f;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
         const int x = v & m, y = (v >> lg) & m, z = v >> (2 * lg);
         const size_t q = blk ? (size_t)b * E * E * E + ((size_t)(z + 2) * E + y + 2) * E + x + 2 : (size_t)b * V + v;
         mx = fmaxf(mx, fabsf((float)phi[q]));
@@ -439,8 +724,17 @@ __global__ void k_scales(const double *__restrict__ phi, const double *__restric
             s = fmaxf(s, red[0][w]);
             sr = fmaxf(sr, red[1][w]);
         }
-        scale[2 * b] = s > 0.f ? s : 1.f;
-        scale[2 * b + 1] = sr > 0.f ? sr : 1.f;
+        atomicMax(&bits[2 * b], __float_as_uint(s));
+        atomicMax(&bits[2 * b + 1], __float_as_uint(sr));
+    }
+}
+
+// scale[2b] = max |Phi|, scale[2b+1] = max |h^2 r| (1 where the maximum is zero)
+__global__ void k_scales_fin(const unsigned *__restrict__ bits, int B, float *__restrict__ scale)
+{
+    for (int e = threadIdx.x; e < 2 * B; e += blockDim.x) {
+        const float v = __uint_as_float(bits[e]);
+        scale[e] = v > 0.f ? v : 1.f;
     }
 }
 
@@ -523,6 +817,9 @@ struct mg_unet {
          *u0 = nullptr, *d0 = nullptr;
     float *y = nullptr, *tgt = nullptr, *scale = nullptr, *loss = nullptr, *gA = nullptr, *gB = nullptr, *gC = nullptr;
     double *frho = nullptr, *rh2 = nullptr;
+    int *tcerr = nullptr;          // set when a tensor-core completion wait ran out
+    bf16 *gbf = nullptr;           // BF16 copy of a data-gradient pass's input gradient
+    unsigned *scale_bits = nullptr; // per-sample maxima as float bit patterns
     char *mem = nullptr;
     long step = 0;
     cudaStream_t stream = nullptr;
@@ -531,23 +828,64 @@ struct mg_unet {
 
 namespace {
 
+// The convolutions run on tcgen05 (k_conv3_tc); UNET_MMA_SYNC=1 selects the
+// warp-level mma.sync kernel instead (for comparison).
+bool use_mma_sync()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("UNET_MMA_SYNC");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
+constexpr int kTcSmemMax = 200 * 1024;  // kTcStages stages of 128 x CK and N x CK BF16 tiles
+
+template <int N, bool FLIP>
+cudaError_t conv_launch_tc(const bf16 *in, int CK, const bf16 *W, const float *bias, void *out, int out_bf16,
+                           int relu, int lg, int V, int *err, cudaStream_t s)
+{
+    static cudaError_t attr = cudaFuncSetAttribute(k_conv3_tc<N, FLIP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   kTcSmemMax);
+    if (attr)
+        return attr;
+    const size_t smem = (size_t)kTcStages * ((size_t)128 * CK * 2 + (size_t)N * CK * 2);
+    if (smem > (size_t)kTcSmemMax || CK % 16 || CK > 128)
+        return cudaErrorInvalidValue;
+    k_conv3_tc<N, FLIP><<<(V + 127) / 128, 128, smem, s>>>(in, CK, W, bias, out, out_bf16, relu, lg, V, err);
+    return cudaGetLastError();
+}
+
+// tcgen05 path: FP32 input (the data-gradient pass) is rounded to BF16 first
+// (into scratch), as the mma.sync kernel rounds it when it loads it
 template <int NT, bool FLIP, typename TIn>
 cudaError_t conv_launch(const TIn *in, int CK, const bf16 *W, const float *bias, void *out, int out_bf16, int relu,
-                        int lg, int V, cudaStream_t s)
+                        int lg, int V, int *err, bf16 *scratch, cudaStream_t s)
 {
+    if (!use_mma_sync()) {
+        const bf16 *src;
+        if constexpr (sizeof(TIn) == 4) {
+            const long n8 = (long)V * CK / 8;
+            k_to_bf16<<<blocks_for(n8), kT, 0, s>>>(in, scratch, n8);
+            src = scratch;
+        } else {
+            src = in;
+        }
+        return conv_launch_tc<NT * 8, FLIP>(src, CK, W, bias, out, out_bf16, relu, lg, V, err, s);
+    }
     k_conv3<NT, FLIP, TIn><<<(V + 63) / 64, 128, 0, s>>>(in, CK, W, bias, out, out_bf16, relu, lg, V);
     return cudaGetLastError();
 }
 
 template <bool FLIP, typename TIn>
 cudaError_t conv_any(const TIn *in, int CK, const bf16 *W, const float *bias, int N, void *out, int out_bf16, int relu,
-                     int lg, int V, cudaStream_t s)
+                     int lg, int V, int *err, bf16 *scratch, cudaStream_t s)
 {
     switch (N) {
-    case 16: return conv_launch<2, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
-    case 32: return conv_launch<4, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
-    case 64: return conv_launch<8, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
-    case 128: return conv_launch<16, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, s);
+    case 16: return conv_launch<2, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, err, scratch, s);
+    case 32: return conv_launch<4, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, err, scratch, s);
+    case 64: return conv_launch<8, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, err, scratch, s);
+    case 128: return conv_launch<16, FLIP, TIn>(in, CK, W, bias, out, out_bf16, relu, lg, V, err, scratch, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -580,7 +918,8 @@ cudaError_t forward(mg_unet *u, int B, int lg)
     auto C = [&](int i) -> const Conv & { return u->conv[i]; };
     float *P = u->p;
 #define FWD(i, in, out, lgv, V)                                                                                   \
-    if ((e = conv_any<false, bf16>(in, C(i).ckin, u->wf[i], P + C(i).boff, C(i).cout, out, 1, 1, lgv, V, s))) \
+    if ((e = conv_any<false, bf16>(in, C(i).ckin, u->wf[i], P + C(i).boff, C(i).cout, out, 1, 1, lgv, V, u->tcerr, \
+                                   nullptr, s)))                                                                \
         return e;
     FWD(0, u->x0, u->a0, lg, V0);
     FWD(1, u->a0, u->s0, lg, V0);
@@ -615,7 +954,8 @@ cudaError_t wgrad(mg_unet *u, int i, const bf16 *in, const float *g, int lg, int
 cudaError_t dgrad(mg_unet *u, int i, const float *g, float *out, int lg, int V)
 {
     const Conv &c = u->conv[i];
-    return conv_any<true, float>(g, c.cout, u->wd[i], nullptr, c.ckin, out, 0, 0, lg, V, u->stream);
+    return conv_any<true, float>(g, c.cout, u->wd[i], nullptr, c.ckin, out, 0, 0, lg, V, u->tcerr, u->gbf,
+                                 u->stream);
 }
 
 cudaError_t mask(mg_unet *u, float *g, const bf16 *act, long n)
@@ -686,6 +1026,21 @@ float hash_uniform(unsigned long long seed, unsigned long long i)
 
 }  // namespace
 
+namespace {
+
+// 4 once a tensor-core completion wait of a convolution ran out (the flag
+// stays set), else 0; synchronises the stream
+int tc_status(mg_unet *u)
+{
+    int f = 0;
+    if (cudaMemcpyAsync(&f, u->tcerr, sizeof(int), cudaMemcpyDeviceToHost, u->stream) ||
+        cudaStreamSynchronize(u->stream))
+        return 3;
+    return f ? 4 : 0;
+}
+
+}  // namespace
+
 extern "C" {
 
 long mg_unet_param_count(void)
@@ -751,8 +1106,11 @@ int mg_unet_create(int nmax, int bmax, unsigned long long seed, void *stream, mg
     A((void **)&u->y, V0 * sizeof(float));
     A((void **)&u->tgt, V0 * sizeof(float));
     A((void **)&u->scale, 2048 * sizeof(float));
+    A((void **)&u->scale_bits, 2048 * sizeof(unsigned));
     A((void **)&u->rh2, V0 * sizeof(double));
     A((void **)&u->loss, 256);
+    A((void **)&u->tcerr, 256);
+    A((void **)&u->gbf, V0 * 32 * sizeof(bf16));
     A((void **)&u->frho, bmax * sizeof(double));
     A((void **)&u->gA, V0 * 32 * sizeof(float));
     A((void **)&u->gB, V0 * 32 * sizeof(float));
@@ -863,7 +1221,10 @@ int mg_unet_predict_dev(mg_unet *u, int B, int n, int blk, const double *rho, do
         return 3;
     }
     k_resid_in<<<blocks_for(V0), kT, 0, s>>>(rho, phi, resid, n, blk, lg, B, frho_dev, u->rh2);
-    k_scales<<<B, kT, 0, s>>>(phi, u->rh2, n, blk, lg, u->scale);
+    cudaMemsetAsync(u->scale_bits, 0, 2 * B * sizeof(unsigned), s);
+    k_scales<<<dim3(std::min(64, std::max(1, V0 / B / (kT * 16))), B), kT, 0, s>>>(phi, u->rh2, n, blk, lg,
+                                                                                  u->scale_bits);
+    k_scales_fin<<<1, 256, 0, s>>>(u->scale_bits, B, u->scale);
     k_make_input<<<blocks_for(V0), kT, 0, s>>>(rho, phi, u->rh2, n, blk, lg, B, frho_dev, u->scale, u->x0);
     cudaError_t e = forward(u, B, lg);
     if (!e && apply) {
@@ -888,7 +1249,7 @@ int mg_unet_forward(mg_unet *u, int B, int n, const double *rho, const double *p
     if (y_out && (cudaMemcpyAsync(y_out, u->y, V0 * sizeof(float), cudaMemcpyDeviceToHost, u->stream) ||
                   cudaStreamSynchronize(u->stream)))
         return 3;
-    return 0;
+    return tc_status(u);
 }
 
 int mg_unet_train_step(mg_unet *u, int B, int n, const double *rho, const double *phi_interp,
@@ -922,7 +1283,9 @@ int mg_unet_train_step(mg_unet *u, int B, int n, const double *rho, const double
         return 3;
     if (loss_out)
         *loss_out = l;
-    return cudaGetLastError() ? 3 : 0;
+    if (cudaGetLastError())
+        return 3;
+    return tc_status(u);
 }
 
 }  // extern "C"
