@@ -9,8 +9,9 @@ then the 1x1 output's 16 weights and bias.  Gradients come from autograd.
 emulate=True rounds to BF16 where the CUDA module stores BF16: the network
 inputs, the convolution weights, every convolution's output (after bias and
 ReLU) and every pooled mean; and, in the backward pass, the gradient that
-enters each convolution's data-gradient product (its weight gradient uses
-the unrounded gradient).  Everything else stays float64.  With data whose
+enters each convolution's data-gradient and weight-gradient products (the
+tensor-core products of the module take BF16 operands; its bias gradient
+sums the unrounded gradient).  Everything else stays float64.  With data whose
 every sum is exact in FP32 (dyadic values of few bits) the forward pass then
 equals the CUDA module's bit for bit.
 """
@@ -65,7 +66,8 @@ class _RoundST(torch.autograd.Function):
 class _ConvBF16(torch.autograd.Function):
     """3x3x3 convolution (padding 1) + bias as the module computes it: the
     data gradient multiplies the BF16-rounded output gradient by the BF16
-    weights; the weight and bias gradients use the unrounded gradient."""
+    weights, the weight gradient the BF16 input by the BF16-rounded output
+    gradient; the bias gradient sums the unrounded gradient."""
 
     @staticmethod
     def forward(ctx, x, w, b):
@@ -76,7 +78,7 @@ class _ConvBF16(torch.autograd.Function):
     def backward(ctx, g):
         x, w = ctx.saved_tensors
         gx = torch.nn.grad.conv3d_input(x.shape, w, bf16(g), padding=1)
-        gw = torch.nn.grad.conv3d_weight(x, w.shape, g, padding=1)
+        gw = torch.nn.grad.conv3d_weight(x, w.shape, bf16(g), padding=1)
         return gx, gw, g.sum(dim=(0, 2, 3, 4))
 
 
@@ -163,7 +165,7 @@ class _ConvBF16Abs(_ConvBF16):
     def backward(ctx, g):
         x, w = ctx.saved_tensors
         gx = torch.nn.grad.conv3d_input(x.shape, w, bf16(g), padding=1)
-        gw = torch.nn.grad.conv3d_weight(x.abs(), w.shape, g.abs(), padding=1)
+        gw = torch.nn.grad.conv3d_weight(x.abs(), w.shape, bf16(g).abs(), padding=1)
         return gx, gw, g.abs().sum(dim=(0, 2, 3, 4))
 
 

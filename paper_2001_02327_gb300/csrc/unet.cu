@@ -418,6 +418,160 @@ __global__ void __launch_bounds__(128) k_conv3_tc(const bf16 *__restrict__ in, i
         atomicExch(err, 1);
 }
 
+// Weight gradients of a 3x3x3 convolution on tcgen05 (bias gradient apart):
+//   dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * bf16(d[v][co])
+// as D = A B^T with the voxels as K: a block takes TG = 128 / CK taps (rows
+// m = tap_local * CK + ci; rows of taps past 26 stay zero) and a run of
+// `vchunk` voxels, gathers 64 voxels per stage -- A[m][k] from the voxels'
+// shifted input rows, B[co][k] from their output gradients rounded to BF16,
+// both transposed into the K-major tiles of k_conv3_tc -- issues 4 MMAs per
+// stage into its TMEM accumulator (two stages, a stage refilled once its
+// MMAs of two stages back have completed), and adds its 128 x N partial sums
+// into dW (FP32 atomics, real channels only).  Waits bounded as in
+// k_conv3_tc.
+template <int CK, int N>
+__global__ void __launch_bounds__(128) k_wgrad_tc(const bf16 *__restrict__ in, int Cin, const float *__restrict__ d,
+                                                  float *__restrict__ dW, int lg, int V, int vchunk,
+                                                  int *__restrict__ err)
+{
+    constexpr int TG = 128 / CK, KB = 64, NS = 2;
+    constexpr int NCOL = N < 32 ? 32 : N;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, N);
+    constexpr int ABYTES = 128 * KB * 2, BBYTES = N * KB * 2, SBYTES = ABYTES + BBYTES;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[NS];
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sm0 = smem_u32(smem), mb0 = smem_u32(&mbar[0]);
+    if (warp == 0) {
+        tc_alloc(smem_u32(&tslot), NCOL);
+        tc_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < NS; q++)
+            mbar_init1(mb0 + 8 * q);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int n = 1 << lg, msk = n - 1;
+    const int tap0 = blockIdx.y * TG;
+    const int v0 = blockIdx.x * vchunk, v1 = min(v0 + vchunk, V);
+    const int nst = (v1 - v0 + KB - 1) / KB;
+    // rows of the tap `tap` shifted from voxel v, or NULL (padding, past the run, or no such tap)
+    auto row_of = [&](int v, int tap) -> const bf16 * {
+        if (v >= v1 || tap >= 27)
+            return nullptr;
+        const int x = v & msk, y = (v >> lg) & msk, z = (v >> (2 * lg)) & msk, b = v >> (3 * lg);
+        const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+        if ((unsigned)zz >= (unsigned)n || (unsigned)yy >= (unsigned)n || (unsigned)xx >= (unsigned)n)
+            return nullptr;
+        return in + (size_t)((((b << lg | zz) << lg | yy) << lg) | xx) * CK;
+    };
+    auto fill = [&](int j, int s) {
+        unsigned char *As = smem + s * SBYTES, *Bs = As + ABYTES;
+        const int vb = v0 + j * KB;
+        // A: (voxel pair p, tap_local) items; a pair of voxels k = 2p, 2p + 1 makes one 32-bit word per row
+        for (int it = tid; it < (KB / 2) * TG; it += 128) {
+            const int p = it % (KB / 2), tl = it / (KB / 2), k = 2 * p;
+            const bf16 *ra = row_of(vb + k, tap0 + tl), *rb = row_of(vb + k + 1, tap0 + tl);
+#pragma unroll 2
+            for (int k8 = 0; k8 < CK / 8; k8++) {
+                const uint4 qa = ra ? *reinterpret_cast<const uint4 *>(ra + 8 * k8) : make_uint4(0u, 0u, 0u, 0u);
+                const uint4 qb = rb ? *reinterpret_cast<const uint4 *>(rb + 8 * k8) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t wa[4] = {qa.x, qa.y, qa.z, qa.w}, wb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const uint32_t lo = (wa[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                    const uint32_t hi = (wb[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                    const int m = tl * CK + 8 * k8 + e;
+                    *reinterpret_cast<uint32_t *>(As + tc_chunk(128, m, k >> 3) + (k & 7) * 2) = lo | (hi << 16);
+                }
+            }
+        }
+        // B: (voxel pair p, 4 output channels) items from the FP32 gradient rows
+        for (int it = tid; it < (KB / 2) * (N / 4); it += 128) {
+            const int p = it % (KB / 2), c4 = it / (KB / 2), k = 2 * p;
+            const int va = vb + k, vbb = vb + k + 1;
+            const float4 ga = va < v1 ? *reinterpret_cast<const float4 *>(d + (size_t)va * N + 4 * c4)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 gb = vbb < v1 ? *reinterpret_cast<const float4 *>(d + (size_t)vbb * N + 4 * c4)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float fa[4] = {ga.x, ga.y, ga.z, ga.w}, fb[4] = {gb.x, gb.y, gb.z, gb.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                *reinterpret_cast<uint32_t *>(Bs + tc_chunk(N, 4 * c4 + e, k >> 3) + (k & 7) * 2) = pack2(fa[e], fb[e]);
+        }
+    };
+    uint32_t phases = 0u;
+    int issued = 0;
+    bool bad = false;
+    for (int j = 0; j < nst; j++) {
+        const int s = j % NS;
+        if (j >= NS) {       // the stage's MMAs of stage j - 2 have finished reading it
+            const bool done = mbar_wait_for(mb0 + 8 * s, (phases >> s) & 1u, kTcBudget);
+            if (__syncthreads_or(!done)) {
+                bad = true;
+                break;
+            }
+            phases ^= 1u << s;
+        }
+        fill(j, s);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t a0 = sm0 + s * SBYTES, b0 = a0 + ABYTES;
+            for (int k = 0; k < KB / 16; k++)
+                tc_mma(tmem, tc_sdesc(a0 + k * 128 * 32, 128, 256), tc_sdesc(b0 + k * N * 32, 128, 256), IDESC,
+                       (j > 0 || k > 0) ? 1u : 0u);
+            tc_commit(mb0 + 8 * s);
+        }
+        issued = j + 1;
+    }
+    bool done = true;
+    if (issued > 0) {
+        const int s = (issued - 1) % NS;
+        done = mbar_wait_for(mb0 + 8 * s, (phases >> s) & 1u, kTcBudget);
+    }
+    done = !__syncthreads_or(!done);
+    tc_fence_after();
+    if (done && !bad && issued > 0) {
+        const int tl = tid / CK, ci = tid - tl * CK, tap = tap0 + tl;
+        const bool mine = tap < 27 && ci < Cin;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc_ld16(lane_base + c0, v);
+            if (mine)
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    atomicAdd(&dW[((size_t)tap * Cin + ci) * N + c0 + i], v[i]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc_dealloc(tmem, NCOL);
+    if ((bad || !done) && tid == 0)
+        atomicExch(err, 1);
+}
+
+// db[co] += sum_v d[v][co]: per block a run of voxels, one atomic per channel
+__global__ void k_bias_grad(const float *__restrict__ d, int N, int V, int vchunk, float *__restrict__ db)
+{
+    const int v0 = blockIdx.x * vchunk, v1 = min(v0 + vchunk, V);
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        float s = 0.f;
+        for (int v = v0; v < v1; v++)
+            s += d[(size_t)v * N + c];
+        atomicAdd(&db[c], s);
+    }
+}
+
 // FP32 -> BF16 (round to nearest even), 8 values per thread
 __global__ void k_to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, long n8)
 {
@@ -941,13 +1095,47 @@ cudaError_t forward(mg_unet *u, int B, int lg)
     return cudaGetLastError();
 }
 
+template <int CK, int N>
+cudaError_t wgrad_tc(const bf16 *in, int Cin, const float *g, float *dW, int lg, int V, int *err, cudaStream_t s)
+{
+    constexpr size_t smem = 2 * ((size_t)128 * 64 * 2 + (size_t)N * 64 * 2);
+    static cudaError_t attr = cudaFuncSetAttribute(k_wgrad_tc<CK, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+    if (attr)
+        return attr;
+    const int vchunk = 4096;
+    dim3 grid((V + vchunk - 1) / vchunk, (27 + 128 / CK - 1) / (128 / CK));
+    k_wgrad_tc<CK, N><<<grid, 128, smem, s>>>(in, Cin, g, dW, lg, V, vchunk, err);
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_tc_any(int CK, int N, const bf16 *in, int Cin, const float *g, float *dW, int lg, int V, int *err,
+                         cudaStream_t s)
+{
+#define WG(ck, nn)                   \
+    if (CK == ck && N == nn)         \
+        return wgrad_tc<ck, nn>(in, Cin, g, dW, lg, V, err, s);
+    WG(16, 16) WG(16, 32) WG(32, 32) WG(32, 64) WG(64, 64) WG(128, 32) WG(64, 16) WG(32, 16)
+#undef WG
+    return cudaErrorInvalidValue;
+}
+
 // weight gradients of conv i from its input activation and output gradient g (FP32, N channels)
 cudaError_t wgrad(mg_unet *u, int i, const bf16 *in, const float *g, int lg, int V)
 {
     const Conv &c = u->conv[i];
-    const int vpb = 4096;
-    dim3 grid((V + vpb - 1) / vpb, 27);
-    k_wgrad<<<grid, kT, 0, u->stream>>>(in, c.ckin, c.cin, g, c.cout, u->grad + c.woff, u->grad + c.boff, lg, V, vpb);
+    if (use_mma_sync()) {
+        const int vpb = 4096;
+        dim3 grid((V + vpb - 1) / vpb, 27);
+        k_wgrad<<<grid, kT, 0, u->stream>>>(in, c.ckin, c.cin, g, c.cout, u->grad + c.woff, u->grad + c.boff, lg, V,
+                                            vpb);
+        return cudaGetLastError();
+    }
+    cudaError_t e = wgrad_tc_any(c.ckin, c.cout, in, c.cin, g, u->grad + c.woff, lg, V, u->tcerr, u->stream);
+    if (e)
+        return e;
+    const int vchunk = 1024;
+    k_bias_grad<<<(V + vchunk - 1) / vchunk, 64, 0, u->stream>>>(g, c.cout, V, vchunk, u->grad + c.boff);
     return cudaGetLastError();
 }
 
