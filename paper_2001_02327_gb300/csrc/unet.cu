@@ -18,6 +18,8 @@
 // (the inverse 7-point Laplacian amplifies smooth residuals by ~n^2: the
 // factor keeps y of order one across level sizes).
 // c3: 3x3x3 convolution, zero padding, bias; pool: 2x2x2 mean; up: nearest.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -560,16 +562,168 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(const bf16 *__restrict__ in, i
         atomicExch(err, 1);
 }
 
-// db[co] += sum_v d[v][co]: per block a run of voxels, one atomic per channel
-__global__ void k_bias_grad(const float *__restrict__ d, int N, int V, int vchunk, float *__restrict__ db)
+// db[co] += sum_v d[v][co]: a block of 256 threads takes a run of voxels,
+// thread t the channel t % N of voxels v0 + t / N, v0 + t / N + 256 / N, ...
+// (coalesced rows), then sums per channel in shared memory and adds once
+__global__ void __launch_bounds__(256) k_bias_grad(const float *__restrict__ d, int N, int V, int vchunk,
+                                                   float *__restrict__ db)
 {
+    __shared__ float part[256];
     const int v0 = blockIdx.x * vchunk, v1 = min(v0 + vchunk, V);
-    for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        float s = 0.f;
-        for (int v = v0; v < v1; v++)
-            s += d[(size_t)v * N + c];
-        atomicAdd(&db[c], s);
+    const int c = threadIdx.x % N, step = 256 / N;
+    float s = 0.f;
+    for (int v = v0 + threadIdx.x / N; v < v1; v += step)
+        s += d[(size_t)v * N + c];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < N) {
+        float t = 0.f;
+        for (int q = threadIdx.x; q < 256; q += N)
+            t += part[q];
+        atomicAdd(&db[threadIdx.x], t);
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution from a TMA-loaded halo: a tile of 8 (x) x 16 (y) x 1
+// (z) voxels of one sample; one TMA box per 8 input channels brings the
+// 10 x 18 x 3 voxels around it (zero outside the grid) into shared memory as
+// 16-byte rows, x fastest.  Tap (dz, dy, dx) is then the 128 x CK operand
+// whose row (x, y) is halo row ((dz+1) 18 + y + dy + 1) 10 + x + dx + 1: a
+// descriptor at that start with 8-row groups one halo row (160 B) apart
+// (SBO) and the channel chunks kHaloChunk apart (LBO) -- no copy per tap.
+// All 27 taps' weights (N x CK each) come in by TMA too, N rows of 16 B per
+// chunk.  One thread issues every copy and MMA; the block waits once for
+// the accumulator.
+// ---------------------------------------------------------------------------
+constexpr int kHaloRows = 10 * 18 * 3;                 // 540 rows of one channel chunk
+constexpr int kHaloChunk = (kHaloRows * 16 + 127) / 128 * 128;   // 8704 B, 128-byte aligned chunks
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                          uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                 "%3, %4, %5, %6}], [%7];" ::"r"(dst),
+                 "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load2(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                 "%3}], [%4];" ::"r"(dst),
+                 "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(mbar)
+                 : "memory");
+}
+
+template <int N, bool FLIP>
+__global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUtensorMap tm_in,
+                                                    const __grid_constant__ CUtensorMap tm_w, int CK,
+                                                    const float *__restrict__ bias, void *__restrict__ out,
+                                                    int out_bf16, int relu, int lg, int B, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];   // 0: halo and weights arrived; 1: accumulator complete
+    __shared__ uint32_t tslot;
+    constexpr int NCOL = N < 32 ? 32 : N;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, N);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nk8 = CK >> 3;
+    const uint32_t halo = smem_u32(smem), wts = halo + nk8 * kHaloChunk;
+    const uint32_t mb_in = smem_u32(&mbar[0]), mb_acc = smem_u32(&mbar[1]);
+    const int n = 1 << lg;
+    const int tx = n >> 3, ty = (n + 15) >> 4;          // tiles per row and per column of a plane
+    int t = blockIdx.x;
+    const int x0 = (t % tx) * 8;
+    t /= tx;
+    const int y0 = (t % ty) * 16;
+    t /= ty;
+    const int z0 = t % n, b = t / n;
+    if (warp == 0) {
+        tc_alloc(smem_u32(&tslot), NCOL);
+        tc_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init1(mb_in);
+        mbar_init1(mb_acc);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    if (tid == 0) {
+        mbar_expect_tx(mb_in, (uint32_t)(nk8 * kHaloRows * 16 + 27 * nk8 * N * 16));
+        for (int k8 = 0; k8 < nk8; k8++)
+            tma_load5(halo + k8 * kHaloChunk, &tm_in, 8 * k8, x0 - 1, y0 - 1, z0 - 1, b, mb_in);
+        for (int tap = 0; tap < 27; tap++)
+            for (int k8 = 0; k8 < nk8; k8++)
+                tma_load2(wts + (tap * nk8 + k8) * N * 16, &tm_w, 8 * k8, tap * N, mb_in);
+        ok = mbar_wait_for(mb_in, 0, kTcBudget);
+        if (!ok)
+            mbar_wait_for(mb_in, 0, kTcBudget);   // the copies still in flight land before the block leaves
+        if (ok) {
+            tc_fence_after();
+            for (int tap = 0; tap < 27; tap++) {
+                int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                if (FLIP) {
+                    dz = -dz;
+                    dy = -dy;
+                    dx = -dx;
+                }
+                const uint32_t a0 = halo + (uint32_t)((((dz + 1) * 18 + dy + 1) * 10 + dx + 1) * 16);
+                for (int k = 0; k < CK / 16; k++)
+                    tc_mma(tmem, tc_sdesc(a0 + 2 * k * kHaloChunk, kHaloChunk, 160),
+                           tc_sdesc(wts + (tap * nk8 + 2 * k) * N * 16, N * 16, 128), IDESC,
+                           (tap > 0 || k > 0) ? 1u : 0u);
+            }
+            tc_commit(mb_acc);
+        }
+    }
+    ok = !__syncthreads_or(!ok);
+    bool done = ok && mbar_wait_for(mb_acc, 0, kTcBudget);
+    done = !__syncthreads_or(!done);
+    tc_fence_after();
+    if (done) {
+        const int x = x0 + (tid & 7), y = y0 + (tid >> 3);
+        const bool mine = y < n;
+        const size_t r = ((((size_t)b * n + z0) * n + y) * n + x);
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc_ld16(lane_base + c0, v);
+            if (bias)
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    v[i] += bias[c0 + i];
+            if (relu)
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    v[i] = fmaxf(v[i], 0.f);
+            if (!mine)
+                continue;
+            if (out_bf16) {
+                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(out) + r * N + c0);
+                o[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                o[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
+            } else {
+                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + r * N + c0);
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc_dealloc(tmem, NCOL);
+    if (!done && tid == 0)
+        atomicExch(err, 1);
 }
 
 // FP32 -> BF16 (round to nearest even), 8 values per thread
@@ -1010,6 +1164,70 @@ cudaError_t conv_launch_tc(const bf16 *in, int CK, const bf16 *W, const float *b
     return cudaGetLastError();
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
+
+// the halo kernel applies when all 27 taps' weights fit beside the halo and
+// the grid has at least 8 cells per edge
+bool halo_applies(int CK, int N, int lg) { return 27 * N * CK * 2 <= 64 * 1024 && lg >= 3 && CK <= 64; }
+
+template <int N, bool FLIP>
+cudaError_t conv_launch_halo(const bf16 *in, int CK, const bf16 *W, const float *bias, void *out, int out_bf16,
+                             int relu, int lg, int V, int *err, cudaStream_t s)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc)
+        return cudaErrorNotSupported;
+    const int n = 1 << lg, B = V >> (3 * lg);
+    CUtensorMap mi{}, mw{};
+    const cuuint64_t di[5] = {(cuuint64_t)CK, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B};
+    const cuuint64_t si[4] = {(cuuint64_t)CK * 2, (cuuint64_t)n * CK * 2, (cuuint64_t)n * n * CK * 2,
+                              (cuuint64_t)n * n * n * CK * 2};
+    const cuuint32_t bi[5] = {8, 10, 18, 3, 1}, e5[5] = {1, 1, 1, 1, 1};
+    if (enc(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(in), di, si, bi, e5,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const cuuint64_t dw[2] = {(cuuint64_t)CK, (cuuint64_t)27 * N};
+    const cuuint64_t sw[1] = {(cuuint64_t)CK * 2};
+    const cuuint32_t bw[2] = {8, (cuuint32_t)N}, e2[2] = {1, 1};
+    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(W), dw, sw, bw, e2,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(CK / 8) * kHaloChunk + (size_t)27 * (CK / 8) * N * 16;
+    static cudaError_t attr = cudaFuncSetAttribute(k_conv3_halo<N, FLIP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   200 * 1024);
+    if (attr)
+        return attr;
+    const int tiles = B * n * ((n + 15) / 16) * (n / 8);
+    k_conv3_halo<N, FLIP><<<tiles, 128, smem, s>>>(mi, mw, CK, bias, out, out_bf16, relu, lg, B, err);
+    return cudaGetLastError();
+}
+
+// the halo kernel unless UNET_HALO=0
+bool use_halo()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("UNET_HALO");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // tcgen05 path: FP32 input (the data-gradient pass) is rounded to BF16 first
 // (into scratch), as the mma.sync kernel rounds it when it loads it
 template <int NT, bool FLIP, typename TIn>
@@ -1025,6 +1243,8 @@ cudaError_t conv_launch(const TIn *in, int CK, const bf16 *W, const float *bias,
         } else {
             src = in;
         }
+        if (use_halo() && halo_applies(CK, NT * 8, lg))
+            return conv_launch_halo<NT * 8, FLIP>(src, CK, W, bias, out, out_bf16, relu, lg, V, err, s);
         return conv_launch_tc<NT * 8, FLIP>(src, CK, W, bias, out, out_bf16, relu, lg, V, err, s);
     }
     k_conv3<NT, FLIP, TIn><<<(V + 63) / 64, 128, 0, s>>>(in, CK, W, bias, out, out_bf16, relu, lg, V);
@@ -1134,8 +1354,8 @@ cudaError_t wgrad(mg_unet *u, int i, const bf16 *in, const float *g, int lg, int
     cudaError_t e = wgrad_tc_any(c.ckin, c.cout, in, c.cin, g, u->grad + c.woff, lg, V, u->tcerr, u->stream);
     if (e)
         return e;
-    const int vchunk = 1024;
-    k_bias_grad<<<(V + vchunk - 1) / vchunk, 64, 0, u->stream>>>(g, c.cout, V, vchunk, u->grad + c.boff);
+    const int vchunk = 4096;
+    k_bias_grad<<<(V + vchunk - 1) / vchunk, 256, 0, u->stream>>>(g, c.cout, V, vchunk, u->grad + c.boff);
     return cudaGetLastError();
 }
 
