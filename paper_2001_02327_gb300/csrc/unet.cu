@@ -592,9 +592,9 @@ __global__ void __launch_bounds__(256) k_bias_grad(const float *__restrict__ d, 
 // whose row (x, y) is halo row ((dz+1) 18 + y + dy + 1) 10 + x + dx + 1: a
 // descriptor at that start with 8-row groups one halo row (160 B) apart
 // (SBO) and the channel chunks kHaloChunk apart (LBO) -- no copy per tap.
-// All 27 taps' weights (N x CK each) come in by TMA too, N rows of 16 B per
-// chunk.  One thread issues every copy and MMA; the block waits once for
-// the accumulator.
+// All 27 taps' weights (N x CK each) come in by cp.async from every thread,
+// N rows of 16 B per chunk.  One thread issues the TMA and every MMA; the
+// block waits once for the accumulator.
 // ---------------------------------------------------------------------------
 constexpr int kHaloRows = 10 * 18 * 3;                 // 540 rows of one channel chunk
 constexpr int kHaloChunk = (kHaloRows * 16 + 127) / 128 * 128;   // 8704 B, 128-byte aligned chunks
@@ -611,17 +611,10 @@ __device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap *map, 
                  "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
                  : "memory");
 }
-__device__ __forceinline__ void tma_load2(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t mbar)
-{
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-                 "%3}], [%4];" ::"r"(dst),
-                 "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(mbar)
-                 : "memory");
-}
-
 template <int N, bool FLIP>
 __global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUtensorMap tm_in,
-                                                    const __grid_constant__ CUtensorMap tm_w, int CK,
+                                                    const bf16 *__restrict__ in, int halo_by_tma,
+                                                    const bf16 *__restrict__ W, int CK,
                                                     const float *__restrict__ bias, void *__restrict__ out,
                                                     int out_bf16, int relu, int lg, int B, int *__restrict__ err)
 {
@@ -656,16 +649,41 @@ __global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUte
     tc_fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
-    if (tid == 0) {
-        mbar_expect_tx(mb_in, (uint32_t)(nk8 * kHaloRows * 16 + 27 * nk8 * N * 16));
-        for (int k8 = 0; k8 < nk8; k8++)
-            tma_load5(halo + k8 * kHaloChunk, &tm_in, 8 * k8, x0 - 1, y0 - 1, z0 - 1, b, mb_in);
-        for (int tap = 0; tap < 27; tap++)
+    if (halo_by_tma) {
+        if (tid == 0) {
+            mbar_expect_tx(mb_in, (uint32_t)(nk8 * kHaloRows * 16));
             for (int k8 = 0; k8 < nk8; k8++)
-                tma_load2(wts + (tap * nk8 + k8) * N * 16, &tm_w, 8 * k8, tap * N, mb_in);
-        ok = mbar_wait_for(mb_in, 0, kTcBudget);
-        if (!ok)
-            mbar_wait_for(mb_in, 0, kTcBudget);   // the copies still in flight land before the block leaves
+                tma_load5(halo + k8 * kHaloChunk, &tm_in, 8 * k8, x0 - 1, y0 - 1, z0 - 1, b, mb_in);
+        }
+    } else {
+        // the halo rows by every thread, zero outside the grid
+        for (int e = tid; e < nk8 * kHaloRows; e += 128) {
+            const int k8 = e / kHaloRows, row = e - k8 * kHaloRows;
+            const int hx = row % 10, hy = (row / 10) % 18, hz = row / 180;
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+            const bool inside = (unsigned)gx < (unsigned)n && (unsigned)gy < (unsigned)n && (unsigned)gz < (unsigned)n;
+            const bf16 *src = inside ? in + ((((size_t)b * n + gz) * n + gy) * n + gx) * CK + 8 * k8 : in;
+            cp16(halo + k8 * kHaloChunk + row * 16, src, inside);
+        }
+    }
+    // the weights by every thread (16-byte copies), N rows of 16 B per (tap, chunk)
+    for (int e = tid; e < 27 * N * nk8; e += 128) {
+        const int k8 = e % nk8, row = e / nk8;   // row = tap * N + output channel
+        const int tap = row / N, nn = row - tap * N;
+        cp16(wts + ((tap * nk8 + k8) * N + nn) * 16, W + (size_t)row * CK + 8 * k8, true);
+    }
+    cp_commit();
+    cp_wait<0>();
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+        if (halo_by_tma) {
+            ok = mbar_wait_for(mb_in, 0, kTcBudget);
+            if (!ok)
+                mbar_wait_for(mb_in, 0, kTcBudget);   // the copies still in flight land before the block leaves
+        }
         if (ok) {
             tc_fence_after();
             for (int tap = 0; tap < 27; tap++) {
@@ -1192,19 +1210,12 @@ cudaError_t conv_launch_halo(const bf16 *in, int CK, const bf16 *W, const float 
     if (!enc)
         return cudaErrorNotSupported;
     const int n = 1 << lg, B = V >> (3 * lg);
-    CUtensorMap mi{}, mw{};
+    CUtensorMap mi{};
     const cuuint64_t di[5] = {(cuuint64_t)CK, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B};
     const cuuint64_t si[4] = {(cuuint64_t)CK * 2, (cuuint64_t)n * CK * 2, (cuuint64_t)n * n * CK * 2,
                               (cuuint64_t)n * n * n * CK * 2};
     const cuuint32_t bi[5] = {8, 10, 18, 3, 1}, e5[5] = {1, 1, 1, 1, 1};
     if (enc(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(in), di, si, bi, e5,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
-    const cuuint64_t dw[2] = {(cuuint64_t)CK, (cuuint64_t)27 * N};
-    const cuuint64_t sw[1] = {(cuuint64_t)CK * 2};
-    const cuuint32_t bw[2] = {8, (cuuint32_t)N}, e2[2] = {1, 1};
-    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(W), dw, sw, bw, e2,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
@@ -1214,7 +1225,12 @@ cudaError_t conv_launch_halo(const bf16 *in, int CK, const bf16 *W, const float 
     if (attr)
         return attr;
     const int tiles = B * n * ((n + 15) / 16) * (n / 8);
-    k_conv3_halo<N, FLIP><<<tiles, 128, smem, s>>>(mi, mw, CK, bias, out, out_bf16, relu, lg, B, err);
+    static const bool by_tma = [] {   // the halo by one TMA box per chunk; UNET_HALO_TMA=0: cp.async rows
+        const char *v = std::getenv("UNET_HALO_TMA");
+        return !(v && v[0] == '0');
+    }();
+    k_conv3_halo<N, FLIP><<<tiles, 128, smem, s>>>(mi, in, by_tma ? 1 : 0, W, CK, bias, out, out_bf16, relu, lg, B,
+                                                   err);
     return cudaGetLastError();
 }
 
