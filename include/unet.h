@@ -20,8 +20,10 @@
  * phi_interp + (s_r n^2 / 16) y (the inverse Laplacian amplifies smooth
  * residuals by about n^2; the factor keeps y of order one for every n).
  * All array pointers are device pointers unless stated.  Return values: 0 ok,
- * 1 bad argument, 2 out of memory, 3 CUDA error.
- */
+ * 1 bad argument, 2 out of memory, 3 CUDA error, 4 a convolution's bounded
+ * wait for its tensor-core work ran out (mg_unet_forward, mg_unet_train_step;
+ * results invalid, the network keeps answering 4).  The convolutions run on
+ * the 5th-generation tensor cores (tcgen05, accumulators in tensor memory). */
 #ifndef MG_UNET_H
 #define MG_UNET_H
 

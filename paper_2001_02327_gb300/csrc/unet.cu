@@ -616,7 +616,8 @@ __global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUte
                                                     const bf16 *__restrict__ in, int halo_by_tma,
                                                     const bf16 *__restrict__ W, int CK,
                                                     const float *__restrict__ bias, void *__restrict__ out,
-                                                    int out_bf16, int relu, int lg, int B, int *__restrict__ err)
+                                                    int out_bf16, int relu, int lg, int B, int fault,
+                                                    int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[2];   // 0: halo and weights arrived; 1: accumulator complete
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUte
             if (!ok)
                 mbar_wait_for(mb_in, 0, kTcBudget);   // the copies still in flight land before the block leaves
         }
-        if (ok) {
+        if (ok && !fault) {   // fault (test of the timeout path): nothing is issued, the accumulator wait runs out
             tc_fence_after();
             for (int tap = 0; tap < 27; tap++) {
                 int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUte
         }
     }
     ok = !__syncthreads_or(!ok);
-    bool done = ok && mbar_wait_for(mb_acc, 0, kTcBudget);
+    bool done = ok && mbar_wait_for(mb_acc, 0, fault ? (1ll << 21) : kTcBudget);
     done = !__syncthreads_or(!done);
     tc_fence_after();
     if (done) {
@@ -1229,8 +1230,12 @@ cudaError_t conv_launch_halo(const bf16 *in, int CK, const bf16 *W, const float 
         const char *v = std::getenv("UNET_HALO_TMA");
         return !(v && v[0] == '0');
     }();
+    static const int fault = [] {   // UNET_FAULT_WAIT=1: the accumulator waits run out (test of that path)
+        const char *v = std::getenv("UNET_FAULT_WAIT");
+        return v && v[0] == '1' ? 1 : 0;
+    }();
     k_conv3_halo<N, FLIP><<<tiles, 128, smem, s>>>(mi, in, by_tma ? 1 : 0, W, CK, bias, out, out_bf16, relu, lg, B,
-                                                   err);
+                                                   fault, err);
     return cudaGetLastError();
 }
 

@@ -355,3 +355,33 @@ def test_learned_guess_gain_measured(un, capsys):
     for k in ("interp", "learned"):
         assert ev[k]["max_rel_diff_vs_zero_guess"] < 1e-8, (k, ev[k])
     assert ev["learned"]["cycles"] < ev["zero"]["cycles"], ev
+
+
+@pytest.mark.gpu
+def test_tensor_core_wait_timeout_reports_code_4():
+    """A convolution whose accumulator never completes (UNET_FAULT_WAIT=1:
+    the issuing thread issues no MMA and no commit, so nothing is in flight)
+    gives up after its clock budget, frees its tensor memory, and the call
+    returns 4 instead of hanging; the flag is read once per process, so the
+    check runs in a child process."""
+    import os
+    import subprocess
+    import sys
+    import textwrap
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = textwrap.dedent("""
+        import sys
+        import numpy as np, torch
+        sys.path.insert(0, %r)
+        from paper_2001_02327_gb300 import unet as U
+        u = U.mg_unet_create(16, 1, seed=1)
+        x = torch.zeros((1, 16, 16, 16), dtype=torch.float64, device="cuda")
+        try:
+            U.mg_unet_forward(u, 1, 16, x, x, x, np.ones(1))
+            print("NO ERROR")
+        except U.UNetError as e:
+            print("ERROR", e)
+    """ % root)
+    env = dict(os.environ, UNET_FAULT_WAIT="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600, cwd=root)
+    assert "failed with code 4" in r.stdout, (r.stdout, r.stderr[-2000:])
