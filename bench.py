@@ -789,14 +789,15 @@ def run_scale_case(args):
     from paper_2001_02327_gb300 import build
     build.build()
     from paper_2001_02327_gb300 import mg
-    H = I.config_3d_spheres(args.level_n if args.level_n != 254 else 256, 4, 8)
+    H = I.config_3d_spheres(args.level_n if args.level_n != 254 else 256, args.scale_levels, 8)
     inp = I.level_inputs(H)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     d_in = [{k: dev(v) for k, v in d.items()} for d in inp]
     n = H.n[0]
     F = [torch.empty((3,) + (m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
     P = [torch.empty((m,) * 3, dtype=torch.float64, device="cuda") for m in H.n]
-    for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+    forms = [f for f in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)) if f[0] in args.forms.split(",")]
+    for name, prec in forms:
         h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=NU[0], nu_post=NU[1], max_cycles=60,
                                                                  rel_tol=TOL, precision=prec,
                                                                  inner_cycles=args.inner_cycles,
@@ -832,7 +833,7 @@ def run_scale_case(args):
                 ep = max(ep, float(np.max(np.abs(P[l].cpu().numpy() - pa)) / np.max(np.abs(pa))))
                 ef = max(ef, float(np.max(np.abs(np.moveaxis(F[l].cpu().numpy(), 0, -1) - fa)) / np.max(np.abs(fa))))
             t = statistics.median(ms)
-            print(json.dumps({"case": f"4 nested {n}^3 levels, 8 spheres", "form": name, "zones": H.zones(),
+            print(json.dumps({"case": f"{H.num_levels} nested {n}^3 levels, 8 spheres", "form": name, "zones": H.zones(),
                               "ms_per_solve": t, "zones_per_s": H.zones() / (t * 1e-3),
                               "cycles_per_level": [st[0][l]["cycles"] for l in range(H.num_levels)],
                               "max_rel_res": max(st[0][l]["rel_res"] for l in range(H.num_levels)),
@@ -1110,6 +1111,8 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--level-n", type=int, default=254)
+    ap.add_argument("--forms", default="fp64,mixed", help="scale case: the forms to run, from fp64,mixed")
+    ap.add_argument("--scale-levels", type=int, default=4, help="scale case: nested levels (4: the workload)")
     ap.add_argument("--cycles", type=int, default=2)
     ap.add_argument("--tune-cache", default=None,
                     help="file for the mixed form's launch plan: read if present, written after tuning")

@@ -181,6 +181,14 @@ __global__ void __launch_bounds__(256) kx_smooth(T *__restrict__ phi, const T *_
 // per-cell form with the ghost rule folded in.
 // Threads run over (row, group of four) linearly -- q groups per row, no
 // idle threads at row ends -- the row and plane found by FastDiv.
+// Loads that a colour pass makes of data it does not touch again before
+// other data has passed through L2 (the other colour's potential, this
+// colour's right-hand side): streaming, evict-first, so that the colour this
+// pass writes -- the next pass's input -- stays in L2.
+__device__ __forceinline__ float4 ld_stream4(const float *p)
+{
+    return __ldcs(reinterpret_cast<const float4 *>(p));
+}
 template <int DIM>
 __global__ void __launch_bounds__(256) kx_smooth32(float *__restrict__ phi, const float *__restrict__ f, BoxGeom g,
                                                    int colour, unsigned total, int q, FastDiv dq, FastDiv dny)
@@ -200,17 +208,17 @@ __global__ void __launch_bounds__(256) kx_smooth32(float *__restrict__ phi, cons
     const float *o = phi + (colour ^ 1) * g.half + row;
     float *own = phi + colour * g.half + row;
     const float *fr = f + colour * g.half + row;
-    const float4 c = *reinterpret_cast<const float4 *>(o + m0);
-    const float s = par ? o[m0 + 4] : o[m0 - 1];
-    const float4 yd = *reinterpret_cast<const float4 *>(o + m0 - g.H);
-    const float4 yu = *reinterpret_cast<const float4 *>(o + m0 + g.H);
+    const float4 c = ld_stream4(o + m0);
+    const float s = __ldcs(par ? o + m0 + 4 : o + m0 - 1);
+    const float4 yd = ld_stream4(o + m0 - g.H);
+    const float4 yu = ld_stream4(o + m0 + g.H);
     float4 zd = make_float4(0.f, 0.f, 0.f, 0.f), zu = zd;
     if (DIM == 3) {
         const int pl = g.E[1] * g.H;
-        zd = *reinterpret_cast<const float4 *>(o + m0 - pl);
-        zu = *reinterpret_cast<const float4 *>(o + m0 + pl);
+        zd = ld_stream4(o + m0 - pl);
+        zu = ld_stream4(o + m0 + pl);
     }
-    const float4 fv = *reinterpret_cast<const float4 *>(fr + m0);
+    const float4 fv = ld_stream4(fr + m0);
     const float xl[4] = {par ? c.x : s, par ? c.y : c.x, par ? c.z : c.y, par ? c.w : c.z};
     const float xr[4] = {par ? c.y : c.x, par ? c.z : c.y, par ? c.w : c.z, par ? s : c.w};
     const float ydv[4] = {yd.x, yd.y, yd.z, yd.w}, yuv[4] = {yu.x, yu.y, yu.z, yu.w};
@@ -304,6 +312,110 @@ __global__ void __launch_bounds__(256) kx_resid_restrict(const T *__restrict__ p
     phic[pc] = T(0);
 }
 
+// The same residual and restriction from a colour-split FP32 level 0 (its
+// ghost layer holds data: no ghost rule) whose every axis halves exactly
+// (N_a = 2 N_a^c), four coarse cells along x per thread: coarse cells
+// I0..I0+3 (I0 = 4u + 1) have fine children x = 8u+1 .. 8u+8, which with
+// their x neighbours 8u and 8u+9 are positions 4u..4u+4 of the two colour
+// arrays of each fine row -- two aligned float4 loads and two words per row
+// instead of one word per cell and neighbour.  Per cell the arithmetic is
+// that of kx_resid_restrict (per-axis pair sums times 1/h_a^2 in x, y, z
+// order, then f - (other + d0 Phi)), the child sums x pairs first, then y,
+// then z, times 2^-d.  Threads run over (coarse row, group of four) linearly.
+// Positions past a row's end read the next row (or the arrays' 16-word
+// tail); they feed only cells of coarse indices past N^c, which are not
+// stored.
+struct Row8 {     // fine cells 8u+1 .. 8u+8 of one row, in x order
+    float v[8];
+};
+
+// odd-x cells from array `od` (positions m..m+3), even-x cells from `ev`
+// (positions m+1..m+4)
+__device__ __forceinline__ Row8 load_row8(const float *od, const float *ev)
+{
+    const float4 a = ld_stream4(od), b = ld_stream4(ev);
+    const float e4 = __ldcs(ev + 4);
+    Row8 r;
+    r.v[0] = a.x; r.v[1] = b.y; r.v[2] = a.y; r.v[3] = b.z;
+    r.v[4] = a.z; r.v[5] = b.w; r.v[6] = a.w; r.v[7] = e4;
+    return r;
+}
+
+template <int DIM, bool CS>
+__global__ void __launch_bounds__(256) kx_restrict32(const float *__restrict__ phi, const float *__restrict__ f,
+                                                     BoxGeom gf, float *__restrict__ fc, float *__restrict__ phic,
+                                                     BoxGeom gc, float wk, unsigned total, int q, FastDiv dq,
+                                                     FastDiv dny)
+{
+    pdl_begin();
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const unsigned r = fdiv(dq, t);
+    const unsigned kz = DIM == 3 ? fdiv(dny, r) : 0u;
+    const int J = (int)(r - kz * (unsigned)gc.N[1]) + 1, K = DIM == 3 ? (int)kz + 1 : 0;
+    const int u = (int)(t - r * (unsigned)q);
+    const int m = 4 * u, I0 = m + 1;
+    // the array holding the odd-x cells of fine row (j, k), and the other
+    auto odd = [&](const float *a, int j, int k) {
+        return a + ((1 + j + k) & 1) * gf.half + ((long long)k * gf.E[1] + j) * gf.H + m;
+    };
+    auto even = [&](const float *a, int j, int k) {
+        return a + ((j + k) & 1) * gf.half + ((long long)k * gf.E[1] + j) * gf.H + m;
+    };
+    float sz[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); dz++) {
+        const int k = DIM == 3 ? 2 * K - 1 + dz : 0;
+        float sy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            const int j = 2 * J - 1 + dy;
+            const float *po = odd(phi, j, k), *pe = even(phi, j, k);
+            const float4 a = ld_stream4(po), b = ld_stream4(pe);
+            const float a4 = __ldcs(po + 4), b4 = __ldcs(pe + 4);
+            // x = 8u .. 8u+9
+            const float xr[10] = {b.x, a.x, b.y, a.y, b.z, a.z, b.w, a.w, b4, a4};
+            const Row8 yd = load_row8(odd(phi, j - 1, k), even(phi, j - 1, k));
+            const Row8 yu = load_row8(odd(phi, j + 1, k), even(phi, j + 1, k));
+            Row8 zd, zu;
+            if (DIM == 3) {
+                zd = load_row8(odd(phi, j, k - 1), even(phi, j, k - 1));
+                zu = load_row8(odd(phi, j, k + 1), even(phi, j, k + 1));
+            }
+            const Row8 fv = load_row8(odd(f, j, k), even(f, j, k));
+            float res[8];
+#pragma unroll
+            for (int d = 0; d < 8; d++) {
+                float other = 0.f;
+                other = other + (xr[d] + xr[d + 2]) * gf.ih2f[0];
+                other = other + (yd.v[d] + yu.v[d]) * gf.ih2f[1];
+                if (DIM == 3)
+                    other = other + (zd.v[d] + zu.v[d]) * gf.ih2f[2];
+                res[d] = fv.v[d] - (other + gf.d0f * xr[d + 1]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                float sx = 0.f;
+                sx = sx + res[2 * c];
+                sx = sx + res[2 * c + 1];
+                sy[c] = sy[c] + sx;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            sz[c] = sz[c] + sy[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        if (I0 + c > gc.N[0])
+            break;
+        const long long pc = lidx<CS>(gc, I0 + c, J, K);
+        fc[pc] = sz[c] * wk;
+        phic[pc] = 0.f;
+    }
+}
+
 // A coarse value read through the ghost rule of Sec. 2.4, applied axis after
 // axis (x, y, z) as a ghost fill would: index 0 -> -Phi_1; N+1 -> cR Phi_N,
 // or at a tie -Phi_{N-1} (+Phi_1 when N = 1).
@@ -386,37 +498,39 @@ __global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom 
     phif[lidx<FS>(gf, i, j, k)] += prolong_value<T, DIM, CS>(gf, phic, gc, cmask, i, j, k);
 }
 
-// The same on a colour-split FP32 fine level whose x axis coarsened, four
-// fine cells of one colour per thread (colour = blockIdx.y; threads over
-// (row, group of four) as in kx_smooth32).  Fine cells i = 2m + p, m in
-// m0..m0+3, take their x taps from coarse cells m and m + 1 (near: m + p),
-// so the thread reads coarse cells m0..m0+4 of each of its (up to four)
-// coarse rows once; threads next to a ghost take the per-cell form.
+// The same on a colour-split FP32 fine level whose x axis coarsened, eight
+// fine cells of a row per thread, both colours (threads over (row, group of
+// eight) linearly, as in kx_smooth32): cells x = 8u .. 8u+7 of row (j, k) --
+// the odd ones at positions 4u..4u+3 of one colour array, the even ones at
+// positions 4u..4u+3 of the other, one aligned float4 each -- take their x
+// taps from coarse cells 4u .. 4u+4 of each of the (up to four) coarse rows
+// (cell 8u+e: near 4u + (e+1)/2, far the other x neighbour), read once per
+// thread.  Coarse indices go through the ghost rule as (cell, factor) pairs,
+// so no thread leaves the common path; threads at a row's ends store cell by
+// cell.
 template <int DIM, bool CS>
-__global__ void __launch_bounds__(256) kx_prolong32(float *__restrict__ phif, BoxGeom gf, const float *__restrict__ phic,
-                                                    BoxGeom gc, int cmask, unsigned total, int q, FastDiv dq,
-                                                    FastDiv dny)
+__global__ void __launch_bounds__(256) kx_prolong8(float *__restrict__ phif, BoxGeom gf, const float *__restrict__ phic,
+                                                   BoxGeom gc, int cmask, unsigned total, int q, FastDiv dq,
+                                                   FastDiv dny)
 {
     pdl_begin();
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total)
         return;
-    const int colour = blockIdx.y;
     const unsigned r = fdiv(dq, t);
     const unsigned kz = DIM == 3 ? fdiv(dny, r) : 0u;
     const int j = (int)(r - kz * (unsigned)gf.N[1]) + 1, k = DIM == 3 ? (int)kz + 1 : 0;
-    const int par = (colour - j - k) & 1;
-    const int m0 = 4 * (int)(t - r * (unsigned)q);
-    const int i0 = 2 * m0 + par;
-    if (i0 > gf.N[0])
-        return;
-    float *own = phif + colour * gf.half + (long long)(k * gf.E[1] + j) * gf.H;
+    const int u = (int)(t - r * (unsigned)q);
+    const int x0 = 8 * u;
+    const long long rowf = ((long long)k * gf.E[1] + j) * gf.H + 4 * u;
+    float *po = phif + ((1 + j + k) & 1) * gf.half + rowf;   // cells x0+1, x0+3, x0+5, x0+7
+    float *pe = phif + ((j + k) & 1) * gf.half + rowf;       // cells x0, x0+2, x0+4, x0+6
     const bool cy = (cmask >> 1) & 1, cz = DIM == 3 && ((cmask >> 2) & 1);
     const int J0 = cy ? (j + 1) >> 1 : j, J1 = cy ? ((j & 1) ? J0 - 1 : J0 + 1) : J0;
     const int K0 = cz ? (k + 1) >> 1 : k, K1 = cz ? ((k & 1) ? K0 - 1 : K0 + 1) : K0;
     // every coarse index through the ghost rule of Sec. 2.4 as a (cell,
     // factor) pair -- factor 1 inside, so the products below are exact there
-    // and equal ghost_read's at the ghosts; no thread leaves the common path
+    // and equal ghost_read's at the ghosts
     auto gmap = [&](int a, int I, int &m) -> float {
         const int N = gc.N[a];
         if (I <= 0) {
@@ -427,7 +541,7 @@ __global__ void __launch_bounds__(256) kx_prolong32(float *__restrict__ phif, Bo
             m = I;
             return 1.0f;
         }
-        if (I > N + 1) {   // past the ghost: only cells outside the level use it
+        if (I > N + 1) {
             m = N;
             return 0.0f;
         }
@@ -451,8 +565,7 @@ __global__ void __launch_bounds__(256) kx_prolong32(float *__restrict__ phif, Bo
     }
 #pragma unroll
     for (int x = 0; x < 5; x++)
-        ci[x] = gmap(0, m0 + x, im[x]);
-    // coarse rows (J, K): 0 = (J0, K0), 1 = (J1, K0), 2 = (J0, K1), 3 = (J1, K1)
+        ci[x] = gmap(0, 4 * u + x, im[x]);
     float w[4][5];
     const int nr = DIM == 3 ? 4 : 2;
 #pragma unroll
@@ -471,15 +584,15 @@ __global__ void __launch_bounds__(256) kx_prolong32(float *__restrict__ phif, Bo
         }
     }
     const float wn = 0.75f, wf = 0.25f;
-    float nv[4];
+    float nv[8];
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
+    for (int e = 0; e < 8; e++) {
+        const int near = (e + 1) >> 1, far = (e & 1) ? near - 1 : near + 1;
         float vx[4];
 #pragma unroll
-        for (int rr = 0; rr < nr; rr++) {   // near coarse x = m0 + e + par, far = the other of e, e + 1
-            const float cn = par ? w[rr][e + 1] : w[rr][e], cf = par ? w[rr][e] : w[rr][e + 1];
-            const float a = 0.0f + wn * cn;
-            vx[rr] = a + wf * cf;
+        for (int rr = 0; rr < nr; rr++) {
+            const float a = 0.0f + wn * w[rr][near];
+            vx[rr] = a + wf * w[rr][far];
         }
         float vy0, vy1 = 0.0f;
         if (cy) {
@@ -498,20 +611,25 @@ __global__ void __launch_bounds__(256) kx_prolong32(float *__restrict__ phif, Bo
             vz = 0.0f + vy0;
         nv[e] = vz;
     }
-    if (i0 >= 1 && i0 + 6 <= gf.N[0]) {
-        float4 o = *reinterpret_cast<float4 *>(own + m0);
-        o.x += nv[0];
-        o.y += nv[1];
-        o.z += nv[2];
-        o.w += nv[3];
-        *reinterpret_cast<float4 *>(own + m0) = o;
+    if (x0 >= 1 && x0 + 7 <= gf.N[0]) {
+        float4 a = *reinterpret_cast<float4 *>(pe), b = *reinterpret_cast<float4 *>(po);
+        a.x += nv[0];
+        b.x += nv[1];
+        a.y += nv[2];
+        b.y += nv[3];
+        a.z += nv[4];
+        b.z += nv[5];
+        a.w += nv[6];
+        b.w += nv[7];
+        *reinterpret_cast<float4 *>(pe) = a;
+        *reinterpret_cast<float4 *>(po) = b;
         return;
     }
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-        const int i = i0 + 2 * e;
+    for (int e = 0; e < 8; e++) {
+        const int i = x0 + e;
         if (i >= 1 && i <= gf.N[0])
-            own[m0 + e] += nv[e];
+            ((e & 1) ? po : pe)[e >> 1] += nv[e];
     }
 }
 
@@ -992,6 +1110,33 @@ cudaError_t colour_pass(int dim, float *phi, const float *f, const BoxGeom &g, i
     return cudaGetLastError();
 }
 
+// kx_restrict32 applies: fine level 0 colour-split, every axis halving exactly
+bool restrict32_applies(int dim, const BoxGeom &gf, const BoxGeom &gc, int cmask)
+{
+    if (gf.L != 0 || cmask != (1 << dim) - 1)
+        return false;
+    for (int a = 0; a < dim; a++)
+        if (gf.N[a] != 2 * gc.N[a])
+            return false;
+    return true;
+}
+
+template <bool CS>
+cudaError_t restrict32(int dim, const float *phi, const float *f, const BoxGeom &gf, float *fc, float *phic,
+                       const BoxGeom &gc, float wk, cudaStream_t s)
+{
+    const int q = (gc.N[0] + 3) / 4;
+    const unsigned total = (unsigned)q * (unsigned)gc.N[1] * (unsigned)(dim == 3 ? gc.N[2] : 1);
+    const dim3 grid((total + 255) / 256);
+    if (dim == 3)
+        mg_launch_kernel(kx_restrict32<3, CS>, grid, dim3(256), 0, s, phi, f, gf, fc, phic, gc, wk, total, q,
+                         fast_div(q), fast_div(gc.N[1]));
+    else
+        mg_launch_kernel(kx_restrict32<2, CS>, grid, dim3(256), 0, s, phi, f, gf, fc, phic, gc, wk, total, q,
+                         fast_div(q), fast_div(gc.N[1]));
+    return cudaGetLastError();
+}
+
 // Prolongation into a colour-split FP32 fine level: four fine cells per
 // thread where the x axis coarsened, else one
 template <bool CS>
@@ -1001,14 +1146,14 @@ cudaError_t prolong32(int dim, float *phif, const BoxGeom &gf, const float *phic
     if (!(cmask & 1))
         return dim == 3 ? launch_cells(kx_prolong<float, 3, CS, true>, gf, s, phif, gf, phic, gc, cmask)
                         : launch_cells(kx_prolong<float, 2, CS, true>, gf, s, phif, gf, phic, gc, cmask);
-    const int q = ((gf.N[0] >> 1) + 4) / 4;
+    const int q = gf.N[0] / 8 + 1;   // groups x = 8u .. 8u+7 with 8u <= N_x
     const unsigned total = (unsigned)q * (unsigned)gf.N[1] * (unsigned)(dim == 3 ? gf.N[2] : 1);
-    const dim3 grid((total + 255) / 256, 2);
+    const dim3 grid((total + 255) / 256);
     if (dim == 3)
-        mg_launch_kernel(kx_prolong32<3, CS>, grid, dim3(256), 0, s, phif, gf, phic, gc, cmask, total, q, fast_div(q),
+        mg_launch_kernel(kx_prolong8<3, CS>, grid, dim3(256), 0, s, phif, gf, phic, gc, cmask, total, q, fast_div(q),
                          fast_div(gf.N[1]));
     else
-        mg_launch_kernel(kx_prolong32<2, CS>, grid, dim3(256), 0, s, phif, gf, phic, gc, cmask, total, q, fast_div(q),
+        mg_launch_kernel(kx_prolong8<2, CS>, grid, dim3(256), 0, s, phif, gf, phic, gc, cmask, total, q, fast_div(q),
                          fast_div(gf.N[1]));
     return cudaGetLastError();
 }
@@ -1039,6 +1184,14 @@ cudaError_t vcycle(const mg_box *b, const BoxPatch &P, cudaStream_t s)
         const BoxLevel &fl = P.lv[L], &cl = P.lv[L + 1];
         const T wk = (T)std::ldexp(1.0, -fl.ncoars);
         constexpr bool S = sizeof(T) == 4;   // FP32 levels colour-split, FP64 plain
+        if constexpr (S)
+            if (restrict32_applies(dim, fl.g, cl.g, fl.cmask)) {
+                e = restrict32<true>(dim, (const float *)lphi<T>(fl), (const float *)lf<T>(fl), fl.g,
+                                     (float *)lf<T>(cl), (float *)lphi<T>(cl), cl.g, (float)wk, s);
+                if (!e)
+                    e = smooth<T>(b, cl, b->opt.nu_pre, s);
+                continue;
+            }
         e = dim == 3 ? launch_cells(kx_resid_restrict<T, 3, S, S>, cl.g, s, (const T *)lphi<T>(fl),
                                     (const T *)lf<T>(fl), fl.g, lf<T>(cl), lphi<T>(cl), cl.g, fl.cmask, wk)
                      : launch_cells(kx_resid_restrict<T, 2, S, S>, cl.g, s, (const T *)lphi<T>(fl),
@@ -1286,6 +1439,8 @@ cudaError_t split_restrict(int dim, const float *phi, const float *f, const BoxG
 {
     const int cmask = (1 << dim) - 1;
     const float wk = dim == 3 ? 0.125f : 0.25f;
+    if (FS && restrict32_applies(dim, bf, bc, cmask))
+        return restrict32<CS>(dim, phi, f, bf, fc, phic, bc, wk, s);
     return dim == 3 ? launch_cells(kx_resid_restrict<float, 3, FS, CS>, bc, s, phi, f, bf, fc, phic, bc, cmask, wk)
                     : launch_cells(kx_resid_restrict<float, 2, FS, CS>, bc, s, phi, f, bf, fc, phic, bc, cmask, wk);
 }

@@ -265,8 +265,9 @@ struct MgSolveCtl {
 // Adaptive mixed mode: FP32 V-cycles of the next defect-correction step.
 // The last step took the relative residual from rel_before to rel_after in
 // `ran` V-cycles; at that per-cycle contraction, the cycles still needed to
-// reach tol, between 1 and inner_max (inner_max when the step did not
-// contract or there is no tolerance to aim at).
+// reach tol (one more after a step of fewer than four cycles), between 1 and
+// inner_max (inner_max when the step did not contract or there is no
+// tolerance to aim at).
 __host__ __device__ inline int mg_next_inner(double rel_before, double rel_after, int ran, double tol, int inner_max)
 {
     if (!(tol > 0.0) || !(rel_after > 0.0) || !(rel_after < rel_before) || ran < 1)
@@ -277,7 +278,10 @@ __host__ __device__ inline int mg_next_inner(double rel_before, double rel_after
     const double need = log(tol / rel_after) / per_cycle;          // > 0
     if (!(need < inner_max))
         return inner_max;
-    const int k = (int)ceil(need - 1e-9);   // a whole number of cycles stays whole under rounding
+    int k = (int)ceil(need - 1e-9);   // a whole number of cycles stays whole under rounding
+    if (ran < 4)   // a contraction read off fewer than four cycles (the first step's, from the
+        k += 1;    // initial guess) is faster than the steps after it: one cycle spare
+    k = k < inner_max ? k : inner_max;
     return k < 1 ? 1 : k;
 }
 

@@ -1652,24 +1652,76 @@ __device__ __forceinline__ double interp(const double *__restrict__ src, int Ep,
     return zs;
 }
 
-// One-way interface (Sec. 2.1; Sec. 2.4).
+// Storage index of the r-th cell of the two outer rings of a block of edge E
+// (E >= 5), rings enumerated so that consecutive r are consecutive ring cells:
+// first the planes k = 0, 1, E-2, E-1 (3D), then per plane between them the
+// rows j = 0, 1, E-2, E-1 and, per row between those, the four cells
+// i = 0, 1, E-2, E-1.
+template <int DIM>
+__device__ __forceinline__ void ring_cell(int r, int E, int *s)
+{
+    auto edge = [E](int q) { return q < 2 ? q : E - 4 + q; };   // 0, 1, E-2, E-1
+    int k = 0;
+    if (DIM == 3) {
+        const int P = E * E;
+        if (r < 4 * P) {
+            const int q = div_small(r, P), rem = r - q * P;
+            const int j = div_small(rem, E);
+            s[0] = rem - j * E;
+            s[1] = j;
+            s[2] = edge(q);
+            return;
+        }
+        r -= 4 * P;
+        const int M = 4 * E + 4 * (E - 4);   // ring cells of one plane between
+        const int q = div_small(r, M);
+        k = 2 + q;
+        r -= q * M;
+    }
+    s[2] = k;
+    if (r < 4 * E) {
+        const int q = div_small(r, E);
+        s[0] = r - q * E;
+        s[1] = edge(q);
+        return;
+    }
+    r -= 4 * E;
+    s[1] = 2 + (r >> 2);
+    s[0] = edge(r & 3);
+}
+
+// One-way interface (Sec. 2.1; Sec. 2.4).  With omega_done the interpolated
+// guess on Omega is k_iface_guess's and this kernel walks the rings only
+// (ring_cell), whole warps of ring cells.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__restrict__ phi_p,
                                                         const double *__restrict__ rho_p, int nc, int ox, int oy, int oz,
                                                         double *__restrict__ phi_c, double *__restrict__ rho_c,
                                                         double *__restrict__ f_c, double fourpiG, int guess,
-                                                        const double *__restrict__ guess_src, int frozen)
+                                                        const double *__restrict__ guess_src, int frozen,
+                                                        int omega_done)
 {
     pdl_begin();
     const int E = nc + 4, Ep = np + 4;
-    const int total = E * E * (DIM == 3 ? E : 1);
-    for (int t = gtid(); t < total; t += gstride()) {
+    const int all = E * E * (DIM == 3 ? E : 1);
+    const int inside = DIM == 3 ? nc * nc * nc : nc * nc;
+    const int total = omega_done ? all - inside : all;
+    for (int u = gtid(); u < total; u += gstride()) {
         int s[3];
-        const int r = div_small(t, E);
-        s[0] = t - r * E;
-        const int rq = DIM == 3 ? div_small(r, E) : 0;
-        s[1] = DIM == 3 ? r - rq * E : r;
-        s[2] = DIM == 3 ? rq : 2;
+        int t;
+        if (omega_done) {
+            ring_cell<DIM>(u, E, s);
+            if (DIM == 2)
+                s[2] = 2;
+            t = lin<DIM>(s[0], s[1], s[2], E);
+        } else {
+            t = u;
+            const int r = div_small(t, E);
+            s[0] = t - r * E;
+            const int rq = DIM == 3 ? div_small(r, E) : 0;
+            s[1] = DIM == 3 ? r - rq * E : r;
+            s[2] = DIM == 3 ? rq : 2;
+        }
         bool outer = false, inner = false;
         for (int a = 0; a < DIM; a++) {
             if (s[a] == 0 || s[a] == nc + 3)
@@ -1702,6 +1754,68 @@ __global__ void __launch_bounds__(kThreads) k_interface(int np, const double *__
             phi_c[t] = 0.0;
         else
             phi_c[t] = guess_src[lin<DIM>(s[0] - 1, s[1] - 1, DIM == 3 ? s[2] - 1 : 0, nc + 2)];
+    }
+}
+
+// The interpolated initial guess (Sec. 2.4; Appendix A) on Omega of a child
+// level: per work item the 2^d children s = 2 sigma, 2 sigma + 1 along each
+// axis, which share 3^d parent centres (off + sigma .. off + sigma + 2).  The
+// x interpolation of each parent row serves both children planes, the y
+// combination both child z planes -- about half of interp's FP64 operations
+// per cell, with interp's arithmetic per cell (x, then y, then z).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_iface_guess(int np, const double *__restrict__ phi_p, int nc, int ox,
+                                                          int oy, int oz, double *__restrict__ phi_c)
+{
+    pdl_begin();
+    const int E = nc + 4, Ep = np + 4, hc = nc / 2;
+    const int total = hc * hc * (DIM == 3 ? hc : 1);
+    constexpr int NZ = DIM == 3 ? 3 : 1;
+    for (int t = gtid(); t < total; t += gstride()) {
+        const int r = div_small(t, hc);
+        const int sx = t - r * hc;
+        const int rq = DIM == 3 ? div_small(r, hc) : 0;
+        const int sy = DIM == 3 ? r - rq * hc : r, sz = DIM == 3 ? rq : 0;
+        // parent cells off + sigma .. off + sigma + 2, sigma = s + 1
+        const int bx = ox + sx + 1, by = oy + sy + 1, bz = DIM == 3 ? oz + sz + 1 : 0;
+        double xv[NZ][3][2];   // [parent z row][parent y row][child x: even, odd]
+#pragma unroll
+        for (int pz = 0; pz < NZ; pz++)
+#pragma unroll
+            for (int py = 0; py < 3; py++) {
+                const int row = DIM == 3 ? ((bz + pz) * Ep + by + py) * Ep : (by + py) * Ep;
+                const double a = phi_p[row + bx], b = phi_p[row + bx + 1], c = phi_p[row + bx + 2];
+                const double te = 0.75, to = 0.25;   // weight of the second parent: even child, odd child
+                xv[pz][py][0] = (1.0 - te) * a + te * b;
+                xv[pz][py][1] = (1.0 - to) * b + to * c;
+            }
+#pragma unroll
+        for (int cx = 0; cx < 2; cx++)
+#pragma unroll
+            for (int cy = 0; cy < 2; cy++) {
+                const double t1 = cy ? 0.25 : 0.75;
+                double ys[NZ];
+#pragma unroll
+                for (int pz = 0; pz < NZ; pz++) {
+                    double v = 0.0;
+                    v += (1.0 - t1) * xv[pz][cy][cx];
+                    v += t1 * xv[pz][cy + 1][cx];
+                    ys[pz] = v;
+                }
+#pragma unroll
+                for (int cz = 0; cz < (DIM == 3 ? 2 : 1); cz++) {
+                    double zs = 0.0;
+                    if (DIM == 3) {
+                        const double t2 = cz ? 0.25 : 0.75;
+                        zs += (1.0 - t2) * ys[cz];
+                        zs += t2 * ys[cz + 1];
+                    } else {
+                        zs += ys[0];
+                    }
+                    const int i = 2 * (sx + 1) + cx, j = 2 * (sy + 1) + cy, k = DIM == 3 ? 2 * (sz + 1) + cz : 0;
+                    phi_c[lin<DIM>(i, j, k, E)] = zs;
+                }
+            }
     }
 }
 
@@ -2743,12 +2857,22 @@ cudaError_t mg_launch_interface(int dim, int np, const double *phi_p, const doub
                                 const double *guess_src, int frozen, cudaStream_t s)
 {
     const int grid = grid_for(cube(nc + 4, dim));
+    const int split = guess == 0;   // Omega by k_iface_guess, the rings here
     if (dim == 3)
         mg_launch_kernel(k_interface<3>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, oz, phi_c, rho_c, f_c, fourpiG, guess,
-                                                 guess_src, frozen);
+                                                 guess_src, frozen, split);
     else
         mg_launch_kernel(k_interface<2>, grid, kThreads, 0, s, np, phi_p, rho_p, nc, ox, oy, 0, phi_c, rho_c, f_c, fourpiG, guess,
-                                                 guess_src, frozen);
+                                                 guess_src, frozen, split);
+    if (cudaError_t e = cudaGetLastError())
+        return e;
+    if (split) {
+        const int g2 = grid_for(cube(nc / 2, dim));
+        if (dim == 3)
+            mg_launch_kernel(k_iface_guess<3>, g2, kThreads, 0, s, np, phi_p, nc, ox, oy, oz, phi_c);
+        else
+            mg_launch_kernel(k_iface_guess<2>, g2, kThreads, 0, s, np, phi_p, nc, ox, oy, 0, phi_c);
+    }
     return cudaGetLastError();
 }
 

@@ -13,8 +13,10 @@ CUDA_INC = "/usr/local/cuda/include"
 
 CASES = [
     # rel_before, rel_after, ran, tol, inner_max, expected
-    (1.0, 1e-3, 3, 1e-10, 8, 7),        # 0.1 per cycle: seven more cycles reach 1e-10
-    (1.0, 2e-3, 3, 1e-10, 12, 9),       # 0.126 per cycle: 8.1 cycles -> 9
+    (1.0, 1e-3, 3, 1e-10, 8, 8),        # 0.1 per cycle: seven more cycles reach 1e-10, one spare after 3
+    (1.0, 2e-3, 3, 1e-10, 12, 10),      # 0.126 per cycle: 8.1 cycles -> 9, one spare
+    (1.0, 1e-3, 4, 1e-10, 12, 10),      # 0.178 per cycle over 4 cycles: 9.33 cycles -> 10, no spare
+    (1e-4, 1e-7, 3, 1e-10, 8, 4),       # 0.1 per cycle: 3 cycles, one spare
     (1.0, 1e-3, 3, 1e-10, 5, 5),        # the cap
     (1.0, 0.125, 3, 1e-10, 8, 8),       # slow contraction: the cap
     (1e-3, 1e-3, 3, 1e-10, 8, 8),       # no contraction: the cap
