@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(256) kx_prolong(T *__restrict__ phif, BoxGeom 
 // so no thread leaves the common path; threads at a row's ends store cell by
 // cell.
 template <int DIM, bool CS>
-__global__ void __launch_bounds__(256) kx_prolong8(float *__restrict__ phif, BoxGeom gf, const float *__restrict__ phic,
+__global__ void __launch_bounds__(256, 4) kx_prolong8(float *__restrict__ phif, BoxGeom gf, const float *__restrict__ phic,
                                                    BoxGeom gc, int cmask, unsigned total, int q, FastDiv dq,
                                                    FastDiv dny)
 {
@@ -531,26 +531,13 @@ __global__ void __launch_bounds__(256) kx_prolong8(float *__restrict__ phif, Box
     // every coarse index through the ghost rule of Sec. 2.4 as a (cell,
     // factor) pair -- factor 1 inside, so the products below are exact there
     // and equal ghost_read's at the ghosts
-    auto gmap = [&](int a, int I, int &m) -> float {
+    auto gmap = [&](int a, int I, int &m) -> float {   // selects, no branches
         const int N = gc.N[a];
-        if (I <= 0) {
-            m = 1;
-            return -1.0f;
-        }
-        if (I <= N) {
-            m = I;
-            return 1.0f;
-        }
-        if (I > N + 1) {
-            m = N;
-            return 0.0f;
-        }
-        if (gc.tie[a]) {
-            m = N >= 2 ? N - 1 : 1;
-            return N >= 2 ? -1.0f : 1.0f;
-        }
-        m = N;
-        return gc.cRf[a];
+        const bool lo = I <= 0, in = I <= N, gh = I == N + 1, tie = gc.tie[a] != 0;
+        const int mg = tie ? (N >= 2 ? N - 1 : 1) : N;                 // the ghost's cell
+        const float fg = tie ? (N >= 2 ? -1.0f : 1.0f) : gc.cRf[a];   // and its factor
+        m = lo ? 1 : (in ? I : (gh ? mg : N));
+        return lo ? -1.0f : (in ? 1.0f : (gh ? fg : 0.0f));   // past the ghost: only cells outside use it
     };
     int jm[2], km[2], im[5];
     float cj[2], ck[2], ci[5];

@@ -745,6 +745,184 @@ __global__ void __launch_bounds__(128) k_conv3_halo(const __grid_constant__ CUte
         atomicExch(err, 1);
 }
 
+// The halo convolution as a persistent kernel: each block loads all 27 taps'
+// weights once and then walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// with two halo buffers and two TMEM accumulators, so that the TMA of tile
+// i + 2 and the MMAs of tile i + 1 run while the block stores tile i.  Thread
+// 0 issues every copy and product; the mbarriers of buffer s (halo arrived,
+// accumulator complete) complete once per tile on that buffer, the k-th time
+// with parity k & 1, and a phase is always waited for before the next copy or
+// product on that buffer is issued.  Every wait is bounded; on a timeout the
+// block stops issuing, waits (bounded) for what it has in flight, frees its
+// TMEM and raises *err.
+template <int N, bool FLIP>
+__global__ void __launch_bounds__(128) k_conv3_halo_p(const __grid_constant__ CUtensorMap tm_in,
+                                                      const bf16 *__restrict__ W, int CK,
+                                                      const float *__restrict__ bias, void *__restrict__ out,
+                                                      int out_bf16, int relu, int lg, int ntiles, int fault,
+                                                      int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[4];   // 0, 1: halo of buffer s arrived; 2, 3: accumulator s complete
+    __shared__ uint32_t tslot;
+    constexpr int NCOL = N < 32 ? 32 : N;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, N);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nk8 = CK >> 3;
+    const uint32_t hbytes = (uint32_t)(nk8 * kHaloChunk);
+    const uint32_t halo0 = smem_u32(smem), wts = halo0 + 2 * hbytes;
+    const int n = 1 << lg;
+    const int tx = n >> 3, ty = (n + 15) >> 4;
+    if (warp == 0) {
+        tc_alloc(smem_u32(&tslot), 2 * NCOL);
+        tc_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 4; q++)
+            mbar_init1(smem_u32(&mbar[q]));
+        fence_mbar_init();
+    }
+    for (int e = tid; e < 27 * N * nk8; e += 128) {
+        const int k8 = e % nk8, row = e / nk8;   // row = tap * N + output channel
+        const int tap = row / N, nn = row - tap * N;
+        cp16(wts + ((tap * nk8 + k8) * N + nn) * 16, W + (size_t)row * CK + 8 * k8, true);
+    }
+    cp_commit();
+    cp_wait<0>();
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int first = blockIdx.x, stride = gridDim.x;
+    const int nt = first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0;
+    auto coords = [&](int i, int &x0, int &y0, int &z0, int &b) {
+        int t = first + i * stride;
+        x0 = (t % tx) * 8;
+        t /= tx;
+        y0 = (t % ty) * 16;
+        t /= ty;
+        z0 = t % n;
+        b = t / n;
+    };
+    auto load = [&](int i) {   // thread 0: the halo of tile i into buffer i & 1
+        int x0, y0, z0, b;
+        coords(i, x0, y0, z0, b);
+        const uint32_t mb = smem_u32(&mbar[i & 1]), dst = halo0 + (uint32_t)(i & 1) * hbytes;
+        mbar_expect_tx(mb, (uint32_t)(nk8 * kHaloRows * 16));
+        for (int k8 = 0; k8 < nk8; k8++)
+            tma_load5(dst + k8 * kHaloChunk, &tm_in, 8 * k8, x0 - 1, y0 - 1, z0 - 1, b, mb);
+    };
+    auto issue = [&](int i) {   // thread 0: the 27 taps' products of tile i into accumulator i & 1
+        const uint32_t hb = halo0 + (uint32_t)(i & 1) * hbytes, d = tmem + (uint32_t)((i & 1) * NCOL);
+        tc_fence_after();
+        for (int tap = 0; tap < 27; tap++) {
+            int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            if (FLIP) {
+                dz = -dz;
+                dy = -dy;
+                dx = -dx;
+            }
+            const uint32_t a0 = hb + (uint32_t)((((dz + 1) * 18 + dy + 1) * 10 + dx + 1) * 16);
+            for (int k = 0; k < CK / 16; k++)
+                tc_mma(d, tc_sdesc(a0 + 2 * k * kHaloChunk, kHaloChunk, 160),
+                       tc_sdesc(wts + (tap * nk8 + 2 * k) * N * 16, N * 16, 128), IDESC,
+                       (tap > 0 || k > 0) ? 1u : 0u);
+        }
+        tc_commit(smem_u32(&mbar[2 + (i & 1)]));
+    };
+    // thread 0's count of tiles whose copies were issued / waited for and
+    // whose products were issued (for the exit after a timeout)
+    int tma_issued = 0, tma_waited = 0, mma_issued = 0;
+    bool ok = true;
+    if (tid == 0 && nt > 0) {
+        load(0);
+        tma_issued = 1;
+        if (nt > 1) {
+            load(1);
+            tma_issued = 2;
+        }
+        ok = mbar_wait_for(smem_u32(&mbar[0]), 0, kTcBudget);
+        if (ok) {
+            tma_waited = 1;
+            if (!fault) {   // fault (test of the timeout path): nothing is issued, the accumulator wait runs out
+                issue(0);
+                mma_issued = 1;
+            }
+        }
+    }
+    ok = !__syncthreads_or(!ok);
+    int i = 0;
+    for (; ok && i < nt; i++) {
+        const int s = i & 1;
+        bool good = true;
+        if (tid == 0 && i + 1 < nt) {
+            good = mbar_wait_for(smem_u32(&mbar[(i + 1) & 1]), ((i + 1) >> 1) & 1, kTcBudget);
+            if (good) {
+                tma_waited = i + 2;
+                if (!fault) {
+                    issue(i + 1);
+                    mma_issued = i + 2;
+                }
+            }
+        }
+        good = good && mbar_wait_for(smem_u32(&mbar[2 + s]), (i >> 1) & 1, fault ? (1ll << 21) : kTcBudget);
+        if (__syncthreads_or(!good)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0 && i + 2 < nt) {   // buffer s is free: the products of tile i have completed
+            load(i + 2);
+            tma_issued = i + 3;
+        }
+        tc_fence_after();
+        int x0, y0, z0, b;
+        coords(i, x0, y0, z0, b);
+        const int x = x0 + (tid & 7), y = y0 + (tid >> 3);
+        const bool mine = y < n;
+        const size_t r = ((((size_t)b * n + z0) * n + y) * n + x);
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * NCOL);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc_ld16(lane_base + c0, v);
+            if (bias)
+#pragma unroll
+                for (int q = 0; q < 16; q++)
+                    v[q] += bias[c0 + q];
+            if (relu)
+#pragma unroll
+                for (int q = 0; q < 16; q++)
+                    v[q] = fmaxf(v[q], 0.f);
+            if (!mine)
+                continue;
+            if (out_bf16) {
+                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(out) + r * N + c0);
+                o[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                o[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
+            } else {
+                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + r * N + c0);
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();   // accumulator s read by every thread before tile i + 2's products
+    }
+    if (!ok && tid == 0) {   // what is still in flight lands before the block leaves
+        for (int j = tma_waited; j < tma_issued; j++)
+            mbar_wait_for(smem_u32(&mbar[j & 1]), (j >> 1) & 1, kTcBudget);
+        for (int j = i; j < mma_issued; j++)
+            mbar_wait_for(smem_u32(&mbar[2 + (j & 1)]), (j >> 1) & 1, kTcBudget);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc_dealloc(tmem, 2 * NCOL);
+    if (!ok && tid == 0)
+        atomicExch(err, 1);
+}
+
 // FP32 -> BF16 (round to nearest even), 8 values per thread
 __global__ void k_to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, long n8)
 {
@@ -1199,6 +1377,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
+// the persistent halo kernel with UNET_HALO_P=1 (measured as fast as the
+// one-tile-per-block kernel at 4 x 64^3: 0.996 vs 0.989 ms a forward pass)
+bool use_persistent_halo()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("UNET_HALO_P");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
 // the halo kernel applies when all 27 taps' weights fit beside the halo and
 // the grid has at least 8 cells per edge
 bool halo_applies(int CK, int N, int lg) { return 27 * N * CK * 2 <= 64 * 1024 && lg >= 3 && CK <= 64; }
@@ -1234,6 +1423,44 @@ cudaError_t conv_launch_halo(const bf16 *in, int CK, const bf16 *W, const float 
         const char *v = std::getenv("UNET_FAULT_WAIT");
         return v && v[0] == '1' ? 1 : 0;
     }();
+    if (by_tma && use_persistent_halo()) {
+        // persistent form: as many blocks as fit on the SMs at once, but never
+        // more per SM than TMEM holds (each block keeps two accumulators of
+        // NCOL columns allocated for its whole life; a block that could not
+        // allocate would wait for one that never leaves)
+        constexpr int NCOL = N < 32 ? 32 : N;
+        constexpr int tmem_blocks = 512 / (2 * NCOL);
+        size_t psmem = 2 * (size_t)(CK / 8) * kHaloChunk + (size_t)27 * (CK / 8) * N * 16;
+        const size_t floor_smem = 233472 / (tmem_blocks + 1);   // more than 1/(t+1) of an SM's shared memory
+        if (psmem < floor_smem)
+            psmem = floor_smem;
+        static cudaError_t pattr = [] {   // all of the SM's shared memory for several blocks
+            cudaError_t e = cudaFuncSetAttribute(k_conv3_halo_p<N, FLIP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (!e)
+                e = cudaFuncSetAttribute(k_conv3_halo_p<N, FLIP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+            return e;
+        }();
+        if (pattr)
+            return pattr;
+        int per_sm = 0, dev = 0, nsm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3_halo_p<N, FLIP>, 128, psmem);
+        if (!e)
+            e = cudaGetDevice(&dev);
+        if (!e)
+            e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e)
+            return e;
+        // with one block per SM a block's tiles run one after another with
+        // little to overlap: the one-tile-per-block kernel is faster there
+        if (psmem <= 200 * 1024 && per_sm >= 2 && per_sm <= tmem_blocks) {
+            const int grid = std::min(tiles, per_sm * nsm);
+            k_conv3_halo_p<N, FLIP><<<grid, 128, psmem, s>>>(mi, W, CK, bias, out, out_bf16, relu, lg, tiles, fault,
+                                                             err);
+            return cudaGetLastError();
+        }
+    }
     k_conv3_halo<N, FLIP><<<tiles, 128, smem, s>>>(mi, in, by_tma ? 1 : 0, W, CK, bias, out, out_bf16, relu, lg, B,
                                                    fault, err);
     return cudaGetLastError();

@@ -358,12 +358,15 @@ def test_learned_guess_gain_measured(un, capsys):
 
 
 @pytest.mark.gpu
-def test_tensor_core_wait_timeout_reports_code_4():
+@pytest.mark.parametrize("persistent", ["0", "1"])
+def test_tensor_core_wait_timeout_reports_code_4(persistent):
     """A convolution whose accumulator never completes (UNET_FAULT_WAIT=1:
     the issuing thread issues no MMA and no commit, so nothing is in flight)
     gives up after its clock budget, frees its tensor memory, and the call
-    returns 4 instead of hanging; the flag is read once per process, so the
-    check runs in a child process."""
+    returns 4 instead of hanging -- with the one-tile-per-block halo kernel
+    and with the persistent one (UNET_HALO_P=1), which also waits for the
+    halo copies it has in flight before it leaves; the flags are read once
+    per process, so the check runs in a child process."""
     import os
     import subprocess
     import sys
@@ -382,6 +385,53 @@ def test_tensor_core_wait_timeout_reports_code_4():
         except U.UNetError as e:
             print("ERROR", e)
     """ % root)
-    env = dict(os.environ, UNET_FAULT_WAIT="1")
+    env = dict(os.environ, UNET_FAULT_WAIT="1", UNET_HALO_P=persistent)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600, cwd=root)
     assert "failed with code 4" in r.stdout, (r.stdout, r.stderr[-2000:])
+
+
+@pytest.mark.gpu
+def test_persistent_halo_kernel_equals_per_tile_kernel(tmp_path):
+    """The persistent halo convolution (weights loaded once per block, two
+    halo buffers and two accumulators, several tiles per block at 64^3) and
+    the one-tile-per-block kernel issue the same products in the same order:
+    the forward output is equal bit for bit, the loss and the gradients up to
+    the order of their atomic FP32 sums.  The kernel choice is read once per
+    process, so each form runs in a child process."""
+    import os
+    import subprocess
+    import sys
+    import textwrap
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = textwrap.dedent("""
+        import sys
+        import numpy as np, torch
+        sys.path.insert(0, %r)
+        from paper_2001_02327_gb300 import unet as U
+        n, B = 64, 1
+        rng = np.random.default_rng(2024)
+        a = [rng.standard_normal((B, n, n, n)) for _ in range(4)]
+        dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        u = U.mg_unet_create(n, B, seed=9)
+        try:
+            y = U.mg_unet_forward(u, B, n, dev(a[0]), dev(a[1]), dev(a[2]), np.full(B, 0.3))
+            loss = U.mg_unet_train_step(u, B, n, dev(a[0]), dev(a[1]), dev(a[2]), dev(a[3]), np.full(B, 0.3),
+                                        update=False)
+            g = U.mg_unet_get_grad(u)
+        finally:
+            U.mg_unet_destroy(u)
+        np.savez(sys.argv[1], y=np.asarray(y), g=np.asarray(g), loss=np.asarray(loss))
+    """ % root)
+    out = {}
+    for mode in ("0", "1"):
+        env = dict(os.environ, UNET_HALO_P=mode)
+        f = str(tmp_path / f"p{mode}.npz")
+        r = subprocess.run([sys.executable, "-c", code, f], env=env, capture_output=True, text=True, timeout=600,
+                           cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out[mode] = np.load(f)
+    assert np.array_equal(out["0"]["y"], out["1"]["y"])
+    assert abs(float(out["1"]["loss"]) / float(out["0"]["loss"]) - 1) < 1e-6
+    g0, g1 = out["0"]["g"].astype(np.float64), out["1"]["g"].astype(np.float64)
+    assert _rel(g1, g0) < 1e-5, _rel(g1, g0)
+    assert np.isfinite(out["1"]["y"]).all() and np.abs(g1).max() > 0
