@@ -4,12 +4,16 @@ configuration bench.py times.
 - The uneven batch of 512 hierarchies (mixed precision, one graph launch):
   sampled hierarchies against the CPU oracle (FP64), within the bar of the
   non-FP64 forms (1e-2 of the discretisation error) and to 1e-7 relative.
-- The 4 nested 256^3 levels with 8 spheres, too large for the oracle:
+- The 4 nested 256^3 levels with 8 spheres, whose converged solve takes the
+  oracle minutes: three fixed V-cycles per level against the oracle element
+  by element (FP64 to 1e-12, mixed within FP32 rounding), and, converged,
   properties every correct result has at any size, checked on sampled cells
   from the returned potential on the host -- the 7-point equation holds, the
   forces are Eq. 2 of the potential, FP64 and mixed agree, and the error
   against the closed form falls from 128^3 to 256^3.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -93,7 +97,10 @@ def test_batch_of_512_sampled_against_oracle(mg, oracle):
         mg.mg_destroy(h)
 
 
+@functools.lru_cache(maxsize=2)
 def _spheres(n):
+    """The scale workload's hierarchy and inputs (built once per module: the
+    host-side generation takes most of a minute at 256^3)."""
     H = I.config_3d_spheres(n, 4, 8)
     return H, I.level_inputs(H)
 
@@ -158,3 +165,39 @@ def test_scale_config_properties(mg):
     r128 = _solve_spheres(mg, H128, inp128, mg.MG_FP64)
     e256, e128 = _sampled_error(H, r64), _sampled_error(H128, r128)
     assert e256[0] < e128[0] / 2.5 and e256[1] < e128[1] / 2.5, (e128, e256)
+
+
+def test_scale_config_fixed_cycles_against_oracle(mg, oracle):
+    """The 4 nested 256^3 levels at full size against the oracle, three
+    V(2,2) cycles per level from the interpolated guess (the oracle runs them
+    in about half a minute on one core): the FP64 path equals it element by
+    element on every level (potential and forces within 1e-12 relative), and
+    the mixed path in the launch plan bench.py times (mg_autotune: the 258^3
+    multigrid level colour-split, its restriction, prolongation and smoothing
+    kernels) -- three FP32 V-cycles in one correction step -- within FP32
+    rounding of the correction (1e-5 relative on the potential, 1e-4 on the
+    forces, whose differences amplify it)."""
+    import torch
+    H, inp = _spheres(256)
+    ref = oracle.solve_hierarchy(H, inp, 2, 2, 3, 0.0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for prec, tp, tf in ((mg.MG_FP64, 1e-12, 1e-12), (mg.MG_MIXED, 1e-5, 1e-4)):
+        h = mg.mg_create_hierarchy([mg.desc_from(H)], mg.options(nu_pre=2, nu_post=2, max_cycles=3, rel_tol=0.0,
+                                                                 precision=prec, inner_cycles=3))
+        try:
+            if prec == mg.MG_MIXED:
+                mg.mg_autotune(h, None)
+                assert mg.mg_tuning(h, 0, 0)[0][0] == 65536   # the 258^3 level colour-split
+            mg.mg_set_density(h, 0, 0, dev(inp[0]["rho"]), dev(inp[0]["bc_rho"]), dev(inp[0]["bc_phi"]))
+            for l in range(1, 4):
+                mg.mg_set_density(h, 0, l, dev(inp[l]["rho"]))
+            _, st = mg.mg_solve(h, 1, allow_noconv=True)
+            for l in range(4):
+                assert st[0][l]["cycles"] == 3 == ref[l]["cycles"], (prec, l)
+                n = H.n[l]
+                phi, F = _read(mg, h, 0, H, l)
+                rphi = ref[l]["phi"][(slice(2, n + 2),) * 3]
+                assert _relmax(phi, rphi) < tp, (prec, l, _relmax(phi, rphi))
+                assert _relmax(F, ref[l]["F"]) < tf, (prec, l, _relmax(F, ref[l]["F"]))
+        finally:
+            mg.mg_destroy(h)
