@@ -637,7 +637,7 @@ double cells_d(int N, int dim) { return dim == 3 ? (double)N * N * N : (double)N
 // sweeps red-black sweeps on level L; ctl != NULL: the last launch also
 // counts one V-cycle of an adaptive step's nested loop (condition hi)
 cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int sweeps, cudaStream_t s,
-                   MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0)
+                   MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0, bool red_done = false)
 {
     const int dim = h->dim;
     const MgGeom &g = ld.g[L];
@@ -647,6 +647,8 @@ cudaError_t smooth(mg_hierarchy *h, const LevelData &ld, int L, bool fp32, int s
     const double bytes = (split ? 1.5 : 2.0) * (fp32 ? 4 : 8) * cells_d(g.N, dim);   // read Phi, read/write one colour
     for (int sw = 0; sw < sweeps; sw++)
         for (int c = 0; c < 2; c++) {
+            if (red_done && sw == 0 && c == 0)
+                continue;   // the restriction into this level did the first red half-sweep
             // the finest multigrid level is profiled apart from the coarser ones
             const bool last = sw == sweeps - 1 && c == 1;
             cudaError_t e = timed(h, L == 0 ? KK_SMOOTH0 : KK_SMOOTH, bytes, [&] {
@@ -730,7 +732,10 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
     for (int cyc = 0; cyc < ncyc; cyc++) {
     // descent: at each level above Lstop, nu_pre sweeps then residual and
     // restriction (steps 2/6, 4, 5) -- one temporally blocked kernel per
-    // level in FP32 when the level has a tile, else one kernel per phase
+    // level in FP32 when the level has a tile, else one kernel per phase.
+    // A plain restriction into a level smoothed next by one kernel per phase
+    // also does that level's first red half-sweep (red_done).
+    bool red_done = false;
     for (int L = 0; L < Lstop; L++) {
         const double nf = cells_d(ld.g[L].N, dim), nc = cells_d(ld.g[L + 1].N, dim);
         if (fp32 && ld.tile[L] < 0) {
@@ -758,16 +763,21 @@ cudaError_t vcycle(mg_hierarchy *h, const LevelData &ld, bool fp32, cudaStream_t
                 return e;
             continue;
         }
-        if ((e = smooth(h, ld, L, fp32, o.nu_pre, s)))
+        if ((e = smooth(h, ld, L, fp32, o.nu_pre, s, nullptr, 0, red_done)))
             return e;
+        const bool split_here = fp32 && L < ld.nsplit;
+        const bool fuse = !split_here && o.nu_pre >= 1 && L + 1 < Lstop && !(fp32 && ld.tile[L + 1] != 0) &&
+                          !(fp32 && L + 1 < ld.nsplit);
         e = timed(h, KK_RESTRICT, 2.0 * w * (nf + nc), [&] {
-            if (fp32 && L < ld.nsplit)
+            if (split_here)
                 return mg_split_resid_restrict(dim, ld.phi32[L], ld.f32[L], ld.g[L], ld.phi32[L + 1], ld.f32[L + 1],
                                                ld.g[L + 1], s);
-            return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s);
+            return mg_launch_resid_restrict(dim, fp32, P(L), F(L), ld.g[L], P(L + 1), F(L + 1), ld.g[L + 1], s,
+                                            fuse);
         });
         if (e)
             return e;
+        red_done = fuse;
     }
     if ((e = clu ? cluster(1) : bottom()))                                                // steps 6-11, L >= Lstop
         return e;

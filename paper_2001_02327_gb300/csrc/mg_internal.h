@@ -180,8 +180,11 @@ cudaError_t mg_launch_wave(const float *phi_in, float *phi_out, const float *f, 
                            int zchunks, cudaStream_t s, MgSolveCtl *ctl = nullptr, cudaGraphConditionalHandle hi = 0,
                            int *err = nullptr, int fault = 0);
 
+// red_first: also the coarse level's first red half-sweep (the V-cycle then
+// starts that level's pre-smoothing with black; nu_pre >= 1 only)
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
-                                     void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s);
+                                     void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s,
+                                     bool red_first = false);
 cudaError_t mg_launch_prolong(int dim, bool fp32, const void *phi_c, const MgGeom &gc, void *phi_f, const MgGeom &gf,
                               cudaStream_t s);
 

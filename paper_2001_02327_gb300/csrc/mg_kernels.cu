@@ -404,17 +404,33 @@ __global__ void __launch_bounds__(kThreads) k_smooth_colour_counted(T *__restric
     op_smooth_colour<T, DIM>(phi, f, g, colour, gtid(), gstride());
 }
 
+// Ghost-rule class of cell (i, j, k) of a coarse multigrid level, as
+// neighbour_sum_ptr forms it: per axis bit 0 at index 1, bit 1 at index N.
+template <int DIM>
+__device__ __forceinline__ int cell_class(const MgGeom &g, int i, int j, int k)
+{
+    const int N = g.N;
+    auto bits = [N](int a) { return (a == 1 ? 1 : 0) | (a == N ? 2 : 0); };
+    return bits(i) | (bits(j) << 2) | (DIM == 3 ? bits(k) << 4 : 0);
+}
+
 // Residual and restriction with one fine cell per thread: 256 threads compute
 // the residuals of a fine tile (16x8x2 in 3D, 32x8 in 2D) into shared memory
 // `r` and the first of them average the children of the coarse cells of the
 // tile (8x4x1 in 3D, 16x4 in 2D).  Tile (bx, by, bz) of the level; `lt` the
 // thread's index in the tile; contains a __syncthreads (every thread of the
 // block must call it, `ok` false for threads without a tile).
+// The coarse correction starts from zero (Sec. 2.3 step 6).  With red_first
+// the first red half-sweep on the coarse level is done here as well: with
+// every black cell zero, a red cell's update is its own right-hand side times
+// the update factor, (0 - h^2 f) * neg_inv_diag, exactly what op_smooth_colour
+// computes there (its neighbour sum is +0.0), so the V-cycle skips that
+// launch and the results do not change in any bit.
 template <typename T, int DIM>
 __device__ __forceinline__ void resid_restrict_tile(const T *__restrict__ phi_f, const T *__restrict__ f_f,
                                                     const MgGeom &gf, T *__restrict__ phi_c, T *__restrict__ f_c,
                                                     const MgGeom &gc, int bx, int by, int bz, int lt, bool ok,
-                                                    T *__restrict__ r)
+                                                    T *__restrict__ r, bool red_first = false)
 {
     const int Nf = gf.N, Nc = gc.N;
     constexpr int FX = DIM == 3 ? 16 : 32, FY = 8;
@@ -438,8 +454,12 @@ __device__ __forceinline__ void resid_restrict_tile(const T *__restrict__ phi_f,
                     for (int dx = 0; dx < 2; dx++)
                         s += r[(dz * FY + 2 * cy + dy) * FX + 2 * cx + dx];
             const int pc = lin<DIM>(I, J, K, gc.E);
-            f_c[pc] = (DIM == 3 ? T(0.125) : T(0.25)) * s;
-            phi_c[pc] = T(0);
+            const T fv = (DIM == 3 ? T(0.125) : T(0.25)) * s;
+            f_c[pc] = fv;
+            T pv = T(0);
+            if (red_first && ((I + J + K) & 1) == 0)
+                pv = (T(0) - geo_h2<T>(gc) * fv) * neg_inv_diag<T, DIM>(gc, cell_class<DIM>(gc, I, J, K));
+            phi_c[pc] = pv;
         }
     }
 }
@@ -455,12 +475,12 @@ __host__ __device__ inline void resid_restrict_tiles(int dim, int Nc, int &nx, i
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(const T *__restrict__ phi_f, const T *__restrict__ f_f,
                                                              MgGeom gf, T *__restrict__ phi_c, T *__restrict__ f_c,
-                                                             MgGeom gc)
+                                                             MgGeom gc, int red_first)
 {
     pdl_begin();
     __shared__ T r[kThreads];
     resid_restrict_tile<T, DIM>(phi_f, f_f, gf, phi_c, f_c, gc, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, true,
-                                r);
+                                r, red_first != 0);
 }
 
 template <typename T, int DIM>
@@ -2756,25 +2776,26 @@ cudaError_t mg_launch_tb_post(int dim, const float *phi_in, float *phi_out, cons
 }
 
 cudaError_t mg_launch_resid_restrict(int dim, bool fp32, const void *phi_f, const void *f_f, const MgGeom &gf,
-                                     void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s)
+                                     void *phi_c, void *f_c, const MgGeom &gc, cudaStream_t s, bool red_first)
 {
+    const int rf = red_first ? 1 : 0;
     int nx, ny, nz;
     resid_restrict_tiles(dim, gc.N, nx, ny, nz);
     const dim3 grid(nx, ny, nz);
     if (dim == 3) {
         if (fp32)
             mg_launch_kernel(k_resid_restrict<float, 3>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
-                                                                 (float *)phi_c, (float *)f_c, gc);
+                                                                 (float *)phi_c, (float *)f_c, gc, rf);
         else
             mg_launch_kernel(k_resid_restrict<double, 3>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
-                                                                  (double *)phi_c, (double *)f_c, gc);
+                                                                  (double *)phi_c, (double *)f_c, gc, rf);
     } else {
         if (fp32)
             mg_launch_kernel(k_resid_restrict<float, 2>, grid, kThreads, 0, s, (const float *)phi_f, (const float *)f_f, gf,
-                                                                 (float *)phi_c, (float *)f_c, gc);
+                                                                 (float *)phi_c, (float *)f_c, gc, rf);
         else
             mg_launch_kernel(k_resid_restrict<double, 2>, grid, kThreads, 0, s, (const double *)phi_f, (const double *)f_f, gf,
-                                                                  (double *)phi_c, (double *)f_c, gc);
+                                                                  (double *)phi_c, (double *)f_c, gc, rf);
     }
     return cudaGetLastError();
 }
