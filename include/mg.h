@@ -132,8 +132,9 @@ typedef struct {
                             FP32 V-cycles in every defect-correction step; > 0 runs inner_cycles in
                             the first step and lets each later step choose its count, 1..inner_max:
                             the cycles that the per-cycle residual contraction of the step before
-                            predicts for reaching rel_tol (decided on the device, in the graph; a
-                            batch then runs as graph branches, not the opt-in batched kernels).
+                            predicts for reaching rel_tol, one more after a step of fewer than four
+                            cycles (decided on the device, in the graph; a batch then runs as graph
+                            branches or the persistent launch, not the opt-in batched kernels).
                             Not part of the paper's method, whose V-cycles are all FP64. */
 } mg_options;
 
